@@ -1,0 +1,250 @@
+"""Oracle, part 2: the worm-LBM time step on a framed 2D grid, plain numpy float64.
+TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
+
+State.  For each direction i the oracle stores the deviation
+    d_i(x) = e_i(x) - w_i e_ref,   e_ref = e_eq(T_ref)
+of the discrete directional energy density (DDED) e_i from the reference equilibrium.
+The update of Eq. lbm-energy / Eq. algorithm is linear and maps w_i e_ref to itself
+(sum_i w_i = 1), so d obeys the same update; only temperatures (Eq. pseudo-T) add e_ref
+back.  Arrays have shape (Q, Ny + 2, Nx + 2): a one-cell ghost frame holds the boundary
+(Sec. 2.6); anything outside the frame reads as zero.
+
+One step n (n = 1, 2, ...), in the order the paper applies it:
+  1. boundary conditions on the ghost frame of state n-1 (Sec. 2.6, "at every time
+     step"): adiabatic-diffuse walls, then isotropic blackbody (isothermal) walls, then
+     periodic links;
+  2. local energy E(x) = sum_i d_i(x)   (Eq. lbm-energy-density);
+  3. for every direction i with due worm hop c_i and every cell y (frame included),
+     with F = W E and the source cell s = y - c_i:
+        propagating:  d_i'(y) = (1 - W(s)) d_i(s) + w_i F(s)
+        paused:       d_i'(y) = (1 - W(y)) d_i(y) + w_i F(s)
+     (Eq. lbm-energy with e_i^eq = w_i E, read from the garbled Eq.
+     lbm-energy-weighting; Eq. algorithm for the paused DDED whose EED still hops).
+     W is the corrected weight W_corr of Eq. W-correction; ghost cells of walls have
+     W = 0 (no scattering inside a wall), periodic ghost cells copy W across the link.
+
+Readings of passages the paper leaves open (each is also listed in the design doc):
+  * per-cell W in the paused branch: the loss uses W(y), the gain uses W(s);
+  * adiabatic diffuse wall (Eq. adiabatic-diffuse, normalisation garbled): a ghost cell
+    collects A = sum of its components that do not point into the domain, zeroes them,
+    and adds A * w_i (s_i . n) / sum_k w_k (s_k . n) to each inward component i;
+    a corner between two diffuse walls uses n = the quadrant diagonal and counts as
+    inward only directions strictly inside the quadrant;
+  * corner ghost cells: a periodic link fills them; otherwise an isothermal x-wall,
+    then an isothermal y-wall, decides; two diffuse walls use the corner rule above;
+  * heat flux (Eq. q_corr) uses the nominal unit vector s_i of each direction, v_g = 1.
+
+Pins: tests/test_oracle_stepper.py (energy conservation on periodic and adiabatic
+grids, exact ballistic translation, reduction to standard D2Q8 at W = 1, the moment
+recursion, the diffusive Gaussian limit, isothermal steady profile).
+"""
+import math
+
+import numpy as np
+
+from . import lattice as L
+
+PERIODIC, ISOTHERMAL, ADIABATIC_DIFFUSE = 0, 1, 2
+XM, XP, YM, YP = 0, 1, 2, 3           # wall order: x-, x+, y-, y+
+INWARD_NORMAL = {XM: (1, 0), XP: (-1, 0), YM: (0, 1), YP: (0, -1)}
+
+
+def shift(a, c):
+    """b(y) = a(y - c) over the last two axes (y, x), zero where y - c leaves the array."""
+    cx, cy = c
+    b = np.zeros_like(a)
+    ny, nx = a.shape[-2], a.shape[-1]
+    ys_dst = slice(max(cy, 0), ny + min(cy, 0))
+    ys_src = slice(max(-cy, 0), ny + min(-cy, 0))
+    xs_dst = slice(max(cx, 0), nx + min(cx, 0))
+    xs_src = slice(max(-cx, 0), nx + min(-cx, 0))
+    b[..., ys_dst, xs_dst] = a[..., ys_src, xs_src]
+    return b
+
+
+class WormLBM:
+    """Plain FP64 worm-LBM on an nx x ny grid with Q directions."""
+
+    def __init__(self, nx, ny, q, mfp, bc_kind=(0, 0, 0, 0), t_wall=(300.0,) * 4,
+                 emulate_3d=True, relax_mode=0, t_ref=300.0, theta=L.THETA_DEFAULT,
+                 w_field=None):
+        self.nx, self.ny, self.q = nx, ny, q
+        self.bc_kind = tuple(int(k) for k in bc_kind)
+        self.t_wall = tuple(float(t) for t in t_wall)
+        if (self.bc_kind[XM] == PERIODIC) != (self.bc_kind[XP] == PERIODIC) or \
+           (self.bc_kind[YM] == PERIODIC) != (self.bc_kind[YP] == PERIODIC):
+            raise ValueError("periodic walls come in opposite pairs")
+        self.t_ref, self.theta = float(t_ref), float(theta)
+        self.dirs = L.ring_directions(q)
+        self.s_hat = L.unit_vectors(self.dirs)
+        self.w = L.angular_weights(self.dirs)
+        self.lam_corr = L.lambda_corr(self.dirs)
+        self.sched = L.TasSchedule(q)
+        self.e_ref = float(L.e_eq(self.t_ref, self.theta))
+        if w_field is not None:            # direct W (tests of the W = 1 limit, adjoint)
+            wc = np.broadcast_to(np.asarray(w_field, np.float64), (ny, nx)).copy()
+        else:
+            mfp = np.broadcast_to(np.asarray(mfp, np.float64), (ny, nx))
+            if np.any(mfp <= 0):
+                raise ValueError("MFP must be positive")
+            wc = L.relax_weight(mfp, self.lam_corr, emulate_3d, relax_mode)
+        if wc.max() > 1.0:
+            # Appendix A: the paused step is stable only for W <= 1.
+            raise ValueError("unstable: max W_corr = %g > 1" % wc.max())
+        self.w_int = wc
+        self.wf = self._frame_scalar(wc)
+        self.d = np.zeros((q, ny + 2, nx + 2))
+        self.n = 0
+
+    # ----------------------------------------------------------------- geometry
+    def _frame_scalar(self, interior):
+        """Embed an interior field in the frame: walls 0, periodic links copied."""
+        f = np.zeros((self.ny + 2, self.nx + 2))
+        f[1:-1, 1:-1] = interior
+        self._periodic_links(f[None])
+        return f
+
+    def _periodic_links(self, a):
+        """Periodic boundary of Sec. 2.6 on arrays (..., Ny+2, Nx+2): the y link first
+        (over all columns unless x is periodic too), then the x link over all rows."""
+        nx, ny = self.nx, self.ny
+        xper = self.bc_kind[XM] == PERIODIC
+        yper = self.bc_kind[YM] == PERIODIC
+        if yper:
+            xs = slice(1, nx + 1) if xper else slice(0, nx + 2)
+            a[..., 0, xs] = a[..., ny, xs]
+            a[..., ny + 1, xs] = a[..., 1, xs]
+        if xper:
+            a[..., :, 0] = a[..., :, nx]
+            a[..., :, nx + 1] = a[..., :, 1]
+
+    def _edge_cells(self, wall):
+        """Framed (Y, X) indices of a wall's ghost cells, corners excluded."""
+        nx, ny = self.nx, self.ny
+        if wall == XM:
+            return [(y, 0) for y in range(1, ny + 1)]
+        if wall == XP:
+            return [(y, nx + 1) for y in range(1, ny + 1)]
+        if wall == YM:
+            return [(0, x) for x in range(1, nx + 1)]
+        return [(ny + 1, x) for x in range(1, nx + 1)]
+
+    def _corners(self):
+        """(Y, X, x-wall, y-wall) for the four corner ghost cells."""
+        nx, ny = self.nx, self.ny
+        return [(0, 0, XM, YM), (0, nx + 1, XP, YM),
+                (ny + 1, 0, XM, YP), (ny + 1, nx + 1, XP, YP)]
+
+    # -------------------------------------------------------- boundary conditions
+    def diffuse_split(self, normal, strict_quadrant=False):
+        """Inward mask and re-emission fractions rho_i = w_i (s_i.n) / sum over inward."""
+        nxn, nyn = normal
+        dirs = np.array(self.dirs)
+        if strict_quadrant:
+            inward = (dirs[:, 0] * nxn > 0) & (dirs[:, 1] * nyn > 0)
+        else:
+            inward = (dirs[:, 0] * nxn + dirs[:, 1] * nyn) > 0
+        nrm = np.array([nxn, nyn], np.float64)
+        nrm /= np.linalg.norm(nrm)
+        cosn = self.s_hat @ nrm
+        rho = np.where(inward, self.w * cosn, 0.0)
+        rho /= rho.sum()
+        return inward, rho
+
+    def _diffuse_cell(self, yy, xx, normal, strict):
+        inward, rho = self.diffuse_split(normal, strict)
+        a = self.d[~inward, yy, xx].sum()
+        self.d[~inward, yy, xx] = 0.0
+        self.d[inward, yy, xx] += a * rho[inward]
+
+    def delta_e(self, t):
+        """e_eq(T) - e_ref in float64."""
+        return float(L.e_eq(t, self.theta)) - self.e_ref
+
+    def apply_bc(self):
+        k = self.bc_kind
+        # 1. adiabatic diffuse walls (edges), then diffuse-diffuse corners
+        for wall in (XM, XP, YM, YP):
+            if k[wall] == ADIABATIC_DIFFUSE:
+                for (yy, xx) in self._edge_cells(wall):
+                    self._diffuse_cell(yy, xx, INWARD_NORMAL[wall], False)
+        for (yy, xx, xw, yw) in self._corners():
+            if k[xw] == ADIABATIC_DIFFUSE and k[yw] == ADIABATIC_DIFFUSE:
+                n = (INWARD_NORMAL[xw][0], INWARD_NORMAL[yw][1])
+                self._diffuse_cell(yy, xx, n, True)
+        # 2. isotropic blackbody walls (Eq. isotropic): d_i = w_i (e_eq(T_w) - e_ref)
+        for wall in (XM, XP, YM, YP):
+            if k[wall] == ISOTHERMAL:
+                de = self.delta_e(self.t_wall[wall])
+                for (yy, xx) in self._edge_cells(wall):
+                    self.d[:, yy, xx] = self.w * de
+        for (yy, xx, xw, yw) in self._corners():
+            if k[xw] == PERIODIC or k[yw] == PERIODIC:
+                continue
+            if k[xw] == ISOTHERMAL:
+                self.d[:, yy, xx] = self.w * self.delta_e(self.t_wall[xw])
+            elif k[yw] == ISOTHERMAL:
+                self.d[:, yy, xx] = self.w * self.delta_e(self.t_wall[yw])
+        # 3. periodic links
+        self._periodic_links(self.d)
+
+    # ------------------------------------------------------------------- state
+    def init_temperature(self, dT):
+        """Equilibrium start (Sec. 2.4: the weights set the initial conditions):
+        e_i = w_i e_eq(T_ref + dT).  Frame cells copy their nearest interior cell."""
+        dT = np.asarray(dT, np.float64).reshape(self.ny, self.nx)
+        de = L.e_eq(self.t_ref + dT, self.theta) - self.e_ref
+        de_f = np.pad(de, 1, mode="edge")
+        self.d = self.w[:, None, None] * de_f[None]
+        self.n = 0
+
+    def set_state(self, d_framed):
+        self.d = np.array(d_framed, dtype=np.float64, copy=True)
+
+    def step(self, nsteps=1):
+        for _ in range(nsteps):
+            self._one_step()
+
+    def _one_step(self):
+        n = self.n + 1
+        self.apply_bc()
+        e_loc = self.d.sum(axis=0)                   # Eq. lbm-energy-density
+        f = self.wf * e_loc                          # scattered energy W E at each cell
+        keep = 1.0 - self.wf                         # (1 - W)
+        hops, paused = self.sched.advance(n)
+        new = np.empty_like(self.d)
+        for i in range(self.q):
+            c = L.BASIC_HOPS[hops[i]]
+            gain = self.w[i] * shift(f, c)           # EED always hops: w_i W(s) E(s)
+            if paused[i]:
+                new[i] = keep * self.d[i] + gain
+            else:
+                new[i] = shift(keep * self.d[i], c) + gain
+        self.d = new
+        self.n = n
+
+    # ---------------------------------------------------------------- moments
+    def energy_dev(self):
+        """E(x) - e_ref on the interior (Eq. lbm-energy-density)."""
+        return self.d[:, 1:-1, 1:-1].sum(axis=0)
+
+    def temperature_dev(self):
+        """T(x) - T_ref by Eq. pseudo-T, float64."""
+        e = self.e_ref + self.energy_dev()
+        return L.temperature(e, self.theta) - self.t_ref
+
+    def heat_flux(self):
+        """(q_x, q_y) by Eq. q_corr with v_g = 1 and c_i/|c_i| = s_i."""
+        di = self.d[:, 1:-1, 1:-1]
+        qx = np.tensordot(self.s_hat[:, 0], di, axes=(0, 0))
+        qy = np.tensordot(self.s_hat[:, 1], di, axes=(0, 0))
+        return qx, qy
+
+    def total_energy(self, include_frame=False):
+        """Sum of E - e_ref over the interior, or over the interior plus the ghost cells
+        that hold energy of their own (wall cells; periodic ghosts are copies)."""
+        if not include_frame:
+            return float(self.d[:, 1:-1, 1:-1].sum())
+        xs = slice(1, -1) if self.bc_kind[XM] == PERIODIC else slice(None)
+        ys = slice(1, -1) if self.bc_kind[YM] == PERIODIC else slice(None)
+        return float(self.d[:, ys, xs].sum())

@@ -1,0 +1,206 @@
+"""Pins of the oracle's time step against what the paper and the mathematics fix
+(CPU only).  None of these retypes the step: each checks a consequence computed another
+way (a lattice translation, a convolution, moment recursions, conservation)."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import lattice as L
+from oracle.stepper import WormLBM, PERIODIC, ISOTHERMAL, ADIABATIC_DIFFUSE
+
+P, I, A = PERIODIC, ISOTHERMAL, ADIABATIC_DIFFUSE
+
+
+def _rand(ny, nx, seed):
+    return np.random.default_rng(seed).standard_normal((ny, nx))
+
+
+def test_energy_conserved_on_periodic_grid():
+    """Eq. lbm-energy-density: scattering conserves energy; with periodic links the
+    grid total is constant to round-off."""
+    m = WormLBM(23, 19, 16, 3.0)
+    m.init_temperature(_rand(19, 23, 1))
+    e0 = m.total_energy()
+    scale = np.abs(m.d).sum()
+    for _ in range(60):
+        m.step()
+        assert abs(m.total_energy() - e0) <= 1e-13 * scale
+
+
+@pytest.mark.parametrize("kinds", [(A, A, A, A), (P, P, A, A), (A, A, P, P)])
+def test_energy_conserved_with_adiabatic_walls(kinds):
+    """Adiabatic walls (Sec. 2.6) neither add nor remove energy: the total over the
+    interior plus the wall cells stays constant."""
+    m = WormLBM(21, 17, 32, 2.5, bc_kind=kinds)
+    m.init_temperature(_rand(17, 21, 2))
+    m.apply_bc()
+    e0 = m.total_energy(include_frame=True)
+    scale = np.abs(m.d).sum()
+    m.step(150)
+    assert abs(m.total_energy(include_frame=True) - e0) <= 1e-13 * scale
+
+
+@pytest.mark.parametrize("kinds", [(P, P, P, P), (I, I, A, A), (A, A, A, A),
+                                   (I, I, P, P), (P, P, I, A), (A, I, I, A)])
+def test_reference_equilibrium_is_a_fixed_point(kinds):
+    """A uniform state at T_ref with all walls at T_ref stays exactly uniform: the
+    update maps w_i e_ref to itself (sum w = 1)."""
+    m = WormLBM(12, 10, 16, 2.0, bc_kind=kinds, t_wall=(300.0,) * 4)
+    m.init_temperature(np.zeros((10, 12)))
+    m.step(40)
+    assert np.abs(m.d).max() == 0.0
+
+
+@pytest.mark.parametrize("q", [8, 16, 32])
+def test_ballistic_limit_translates_each_plane_exactly(q):
+    """W = 0 (MFP -> infinity): each DDED only advects, so plane i after n steps is the
+    initial plane translated by the cumulative worm displacement p_i(n) (Sec. 2.3-2.5);
+    checked against np.roll on a periodic grid, bit for bit."""
+    nx, ny = 29, 26
+    m = WormLBM(nx, ny, q, None, w_field=0.0)
+    rng = np.random.default_rng(q)
+    d0 = np.zeros((q, ny + 2, nx + 2))
+    d0[:, 1:-1, 1:-1] = rng.standard_normal((q, ny, nx))
+    m.set_state(d0)
+    ref = L.TasSchedule(q)
+    for n in range(1, 41):
+        m.step()
+        ref.advance(n)
+        p = ref.displacement()
+        for i in range(q):
+            want = np.roll(d0[i, 1:-1, 1:-1], shift=(p[i, 1], p[i, 0]), axis=(0, 1))
+            assert np.array_equal(m.d[i, 1:-1, 1:-1], want)
+
+
+def test_w_equal_one_reduces_to_standard_d2q8():
+    """Sec. 2.3: at W = 1 only the EED evolves and the scheme is the standard D2Q8, i.e.
+    E(n+1)(y) = 1/8 sum_k E(n)(y - c_k) over the 8 basic hops (pauses included, since
+    the EED always hops)."""
+    nx, ny = 20, 18
+    m = WormLBM(nx, ny, 8, None, w_field=1.0)
+    m.init_temperature(_rand(ny, nx, 3) * 0.3)
+    e = m.energy_dev().copy()
+    for _ in range(12):
+        m.step()
+        e = sum(np.roll(e, shift=(cy, cx), axis=(0, 1)) for (cx, cy) in L.BASIC_HOPS) / 8
+        assert np.allclose(m.energy_dev(), e, rtol=0, atol=1e-15)
+
+
+def _moment_recursion(q, w_uniform, steps, m0, m1x, m1y, m2x):
+    """Per-direction spatial moments propagated in moment space: sum_x d_i, sum_x x d_i,
+    sum_x y d_i, sum_x x^2 d_i.  Translation by c shifts moments; scattering mixes
+    directions through the totals.  Independent of the field code."""
+    dirs = L.ring_directions(q)
+    w = L.angular_weights(dirs)
+    W = w_uniform
+    sched = L.TasSchedule(q)
+    out = []
+    for n in range(1, steps + 1):
+        hops, paused = sched.advance(n)
+        T0, T1x, T1y, T2x = m0.sum(), m1x.sum(), m1y.sum(), m2x.sum()
+        g0 = (1 - W) * m0 + w * W * T0
+        g1x = (1 - W) * m1x + w * W * T1x
+        g1y = (1 - W) * m1y + w * W * T1y
+        g2x = (1 - W) * m2x + w * W * T2x
+        n0, n1x, n1y, n2x = g0.copy(), g1x.copy(), g1y.copy(), g2x.copy()
+        for i in range(q):
+            cx, cy = L.BASIC_HOPS[hops[i]]
+            if paused[i]:    # only the scattered part moves
+                n1x[i] = g1x[i] + cx * w[i] * W * T0
+                n1y[i] = g1y[i] + cy * w[i] * W * T0
+                n2x[i] = g2x[i] + w[i] * W * (2 * cx * T1x + cx * cx * T0)
+            else:            # everything moves by c
+                n1x[i] = g1x[i] + cx * g0[i]
+                n1y[i] = g1y[i] + cy * g0[i]
+                n2x[i] = g2x[i] + 2 * cx * g1x[i] + cx * cx * g0[i]
+        m0, m1x, m1y, m2x = n0, n1x, n1y, n2x
+        out.append((m0.copy(), m1x.copy(), m1y.copy(), m2x.copy()))
+    return out
+
+
+def test_field_step_matches_moment_recursion():
+    """The field oracle and the moment-space recursion agree exactly while the support
+    stays away from the periodic seam."""
+    q, nx, ny, steps = 16, 90, 90, 30
+    mfp = 3.0
+    m = WormLBM(nx, ny, q, mfp, emulate_3d=True)
+    W = float(m.w_int[0, 0])
+    rng = np.random.default_rng(7)
+    d0 = np.zeros((q, ny + 2, nx + 2))
+    d0[:, 44:49, 43:48] = rng.standard_normal((q, 5, 5))
+    m.set_state(d0)
+    y, x = np.mgrid[0:ny + 2, 0:nx + 2].astype(np.float64)
+    mom = lambda d: (d.sum((1, 2)), (d * x).sum((1, 2)), (d * y).sum((1, 2)),
+                     (d * x * x).sum((1, 2)))
+    ref = _moment_recursion(q, W, steps, *mom(d0))
+    for n in range(steps):
+        m.step()
+        got = mom(m.d)
+        for a, b in zip(got, ref[n]):
+            assert np.allclose(a, b, rtol=1e-11, atol=1e-9)
+
+
+def _diffusivity(q, mfp, emulate_3d, steps):
+    dirs = L.ring_directions(q)
+    W = float(L.relax_weight(mfp, L.lambda_corr(dirs), emulate_3d))
+    w = L.angular_weights(dirs)
+    z = np.zeros(q)
+    hist = _moment_recursion(q, W, steps, w.copy(), z.copy(), z.copy(), z.copy())
+
+    def var(t):
+        m0, m1x, _, m2x = hist[t]
+        return m2x.sum() / m0.sum() - (m1x.sum() / m0.sum()) ** 2
+    t1, t2 = steps // 2, steps - 1
+    return (var(t2) - var(t1)) / (2.0 * (t2 - t1))
+
+
+@pytest.mark.parametrize("emulate_3d,target", [(True, 1.0 / 3.0), (False, 0.5)])
+def test_diffusive_limit_grid_mfp_correction(emulate_3d, target):
+    """Sec. 2.3 / Eq. W-correction and Sec. 4.3: in the Fourier limit the corrected
+    scheme diffuses with D = v_g Lambda / 3 when a 2D run emulates 3D (D = Lambda / 2
+    for plain 2D), up to a first-order lattice error in 1/Lambda."""
+    d16 = _diffusivity(8, 16.0, emulate_3d, 1400)
+    d32 = _diffusivity(8, 32.0, emulate_3d, 2400)
+    slope = (d32 - d16) / 16.0
+    assert slope == pytest.approx(target, rel=0.01)
+    e16 = 1 - d16 / (16 * target)
+    e32 = 1 - d32 / (32 * target)
+    assert 0 < e32 < e16 and 0.3 < e32 / e16 < 0.7          # first order in 1/Lambda
+
+
+def test_heat_flux_of_equilibrium_is_zero_and_single_beam_is_exact():
+    """Eq. q_corr: an isotropic equilibrium carries no flux; a single populated
+    direction carries exactly e_i s_i."""
+    m = WormLBM(8, 8, 32, 4.0)
+    m.init_temperature(np.full((8, 8), 0.7))
+    qx, qy = m.heat_flux()
+    assert np.abs(qx).max() < 1e-17 and np.abs(qy).max() < 1e-17
+    d = np.zeros_like(m.d)
+    d[5, 1:-1, 1:-1] = 2.0
+    m.set_state(d)
+    qx, qy = m.heat_flux()
+    assert np.allclose(qx, 2.0 * m.s_hat[5, 0]) and np.allclose(qy, 2.0 * m.s_hat[5, 1])
+
+
+def test_cross_plane_fourier_steady_profile_is_linear():
+    """Sec. 4.4 (cross-plane, Fourier limit): isothermal walls at T_h and T_c and
+    periodic y give, once steady and averaged over TAS fluctuations (Sec. 4.4 averages
+    the flux over steps), a linear energy profile away from the wall layers and a
+    uniform heat flux."""
+    nx = 40
+    m = WormLBM(nx, 1, 16, 1.5, bc_kind=(I, I, P, P), t_wall=(301.0, 300.0, 0, 0))
+    m.init_temperature(np.zeros((1, nx)))
+    m.step(5000)
+    e_acc = np.zeros(nx)
+    q_acc = np.zeros(nx)
+    for _ in range(400):
+        m.step()
+        e_acc += m.energy_dev()[0]
+        q_acc += m.heat_flux()[0][0]
+    e, q = e_acc / 400, q_acc / 400
+    x = np.arange(nx)
+    fit = np.polyfit(x[6:-6], e[6:-6], 1)
+    assert np.abs(np.polyval(fit, x) - e)[6:-6].max() < 1e-4 * np.ptp(e)
+    assert fit[0] < 0 and q.mean() > 0
+    assert np.ptp(q[2:-2]) < 0.03 * q.mean()
