@@ -1,0 +1,310 @@
+"""Benchmark of the worm-LBM time step on GB300 (one JSON line on rank 0).
+
+Workload (default): 2048 x 2048 periodic grid, Q = 64 worm directions, float32
+deviation storage, uniform MFP drawn log-uniform in [1, 1000] cells from the seed, 16
+seeded Gaussian pulses.  One bench step = one worm-LBM time step over the whole grid:
+the periodic ghost-frame refresh plus the fused relax-and-stream kernel.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                  [--storage fp32|bf16] [--nx N] [--q Q]
+
+value     site-direction updates/s of the whole job (Q * nx * ny * K * N / max time).
+e2e       the same metric through the public API with host buffers: per e2e step the
+          host->device copy of the start field (pinned), the init, a full run of the
+          workload's step count, and the device->host read of the temperature field.
+roofline  the fused step kernel: algorithmic bytes per launch (8 B per site-direction for
+          float32, 4 B for bfloat16, plus 8 B per cell for the local-energy read and
+          write) over its CUDA-event duration, against the measured HBM copy bandwidth.
+cpu_baseline  the FP64 oracle on the host cores, on a bounded sample of the same grid.
+
+Under torchrun (N > 1) every rank runs an independent replica of the workload (the grid
+does not shard without a halo exchange; replicas only) and the time is the max over
+ranks.  `--impl reference` times the oracle instead (rank 0 only).
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "site-direction updates/s (% of HBM roofline); adjoint-to-forward time ratio"
+UNIT = "site-direction updates/s"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=2000)
+    p.add_argument("--warmup", type=int, default=20)
+    p.add_argument("--impl", default="native", choices=["native", "reference"])
+    p.add_argument("--storage", default="fp32", choices=["fp32", "bf16"])
+    p.add_argument("--nx", type=int, default=2048)
+    p.add_argument("--q", type=int, default=64)
+    p.add_argument("--seed", type=int, default=2)
+    p.add_argument("--workload", default="pulses", choices=["pulses", "film"],
+                   help="pulses: 2048^2 periodic Q=64 (default); film: 4096x256 in-plane "
+                        "film, Q=128, isothermal x walls, diffuse y walls (Kn = 1)")
+    p.add_argument("--e2e-steps", type=int, default=3)
+    p.add_argument("--no-extras", action="store_true",
+                   help="skip e2e, cpu baseline and clock sampling (profiling runs)")
+    return p.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def workload(args):
+    import workloads as W
+    if args.workload == "film":
+        return W.film_c3(kn=1.0, nx=2 * args.nx, ny=args.nx // 8, q=2 * args.q)
+    return W.pulses_c2(seed=args.seed, n=args.nx, q=args.q)
+
+
+def bytes_per_update(storage, q):
+    elem = 2 if storage == "bf16" else 4
+    return 2 * elem + 8.0 / q        # plane read + write, E read + write per cell
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(cfg, seconds=12.0):
+    """Oracle (numpy float64, one thread) on a bounded sample: a square window of the
+    benchmark grid with the same Q and MFP, stepped until ~`seconds` of work."""
+    import numpy as np
+    from oracle.stepper import WormLBM as Oracle
+    nx, ny = min(512, cfg["nx"]), min(512, cfg["ny"])
+    sub = cfg["dT"][:ny, :nx].astype(np.float64)
+    m = Oracle(nx, ny, cfg["q"], cfg["mfp"], bc_kind=cfg["bc"], t_wall=cfg["t_wall"],
+               emulate_3d=cfg["emulate_3d"], relax_mode=cfg["relax_mode"],
+               theta=624.8074248458514)
+    m.init_temperature(sub)
+    t0 = time.perf_counter()
+    steps = 0
+    while time.perf_counter() - t0 < seconds:
+        m.step()
+        steps += 1
+    dt = time.perf_counter() - t0
+    return {"value": cfg["q"] * nx * ny * steps / dt, "unit": UNIT, "cores": 1,
+            "kind": "oracle",
+            "sample": "%d steps of a %dx%d window of the workload (Q=%d, MFP=%.3g), numpy "
+                      "float64 single thread" % (steps, nx, ny, cfg["q"], cfg["mfp"])}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import numpy as np
+    from oracle.stepper import WormLBM as Oracle
+    cfg = workload(args)
+    n = 128                                  # bounded sample per bench step
+    m = Oracle(n, n, cfg["q"], cfg["mfp"], emulate_3d=cfg["emulate_3d"],
+               relax_mode=cfg["relax_mode"], theta=624.8074248458514)
+    m.init_temperature(cfg["dT"][:n, :n].astype(np.float64))
+    for _ in range(args.warmup):
+        m.step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        m.step()
+    dt = time.perf_counter() - t0
+    value = cfg["q"] * n * n * args.steps / dt
+    sample = ("each step: one time step of a %dx%d window of the %dx%d workload (Q=%d), "
+              "numpy float64 oracle, single thread" % (n, n, cfg["nx"], cfg["ny"], cfg["q"]))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "pulses_c2 window %dx%d of %dx%d, Q=%d, periodic"
+                       % (n, n, cfg["nx"], cfg["ny"], cfg["q"]), "q": cfg["q"],
+                       "mfp_cells": cfg["mfp"]},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    import paper_1911_00180_gb300 as wl
+
+    cfg = workload(args)
+    storage = wl.STORE_BF16_DEV if args.storage == "bf16" else wl.STORE_FP32_DEV
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        h = wl.WormLBM(cfg["nx"], cfg["ny"], cfg["q"], mfp=cfg["mfp"], bc=cfg["bc"],
+                       t_wall=cfg["t_wall"], storage=storage, emulate_3d=cfg["emulate_3d"],
+                       relax_mode=cfg["relax_mode"], stream=stream)
+        dT = torch.as_tensor(cfg["dT"]).to("cuda", non_blocking=False)
+        h.wlbm_init_temperature(dT)
+        h.wlbm_step(args.warmup)
+        stream.synchronize()
+        _, _, launches0 = h.wlbm_profile_read()
+
+        def barrier():
+            if world > 1:
+                dist.barrier()
+            torch.cuda.synchronize()
+
+        clocks = None if args.no_extras else Clocks(local)
+        h.wlbm_profile(True)
+        barrier()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        h.wlbm_step(args.steps)
+        ev1.record(stream)
+        barrier()
+        h.wlbm_profile(False)
+        clk = clocks.stop() if clocks else None
+        elapsed_ms = ev0.elapsed_time(ev1)
+        step_ms, step_launches, launches1 = h.wlbm_profile_read()
+        t = torch.tensor([elapsed_ms], device="cuda", dtype=torch.float64)
+        if world > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+
+        cells = cfg["nx"] * cfg["ny"]
+        updates = cfg["q"] * cells * args.steps * world
+        value = updates / (elapsed_ms * 1e-3)
+        bpu = bytes_per_update(args.storage, cfg["q"])
+        per_launch_ms = step_ms / max(step_launches, 1)
+        achieved = bpu * cfg["q"] * cells / (per_launch_ms * 1e-3) / 1e9
+        peak, peak_kind = peaks()
+
+        e2e = None
+        if not args.no_extras:
+            # public API end to end: pinned host start field -> device, init, full run,
+            # temperature field -> pinned host, all inside the timed region.
+            host_in = torch.as_tensor(cfg["dT"]).pin_memory()
+            host_out = torch.empty_like(host_in).pin_memory()
+            dev_in = torch.empty_like(host_in, device="cuda")
+            run_steps = cfg["steps"]
+            times = []
+            for k in range(args.e2e_steps + 1):
+                barrier()
+                t0 = time.perf_counter()
+                dev_in.copy_(host_in, non_blocking=True)
+                h.wlbm_init_temperature(dev_in)
+                h.wlbm_step(run_steps)
+                dTo, _, _ = h.wlbm_moments(want_q=False)
+                host_out.copy_(dTo, non_blocking=True)
+                stream.synchronize()
+                if k > 0:
+                    times.append(time.perf_counter() - t0)
+            tt = torch.tensor([max(times)], dtype=torch.float64, device="cuda")
+            if world > 1:
+                dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            e2e = {"value": cfg["q"] * cells * run_steps * world / (sum(times) / len(times)),
+                   "unit": UNIT, "h2d_bytes_per_step": int(host_in.numel() * 4),
+                   "d2h_bytes_per_step": int(host_out.numel() * 4),
+                   "lbm_steps_per_e2e_step": run_steps}
+        h.close()
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.storage == "fp32" else "bf16-storage/f32-math",
+            "data": "synthetic",
+            "config": {"workload": (
+                           "pulses_c2 %dx%d periodic, Q=%d, %s deviation storage, "
+                           "uniform MFP %.4g cells, 16 Gaussian pulses"
+                           % (cfg["nx"], cfg["ny"], cfg["q"], args.storage, cfg["mfp"]))
+                       if args.workload == "pulses" else (
+                           "film_c3 %dx%d, Q=%d, %s deviation storage, isothermal x walls "
+                           "301/300 K, adiabatic-diffuse y walls, Kn=1 (MFP %.4g cells)"
+                           % (cfg["nx"], cfg["ny"], cfg["q"], args.storage, cfg["mfp"])),
+                       "nx": cfg["nx"], "ny": cfg["ny"], "q": cfg["q"],
+                       "mfp_cells": cfg["mfp"], "parallelism": "replicas x%d" % world,
+                       "l2": "state %.2f GB > L2 (no flush needed)"
+                             % (2 * cfg["q"] * cells * (4 if args.storage == "fp32" else 2) / 1e9)},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": "k_step", "peak_kind": peak_kind,
+                         "bytes_per_update": bpu,
+                         "kernel_ms_per_launch": per_launch_ms},
+            "gpu_launches": int(launches1 - launches0),
+            "hbm_roofline_pct_of_measured": 100.0 * achieved / peak,
+        }
+        if e2e is not None:
+            line["e2e"] = e2e
+        if clk is not None:
+            line["clocks"] = clk
+        if not args.no_extras:
+            line["cpu_baseline"] = cpu_baseline(cfg)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,162 @@
+/*
+ * wlbm.h - C ABI of libwlbm, a GB300 (sm_103a) implementation of the worm lattice
+ * Boltzmann method for the gray phonon Boltzmann transport equation (Hammer, Fritz,
+ * Bedoya-Martinez, arXiv 1911.00180).
+ *
+ * Conventions for every entry point
+ *  - Plain C types only.  "device" pointers are CUDA device (or managed) memory of the
+ *    current device; "host" pointers are ordinary CPU memory.
+ *  - Calls that touch the GPU are asynchronous on the handle's stream unless stated;
+ *    they return a wlbm_status and never abort or throw.  A failed call leaves a
+ *    message readable with wlbm_last_error(handle) (or wlbm_last_error(NULL) for
+ *    failures before a handle exists).
+ *  - Lattice units: one grid spacing, one time step, group velocity v_g = 1.  The grid
+ *    has nx x ny interior cells, row-major (x fastest).  Temperatures are absolute in
+ *    kelvin except where a "dT" (deviation T - t_ref, kelvin) is named: deviations keep
+ *    full float32 precision near 300 K.
+ *  - The library owns the lattice state (two copies of Q direction planes, the local
+ *    energy planes, the relaxation-weight plane); the caller owns every buffer it passes.
+ */
+#ifndef WLBM_H
+#define WLBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum wlbm_status {
+  WLBM_OK = 0,
+  WLBM_ERR_INVALID_ARG = 1, /* bad size, kind, pointer or Q (Q must be 8M, 8 <= Q <= 1024) */
+  WLBM_ERR_UNSTABLE = 2,    /* max W_corr > 1: the paused step is unstable (Appendix A) */
+  WLBM_ERR_OOM = 3,         /* the allocator returned NULL */
+  WLBM_ERR_CUDA = 4,        /* a CUDA runtime call failed (message has the CUDA error) */
+  WLBM_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up */
+  WLBM_ERR_STATE = 6        /* call out of order (e.g. step before init) */
+} wlbm_status;
+
+/* Boundary kinds of Sec. 2.6 of the paper. */
+enum {
+  WLBM_BC_PERIODIC = 0,          /* periodic link to the opposite wall (must be paired) */
+  WLBM_BC_ISOTHERMAL = 1,        /* isotropic blackbody wall, Eq. isotropic            */
+  WLBM_BC_ADIABATIC_DIFFUSE = 2  /* adiabatic diffuse wall, Eq. adiabatic-diffuse      */
+};
+
+/* Storage of the direction planes.  Both store the deviation of e_i from the reference
+ * equilibrium w_i e_eq(t_ref); arithmetic is float32 in both. */
+enum {
+  WLBM_STORE_FP32_DEV = 0,  /* float32 deviation                                   */
+  WLBM_STORE_BF16_DEV = 1   /* bfloat16 deviation divided by a per-run scale (RNE)  */
+};
+
+typedef struct wlbm_grid {
+  int32_t nx, ny;      /* interior cells, >= 1 each                                   */
+  int32_t q;           /* directions Q = 8M of the worm-D2Q[8M] scheme (Sec. 2.5)       */
+  int32_t storage;     /* WLBM_STORE_*                                                 */
+  int32_t emulate_3d;  /* 1: apply the 3/2 factor of Eq. W-correction (2D emulating 3D) */
+  int32_t relax_mode;  /* 0: W_corr as in Eq. W-correction (the paper).  1: opt-in
+                          1 - exp(-W_corr), stable for MFP < 1 cell (not in the paper)  */
+  double t_ref;        /* reference temperature, K (e.g. 300)                          */
+  double theta;        /* hbar omega0 / k_B, K (624.8 for the paper's 81.8e12 rad/s)   */
+} wlbm_grid;
+
+typedef struct wlbm_boundary {
+  int32_t kind[4];     /* WLBM_BC_* for the walls x-, x+, y-, y+                        */
+  double t_wall[4];    /* wall temperature (K) of isothermal walls; ignored otherwise   */
+} wlbm_boundary;
+
+/* Device-memory provider.  alloc returns a device pointer of at least `bytes` bytes
+ * aligned to 256 bytes, or NULL (the library then fails with WLBM_ERR_OOM).  NULL for the
+ * whole struct means cudaMalloc / cudaFree. */
+typedef struct wlbm_allocator {
+  void* (*alloc)(size_t bytes, void* ctx);
+  void (*free)(void* ptr, void* ctx);
+  void* ctx;
+} wlbm_allocator;
+
+typedef struct wlbm_handle wlbm_handle;
+
+/* ---------------------------------------------------------------- lifecycle -------
+ * wlbm_create: build the lattice for one grid (Sec. 2.2-2.5): the Q ring directions,
+ * the angular weights (Eq. weight), the worm paths (Eq. worm-paths), Lambda_corr
+ * (Eq. W-correction-factor-generalized) and the per-cell corrected relaxation weight
+ * W_corr = f W (1 - W + W Lambda_corr), W = 1 / MFP (Eq. W-Kn and Eq. W-correction).
+ *   mfp_cells    device, nx*ny float32 mean free path in cells (row-major), or NULL to
+ *                use mfp_uniform for every cell.  +inf gives W = 0 (ballistic).
+ *   stream       cudaStream_t used for every later call (NULL = legacy default stream).
+ * Fails with WLBM_ERR_UNSTABLE if any W_corr > 1 (relax_mode 0), WLBM_ERR_INVALID_ARG
+ * for an unpaired periodic wall, Q not a multiple of 8, non-positive MFP or sizes.
+ * Synchronous (copies the MFP field to the host once).  The state starts at zero
+ * deviation (uniform t_ref) and must be set by wlbm_init_temperature or wlbm_set_state.
+ */
+wlbm_status wlbm_create(const wlbm_grid* grid, const float* mfp_cells, double mfp_uniform,
+                        const wlbm_boundary* bc, const wlbm_allocator* alloc,
+                        void* stream, wlbm_handle** out);
+void wlbm_destroy(wlbm_handle* h);
+const char* wlbm_last_error(const wlbm_handle* h);
+wlbm_status wlbm_set_stream(wlbm_handle* h, void* stream);
+
+/* wlbm_init_temperature: local-equilibrium start e_i = w_i e_eq(t_ref + dT) in every
+ * interior cell (Sec. 2.4: the weights set initial conditions); ghost cells copy their
+ * nearest interior cell.  dT: device, nx*ny float32 (K).  Resets the step counter and
+ * the TAS schedule.  With BF16 storage the per-run scale is set here from max |dT| and
+ * the wall temperatures (synchronous in that case). */
+wlbm_status wlbm_init_temperature(wlbm_handle* h, const float* dT);
+
+/* wlbm_step: advance n >= 0 time steps.  Each step applies the wall conditions to the
+ * ghost frame (Sec. 2.6), then the fused update of every cell and direction (Eq.
+ * lbm-energy with e_i^eq = w_i E, Eq. lbm-energy-density, and the TAS rule of Eq.
+ * algorithm along the worm paths of Eq. worm-paths). */
+wlbm_status wlbm_step(wlbm_handle* h, int64_t n);
+int64_t wlbm_step_count(const wlbm_handle* h);
+
+/* wlbm_moments: temperature deviation T - t_ref by Eq. pseudo-T (computed in a
+ * cancellation-free form) and heat flux q = sum_i e_i s_i (Eq. q_corr, v_g = 1) of the
+ * current state.  Each output is device nx*ny float32, or NULL to skip it. */
+wlbm_status wlbm_moments(wlbm_handle* h, float* dT, float* qx, float* qy);
+
+/* wlbm_reduce: float64 reductions over the current state, written to host out[4]:
+ *   out[0] sum over interior cells of E - e_ref      (energy conservation, Eq.
+ *          lbm-energy-density; the paper's energy with its unit prefactor set to 1)
+ *   out[1] the same plus wall ghost cells (energy held by adiabatic walls)
+ *   out[2] mean of q_x over interior cells, out[3] mean of q_y  (Eq. q_corr)
+ * Synchronous. */
+wlbm_status wlbm_reduce(wlbm_handle* h, double* out);
+
+/* wlbm_get_state / wlbm_set_state: the deviations e_i - w_i e_ref of the current state,
+ * unscaled float32, layout [Q][ny+2][nx+2] including the one-cell ghost frame (index
+ * (y+1, x+1) is interior cell (x, y)).  device pointers.  set_state also recomputes the
+ * local energy and keeps the step counter and schedule. */
+wlbm_status wlbm_get_state(wlbm_handle* h, float* framed);
+wlbm_status wlbm_set_state(wlbm_handle* h, const float* framed);
+
+/* wlbm_profile: enable (1) or disable (0) CUDA-event timing of every launch of the
+ * fused step kernel on the handle's stream (an event pair around each launch).
+ * wlbm_profile_read: synchronises the stream, returns the summed duration (ms) and count
+ * of the timed step-kernel launches since the last read (then resets them), and the
+ * number of kernels this handle has launched since it was created.  Any output may be
+ * NULL. */
+wlbm_status wlbm_profile(wlbm_handle* h, int32_t enable);
+wlbm_status wlbm_profile_read(wlbm_handle* h, double* step_ms, int64_t* step_launches,
+                              int64_t* all_launches);
+
+/* ------------------------------------------------------------ host-only queries ----
+ * No GPU needed.  wlbm_lattice: the lattice of Sec. 2.4-2.5 for Q directions.
+ *   dirs      host int32[2Q] lattice vectors (x, y) of the ring directions, counter-
+ *             clockwise from +x; weights host double[Q] (Eq. weight); worm host
+ *             int8[Q*M] basic-hop indices K_{s,n} (Eq. worm-paths; hops numbered
+ *             (1,0),(0,1),(-1,0),(0,-1),(1,1),(-1,1),(-1,-1),(1,-1)); lam_corr host
+ *             double[1].  Any output may be NULL. */
+wlbm_status wlbm_lattice(int32_t q, int32_t* dirs, double* weights, int8_t* worm,
+                         double* lam_corr);
+
+/* wlbm_schedule: the TAS schedule (Eq. algorithm) of steps 1..n_steps: host
+ * uint8[n_steps*Q]; entry [t][i] = hop index (bits 0-2) | paused << 3. */
+wlbm_status wlbm_schedule(int32_t q, int64_t n_steps, uint8_t* codes);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WLBM_H */

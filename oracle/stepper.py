@@ -208,20 +208,25 @@ class WormLBM:
     def _one_step(self):
         n = self.n + 1
         self.apply_bc()
-        e_loc = self.d.sum(axis=0)                   # Eq. lbm-energy-density
+        hops, paused = self.sched.advance(n)
+        self.d = self.collide_stream(self.d, hops, paused)
+        self.n = n
+
+    def collide_stream(self, d, hops, paused):
+        """One update of Eq. lbm-energy / Eq. algorithm on a framed state d whose ghost
+        frame already holds the boundary values."""
+        e_loc = d.sum(axis=0)                        # Eq. lbm-energy-density
         f = self.wf * e_loc                          # scattered energy W E at each cell
         keep = 1.0 - self.wf                         # (1 - W)
-        hops, paused = self.sched.advance(n)
-        new = np.empty_like(self.d)
+        new = np.empty_like(d)
         for i in range(self.q):
             c = L.BASIC_HOPS[hops[i]]
             gain = self.w[i] * shift(f, c)           # EED always hops: w_i W(s) E(s)
             if paused[i]:
-                new[i] = keep * self.d[i] + gain
+                new[i] = keep * d[i] + gain
             else:
-                new[i] = shift(keep * self.d[i], c) + gain
-        self.d = new
-        self.n = n
+                new[i] = shift(keep * d[i], c) + gain
+        return new
 
     # ---------------------------------------------------------------- moments
     def energy_dev(self):

@@ -1,0 +1,332 @@
+// Boundary, initialisation, moment and reduction kernels of libwlbm.
+//
+//  k_walls     ghost cells of non-periodic walls (Sec. 2.6): isotropic blackbody walls
+//              overwrite d_i = w_i (e_eq(T_w) - e_ref) (Eq. isotropic); adiabatic diffuse
+//              walls collect the components that do not point into the domain and
+//              re-emit them into the inward ones with fractions w_i (s_i.n) / sum
+//              (Eq. adiabatic-diffuse, normalised so that energy is conserved).
+//  k_periodic  periodic links (Sec. 2.6): ghost rows copy the opposite interior rows,
+//              then ghost columns copy the opposite columns (corners via the diagonal).
+//  k_init      local equilibrium start e_i = w_i e_eq(T) (Sec. 2.4) in float64.
+//  k_moments   T - T_ref by Eq. pseudo-T in a cancellation-free form, q by Eq. q_corr.
+//  k_reduce    float64 sums: energy (interior, + wall cells), mean heat flux.
+#include "elem.cuh"
+#include "wlbm_internal.hpp"
+
+namespace wlbm {
+
+namespace {
+
+__device__ __forceinline__ int parity_of(const ParityMask& m, int i) {
+  return (m.bits[i >> 5] >> (i & 31)) & 1;
+}
+
+// Deviation d_i of a stored value (float32: the value itself; bfloat16: scale * v +
+// w_i R at a cell whose reference energy is R, see wlbm_internal.hpp).
+template <typename T>
+__device__ __forceinline__ float dev_load(const T* p, float wi, const float* ref, int64_t off,
+                                          float scale) {
+  const float v = Elem<T>::ld(p);
+  return ref ? fmaf(v, scale, wi * ref[off]) : v;
+}
+
+// Store deviation d; returns the deviation the stored value represents.
+template <typename T>
+__device__ __forceinline__ float dev_store(T* p, float d, float wi, const float* ref,
+                                           int64_t off, float scale, float inv_scale) {
+  if (!ref) return Elem<T>::st(p, d);
+  const float r = wi * ref[off];
+  return fmaf(Elem<T>::st(p, (d - r) * inv_scale), scale, r);
+}
+
+template <typename T>
+__global__ void k_walls(const WallArgs a) {
+  const int warp = int((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  int s = 0, idx = warp;
+  while (s < a.nseg && idx >= a.seg[s].count) {
+    idx -= a.seg[s].count;
+    ++s;
+  }
+  if (s >= a.nseg) return;
+  const WallSeg g = a.seg[s];
+  const int64_t off = int64_t(g.r0 + idx * g.dr) * a.pitch + (g.c0 + idx * g.dc);
+  T* planes = static_cast<T*>(a.planes);
+  auto ptr = [&](int i) {
+    return planes + int64_t(((a.codes[i] >> 4) & 1) * a.q + i) * a.plane + off;
+  };
+  if (g.action == WLBM_BC_ISOTHERMAL) {
+    for (int i = lane; i < a.q; i += 32)
+      dev_store(ptr(i), a.w[i] * g.iso, a.w[i], a.e_ref, off, a.scale, a.inv_scale);
+    return;
+  }
+  const float* rho = a.rho + int64_t(g.table) * a.q;
+  float part = 0.f;
+  for (int i = lane; i < a.q; i += 32)
+    if (rho[i] == 0.f) part += dev_load(ptr(i), a.w[i], a.e_ref, off, a.scale);
+  const float A = warp_sum(part);
+  for (int i = lane; i < a.q; i += 32) {
+    const float d = rho[i] == 0.f ? 0.f
+                                  : fmaf(A, rho[i], dev_load(ptr(i), a.w[i], a.e_ref, off, a.scale));
+    dev_store(ptr(i), d, a.w[i], a.e_ref, off, a.scale, a.inv_scale);
+  }
+}
+
+template <typename T>
+__global__ void k_periodic(const PeriodicArgs a) {
+  const int ncy = a.yper ? (a.xper ? a.nx : a.nx + 2) : 0;
+  const int cy0 = a.xper ? kX0 : kGhostCol;
+  const int ncx = a.xper ? 2 * (a.ny + 2) : 0;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 2 * ncy + ncx) return;
+  int rd, cd, rs, cs;
+  if (t < 2 * ncy) {
+    const int side = t / ncy, k = t - side * ncy;
+    cd = cs = cy0 + k;
+    rd = side == 0 ? 1 : a.ny + 2;
+    rs = side == 0 ? a.ny + 1 : 2;
+  } else {
+    const int k = t - 2 * ncy;
+    const int side = k / (a.ny + 2);
+    rd = 1 + (k - side * (a.ny + 2));
+    rs = rd;
+    if (a.yper) {
+      if (rd == 1) rs = a.ny + 1;
+      else if (rd == a.ny + 2) rs = 2;
+    }
+    cd = side == 0 ? kGhostCol : kX0 + a.nx;
+    cs = side == 0 ? kX0 + a.nx - 1 : kX0;
+  }
+  const int64_t od = int64_t(rd) * a.pitch + cd, os = int64_t(rs) * a.pitch + cs;
+  const int p = blockIdx.y;
+  if (p == a.q) {
+    a.e_cur[od] = a.e_cur[os];
+  } else if (p == a.q + 1) {
+    a.e_ref[od] = a.e_ref[os];
+  } else {
+    T* base = static_cast<T*>(a.planes) + int64_t(((a.codes[p] >> 4) & 1) * a.q + p) * a.plane;
+    base[od] = base[os];
+  }
+}
+
+template <typename T>
+__global__ void k_init(const InitArgs a) {
+  const int fw = a.nx + 2, fh = a.ny + 2;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= fw * fh) return;
+  const int fy = t / fw, fx = t - fy * fw;            // framed coordinates
+  const int x = min(max(fx - 1, 0), a.nx - 1), y = min(max(fy - 1, 0), a.ny - 1);
+  const double temp = a.t_ref + double(a.dT[int64_t(y) * a.nx + x]);
+  const double de = 1.0 / expm1(a.theta / temp) - a.e_ref;
+  const int64_t off = int64_t(fy + 1) * a.pitch + (kGhostCol + fx);
+  T* planes = static_cast<T*>(a.planes);
+  if (a.e_refp) {   // reference energy = the equilibrium energy of this cell
+    float e0 = 0.f;
+    for (int i = 0; i < a.q; ++i) e0 += float(double(a.w[i]) * de);
+    a.e_refp[off] = e0;
+  }
+  float e = 0.f;
+  for (int i = 0; i < a.q; ++i)
+    e += dev_store(planes + int64_t(i) * a.plane + off, float(double(a.w[i]) * de), a.w[i],
+                   a.e_refp, off, a.scale, a.inv_scale);
+  a.e_cur[off] = e;
+}
+
+template <typename T>
+__global__ void k_moments(const MomentArgs a) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= a.nx * a.ny) return;
+  const int y = t / a.nx, x = t - y * a.nx;
+  const int64_t off = int64_t(y + 2) * a.pitch + (x + kX0);
+  if (a.dT) {
+    // L = ln(1 + 1/e) = L_ref + log1p(dE/(e_ref+1)) - log1p(dE/e_ref);
+    // T - T_ref = theta/L - theta/L_ref = -theta dL / (L_ref (L_ref + dL)).
+    const float de = a.e_cur[off];
+    const float dl = log1pf(de / a.e_ref1) - log1pf(de / a.e_ref);
+    a.dT[t] = -a.theta * dl / (a.l_ref * (a.l_ref + dl));
+  }
+  if (a.qx || a.qy) {
+    const T* planes = static_cast<const T*>(a.planes);
+    float qx = 0.f, qy = 0.f;
+    for (int i = 0; i < a.q; ++i) {
+      const float v = dev_load(planes + int64_t(parity_of(a.par, i) * a.q + i) * a.plane + off,
+                               a.w[i], a.e_refp, off, a.scale);
+      qx = fmaf(v, a.sx[i], qx);
+      qy = fmaf(v, a.sy[i], qy);
+    }
+    if (a.qx) a.qx[t] = qx;
+    if (a.qy) a.qy[t] = qy;
+  }
+}
+
+template <typename T>
+__global__ void k_reduce(const ReduceArgs a) {
+  const int fw = a.nx + 2, fh = a.ny + 2;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  double v[4] = {0.0, 0.0, 0.0, 0.0};
+  if (t < fw * fh) {
+    const int fy = t / fw, fx = t - fy * fw;
+    const bool gx = fx == 0 || fx == fw - 1, gy = fy == 0 || fy == fh - 1;
+    const int64_t off = int64_t(fy + 1) * a.pitch + (kGhostCol + fx);
+    const T* planes = static_cast<const T*>(a.planes);
+    if (!gx && !gy) {
+      v[0] = double(a.e_cur[off]);
+      v[1] = v[0];
+      double qx = 0.0, qy = 0.0;
+      for (int i = 0; i < a.q; ++i) {
+        const double u = dev_load(planes + int64_t(parity_of(a.par, i) * a.q + i) * a.plane + off,
+                                  a.w[i], a.e_refp, off, float(a.scale));
+        qx += u * a.sx[i];
+        qy += u * a.sy[i];
+      }
+      v[2] = qx;
+      v[3] = qy;
+    } else if (!(gx && a.xper) && !(gy && a.yper)) {
+      double e = 0.0;
+      for (int i = 0; i < a.q; ++i)
+        e += dev_load(planes + int64_t(parity_of(a.par, i) * a.q + i) * a.plane + off, a.w[i],
+                      a.e_refp, off, float(a.scale));
+      v[1] = e;
+    }
+  }
+  __shared__ double red[4][32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const double s = warp_sum(v[k]);
+    if (lane == 0) red[k][wid] = s;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    const int nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      double s = lane < nw ? red[k][lane] : 0.0;
+      s = warp_sum(s);
+      if (lane == 0 && s != 0.0) atomicAdd(a.out + k, s);
+    }
+  }
+}
+
+template <typename T>
+__global__ void k_get_state(const StateArgs a) {
+  const int fw = a.nx + 2, fh = a.ny + 2;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = blockIdx.y;
+  if (t >= fw * fh) return;
+  const int fy = t / fw, fx = t - fy * fw;
+  const int64_t off = int64_t(fy + 1) * a.pitch + (kGhostCol + fx);
+  const T* p = static_cast<const T*>(a.planes) + int64_t(parity_of(a.par, i) * a.q + i) * a.plane;
+  a.framed[int64_t(i) * fw * fh + t] = dev_load(p + off, a.w[i], a.e_refp, off, a.scale);
+}
+
+template <typename T>
+__global__ void k_set_state(const StateArgs a) {
+  const int fw = a.nx + 2, fh = a.ny + 2;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = blockIdx.y;
+  if (t >= fw * fh) return;
+  const int fy = t / fw, fx = t - fy * fw;
+  const int64_t off = int64_t(fy + 1) * a.pitch + (kGhostCol + fx);
+  T* p = static_cast<T*>(a.planes) + int64_t(parity_of(a.par, i) * a.q + i) * a.plane;
+  dev_store(p + off, a.framed[int64_t(i) * fw * fh + t], a.w[i], a.e_refp, off, a.scale,
+            a.inv_scale);
+}
+
+template <typename T>
+__global__ void k_energy(const StateArgs a) {
+  const int fw = a.nx + 2, fh = a.ny + 2;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= fw * fh) return;
+  const int fy = t / fw, fx = t - fy * fw;
+  const int64_t off = int64_t(fy + 1) * a.pitch + (kGhostCol + fx);
+  const T* planes = static_cast<const T*>(a.planes);
+  float e = 0.f;
+  for (int i = 0; i < a.q; ++i)
+    e += dev_load(planes + int64_t(parity_of(a.par, i) * a.q + i) * a.plane + off, a.w[i],
+                  a.e_refp, off, a.scale);
+  a.e_cur[off] = e;
+}
+
+inline unsigned blocks_for(int64_t n, int per) { return unsigned((n + per - 1) / per); }
+
+template <typename T>
+cudaError_t walls_t(const WallArgs& a, cudaStream_t s) {
+  int cells = 0;
+  for (int k = 0; k < a.nseg; ++k) cells += a.seg[k].count;
+  if (cells == 0) return cudaSuccess;
+  k_walls<T><<<blocks_for(int64_t(cells) * 32, 256), 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t periodic_t(const PeriodicArgs& a, cudaStream_t s) {
+  const int ncy = a.yper ? (a.xper ? a.nx : a.nx + 2) : 0;
+  const int ncx = a.xper ? 2 * (a.ny + 2) : 0;
+  const int total = 2 * ncy + ncx;
+  if (total == 0) return cudaSuccess;
+  k_periodic<T><<<dim3(blocks_for(total, 256), a.q + (a.e_ref ? 2 : 1)), 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_walls(int storage, const WallArgs& a, cudaStream_t s) {
+  return storage == WLBM_STORE_BF16_DEV ? walls_t<__nv_bfloat16>(a, s) : walls_t<float>(a, s);
+}
+
+cudaError_t launch_periodic(int storage, const PeriodicArgs& a, cudaStream_t s) {
+  return storage == WLBM_STORE_BF16_DEV ? periodic_t<__nv_bfloat16>(a, s)
+                                        : periodic_t<float>(a, s);
+}
+
+cudaError_t launch_init(int storage, const InitArgs& a, cudaStream_t s) {
+  const unsigned g = blocks_for(int64_t(a.nx + 2) * (a.ny + 2), 256);
+  if (storage == WLBM_STORE_BF16_DEV)
+    k_init<__nv_bfloat16><<<g, 256, 0, s>>>(a);
+  else
+    k_init<float><<<g, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_moments(int storage, const MomentArgs& a, cudaStream_t s) {
+  const unsigned g = blocks_for(int64_t(a.nx) * a.ny, 256);
+  if (storage == WLBM_STORE_BF16_DEV)
+    k_moments<__nv_bfloat16><<<g, 256, 0, s>>>(a);
+  else
+    k_moments<float><<<g, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce(int storage, const ReduceArgs& a, cudaStream_t s) {
+  const unsigned g = blocks_for(int64_t(a.nx + 2) * (a.ny + 2), 256);
+  if (storage == WLBM_STORE_BF16_DEV)
+    k_reduce<__nv_bfloat16><<<g, 256, 0, s>>>(a);
+  else
+    k_reduce<float><<<g, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_get_state(int storage, const StateArgs& a, cudaStream_t s) {
+  const dim3 g(blocks_for(int64_t(a.nx + 2) * (a.ny + 2), 256), a.q);
+  if (storage == WLBM_STORE_BF16_DEV)
+    k_get_state<__nv_bfloat16><<<g, 256, 0, s>>>(a);
+  else
+    k_get_state<float><<<g, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_state(int storage, const StateArgs& a, cudaStream_t s) {
+  const dim3 g(blocks_for(int64_t(a.nx + 2) * (a.ny + 2), 256), a.q);
+  const unsigned g1 = blocks_for(int64_t(a.nx + 2) * (a.ny + 2), 256);
+  if (storage == WLBM_STORE_BF16_DEV) {
+    k_set_state<__nv_bfloat16><<<g, 256, 0, s>>>(a);
+    k_energy<__nv_bfloat16><<<g1, 256, 0, s>>>(a);
+  } else {
+    k_set_state<float><<<g, 256, 0, s>>>(a);
+    k_energy<float><<<g1, 256, 0, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace wlbm

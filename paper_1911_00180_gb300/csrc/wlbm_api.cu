@@ -1,0 +1,602 @@
+// C ABI of libwlbm: handle lifecycle, boundary tables, the per-step launch sequence.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "wlbm_internal.hpp"
+
+using namespace wlbm;
+
+namespace {
+
+constexpr int kChunk = 1024;   // steps whose codes are uploaded per host->device copy
+
+std::mutex g_err_mu;
+std::string g_err;             // errors before a handle exists
+
+void set_global_error(const std::string& m) {
+  std::lock_guard<std::mutex> lk(g_err_mu);
+  g_err = m;
+}
+
+int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
+
+}  // namespace
+
+struct wlbm_handle {
+  Geom g;
+  int storage = 0, emulate_3d = 0, relax_mode = 0;
+  double t_ref = 300.0, theta = 624.8, e_eq_ref = 0.0;
+  float scale = 1.f, inv_scale = 1.f;
+  int bc_kind[4] = {0, 0, 0, 0};
+  double t_wall[4] = {0, 0, 0, 0};
+  int xper = 1, yper = 1;
+  Lattice lat;
+  TasState tas;
+  bool field_w = false;
+  float w0 = 0.f;
+  wlbm_allocator alloc{nullptr, nullptr, nullptr};
+  cudaStream_t stream = nullptr;
+  // device memory
+  void* planes = nullptr;     // [2][q][plane] storage elements
+  float* e[3] = {nullptr, nullptr, nullptr};   // local-energy planes (3 for bfloat16)
+  int e_cur = 0, e_ref = -1, e_spare = 1;      // roles of the energy planes
+  float wsum = 1.f;                            // sum of the float32 weights
+  float* wfield = nullptr;    // framed W_corr (per-cell MFP only)
+  float* consts = nullptr;    // w[q], sx[q], sy[q], rho[8][q]
+  uint8_t* d_codes = nullptr; // [kChunk][q]
+  double* d_red = nullptr;    // [4]
+  std::vector<void*> owned;
+  // host staging
+  uint8_t* h_codes[2] = {nullptr, nullptr};
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  int slot = 0;
+  WallArgs walls{};
+  std::string err;
+  // launch accounting and optional per-launch timing of the step kernel
+  int64_t launches = 0;
+  bool profiling = false;
+  std::vector<cudaEvent_t> prof_ev;   // pairs (start, stop)
+  size_t prof_used = 0;
+
+  size_t elem() const { return storage == WLBM_STORE_BF16_DEV ? 2 : 4; }
+  float* w_dev() const { return consts; }
+  float* sx_dev() const { return consts + g.q; }
+  float* sy_dev() const { return consts + 2 * g.q; }
+  float* rho_dev() const { return consts + 3 * g.q; }
+
+  wlbm_status fail(wlbm_status s, const std::string& m) {
+    err = m;
+    return s;
+  }
+  wlbm_status cuda(cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return WLBM_OK;
+    return fail(WLBM_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  }
+  void* dev_alloc(size_t bytes) {
+    bytes = size_t(round_up(int64_t(bytes), 256));
+    void* p = nullptr;
+    if (alloc.alloc) {
+      p = alloc.alloc(bytes, alloc.ctx);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+    }
+    if (p) owned.push_back(p);
+    return p;
+  }
+  void release() {
+    for (void* p : owned) {
+      if (alloc.alloc) {
+        if (alloc.free) alloc.free(p, alloc.ctx);
+      } else {
+        cudaFree(p);
+      }
+    }
+    owned.clear();
+    for (cudaEvent_t e : prof_ev) cudaEventDestroy(e);
+    prof_ev.clear();
+    for (int k = 0; k < 2; ++k) {
+      if (h_codes[k]) cudaFreeHost(h_codes[k]);
+      if (ev[k]) cudaEventDestroy(ev[k]);
+      h_codes[k] = nullptr;
+      ev[k] = nullptr;
+    }
+  }
+  ParityMask parity_mask() const {
+    ParityMask m{};
+    for (int i = 0; i < g.q; ++i)
+      if (tas.parity[i]) m.bits[i >> 5] |= 1u << (i & 31);
+    return m;
+  }
+  double delta_e(double t) const { return 1.0 / std::expm1(theta / t) - e_eq_ref; }
+  bool bf16() const { return storage == WLBM_STORE_BF16_DEV; }
+  float* ref_plane() const { return e_ref >= 0 ? e[e_ref] : nullptr; }
+  void rotate_energy() {      // after a step: new state's E becomes current
+    if (e_ref >= 0) {
+      const int old_ref = e_ref;
+      e_ref = e_cur;
+      e_cur = e_spare;
+      e_spare = old_ref;
+    } else {
+      std::swap(e_cur, e_spare);
+    }
+  }
+  void build_wall_segments();
+};
+
+// Ghost-cell segments handled by the wall kernel: non-periodic edges and the corners
+// that touch no periodic wall.  Corners: an isothermal x-wall decides, then an
+// isothermal y-wall, else two diffuse walls use the quadrant-diagonal rule.
+void wlbm_handle::build_wall_segments() {
+  WallArgs& a = walls;
+  a.nseg = 0;
+  const int nx = g.nx, ny = g.ny;
+  const int gl = kGhostCol, gr = kX0 + nx;
+  struct Edge { int count, r0, c0, dr, dc; };
+  const Edge edges[4] = {{ny, 2, gl, 1, 0}, {ny, 2, gr, 1, 0},
+                         {nx, 1, kX0, 0, 1}, {nx, ny + 2, kX0, 0, 1}};
+  auto push = [&](int count, int r0, int c0, int dr, int dc, int kind, int table, double tw) {
+    WallSeg& s = a.seg[a.nseg++];
+    s.count = count; s.r0 = r0; s.c0 = c0; s.dr = dr; s.dc = dc;
+    s.action = kind;
+    s.table = table;
+    s.iso = kind == WLBM_BC_ISOTHERMAL ? float(delta_e(tw)) : 0.f;
+  };
+  for (int k = 0; k < 4; ++k) {
+    if (bc_kind[k] == WLBM_BC_PERIODIC) continue;
+    push(edges[k].count, edges[k].r0, edges[k].c0, edges[k].dr, edges[k].dc, bc_kind[k], k,
+         t_wall[k]);
+  }
+  const int cr[4] = {1, 1, ny + 2, ny + 2}, cc[4] = {gl, gr, gl, gr};
+  const int cxw[4] = {0, 1, 0, 1}, cyw[4] = {2, 2, 3, 3};
+  for (int k = 0; k < 4; ++k) {
+    const int xw = cxw[k], yw = cyw[k];
+    if (bc_kind[xw] == WLBM_BC_PERIODIC || bc_kind[yw] == WLBM_BC_PERIODIC) continue;
+    if (bc_kind[xw] == WLBM_BC_ISOTHERMAL)
+      push(1, cr[k], cc[k], 0, 0, WLBM_BC_ISOTHERMAL, 0, t_wall[xw]);
+    else if (bc_kind[yw] == WLBM_BC_ISOTHERMAL)
+      push(1, cr[k], cc[k], 0, 0, WLBM_BC_ISOTHERMAL, 0, t_wall[yw]);
+    else
+      push(1, cr[k], cc[k], 0, 0, WLBM_BC_ADIABATIC_DIFFUSE, 4 + k, 0.0);
+  }
+  a.planes = planes;
+  a.plane = g.plane;
+  a.pitch = g.pitch;
+  a.q = g.q;
+  a.w = w_dev();
+  a.rho = rho_dev();
+  a.scale = scale;
+  a.inv_scale = inv_scale;
+}
+
+// Diffuse re-emission fractions: tables 0-3 for the walls (inward normals +x, -x, +y,
+// -y), 4-7 for the corners (quadrant diagonal, strictly inward directions only).
+static std::vector<float> rho_tables(const Lattice& L) {
+  const int q = L.q;
+  std::vector<float> rho(size_t(8) * q, 0.f);
+  const int nrm[8][2] = {{1, 0}, {-1, 0}, {0, 1}, {0, -1}, {1, 1}, {-1, 1}, {1, -1}, {-1, -1}};
+  for (int t = 0; t < 8; ++t) {
+    const int nx = nrm[t][0], ny = nrm[t][1];
+    const double len = std::sqrt(double(nx * nx + ny * ny));
+    std::vector<double> r(q, 0.0);
+    double sum = 0.0;
+    for (int i = 0; i < q; ++i) {
+      const bool inward = t < 4 ? (L.dx[i] * nx + L.dy[i] * ny > 0)
+                                : (L.dx[i] * nx > 0 && L.dy[i] * ny > 0);
+      if (!inward) continue;
+      r[i] = L.w[i] * (L.sx[i] * nx + L.sy[i] * ny) / len;
+      sum += r[i];
+    }
+    for (int i = 0; i < q; ++i) rho[size_t(t) * q + i] = float(r[i] / sum);
+  }
+  return rho;
+}
+
+extern "C" {
+
+const char* wlbm_last_error(const wlbm_handle* h) {
+  if (h) return h->err.c_str();
+  std::lock_guard<std::mutex> lk(g_err_mu);
+  return g_err.c_str();
+}
+
+wlbm_status wlbm_lattice(int32_t q, int32_t* dirs, double* weights, int8_t* worm,
+                         double* lam_corr) {
+  Lattice L;
+  if (!build_lattice(q, &L)) {
+    set_global_error("wlbm_lattice: Q must be a multiple of 8 in [8, 1024]");
+    return WLBM_ERR_INVALID_ARG;
+  }
+  for (int i = 0; i < q; ++i) {
+    if (dirs) { dirs[2 * i] = L.dx[i]; dirs[2 * i + 1] = L.dy[i]; }
+    if (weights) weights[i] = L.w[i];
+  }
+  if (worm) std::memcpy(worm, L.worm.data(), L.worm.size());
+  if (lam_corr) *lam_corr = L.lam_corr;
+  return WLBM_OK;
+}
+
+wlbm_status wlbm_schedule(int32_t q, int64_t n_steps, uint8_t* codes) {
+  Lattice L;
+  if (!build_lattice(q, &L) || n_steps < 0 || (n_steps > 0 && !codes)) {
+    set_global_error("wlbm_schedule: invalid Q, step count or output");
+    return WLBM_ERR_INVALID_ARG;
+  }
+  TasState st;
+  st.reset(q);
+  for (int64_t t = 0; t < n_steps; ++t) {
+    tas_advance(L, &st, codes + t * q);
+    for (int i = 0; i < q; ++i) codes[t * q + i] &= 0x0f;   // drop buffer parity
+  }
+  return WLBM_OK;
+}
+
+wlbm_status wlbm_create(const wlbm_grid* grid, const float* mfp_cells, double mfp_uniform,
+                        const wlbm_boundary* bc, const wlbm_allocator* alloc, void* stream,
+                        wlbm_handle** out) {
+  if (!grid || !bc || !out) {
+    set_global_error("wlbm_create: NULL grid, boundary or output pointer");
+    return WLBM_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  const wlbm_grid& G = *grid;
+  if (G.nx < 1 || G.ny < 1 || int64_t(G.nx) * G.ny > (int64_t(1) << 31) ||
+      (G.storage != WLBM_STORE_FP32_DEV && G.storage != WLBM_STORE_BF16_DEV) ||
+      (G.relax_mode != 0 && G.relax_mode != 1) || !(G.t_ref > 0) || !(G.theta > 0)) {
+    set_global_error("wlbm_create: invalid grid (sizes, storage, relax_mode, t_ref, theta)");
+    return WLBM_ERR_INVALID_ARG;
+  }
+  for (int k = 0; k < 4; ++k) {
+    if (bc->kind[k] < 0 || bc->kind[k] > 2 ||
+        (bc->kind[k] == WLBM_BC_ISOTHERMAL && !(bc->t_wall[k] > 0))) {
+      set_global_error("wlbm_create: invalid boundary kind or wall temperature");
+      return WLBM_ERR_INVALID_ARG;
+    }
+  }
+  if ((bc->kind[0] == WLBM_BC_PERIODIC) != (bc->kind[1] == WLBM_BC_PERIODIC) ||
+      (bc->kind[2] == WLBM_BC_PERIODIC) != (bc->kind[3] == WLBM_BC_PERIODIC)) {
+    set_global_error("wlbm_create: periodic walls must come in opposite pairs");
+    return WLBM_ERR_INVALID_ARG;
+  }
+  auto* h = new wlbm_handle();
+  h->storage = G.storage;
+  h->emulate_3d = G.emulate_3d ? 1 : 0;
+  h->relax_mode = G.relax_mode;
+  h->t_ref = G.t_ref;
+  h->theta = G.theta;
+  h->e_eq_ref = 1.0 / std::expm1(G.theta / G.t_ref);
+  for (int k = 0; k < 4; ++k) { h->bc_kind[k] = bc->kind[k]; h->t_wall[k] = bc->t_wall[k]; }
+  h->xper = bc->kind[0] == WLBM_BC_PERIODIC;
+  h->yper = bc->kind[2] == WLBM_BC_PERIODIC;
+  if (!build_lattice(G.q, &h->lat)) {
+    delete h;
+    set_global_error("wlbm_create: Q must be a multiple of 8 in [8, 1024]");
+    return WLBM_ERR_INVALID_ARG;
+  }
+  h->tas.reset(G.q);
+  Geom& g = h->g;
+  g.nx = G.nx; g.ny = G.ny; g.q = G.q;
+  g.pitch = int(round_up(kX0 + G.nx + 2, 32));
+  g.rows = G.ny + 4;
+  g.plane = int64_t(g.pitch) * g.rows;
+  if (alloc) h->alloc = *alloc;
+  h->stream = static_cast<cudaStream_t>(stream);
+
+  // relaxation weight (Eq. W-Kn, Eq. W-correction), stability (Appendix A: W <= 1)
+  std::vector<float> wframe;
+  auto bad = [&](wlbm_status s, const std::string& m) {
+    h->release();
+    delete h;
+    set_global_error(m);
+    return s;
+  };
+  if (mfp_cells) {
+    std::vector<float> mfp(size_t(G.nx) * G.ny);
+    if (cudaMemcpy(mfp.data(), mfp_cells, mfp.size() * 4, cudaMemcpyDeviceToHost) != cudaSuccess) {
+      cudaGetLastError();
+      return bad(WLBM_ERR_CUDA, "wlbm_create: cannot read the MFP field");
+    }
+    h->field_w = true;
+    wframe.assign(size_t(g.plane), 0.f);
+    double wmax = 0.0;
+    for (int y = 0; y < G.ny; ++y)
+      for (int x = 0; x < G.nx; ++x) {
+        const double m = mfp[size_t(y) * G.nx + x];
+        if (!(m > 0)) return bad(WLBM_ERR_INVALID_ARG, "wlbm_create: MFP must be positive");
+        const double wc = corrected_weight(m, h->lat.lam_corr, h->emulate_3d, h->relax_mode);
+        wmax = std::max(wmax, wc);
+        wframe[size_t(g.cell(x, y))] = float(wc);
+      }
+    if (wmax > 1.0)
+      return bad(WLBM_ERR_UNSTABLE, "wlbm_create: max W_corr > 1, unstable (use a larger MFP)");
+    // periodic ghost cells carry W across the link (walls keep 0)
+    auto at = [&](int r, int c) -> float& { return wframe[size_t(r) * g.pitch + c]; };
+    if (h->yper) {
+      const int c0 = h->xper ? kX0 : kGhostCol, c1 = h->xper ? kX0 + G.nx - 1 : kX0 + G.nx;
+      for (int c = c0; c <= c1; ++c) { at(1, c) = at(G.ny + 1, c); at(G.ny + 2, c) = at(2, c); }
+    }
+    if (h->xper) {
+      for (int r = 1; r <= G.ny + 2; ++r) {
+        at(r, kGhostCol) = at(r, kX0 + G.nx - 1);
+        at(r, kX0 + G.nx) = at(r, kX0);
+      }
+    }
+  } else {
+    if (!(mfp_uniform > 0))
+      return bad(WLBM_ERR_INVALID_ARG, "wlbm_create: MFP must be positive");
+    const double wc = corrected_weight(mfp_uniform, h->lat.lam_corr, h->emulate_3d, h->relax_mode);
+    if (wc > 1.0)
+      return bad(WLBM_ERR_UNSTABLE, "wlbm_create: W_corr > 1, unstable (use a larger MFP)");
+    h->w0 = float(wc);
+  }
+
+  // device memory through the caller's allocator
+  const size_t plane_bytes = size_t(g.plane) * h->elem();
+  h->planes = h->dev_alloc(2 * size_t(G.q) * plane_bytes);
+  const int n_e = h->bf16() ? 3 : 2;
+  for (int k = 0; k < n_e; ++k) h->e[k] = static_cast<float*>(h->dev_alloc(size_t(g.plane) * 4));
+  h->e_cur = 0;
+  h->e_spare = 1;
+  h->e_ref = h->bf16() ? 2 : -1;
+  h->consts = static_cast<float*>(h->dev_alloc(size_t(11) * G.q * 4));
+  h->d_codes = static_cast<uint8_t*>(h->dev_alloc(size_t(kChunk) * G.q));
+  h->d_red = static_cast<double*>(h->dev_alloc(8 * sizeof(double)));
+  if (h->field_w) h->wfield = static_cast<float*>(h->dev_alloc(size_t(g.plane) * 4));
+  if (!h->planes || !h->e[0] || !h->e[1] || (n_e == 3 && !h->e[2]) || !h->consts ||
+      !h->d_codes || !h->d_red ||
+      (h->field_w && !h->wfield))
+    return bad(WLBM_ERR_OOM, "wlbm_create: device allocation failed");
+
+  std::vector<float> consts(size_t(11) * G.q);
+  double wsum = 0.0;
+  for (int i = 0; i < G.q; ++i) wsum += double(float(h->lat.w[i]));
+  h->wsum = float(wsum);
+  for (int i = 0; i < G.q; ++i) {
+    consts[i] = float(h->lat.w[i]);
+    consts[G.q + i] = float(h->lat.sx[i]);
+    consts[2 * G.q + i] = float(h->lat.sy[i]);
+  }
+  const std::vector<float> rho = rho_tables(h->lat);
+  std::memcpy(consts.data() + 3 * G.q, rho.data(), rho.size() * 4);
+  cudaStream_t s = h->stream;
+  cudaError_t e = cudaMemsetAsync(h->planes, 0, 2 * size_t(G.q) * plane_bytes, s);
+  for (int k = 0; k < n_e && e == cudaSuccess; ++k)
+    e = cudaMemsetAsync(h->e[k], 0, size_t(g.plane) * 4, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->consts, consts.data(), consts.size() * 4, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && h->field_w)
+    e = cudaMemcpyAsync(h->wfield, wframe.data(), wframe.size() * 4, cudaMemcpyHostToDevice, s);
+  for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+    e = cudaHostAlloc(reinterpret_cast<void**>(&h->h_codes[k]), size_t(kChunk) * G.q,
+                      cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev[k], cudaEventDisableTiming);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // host vectors die here
+  if (e != cudaSuccess) {
+    const std::string m = std::string("wlbm_create: ") + cudaGetErrorString(e);
+    cudaGetLastError();
+    return bad(WLBM_ERR_CUDA, m);
+  }
+  h->build_wall_segments();
+  *out = h;
+  return WLBM_OK;
+}
+
+void wlbm_destroy(wlbm_handle* h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->stream);
+  h->release();
+  delete h;
+}
+
+wlbm_status wlbm_set_stream(wlbm_handle* h, void* stream) {
+  if (!h) return WLBM_ERR_INVALID_ARG;
+  h->stream = static_cast<cudaStream_t>(stream);
+  return WLBM_OK;
+}
+
+int64_t wlbm_step_count(const wlbm_handle* h) { return h ? h->tas.n : -1; }
+
+wlbm_status wlbm_init_temperature(wlbm_handle* h, const float* dT) {
+  if (!h) return WLBM_ERR_INVALID_ARG;
+  if (!dT) return h->fail(WLBM_ERR_INVALID_ARG, "wlbm_init_temperature: NULL dT");
+  const Geom& g = h->g;
+  h->scale = 1.f;
+  if (h->storage == WLBM_STORE_BF16_DEV) {
+    // per-run scale: the largest |e_eq(T) - e_ref| of the start field and the walls
+    std::vector<float> host(size_t(g.nx) * g.ny);
+    wlbm_status st = h->cuda(cudaMemcpyAsync(host.data(), dT, host.size() * 4,
+                                             cudaMemcpyDeviceToHost, h->stream), "init");
+    if (st == WLBM_OK) st = h->cuda(cudaStreamSynchronize(h->stream), "init");
+    if (st != WLBM_OK) return st;
+    double m = 0.0;
+    for (float v : host) m = std::max(m, std::fabs(h->delta_e(h->t_ref + double(v))));
+    // values are stored relative to the local energy, so a fraction of the largest
+    // deviation keeps them of order one
+    for (int k = 0; k < 4; ++k)
+      if (h->bc_kind[k] == WLBM_BC_ISOTHERMAL) m = std::max(m, std::fabs(h->delta_e(h->t_wall[k])));
+    h->scale = m > 0 ? float(m) : 1.f;
+  }
+  h->inv_scale = 1.f / h->scale;
+  h->build_wall_segments();
+  h->tas.reset(g.q);
+  InitArgs a{};
+  a.planes = h->planes; a.plane = g.plane; a.pitch = g.pitch; a.nx = g.nx; a.ny = g.ny; a.q = g.q;
+  a.dT = dT; a.w = h->w_dev(); a.e_cur = h->e[h->e_cur]; a.e_refp = h->ref_plane();
+  a.t_ref = h->t_ref; a.theta = h->theta; a.e_ref = h->e_eq_ref;
+  a.scale = h->scale; a.inv_scale = h->inv_scale;
+  ++h->launches;
+  return h->cuda(launch_init(h->storage, a, h->stream), "wlbm_init_temperature");
+}
+
+wlbm_status wlbm_step(wlbm_handle* h, int64_t n) {
+  if (!h) return WLBM_ERR_INVALID_ARG;
+  if (n < 0) return h->fail(WLBM_ERR_INVALID_ARG, "wlbm_step: negative step count");
+  const Geom& g = h->g;
+  const bool any_wall = h->walls.nseg > 0;
+  const bool any_per = h->xper || h->yper;
+  while (n > 0) {
+    const int ch = int(std::min<int64_t>(n, kChunk));
+    const int slot = h->slot;
+    wlbm_status st = h->cuda(cudaEventSynchronize(h->ev[slot]), "wlbm_step");
+    if (st != WLBM_OK) return st;
+    uint8_t* hc = h->h_codes[slot];
+    for (int t = 0; t < ch; ++t) tas_advance(h->lat, &h->tas, hc + size_t(t) * g.q);
+    st = h->cuda(cudaMemcpyAsync(h->d_codes, hc, size_t(ch) * g.q, cudaMemcpyHostToDevice,
+                                 h->stream), "wlbm_step: schedule upload");
+    if (st == WLBM_OK) st = h->cuda(cudaEventRecord(h->ev[slot], h->stream), "wlbm_step");
+    if (st != WLBM_OK) return st;
+    for (int t = 0; t < ch; ++t) {
+      const uint8_t* codes = h->d_codes + size_t(t) * g.q;
+      if (any_wall) {
+        WallArgs wa = h->walls;
+        wa.codes = codes;
+        wa.e_ref = h->ref_plane();
+        st = h->cuda(launch_walls(h->storage, wa, h->stream), "wlbm_step: walls");
+        if (st != WLBM_OK) return st;
+        ++h->launches;
+      }
+      if (any_per) {
+        PeriodicArgs pa{};
+        pa.planes = h->planes; pa.plane = g.plane; pa.pitch = g.pitch; pa.nx = g.nx;
+        pa.ny = g.ny; pa.q = g.q; pa.codes = codes; pa.e_cur = h->e[h->e_cur];
+        pa.e_ref = h->ref_plane();
+        pa.xper = h->xper; pa.yper = h->yper;
+        st = h->cuda(launch_periodic(h->storage, pa, h->stream), "wlbm_step: periodic");
+        if (st != WLBM_OK) return st;
+        ++h->launches;
+      }
+      StepArgs sa{};
+      sa.planes = h->planes; sa.plane = g.plane; sa.pitch = g.pitch; sa.rows = g.rows;
+      sa.nx = g.nx; sa.ny = g.ny; sa.q = g.q; sa.codes = codes; sa.w = h->w_dev();
+      sa.e_in = h->e[h->e_cur]; sa.e_out = h->e[h->e_spare]; sa.e_ref = h->ref_plane();
+      sa.wfield = h->field_w ? h->wfield : nullptr; sa.w0 = h->w0;
+      sa.scale = h->scale; sa.inv_scale = h->inv_scale; sa.wsum = h->wsum;
+      sa.xper = h->xper; sa.yper = h->yper;
+      cudaEvent_t e0 = nullptr, e1 = nullptr;
+      if (h->profiling) {
+        if (h->prof_used + 2 > h->prof_ev.size()) {
+          for (int k = 0; k < 2; ++k) {
+            cudaEvent_t ev;
+            st = h->cuda(cudaEventCreate(&ev), "wlbm_step: profiling event");
+            if (st != WLBM_OK) return st;
+            h->prof_ev.push_back(ev);
+          }
+        }
+        e0 = h->prof_ev[h->prof_used];
+        e1 = h->prof_ev[h->prof_used + 1];
+        h->prof_used += 2;
+        st = h->cuda(cudaEventRecord(e0, h->stream), "wlbm_step: profiling");
+        if (st != WLBM_OK) return st;
+      }
+      st = h->cuda(launch_step(h->storage, sa, h->stream), "wlbm_step: step");
+      if (st != WLBM_OK) return st;
+      ++h->launches;
+      if (e1) {
+        st = h->cuda(cudaEventRecord(e1, h->stream), "wlbm_step: profiling");
+        if (st != WLBM_OK) return st;
+      }
+      h->rotate_energy();
+    }
+    h->slot ^= 1;
+    n -= ch;
+  }
+  return WLBM_OK;
+}
+
+wlbm_status wlbm_profile(wlbm_handle* h, int32_t enable) {
+  if (!h) return WLBM_ERR_INVALID_ARG;
+  h->profiling = enable != 0;
+  return WLBM_OK;
+}
+
+wlbm_status wlbm_profile_read(wlbm_handle* h, double* step_ms, int64_t* step_launches,
+                              int64_t* all_launches) {
+  if (!h) return WLBM_ERR_INVALID_ARG;
+  wlbm_status st = h->cuda(cudaStreamSynchronize(h->stream), "wlbm_profile_read");
+  if (st != WLBM_OK) return st;
+  double total = 0.0;
+  for (size_t k = 0; k + 1 < h->prof_used; k += 2) {
+    float ms = 0.f;
+    st = h->cuda(cudaEventElapsedTime(&ms, h->prof_ev[k], h->prof_ev[k + 1]), "wlbm_profile_read");
+    if (st != WLBM_OK) return st;
+    total += ms;
+  }
+  if (step_ms) *step_ms = total;
+  if (step_launches) *step_launches = int64_t(h->prof_used / 2);
+  if (all_launches) *all_launches = h->launches;
+  h->prof_used = 0;
+  return WLBM_OK;
+}
+
+wlbm_status wlbm_moments(wlbm_handle* h, float* dT, float* qx, float* qy) {
+  if (!h) return WLBM_ERR_INVALID_ARG;
+  if (!dT && !qx && !qy) return WLBM_OK;
+  const Geom& g = h->g;
+  MomentArgs a{};
+  a.planes = h->planes; a.plane = g.plane; a.pitch = g.pitch; a.nx = g.nx; a.ny = g.ny;
+  a.q = g.q; a.par = h->parity_mask(); a.e_cur = h->e[h->e_cur]; a.e_refp = h->ref_plane();
+  a.w = h->w_dev(); a.sx = h->sx_dev(); a.sy = h->sy_dev(); a.dT = dT; a.qx = qx; a.qy = qy;
+  a.scale = h->scale;
+  a.e_ref = float(h->e_eq_ref);
+  a.e_ref1 = float(h->e_eq_ref + 1.0);
+  a.l_ref = float(std::log1p(1.0 / h->e_eq_ref));
+  a.theta = float(h->theta);
+  ++h->launches;
+  return h->cuda(launch_moments(h->storage, a, h->stream), "wlbm_moments");
+}
+
+wlbm_status wlbm_reduce(wlbm_handle* h, double* out) {
+  if (!h) return WLBM_ERR_INVALID_ARG;
+  if (!out) return h->fail(WLBM_ERR_INVALID_ARG, "wlbm_reduce: NULL output");
+  const Geom& g = h->g;
+  wlbm_status st = h->cuda(cudaMemsetAsync(h->d_red, 0, 4 * sizeof(double), h->stream), "reduce");
+  if (st != WLBM_OK) return st;
+  ReduceArgs a{};
+  a.planes = h->planes; a.plane = g.plane; a.pitch = g.pitch; a.nx = g.nx; a.ny = g.ny;
+  a.q = g.q; a.par = h->parity_mask(); a.e_cur = h->e[h->e_cur]; a.e_refp = h->ref_plane();
+  a.w = h->w_dev(); a.sx = h->sx_dev(); a.sy = h->sy_dev(); a.out = h->d_red; a.scale = h->scale;
+  a.xper = h->xper; a.yper = h->yper;
+  st = h->cuda(launch_reduce(h->storage, a, h->stream), "wlbm_reduce");
+  double tmp[4];
+  if (st == WLBM_OK)
+    st = h->cuda(cudaMemcpyAsync(tmp, h->d_red, sizeof(tmp), cudaMemcpyDeviceToHost, h->stream),
+                 "wlbm_reduce");
+  if (st == WLBM_OK) st = h->cuda(cudaStreamSynchronize(h->stream), "wlbm_reduce");
+  if (st != WLBM_OK) return st;
+  const double cells = double(g.nx) * g.ny;
+  out[0] = tmp[0];
+  out[1] = tmp[1];
+  out[2] = tmp[2] / cells;
+  out[3] = tmp[3] / cells;
+  return WLBM_OK;
+}
+
+static StateArgs state_args(wlbm_handle* h, float* framed) {
+  const Geom& g = h->g;
+  StateArgs a{};
+  a.planes = h->planes; a.plane = g.plane; a.pitch = g.pitch; a.nx = g.nx; a.ny = g.ny;
+  a.q = g.q; a.par = h->parity_mask(); a.framed = framed; a.e_cur = h->e[h->e_cur];
+  a.e_refp = h->ref_plane(); a.w = h->w_dev();
+  a.scale = h->scale; a.inv_scale = h->inv_scale;
+  return a;
+}
+
+wlbm_status wlbm_get_state(wlbm_handle* h, float* framed) {
+  if (!h) return WLBM_ERR_INVALID_ARG;
+  if (!framed) return h->fail(WLBM_ERR_INVALID_ARG, "wlbm_get_state: NULL output");
+  return h->cuda(launch_get_state(h->storage, state_args(h, framed), h->stream), "wlbm_get_state");
+}
+
+wlbm_status wlbm_set_state(wlbm_handle* h, const float* framed) {
+  if (!h) return WLBM_ERR_INVALID_ARG;
+  if (!framed) return h->fail(WLBM_ERR_INVALID_ARG, "wlbm_set_state: NULL input");
+  return h->cuda(launch_set_state(h->storage, state_args(h, const_cast<float*>(framed)), h->stream),
+                 "wlbm_set_state");
+}
+
+}  // extern "C"

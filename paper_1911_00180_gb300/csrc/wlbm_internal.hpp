@@ -1,0 +1,157 @@
+// Internal declarations shared by the C-ABI layer and the kernels of libwlbm.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/wlbm.h"
+#include "lattice.hpp"
+
+namespace wlbm {
+
+// Framed geometry of every plane (in cells, any element type).
+//   rows: 0 = zero pad, 1 = ghost, 2..ny+1 = interior y = 0..ny-1, ny+2 = ghost,
+//         ny+3 = zero pad.
+//   cols: kGhostCol = ghost x = -1, kGhostCol+1.. = interior, kGhostCol+nx+1 = ghost,
+//         the column after it is a zero pad; columns before kGhostCol are zero pads.
+// The left ghost column sits on a 32-element boundary so that unshifted warp accesses
+// are aligned.  Pads are never written, so shifted reads past the frame read zero.
+constexpr int kGhostCol = 32;
+constexpr int kX0 = kGhostCol + 1;
+constexpr int kMaxQ = 1024;
+
+struct Geom {
+  int nx = 0, ny = 0, q = 0;
+  int pitch = 0;        // elements per row, multiple of 32
+  int rows = 0;         // ny + 4
+  int64_t plane = 0;    // pitch * rows
+  int64_t cell(int x, int y) const { return int64_t(y + 2) * pitch + (x + kX0); }
+};
+
+struct ParityMask {
+  uint32_t bits[kMaxQ / 32];
+};
+
+// Stored plane values.  float32 storage keeps d_i = e_i - w_i e_ref directly.  bfloat16
+// storage keeps v_i = (d_i - w_i R) / scale, where R is a per-cell reference energy: the
+// local energy of the state that was read when the value was written (the previous
+// step's E).  Near local equilibrium v is small, so the bfloat16 rounding error is small
+// relative to the signal; R is kept in a third energy plane ("e_ref", nullptr for
+// float32).  Every kernel that reads or writes plane values applies the same R.
+
+// Step kernel arguments.
+struct StepArgs {
+  void* planes;          // [2][q][plane] elements of the storage type
+  int64_t plane;         // elements per plane
+  int pitch, rows, nx, ny, q;
+  const uint8_t* codes;  // this step's codes [q]: hop | paused<<3 | parity<<4
+  const float* w;        // weights [q]
+  const float* e_in;     // local energy of the current state (framed, float32)
+  const float* e_ref;    // reference of the stored current values (bfloat16 only)
+  float* e_out;          // local energy of the new state
+  const float* wfield;   // framed W_corr or nullptr (uniform)
+  float w0;              // uniform W_corr of interior cells
+  float scale, inv_scale, wsum;   // bfloat16 value scale, sum of the float weights
+  int xper, yper;        // periodic axes (uniform W: their ghost cells carry w0)
+};
+
+// Wall segment for the boundary kernel (one warp per ghost cell).
+struct WallSeg {
+  int count;             // ghost cells in this segment
+  int r0, c0, dr, dc;    // first cell (row, col) and step between cells
+  int action;            // 1 isothermal, 2 diffuse
+  int table;             // diffuse re-emission table index into rho[]
+  float iso;             // isothermal e_eq(T_w) - e_ref (times w_i per direction)
+};
+constexpr int kMaxSeg = 8;
+struct WallArgs {
+  void* planes;
+  int64_t plane;
+  int pitch, q, nseg;
+  const float* e_ref;    // reference energy of the stored values (bfloat16 only)
+  float scale, inv_scale;
+  const uint8_t* codes;  // current parity from the next step's codes
+  const float* w;
+  const float* rho;      // [8][q] re-emission fractions (0 = collected direction)
+  WallSeg seg[kMaxSeg];
+};
+
+struct PeriodicArgs {
+  void* planes;
+  int64_t plane;
+  int pitch, nx, ny, q;
+  const uint8_t* codes;
+  float* e_cur;          // local energy plane copied along with the direction planes
+  float* e_ref;          // reference energy plane (bfloat16 only), copied likewise
+  int xper, yper;
+};
+
+struct InitArgs {
+  void* planes;
+  int64_t plane;
+  int pitch, nx, ny, q;
+  const float* dT;       // interior nx*ny
+  const float* w;
+  float* e_cur;
+  float* e_refp;         // reference energy plane (bfloat16 only): set to e_cur
+  double t_ref, theta, e_ref;
+  float scale, inv_scale;
+};
+
+struct MomentArgs {
+  const void* planes;
+  int64_t plane;
+  int pitch, nx, ny, q;
+  ParityMask par;
+  const float* e_cur;
+  const float* e_refp;
+  const float* w;
+  const float* sx;
+  const float* sy;
+  float* dT;
+  float* qx;
+  float* qy;
+  float scale;
+  float e_ref, e_ref1, l_ref, theta;   // e_ref, e_ref + 1, ln(1 + 1/e_ref), theta
+};
+
+struct ReduceArgs {
+  const void* planes;
+  int64_t plane;
+  int pitch, nx, ny, q;
+  ParityMask par;
+  const float* e_cur;
+  const float* e_refp;
+  const float* w;
+  const float* sx;
+  const float* sy;
+  double* out;           // [4], zeroed before launch
+  double scale;
+  int xper, yper;
+};
+
+struct StateArgs {
+  void* planes;
+  int64_t plane;
+  int pitch, nx, ny, q;
+  ParityMask par;
+  float* framed;         // [q][ny+2][nx+2]
+  float* e_cur;
+  const float* e_refp;
+  const float* w;
+  float scale, inv_scale;
+};
+
+// Kernel launchers (k_step.cu, k_aux.cu).  Return cudaGetLastError().
+cudaError_t launch_step(int storage, const StepArgs& a, cudaStream_t s);
+cudaError_t launch_walls(int storage, const WallArgs& a, cudaStream_t s);
+cudaError_t launch_periodic(int storage, const PeriodicArgs& a, cudaStream_t s);
+cudaError_t launch_init(int storage, const InitArgs& a, cudaStream_t s);
+cudaError_t launch_moments(int storage, const MomentArgs& a, cudaStream_t s);
+cudaError_t launch_reduce(int storage, const ReduceArgs& a, cudaStream_t s);
+cudaError_t launch_get_state(int storage, const StateArgs& a, cudaStream_t s);
+cudaError_t launch_set_state(int storage, const StateArgs& a, cudaStream_t s);
+
+}  // namespace wlbm

@@ -1,0 +1,207 @@
+"""Thin ctypes binding of libwlbm (include/wlbm.h).
+
+Functions carry the C names and only marshal arguments: every step of the worm-LBM runs
+inside the library's CUDA kernels.  PyTorch supplies device memory (through the
+library's allocator callback) and the CUDA stream; tensors passed in or out are plain
+device buffers.  If the shared library is missing the import fails: there is no CPU or
+eager fallback.
+"""
+import ctypes as C
+import os
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "_lib", "libwlbm.so")
+
+WLBM_OK, WLBM_ERR_INVALID_ARG, WLBM_ERR_UNSTABLE, WLBM_ERR_OOM = 0, 1, 2, 3
+WLBM_ERR_CUDA, WLBM_ERR_TIMEOUT, WLBM_ERR_STATE = 4, 5, 6
+BC_PERIODIC, BC_ISOTHERMAL, BC_ADIABATIC_DIFFUSE = 0, 1, 2
+STORE_FP32_DEV, STORE_BF16_DEV = 0, 1
+STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "UNSTABLE", 3: "OOM", 4: "CUDA", 5: "TIMEOUT",
+                6: "STATE"}
+
+
+class wlbm_grid(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("q", C.c_int32),
+                ("storage", C.c_int32), ("emulate_3d", C.c_int32),
+                ("relax_mode", C.c_int32), ("t_ref", C.c_double), ("theta", C.c_double)]
+
+
+class wlbm_boundary(C.Structure):
+    _fields_ = [("kind", C.c_int32 * 4), ("t_wall", C.c_double * 4)]
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
+class wlbm_allocator(C.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("ctx", C.c_void_p)]
+
+
+class WlbmError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), message))
+        self.status = status
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libwlbm.so is not built (%s); run "
+                          "`python -m paper_1911_00180_gb300.build`" % LIB_PATH)
+    lib = C.CDLL(LIB_PATH)
+    vp, i32, i64, dbl = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+    sig = {
+        "wlbm_create": (C.c_int, [C.POINTER(wlbm_grid), vp, dbl, C.POINTER(wlbm_boundary),
+                                  C.POINTER(wlbm_allocator), vp, C.POINTER(vp)]),
+        "wlbm_destroy": (None, [vp]),
+        "wlbm_last_error": (C.c_char_p, [vp]),
+        "wlbm_set_stream": (C.c_int, [vp, vp]),
+        "wlbm_init_temperature": (C.c_int, [vp, vp]),
+        "wlbm_step": (C.c_int, [vp, i64]),
+        "wlbm_step_count": (i64, [vp]),
+        "wlbm_moments": (C.c_int, [vp, vp, vp, vp]),
+        "wlbm_reduce": (C.c_int, [vp, C.POINTER(dbl)]),
+        "wlbm_get_state": (C.c_int, [vp, vp]),
+        "wlbm_set_state": (C.c_int, [vp, vp]),
+        "wlbm_profile": (C.c_int, [vp, i32]),
+        "wlbm_profile_read": (C.c_int, [vp, C.POINTER(dbl), C.POINTER(i64), C.POINTER(i64)]),
+        "wlbm_lattice": (C.c_int, [i32, C.POINTER(i32), C.POINTER(dbl), C.POINTER(C.c_int8),
+                                   C.POINTER(dbl)]),
+        "wlbm_schedule": (C.c_int, [i32, i64, C.POINTER(C.c_uint8)]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+lib = _load()
+
+
+def _check(status, handle=None):
+    if status != WLBM_OK:
+        msg = lib.wlbm_last_error(handle)
+        raise WlbmError(status, msg.decode() if msg else "")
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+# ---------------------------------------------------------------- host-only queries
+def wlbm_lattice(q):
+    """Ring directions (Q, 2) int32, weights (Q,) float64, worm table (Q, M) int8,
+    Lambda_corr (Sec. 2.4-2.5), computed by the library's host code."""
+    import numpy as np
+    dirs = np.zeros(2 * q, np.int32)
+    w = np.zeros(q, np.float64)
+    worm = np.zeros(q * (q // 8), np.int8)
+    lam = C.c_double()
+    _check(lib.wlbm_lattice(q, dirs.ctypes.data_as(C.POINTER(C.c_int32)),
+                            w.ctypes.data_as(C.POINTER(C.c_double)),
+                            worm.ctypes.data_as(C.POINTER(C.c_int8)), C.byref(lam)))
+    return dirs.reshape(q, 2), w, worm.reshape(q, q // 8), lam.value
+
+
+def wlbm_schedule(q, n_steps):
+    """TAS codes (n_steps, Q) uint8: hop index | paused << 3 (Eq. algorithm)."""
+    import numpy as np
+    out = np.zeros(max(n_steps, 1) * q, np.uint8)
+    _check(lib.wlbm_schedule(q, n_steps, out.ctypes.data_as(C.POINTER(C.c_uint8))))
+    return out[:n_steps * q].reshape(n_steps, q)
+
+
+# ------------------------------------------------------------------ device handle
+class WormLBM:
+    """One worm-LBM grid on the current CUDA device (wraps a wlbm_handle*)."""
+
+    def __init__(self, nx, ny, q, mfp=None, mfp_field=None, bc=(0, 0, 0, 0),
+                 t_wall=(300.0,) * 4, storage=STORE_FP32_DEV, emulate_3d=True,
+                 relax_mode=0, t_ref=300.0, theta=624.8074248458514, stream=None,
+                 allocator=None):
+        import torch
+        self._torch = torch
+        self.nx, self.ny, self.q = nx, ny, q
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        g = wlbm_grid(nx, ny, q, storage, 1 if emulate_3d else 0, relax_mode, t_ref, theta)
+        b = wlbm_boundary((C.c_int32 * 4)(*bc), (C.c_double * 4)(*t_wall))
+        if allocator is None:
+            dev, strm = self.device.index, self.stream.cuda_stream
+
+            def _alloc(n, ctx):
+                return torch.cuda.caching_allocator_alloc(int(n), dev, strm)
+
+            def _free(p, ctx):
+                torch.cuda.caching_allocator_delete(p)
+            allocator = (_alloc, _free)
+        self._alloc_fns = (ALLOC_FN(allocator[0]), FREE_FN(allocator[1]))
+        self._alloc = wlbm_allocator(self._alloc_fns[0], self._alloc_fns[1], None)
+        mfp_t = None
+        if mfp_field is not None:
+            mfp_t = torch.as_tensor(mfp_field, dtype=torch.float32, device=self.device).contiguous()
+        handle = C.c_void_p()
+        st = lib.wlbm_create(C.byref(g), _ptr(mfp_t), float(mfp if mfp is not None else 0.0),
+                             C.byref(b), C.byref(self._alloc),
+                             C.c_void_p(self.stream.cuda_stream), C.byref(handle))
+        _check(st, None)
+        self.h = handle
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib.wlbm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # entry points ---------------------------------------------------------------
+    def wlbm_init_temperature(self, dT):
+        t = self._torch.as_tensor(dT, dtype=self._torch.float32, device=self.device).contiguous()
+        _check(lib.wlbm_init_temperature(self.h, _ptr(t)), self.h)
+        self._keep = t            # keep alive until the stream has consumed it
+
+    def wlbm_step(self, n=1):
+        _check(lib.wlbm_step(self.h, int(n)), self.h)
+
+    def wlbm_step_count(self):
+        return lib.wlbm_step_count(self.h)
+
+    def wlbm_moments(self, want_t=True, want_q=True, out=None):
+        torch = self._torch
+        if out is None:
+            mk = lambda f: torch.empty((self.ny, self.nx), dtype=torch.float32,
+                                       device=self.device) if f else None
+            out = (mk(want_t), mk(want_q), mk(want_q))
+        dT, qx, qy = out
+        _check(lib.wlbm_moments(self.h, _ptr(dT), _ptr(qx), _ptr(qy)), self.h)
+        return dT, qx, qy
+
+    def wlbm_reduce(self):
+        out = (C.c_double * 4)()
+        _check(lib.wlbm_reduce(self.h, out), self.h)
+        return list(out)
+
+    def wlbm_profile(self, enable=True):
+        _check(lib.wlbm_profile(self.h, 1 if enable else 0), self.h)
+
+    def wlbm_profile_read(self):
+        """(summed step-kernel ms, timed step launches, all kernel launches so far)."""
+        ms, n, alln = C.c_double(), C.c_int64(), C.c_int64()
+        _check(lib.wlbm_profile_read(self.h, C.byref(ms), C.byref(n), C.byref(alln)), self.h)
+        return ms.value, n.value, alln.value
+
+    def wlbm_get_state(self):
+        t = self._torch.empty((self.q, self.ny + 2, self.nx + 2), dtype=self._torch.float32,
+                              device=self.device)
+        _check(lib.wlbm_get_state(self.h, _ptr(t)), self.h)
+        return t
+
+    def wlbm_set_state(self, framed):
+        t = self._torch.as_tensor(framed, dtype=self._torch.float32, device=self.device).contiguous()
+        _check(lib.wlbm_set_state(self.h, _ptr(t)), self.h)
+        self._keep = t

@@ -1,0 +1,55 @@
+"""Helpers that run one workload through the oracle and through the CUDA library on the
+same seeded inputs (tests only)."""
+import numpy as np
+
+from oracle.stepper import WormLBM as OracleLBM
+
+THETA = 624.8074248458514
+
+
+def oracle_run(cfg, steps, state=None):
+    m = OracleLBM(cfg["nx"], cfg["ny"], cfg["q"],
+                  cfg["mfp"] if cfg.get("mfp_field") is None else cfg["mfp_field"],
+                  bc_kind=cfg["bc"], t_wall=cfg["t_wall"], emulate_3d=cfg["emulate_3d"],
+                  relax_mode=cfg.get("relax_mode", 0), theta=THETA,
+                  w_field=cfg.get("w_field"))
+    if state is None:
+        m.init_temperature(cfg["dT"].astype(np.float64))
+    else:
+        m.set_state(state)
+    m.step(steps)
+    return m
+
+
+def gpu_handle(cfg, storage=0):
+    import paper_1911_00180_gb300 as wl
+    mfp = cfg.get("mfp")
+    if mfp is None:
+        mfp = 0.0
+    return wl.WormLBM(cfg["nx"], cfg["ny"], cfg["q"], mfp=mfp,
+                      mfp_field=cfg.get("mfp_field"), bc=cfg["bc"], t_wall=cfg["t_wall"],
+                      storage=storage, emulate_3d=cfg["emulate_3d"],
+                      relax_mode=cfg.get("relax_mode", 0), theta=THETA)
+
+
+def gpu_run(cfg, steps, storage=0, state=None):
+    import torch
+    h = gpu_handle(cfg, storage)
+    if state is None:
+        h.wlbm_init_temperature(cfg["dT"])
+    else:
+        h.wlbm_init_temperature(np.zeros((cfg["ny"], cfg["nx"]), np.float32))
+        h.wlbm_set_state(torch.as_tensor(state, dtype=torch.float32))
+    h.wlbm_step(steps)
+    dT, qx, qy = h.wlbm_moments()
+    st = h.wlbm_get_state()
+    torch.cuda.synchronize()
+    out = dict(dT=dT.cpu().numpy().astype(np.float64), qx=qx.cpu().numpy().astype(np.float64),
+               qy=qy.cpu().numpy().astype(np.float64),
+               state=st.cpu().numpy().astype(np.float64), red=h.wlbm_reduce())
+    h.close()
+    return out
+
+
+def rel_linf(a, b, scale):
+    return float(np.abs(np.asarray(a) - np.asarray(b)).max() / scale)

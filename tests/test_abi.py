@@ -1,0 +1,91 @@
+"""C-ABI checks that need no GPU: the library loads, exports every declared entry point,
+its host-side lattice and TAS schedule equal the oracle's (written independently), and
+argument / stability / allocation failures come back as status codes."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import lattice as L
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def wl():
+    import paper_1911_00180_gb300 as pkg
+    return pkg
+
+
+def test_library_exports_every_declared_symbol(wl):
+    header = open(os.path.join(ROOT, "include", "wlbm.h")).read()
+    names = set(re.findall(r"\b(wlbm_[a-z_0-9]+)\s*\(", header))
+    assert {"wlbm_create", "wlbm_step", "wlbm_moments"} <= names
+    for n in sorted(names):
+        assert hasattr(wl.lib, n), n
+
+
+@pytest.mark.parametrize("q", [8, 16, 24, 64, 128, 256, 512])
+def test_library_lattice_equals_oracle(wl, q):
+    dirs, w, worm, lam = wl.wlbm_lattice(q)
+    assert [tuple(d) for d in dirs] == L.ring_directions(q)
+    assert np.allclose(w, L.angular_weights(L.ring_directions(q)), rtol=0, atol=1e-15)
+    assert worm.tolist() == L.worm_table(L.ring_directions(q))
+    assert lam == pytest.approx(L.lambda_corr(L.ring_directions(q)), abs=1e-14)
+
+
+@pytest.mark.parametrize("q,steps", [(8, 3000), (16, 2000), (64, 1500), (256, 600)])
+def test_library_schedule_equals_oracle_byte_for_byte(wl, q, steps):
+    codes = wl.wlbm_schedule(q, steps)
+    sched = L.TasSchedule(q)
+    for n in range(1, steps + 1):
+        hops, paused = sched.advance(n)
+        want = np.array(hops, np.uint8) | (np.array(paused, np.uint8) << 3)
+        assert np.array_equal(codes[n - 1], want), n
+
+
+def _create(wl, nx=16, ny=16, q=16, mfp=4.0, kinds=(0, 0, 0, 0), relax=0, alloc=None,
+            storage=0):
+    g = wl.wlbm.wlbm_grid(nx, ny, q, storage, 1, relax, 300.0, 624.8)
+    b = wl.wlbm.wlbm_boundary((C.c_int32 * 4)(*kinds), (C.c_double * 4)(300.0, 301.0, 300.0, 300.0))
+    if alloc is None:
+        fns = (wl.wlbm.ALLOC_FN(lambda n, ctx: None), wl.wlbm.FREE_FN(lambda p, ctx: None))
+    else:
+        fns = alloc
+    a = wl.wlbm.wlbm_allocator(fns[0], fns[1], None)
+    h = C.c_void_p()
+    st = wl.lib.wlbm_create(C.byref(g), None, mfp, C.byref(b), C.byref(a), None, C.byref(h))
+    return st, h, fns
+
+
+def test_create_rejects_bad_arguments(wl):
+    assert _create(wl, q=12)[0] == wl.wlbm.WLBM_ERR_INVALID_ARG
+    assert _create(wl, nx=0)[0] == wl.wlbm.WLBM_ERR_INVALID_ARG
+    assert _create(wl, kinds=(0, 1, 0, 0))[0] == wl.wlbm.WLBM_ERR_INVALID_ARG   # unpaired
+    assert b"pairs" in wl.lib.wlbm_last_error(None)
+    assert _create(wl, mfp=-1.0)[0] == wl.wlbm.WLBM_ERR_INVALID_ARG
+
+
+def test_create_rejects_unstable_relaxation(wl):
+    """Appendix A: the paused step is stable only for W <= 1.  MFP = 0.5 cell gives
+    W_corr > 1 under the paper's weight; the opt-in exponential mode accepts it."""
+    st, _, _ = _create(wl, mfp=0.5)
+    assert st == wl.wlbm.WLBM_ERR_UNSTABLE
+    assert b"W_corr" in wl.lib.wlbm_last_error(None)
+    st, _, _ = _create(wl, mfp=0.5, relax=1)     # passes the check; fails later at alloc
+    assert st == wl.wlbm.WLBM_ERR_OOM
+
+
+def test_failing_allocator_reports_oom(wl):
+    """Fault injection on the host: the allocator callback returns NULL."""
+    calls = []
+
+    def alloc(n, ctx):
+        calls.append(n)
+        return None
+    fns = (wl.wlbm.ALLOC_FN(alloc), wl.wlbm.FREE_FN(lambda p, ctx: None))
+    st, h, _ = _create(wl, alloc=fns)
+    assert st == wl.wlbm.WLBM_ERR_OOM and not h.value
+    assert calls and max(calls) >= 2 * 16 * 16 * 16 * 4

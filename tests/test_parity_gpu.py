@@ -1,0 +1,221 @@
+"""GPU parity: the CUDA library (through the C ABI) against the FP64 oracle on the same
+seeded inputs.
+
+Tolerances.  Temperature: relative L-inf of the pulse (or wall) amplitude, 1e-5 for
+float32 storage and 2e-3 for bfloat16 storage.  Per-direction state and heat flux with
+float32 storage: 1e-5 of the largest initial per-direction deviation.  With bfloat16
+storage every stored value carries a rounding of up to 2^-9 of its non-equilibrium
+part, several times over near walls (ghost values are re-stored by the wall pass and the
+step), and the heat flux is a small difference of such values: those two are held to
+1e-2 (of the largest initial deviation, and of the flux amplitude).  The ballistic limit
+is exact (no arithmetic happens there)."""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from tests._pair import gpu_run, oracle_run, rel_linf
+
+pytestmark = pytest.mark.gpu
+P, I, A = W.PERIODIC, W.ISOTHERMAL, W.ADIABATIC_DIFFUSE
+TOL32, TOL16 = 1e-5, 2e-3
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1911_00180_gb300  # noqa: F401  (fails loudly if the library is missing)
+
+
+TOL16_STATE = 1e-2
+
+
+def _compare(cfg, steps, storage=0, tol=TOL32, state_tol=None):
+    orc = oracle_run(cfg, steps)
+    gpu = gpu_run(cfg, steps, storage)
+    amp = max(float(np.abs(cfg["dT"]).max()),
+              max(abs(t - 300.0) for k, t in zip(cfg["bc"], cfg["t_wall"]) if k == I)
+              if I in cfg["bc"] else 0.0)
+    ref0 = oracle_run(cfg, 0).d
+    dscale = float(np.abs(ref0).max())
+    e_t = rel_linf(gpu["dT"], orc.temperature_dev(), amp)
+    e_s = rel_linf(gpu["state"][:, 1:-1, 1:-1], orc.d[:, 1:-1, 1:-1], dscale)
+    qx, qy = orc.heat_flux()
+    qscale = dscale if storage == 0 else float(max(np.abs(qx).max(), np.abs(qy).max()))
+    e_q = max(rel_linf(gpu["qx"], qx, qscale), rel_linf(gpu["qy"], qy, qscale))
+    assert e_t <= tol, ("T", e_t)
+    assert e_s <= (state_tol or tol), ("state", e_s)
+    assert e_q <= (state_tol or tol), ("q", e_q)
+    return orc, gpu
+
+
+def test_c1_gaussian_fp32_full_run():
+    """Gaussian pulse, 64 x 64 periodic, Q = 16, MFP = 8 cells, 500 steps."""
+    _compare(W.gaussian_c1(seed=1), 500)
+
+
+def test_c1_gaussian_bf16_full_run():
+    _compare(W.gaussian_c1(seed=1), 500, storage=1, tol=TOL16, state_tol=TOL16_STATE)
+
+
+def test_init_roundtrip_temperature():
+    cfg = W.gaussian_c1(seed=3)
+    gpu = gpu_run(cfg, 0)
+    assert rel_linf(gpu["dT"], cfg["dT"], 1.0) <= TOL32
+
+
+@pytest.mark.parametrize("q", [8, 16, 64])
+def test_ballistic_limit_bitwise(q):
+    """MFP = inf (W = 0): pure advection, so GPU and oracle agree bit for bit."""
+    nx, ny = 45, 38
+    rng = np.random.default_rng(q)
+    state = np.zeros((q, ny + 2, nx + 2))
+    state[:, 1:-1, 1:-1] = rng.standard_normal((q, ny, nx)).astype(np.float32)
+    cfg = dict(nx=nx, ny=ny, q=q, mfp=math.inf, bc=(P,) * 4, t_wall=(300.0,) * 4,
+               emulate_3d=True, dT=np.zeros((ny, nx), np.float32))
+    orc = oracle_run(dict(cfg, w_field=0.0), 47, state=state)
+    gpu = gpu_run(cfg, 47, state=state)
+    assert np.array_equal(gpu["state"][:, 1:-1, 1:-1], orc.d[:, 1:-1, 1:-1])
+
+
+WALL_CASES = [
+    ((I, I, A, A), (301.0, 300.0, 300.0, 300.0)),     # in-plane film
+    ((A, A, A, A), (300.0,) * 4),                     # adiabatic box
+    ((P, P, A, A), (300.0,) * 4),
+    ((A, A, P, P), (300.0,) * 4),
+    ((I, I, P, P), (300.6, 299.7, 300.0, 300.0)),     # cross-plane
+    ((P, P, I, A), (300.0, 300.0, 300.8, 300.0)),
+    ((I, A, I, A), (300.9, 300.0, 299.4, 300.0)),
+]
+
+
+@pytest.mark.parametrize("kinds,tw", WALL_CASES)
+@pytest.mark.parametrize("nx,ny,q", [(61, 37, 16), (130, 9, 32)])
+def test_walls_parity_ragged_grids(kinds, tw, nx, ny, q):
+    cfg = dict(nx=nx, ny=ny, q=q, mfp=3.0, bc=kinds, t_wall=tw, emulate_3d=True,
+               dT=W.random_dT(nx, ny, seed=nx * ny + q, scale=0.4))
+    _compare(cfg, 120)
+
+
+@pytest.mark.parametrize("kinds,tw", [WALL_CASES[1], WALL_CASES[2], WALL_CASES[4],
+                                      WALL_CASES[6]])
+def test_walls_parity_bf16(kinds, tw):
+    """bfloat16 storage through every wall kind (values stored against the local
+    reference energy in the wall pass as well as in the step)."""
+    nx, ny, q = 77, 29, 16
+    cfg = dict(nx=nx, ny=ny, q=q, mfp=3.0, bc=kinds, t_wall=tw, emulate_3d=True,
+               dT=W.random_dT(nx, ny, seed=nx * ny + q, scale=0.4))
+    _compare(cfg, 120, storage=1, tol=TOL16, state_tol=TOL16_STATE)
+
+
+def test_mfp_field_parity():
+    """Per-cell MFP (log-normal field) with isothermal x walls and periodic y."""
+    n = 96
+    mfp = W.lognormal_mfp(n, n + 7, seed=5, corr=8.0)
+    cfg = dict(nx=n, ny=n + 7, q=16, mfp=None, mfp_field=mfp, bc=(I, I, P, P),
+               t_wall=(300.5, 300.0, 300.0, 300.0), emulate_3d=True,
+               dT=W.gaussian_field(n, n + 7, [(48.0, 50.0)], [10.0], [1.0]).astype(np.float32))
+    _compare(cfg, 150)
+
+
+def test_bf16_film_parity():
+    cfg = W.film_c3(kn=0.5, nx=200, ny=24, q=32)
+    _compare(cfg, 300, storage=1, tol=TOL16, state_tol=TOL16_STATE)
+
+
+def test_exponential_relaxation_mode_parity():
+    """MFP = 0.5 cell needs the opt-in exponential weight (the paper's is unstable)."""
+    cfg = W.pulses_c2(seed=2, n=64, q=64, mfp=0.5, npulse=3, relax_mode=1)
+    _compare(cfg, 80)
+
+
+@pytest.mark.parametrize("nx,ny,kinds", [(1, 1, (P,) * 4), (1, 7, (P, P, A, A)),
+                                         (5, 1, (I, I, P, P)), (2, 3, (A, A, A, A))])
+def test_degenerate_grids(nx, ny, kinds):
+    cfg = dict(nx=nx, ny=ny, q=8, mfp=2.0, bc=kinds, t_wall=(300.5, 300.0, 300.2, 300.0),
+               emulate_3d=True, dT=W.random_dT(nx, ny, seed=11, scale=0.5))
+    _compare(cfg, 40)
+
+
+def test_energy_conservation_fp64_reductions():
+    """Periodic grid: the FP64 total energy of the float32 state drifts by round-off
+    only; an adiabatic box keeps interior + wall energy."""
+    import paper_1911_00180_gb300 as wl
+    for kinds in [(P,) * 4, (A,) * 4]:
+        cfg = dict(nx=256, ny=200, q=32, mfp=4.0, bc=kinds, t_wall=(300.0,) * 4,
+                   emulate_3d=True, dT=W.random_dT(256, 200, seed=9, scale=1.0))
+        orc = oracle_run(cfg, 0)
+        orc.apply_bc()
+        e0 = orc.total_energy(include_frame=True)
+        gpu = gpu_run(cfg, 300)
+        scale = float(np.abs(orc.d).sum())
+        assert abs(gpu["red"][1] - e0) <= 1e-6 * scale
+
+
+def _window_oracle(cfg, cx, cy, steps, pad):
+    """Oracle on a periodic window around (cx, cy): the update is local (one cell per
+    step), so the centre after `steps` steps is exact when pad > steps."""
+    nx, ny = cfg["nx"], cfg["ny"]
+    xs = (np.arange(cx - pad, cx + pad + 1)) % nx
+    ys = (np.arange(cy - pad, cy + pad + 1)) % ny
+    sub = dict(cfg, nx=len(xs), ny=len(ys), dT=cfg["dT"][np.ix_(ys, xs)])
+    return oracle_run(sub, steps)
+
+
+def _sampled_full_size(cfg, steps, samples, window_fn):
+    """Run the full-size grid on the GPU (the benchmark launch path), then check sampled
+    cells one by one against the oracle on a window around each."""
+    import torch
+    from oracle import lattice as L
+    from tests._pair import gpu_handle
+    h = gpu_handle(cfg)
+    h.wlbm_init_temperature(cfg["dT"])
+    h.wlbm_step(steps)
+    dT, _, _ = h.wlbm_moments(want_q=False)
+    state = h.wlbm_get_state()
+    torch.cuda.synchronize()
+    w = L.angular_weights(L.ring_directions(cfg["q"]))
+    dscale = float(w.max() * (L.e_eq(301.0, 624.8074248458514) - L.e_eq(300.0, 624.8074248458514)))
+    for (cx, cy) in samples:
+        orc, (ox, oy) = window_fn(cfg, cx, cy, steps)
+        assert abs(float(dT[cy, cx]) - orc.temperature_dev()[oy, ox]) <= TOL32
+        got = state[:, cy + 1, cx + 1].double().cpu().numpy()
+        want = orc.d[:, oy + 1, ox + 1]
+        assert np.abs(got - want).max() <= TOL32 * dscale
+    h.close()
+
+
+def test_full_size_c2_sampled_cells():
+    """2048 x 2048, Q = 64, periodic, 16 pulses (the benchmark workload)."""
+    cfg = W.pulses_c2(seed=2)
+    steps, pad = 16, 18
+    rng = np.random.default_rng(0)
+    samples = [tuple(int(v) for v in rng.integers(0, 2048, size=2)) for _ in range(5)]
+    # plus the hottest cell, where the pulse signal is largest
+    cy, cx = np.unravel_index(np.argmax(cfg["dT"]), cfg["dT"].shape)
+    samples.append((int(cx), int(cy)))
+
+    def window(cfg, cx, cy, steps):
+        return _window_oracle(cfg, cx, cy, steps, pad), (pad, pad)
+    _sampled_full_size(cfg, steps, samples, window)
+
+
+def test_full_size_c3_film_sampled_cells():
+    """4096 x 256 film, Q = 128, isothermal x walls, diffuse y walls: sampled cells
+    (including ones next to the diffuse walls) against the oracle on an x-window that
+    keeps the full film thickness and its walls."""
+    cfg = W.film_c3(kn=1.0)
+    steps, pad = 12, 14
+    samples = [(1000, 0), (2500, 255), (3100, 128), (7, 40), (4090, 200)]
+
+    def window(cfg, cx, cy, steps):
+        # x-window with the film's own walls: where the window is cut inside the film
+        # the (artificial) wall is more than `steps` cells from the sample, so it cannot
+        # reach it; where the window meets a real wall, that wall is exact.
+        x0, x1 = max(cx - pad, 0), min(cx + pad, cfg["nx"] - 1)
+        sub = dict(cfg, nx=x1 - x0 + 1, dT=cfg["dT"][:, x0:x1 + 1])
+        return oracle_run(sub, steps), (cx - x0, cy)
+    _sampled_full_size(cfg, steps, samples, window)
