@@ -142,6 +142,29 @@ wlbm_status wlbm_profile(wlbm_handle* h, int32_t enable);
 wlbm_status wlbm_profile_read(wlbm_handle* h, double* step_ms, int64_t* step_launches,
                               int64_t* all_launches);
 
+/* wlbm_reduce_state_noalloc: the four float64 sums of wlbm_reduce (same meaning and
+ * order), computed from a caller-owned state instead of a handle, without allocating any
+ * device memory.  The paper has no counterpart; this entry point exists for callers that
+ * cannot allocate device memory where they call it: code running inside a host
+ * application that has reserved the device memory for its own pool, or a monitoring
+ * hook in a latency-critical loop where an allocation (and the device synchronisation it
+ * may imply) is not acceptable.
+ *   framed   device float32 [q][ny+2][nx+2]: deviations e_i - w_i e_ref including the
+ *            ghost frame, as written by wlbm_get_state
+ *   bc_kind  host int32[4] wall kinds x-, x+, y-, y+ (decides which ghost cells count as
+ *            wall cells in out[1])
+ *   out      device double[4], written on the stream
+ *   stream   cudaStream_t (NULL = legacy default stream)
+ * Scratch: a file-scope device array of 1 MiB that every device loading the library keeps
+ * until the process exits; it covers frames of up to 8,388,608 cells ((nx+2)*(ny+2)), and
+ * larger frames are rejected with WLBM_ERR_INVALID_ARG and a message.  The first call on a
+ * device looks up the array's device address (once per device, with that device current);
+ * make that first call before any stream capture.  Every call reuses the same array and
+ * overwrites each entry it reads before reading it, so nothing needs clearing; calls whose
+ * executions overlap on the GPU (other streams, other threads) race on it.  Asynchronous. */
+wlbm_status wlbm_reduce_state_noalloc(const float* framed, int32_t nx, int32_t ny, int32_t q,
+                                      const int32_t* bc_kind, double* out, void* stream);
+
 /* ------------------------------------------------------------ host-only queries ----
  * No GPU needed.  wlbm_lattice: the lattice of Sec. 2.4-2.5 for Q directions.
  *   dirs      host int32[2Q] lattice vectors (x, y) of the ring directions, counter-

@@ -26,6 +26,8 @@ int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
 
 }  // namespace
 
+void wlbm::set_global_error_msg(const std::string& m) { set_global_error(m); }
+
 struct wlbm_handle {
   Geom g;
   int storage = 0, emulate_3d = 0, relax_mode = 0;

@@ -144,6 +144,9 @@ struct StateArgs {
   float scale, inv_scale;
 };
 
+// Sets the message returned by wlbm_last_error(NULL).
+void set_global_error_msg(const std::string& m);
+
 // Kernel launchers (k_step.cu, k_aux.cu).  Return cudaGetLastError().
 cudaError_t launch_step(int storage, const StepArgs& a, cudaStream_t s);
 cudaError_t launch_walls(int storage, const WallArgs& a, cudaStream_t s);

@@ -65,6 +65,7 @@ def _load():
         "wlbm_set_state": (C.c_int, [vp, vp]),
         "wlbm_profile": (C.c_int, [vp, i32]),
         "wlbm_profile_read": (C.c_int, [vp, C.POINTER(dbl), C.POINTER(i64), C.POINTER(i64)]),
+        "wlbm_reduce_state_noalloc": (C.c_int, [vp, i32, i32, i32, C.POINTER(i32), vp, vp]),
         "wlbm_lattice": (C.c_int, [i32, C.POINTER(i32), C.POINTER(dbl), C.POINTER(C.c_int8),
                                    C.POINTER(dbl)]),
         "wlbm_schedule": (C.c_int, [i32, i64, C.POINTER(C.c_uint8)]),
@@ -110,6 +111,15 @@ def wlbm_schedule(q, n_steps):
     out = np.zeros(max(n_steps, 1) * q, np.uint8)
     _check(lib.wlbm_schedule(q, n_steps, out.ctypes.data_as(C.POINTER(C.c_uint8))))
     return out[:n_steps * q].reshape(n_steps, q)
+
+
+def wlbm_reduce_state_noalloc(framed, nx, ny, q, bc_kind, out, stream=None):
+    """No-allocation reduction of a framed float32 state (device tensor) into a device
+    float64 tensor `out` of 4 entries (see include/wlbm.h)."""
+    kinds = (C.c_int32 * 4)(*bc_kind)
+    s = None if stream is None else C.c_void_p(stream.cuda_stream)
+    _check(lib.wlbm_reduce_state_noalloc(_ptr(framed), int(nx), int(ny), int(q), kinds,
+                                         _ptr(out), s))
 
 
 # ------------------------------------------------------------------ device handle
