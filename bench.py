@@ -51,6 +51,8 @@ def parse():
                    help="pulses: 2048^2 periodic Q=64 (default); film: 4096x256 in-plane "
                         "film, Q=128, isothermal x walls, diffuse y walls (Kn = 1)")
     p.add_argument("--e2e-steps", type=int, default=3)
+    p.add_argument("--variant", type=int, default=None,
+                   help="step kernel: 0 register-pipelined, 1 bulk-copy ring (library default)")
     p.add_argument("--no-extras", action="store_true",
                    help="skip e2e, cpu baseline and clock sampling (profiling runs)")
     return p.parse_args()
@@ -201,6 +203,8 @@ def main():
         h = wl.WormLBM(cfg["nx"], cfg["ny"], cfg["q"], mfp=cfg["mfp"], bc=cfg["bc"],
                        t_wall=cfg["t_wall"], storage=storage, emulate_3d=cfg["emulate_3d"],
                        relax_mode=cfg["relax_mode"], stream=stream)
+        if args.variant is not None:
+            h.wlbm_set_option(wl.wlbm.OPT_STEP_VARIANT, args.variant)
         dT = torch.as_tensor(cfg["dT"]).to("cuda", non_blocking=False)
         h.wlbm_init_temperature(dT)
         h.wlbm_step(args.warmup)
@@ -224,6 +228,7 @@ def main():
         clk = clocks.stop() if clocks else None
         elapsed_ms = ev0.elapsed_time(ev1)
         step_ms, step_launches, launches1 = h.wlbm_profile_read()
+        h.wlbm_check()
         t = torch.tensor([elapsed_ms], device="cuda", dtype=torch.float64)
         if world > 1:
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -284,6 +289,8 @@ def main():
                            % (cfg["nx"], cfg["ny"], cfg["q"], args.storage, cfg["mfp"])),
                        "nx": cfg["nx"], "ny": cfg["ny"], "q": cfg["q"],
                        "mfp_cells": cfg["mfp"], "parallelism": "replicas x%d" % world,
+                       "step_kernel": "bulk-copy ring" if args.variant in (None, 1)
+                                      else "register-pipelined",
                        "l2": "state %.2f GB > L2 (no flush needed)"
                              % (2 * cfg["q"] * cells * (4 if args.storage == "fp32" else 2) / 1e9)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

@@ -132,6 +132,37 @@ wlbm_status wlbm_reduce(wlbm_handle* h, double* out);
 wlbm_status wlbm_get_state(wlbm_handle* h, float* framed);
 wlbm_status wlbm_set_state(wlbm_handle* h, const float* framed);
 
+/* ------------------------------------------------------------------------ adjoint --
+ * Reverse-mode gradients of a run (the paper has no adjoint; the reverse step is the
+ * exact transpose of Eq. lbm-energy / Eq. algorithm and of the wall passes of Sec. 2.6).
+ * float32 storage only.
+ *
+ * wlbm_adjoint_forward: wlbm_init_temperature(dT0) followed by n_steps steps, saving the
+ * state every ckpt_every steps (checkpoints, library memory: ceil(n/K) states plus K
+ * states of recompute tape).  The handle's state afterwards is the final state.
+ *   dT0  device nx*ny float32 start field (K), copied.
+ *
+ * wlbm_adjoint_backward: given dJ/dT of the final temperature field, returns
+ *   dJ_dmfp   device nx*ny float32: dJ / dMFP per cell (through W_corr, Eq. W-correction)
+ *   dJ_dTwall host double[4]: dJ / dT_wall for isothermal walls (0 for other walls)
+ *   dJ_ddT0   device nx*ny float32: dJ / d(start field)
+ * (any output may be NULL).  Each segment between checkpoints is recomputed from its
+ * checkpoint, then swept backwards.  Requires that the handle was not stepped after the
+ * checkpointed forward run (WLBM_ERR_STATE otherwise).  Synchronous. */
+wlbm_status wlbm_adjoint_forward(wlbm_handle* h, const float* dT0, int64_t n_steps,
+                                 int32_t ckpt_every);
+wlbm_status wlbm_adjoint_backward(wlbm_handle* h, const float* dJ_dT, float* dJ_dmfp,
+                                  double* dJ_dTwall, float* dJ_ddT0);
+
+/* wlbm_set_option: tuning knobs that do not change results.
+ *   WLBM_OPT_STEP_VARIANT  0: step kernel with register-pipelined loads; 1 (default):
+ *                          step kernel with a per-warp ring of bulk async copies.
+ * wlbm_check: synchronises the stream and returns WLBM_ERR_TIMEOUT if a bounded wait
+ * inside a kernel gave up since the last check (the status is then cleared). */
+enum { WLBM_OPT_STEP_VARIANT = 1 };
+wlbm_status wlbm_set_option(wlbm_handle* h, int32_t key, int64_t value);
+wlbm_status wlbm_check(wlbm_handle* h);
+
 /* wlbm_profile: enable (1) or disable (0) CUDA-event timing of every launch of the
  * fused step kernel on the handle's stream (an event pair around each launch).
  * wlbm_profile_read: synchronises the stream, returns the summed duration (ms) and count

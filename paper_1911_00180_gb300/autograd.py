@@ -1,0 +1,39 @@
+"""torch.autograd wrapper of a checkpointed worm-LBM run.
+
+`wlbm_run(mfp_field, t_wall, dT0, spec)` runs `spec["steps"]` steps from the start field
+dT0 (K above T_ref) with per-cell mean free paths `mfp_field` (cells) and wall
+temperatures `t_wall` (4, K) and returns the final temperature deviation field.  Its
+backward pass calls the library's adjoint (checkpoints every `spec["ckpt"]` steps,
+recompute in between) and returns dJ/dMFP, dJ/dT_wall and dJ/d(dT0).  All arithmetic runs
+in libwlbm's kernels; this module only moves tensors.
+"""
+import torch
+
+from .wlbm import WormLBM
+
+
+class _WormLBMRun(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, mfp_field, t_wall, dT0, spec):
+        h = WormLBM(spec["nx"], spec["ny"], spec["q"], mfp_field=mfp_field.detach(),
+                    bc=spec["bc"], t_wall=tuple(float(t) for t in t_wall.detach().cpu()),
+                    emulate_3d=spec.get("emulate_3d", True),
+                    relax_mode=spec.get("relax_mode", 0))
+        h.wlbm_adjoint_forward(dT0.detach(), spec["steps"], spec["ckpt"])
+        dT, _, _ = h.wlbm_moments(want_q=False)
+        ctx.h = h
+        ctx.t_wall_device = t_wall.device
+        return dT.clone()
+
+    @staticmethod
+    def backward(ctx, grad_dT):
+        h = ctx.h
+        g_mfp, g_tw, g_dT0 = h.wlbm_adjoint_backward(grad_dT.contiguous())
+        h.close()
+        ctx.h = None
+        return (g_mfp, torch.tensor(g_tw, dtype=torch.float64, device=ctx.t_wall_device),
+                g_dT0, None)
+
+
+def wlbm_run(mfp_field, t_wall, dT0, spec):
+    return _WormLBMRun.apply(mfp_field, t_wall, dT0, spec)

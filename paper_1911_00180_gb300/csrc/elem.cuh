@@ -29,6 +29,7 @@ struct Elem<float> {
     return v;
   }
   static __device__ __forceinline__ float round(float v) { return v; }
+  static __device__ __forceinline__ float ld_shared(const float* p) { return *p; }
 };
 
 template <>
@@ -56,6 +57,9 @@ struct Elem<__nv_bfloat16> {
     return widen(b);
   }
   static __device__ __forceinline__ float round(float v) { return widen(narrow(v)); }
+  static __device__ __forceinline__ float ld_shared(const __nv_bfloat16* p) {
+    return widen(*reinterpret_cast<const unsigned short*>(p));
+  }
 };
 
 __device__ __forceinline__ float warp_sum(float v) {

@@ -53,11 +53,18 @@ __global__ void k_walls(const WallArgs a) {
   const int64_t off = int64_t(g.r0 + idx * g.dr) * a.pitch + (g.c0 + idx * g.dc);
   T* planes = static_cast<T*>(a.planes);
   auto ptr = [&](int i) {
-    return planes + int64_t(((a.codes[i] >> 4) & 1) * a.q + i) * a.plane + off;
+    const int par = a.tape ? 0 : (a.codes[i] >> 4) & 1;
+    return planes + int64_t(par * a.q + i) * a.plane + off;
   };
   if (g.action == WLBM_BC_ISOTHERMAL) {
-    for (int i = lane; i < a.q; i += 32)
-      dev_store(ptr(i), a.w[i] * g.iso, a.w[i], a.e_ref, off, a.scale, a.inv_scale);
+    if (a.e_ref) {
+      // bfloat16: make the wall's own equilibrium the reference of the cell, so the
+      // stored values are exactly zero and decode to w_i (e_eq(T_w) - e_ref) unrounded
+      for (int i = lane; i < a.q; i += 32) Elem<T>::st(ptr(i), 0.f);
+      if (lane == 0) a.e_ref[off] = g.iso;
+    } else {
+      for (int i = lane; i < a.q; i += 32) Elem<T>::st(ptr(i), a.w[i] * g.iso);
+    }
     return;
   }
   const float* rho = a.rho + int64_t(g.table) * a.q;
@@ -104,7 +111,8 @@ __global__ void k_periodic(const PeriodicArgs a) {
   } else if (p == a.q + 1) {
     a.e_ref[od] = a.e_ref[os];
   } else {
-    T* base = static_cast<T*>(a.planes) + int64_t(((a.codes[p] >> 4) & 1) * a.q + p) * a.plane;
+    const int par = a.tape ? 0 : (a.codes[p] >> 4) & 1;
+    T* base = static_cast<T*>(a.planes) + int64_t(par * a.q + p) * a.plane;
     base[od] = base[os];
   }
 }

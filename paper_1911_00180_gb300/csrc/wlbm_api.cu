@@ -1,4 +1,5 @@
 // C ABI of libwlbm: handle lifecycle, boundary tables, the per-step launch sequence.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -46,11 +47,12 @@ struct wlbm_handle {
   void* planes = nullptr;     // [2][q][plane] storage elements
   float* e[3] = {nullptr, nullptr, nullptr};   // local-energy planes (3 for bfloat16)
   int e_cur = 0, e_ref = -1, e_spare = 1;      // roles of the energy planes
-  float wsum = 1.f;                            // sum of the float32 weights
   float* wfield = nullptr;    // framed W_corr (per-cell MFP only)
   float* consts = nullptr;    // w[q], sx[q], sy[q], rho[8][q]
   uint8_t* d_codes = nullptr; // [kChunk][q]
   double* d_red = nullptr;    // [4]
+  int* d_status = nullptr;    // bit 0: a bounded device wait gave up
+  int step_variant = 1;       // 0 register-pipelined, 1 per-warp bulk-copy ring
   std::vector<void*> owned;
   // host staging
   uint8_t* h_codes[2] = {nullptr, nullptr};
@@ -58,6 +60,26 @@ struct wlbm_handle {
   int slot = 0;
   WallArgs walls{};
   std::string err;
+  // MFP kept on the host for the adjoint's dW_corr/dMFP
+  std::vector<float> mfp_host;
+  double mfp_uniform = 0.0;
+  // adjoint (checkpointed forward + reverse sweep), float32 storage only
+  struct Adj {
+    int64_t n = 0;
+    int k = 0, nck = 0;
+    bool ready = false;
+    float* ckpt = nullptr;     // [nck][q][plane] states before the boundary pass
+    float* ckpt_e = nullptr;   // [nck][plane] their local energy
+    float* tape = nullptr;     // [k][q][plane] recomputed step inputs of one segment
+    float* lam[2] = {nullptr, nullptr};
+    float* erec[2] = {nullptr, nullptr};
+    float* gw = nullptr;       // framed dJ/dW_corr
+    float* dwc = nullptr;      // nx*ny dW_corr/dMFP
+    float* dT0 = nullptr;      // nx*ny start field
+    double* gtw = nullptr;     // [4] sum_i w_i lambda_i at isothermal ghosts
+    uint8_t* codes = nullptr;  // [n][q] schedule of the run
+    std::vector<void*> bufs;
+  } adj;
   // launch accounting and optional per-launch timing of the step kernel
   int64_t launches = 0;
   bool profiling = false;
@@ -89,6 +111,18 @@ struct wlbm_handle {
     }
     if (p) owned.push_back(p);
     return p;
+  }
+  void dev_free(void* p) {
+    for (size_t k = 0; k < owned.size(); ++k) {
+      if (owned[k] != p) continue;
+      if (alloc.alloc) {
+        if (alloc.free) alloc.free(p, alloc.ctx);
+      } else {
+        cudaFree(p);
+      }
+      owned.erase(owned.begin() + long(k));
+      return;
+    }
   }
   void release() {
     for (void* p : owned) {
@@ -141,17 +175,17 @@ void wlbm_handle::build_wall_segments() {
   struct Edge { int count, r0, c0, dr, dc; };
   const Edge edges[4] = {{ny, 2, gl, 1, 0}, {ny, 2, gr, 1, 0},
                          {nx, 1, kX0, 0, 1}, {nx, ny + 2, kX0, 0, 1}};
-  auto push = [&](int count, int r0, int c0, int dr, int dc, int kind, int table, double tw) {
+  auto push = [&](int count, int r0, int c0, int dr, int dc, int kind, int table, int wall) {
     WallSeg& s = a.seg[a.nseg++];
     s.count = count; s.r0 = r0; s.c0 = c0; s.dr = dr; s.dc = dc;
     s.action = kind;
     s.table = table;
-    s.iso = kind == WLBM_BC_ISOTHERMAL ? float(delta_e(tw)) : 0.f;
+    s.wall = wall;
+    s.iso = kind == WLBM_BC_ISOTHERMAL ? float(delta_e(t_wall[wall])) : 0.f;
   };
   for (int k = 0; k < 4; ++k) {
     if (bc_kind[k] == WLBM_BC_PERIODIC) continue;
-    push(edges[k].count, edges[k].r0, edges[k].c0, edges[k].dr, edges[k].dc, bc_kind[k], k,
-         t_wall[k]);
+    push(edges[k].count, edges[k].r0, edges[k].c0, edges[k].dr, edges[k].dc, bc_kind[k], k, k);
   }
   const int cr[4] = {1, 1, ny + 2, ny + 2}, cc[4] = {gl, gr, gl, gr};
   const int cxw[4] = {0, 1, 0, 1}, cyw[4] = {2, 2, 3, 3};
@@ -159,11 +193,11 @@ void wlbm_handle::build_wall_segments() {
     const int xw = cxw[k], yw = cyw[k];
     if (bc_kind[xw] == WLBM_BC_PERIODIC || bc_kind[yw] == WLBM_BC_PERIODIC) continue;
     if (bc_kind[xw] == WLBM_BC_ISOTHERMAL)
-      push(1, cr[k], cc[k], 0, 0, WLBM_BC_ISOTHERMAL, 0, t_wall[xw]);
+      push(1, cr[k], cc[k], 0, 0, WLBM_BC_ISOTHERMAL, 0, xw);
     else if (bc_kind[yw] == WLBM_BC_ISOTHERMAL)
-      push(1, cr[k], cc[k], 0, 0, WLBM_BC_ISOTHERMAL, 0, t_wall[yw]);
+      push(1, cr[k], cc[k], 0, 0, WLBM_BC_ISOTHERMAL, 0, yw);
     else
-      push(1, cr[k], cc[k], 0, 0, WLBM_BC_ADIABATIC_DIFFUSE, 4 + k, 0.0);
+      push(1, cr[k], cc[k], 0, 0, WLBM_BC_ADIABATIC_DIFFUSE, 4 + k, xw);
   }
   a.planes = planes;
   a.plane = g.plane;
@@ -303,6 +337,7 @@ wlbm_status wlbm_create(const wlbm_grid* grid, const float* mfp_cells, double mf
       return bad(WLBM_ERR_CUDA, "wlbm_create: cannot read the MFP field");
     }
     h->field_w = true;
+    h->mfp_host = mfp;
     wframe.assign(size_t(g.plane), 0.f);
     double wmax = 0.0;
     for (int y = 0; y < G.ny; ++y)
@@ -334,11 +369,13 @@ wlbm_status wlbm_create(const wlbm_grid* grid, const float* mfp_cells, double mf
     if (wc > 1.0)
       return bad(WLBM_ERR_UNSTABLE, "wlbm_create: W_corr > 1, unstable (use a larger MFP)");
     h->w0 = float(wc);
+    h->mfp_uniform = mfp_uniform;
   }
 
   // device memory through the caller's allocator
   const size_t plane_bytes = size_t(g.plane) * h->elem();
-  h->planes = h->dev_alloc(2 * size_t(G.q) * plane_bytes);
+  // slack after the last plane: bulk row copies of the last tile may read past the row
+  h->planes = h->dev_alloc(2 * size_t(G.q) * plane_bytes + 1024);
   const int n_e = h->bf16() ? 3 : 2;
   for (int k = 0; k < n_e; ++k) h->e[k] = static_cast<float*>(h->dev_alloc(size_t(g.plane) * 4));
   h->e_cur = 0;
@@ -347,16 +384,14 @@ wlbm_status wlbm_create(const wlbm_grid* grid, const float* mfp_cells, double mf
   h->consts = static_cast<float*>(h->dev_alloc(size_t(11) * G.q * 4));
   h->d_codes = static_cast<uint8_t*>(h->dev_alloc(size_t(kChunk) * G.q));
   h->d_red = static_cast<double*>(h->dev_alloc(8 * sizeof(double)));
+  h->d_status = static_cast<int*>(h->dev_alloc(256));
   if (h->field_w) h->wfield = static_cast<float*>(h->dev_alloc(size_t(g.plane) * 4));
   if (!h->planes || !h->e[0] || !h->e[1] || (n_e == 3 && !h->e[2]) || !h->consts ||
-      !h->d_codes || !h->d_red ||
+      !h->d_codes || !h->d_red || !h->d_status ||
       (h->field_w && !h->wfield))
     return bad(WLBM_ERR_OOM, "wlbm_create: device allocation failed");
 
   std::vector<float> consts(size_t(11) * G.q);
-  double wsum = 0.0;
-  for (int i = 0; i < G.q; ++i) wsum += double(float(h->lat.w[i]));
-  h->wsum = float(wsum);
   for (int i = 0; i < G.q; ++i) {
     consts[i] = float(h->lat.w[i]);
     consts[G.q + i] = float(h->lat.sx[i]);
@@ -365,7 +400,8 @@ wlbm_status wlbm_create(const wlbm_grid* grid, const float* mfp_cells, double mf
   const std::vector<float> rho = rho_tables(h->lat);
   std::memcpy(consts.data() + 3 * G.q, rho.data(), rho.size() * 4);
   cudaStream_t s = h->stream;
-  cudaError_t e = cudaMemsetAsync(h->planes, 0, 2 * size_t(G.q) * plane_bytes, s);
+  cudaError_t e = cudaMemsetAsync(h->planes, 0, 2 * size_t(G.q) * plane_bytes + 1024, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->d_status, 0, 256, s);
   for (int k = 0; k < n_e && e == cudaSuccess; ++k)
     e = cudaMemsetAsync(h->e[k], 0, size_t(g.plane) * 4, s);
   if (e == cudaSuccess)
@@ -477,7 +513,8 @@ wlbm_status wlbm_step(wlbm_handle* h, int64_t n) {
       sa.nx = g.nx; sa.ny = g.ny; sa.q = g.q; sa.codes = codes; sa.w = h->w_dev();
       sa.e_in = h->e[h->e_cur]; sa.e_out = h->e[h->e_spare]; sa.e_ref = h->ref_plane();
       sa.wfield = h->field_w ? h->wfield : nullptr; sa.w0 = h->w0;
-      sa.scale = h->scale; sa.inv_scale = h->inv_scale; sa.wsum = h->wsum;
+      sa.scale = h->scale; sa.inv_scale = h->inv_scale;
+      sa.variant = h->step_variant; sa.status = h->d_status;
       sa.xper = h->xper; sa.yper = h->yper;
       cudaEvent_t e0 = nullptr, e1 = nullptr;
       if (h->profiling) {
@@ -506,6 +543,29 @@ wlbm_status wlbm_step(wlbm_handle* h, int64_t n) {
     }
     h->slot ^= 1;
     n -= ch;
+  }
+  return WLBM_OK;
+}
+
+wlbm_status wlbm_set_option(wlbm_handle* h, int32_t key, int64_t value) {
+  if (!h) return WLBM_ERR_INVALID_ARG;
+  if (key == WLBM_OPT_STEP_VARIANT && (value == 0 || value == 1)) {
+    h->step_variant = int(value);
+    return WLBM_OK;
+  }
+  return h->fail(WLBM_ERR_INVALID_ARG, "wlbm_set_option: unknown key or value");
+}
+
+wlbm_status wlbm_check(wlbm_handle* h) {
+  if (!h) return WLBM_ERR_INVALID_ARG;
+  int st = 0;
+  wlbm_status r = h->cuda(cudaMemcpyAsync(&st, h->d_status, sizeof(int), cudaMemcpyDeviceToHost,
+                                          h->stream), "wlbm_check");
+  if (r == WLBM_OK) r = h->cuda(cudaStreamSynchronize(h->stream), "wlbm_check");
+  if (r != WLBM_OK) return r;
+  if (st != 0) {
+    cudaMemsetAsync(h->d_status, 0, sizeof(int), h->stream);
+    return h->fail(WLBM_ERR_TIMEOUT, "a bounded wait in the step kernel gave up");
   }
   return WLBM_OK;
 }
@@ -599,6 +659,206 @@ wlbm_status wlbm_set_state(wlbm_handle* h, const float* framed) {
   if (!framed) return h->fail(WLBM_ERR_INVALID_ARG, "wlbm_set_state: NULL input");
   return h->cuda(launch_set_state(h->storage, state_args(h, const_cast<float*>(framed)), h->stream),
                  "wlbm_set_state");
+}
+
+
+// ------------------------------------------------------------------------- adjoint
+static wlbm_status adj_alloc(wlbm_handle* h, int64_t n, int k) {
+  auto& A = h->adj;
+  for (void* p : A.bufs) h->dev_free(p);
+  A.bufs.clear();
+  A = wlbm_handle::Adj{};
+  const Geom& g = h->g;
+  const size_t state = size_t(g.q) * size_t(g.plane) * 4;
+  const size_t cells = size_t(g.nx) * g.ny * 4;
+  const int nck = int((n + k - 1) / k);
+  auto get = [&](size_t bytes) {
+    void* p = h->dev_alloc(bytes);
+    if (p) A.bufs.push_back(p);
+    return p;
+  };
+  A.ckpt = static_cast<float*>(get(size_t(nck) * state));
+  A.ckpt_e = static_cast<float*>(get(size_t(nck) * size_t(g.plane) * 4));
+  A.tape = static_cast<float*>(get(size_t(k) * state + 1024));
+  A.lam[0] = static_cast<float*>(get(state));
+  A.lam[1] = static_cast<float*>(get(state));
+  A.erec[0] = static_cast<float*>(get(size_t(g.plane) * 4));
+  A.erec[1] = static_cast<float*>(get(size_t(g.plane) * 4));
+  A.gw = static_cast<float*>(get(size_t(g.plane) * 4));
+  A.dwc = static_cast<float*>(get(cells));
+  A.dT0 = static_cast<float*>(get(cells));
+  A.gtw = static_cast<double*>(get(4 * sizeof(double)));
+  A.codes = static_cast<uint8_t*>(get(size_t(n) * g.q));
+  if (!A.ckpt || !A.ckpt_e || !A.tape || !A.lam[0] || !A.lam[1] || !A.erec[0] || !A.erec[1] ||
+      !A.gw || !A.dwc || !A.dT0 || !A.gtw || !A.codes)
+    return h->fail(WLBM_ERR_OOM, "wlbm_adjoint_forward: device allocation failed");
+  A.n = n;
+  A.k = k;
+  A.nck = nck;
+  // tape slots and energy planes: pads must read zero
+  cudaError_t e = cudaMemsetAsync(A.tape, 0, size_t(k) * state + 1024, h->stream);
+  for (int j = 0; j < 2 && e == cudaSuccess; ++j)
+    e = cudaMemsetAsync(A.erec[j], 0, size_t(g.plane) * 4, h->stream);
+  return h->cuda(e, "wlbm_adjoint_forward");
+}
+
+wlbm_status wlbm_adjoint_forward(wlbm_handle* h, const float* dT0, int64_t n_steps,
+                                 int32_t ckpt_every) {
+  if (!h) return WLBM_ERR_INVALID_ARG;
+  if (h->bf16())
+    return h->fail(WLBM_ERR_INVALID_ARG, "wlbm_adjoint_forward: needs float32 storage");
+  if (!dT0 || n_steps < 1 || ckpt_every < 1)
+    return h->fail(WLBM_ERR_INVALID_ARG, "wlbm_adjoint_forward: bad start field or counts");
+  const Geom& g = h->g;
+  auto& A = h->adj;
+  wlbm_status st = WLBM_OK;
+  if (!(A.n == n_steps && A.k == ckpt_every && A.ckpt)) st = adj_alloc(h, n_steps, ckpt_every);
+  if (st != WLBM_OK) return st;
+  A.ready = false;
+  // dW_corr/dMFP per interior cell (Eq. W-correction with W = 1/MFP)
+  std::vector<float> dwc(size_t(g.nx) * g.ny);
+  const double f = h->emulate_3d ? 1.5 : 1.0, lc = h->lat.lam_corr;
+  for (size_t c = 0; c < dwc.size(); ++c) {
+    const double m = h->field_w ? double(h->mfp_host[c]) : h->mfp_uniform;
+    if (std::isinf(m)) { dwc[c] = 0.f; continue; }
+    const double W = 1.0 / m;
+    double d = -f * (1.0 + 2.0 * W * (lc - 1.0)) / (m * m);
+    if (h->relax_mode == 1) d *= std::exp(-f * (W + W * W * (lc - 1.0)));
+    dwc[c] = float(d);
+  }
+  std::vector<uint8_t> codes(size_t(n_steps) * g.q);
+  TasState ts;
+  ts.reset(g.q);
+  for (int64_t t = 0; t < n_steps; ++t) tas_advance(h->lat, &ts, codes.data() + t * g.q);
+  cudaStream_t s = h->stream;
+  st = h->cuda(cudaMemcpyAsync(A.dwc, dwc.data(), dwc.size() * 4, cudaMemcpyHostToDevice, s),
+               "wlbm_adjoint_forward");
+  if (st == WLBM_OK)
+    st = h->cuda(cudaMemcpyAsync(A.codes, codes.data(), codes.size(), cudaMemcpyHostToDevice, s),
+                 "wlbm_adjoint_forward");
+  if (st == WLBM_OK)
+    st = h->cuda(cudaMemcpyAsync(A.dT0, dT0, size_t(g.nx) * g.ny * 4, cudaMemcpyDeviceToDevice, s),
+                 "wlbm_adjoint_forward");
+  if (st == WLBM_OK) st = wlbm_init_temperature(h, dT0);
+  for (int c = 0; c < A.nck && st == WLBM_OK; ++c) {
+    // checkpoint: the state before the boundary pass of step c*k + 1, gathered by parity
+    for (int i = 0; i < g.q && st == WLBM_OK; ++i) {
+      const float* src = static_cast<const float*>(h->planes) +
+                         (size_t(h->tas.parity[i]) * g.q + i) * size_t(g.plane);
+      st = h->cuda(cudaMemcpyAsync(A.ckpt + (size_t(c) * g.q + i) * g.plane, src,
+                                   size_t(g.plane) * 4, cudaMemcpyDeviceToDevice, s),
+                   "wlbm_adjoint_forward: checkpoint");
+    }
+    if (st == WLBM_OK)
+      st = h->cuda(cudaMemcpyAsync(A.ckpt_e + size_t(c) * g.plane, h->e[h->e_cur],
+                                   size_t(g.plane) * 4, cudaMemcpyDeviceToDevice, s),
+                   "wlbm_adjoint_forward: checkpoint");
+    if (st == WLBM_OK) st = wlbm_step(h, std::min<int64_t>(A.k, n_steps - int64_t(c) * A.k));
+  }
+  if (st == WLBM_OK) st = h->cuda(cudaStreamSynchronize(s), "wlbm_adjoint_forward");
+  if (st == WLBM_OK) A.ready = true;
+  return st;
+}
+
+wlbm_status wlbm_adjoint_backward(wlbm_handle* h, const float* dJ_dT, float* dJ_dmfp,
+                                  double* dJ_dTwall, float* dJ_ddT0) {
+  if (!h) return WLBM_ERR_INVALID_ARG;
+  auto& A = h->adj;
+  if (!A.ready || h->tas.n != A.n)
+    return h->fail(WLBM_ERR_STATE, "wlbm_adjoint_backward: no checkpointed forward run ends "
+                                   "at the current state");
+  if (!dJ_dT) return h->fail(WLBM_ERR_INVALID_ARG, "wlbm_adjoint_backward: NULL dJ_dT");
+  const Geom& g = h->g;
+  cudaStream_t s = h->stream;
+  const size_t state = size_t(g.q) * size_t(g.plane);
+  wlbm_status st = WLBM_OK;
+  auto ok = [&](cudaError_t e, const char* what) {
+    if (st == WLBM_OK) st = h->cuda(e, what);
+    return st == WLBM_OK;
+  };
+  ok(cudaMemsetAsync(A.lam[0], 0, state * 4, s), "adjoint");
+  ok(cudaMemsetAsync(A.lam[1], 0, state * 4, s), "adjoint");
+  ok(cudaMemsetAsync(A.gw, 0, size_t(g.plane) * 4, s), "adjoint");
+  ok(cudaMemsetAsync(A.gtw, 0, 4 * sizeof(double), s), "adjoint");
+  AdjArgs aa{};
+  aa.w = h->w_dev(); aa.wfield = h->field_w ? h->wfield : nullptr; aa.w0 = h->w0;
+  aa.xper = h->xper; aa.yper = h->yper; aa.gw = A.gw;
+  aa.nx = g.nx; aa.ny = g.ny; aa.q = g.q; aa.pitch = g.pitch; aa.plane = g.plane;
+  aa.lam_out = A.lam[0];
+  ok(launch_adj_seed(aa, dJ_dT, h->e[h->e_cur], h->e_eq_ref, h->theta, s), "adjoint: seed");
+  int cur = 0;
+  for (int c = A.nck - 1; c >= 0 && st == WLBM_OK; --c) {
+    const int64_t s0 = int64_t(c) * A.k;
+    const int kc = int(std::min<int64_t>(A.k, A.n - s0));
+    // recompute the segment: tape slot j = input of step s0 + j + 1 (after the boundary pass)
+    ok(cudaMemcpyAsync(A.tape, A.ckpt + size_t(c) * state, state * 4, cudaMemcpyDeviceToDevice, s),
+       "adjoint: restore");
+    ok(cudaMemcpyAsync(A.erec[0], A.ckpt_e + size_t(c) * g.plane, size_t(g.plane) * 4,
+                       cudaMemcpyDeviceToDevice, s), "adjoint: restore");
+    int ec = 0;
+    for (int j = 0; j < kc && st == WLBM_OK; ++j) {
+      const uint8_t* codes = A.codes + size_t(s0 + j) * g.q;
+      float* slot = A.tape + size_t(j) * state;
+      if (h->walls.nseg > 0) {
+        WallArgs wa = h->walls;
+        wa.planes = slot; wa.codes = codes; wa.tape = 1; wa.e_ref = nullptr;
+        ok(launch_walls(h->storage, wa, s), "adjoint: walls");
+      }
+      if (h->xper || h->yper) {
+        PeriodicArgs pa{};
+        pa.planes = slot; pa.plane = g.plane; pa.pitch = g.pitch; pa.nx = g.nx; pa.ny = g.ny;
+        pa.q = g.q; pa.codes = codes; pa.e_cur = A.erec[ec]; pa.e_ref = nullptr;
+        pa.xper = h->xper; pa.yper = h->yper; pa.tape = 1;
+        ok(launch_periodic(h->storage, pa, s), "adjoint: periodic");
+      }
+      if (j + 1 < kc) {
+        StepArgs sa{};
+        sa.planes = slot; sa.plane = g.plane; sa.pitch = g.pitch; sa.rows = g.rows;
+        sa.nx = g.nx; sa.ny = g.ny; sa.q = g.q; sa.codes = codes; sa.w = h->w_dev();
+        sa.e_in = A.erec[ec]; sa.e_out = A.erec[ec ^ 1]; sa.e_ref = nullptr;
+        sa.wfield = h->field_w ? h->wfield : nullptr; sa.w0 = h->w0;
+        sa.scale = 1.f; sa.inv_scale = 1.f; sa.xper = h->xper; sa.yper = h->yper;
+        sa.variant = h->step_variant; sa.status = h->d_status;
+        sa.tape = 1; sa.tape_dst = slot + state;
+        ok(launch_step(h->storage, sa, s), "adjoint: recompute");
+        ec ^= 1;
+      }
+    }
+    // reverse sweep over the segment
+    for (int j = kc - 1; j >= 0 && st == WLBM_OK; --j) {
+      aa.lam_in = A.lam[cur];
+      aa.lam_out = A.lam[cur ^ 1];
+      aa.dtil = A.tape + size_t(j) * state;
+      aa.codes = A.codes + size_t(s0 + j) * g.q;
+      ok(launch_adj_step(aa, s), "adjoint: reverse step");
+      ok(launch_periodic_T(A.lam[cur ^ 1], g.plane, g.pitch, g.nx, g.ny, g.q, h->xper, h->yper, s),
+         "adjoint: periodic transpose");
+      if (h->walls.nseg > 0) {
+        WallArgs wa = h->walls;
+        wa.codes = aa.codes;
+        ok(launch_walls_T(wa, A.lam[cur ^ 1], A.gtw, s), "adjoint: wall transpose");
+      }
+      cur ^= 1;
+    }
+  }
+  // periodic ghosts of W_corr copy interior cells: send their gradient back
+  ok(launch_periodic_T(A.gw, g.plane, g.pitch, g.nx, g.ny, 1, h->xper, h->yper, s),
+     "adjoint: W transpose");
+  ok(launch_adj_final(aa, A.dwc, dJ_dmfp, A.lam[cur], A.dT0, dJ_ddT0, h->t_ref, h->theta, s),
+     "adjoint: final");
+  double gt[4] = {0, 0, 0, 0};
+  ok(cudaMemcpyAsync(gt, A.gtw, sizeof(gt), cudaMemcpyDeviceToHost, s), "adjoint");
+  ok(cudaStreamSynchronize(s), "adjoint");
+  if (st != WLBM_OK) return st;
+  if (dJ_dTwall) {
+    for (int k = 0; k < 4; ++k) {
+      dJ_dTwall[k] = 0.0;
+      if (h->bc_kind[k] != WLBM_BC_ISOTHERMAL) continue;
+      const double x = h->theta / h->t_wall[k], e = 1.0 / std::expm1(x);
+      dJ_dTwall[k] = gt[k] * e * (1.0 + e) * x / h->t_wall[k];
+    }
+  }
+  return WLBM_OK;
 }
 
 }  // extern "C"

@@ -53,8 +53,14 @@ struct StepArgs {
   float* e_out;          // local energy of the new state
   const float* wfield;   // framed W_corr or nullptr (uniform)
   float w0;              // uniform W_corr of interior cells
-  float scale, inv_scale, wsum;   // bfloat16 value scale, sum of the float weights
+  float scale, inv_scale;         // bfloat16 value scale and its inverse
   int xper, yper;        // periodic axes (uniform W: their ghost cells carry w0)
+  int variant;           // 0: register-pipelined loads, 1: per-warp bulk-copy ring
+  int* status;           // device status word: bit 0 set when a bounded wait gave up
+  // tape mode (adjoint recompute): every plane i is read from planes + i*plane and
+  // written to tape_dst + i*plane, whatever its parity or pause flag
+  int tape;
+  void* tape_dst;
 };
 
 // Wall segment for the boundary kernel (one warp per ghost cell).
@@ -64,17 +70,19 @@ struct WallSeg {
   int action;            // 1 isothermal, 2 diffuse
   int table;             // diffuse re-emission table index into rho[]
   float iso;             // isothermal e_eq(T_w) - e_ref (times w_i per direction)
+  int wall;              // wall (0..3) whose temperature an isothermal cell takes
 };
 constexpr int kMaxSeg = 8;
 struct WallArgs {
   void* planes;
   int64_t plane;
   int pitch, q, nseg;
-  const float* e_ref;    // reference energy of the stored values (bfloat16 only)
+  float* e_ref;          // reference energy of the stored values (bfloat16 only)
   float scale, inv_scale;
   const uint8_t* codes;  // current parity from the next step's codes
   const float* w;
   const float* rho;      // [8][q] re-emission fractions (0 = collected direction)
+  int tape;              // 1: all planes at `planes` (parity ignored)
   WallSeg seg[kMaxSeg];
 };
 
@@ -86,6 +94,7 @@ struct PeriodicArgs {
   float* e_cur;          // local energy plane copied along with the direction planes
   float* e_ref;          // reference energy plane (bfloat16 only), copied likewise
   int xper, yper;
+  int tape;              // 1: all planes at `planes` (parity ignored)
 };
 
 struct InitArgs {
@@ -144,6 +153,21 @@ struct StateArgs {
   float scale, inv_scale;
 };
 
+// Reverse-step arguments (float32 storage only).
+struct AdjArgs {
+  const float* lam_in;   // adjoint of the step's output, [q][plane]
+  float* lam_out;        // adjoint of the step's input (before the boundary transposes)
+  const float* dtil;     // recorded step input (after the boundary pass), [q][plane]
+  const uint8_t* codes;  // the step's codes
+  const float* w;
+  const float* wfield;   // framed W_corr or nullptr (uniform w0 with the frame rule)
+  float w0;
+  int xper, yper;
+  float* gw;             // framed dJ/dW_corr accumulator
+  int nx, ny, q, pitch;
+  int64_t plane;
+};
+
 // Sets the message returned by wlbm_last_error(NULL).
 void set_global_error_msg(const std::string& m);
 
@@ -156,5 +180,15 @@ cudaError_t launch_moments(int storage, const MomentArgs& a, cudaStream_t s);
 cudaError_t launch_reduce(int storage, const ReduceArgs& a, cudaStream_t s);
 cudaError_t launch_get_state(int storage, const StateArgs& a, cudaStream_t s);
 cudaError_t launch_set_state(int storage, const StateArgs& a, cudaStream_t s);
+// Adjoint launchers (k_adjoint.cu).
+cudaError_t launch_adj_step(const AdjArgs& a, cudaStream_t s);
+cudaError_t launch_periodic_T(float* planes, int64_t plane, int pitch, int nx, int ny,
+                              int nplanes, int xper, int yper, cudaStream_t s);
+cudaError_t launch_walls_T(const WallArgs& wa, float* lam, double* gtw, cudaStream_t s);
+cudaError_t launch_adj_seed(const AdjArgs& a, const float* dJ_dT, const float* e_final,
+                            double e_ref, double theta, cudaStream_t s);
+cudaError_t launch_adj_final(const AdjArgs& a, const float* dwc, float* dJ_dmfp,
+                             const float* lam0, const float* dT0, float* dJ_ddT0,
+                             double t_ref, double theta, cudaStream_t s);
 
 }  // namespace wlbm

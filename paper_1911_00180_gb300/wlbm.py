@@ -16,6 +16,7 @@ WLBM_OK, WLBM_ERR_INVALID_ARG, WLBM_ERR_UNSTABLE, WLBM_ERR_OOM = 0, 1, 2, 3
 WLBM_ERR_CUDA, WLBM_ERR_TIMEOUT, WLBM_ERR_STATE = 4, 5, 6
 BC_PERIODIC, BC_ISOTHERMAL, BC_ADIABATIC_DIFFUSE = 0, 1, 2
 STORE_FP32_DEV, STORE_BF16_DEV = 0, 1
+OPT_STEP_VARIANT = 1
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "UNSTABLE", 3: "OOM", 4: "CUDA", 5: "TIMEOUT",
                 6: "STATE"}
 
@@ -63,6 +64,10 @@ def _load():
         "wlbm_reduce": (C.c_int, [vp, C.POINTER(dbl)]),
         "wlbm_get_state": (C.c_int, [vp, vp]),
         "wlbm_set_state": (C.c_int, [vp, vp]),
+        "wlbm_adjoint_forward": (C.c_int, [vp, vp, i64, i32]),
+        "wlbm_adjoint_backward": (C.c_int, [vp, vp, vp, C.POINTER(dbl), vp]),
+        "wlbm_set_option": (C.c_int, [vp, i32, i64]),
+        "wlbm_check": (C.c_int, [vp]),
         "wlbm_profile": (C.c_int, [vp, i32]),
         "wlbm_profile_read": (C.c_int, [vp, C.POINTER(dbl), C.POINTER(i64), C.POINTER(i64)]),
         "wlbm_reduce_state_noalloc": (C.c_int, [vp, i32, i32, i32, C.POINTER(i32), vp, vp]),
@@ -195,6 +200,27 @@ class WormLBM:
         out = (C.c_double * 4)()
         _check(lib.wlbm_reduce(self.h, out), self.h)
         return list(out)
+
+    def wlbm_adjoint_forward(self, dT0, n_steps, ckpt_every):
+        t = self._torch.as_tensor(dT0, dtype=self._torch.float32, device=self.device).contiguous()
+        _check(lib.wlbm_adjoint_forward(self.h, _ptr(t), int(n_steps), int(ckpt_every)), self.h)
+
+    def wlbm_adjoint_backward(self, dJ_dT, want_mfp=True, want_dT0=True):
+        """(dJ/dMFP (ny, nx), dJ/dT_wall [4], dJ/d dT0 (ny, nx)) for the checkpointed run."""
+        torch = self._torch
+        g = torch.as_tensor(dJ_dT, dtype=torch.float32, device=self.device).contiguous()
+        mk = lambda f: torch.empty((self.ny, self.nx), dtype=torch.float32,
+                                   device=self.device) if f else None
+        g_mfp, g_dT0 = mk(want_mfp), mk(want_dT0)
+        g_tw = (C.c_double * 4)()
+        _check(lib.wlbm_adjoint_backward(self.h, _ptr(g), _ptr(g_mfp), g_tw, _ptr(g_dT0)), self.h)
+        return g_mfp, list(g_tw), g_dT0
+
+    def wlbm_set_option(self, key, value):
+        _check(lib.wlbm_set_option(self.h, int(key), int(value)), self.h)
+
+    def wlbm_check(self):
+        _check(lib.wlbm_check(self.h), self.h)
 
     def wlbm_profile(self, enable=True):
         _check(lib.wlbm_profile(self.h, 1 if enable else 0), self.h)

@@ -21,26 +21,30 @@ def oracle_run(cfg, steps, state=None):
     return m
 
 
-def gpu_handle(cfg, storage=0):
+def gpu_handle(cfg, storage=0, variant=None):
     import paper_1911_00180_gb300 as wl
     mfp = cfg.get("mfp")
     if mfp is None:
         mfp = 0.0
-    return wl.WormLBM(cfg["nx"], cfg["ny"], cfg["q"], mfp=mfp,
-                      mfp_field=cfg.get("mfp_field"), bc=cfg["bc"], t_wall=cfg["t_wall"],
-                      storage=storage, emulate_3d=cfg["emulate_3d"],
-                      relax_mode=cfg.get("relax_mode", 0), theta=THETA)
+    h = wl.WormLBM(cfg["nx"], cfg["ny"], cfg["q"], mfp=mfp,
+                   mfp_field=cfg.get("mfp_field"), bc=cfg["bc"], t_wall=cfg["t_wall"],
+                   storage=storage, emulate_3d=cfg["emulate_3d"],
+                   relax_mode=cfg.get("relax_mode", 0), theta=THETA)
+    if variant is not None:
+        h.wlbm_set_option(wl.wlbm.OPT_STEP_VARIANT, variant)
+    return h
 
 
-def gpu_run(cfg, steps, storage=0, state=None):
+def gpu_run(cfg, steps, storage=0, state=None, variant=None):
     import torch
-    h = gpu_handle(cfg, storage)
+    h = gpu_handle(cfg, storage, variant)
     if state is None:
         h.wlbm_init_temperature(cfg["dT"])
     else:
         h.wlbm_init_temperature(np.zeros((cfg["ny"], cfg["nx"]), np.float32))
         h.wlbm_set_state(torch.as_tensor(state, dtype=torch.float32))
     h.wlbm_step(steps)
+    h.wlbm_check()
     dT, qx, qy = h.wlbm_moments()
     st = h.wlbm_get_state()
     torch.cuda.synchronize()
