@@ -47,14 +47,19 @@ def parse():
     p.add_argument("--nx", type=int, default=2048)
     p.add_argument("--q", type=int, default=64)
     p.add_argument("--seed", type=int, default=2)
-    p.add_argument("--workload", default="pulses", choices=["pulses", "film"],
+    p.add_argument("--workload", default="pulses", choices=["pulses", "film", "batch"],
                    help="pulses: 2048^2 periodic Q=64 (default); film: 4096x256 in-plane "
                         "film, Q=128, isothermal x walls, diffuse y walls (Kn = 1)")
     p.add_argument("--e2e-steps", type=int, default=3)
+    p.add_argument("--fuse", type=int, default=None,
+                   help="1: step kernel mirrors periodic edges (library default), 0: separate pass")
+    p.add_argument("--graph", type=int, default=0,
+                   help="replay chunks of this many steps as one CUDA graph (multiple of 6)")
     p.add_argument("--variant", type=int, default=None,
                    help="step kernel: 0 register-pipelined, 1 bulk-copy ring (library default)")
     p.add_argument("--no-extras", action="store_true",
-                   help="skip e2e, cpu baseline and clock sampling (profiling runs)")
+                   help="skip e2e, cpu baseline, adjoint and clock sampling (profiling runs)")
+    p.add_argument("--no-adjoint", action="store_true", help="skip the adjoint ratio")
     return p.parse_args()
 
 
@@ -71,6 +76,91 @@ def workload(args):
     if args.workload == "film":
         return W.film_c3(kn=1.0, nx=2 * args.nx, ny=args.nx // 8, q=2 * args.q)
     return W.pulses_c2(seed=args.seed, n=args.nx, q=args.q)
+
+
+def run_batch(args):
+    """96 in-plane films of uneven thickness (16-512 cells), aspect (8-32), Kn (0.01-100)
+    and Q (16-256), bfloat16 storage by default, one wall launch and one step launch per
+    step for all of them, variant and graph replay chosen by the autotuner."""
+    import torch
+    import torch.distributed as tdist
+    import workloads as W
+    import paper_1911_00180_gb300 as wl
+    from paper_1911_00180_gb300 import autotune
+    from paper_1911_00180_gb300 import dist as D
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    if world > 1 and not tdist.is_initialized():
+        tdist.init_process_group("nccl")
+    storage = wl.STORE_FP32_DEV if args.storage == "fp32" else wl.STORE_BF16_DEV
+    insts = W.batch_c4(seed=4)
+    n_all = len(insts)
+    # instances are independent: each rank takes a cost-balanced share, no collective
+    mine = D.shard_by_cost([c["q"] * c["nx"] * c["ny"] for c in insts], rank, world)
+    insts = [insts[k] for k in mine]
+    specs = []
+    for c in insts:
+        mfp = c["mfp"]
+        specs.append(dict(nx=c["nx"], ny=c["ny"], q=c["q"], bc=c["bc"], t_wall=c["t_wall"],
+                          mfp=mfp, emulate_3d=True))
+    # instances whose MFP would make W_corr > 1 take 1.5 cells (stability, Appendix A)
+    for sp in specs:
+        if sp["mfp"] < 1.5:
+            sp["mfp"] = 1.5
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        b = wl.WormLBMBatch(specs, storage=storage, stream=stream)
+        tuned = autotune.tune_batch(b, storage, trial_steps=48)
+        b.wlbm_batch_init_temperature([c["dT"] for c in insts])
+        b.wlbm_batch_step(args.warmup)
+        stream.synchronize()
+        _, _, l0 = b.wlbm_batch_profile_read()
+        graphs = tuned["graph_steps"] > 0
+        b.wlbm_batch_profile(not graphs)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        if world > 1:
+            tdist.barrier()
+        e0.record(stream)
+        b.wlbm_batch_step(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            tdist.barrier()
+        b.wlbm_batch_profile(False)
+        ms = D.max_over_ranks(e0.elapsed_time(e1), device="cuda")
+        step_ms, nlaunch, l1 = b.wlbm_batch_profile_read()
+        b.close()
+    upd = D.sum_over_ranks(sum(sp["q"] * sp["nx"] * sp["ny"] for sp in specs), device="cuda")
+    elem = 2 if args.storage != "fp32" else 4
+    algo = sum(sp["q"] * sp["nx"] * sp["ny"] * (2 * elem + (12.0 if elem == 2 else 8.0) / sp["q"])
+               for sp in specs)
+    per_launch = step_ms / nlaunch if nlaunch else ms / args.steps
+    peak, kind = peaks()
+    achieved = algo / (per_launch * 1e-3) / 1e9
+    if rank != 0:
+        if world > 1:
+            tdist.destroy_process_group()
+        return 0
+    line = {"metric": METRIC, "value": upd * args.steps / (ms * 1e-3), "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16-storage/f32-math" if elem == 2 else "f32",
+            "data": "synthetic",
+            "config": {"workload": "batch_c4: 96 films, thickness 16-512, aspect 8-32, "
+                                   "Kn 0.01-100, Q in {16..256}, %s storage" % args.storage,
+                       "instances": n_all, "instances_rank0": len(specs),
+                       "site_directions": upd, "parallelism": "instances sharded x%d" % world,
+                       "autotune": tuned},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "kernel": "k_step_*_batch",
+                         "peak_kind": kind, "kernel_ms_per_launch": per_launch},
+            "gpu_launches": int(l1 - l0)}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        tdist.destroy_process_group()
+    return 0
 
 
 def bytes_per_update(storage, q):
@@ -147,6 +237,46 @@ def cpu_baseline(cfg, seconds=12.0):
                       "float64 single thread" % (steps, nx, ny, cfg["q"], cfg["mfp"])}
 
 
+def adjoint_ratio(wl, torch, stream, steps=None):
+    """Adjoint workload (1024^2, Q = 64, log-normal per-cell MFP, isothermal x walls,
+    periodic y, 1000 steps, checkpoints every 50): wall time of the backward pass (segment
+    recompute + reverse sweep) over that of a plain forward run of the same steps."""
+    import numpy as np
+    import workloads as W
+    cfg = W.adjoint_c5()
+    n = cfg["steps"] if steps is None else steps
+    h = wl.WormLBM(cfg["nx"], cfg["ny"], cfg["q"], mfp_field=cfg["mfp_field"], bc=cfg["bc"],
+                   t_wall=cfg["t_wall"], emulate_3d=True, stream=stream)
+    dT0 = torch.as_tensor(cfg["dT"], device="cuda")
+    probe = np.zeros((cfg["ny"], cfg["nx"]), np.float32)
+    probe[:, cfg["probe_x"]] = 1.0 / cfg["ny"]
+    g = torch.as_tensor(probe, device="cuda")
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        stream.synchronize()
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1)
+    # warm-up: allocations of checkpoints and tape, first launches
+    h.wlbm_adjoint_forward(dT0, 2 * cfg["ckpt"], cfg["ckpt"])
+    h.wlbm_adjoint_backward(g)
+    h.wlbm_init_temperature(dT0)
+    h.wlbm_step(20)
+    fwd = timed(lambda: (h.wlbm_init_temperature(dT0), h.wlbm_step(n)))
+    fwd_ck = timed(lambda: h.wlbm_adjoint_forward(dT0, n, cfg["ckpt"]))
+    bwd = timed(lambda: h.wlbm_adjoint_backward(g))
+    h.wlbm_check()
+    h.close()
+    return {"workload": "adjoint_c5 %dx%d, Q=%d, log-normal MFP field, isothermal x walls, "
+                        "periodic y, %d steps, checkpoints every %d"
+                        % (cfg["nx"], cfg["ny"], cfg["q"], n, cfg["ckpt"]),
+            "forward_ms": fwd, "checkpointed_forward_ms": fwd_ck, "backward_ms": bwd,
+            "ratio_backward_over_forward": bwd / fwd}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -186,6 +316,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch":
+        return run_batch(args)
     import torch
     import torch.distributed as dist
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -205,6 +337,10 @@ def main():
                        relax_mode=cfg["relax_mode"], stream=stream)
         if args.variant is not None:
             h.wlbm_set_option(wl.wlbm.OPT_STEP_VARIANT, args.variant)
+        if args.graph:
+            h.wlbm_set_option(wl.wlbm.OPT_GRAPH_STEPS, args.graph)
+        if args.fuse is not None:
+            h.wlbm_set_option(wl.wlbm.OPT_FUSE_PERIODIC, args.fuse)
         dT = torch.as_tensor(cfg["dT"]).to("cuda", non_blocking=False)
         h.wlbm_init_temperature(dT)
         h.wlbm_step(args.warmup)
@@ -217,7 +353,7 @@ def main():
             torch.cuda.synchronize()
 
         clocks = None if args.no_extras else Clocks(local)
-        h.wlbm_profile(True)
+        h.wlbm_profile(not args.graph)
         barrier()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
@@ -238,7 +374,7 @@ def main():
         updates = cfg["q"] * cells * args.steps * world
         value = updates / (elapsed_ms * 1e-3)
         bpu = bytes_per_update(args.storage, cfg["q"])
-        per_launch_ms = step_ms / max(step_launches, 1)
+        per_launch_ms = step_ms / step_launches if step_launches else elapsed_ms / args.steps
         achieved = bpu * cfg["q"] * cells / (per_launch_ms * 1e-3) / 1e9
         peak, peak_kind = peaks()
 
@@ -270,6 +406,9 @@ def main():
                    "d2h_bytes_per_step": int(host_out.numel() * 4),
                    "lbm_steps_per_e2e_step": run_steps}
         h.close()
+        adj = None
+        if not args.no_extras and not args.no_adjoint and rank == 0:
+            adj = adjoint_ratio(wl, torch, stream)
 
     if rank == 0:
         line = {
@@ -289,8 +428,9 @@ def main():
                            % (cfg["nx"], cfg["ny"], cfg["q"], args.storage, cfg["mfp"])),
                        "nx": cfg["nx"], "ny": cfg["ny"], "q": cfg["q"],
                        "mfp_cells": cfg["mfp"], "parallelism": "replicas x%d" % world,
-                       "step_kernel": "bulk-copy ring" if args.variant in (None, 1)
-                                      else "register-pipelined",
+                       "step_kernel": {0: "register-pipelined", 1: "bulk-copy ring",
+                                       2: "warp-specialised"}[1 if args.variant is None
+                                                               else args.variant],
                        "l2": "state %.2f GB > L2 (no flush needed)"
                              % (2 * cfg["q"] * cells * (4 if args.storage == "fp32" else 2) / 1e9)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -303,6 +443,8 @@ def main():
         }
         if e2e is not None:
             line["e2e"] = e2e
+        if adj is not None:
+            line["adjoint"] = adj
         if clk is not None:
             line["clocks"] = clk
         if not args.no_extras:

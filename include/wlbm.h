@@ -156,10 +156,19 @@ wlbm_status wlbm_adjoint_backward(wlbm_handle* h, const float* dJ_dT, float* dJ_
 
 /* wlbm_set_option: tuning knobs that do not change results.
  *   WLBM_OPT_STEP_VARIANT  0: step kernel with register-pipelined loads; 1 (default):
- *                          step kernel with a per-warp ring of bulk async copies.
+ *                          step kernel with a per-warp ring of bulk async copies; 2:
+ *                          warp-specialised step kernel (a producer warp issues the bulk
+ *                          copies of all rows, consumer warps compute).
+ *   WLBM_OPT_GRAPH_STEPS   0 (default): launch every step's kernels directly; G > 0, a
+ *                          multiple of 6: run chunks of G steps as one captured CUDA
+ *                          graph (for small, launch-bound grids; not while profiling and
+ *                          not on the legacy default stream).
+ *   WLBM_OPT_FUSE_PERIODIC 0 (default): a separate periodic pass before every step; 1:
+ *                          when both axes are periodic the step kernel also writes the
+ *                          ghost cells mirroring each edge cell (no separate pass).
  * wlbm_check: synchronises the stream and returns WLBM_ERR_TIMEOUT if a bounded wait
  * inside a kernel gave up since the last check (the status is then cleared). */
-enum { WLBM_OPT_STEP_VARIANT = 1 };
+enum { WLBM_OPT_STEP_VARIANT = 1, WLBM_OPT_GRAPH_STEPS = 2, WLBM_OPT_FUSE_PERIODIC = 3 };
 wlbm_status wlbm_set_option(wlbm_handle* h, int32_t key, int64_t value);
 wlbm_status wlbm_check(wlbm_handle* h);
 
@@ -195,6 +204,47 @@ wlbm_status wlbm_profile_read(wlbm_handle* h, double* step_ms, int64_t* step_lau
  * executions overlap on the GPU (other streams, other threads) race on it.  Asynchronous. */
 wlbm_status wlbm_reduce_state_noalloc(const float* framed, int32_t nx, int32_t ny, int32_t q,
                                       const int32_t* bc_kind, double* out, void* stream);
+
+/* wlbm_autotune: native search over WLBM_OPT_STEP_VARIANT (0, 1, 2) x WLBM_OPT_GRAPH_STEPS
+ * (0 and the largest multiple of 6 <= trial_steps) for this grid: each candidate runs trial_steps (>= 6) steps after a warm-up; the fastest is kept
+ * and returned (any output may be NULL).  The trial steps advance the state: call it
+ * before wlbm_init_temperature. */
+wlbm_status wlbm_autotune(wlbm_handle* h, int32_t trial_steps, int32_t* variant,
+                          int32_t* graph_steps, double* ms_per_step);
+
+/* -------------------------------------------------------------------------- batches --
+ * Many independent grids (instances: films of different sizes, Knudsen numbers and Q)
+ * advanced together; the multigray extension of Sec. 2.1 maps onto the same path.  Each
+ * step is one wall launch and one step launch for the whole batch (the batched kernels
+ * find their instance from the block index), optionally replayed as a CUDA graph.
+ *   grids, bcs          host arrays of n entries (one storage type for all)
+ *   mfp_cells           host array of n device pointers (NULL entries: uniform), or NULL
+ *   mfp_uniform         host array of n uniform MFPs (used where mfp_cells[k] is NULL)
+ * wlbm_batch_instance returns the handle of instance k (owned by the batch) for
+ * moments, reductions and state access.  Options (wlbm_batch_set_option) are those of
+ * wlbm_set_option, for every instance: WLBM_OPT_STEP_VARIANT 0 or 1, WLBM_OPT_GRAPH_STEPS,
+ * WLBM_OPT_FUSE_PERIODIC.  Instances with a periodic axis whose edges the step kernel does
+ * not mirror get their own periodic pass each step; graph replay then keeps one captured
+ * graph per starting energy-plane phase of those instances (at most three). */
+typedef struct wlbm_batch wlbm_batch;
+wlbm_status wlbm_batch_create(int32_t n, const wlbm_grid* grids, const float* const* mfp_cells,
+                              const double* mfp_uniform, const wlbm_boundary* bcs,
+                              const wlbm_allocator* alloc, void* stream, wlbm_batch** out);
+void wlbm_batch_destroy(wlbm_batch* b);
+const char* wlbm_batch_last_error(const wlbm_batch* b);
+int32_t wlbm_batch_size(const wlbm_batch* b);
+wlbm_handle* wlbm_batch_instance(wlbm_batch* b, int32_t k);
+/* dT: host array of n device pointers (nx*ny float32 each). */
+wlbm_status wlbm_batch_init_temperature(wlbm_batch* b, const float* const* dT);
+wlbm_status wlbm_batch_set_option(wlbm_batch* b, int32_t key, int64_t value);
+wlbm_status wlbm_batch_step(wlbm_batch* b, int64_t n);
+wlbm_status wlbm_batch_profile(wlbm_batch* b, int32_t enable);
+wlbm_status wlbm_batch_profile_read(wlbm_batch* b, double* step_ms, int64_t* step_launches,
+                                    int64_t* all_launches);
+/* wlbm_batch_autotune: as wlbm_autotune over variants 0 and 1, for the whole batch (call
+ * before init). */
+wlbm_status wlbm_batch_autotune(wlbm_batch* b, int32_t trial_steps, int32_t* variant,
+                                int32_t* graph_steps, double* ms_per_step);
 
 /* ------------------------------------------------------------ host-only queries ----
  * No GPU needed.  wlbm_lattice: the lattice of Sec. 2.4-2.5 for Q directions.

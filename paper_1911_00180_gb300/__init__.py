@@ -7,7 +7,7 @@ that raises ImportError when it is not built: there is no fallback path.  The bu
 module (``paper_1911_00180_gb300.build``) imports without the library.
 """
 _EXPORTS = ("WormLBM", "WlbmError", "wlbm_lattice", "wlbm_schedule", "lib", "LIB_PATH",
-            "wlbm_reduce_state_noalloc",
+            "wlbm_reduce_state_noalloc", "WormLBMBatch",
             "BC_PERIODIC", "BC_ISOTHERMAL", "BC_ADIABATIC_DIFFUSE",
             "STORE_FP32_DEV", "STORE_BF16_DEV")
 

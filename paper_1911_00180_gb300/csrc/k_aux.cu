@@ -27,7 +27,7 @@ template <typename T>
 __device__ __forceinline__ float dev_load(const T* p, float wi, const float* ref, int64_t off,
                                           float scale) {
   const float v = Elem<T>::ld(p);
-  return ref ? fmaf(v, scale, wi * ref[off]) : v;
+  return ref ? fmaf(v, scale, __fmul_rn(wi, ref[off])) : v;
 }
 
 // Store deviation d; returns the deviation the stored value represents.
@@ -35,14 +35,14 @@ template <typename T>
 __device__ __forceinline__ float dev_store(T* p, float d, float wi, const float* ref,
                                            int64_t off, float scale, float inv_scale) {
   if (!ref) return Elem<T>::st(p, d);
-  const float r = wi * ref[off];
-  return fmaf(Elem<T>::st(p, (d - r) * inv_scale), scale, r);
+  // explicitly rounded operations: the same bits in every kernel that inlines this
+  const float r = __fmul_rn(wi, ref[off]);
+  return fmaf(Elem<T>::st(p, __fmul_rn(__fsub_rn(d, r), inv_scale)), scale, r);
 }
 
 template <typename T>
-__global__ void k_walls(const WallArgs a) {
-  const int warp = int((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-  const int lane = threadIdx.x & 31;
+__device__ __forceinline__ void walls_cell(const WallArgs& a, const uint8_t* codes,
+                                           float* e_ref, int warp, int lane) {
   int s = 0, idx = warp;
   while (s < a.nseg && idx >= a.seg[s].count) {
     idx -= a.seg[s].count;
@@ -53,15 +53,15 @@ __global__ void k_walls(const WallArgs a) {
   const int64_t off = int64_t(g.r0 + idx * g.dr) * a.pitch + (g.c0 + idx * g.dc);
   T* planes = static_cast<T*>(a.planes);
   auto ptr = [&](int i) {
-    const int par = a.tape ? 0 : (a.codes[i] >> 4) & 1;
+    const int par = a.tape ? 0 : (codes[i] >> 4) & 1;
     return planes + int64_t(par * a.q + i) * a.plane + off;
   };
   if (g.action == WLBM_BC_ISOTHERMAL) {
-    if (a.e_ref) {
+    if (e_ref) {
       // bfloat16: make the wall's own equilibrium the reference of the cell, so the
       // stored values are exactly zero and decode to w_i (e_eq(T_w) - e_ref) unrounded
       for (int i = lane; i < a.q; i += 32) Elem<T>::st(ptr(i), 0.f);
-      if (lane == 0) a.e_ref[off] = g.iso;
+      if (lane == 0) e_ref[off] = g.iso;
     } else {
       for (int i = lane; i < a.q; i += 32) Elem<T>::st(ptr(i), a.w[i] * g.iso);
     }
@@ -70,13 +70,36 @@ __global__ void k_walls(const WallArgs a) {
   const float* rho = a.rho + int64_t(g.table) * a.q;
   float part = 0.f;
   for (int i = lane; i < a.q; i += 32)
-    if (rho[i] == 0.f) part += dev_load(ptr(i), a.w[i], a.e_ref, off, a.scale);
+    if (rho[i] == 0.f) part += dev_load(ptr(i), a.w[i], e_ref, off, a.scale);
   const float A = warp_sum(part);
   for (int i = lane; i < a.q; i += 32) {
     const float d = rho[i] == 0.f ? 0.f
-                                  : fmaf(A, rho[i], dev_load(ptr(i), a.w[i], a.e_ref, off, a.scale));
-    dev_store(ptr(i), d, a.w[i], a.e_ref, off, a.scale, a.inv_scale);
+                                  : fmaf(A, rho[i], dev_load(ptr(i), a.w[i], e_ref, off, a.scale));
+    dev_store(ptr(i), d, a.w[i], e_ref, off, a.scale, a.inv_scale);
   }
+}
+
+template <typename T>
+__global__ void k_walls(const WallArgs a) {
+  const int warp = int((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  walls_cell<T>(a, a.codes, a.e_ref, warp, threadIdx.x & 31);
+}
+
+// Batched wall pass: warp w belongs to the instance whose first_warp is the largest one
+// <= w; codes and the reference-energy plane of step t come from the instance record.
+template <typename T>
+__global__ void k_walls_batch(const BatchWalls* B, int n, int t) {
+  const int gw = int((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (B[mid].first_warp <= gw) lo = mid;
+    else hi = mid - 1;
+  }
+  const BatchWalls& I = B[lo];
+  const int cur = (I.phase + t) % I.n_e;
+  float* e_ref = I.n_e == 3 ? I.e[(cur + 2) % 3] : nullptr;
+  walls_cell<T>(I.w, I.codes + size_t(t) * I.w.q, e_ref, gw - I.first_warp, threadIdx.x & 31);
 }
 
 template <typename T>
@@ -111,7 +134,7 @@ __global__ void k_periodic(const PeriodicArgs a) {
   } else if (p == a.q + 1) {
     a.e_ref[od] = a.e_ref[os];
   } else {
-    const int par = a.tape ? 0 : (a.codes[p] >> 4) & 1;
+    const int par = a.tape ? 0 : a.par ? parity_of(*a.par, p) : (a.codes[p] >> 4) & 1;
     T* base = static_cast<T*>(a.planes) + int64_t(par * a.q + p) * a.plane;
     base[od] = base[os];
   }
@@ -278,6 +301,17 @@ cudaError_t periodic_t(const PeriodicArgs& a, cudaStream_t s) {
 }
 
 }  // namespace
+
+cudaError_t launch_walls_batch(int storage, const BatchWalls* b, int n, int total_warps, int t,
+                               cudaStream_t s) {
+  if (total_warps <= 0) return cudaSuccess;
+  const unsigned g = blocks_for(int64_t(total_warps) * 32, 256);
+  if (storage == WLBM_STORE_BF16_DEV)
+    k_walls_batch<__nv_bfloat16><<<g, 256, 0, s>>>(b, n, t);
+  else
+    k_walls_batch<float><<<g, 256, 0, s>>>(b, n, t);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_walls(int storage, const WallArgs& a, cudaStream_t s) {
   return storage == WLBM_STORE_BF16_DEV ? walls_t<__nv_bfloat16>(a, s) : walls_t<float>(a, s);

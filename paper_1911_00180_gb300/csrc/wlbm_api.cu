@@ -53,6 +53,10 @@ struct wlbm_handle {
   double* d_red = nullptr;    // [4]
   int* d_status = nullptr;    // bit 0: a bounded device wait gave up
   int step_variant = 1;       // 0 register-pipelined, 1 per-warp bulk-copy ring
+  int graph_steps = 0;        // >0: replay chunks of this many steps as one CUDA graph
+  int fuse_periodic = 0;      // 1: both axes periodic, the step kernel mirrors the edges
+  cudaGraphExec_t graphs[3] = {nullptr, nullptr, nullptr};   // per energy-plane role
+  int64_t graph_launches = 0; // kernels per graph replay
   std::vector<void*> owned;
   // host staging
   uint8_t* h_codes[2] = {nullptr, nullptr};
@@ -124,7 +128,14 @@ struct wlbm_handle {
       return;
     }
   }
+  void drop_graphs() {
+    for (auto& gx : graphs) {
+      if (gx) cudaGraphExecDestroy(gx);
+      gx = nullptr;
+    }
+  }
   void release() {
+    drop_graphs();
     for (void* p : owned) {
       if (alloc.alloc) {
         if (alloc.free) alloc.free(p, alloc.ctx);
@@ -207,6 +218,27 @@ void wlbm_handle::build_wall_segments() {
   a.rho = rho_dev();
   a.scale = scale;
   a.inv_scale = inv_scale;
+}
+
+// Fill the periodic ghost cells (and their energies) from the current state, with plane
+// parities from the host mask.  Used after the state is set from outside the step loop.
+static wlbm_status refresh_periodic(wlbm_handle* h) {
+  if (!h->xper && !h->yper) return WLBM_OK;
+  const Geom& g = h->g;
+  const ParityMask m = h->parity_mask();
+  PeriodicArgs pa{};
+  pa.planes = h->planes; pa.plane = g.plane; pa.pitch = g.pitch; pa.nx = g.nx; pa.ny = g.ny;
+  pa.q = g.q; pa.codes = nullptr; pa.e_cur = h->e[h->e_cur]; pa.e_ref = h->ref_plane();
+  pa.xper = h->xper; pa.yper = h->yper;
+  // the mask goes to the device through the schedule buffer (stream-ordered)
+  wlbm_status st = h->cuda(cudaMemcpyAsync(h->d_codes, m.bits, sizeof(m.bits),
+                                           cudaMemcpyHostToDevice, h->stream), "periodic refresh");
+  if (st != WLBM_OK) return st;
+  st = h->cuda(cudaStreamSynchronize(h->stream), "periodic refresh");   // m is on the stack
+  if (st != WLBM_OK) return st;
+  pa.par = reinterpret_cast<const ParityMask*>(h->d_codes);
+  ++h->launches;
+  return h->cuda(launch_periodic(h->storage, pa, h->stream), "periodic refresh");
 }
 
 // Diffuse re-emission fractions: tables 0-3 for the walls (inward normals +x, -x, +y,
@@ -413,6 +445,7 @@ wlbm_status wlbm_create(const wlbm_grid* grid, const float* mfp_cells, double mf
                       cudaHostAllocDefault);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev[k], cudaEventDisableTiming);
   }
+  if (e == cudaSuccess) e = prepare_step_kernels();
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // host vectors die here
   if (e != cudaSuccess) {
     const std::string m = std::string("wlbm_create: ") + cudaGetErrorString(e);
@@ -461,6 +494,7 @@ wlbm_status wlbm_init_temperature(wlbm_handle* h, const float* dT) {
   }
   h->inv_scale = 1.f / h->scale;
   h->build_wall_segments();
+  h->drop_graphs();
   h->tas.reset(g.q);
   InitArgs a{};
   a.planes = h->planes; a.plane = g.plane; a.pitch = g.pitch; a.nx = g.nx; a.ny = g.ny; a.q = g.q;
@@ -468,17 +502,111 @@ wlbm_status wlbm_init_temperature(wlbm_handle* h, const float* dT) {
   a.t_ref = h->t_ref; a.theta = h->theta; a.e_ref = h->e_eq_ref;
   a.scale = h->scale; a.inv_scale = h->inv_scale;
   ++h->launches;
-  return h->cuda(launch_init(h->storage, a, h->stream), "wlbm_init_temperature");
+  const wlbm_status st = h->cuda(launch_init(h->storage, a, h->stream), "wlbm_init_temperature");
+  return st == WLBM_OK ? refresh_periodic(h) : st;
+}
+
+// Launch the kernels of `count` steps whose codes sit at d_codes[t][q], t < count.
+static wlbm_status enqueue_steps(wlbm_handle* h, int count, bool profile) {
+  const Geom& g = h->g;
+  const bool any_wall = h->walls.nseg > 0;
+  // both axes periodic: the step kernel mirrors the edges itself (grids of 2+ cells)
+  const bool wrap = h->fuse_periodic && h->xper && h->yper && g.nx >= 2 && g.ny >= 2;
+  const bool any_per = (h->xper || h->yper) && !wrap;
+  wlbm_status st = WLBM_OK;
+  for (int t = 0; t < count; ++t) {
+    const uint8_t* codes = h->d_codes + size_t(t) * g.q;
+    if (any_wall) {
+      WallArgs wa = h->walls;
+      wa.codes = codes;
+      wa.e_ref = h->ref_plane();
+      st = h->cuda(launch_walls(h->storage, wa, h->stream), "wlbm_step: walls");
+      if (st != WLBM_OK) return st;
+      ++h->launches;
+    }
+    if (any_per) {
+      PeriodicArgs pa{};
+      pa.planes = h->planes; pa.plane = g.plane; pa.pitch = g.pitch; pa.nx = g.nx;
+      pa.ny = g.ny; pa.q = g.q; pa.codes = codes; pa.e_cur = h->e[h->e_cur];
+      pa.e_ref = h->ref_plane();
+      pa.xper = h->xper; pa.yper = h->yper;
+      st = h->cuda(launch_periodic(h->storage, pa, h->stream), "wlbm_step: periodic");
+      if (st != WLBM_OK) return st;
+      ++h->launches;
+    }
+    StepArgs sa{};
+    sa.planes = h->planes; sa.plane = g.plane; sa.pitch = g.pitch; sa.rows = g.rows;
+    sa.nx = g.nx; sa.ny = g.ny; sa.q = g.q; sa.codes = codes; sa.w = h->w_dev();
+    sa.e_in = h->e[h->e_cur]; sa.e_out = h->e[h->e_spare]; sa.e_ref = h->ref_plane();
+    sa.wfield = h->field_w ? h->wfield : nullptr; sa.w0 = h->w0;
+    sa.scale = h->scale; sa.inv_scale = h->inv_scale;
+    sa.variant = h->step_variant; sa.status = h->d_status;
+    sa.xper = h->xper; sa.yper = h->yper; sa.wrap = wrap;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (profile) {
+      if (h->prof_used + 2 > h->prof_ev.size()) {
+        for (int k = 0; k < 2; ++k) {
+          cudaEvent_t ev;
+          st = h->cuda(cudaEventCreate(&ev), "wlbm_step: profiling event");
+          if (st != WLBM_OK) return st;
+          h->prof_ev.push_back(ev);
+        }
+      }
+      e0 = h->prof_ev[h->prof_used];
+      e1 = h->prof_ev[h->prof_used + 1];
+      h->prof_used += 2;
+      st = h->cuda(cudaEventRecord(e0, h->stream), "wlbm_step: profiling");
+      if (st != WLBM_OK) return st;
+    }
+    st = h->cuda(launch_step(h->storage, sa, h->stream), "wlbm_step: step");
+    if (st != WLBM_OK) return st;
+    ++h->launches;
+    if (e1) {
+      st = h->cuda(cudaEventRecord(e1, h->stream), "wlbm_step: profiling");
+      if (st != WLBM_OK) return st;
+    }
+    h->rotate_energy();
+  }
+  return WLBM_OK;
+}
+
+// Replay (capturing on first use) a CUDA graph of graph_steps steps.  The energy-plane
+// roles return to the same state after a multiple of 6 steps, so one graph per starting
+// role serves every chunk.
+static wlbm_status run_graph(wlbm_handle* h) {
+  const int G = h->graph_steps;
+  const int phase = h->e_cur;
+  if (!h->graphs[phase]) {
+    const int64_t launches0 = h->launches;
+    wlbm_status st = h->cuda(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal),
+                             "wlbm_step: graph capture");
+    if (st != WLBM_OK) return st;
+    const wlbm_status est = enqueue_steps(h, G, false);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(h->stream, &graph);
+    if (est != WLBM_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return est;
+    }
+    st = h->cuda(ce, "wlbm_step: graph capture");
+    if (st == WLBM_OK)
+      st = h->cuda(cudaGraphInstantiate(&h->graphs[phase], graph, 0), "wlbm_step: graph");
+    if (graph) cudaGraphDestroy(graph);
+    if (st != WLBM_OK) return st;
+    h->graph_launches = h->launches - launches0;
+    h->launches = launches0;
+  }
+  h->launches += h->graph_launches;
+  return h->cuda(cudaGraphLaunch(h->graphs[phase], h->stream), "wlbm_step: graph launch");
 }
 
 wlbm_status wlbm_step(wlbm_handle* h, int64_t n) {
   if (!h) return WLBM_ERR_INVALID_ARG;
   if (n < 0) return h->fail(WLBM_ERR_INVALID_ARG, "wlbm_step: negative step count");
   const Geom& g = h->g;
-  const bool any_wall = h->walls.nseg > 0;
-  const bool any_per = h->xper || h->yper;
+  const bool graphs = h->graph_steps > 0 && !h->profiling && h->stream != nullptr;
   while (n > 0) {
-    const int ch = int(std::min<int64_t>(n, kChunk));
+    const int ch = int(std::min<int64_t>(n, graphs ? h->graph_steps : kChunk));
     const int slot = h->slot;
     wlbm_status st = h->cuda(cudaEventSynchronize(h->ev[slot]), "wlbm_step");
     if (st != WLBM_OK) return st;
@@ -488,59 +616,11 @@ wlbm_status wlbm_step(wlbm_handle* h, int64_t n) {
                                  h->stream), "wlbm_step: schedule upload");
     if (st == WLBM_OK) st = h->cuda(cudaEventRecord(h->ev[slot], h->stream), "wlbm_step");
     if (st != WLBM_OK) return st;
-    for (int t = 0; t < ch; ++t) {
-      const uint8_t* codes = h->d_codes + size_t(t) * g.q;
-      if (any_wall) {
-        WallArgs wa = h->walls;
-        wa.codes = codes;
-        wa.e_ref = h->ref_plane();
-        st = h->cuda(launch_walls(h->storage, wa, h->stream), "wlbm_step: walls");
-        if (st != WLBM_OK) return st;
-        ++h->launches;
-      }
-      if (any_per) {
-        PeriodicArgs pa{};
-        pa.planes = h->planes; pa.plane = g.plane; pa.pitch = g.pitch; pa.nx = g.nx;
-        pa.ny = g.ny; pa.q = g.q; pa.codes = codes; pa.e_cur = h->e[h->e_cur];
-        pa.e_ref = h->ref_plane();
-        pa.xper = h->xper; pa.yper = h->yper;
-        st = h->cuda(launch_periodic(h->storage, pa, h->stream), "wlbm_step: periodic");
-        if (st != WLBM_OK) return st;
-        ++h->launches;
-      }
-      StepArgs sa{};
-      sa.planes = h->planes; sa.plane = g.plane; sa.pitch = g.pitch; sa.rows = g.rows;
-      sa.nx = g.nx; sa.ny = g.ny; sa.q = g.q; sa.codes = codes; sa.w = h->w_dev();
-      sa.e_in = h->e[h->e_cur]; sa.e_out = h->e[h->e_spare]; sa.e_ref = h->ref_plane();
-      sa.wfield = h->field_w ? h->wfield : nullptr; sa.w0 = h->w0;
-      sa.scale = h->scale; sa.inv_scale = h->inv_scale;
-      sa.variant = h->step_variant; sa.status = h->d_status;
-      sa.xper = h->xper; sa.yper = h->yper;
-      cudaEvent_t e0 = nullptr, e1 = nullptr;
-      if (h->profiling) {
-        if (h->prof_used + 2 > h->prof_ev.size()) {
-          for (int k = 0; k < 2; ++k) {
-            cudaEvent_t ev;
-            st = h->cuda(cudaEventCreate(&ev), "wlbm_step: profiling event");
-            if (st != WLBM_OK) return st;
-            h->prof_ev.push_back(ev);
-          }
-        }
-        e0 = h->prof_ev[h->prof_used];
-        e1 = h->prof_ev[h->prof_used + 1];
-        h->prof_used += 2;
-        st = h->cuda(cudaEventRecord(e0, h->stream), "wlbm_step: profiling");
-        if (st != WLBM_OK) return st;
-      }
-      st = h->cuda(launch_step(h->storage, sa, h->stream), "wlbm_step: step");
-      if (st != WLBM_OK) return st;
-      ++h->launches;
-      if (e1) {
-        st = h->cuda(cudaEventRecord(e1, h->stream), "wlbm_step: profiling");
-        if (st != WLBM_OK) return st;
-      }
-      h->rotate_energy();
-    }
+    if (graphs && ch == h->graph_steps)
+      st = run_graph(h);
+    else
+      st = enqueue_steps(h, ch, h->profiling);
+    if (st != WLBM_OK) return st;
     h->slot ^= 1;
     n -= ch;
   }
@@ -549,8 +629,19 @@ wlbm_status wlbm_step(wlbm_handle* h, int64_t n) {
 
 wlbm_status wlbm_set_option(wlbm_handle* h, int32_t key, int64_t value) {
   if (!h) return WLBM_ERR_INVALID_ARG;
-  if (key == WLBM_OPT_STEP_VARIANT && (value == 0 || value == 1)) {
+  if (key == WLBM_OPT_STEP_VARIANT && value >= 0 && value <= 2) {
     h->step_variant = int(value);
+    h->drop_graphs();
+    return WLBM_OK;
+  }
+  if (key == WLBM_OPT_GRAPH_STEPS && value >= 0 && value <= kChunk && value % 6 == 0) {
+    h->graph_steps = int(value);
+    h->drop_graphs();
+    return WLBM_OK;
+  }
+  if (key == WLBM_OPT_FUSE_PERIODIC && (value == 0 || value == 1)) {
+    h->fuse_periodic = int(value);
+    h->drop_graphs();
     return WLBM_OK;
   }
   return h->fail(WLBM_ERR_INVALID_ARG, "wlbm_set_option: unknown key or value");
@@ -657,8 +748,10 @@ wlbm_status wlbm_get_state(wlbm_handle* h, float* framed) {
 wlbm_status wlbm_set_state(wlbm_handle* h, const float* framed) {
   if (!h) return WLBM_ERR_INVALID_ARG;
   if (!framed) return h->fail(WLBM_ERR_INVALID_ARG, "wlbm_set_state: NULL input");
-  return h->cuda(launch_set_state(h->storage, state_args(h, const_cast<float*>(framed)), h->stream),
-                 "wlbm_set_state");
+  const wlbm_status st = h->cuda(
+      launch_set_state(h->storage, state_args(h, const_cast<float*>(framed)), h->stream),
+      "wlbm_set_state");
+  return st == WLBM_OK ? refresh_periodic(h) : st;
 }
 
 
@@ -820,6 +913,7 @@ wlbm_status wlbm_adjoint_backward(wlbm_handle* h, const float* dJ_dT, float* dJ_
         sa.scale = 1.f; sa.inv_scale = 1.f; sa.xper = h->xper; sa.yper = h->yper;
         sa.variant = h->step_variant; sa.status = h->d_status;
         sa.tape = 1; sa.tape_dst = slot + state;
+        sa.wrap = h->xper && h->yper && g.nx >= 2 && g.ny >= 2;
         ok(launch_step(h->storage, sa, s), "adjoint: recompute");
         ec ^= 1;
       }
@@ -858,6 +952,471 @@ wlbm_status wlbm_adjoint_backward(wlbm_handle* h, const float* dJ_dT, float* dJ_
       dJ_dTwall[k] = gt[k] * e * (1.0 + e) * x / h->t_wall[k];
     }
   }
+  return WLBM_OK;
+}
+
+}  // extern "C"
+
+// ============================================================================ batches
+// Many independent grids (instances) advanced together: one wall launch and one step
+// launch per step for the whole batch.  Each instance is a full wlbm_handle; the batch
+// adds the per-chunk instance records the batched kernels read.
+namespace {
+constexpr int kBatchChunk = 64;   // steps per schedule upload of a batch
+}
+
+struct wlbm_batch {
+  std::vector<wlbm_handle*> h;
+  int storage = 0, variant = 1, graph_steps = 0, fuse_periodic = 0;
+  cudaStream_t stream = nullptr;
+  wlbm_allocator alloc{nullptr, nullptr, nullptr};
+  std::vector<void*> owned;
+  BatchInst* d_inst = nullptr;
+  BatchWalls* d_walls = nullptr;
+  uint8_t* d_codes = nullptr;
+  BatchInst* h_inst = nullptr;      // pinned staging
+  BatchWalls* h_walls = nullptr;
+  uint8_t* h_codes = nullptr;
+  cudaEvent_t ev = nullptr;
+  std::vector<size_t> code_off;
+  size_t code_bytes = 0;
+  int total_tiles = 0, total_wall_warps = 0;
+  std::vector<int> per;             // instances whose periodic edges need their own launch
+  // Captured chunks, keyed by the energy-plane phases of the instances in `per` (their
+  // periodic launches bake plane pointers; the batched kernels read phases at run time).
+  struct Graph {
+    std::vector<int> key;
+    cudaGraphExec_t exec = nullptr;
+  };
+  std::vector<Graph> graphs;
+  int64_t graph_launches = 0, launches = 0;
+  bool profiling = false;
+  std::vector<cudaEvent_t> prof_ev;
+  size_t prof_used = 0;
+  std::string err;
+
+  wlbm_status fail(wlbm_status s, const std::string& m) {
+    err = m;
+    return s;
+  }
+  wlbm_status cuda(cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return WLBM_OK;
+    return fail(WLBM_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  }
+  void* dev_alloc(size_t bytes) {
+    bytes = size_t(round_up(int64_t(bytes), 256));
+    void* p = nullptr;
+    if (alloc.alloc) {
+      p = alloc.alloc(bytes, alloc.ctx);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+    }
+    if (p) owned.push_back(p);
+    return p;
+  }
+  void drop_graph() {
+    for (Graph& gr : graphs) cudaGraphExecDestroy(gr.exec);
+    graphs.clear();
+  }
+  std::vector<int> phase_key() const {
+    std::vector<int> key;
+    for (int k : per) key.push_back(h[k]->e_cur);
+    return key;
+  }
+  void release() {
+    drop_graph();
+    for (void* p : owned) {
+      if (alloc.alloc) {
+        if (alloc.free) alloc.free(p, alloc.ctx);
+      } else {
+        cudaFree(p);
+      }
+    }
+    owned.clear();
+    if (h_inst) cudaFreeHost(h_inst);
+    if (h_walls) cudaFreeHost(h_walls);
+    if (h_codes) cudaFreeHost(h_codes);
+    if (ev) cudaEventDestroy(ev);
+    for (cudaEvent_t e : prof_ev) cudaEventDestroy(e);
+    h_inst = nullptr; h_walls = nullptr; h_codes = nullptr; ev = nullptr;
+    prof_ev.clear();
+    for (wlbm_handle* x : h) wlbm_destroy(x);
+    h.clear();
+  }
+  // Both axes periodic and fused: the step kernel mirrors the edges of that instance.
+  bool wraps(const wlbm_handle* x) const {
+    return fuse_periodic && x->xper && x->yper && x->g.nx >= 2 && x->g.ny >= 2;
+  }
+  void classify() {
+    per.clear();
+    for (size_t k = 0; k < h.size(); ++k)
+      if ((h[k]->xper || h[k]->yper) && !wraps(h[k])) per.push_back(int(k));
+  }
+  // Block and warp offsets of every instance in the batched grids.
+  void layout() {
+    total_tiles = 0;
+    total_wall_warps = 0;
+    const int tw = step_tile_width(storage, variant);
+    for (size_t k = 0; k < h.size(); ++k) {
+      const Geom& g = h[k]->g;
+      const int tx = (g.nx + 2 + tw - 1) / tw, ty = (g.ny + 2 + kStepRows - 1) / kStepRows;
+      h_inst[k].tiles_x = tx;
+      h_inst[k].first_tile = total_tiles;
+      total_tiles += tx * ty;
+      h_walls[k].first_warp = total_wall_warps;
+      for (int s = 0; s < h[k]->walls.nseg; ++s) total_wall_warps += h[k]->walls.seg[s].count;
+    }
+  }
+};
+
+extern "C" {
+
+wlbm_status wlbm_batch_create(int32_t n, const wlbm_grid* grids, const float* const* mfp_cells,
+                              const double* mfp_uniform, const wlbm_boundary* bcs,
+                              const wlbm_allocator* alloc, void* stream, wlbm_batch** out) {
+  if (n < 1 || !grids || !bcs || !out || (!mfp_cells && !mfp_uniform)) {
+    set_global_error("wlbm_batch_create: bad count or NULL argument");
+    return WLBM_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  auto* b = new wlbm_batch();
+  b->stream = static_cast<cudaStream_t>(stream);
+  if (alloc) b->alloc = *alloc;
+  auto bad = [&](wlbm_status st, const std::string& m) {
+    b->release();
+    delete b;
+    if (!m.empty()) set_global_error(m);
+    return st;
+  };
+  for (int k = 0; k < n; ++k) {
+    wlbm_handle* x = nullptr;
+    const wlbm_status st = wlbm_create(&grids[k], mfp_cells ? mfp_cells[k] : nullptr,
+                                       mfp_uniform ? mfp_uniform[k] : 0.0, &bcs[k], alloc, stream,
+                                       &x);
+    if (st != WLBM_OK) return bad(st, "");   // message of wlbm_create stays in place
+    b->h.push_back(x);
+    if (grids[k].storage != grids[0].storage)
+      return bad(WLBM_ERR_INVALID_ARG, "wlbm_batch_create: all instances need one storage type");
+  }
+  b->storage = grids[0].storage;
+  b->classify();
+  b->code_off.resize(n);
+  for (int k = 0; k < n; ++k) {
+    b->code_off[k] = b->code_bytes;
+    b->code_bytes += size_t(kBatchChunk) * grids[k].q;
+  }
+  b->d_codes = static_cast<uint8_t*>(b->dev_alloc(b->code_bytes));
+  b->d_inst = static_cast<BatchInst*>(b->dev_alloc(sizeof(BatchInst) * n));
+  b->d_walls = static_cast<BatchWalls*>(b->dev_alloc(sizeof(BatchWalls) * n));
+  if (!b->d_codes || !b->d_inst || !b->d_walls)
+    return bad(WLBM_ERR_OOM, "wlbm_batch_create: device allocation failed");
+  cudaError_t e = cudaHostAlloc(reinterpret_cast<void**>(&b->h_codes), b->code_bytes,
+                                cudaHostAllocDefault);
+  if (e == cudaSuccess)
+    e = cudaHostAlloc(reinterpret_cast<void**>(&b->h_inst), sizeof(BatchInst) * n,
+                      cudaHostAllocDefault);
+  if (e == cudaSuccess)
+    e = cudaHostAlloc(reinterpret_cast<void**>(&b->h_walls), sizeof(BatchWalls) * n,
+                      cudaHostAllocDefault);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return bad(WLBM_ERR_CUDA, std::string("wlbm_batch_create: ") + cudaGetErrorString(e));
+  }
+  std::memset(b->h_inst, 0, sizeof(BatchInst) * n);
+  std::memset(b->h_walls, 0, sizeof(BatchWalls) * n);
+  b->layout();
+  *out = b;
+  return WLBM_OK;
+}
+
+void wlbm_batch_destroy(wlbm_batch* b) {
+  if (!b) return;
+  cudaStreamSynchronize(b->stream);
+  b->release();
+  delete b;
+}
+
+const char* wlbm_batch_last_error(const wlbm_batch* b) {
+  return b ? b->err.c_str() : wlbm_last_error(nullptr);
+}
+
+int32_t wlbm_batch_size(const wlbm_batch* b) { return b ? int32_t(b->h.size()) : -1; }
+
+wlbm_handle* wlbm_batch_instance(wlbm_batch* b, int32_t k) {
+  return (b && k >= 0 && k < int32_t(b->h.size())) ? b->h[k] : nullptr;
+}
+
+wlbm_status wlbm_batch_init_temperature(wlbm_batch* b, const float* const* dT) {
+  if (!b || !dT) return WLBM_ERR_INVALID_ARG;
+  for (size_t k = 0; k < b->h.size(); ++k) {
+    const wlbm_status st = wlbm_init_temperature(b->h[k], dT[k]);
+    if (st != WLBM_OK) return b->fail(st, "instance " + std::to_string(k) + ": " + b->h[k]->err);
+  }
+  b->drop_graph();   // wall values may have changed
+  return WLBM_OK;
+}
+
+wlbm_status wlbm_batch_set_option(wlbm_batch* b, int32_t key, int64_t value) {
+  if (!b) return WLBM_ERR_INVALID_ARG;
+  if (key == WLBM_OPT_STEP_VARIANT && (value == 0 || value == 1)) {
+    b->variant = int(value);
+    b->layout();
+    b->drop_graph();
+    return WLBM_OK;
+  }
+  if (key == WLBM_OPT_GRAPH_STEPS && value >= 0 && value <= kBatchChunk && value % 6 == 0) {
+    b->graph_steps = int(value);
+    b->drop_graph();
+    return WLBM_OK;
+  }
+  if (key == WLBM_OPT_FUSE_PERIODIC && (value == 0 || value == 1)) {
+    b->fuse_periodic = int(value);
+    b->classify();
+    b->drop_graph();
+    return WLBM_OK;
+  }
+  return b->fail(WLBM_ERR_INVALID_ARG, "wlbm_batch_set_option: unknown key or value");
+}
+
+}  // extern "C"
+
+// Kernels of `count` steps for the whole batch, instance records already on the device.
+static wlbm_status batch_enqueue(wlbm_batch* b, int count, bool profile) {
+  const int n = int(b->h.size());
+  wlbm_status st = WLBM_OK;
+  for (int t = 0; t < count && st == WLBM_OK; ++t) {
+    if (b->total_wall_warps > 0) {
+      st = b->cuda(launch_walls_batch(b->storage, b->d_walls, n, b->total_wall_warps, t, b->stream),
+                   "wlbm_batch_step: walls");
+      ++b->launches;
+    }
+    for (int k : b->per) {
+      if (st != WLBM_OK) break;
+      wlbm_handle* x = b->h[k];
+      const Geom& g = x->g;
+      const BatchInst& I = b->h_inst[k];
+      const int cur = (I.phase + t) % I.n_e;
+      PeriodicArgs pa{};
+      pa.planes = x->planes; pa.plane = g.plane; pa.pitch = g.pitch; pa.nx = g.nx; pa.ny = g.ny;
+      pa.q = g.q; pa.codes = b->d_codes + b->code_off[k] + size_t(t) * g.q;
+      pa.e_cur = I.e[cur]; pa.e_ref = I.n_e == 3 ? I.e[(cur + 2) % 3] : nullptr;
+      pa.xper = x->xper; pa.yper = x->yper;
+      st = b->cuda(launch_periodic(b->storage, pa, b->stream), "wlbm_batch_step: periodic");
+      ++b->launches;
+    }
+    if (st != WLBM_OK) break;
+    cudaEvent_t e1 = nullptr;
+    if (profile) {
+      if (b->prof_used + 2 > b->prof_ev.size()) {
+        for (int j = 0; j < 2; ++j) {
+          cudaEvent_t ev;
+          st = b->cuda(cudaEventCreate(&ev), "wlbm_batch_step: profiling");
+          if (st != WLBM_OK) return st;
+          b->prof_ev.push_back(ev);
+        }
+      }
+      st = b->cuda(cudaEventRecord(b->prof_ev[b->prof_used], b->stream), "profiling");
+      e1 = b->prof_ev[b->prof_used + 1];
+      b->prof_used += 2;
+    }
+    if (st == WLBM_OK)
+      st = b->cuda(launch_step_batch(b->storage, b->variant, b->d_inst, n, b->total_tiles, t,
+                                     b->stream), "wlbm_batch_step: step");
+    ++b->launches;
+    if (st == WLBM_OK && e1) st = b->cuda(cudaEventRecord(e1, b->stream), "profiling");
+  }
+  return st;
+}
+
+extern "C" {
+
+wlbm_status wlbm_batch_step(wlbm_batch* b, int64_t n) {
+  if (!b) return WLBM_ERR_INVALID_ARG;
+  if (n < 0) return b->fail(WLBM_ERR_INVALID_ARG, "wlbm_batch_step: negative step count");
+  const int ni = int(b->h.size());
+  const bool graphs = b->graph_steps > 0 && !b->profiling && b->stream;
+  while (n > 0) {
+    const int ch = int(std::min<int64_t>(n, graphs ? b->graph_steps : kBatchChunk));
+    wlbm_status st = b->cuda(cudaEventSynchronize(b->ev), "wlbm_batch_step");
+    if (st != WLBM_OK) return st;
+    for (int k = 0; k < ni; ++k) {
+      wlbm_handle* x = b->h[k];
+      const Geom& g = x->g;
+      uint8_t* hc = b->h_codes + b->code_off[k];
+      for (int t = 0; t < ch; ++t) tas_advance(x->lat, &x->tas, hc + size_t(t) * g.q);
+      BatchInst& I = b->h_inst[k];
+      StepArgs& a = I.a;
+      a = StepArgs{};
+      a.planes = x->planes; a.plane = g.plane; a.pitch = g.pitch; a.rows = g.rows;
+      a.nx = g.nx; a.ny = g.ny; a.q = g.q; a.w = x->w_dev();
+      a.wfield = x->field_w ? x->wfield : nullptr; a.w0 = x->w0;
+      a.scale = x->scale; a.inv_scale = x->inv_scale;
+      a.variant = b->variant; a.status = x->d_status;
+      a.xper = x->xper; a.yper = x->yper;
+      a.wrap = b->wraps(x);
+      for (int j = 0; j < 3; ++j) I.e[j] = x->e[j];
+      I.codes = b->d_codes + b->code_off[k];
+      I.n_e = x->bf16() ? 3 : 2;
+      I.phase = x->e_cur;
+      BatchWalls& Wk = b->h_walls[k];
+      Wk.w = x->walls;
+      for (int j = 0; j < 3; ++j) Wk.e[j] = x->e[j];
+      Wk.codes = I.codes;
+      Wk.n_e = I.n_e;
+      Wk.phase = I.phase;
+    }
+    st = b->cuda(cudaMemcpyAsync(b->d_codes, b->h_codes, b->code_bytes, cudaMemcpyHostToDevice,
+                                 b->stream), "wlbm_batch_step: upload");
+    if (st == WLBM_OK)
+      st = b->cuda(cudaMemcpyAsync(b->d_inst, b->h_inst, sizeof(BatchInst) * ni,
+                                   cudaMemcpyHostToDevice, b->stream), "wlbm_batch_step: upload");
+    if (st == WLBM_OK)
+      st = b->cuda(cudaMemcpyAsync(b->d_walls, b->h_walls, sizeof(BatchWalls) * ni,
+                                   cudaMemcpyHostToDevice, b->stream), "wlbm_batch_step: upload");
+    if (st == WLBM_OK) st = b->cuda(cudaEventRecord(b->ev, b->stream), "wlbm_batch_step");
+    if (st != WLBM_OK) return st;
+    if (graphs && ch == b->graph_steps) {
+      const std::vector<int> key = b->phase_key();
+      cudaGraphExec_t exec = nullptr;
+      for (const wlbm_batch::Graph& gr : b->graphs)
+        if (gr.key == key) exec = gr.exec;
+      if (!exec) {
+        if (b->graphs.size() >= 3) b->drop_graph();
+        const int64_t l0 = b->launches;
+        st = b->cuda(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal),
+                     "wlbm_batch_step: capture");
+        if (st != WLBM_OK) return st;
+        const wlbm_status est = batch_enqueue(b, ch, false);
+        cudaGraph_t gr = nullptr;
+        const cudaError_t ce = cudaStreamEndCapture(b->stream, &gr);
+        if (est == WLBM_OK) st = b->cuda(ce, "wlbm_batch_step: capture");
+        else st = est;
+        if (st == WLBM_OK)
+          st = b->cuda(cudaGraphInstantiate(&exec, gr, 0), "wlbm_batch_step: graph");
+        if (gr) cudaGraphDestroy(gr);
+        if (st != WLBM_OK) return st;
+        b->graphs.push_back({key, exec});
+        b->graph_launches = b->launches - l0;
+        b->launches = l0;
+      }
+      b->launches += b->graph_launches;
+      st = b->cuda(cudaGraphLaunch(exec, b->stream), "wlbm_batch_step: graph launch");
+    } else {
+      st = batch_enqueue(b, ch, b->profiling);
+    }
+    if (st != WLBM_OK) return st;
+    for (wlbm_handle* x : b->h)
+      for (int t = 0; t < ch; ++t) x->rotate_energy();
+    n -= ch;
+  }
+  return WLBM_OK;
+}
+
+wlbm_status wlbm_batch_profile(wlbm_batch* b, int32_t enable) {
+  if (!b) return WLBM_ERR_INVALID_ARG;
+  b->profiling = enable != 0;
+  return WLBM_OK;
+}
+
+wlbm_status wlbm_batch_profile_read(wlbm_batch* b, double* step_ms, int64_t* step_launches,
+                                    int64_t* all_launches) {
+  if (!b) return WLBM_ERR_INVALID_ARG;
+  wlbm_status st = b->cuda(cudaStreamSynchronize(b->stream), "wlbm_batch_profile_read");
+  if (st != WLBM_OK) return st;
+  double total = 0.0;
+  for (size_t k = 0; k + 1 < b->prof_used; k += 2) {
+    float ms = 0.f;
+    st = b->cuda(cudaEventElapsedTime(&ms, b->prof_ev[k], b->prof_ev[k + 1]), "profile_read");
+    if (st != WLBM_OK) return st;
+    total += ms;
+  }
+  if (step_ms) *step_ms = total;
+  if (step_launches) *step_launches = int64_t(b->prof_used / 2);
+  if (all_launches) *all_launches = b->launches;
+  b->prof_used = 0;
+  return WLBM_OK;
+}
+
+// Native autotuner: times `trial_steps` steps for every candidate (step-kernel variant x
+// graph replay) after one warm-up run of each, keeps the fastest, and reports it.  The
+// trial steps advance the instances: call it before wlbm_batch_init_temperature.
+wlbm_status wlbm_batch_autotune(wlbm_batch* b, int32_t trial_steps, int32_t* variant,
+                                int32_t* graph_steps, double* ms_per_step) {
+  if (!b || trial_steps < 6) return WLBM_ERR_INVALID_ARG;
+  const int g = std::min(kBatchChunk, (trial_steps / 6) * 6);
+  const int cand[4][2] = {{1, 0}, {0, 0}, {1, g}, {0, g}};
+  double best = 1e300;
+  int bv = 1, bg = 0;
+  cudaEvent_t e0, e1;
+  wlbm_status st = b->cuda(cudaEventCreate(&e0), "autotune");
+  if (st != WLBM_OK) return st;
+  st = b->cuda(cudaEventCreate(&e1), "autotune");
+  for (int c = 0; c < 4 && st == WLBM_OK; ++c) {
+    st = wlbm_batch_set_option(b, WLBM_OPT_STEP_VARIANT, cand[c][0]);
+    if (st == WLBM_OK) st = wlbm_batch_set_option(b, WLBM_OPT_GRAPH_STEPS, cand[c][1]);
+    if (st == WLBM_OK) st = wlbm_batch_step(b, g > 0 ? g : 6);           // warm-up / capture
+    if (st == WLBM_OK) st = b->cuda(cudaEventRecord(e0, b->stream), "autotune");
+    if (st == WLBM_OK) st = wlbm_batch_step(b, trial_steps);
+    if (st == WLBM_OK) st = b->cuda(cudaEventRecord(e1, b->stream), "autotune");
+    if (st == WLBM_OK) st = b->cuda(cudaEventSynchronize(e1), "autotune");
+    float ms = 0.f;
+    if (st == WLBM_OK) st = b->cuda(cudaEventElapsedTime(&ms, e0, e1), "autotune");
+    if (st == WLBM_OK && ms / trial_steps < best) {
+      best = ms / trial_steps;
+      bv = cand[c][0];
+      bg = cand[c][1];
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != WLBM_OK) return st;
+  wlbm_batch_set_option(b, WLBM_OPT_STEP_VARIANT, bv);
+  wlbm_batch_set_option(b, WLBM_OPT_GRAPH_STEPS, bg);
+  if (variant) *variant = bv;
+  if (graph_steps) *graph_steps = bg;
+  if (ms_per_step) *ms_per_step = best;
+  return WLBM_OK;
+}
+
+// The same search for one grid.
+wlbm_status wlbm_autotune(wlbm_handle* h, int32_t trial_steps, int32_t* variant,
+                          int32_t* graph_steps, double* ms_per_step) {
+  if (!h || trial_steps < 6) return WLBM_ERR_INVALID_ARG;
+  const int g = std::min(kChunk, (trial_steps / 6) * 6);
+  const int cand[6][2] = {{1, 0}, {0, 0}, {2, 0}, {1, g}, {0, g}, {2, g}};
+  double best = 1e300;
+  int bv = 1, bg = 0;
+  cudaEvent_t e0, e1;
+  wlbm_status st = h->cuda(cudaEventCreate(&e0), "autotune");
+  if (st != WLBM_OK) return st;
+  st = h->cuda(cudaEventCreate(&e1), "autotune");
+  for (int c = 0; c < 6 && st == WLBM_OK; ++c) {
+    if (cand[c][1] > 0 && !h->stream) continue;     // graphs need a capturable stream
+    st = wlbm_set_option(h, WLBM_OPT_STEP_VARIANT, cand[c][0]);
+    if (st == WLBM_OK) st = wlbm_set_option(h, WLBM_OPT_GRAPH_STEPS, cand[c][1]);
+    if (st == WLBM_OK) st = wlbm_step(h, g > 0 ? g : 6);
+    if (st == WLBM_OK) st = h->cuda(cudaEventRecord(e0, h->stream), "autotune");
+    if (st == WLBM_OK) st = wlbm_step(h, trial_steps);
+    if (st == WLBM_OK) st = h->cuda(cudaEventRecord(e1, h->stream), "autotune");
+    if (st == WLBM_OK) st = h->cuda(cudaEventSynchronize(e1), "autotune");
+    float ms = 0.f;
+    if (st == WLBM_OK) st = h->cuda(cudaEventElapsedTime(&ms, e0, e1), "autotune");
+    if (st == WLBM_OK && ms / trial_steps < best) {
+      best = ms / trial_steps;
+      bv = cand[c][0];
+      bg = cand[c][1];
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != WLBM_OK) return st;
+  wlbm_set_option(h, WLBM_OPT_STEP_VARIANT, bv);
+  wlbm_set_option(h, WLBM_OPT_GRAPH_STEPS, bg);
+  if (variant) *variant = bv;
+  if (graph_steps) *graph_steps = bg;
+  if (ms_per_step) *ms_per_step = best;
   return WLBM_OK;
 }
 

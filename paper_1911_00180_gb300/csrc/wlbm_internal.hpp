@@ -21,6 +21,7 @@ namespace wlbm {
 constexpr int kGhostCol = 32;
 constexpr int kX0 = kGhostCol + 1;
 constexpr int kMaxQ = 1024;
+constexpr int kStepRows = 8;   // rows (warps) per block of the step kernels
 
 struct Geom {
   int nx = 0, ny = 0, q = 0;
@@ -61,6 +62,10 @@ struct StepArgs {
   // written to tape_dst + i*plane, whatever its parity or pause flag
   int tape;
   void* tape_dst;
+  // both axes periodic: ghost rows/columns are not computed; instead every edge cell
+  // also writes its new value (and E') into the ghost cells that mirror it, so the next
+  // step needs no separate periodic pass
+  int wrap;
 };
 
 // Wall segment for the boundary kernel (one warp per ghost cell).
@@ -95,6 +100,7 @@ struct PeriodicArgs {
   float* e_ref;          // reference energy plane (bfloat16 only), copied likewise
   int xper, yper;
   int tape;              // 1: all planes at `planes` (parity ignored)
+  const ParityMask* par; // if non-null, plane parities come from this mask, not codes
 };
 
 struct InitArgs {
@@ -153,6 +159,26 @@ struct StateArgs {
   float scale, inv_scale;
 };
 
+// One instance of a batch: its constant step arguments plus what changes per step.  The
+// batched kernels fill codes / e_in / e_out / e_ref for step t of the chunk from these.
+struct BatchInst {
+  StepArgs a;             // per-instance constants (codes, e_* are set per step)
+  float* e[3];            // local-energy planes; roles rotate with the step
+  const uint8_t* codes;   // this instance's codes of the chunk, [t][q]
+  int n_e;                // 2 (float32) or 3 (bfloat16: with the reference plane)
+  int phase;              // index of the current energy plane at the start of the chunk
+  int tiles_x;            // step-kernel tiles per row
+  int first_tile;         // first block of this instance in the batched grid
+};
+
+struct BatchWalls {
+  WallArgs w;             // per-instance wall segments (codes / e_ref set per step)
+  float* e[3];
+  const uint8_t* codes;
+  int n_e, phase;
+  int first_warp;         // first warp of this instance in the batched wall grid
+};
+
 // Reverse-step arguments (float32 storage only).
 struct AdjArgs {
   const float* lam_in;   // adjoint of the step's output, [q][plane]
@@ -173,6 +199,13 @@ void set_global_error_msg(const std::string& m);
 
 // Kernel launchers (k_step.cu, k_aux.cu).  Return cudaGetLastError().
 cudaError_t launch_step(int storage, const StepArgs& a, cudaStream_t s);
+cudaError_t prepare_step_kernels();   // per-device kernel attributes; call before capture
+// Batched launches (one launch per step for all instances of a batch).
+int step_tile_width(int storage, int variant);
+cudaError_t launch_step_batch(int storage, int variant, const BatchInst* insts, int n,
+                              int total_tiles, int t, cudaStream_t s);
+cudaError_t launch_walls_batch(int storage, const BatchWalls* b, int n, int total_warps, int t,
+                               cudaStream_t s);
 cudaError_t launch_walls(int storage, const WallArgs& a, cudaStream_t s);
 cudaError_t launch_periodic(int storage, const PeriodicArgs& a, cudaStream_t s);
 cudaError_t launch_init(int storage, const InitArgs& a, cudaStream_t s);

@@ -16,7 +16,7 @@ WLBM_OK, WLBM_ERR_INVALID_ARG, WLBM_ERR_UNSTABLE, WLBM_ERR_OOM = 0, 1, 2, 3
 WLBM_ERR_CUDA, WLBM_ERR_TIMEOUT, WLBM_ERR_STATE = 4, 5, 6
 BC_PERIODIC, BC_ISOTHERMAL, BC_ADIABATIC_DIFFUSE = 0, 1, 2
 STORE_FP32_DEV, STORE_BF16_DEV = 0, 1
-OPT_STEP_VARIANT = 1
+OPT_STEP_VARIANT, OPT_GRAPH_STEPS, OPT_FUSE_PERIODIC = 1, 2, 3
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "UNSTABLE", 3: "OOM", 4: "CUDA", 5: "TIMEOUT",
                 6: "STATE"}
 
@@ -67,6 +67,22 @@ def _load():
         "wlbm_adjoint_forward": (C.c_int, [vp, vp, i64, i32]),
         "wlbm_adjoint_backward": (C.c_int, [vp, vp, vp, C.POINTER(dbl), vp]),
         "wlbm_set_option": (C.c_int, [vp, i32, i64]),
+        "wlbm_autotune": (C.c_int, [vp, i32, C.POINTER(i32), C.POINTER(i32), C.POINTER(dbl)]),
+        "wlbm_batch_create": (C.c_int, [i32, C.POINTER(wlbm_grid), C.POINTER(vp), C.POINTER(dbl),
+                                        C.POINTER(wlbm_boundary), C.POINTER(wlbm_allocator), vp,
+                                        C.POINTER(vp)]),
+        "wlbm_batch_destroy": (None, [vp]),
+        "wlbm_batch_last_error": (C.c_char_p, [vp]),
+        "wlbm_batch_size": (i32, [vp]),
+        "wlbm_batch_instance": (vp, [vp, i32]),
+        "wlbm_batch_init_temperature": (C.c_int, [vp, C.POINTER(vp)]),
+        "wlbm_batch_set_option": (C.c_int, [vp, i32, i64]),
+        "wlbm_batch_step": (C.c_int, [vp, i64]),
+        "wlbm_batch_profile": (C.c_int, [vp, i32]),
+        "wlbm_batch_profile_read": (C.c_int, [vp, C.POINTER(dbl), C.POINTER(i64),
+                                              C.POINTER(i64)]),
+        "wlbm_batch_autotune": (C.c_int, [vp, i32, C.POINTER(i32), C.POINTER(i32),
+                                          C.POINTER(dbl)]),
         "wlbm_check": (C.c_int, [vp]),
         "wlbm_profile": (C.c_int, [vp, i32]),
         "wlbm_profile_read": (C.c_int, [vp, C.POINTER(dbl), C.POINTER(i64), C.POINTER(i64)]),
@@ -219,6 +235,14 @@ class WormLBM:
     def wlbm_set_option(self, key, value):
         _check(lib.wlbm_set_option(self.h, int(key), int(value)), self.h)
 
+    def wlbm_autotune(self, trial_steps=48):
+        """Native search over step-kernel variant x CUDA-graph replay (advances the state:
+        call before wlbm_init_temperature).  Returns (variant, graph_steps, ms/step)."""
+        v, g, ms = C.c_int32(), C.c_int32(), C.c_double()
+        _check(lib.wlbm_autotune(self.h, int(trial_steps), C.byref(v), C.byref(g), C.byref(ms)),
+               self.h)
+        return v.value, g.value, ms.value
+
     def wlbm_check(self):
         _check(lib.wlbm_check(self.h), self.h)
 
@@ -241,3 +265,111 @@ class WormLBM:
         t = self._torch.as_tensor(framed, dtype=self._torch.float32, device=self.device).contiguous()
         _check(lib.wlbm_set_state(self.h, _ptr(t)), self.h)
         self._keep = t
+
+
+# ---------------------------------------------------------------------------------- batch
+def _batch_check(status, b):
+    if status != WLBM_OK:
+        msg = lib.wlbm_batch_last_error(b) if b else lib.wlbm_last_error(None)
+        raise WlbmError(status, msg.decode() if msg else "")
+
+
+class _InstanceView(WormLBM):
+    """A WormLBM facade over one instance of a batch (owned by the batch)."""
+
+    def __init__(self, batch, k, spec):
+        self._torch = batch._torch
+        self.nx, self.ny, self.q = spec["nx"], spec["ny"], spec["q"]
+        self.device, self.stream = batch.device, batch.stream
+        self.h = lib.wlbm_batch_instance(batch.b, k)
+        self._owner = batch
+
+    def close(self):        # the batch owns the handle
+        self.h = None
+
+
+class WormLBMBatch:
+    """Many independent grids advanced by one wall launch and one step launch per step.
+
+    specs: list of dicts with nx, ny, q, bc, t_wall, mfp or mfp_field, emulate_3d,
+    relax_mode; every instance uses the same storage."""
+
+    def __init__(self, specs, storage=STORE_FP32_DEV, t_ref=300.0, theta=624.8074248458514,
+                 stream=None):
+        import torch
+        self._torch = torch
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        n = len(specs)
+        grids = (wlbm_grid * n)()
+        bcs = (wlbm_boundary * n)()
+        mfps = (C.c_void_p * n)()
+        mfpu = (C.c_double * n)()
+        self._keep = []
+        for k, sp in enumerate(specs):
+            grids[k] = wlbm_grid(sp["nx"], sp["ny"], sp["q"], storage,
+                                 1 if sp.get("emulate_3d", True) else 0, sp.get("relax_mode", 0),
+                                 t_ref, theta)
+            bcs[k] = wlbm_boundary((C.c_int32 * 4)(*sp["bc"]), (C.c_double * 4)(*sp["t_wall"]))
+            if sp.get("mfp_field") is not None:
+                t = torch.as_tensor(sp["mfp_field"], dtype=torch.float32,
+                                    device=self.device).contiguous()
+                self._keep.append(t)
+                mfps[k] = t.data_ptr()
+            else:
+                mfps[k] = None
+                mfpu[k] = float(sp["mfp"])
+        dev, strm = self.device.index, self.stream.cuda_stream
+        self._alloc_fns = (ALLOC_FN(lambda nb, ctx: torch.cuda.caching_allocator_alloc(
+                               int(nb), dev, strm)),
+                           FREE_FN(lambda p, ctx: torch.cuda.caching_allocator_delete(p)))
+        self._alloc = wlbm_allocator(self._alloc_fns[0], self._alloc_fns[1], None)
+        b = C.c_void_p()
+        st = lib.wlbm_batch_create(n, grids, mfps, mfpu, bcs, C.byref(self._alloc),
+                                   C.c_void_p(strm), C.byref(b))
+        _batch_check(st, None)
+        self.b = b
+        self.specs = specs
+        self.instances = [_InstanceView(self, k, sp) for k, sp in enumerate(specs)]
+
+    def close(self):
+        if getattr(self, "b", None):
+            for v in self.instances:
+                v.close()
+            lib.wlbm_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def wlbm_batch_init_temperature(self, dTs):
+        torch = self._torch
+        ts = [torch.as_tensor(d, dtype=torch.float32, device=self.device).contiguous()
+              for d in dTs]
+        ptrs = (C.c_void_p * len(ts))(*[t.data_ptr() for t in ts])
+        _batch_check(lib.wlbm_batch_init_temperature(self.b, ptrs), self.b)
+        self._keep_dT = ts
+
+    def wlbm_batch_step(self, n=1):
+        _batch_check(lib.wlbm_batch_step(self.b, int(n)), self.b)
+
+    def wlbm_batch_set_option(self, key, value):
+        _batch_check(lib.wlbm_batch_set_option(self.b, int(key), int(value)), self.b)
+
+    def wlbm_batch_profile(self, enable=True):
+        _batch_check(lib.wlbm_batch_profile(self.b, 1 if enable else 0), self.b)
+
+    def wlbm_batch_profile_read(self):
+        ms, n, alln = C.c_double(), C.c_int64(), C.c_int64()
+        _batch_check(lib.wlbm_batch_profile_read(self.b, C.byref(ms), C.byref(n), C.byref(alln)),
+                     self.b)
+        return ms.value, n.value, alln.value
+
+    def wlbm_batch_autotune(self, trial_steps=48):
+        v, g, ms = C.c_int32(), C.c_int32(), C.c_double()
+        _batch_check(lib.wlbm_batch_autotune(self.b, int(trial_steps), C.byref(v), C.byref(g),
+                                             C.byref(ms)), self.b)
+        return v.value, g.value, ms.value

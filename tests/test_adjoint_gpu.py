@@ -1,0 +1,147 @@
+"""GPU adjoint (through the C ABI) against the oracle's exact transpose (itself pinned to
+the one-step matrix transpose and to central differences, tests/test_oracle_adjoint.py).
+
+J = mean of T - T_ref over a probe column of the final state.  Tolerance: 1e-4 of the
+largest gradient entry (float32 forward and reverse sweeps against float64)."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import adjoint as A
+
+pytestmark = pytest.mark.gpu
+P, I, D = W.PERIODIC, W.ISOTHERMAL, W.ADIABATIC_DIFFUSE
+TOL = 1e-4
+THETA = 624.8074248458514
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1911_00180_gb300  # noqa: F401
+
+
+def _case(kinds, nx=26, ny=18, q=16, steps=60, seed=3, field=True):
+    rng = np.random.default_rng(seed)
+    # log-normal MFP around 4 cells, kept above the W_corr <= 1 limit (1.37 cells)
+    mfp = (np.maximum(np.exp(np.log(4.0) + 0.25 * rng.standard_normal((ny, nx))), 1.6)
+           .astype(np.float32) if field else None)
+    y, x = np.mgrid[0:ny, 0:nx]
+    dT0 = np.exp(-((x - nx / 3.0) ** 2 + (y - ny / 2.0) ** 2) / 20.0).astype(np.float32)
+    probe = np.zeros((ny, nx), bool)
+    probe[:, (3 * nx) // 4] = True
+    tw = (300.6, 299.7, 300.2, 299.9)
+    return mfp, dT0, probe, tw
+
+
+def _gpu(kinds, mfp, dT0, probe, tw, steps, ckpt, q, mfp_uniform=3.0, variant=None):
+    import torch
+    import paper_1911_00180_gb300 as wl
+    ny, nx = dT0.shape
+    h = wl.WormLBM(nx, ny, q, mfp=mfp_uniform if mfp is None else None, mfp_field=mfp,
+                   bc=kinds, t_wall=tw, emulate_3d=True, theta=THETA)
+    if variant is not None:
+        h.wlbm_set_option(wl.wlbm.OPT_STEP_VARIANT, variant)
+    h.wlbm_adjoint_forward(dT0, steps, ckpt)
+    dT, _, _ = h.wlbm_moments(want_q=False)
+    g = torch.as_tensor(probe.astype(np.float32) / probe.sum(), device="cuda")
+    g_mfp, g_tw, g_dT0 = h.wlbm_adjoint_backward(g)
+    h.wlbm_check()
+    torch.cuda.synchronize()
+    J = float(dT.cpu().numpy()[probe].mean())
+    out = (J, g_mfp.cpu().numpy().astype(np.float64), np.array(g_tw),
+           g_dT0.cpu().numpy().astype(np.float64))
+    h.close()
+    return out
+
+
+def _oracle(kinds, mfp, dT0, probe, tw, steps, q, mfp_uniform=3.0):
+    ny, nx = dT0.shape
+    kw = dict(nx=nx, ny=ny, q=q,
+              mfp=(np.full((ny, nx), mfp_uniform) if mfp is None else mfp.astype(np.float64)),
+              bc_kind=kinds, t_wall=tw, emulate_3d=True, theta=THETA)
+    return A.AdjointRun(kw, dT0.astype(np.float64), steps, probe).gradients()
+
+
+def _rel(a, b):
+    return float(np.abs(np.asarray(a) - np.asarray(b)).max() / max(np.abs(b).max(), 1e-300))
+
+
+@pytest.mark.parametrize("kinds", [(I, I, P, P), (I, I, D, D), (P, P, P, P), (D, D, D, D),
+                                   (P, P, I, D), (D, I, I, D)])
+def test_adjoint_gradients_match_oracle(kinds):
+    steps, ckpt, q = 60, 7, 16              # ragged last segment (60 = 8*7 + 4)
+    mfp, dT0, probe, tw = _case(kinds)
+    J, g_mfp, g_tw, g_dT0 = _gpu(kinds, mfp, dT0, probe, tw, steps, ckpt, q)
+    ref = _oracle(kinds, mfp, dT0, probe, tw, steps, q)
+    assert abs(J - ref["J"]) <= 1e-5
+    assert _rel(g_mfp, ref["dJ_dmfp"]) <= TOL
+    assert _rel(g_dT0, ref["dJ_ddT0"]) <= TOL
+    iso = [k for k in range(4) if kinds[k] == I]
+    if iso:
+        assert _rel(g_tw[iso], ref["dJ_dTwall"][iso]) <= TOL
+    assert np.all(g_tw[[k for k in range(4) if kinds[k] != I]] == 0.0)
+
+
+def test_adjoint_uniform_mfp_and_register_variant():
+    kinds = (I, I, P, P)
+    _, dT0, probe, tw = _case(kinds, nx=33, ny=12, q=24)
+    J, g_mfp, g_tw, g_dT0 = _gpu(kinds, None, dT0, probe, tw, 45, 10, 24, mfp_uniform=2.2,
+                                 variant=0)
+    ref = _oracle(kinds, None, dT0, probe, tw, 45, 24, mfp_uniform=2.2)
+    assert _rel(g_mfp, ref["dJ_dmfp"]) <= TOL
+    assert _rel(g_dT0, ref["dJ_ddT0"]) <= TOL
+    assert _rel(g_tw[:2], ref["dJ_dTwall"][:2]) <= TOL
+
+
+def test_autograd_function_matches_direct_backward():
+    import torch
+    from paper_1911_00180_gb300.autograd import wlbm_run
+    kinds = (I, I, P, P)
+    mfp, dT0, probe, tw = _case(kinds, nx=20, ny=14)
+    spec = dict(nx=20, ny=14, q=16, bc=kinds, steps=30, ckpt=8)
+    m = torch.tensor(mfp, device="cuda", requires_grad=True)
+    t = torch.tensor(tw, dtype=torch.float64, device="cuda", requires_grad=True)
+    d0 = torch.tensor(dT0, device="cuda", requires_grad=True)
+    out = wlbm_run(m, t, d0, spec)
+    J = out[torch.as_tensor(probe, device="cuda")].mean()
+    J.backward()
+    ref = _oracle(kinds, mfp, dT0, probe, tw, 30, 16)
+    assert _rel(m.grad.double().cpu().numpy(), ref["dJ_dmfp"]) <= TOL
+    assert _rel(d0.grad.double().cpu().numpy(), ref["dJ_ddT0"]) <= TOL
+    assert _rel(t.grad.cpu().numpy()[:2], ref["dJ_dTwall"][:2]) <= TOL
+
+
+def test_adjoint_directional_derivative_mid_size():
+    """256 x 192, Q = 32, 200 steps: <dJ/d dT0, v> against a central difference of the GPU
+    forward along a smooth direction v (a property that holds at any size)."""
+    import torch
+    import paper_1911_00180_gb300 as wl
+    nx, ny, q, steps = 256, 192, 32, 200
+    kinds = (I, I, P, P)
+    mfp = W.lognormal_mfp(nx, ny, seed=7, corr=16.0)
+    dT0 = W.gaussian_field(nx, ny, [(128.0, 96.0)], [24.0], [1.0], periodic=False).astype(np.float32)
+    v = W.gaussian_field(nx, ny, [(100.0, 80.0)], [30.0], [1.0], periodic=False).astype(np.float32)
+    probe = np.zeros((ny, nx), bool)
+    probe[:, 192] = True
+    tw = (300.0,) * 4
+
+    def J_of(d):
+        h = wl.WormLBM(nx, ny, q, mfp_field=mfp, bc=kinds, t_wall=tw, theta=THETA)
+        h.wlbm_init_temperature(d)
+        h.wlbm_step(steps)
+        dT, _, _ = h.wlbm_moments(want_q=False)
+        val = float(dT.double().cpu().numpy()[probe].mean())
+        h.close()
+        return val
+    h = wl.WormLBM(nx, ny, q, mfp_field=mfp, bc=kinds, t_wall=tw, theta=THETA)
+    h.wlbm_adjoint_forward(dT0, steps, 25)
+    g = torch.as_tensor(probe.astype(np.float32) / probe.sum(), device="cuda")
+    _, _, g_dT0 = h.wlbm_adjoint_backward(g, want_mfp=False)
+    ad = float((g_dT0.double().cpu().numpy() * v).sum())
+    h.close()
+    eps = 0.05
+    fd = (J_of(dT0 + eps * v) - J_of(dT0 - eps * v)) / (2 * eps)
+    assert ad == pytest.approx(fd, rel=2e-3)

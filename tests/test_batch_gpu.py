@@ -1,0 +1,103 @@
+"""Batched launches: a batch of uneven grids (different sizes, Q, walls, MFP fields)
+stepped by one wall launch and one step launch per step must give, bit for bit, the
+states of the same grids stepped one by one (same tile code, same arithmetic), for both
+step-kernel variants, with and without CUDA-graph replay, in float32 and bfloat16."""
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+P, I, A = W.PERIODIC, W.ISOTHERMAL, W.ADIABATIC_DIFFUSE
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1911_00180_gb300  # noqa: F401
+
+
+def _specs():
+    return [
+        dict(nx=150, ny=21, q=32, bc=(I, I, A, A), t_wall=(301.0, 300.0, 300.0, 300.0), mfp=4.0),
+        dict(nx=47, ny=33, q=16, bc=(A, A, A, A), t_wall=(300.0,) * 4, mfp=2.5),
+        dict(nx=64, ny=40, q=24, bc=(P, P, P, P), t_wall=(300.0,) * 4, mfp=8.0),
+        dict(nx=90, ny=17, q=8, bc=(I, I, P, P), t_wall=(300.4, 299.8, 300.0, 300.0),
+             mfp_field=W.lognormal_mfp(90, 17, seed=3, corr=4.0)),
+        dict(nx=33, ny=260, q=64, bc=(P, P, I, A), t_wall=(300.0, 300.0, 300.7, 300.0), mfp=30.0),
+    ]
+
+
+def _dTs(specs):
+    return [W.random_dT(s["nx"], s["ny"], seed=11 + k, scale=0.5) for k, s in enumerate(specs)]
+
+
+def _single(spec, dT, steps, storage, fuse=0):
+    import paper_1911_00180_gb300 as wl
+    h = wl.WormLBM(spec["nx"], spec["ny"], spec["q"], mfp=spec.get("mfp"),
+                   mfp_field=spec.get("mfp_field"), bc=spec["bc"], t_wall=spec["t_wall"],
+                   storage=storage)
+    h.wlbm_set_option(wl.wlbm.OPT_FUSE_PERIODIC, fuse)
+    h.wlbm_init_temperature(dT)
+    h.wlbm_step(steps)
+    st = h.wlbm_get_state().cpu().numpy()
+    h.close()
+    return st
+
+
+@pytest.mark.parametrize("storage", [0, 1])
+@pytest.mark.parametrize("variant,graph,fuse", [(1, 0, 0), (0, 0, 0), (1, 12, 0), (0, 12, 0),
+                                                (1, 0, 1), (1, 12, 1)])
+def test_batch_equals_single_grids_bitwise(storage, variant, graph, fuse):
+    """37 steps = three 12-step graph replays and one single step; the second call starts
+    the graph chunks on another energy-plane phase (a second captured graph)."""
+    import paper_1911_00180_gb300 as wl
+    specs = _specs()
+    dTs = _dTs(specs)
+    b = wl.WormLBMBatch(specs, storage=storage)
+    b.wlbm_batch_set_option(wl.wlbm.OPT_STEP_VARIANT, variant)
+    b.wlbm_batch_set_option(wl.wlbm.OPT_GRAPH_STEPS, graph)
+    b.wlbm_batch_set_option(wl.wlbm.OPT_FUSE_PERIODIC, fuse)
+    b.wlbm_batch_init_temperature(dTs)
+    b.wlbm_batch_step(37)
+    b.wlbm_batch_step(24)
+    got = [v.wlbm_get_state().cpu().numpy() for v in b.instances]
+    b.close()
+    for k, (spec, dT) in enumerate(zip(specs, dTs)):
+        want = _single(spec, dT, 61, storage, fuse)
+        assert np.array_equal(got[k], want), k
+
+
+def test_batch_autotune_then_run():
+    import paper_1911_00180_gb300 as wl
+    from paper_1911_00180_gb300 import autotune
+    specs = _specs()
+    dTs = _dTs(specs)
+    b = wl.WormLBMBatch(specs, storage=1)
+    rec = autotune.tune_batch(b, 1, trial_steps=12, use_cache=False)
+    assert rec["variant"] in (0, 1) and rec["graph_steps"] in (0, 12)
+    b.wlbm_batch_init_temperature(dTs)
+    b.wlbm_batch_step(20)
+    got = [v.wlbm_get_state().cpu().numpy() for v in b.instances]
+    b.close()
+    for k, (spec, dT) in enumerate(zip(specs, dTs)):
+        assert np.array_equal(got[k], _single(spec, dT, 20, 1)), k
+
+
+def test_single_grid_autotune_keeps_results():
+    """The single-grid tuner picks among three step kernels and graph replay; the pick
+    changes no bit of the result."""
+    import paper_1911_00180_gb300 as wl
+    spec = _specs()[0]
+    dT = _dTs([spec])[0]
+    h = wl.WormLBM(spec["nx"], spec["ny"], spec["q"], mfp=spec.get("mfp"), bc=spec["bc"],
+                   t_wall=spec["t_wall"], storage=1)
+    v, g, ms = h.wlbm_autotune(12)
+    assert v in (0, 1, 2) and g in (0, 12) and ms > 0
+    h.wlbm_init_temperature(dT)
+    h.wlbm_step(30)
+    got = h.wlbm_get_state().cpu().numpy()
+    h.close()
+    assert np.array_equal(got, _single(spec, dT, 30, 1))
