@@ -429,8 +429,8 @@ def main():
                        "nx": cfg["nx"], "ny": cfg["ny"], "q": cfg["q"],
                        "mfp_cells": cfg["mfp"], "parallelism": "replicas x%d" % world,
                        "step_kernel": {0: "register-pipelined", 1: "bulk-copy ring",
-                                       2: "warp-specialised"}[1 if args.variant is None
-                                                               else args.variant],
+                                       2: "warp-specialised", 3: "TMA tiles"}[
+                                           1 if args.variant is None else args.variant],
                        "l2": "state %.2f GB > L2 (no flush needed)"
                              % (2 * cfg["q"] * cells * (4 if args.storage == "fp32" else 2) / 1e9)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

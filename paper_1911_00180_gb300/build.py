@@ -16,7 +16,8 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIBDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIBDIR, "libwlbm.so")
-SOURCES = ["lattice.cpp", "wlbm_api.cu", "k_step.cu", "k_aux.cu", "k_adjoint.cu", "noalloc.cu"]
+SOURCES = ["lattice.cpp", "wlbm_api.cu", "k_step.cu", "k_step_tma.cu", "k_aux.cu", "k_adjoint.cu",
+           "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",
          "-I" + os.path.join(PKG, "..", "include")]

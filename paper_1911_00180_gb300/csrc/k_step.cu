@@ -15,6 +15,7 @@
 // without bank conflicts.  A paused plane is updated in place (its source is its own
 // cell), which is why every plane carries its own buffer parity in the step code.
 #include "elem.cuh"
+#include "mbar.cuh"
 #include "wlbm_internal.hpp"
 
 namespace wlbm {
@@ -23,14 +24,6 @@ namespace {
 
 constexpr int kTY = kStepRows;   // rows (warps) per block
 
-__device__ __forceinline__ float uniform_w(const StepArgs& a, int r, int c) {
-  if (r < 1 || r > a.ny + 2 || c < kGhostCol || c > kX0 + a.nx) return 0.f;  // pads
-  const bool gx = (c == kGhostCol) || (c == kX0 + a.nx);
-  const bool gy = (r == 1) || (r == a.ny + 2);
-  if (gx && !a.xper) return 0.f;   // wall cells do not scatter
-  if (gy && !a.yper) return 0.f;
-  return a.w0;
-}
 
 // Shared-memory layout of the register-pipelined variant (one static buffer per kernel).
 template <int CPT, bool REF>
@@ -221,49 +214,6 @@ __global__ void __launch_bounds__(32 * kTY, 4) k_step(const StepArgs a) {
 // -1, 0, +1.  Every mbarrier wait is bounded in time; on expiry the kernel sets bit 0 of
 // the status word, waits (bounded) for its own copies still in flight and returns.
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
-               : "memory");
-}
-
-__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes,
-                                          uint64_t* bar) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-               "r"(bytes)
-               : "memory");
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
-          "r"(smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar))
-      : "memory");
-}
-
-__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Wait for the phase of the given parity to complete, at most ~`limit` clock cycles.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long limit) {
-  if (mbar_test(bar, parity)) return true;
-  const long long t0 = clock64();
-  while (!mbar_test(bar, parity)) {
-    if (clock64() - t0 > limit) return false;
-  }
-  return true;
-}
-
-constexpr long long kWaitCycles = 4000000000LL;   // about two seconds at GB300 clocks
 
 // Shared-memory layout of the bulk variant (dynamic shared memory, 128-byte aligned).
 template <typename T, int CPT, int S, bool REF>
@@ -554,24 +504,8 @@ struct WsLayout {
   static_assert(kBytes % 16 == 0, "bulk copies move multiples of 16 bytes");
 };
 
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
 
-__device__ __forceinline__ void mbar_expect(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-               "r"(bytes)
-               : "memory");
-}
 
-__device__ __forceinline__ void bulk_copy(void* dst, const void* src, uint32_t bytes,
-                                          uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
-          "r"(smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar))
-      : "memory");
-}
 
 template <typename T, int CPT, int S, bool FIELD_W, bool REF, bool WRAP>
 __device__ __forceinline__ void step_ws_tile(const StepArgs& a, int bx, int by,
@@ -919,15 +853,19 @@ cudaError_t prepare_step_kernels() {
   if (e == cudaSuccess) e = configure_bulk_batch<float, 4, 6, false>();
   if (e == cudaSuccess) e = configure_ws<__nv_bfloat16, 8, 8, true>();
   if (e == cudaSuccess) e = configure_ws<float, 4, 8, false>();
+  if (e == cudaSuccess) e = configure_step_tma();
   return e;
 }
 
 cudaError_t launch_step(int storage, const StepArgs& a, cudaStream_t s) {
+  // variant 3 covers plain steps (no fused periodic mirrors, no adjoint tape) of grids
+  // that have a tensor map; the others run variant 1
+  if (a.variant == 3 && !a.wrap && !a.tape && a.tmap) return launch_step_tma(storage, a, s);
   if (a.variant == 2) {
     if (storage == WLBM_STORE_BF16_DEV) return launch_ws<__nv_bfloat16, 8, 8, true>(a, s);
     return launch_ws<float, 4, 8, false>(a, s);
   }
-  if (a.variant == 1) {
+  if (a.variant == 1 || a.variant == 3) {
     if (storage == WLBM_STORE_BF16_DEV) return launch_bulk<__nv_bfloat16, 8, 6, true>(a, s);
     return launch_bulk<float, 4, 6, false>(a, s);
   }

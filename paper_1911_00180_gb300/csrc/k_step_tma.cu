@@ -1,0 +1,395 @@
+// Step kernel variant 3: tensor-memory-access (TMA) tiles, register-resident cell data.
+//
+// Same update as the other step kernels (Eq. lbm-energy with the due worm hop c of each
+// direction, Eq. worm-paths; E' = sum_i d_i', Eq. lbm-energy-density), organised so that
+// the per-element work is a handful of instructions:
+//   * one producer thread per block issues, for direction i, ONE tiled 3-D tensor copy of
+//     the shifted source box (7 rows x 128 + 2V columns of plane par*q + i) into a stage
+//     of a shared-memory ring; full/empty mbarriers pair it with 7 consumer warps (a block
+//     is 8 warps, so two blocks of up to 128 registers a thread fit on an SM);
+//   * a consumer lane owns 4 consecutive cells of one row and keeps 1 - W, the scattered
+//     energy W E (and, for bfloat16, the reference term) of the 3 x 6 cells around them in
+//     registers, loaded once per step;
+//   * the direction's hop selects one of 16 specialised bodies (8 hops x paused or not),
+//     so every neighbour index is a compile-time register, source values arrive with one
+//     or two vector shared-memory loads, and results leave with one 8- or 16-byte
+//     streaming store per lane.
+// Edge groups (columns past the right ghost) store element by element, so pad columns
+// stay zero.  Fully periodic grids with fused mirrors and the adjoint's tape mode are
+// served by variant 1 (the dispatcher routes them there).
+#include <cuda.h>
+
+#include "elem.cuh"
+#include "mbar.cuh"
+#include "wlbm_internal.hpp"
+
+namespace wlbm {
+
+namespace {
+
+constexpr int kTY3 = 7;           // consumer warps (rows) per block; + 1 producer warp
+constexpr int kCPT3 = 4;          // consecutive cells per lane
+constexpr int kTW3 = 32 * kCPT3;  // tile width
+
+// Per-direction record built once per block (16 bytes, one shared-memory vector load).
+struct alignas(16) Dir3 {
+  int64_t dst_off;   // element offset of the destination plane
+  float wi;          // angular weight w_i
+  uint16_t z;        // source plane index par*q + i (tensor-map z coordinate)
+  uint8_t kase;      // hop | paused << 3
+  int8_t dy;         // source row shift of the box (0 when paused)
+};
+
+template <typename T, int S>
+struct TmaLayout {
+  static constexpr int V = 16 / int(sizeof(T));          // elements per 16 bytes
+  static constexpr int BW = kTW3 + 2 * V;                // box width: columns col0-V ..
+  static constexpr int kBoxElems = BW * kTY3;
+  static constexpr uint32_t kBoxBytes = uint32_t(kBoxElems) * sizeof(T);
+  static constexpr size_t kStage = (size_t(kBoxBytes) + 127) / 128 * 128;   // aligned stride
+  static constexpr size_t off_bar = size_t(S) * kStage;
+  static constexpr size_t off_table = off_bar + ((2 * S * 8 + 127) / 128) * 128;
+  static size_t bytes(int q) { return off_table + size_t(q) * sizeof(Dir3); }
+};
+
+__device__ __forceinline__ float bf_lo(uint32_t w) { return __uint_as_float(w << 16); }
+__device__ __forceinline__ float bf_hi(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
+
+
+// Register tile of one lane: rows r-1, r, r+1 (index 0..2) and columns c0-1 .. c0+4
+// (index 0..5) around its cells c0 .. c0+3.
+struct Regs3 {
+  float G[3][6];   // 1 - W
+  float F[3][6];   // W E (bfloat16: W E / scale)
+  float R[3][6];   // bfloat16 only: ((1 - W) E_ref + W E) / scale
+  float eins[4];   // bfloat16 only: E_in / scale of the lane's own cells
+  float acc[4];    // sum over directions of the stored new values
+};
+
+// Source values of the 4 cells for a DDED shift DX (-1, 0, +1) from the ring row.
+template <typename T, int DX>
+__device__ __forceinline__ void ring_values(const T* row, int lane, float (&v)[4]) {
+  constexpr int V = 16 / int(sizeof(T));
+  if constexpr (sizeof(T) == 4) {
+    const float* p = reinterpret_cast<const float*>(row) + V + 4 * lane;   // 16-byte aligned
+    const float4 q = *reinterpret_cast<const float4*>(p);
+    if constexpr (DX == 0) {
+      v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+    } else if constexpr (DX < 0) {
+      v[0] = p[-1]; v[1] = q.x; v[2] = q.y; v[3] = q.z;
+    } else {
+      v[0] = q.y; v[1] = q.z; v[2] = q.w; v[3] = p[4];
+    }
+  } else {
+    const uint32_t* p = reinterpret_cast<const uint32_t*>(row) + (V + 4 * lane) / 2;  // 8 B
+    const uint2 q = *reinterpret_cast<const uint2*>(p);
+    if constexpr (DX == 0) {
+      v[0] = bf_lo(q.x); v[1] = bf_hi(q.x); v[2] = bf_lo(q.y); v[3] = bf_hi(q.y);
+    } else if constexpr (DX < 0) {
+      v[0] = bf_hi(p[-1]); v[1] = bf_lo(q.x); v[2] = bf_hi(q.x); v[3] = bf_lo(q.y);
+    } else {
+      v[0] = bf_hi(q.x); v[1] = bf_lo(q.y); v[2] = bf_hi(q.y); v[3] = bf_lo(p[2]);
+    }
+  }
+}
+
+// Store the 4 new values (nvalid of them when the group crosses the right edge) and
+// return what was stored (bfloat16: the rounded values).
+template <typename T>
+__device__ __forceinline__ void store4(T* dst, const float (&o)[4], int nvalid, float (&s)[4]) {
+  if constexpr (sizeof(T) == 4) {
+    if (nvalid == 4) {
+      __stcs(reinterpret_cast<float4*>(dst), make_float4(o[0], o[1], o[2], o[3]));
+    } else {
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (j < nvalid) __stcs(reinterpret_cast<float*>(dst) + j, o[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) s[j] = o[j];
+  } else {
+    const __nv_bfloat162 p0 = __floats2bfloat162_rn(o[0], o[1]);
+    const __nv_bfloat162 p1 = __floats2bfloat162_rn(o[2], o[3]);
+    const uint32_t w0 = *reinterpret_cast<const uint32_t*>(&p0);
+    const uint32_t w1 = *reinterpret_cast<const uint32_t*>(&p1);
+    if (nvalid == 4) {
+      __stcs(reinterpret_cast<uint2*>(dst), make_uint2(w0, w1));
+    } else {
+      unsigned short* d = reinterpret_cast<unsigned short*>(dst);
+      const unsigned short h[4] = {static_cast<unsigned short>(w0 & 0xffffu),
+                                   static_cast<unsigned short>(w0 >> 16),
+                                   static_cast<unsigned short>(w1 & 0xffffu),
+                                   static_cast<unsigned short>(w1 >> 16)};
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (j < nvalid) __stcs(d + j, h[j]);
+    }
+    s[0] = bf_lo(w0); s[1] = bf_hi(w0); s[2] = bf_lo(w1); s[3] = bf_hi(w1);
+  }
+}
+
+// One direction for the lane's 4 cells; hop (CX, CY), paused or propagating.
+template <typename T, bool REF, int CX, int CY, bool PAUSED>
+__device__ __forceinline__ void dir_body(Regs3& t, const T* ring_row, int lane, T* dst, float wi,
+                                         int nvalid) {
+  constexpr int DX = PAUSED ? 0 : -CX;
+  constexpr int SR = PAUSED ? 1 : 1 - CY;   // tile row of the DDED source
+  constexpr int SC = PAUSED ? 1 : 1 - CX;   // tile column of the DDED source of cell 0
+  constexpr int FR = 1 - CY, FC = 1 - CX;   // EED source (y - c) of cell 0
+  float v[4], o[4], s[4];
+  ring_values<T, DX>(ring_row, lane, v);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    if constexpr (REF) {
+      // stored v' = (d' - w_i E_in(y)) / scale, d' from Eq. lbm-energy with the local
+      // reference R of the stored source value (see the bfloat16 storage note)
+      const float tt = PAUSED ? __fadd_rn(__fsub_rn(t.R[1][1 + j], t.F[1][1 + j]),
+                                          t.F[FR][FC + j])
+                              : t.R[SR][SC + j];
+      o[j] = fmaf(t.G[SR][SC + j], v[j], __fmul_rn(wi, __fsub_rn(tt, t.eins[j])));
+    } else {
+      o[j] = fmaf(t.G[SR][SC + j], v[j], __fmul_rn(wi, t.F[FR][FC + j]));
+    }
+  }
+  store4<T>(dst, o, nvalid, s);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) t.acc[j] += s[j];
+}
+
+// kase = hop | paused << 3; hop numbering of the host lattice:
+// (1,0) (0,1) (-1,0) (0,-1) (1,1) (-1,1) (-1,-1) (1,-1)
+template <typename T, bool REF>
+__device__ __forceinline__ void dir_kase(int kase, Regs3& t, const T* ring_row, int lane, T* dst,
+                                         float wi, int nvalid) {
+  switch (kase) {
+    case 0: dir_body<T, REF, 1, 0, false>(t, ring_row, lane, dst, wi, nvalid); break;
+    case 1: dir_body<T, REF, 0, 1, false>(t, ring_row, lane, dst, wi, nvalid); break;
+    case 2: dir_body<T, REF, -1, 0, false>(t, ring_row, lane, dst, wi, nvalid); break;
+    case 3: dir_body<T, REF, 0, -1, false>(t, ring_row, lane, dst, wi, nvalid); break;
+    case 4: dir_body<T, REF, 1, 1, false>(t, ring_row, lane, dst, wi, nvalid); break;
+    case 5: dir_body<T, REF, -1, 1, false>(t, ring_row, lane, dst, wi, nvalid); break;
+    case 6: dir_body<T, REF, -1, -1, false>(t, ring_row, lane, dst, wi, nvalid); break;
+    case 7: dir_body<T, REF, 1, -1, false>(t, ring_row, lane, dst, wi, nvalid); break;
+    case 8: dir_body<T, REF, 1, 0, true>(t, ring_row, lane, dst, wi, nvalid); break;
+    case 9: dir_body<T, REF, 0, 1, true>(t, ring_row, lane, dst, wi, nvalid); break;
+    case 10: dir_body<T, REF, -1, 0, true>(t, ring_row, lane, dst, wi, nvalid); break;
+    case 11: dir_body<T, REF, 0, -1, true>(t, ring_row, lane, dst, wi, nvalid); break;
+    case 12: dir_body<T, REF, 1, 1, true>(t, ring_row, lane, dst, wi, nvalid); break;
+    case 13: dir_body<T, REF, -1, 1, true>(t, ring_row, lane, dst, wi, nvalid); break;
+    case 14: dir_body<T, REF, -1, -1, true>(t, ring_row, lane, dst, wi, nvalid); break;
+    default: dir_body<T, REF, 1, -1, true>(t, ring_row, lane, dst, wi, nvalid); break;
+  }
+}
+
+template <typename T, int S, bool FIELD_W, bool REF>
+__global__ void __maxnreg__(128)
+    k_step_tma(const StepArgs a, const __grid_constant__ CUtensorMap tmap) {
+  using LY = TmaLayout<T, S>;
+  constexpr int V = LY::V, BW = LY::BW;
+  extern __shared__ __align__(128) unsigned char smem[];
+  // smem: S ring stages of [kTY3][BW] elements (stride kStage), then the barriers
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + LY::off_bar);      // [S]
+  uint64_t* empty = full + S;                                            // [S]
+  Dir3* table = reinterpret_cast<Dir3*>(smem + LY::off_table);           // [q]
+
+  const int lane = threadIdx.x, ty = threadIdx.y;
+  const int tid = ty * 32 + lane, nthr = 32 * (kTY3 + 1);
+  const int col0 = kGhostCol + int(blockIdx.x) * kTW3;
+  const int row0 = 1 + int(blockIdx.y) * kTY3;
+  const int nrows = min(kTY3, a.ny + 2 - row0 + 1);   // rows row0 .. ny+2 are computed
+
+  for (int i = tid; i < a.q; i += nthr) {
+    const int code = a.codes[i];
+    const int hop = code & 7, paused = (code >> 3) & 1, par = (code >> 4) & 1;
+    Dir3 d;
+    d.dst_off = int64_t((paused ? par : 1 - par) * a.q + i) * a.plane;
+    d.wi = a.w[i];
+    d.z = uint16_t(par * a.q + i);
+    d.kase = uint8_t(hop | (paused << 3));
+    d.dy = int8_t(paused ? 0 : -c_hop_y[hop]);
+    table[i] = d;
+  }
+  if (tid == 0) {
+    for (int st = 0; st < S; ++st) {
+      mbar_init(&full[st], 1);
+      mbar_init(&empty[st], nrows > 0 ? nrows : 1);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (nrows <= 0) return;
+
+  if (ty == kTY3) {
+    // ------------------------------------------------------------- producer thread
+    if (lane != 0) return;
+    for (int i = 0; i < a.q; ++i) {
+      const int st = i % S, k = i / S;
+      if (k > 0 && !mbar_wait(&empty[st], uint32_t(k - 1) & 1u, kWaitCycles)) {
+        atomicOr(a.status, 1);
+        for (int j = (i > S ? i - S : 0); j < i; ++j)   // copies still in flight
+          mbar_wait(&full[j % S], uint32_t(j / S) & 1u, kWaitCycles);
+        return;
+      }
+      const Dir3 d = table[i];
+      mbar_expect(&full[st], LY::kBoxBytes);
+      tma_load_3d(smem + st * LY::kStage, &tmap, col0 - V, row0 + d.dy, int(d.z), &full[st]);
+    }
+    return;
+  }
+
+  // ---------------------------------------------------------------- consumer warps
+  const int r = row0 + ty;
+  if (ty >= nrows) return;
+  const int c0 = col0 + 4 * lane;
+  const int nvalid = max(0, min(4, kX0 + a.nx - c0 + 1));   // cells c0.. up to the ghost
+  Regs3 t;
+#pragma unroll
+  for (int rr = 0; rr < 3; ++rr) {
+    const int row = r - 1 + rr;                 // 0 <= row < rows for computed rows
+#pragma unroll
+    for (int cc = 0; cc < 6; ++cc) {
+      const int c = c0 - 1 + cc;
+      float wv = 0.f, ev = 0.f, rv = 0.f;
+      if (c < a.pitch) {
+        const int64_t o = int64_t(row) * a.pitch + c;
+        ev = a.e_in[o];
+        wv = FIELD_W ? a.wfield[o] : uniform_w(a, row, c);
+        if (REF) rv = a.e_ref[o];
+      }
+      const float fv = __fmul_rn(wv, ev), gv = __fsub_rn(1.f, wv);
+      t.G[rr][cc] = gv;
+      if (REF) {
+        t.F[rr][cc] = __fmul_rn(fv, a.inv_scale);
+        t.R[rr][cc] = __fmul_rn(fmaf(gv, rv, fv), a.inv_scale);
+      } else {
+        t.F[rr][cc] = fv;
+        t.R[rr][cc] = 0.f;
+      }
+      if (rr == 1 && cc >= 1 && cc <= 4)
+        t.eins[cc - 1] = REF && cc - 1 < nvalid ? __fmul_rn(ev, a.inv_scale) : 0.f;
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) t.acc[j] = 0.f;
+  float accw = 0.f;
+  T* obase = static_cast<T*>(a.planes) + int64_t(r) * a.pitch + c0;
+
+  for (int i = 0; i < a.q; ++i) {
+    const int st = i % S;
+    if (!mbar_wait(&full[st], uint32_t(i / S) & 1u, kWaitCycles)) {
+      if (lane == 0) atomicOr(a.status, 1);
+      return;
+    }
+    const Dir3 d = table[i];
+    const T* ring_row = reinterpret_cast<const T*>(smem + st * LY::kStage) + ty * BW;
+    T* dst = obase + d.dst_off;
+    if (REF) accw += d.wi;
+    if (nvalid > 0) dir_kase<T, REF>(d.kase, t, ring_row, lane, dst, d.wi, nvalid);
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[st]);
+  }
+  // E'(y) = sum_i d_i'(y) (Eq. lbm-energy-density); bfloat16: d' = scale v' + w_i E_in(y)
+  const int64_t own = int64_t(r) * a.pitch + c0;
+  float eo[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const float ein = REF && j < nvalid ? a.e_in[own + j] : 0.f;
+    eo[j] = REF ? fmaf(t.acc[j], a.scale, __fmul_rn(ein, accw)) : t.acc[j];
+  }
+  float* e_out = a.e_out + own;
+  if (nvalid == 4) {
+    *reinterpret_cast<float4*>(e_out) = make_float4(eo[0], eo[1], eo[2], eo[3]);
+  } else {
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (j < nvalid) e_out[j] = eo[j];
+  }
+}
+
+template <typename T, int S>
+cudaError_t configure_tma_t() {
+  const int bytes = int(TmaLayout<T, S>::bytes(kMaxQ));
+  const void* fns[2] = {(const void*)k_step_tma<T, S, false, sizeof(T) == 2>,
+                        (const void*)k_step_tma<T, S, true, sizeof(T) == 2>};
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+    e = cudaFuncSetAttribute(fns[k], cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    // several blocks per SM: ask for the largest shared-memory carveout
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(fns[k], cudaFuncAttributePreferredSharedMemoryCarveout,
+                               int(cudaSharedmemCarveoutMaxShared));
+  }
+  return e;
+}
+
+template <typename T, int S>
+cudaError_t launch_tma_t(const StepArgs& a, const CUtensorMap& tm, cudaStream_t s) {
+  using LY = TmaLayout<T, S>;
+  const dim3 block(32, kTY3 + 1);
+  const dim3 grid((a.nx + 2 + kTW3 - 1) / kTW3, (a.ny + 2 + kTY3 - 1) / kTY3);
+  const size_t bytes = LY::bytes(a.q);
+  constexpr bool REF = sizeof(T) == 2;
+  if (a.wfield) k_step_tma<T, S, true, REF><<<grid, block, bytes, s>>>(a, tm);
+  else k_step_tma<T, S, false, REF><<<grid, block, bytes, s>>>(a, tm);
+  return cudaGetLastError();
+}
+
+constexpr int kStagesF32 = 8;    // 8 x 4352 B of boxes in flight per block
+constexpr int kStagesBF16 = 16;  // 16 x 2304 B
+
+}  // namespace
+
+cudaError_t configure_step_tma() {
+  cudaError_t e = configure_tma_t<float, kStagesF32>();
+  if (e == cudaSuccess) e = configure_tma_t<__nv_bfloat16, kStagesBF16>();
+  return e;
+}
+
+cudaError_t launch_step_tma(int storage, const StepArgs& a, cudaStream_t s) {
+  const CUtensorMap& tm = *static_cast<const CUtensorMap*>(a.tmap);
+  if (storage == WLBM_STORE_BF16_DEV) return launch_tma_t<__nv_bfloat16, kStagesBF16>(a, tm, s);
+  return launch_tma_t<float, kStagesF32>(a, tm, s);
+}
+
+// Tensor map of the 2q direction planes as a 3-D tensor (columns, rows, planes) with the
+// box of one TMA stage.  The encoder comes from the driver through the runtime's entry
+// point query, so the library does not link the driver library directly.
+bool make_plane_tensor_map(void* out, void* planes, int storage, const Geom& g,
+                           std::string* why) {
+  using Encode = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                              const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                              const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                              CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+  static Encode encode = nullptr;
+  if (!encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn) {
+      cudaGetLastError();
+      *why = "cuTensorMapEncodeTiled is not available from the driver";
+      return false;
+    }
+    encode = reinterpret_cast<Encode>(fn);
+  }
+  const bool bf = storage == WLBM_STORE_BF16_DEV;
+  const cuuint64_t es = bf ? 2 : 4;
+  const cuuint32_t V = cuuint32_t(16 / es);
+  const cuuint64_t dims[3] = {cuuint64_t(g.pitch), cuuint64_t(g.rows), cuuint64_t(2 * g.q)};
+  const cuuint64_t strides[2] = {cuuint64_t(g.pitch) * es, cuuint64_t(g.plane) * es};
+  const cuuint32_t box[3] = {cuuint32_t(kTW3) + 2 * V, cuuint32_t(kTY3), 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  const CUresult r = encode(static_cast<CUtensorMap*>(out),
+                            bf ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                            3, planes, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    *why = "cuTensorMapEncodeTiled failed with code " + std::to_string(int(r));
+    return false;
+  }
+  return true;
+}
+
+}  // namespace wlbm

@@ -52,7 +52,11 @@ struct wlbm_handle {
   uint8_t* d_codes = nullptr; // [kChunk][q]
   double* d_red = nullptr;    // [4]
   int* d_status = nullptr;    // bit 0: a bounded device wait gave up
-  int step_variant = 1;       // 0 register-pipelined, 1 per-warp bulk-copy ring
+  int step_variant = 1;       // 0 register-pipelined, 1 per-warp bulk-copy ring,
+                              // 2 warp-specialised ring, 3 TMA tiles
+  alignas(64) unsigned char tmap[128] = {};   // CUtensorMap of the planes (variant 3)
+  bool has_tmap = false;
+  std::string tmap_why;       // why there is no tensor map
   int graph_steps = 0;        // >0: replay chunks of this many steps as one CUDA graph
   int fuse_periodic = 0;      // 1: both axes periodic, the step kernel mirrors the edges
   cudaGraphExec_t graphs[3] = {nullptr, nullptr, nullptr};   // per energy-plane role
@@ -417,6 +421,7 @@ wlbm_status wlbm_create(const wlbm_grid* grid, const float* mfp_cells, double mf
   h->d_codes = static_cast<uint8_t*>(h->dev_alloc(size_t(kChunk) * G.q));
   h->d_red = static_cast<double*>(h->dev_alloc(8 * sizeof(double)));
   h->d_status = static_cast<int*>(h->dev_alloc(256));
+  if (h->planes) h->has_tmap = make_plane_tensor_map(h->tmap, h->planes, h->storage, g, &h->tmap_why);
   if (h->field_w) h->wfield = static_cast<float*>(h->dev_alloc(size_t(g.plane) * 4));
   if (!h->planes || !h->e[0] || !h->e[1] || (n_e == 3 && !h->e[2]) || !h->consts ||
       !h->d_codes || !h->d_red || !h->d_status ||
@@ -542,6 +547,7 @@ static wlbm_status enqueue_steps(wlbm_handle* h, int count, bool profile) {
     sa.scale = h->scale; sa.inv_scale = h->inv_scale;
     sa.variant = h->step_variant; sa.status = h->d_status;
     sa.xper = h->xper; sa.yper = h->yper; sa.wrap = wrap;
+    sa.tmap = h->has_tmap ? h->tmap : nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (profile) {
       if (h->prof_used + 2 > h->prof_ev.size()) {
@@ -629,7 +635,10 @@ wlbm_status wlbm_step(wlbm_handle* h, int64_t n) {
 
 wlbm_status wlbm_set_option(wlbm_handle* h, int32_t key, int64_t value) {
   if (!h) return WLBM_ERR_INVALID_ARG;
-  if (key == WLBM_OPT_STEP_VARIANT && value >= 0 && value <= 2) {
+  if (key == WLBM_OPT_STEP_VARIANT && value == 3 && !h->has_tmap)
+    return h->fail(WLBM_ERR_INVALID_ARG, "wlbm_set_option: step variant 3 needs a tensor map of "
+                                         "the planes: " + h->tmap_why);
+  if (key == WLBM_OPT_STEP_VARIANT && value >= 0 && value <= 3) {
     h->step_variant = int(value);
     h->drop_graphs();
     return WLBM_OK;
@@ -1385,15 +1394,16 @@ wlbm_status wlbm_autotune(wlbm_handle* h, int32_t trial_steps, int32_t* variant,
                           int32_t* graph_steps, double* ms_per_step) {
   if (!h || trial_steps < 6) return WLBM_ERR_INVALID_ARG;
   const int g = std::min(kChunk, (trial_steps / 6) * 6);
-  const int cand[6][2] = {{1, 0}, {0, 0}, {2, 0}, {1, g}, {0, g}, {2, g}};
+  const int cand[8][2] = {{1, 0}, {0, 0}, {2, 0}, {3, 0}, {1, g}, {0, g}, {2, g}, {3, g}};
   double best = 1e300;
   int bv = 1, bg = 0;
   cudaEvent_t e0, e1;
   wlbm_status st = h->cuda(cudaEventCreate(&e0), "autotune");
   if (st != WLBM_OK) return st;
   st = h->cuda(cudaEventCreate(&e1), "autotune");
-  for (int c = 0; c < 6 && st == WLBM_OK; ++c) {
+  for (int c = 0; c < 8 && st == WLBM_OK; ++c) {
     if (cand[c][1] > 0 && !h->stream) continue;     // graphs need a capturable stream
+    if (cand[c][0] == 3 && !h->has_tmap) continue;
     st = wlbm_set_option(h, WLBM_OPT_STEP_VARIANT, cand[c][0]);
     if (st == WLBM_OK) st = wlbm_set_option(h, WLBM_OPT_GRAPH_STEPS, cand[c][1]);
     if (st == WLBM_OK) st = wlbm_step(h, g > 0 ? g : 6);

@@ -66,7 +66,23 @@ struct StepArgs {
   // also writes its new value (and E') into the ghost cells that mirror it, so the next
   // step needs no separate periodic pass
   int wrap;
+  // host pointer to the planes' CUtensorMap (128 bytes, variant 3), or nullptr; read by
+  // the launcher on the host, never by a kernel
+  const void* tmap;
 };
+
+#ifdef __CUDACC__
+// Uniform W_corr of a frame cell: w0 inside the frame, 0 on pads and on the ghost cells of
+// walls (wall cells do not scatter); periodic ghost cells carry w0.
+__device__ __forceinline__ float uniform_w(const StepArgs& a, int r, int c) {
+  if (r < 1 || r > a.ny + 2 || c < kGhostCol || c > kX0 + a.nx) return 0.f;  // pads
+  const bool gx = (c == kGhostCol) || (c == kX0 + a.nx);
+  const bool gy = (r == 1) || (r == a.ny + 2);
+  if (gx && !a.xper) return 0.f;
+  if (gy && !a.yper) return 0.f;
+  return a.w0;
+}
+#endif
 
 // Wall segment for the boundary kernel (one warp per ghost cell).
 struct WallSeg {
@@ -200,6 +216,12 @@ void set_global_error_msg(const std::string& m);
 // Kernel launchers (k_step.cu, k_aux.cu).  Return cudaGetLastError().
 cudaError_t launch_step(int storage, const StepArgs& a, cudaStream_t s);
 cudaError_t prepare_step_kernels();   // per-device kernel attributes; call before capture
+// Variant 3 (TMA tiles): kernel attributes, launch, and the planes' tensor map (written to
+// `out`, 128 bytes, 64-byte aligned; false with a reason when it cannot be made).
+cudaError_t configure_step_tma();
+cudaError_t launch_step_tma(int storage, const StepArgs& a, cudaStream_t s);
+bool make_plane_tensor_map(void* out, void* planes, int storage, const Geom& g,
+                           std::string* why);
 // Batched launches (one launch per step for all instances of a batch).
 int step_tile_width(int storage, int variant);
 cudaError_t launch_step_batch(int storage, int variant, const BatchInst* insts, int n,

@@ -6,11 +6,12 @@ float32 storage and 2e-3 for bfloat16 storage.  Per-direction state and heat flu
 relative to the largest initial per-direction deviation, 1e-5 for float32 storage.
 With bfloat16 storage every stored value carries a rounding of up to 2^-9 of its
 non-equilibrium part, several times over near walls (ghost values are re-stored by the
-wall pass and by the step), so those two are held to 1e-2: the state relative to the
-largest initial per-direction deviation, the heat flux relative to the larger of that
-and the flux's own amplitude (q is a weighted sum of stored values, so its rounding
-error scales with whichever of the two is larger).  The ballistic limit is exact (no
-arithmetic happens there)."""
+wall pass and by the step), so the state is held to 1e-2 of the largest initial
+per-direction deviation.  The heat flux q_x = sum_i s_ix d_i is a fixed linear map of
+the state, so that state bound implies |dq_x| <= 1e-2 * scale * sum_i |s_ix|, the bound
+q is held to; separately, the flux the library returns must equal the oracle's formula
+applied to the library's own state to 1e-5 of that scale (the moment kernel, free of the
+storage rounding).  The ballistic limit is exact (no arithmetic happens there)."""
 import math
 
 import numpy as np
@@ -48,7 +49,11 @@ def _compare(cfg, steps, storage=0, tol=TOL32, state_tol=None, variant=None):
     qx, qy = orc.heat_flux()
     qscale = dscale
     if storage == 1:
-        qscale = max(dscale, float(np.abs(qx).max()), float(np.abs(qy).max()))
+        qscale = dscale * float(max(np.abs(orc.s_hat[:, 0]).sum(), np.abs(orc.s_hat[:, 1]).sum()))
+        own = gpu["state"][:, 1:-1, 1:-1]
+        e_m = max(rel_linf(gpu["qx"], np.tensordot(orc.s_hat[:, 0], own, axes=(0, 0)), qscale),
+                  rel_linf(gpu["qy"], np.tensordot(orc.s_hat[:, 1], own, axes=(0, 0)), qscale))
+        assert e_m <= TOL32, ("q of own state", e_m)
     e_q = max(rel_linf(gpu["qx"], qx, qscale), rel_linf(gpu["qy"], qy, qscale))
     assert e_t <= tol, ("T", e_t)
     assert e_s <= (state_tol or tol), ("state", e_s)
@@ -65,12 +70,12 @@ def test_c1_gaussian_bf16_full_run():
     _compare(W.gaussian_c1(seed=1), 500, storage=1, tol=TOL16, state_tol=TOL16_STATE)
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
 @pytest.mark.parametrize("storage,tol,stol", [(0, TOL32, None), (1, TOL16, TOL16_STATE)])
 @pytest.mark.parametrize("kinds", [(P,) * 4, (I, I, A, A), (A, A, P, P)])
 def test_step_kernel_variants(variant, storage, tol, stol, kinds):
     """Every step-kernel variant (0 register-pipelined, 1 per-warp bulk rings, 2
-    warp-specialised) meets the parity tolerances."""
+    warp-specialised, 3 TMA tiles) meets the parity tolerances."""
     nx, ny, q = 141, 23, 32
     cfg = dict(nx=nx, ny=ny, q=q, mfp=2.5, bc=kinds, t_wall=(300.8, 300.0, 300.0, 300.0),
                emulate_3d=True, dT=W.gaussian_field(nx, ny, [(70.0, 11.0)], [6.0], [1.0])
@@ -88,7 +93,7 @@ def test_step_kernel_variants_bitwise_equal(storage, fuse):
     cfg = W.pulses_c2(seed=2, n=157, q=32, npulse=4)
     cfg["mfp"] = 5.0
     out = []
-    for variant in (0, 1, 2):
+    for variant in (0, 1, 2, 3):
         h = gpu_handle(cfg, storage, variant)
         h.wlbm_set_option(wl.wlbm.OPT_FUSE_PERIODIC, fuse)
         h.wlbm_init_temperature(cfg["dT"])
@@ -96,7 +101,24 @@ def test_step_kernel_variants_bitwise_equal(storage, fuse):
         h.wlbm_check()
         out.append(h.wlbm_get_state().cpu().numpy())
         h.close()
-    assert np.array_equal(out[0], out[1]) and np.array_equal(out[0], out[2])
+    for k in range(1, 4):
+        assert np.array_equal(out[0], out[k]), k
+
+
+@pytest.mark.parametrize("storage,tol,stol", [(0, TOL32, None), (1, TOL16, TOL16_STATE)])
+@pytest.mark.parametrize("nx,ny,q", [(1, 1, 8), (1, 7, 16), (5, 1, 8), (2, 3, 24), (126, 9, 16),
+                                     (127, 17, 8), (258, 41, 40)])
+def test_tma_variant_edges_and_field(storage, tol, stol, nx, ny, q):
+    """Variant 3 on degenerate grids, on widths around its 128-column tile (126 + 2 ghost
+    columns fill one tile exactly, 127 spills one column into a second tile), with a
+    per-cell MFP field and mixed walls."""
+    # log-normal MFP (a constant field on 1 x 1), kept above the W_corr <= 1 limit
+    mfp = (np.full((1, 1), 6.0, np.float32) if nx * ny == 1 else
+           np.maximum(W.lognormal_mfp(nx, ny, seed=nx + ny, corr=3.0), 1.6).astype(np.float32))
+    cfg = dict(nx=nx, ny=ny, q=q, mfp=None, mfp_field=mfp, bc=(I, A, P, P),
+               t_wall=(300.6, 300.0, 300.0, 300.0), emulate_3d=True,
+               dT=W.random_dT(nx, ny, seed=nx * ny + q, scale=0.5))
+    _compare(cfg, 40, storage=storage, tol=tol, state_tol=stol, variant=3)
 
 
 def test_init_roundtrip_temperature():
