@@ -860,7 +860,8 @@ cudaError_t prepare_step_kernels() {
 cudaError_t launch_step(int storage, const StepArgs& a, cudaStream_t s) {
   // variant 3 covers plain steps (no fused periodic mirrors, no adjoint tape) of grids
   // that have a tensor map; the others run variant 1
-  if (a.variant == 3 && !a.wrap && !a.tape && a.tmap) return launch_step_tma(storage, a, s);
+  if (a.variant == 3 && !a.wrap && !a.tape && a.tmap && a.order)
+    return launch_step_tma(storage, a, s);
   if (a.variant == 2) {
     if (storage == WLBM_STORE_BF16_DEV) return launch_ws<__nv_bfloat16, 8, 8, true>(a, s);
     return launch_ws<float, 4, 8, false>(a, s);

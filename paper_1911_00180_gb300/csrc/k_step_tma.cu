@@ -4,19 +4,24 @@
 // direction, Eq. worm-paths; E' = sum_i d_i', Eq. lbm-energy-density), organised so that
 // the per-element work is a handful of instructions:
 //   * one producer thread per block issues, for direction i, ONE tiled 3-D tensor copy of
-//     the shifted source box (7 rows x 128 + 2V columns of plane par*q + i) into a stage
-//     of a shared-memory ring; full/empty mbarriers pair it with 7 consumer warps (a block
-//     is 8 warps, so two blocks of up to 128 registers a thread fit on an SM);
-//   * a consumer lane owns 4 consecutive cells of one row and keeps 1 - W, the scattered
-//     energy W E (and, for bfloat16, the reference term) of the 3 x 6 cells around them in
-//     registers, loaded once per step;
-//   * the direction's hop selects one of 16 specialised bodies (8 hops x paused or not),
-//     so every neighbour index is a compile-time register, source values arrive with one
-//     or two vector shared-memory loads, and results leave with one 8- or 16-byte
-//     streaming store per lane.
-// Edge groups (columns past the right ghost) store element by element, so pad columns
-// stay zero.  Fully periodic grids with fused mirrors and the adjoint's tape mode are
-// served by variant 1 (the dispatcher routes them there).
+//     the shifted source box (14 rows x 128 + 2V columns of plane par*q + i) into a stage
+//     of a shared-memory ring; full/empty mbarriers pair it with 7 consumer warps.  Tall
+//     boxes matter: the copy engine's throughput grows with the rows per box (7-row boxes
+//     streamed less than half of what 14-16-row boxes do);
+//   * a consumer warp owns 2 adjacent rows; a lane owns 4 consecutive cells of each and
+//     keeps 1 - W and the source term of the 4 x 6 cells around them in registers, loaded
+//     once per step (bfloat16 also keeps W E of those cells in a lane-private stretch of
+//     shared memory, read only by paused directions);
+//   * the directions of the step are processed sorted by kind (8 hops x paused or not;
+//     the host sorts them, stably), as 16 loops with specialised bodies: every neighbour
+//     index is a compile-time register, no per-direction indirect branch is taken, source
+//     values arrive with one or two vector shared-memory loads, and results leave with
+//     one 8- or 16-byte streaming store per lane and row.  E' sums the directions in that
+//     order, so the result equals the other variants' up to float rounding.
+// A block is 8 warps, so two blocks of up to 128 registers a thread fit on an SM.  Edge
+// groups (columns past the right ghost) store element by element, so pad columns stay
+// zero.  Fully periodic grids with fused mirrors and the adjoint's tape mode are served by
+// variant 1 (the dispatcher routes them there).
 #include <cuda.h>
 
 #include "elem.cuh"
@@ -27,9 +32,12 @@ namespace wlbm {
 
 namespace {
 
-constexpr int kTY3 = 7;           // consumer warps (rows) per block; + 1 producer warp
-constexpr int kCPT3 = 4;          // consecutive cells per lane
-constexpr int kTW3 = 32 * kCPT3;  // tile width
+constexpr int kWarps3 = 7;              // consumer warps per block; + 1 producer warp
+constexpr int kRPW = 2;                 // rows per consumer warp
+constexpr int kRows3 = kWarps3 * kRPW;  // rows per block (box height)
+constexpr int kCPT3 = 4;                // consecutive cells per lane
+constexpr int kTW3 = 32 * kCPT3;        // tile width
+constexpr int kTR = kRPW + 2;           // register-tile rows (one halo row each side)
 
 // Per-direction record built once per block (16 bytes, one shared-memory vector load).
 struct alignas(16) Dir3 {
@@ -42,31 +50,34 @@ struct alignas(16) Dir3 {
 
 template <typename T, int S>
 struct TmaLayout {
+  static constexpr bool REF = sizeof(T) == 2;
   static constexpr int V = 16 / int(sizeof(T));          // elements per 16 bytes
   static constexpr int BW = kTW3 + 2 * V;                // box width: columns col0-V ..
-  static constexpr int kBoxElems = BW * kTY3;
+  static constexpr int kBoxElems = BW * kRows3;
   static constexpr uint32_t kBoxBytes = uint32_t(kBoxElems) * sizeof(T);
   static constexpr size_t kStage = (size_t(kBoxBytes) + 127) / 128 * 128;   // aligned stride
-  static constexpr size_t off_bar = size_t(S) * kStage;
-  static constexpr size_t off_table = off_bar + ((2 * S * 8 + 127) / 128) * 128;
+  // bfloat16: W E / scale of every lane's kTR x 6 register-tile cells, [warp][cell][lane]
+  static constexpr size_t off_f = size_t(S) * kStage;
+  static constexpr size_t f_bytes = REF ? size_t(kWarps3) * kTR * 6 * 32 * 4 : 0;
+  static constexpr size_t off_bar = (off_f + f_bytes + 127) / 128 * 128;
+  static constexpr size_t off_kind = off_bar + 2 * S * 8;           // 17 ints
+  static constexpr size_t off_table = (off_kind + 17 * 4 + 127) / 128 * 128;
   static size_t bytes(int q) { return off_table + size_t(q) * sizeof(Dir3); }
 };
 
 __device__ __forceinline__ float bf_lo(uint32_t w) { return __uint_as_float(w << 16); }
 __device__ __forceinline__ float bf_hi(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
 
-
-// Register tile of one lane: rows r-1, r, r+1 (index 0..2) and columns c0-1 .. c0+4
-// (index 0..5) around its cells c0 .. c0+3.
+// Register tile of one lane: rows r-1 .. r+kRPW (index 0..kTR-1) and columns c0-1 .. c0+4
+// (index 0..5) around its cells (rows r, r+1; columns c0 .. c0+3).
 struct Regs3 {
-  float G[3][6];   // 1 - W
-  float F[3][6];   // W E (bfloat16: W E / scale)
-  float R[3][6];   // bfloat16 only: ((1 - W) E_ref + W E) / scale
-  float eins[4];   // bfloat16 only: E_in / scale of the lane's own cells
-  float acc[4];    // sum over directions of the stored new values
+  float G[kTR][6];      // 1 - W
+  float X[kTR][6];      // float32: W E; bfloat16: ((1 - W) E_ref + W E) / scale
+  float eins[kRPW][4];  // bfloat16: E_in / scale of the own cells
+  float acc[kRPW][4];   // sum over directions of the stored new values
 };
 
-// Source values of the 4 cells for a DDED shift DX (-1, 0, +1) from the ring row.
+// Source values of the 4 cells for a DDED shift DX (-1, 0, +1) from a ring row.
 template <typename T, int DX>
 __device__ __forceinline__ void ring_values(const T* row, int lane, float (&v)[4]) {
   constexpr int V = 16 / int(sizeof(T));
@@ -128,77 +139,101 @@ __device__ __forceinline__ void store4(T* dst, const float (&o)[4], int nvalid, 
   }
 }
 
-// One direction for the lane's 4 cells; hop (CX, CY), paused or propagating.
+// Arguments of one direction for one lane.
+template <typename T>
+struct DirCtx {
+  const T* ring_row;   // first of the warp's rows in the stage
+  T* dst;              // destination of the lane's first cell in the warp's first row
+  const float* fsc;    // bfloat16: this lane's W E / scale scratch (stride 32 floats)
+  int64_t pitch;
+  float wi;
+  int lane, nvalid, nrw;   // nrw: computed rows of this warp (1 or 2)
+};
+
+// One direction for the lane's cells; hop (CX, CY), paused or propagating.
 template <typename T, bool REF, int CX, int CY, bool PAUSED>
-__device__ __forceinline__ void dir_body(Regs3& t, const T* ring_row, int lane, T* dst, float wi,
-                                         int nvalid) {
+__device__ __forceinline__ void dir_body(Regs3& t, const DirCtx<T>& c) {
+  constexpr int BW = kTW3 + 2 * (16 / int(sizeof(T)));
   constexpr int DX = PAUSED ? 0 : -CX;
-  constexpr int SR = PAUSED ? 1 : 1 - CY;   // tile row of the DDED source
   constexpr int SC = PAUSED ? 1 : 1 - CX;   // tile column of the DDED source of cell 0
-  constexpr int FR = 1 - CY, FC = 1 - CX;   // EED source (y - c) of cell 0
-  float v[4], o[4], s[4];
-  ring_values<T, DX>(ring_row, lane, v);
+  constexpr int FC = 1 - CX;                // tile column of the EED source (y - c)
 #pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    if constexpr (REF) {
-      // stored v' = (d' - w_i E_in(y)) / scale, d' from Eq. lbm-energy with the local
-      // reference R of the stored source value (see the bfloat16 storage note)
-      const float tt = PAUSED ? __fadd_rn(__fsub_rn(t.R[1][1 + j], t.F[1][1 + j]),
-                                          t.F[FR][FC + j])
-                              : t.R[SR][SC + j];
-      o[j] = fmaf(t.G[SR][SC + j], v[j], __fmul_rn(wi, __fsub_rn(tt, t.eins[j])));
-    } else {
-      o[j] = fmaf(t.G[SR][SC + j], v[j], __fmul_rn(wi, t.F[FR][FC + j]));
+  for (int k = 0; k < kRPW; ++k) {
+    if (k >= c.nrw) break;
+    const int SR = PAUSED ? 1 + k : 1 + k - CY;   // tile row of the DDED source
+    const int FR = 1 + k - CY;                    // tile row of the EED source
+    float v[4], o[4], s[4];
+    ring_values<T, DX>(c.ring_row + k * BW, c.lane, v);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if constexpr (REF) {
+        // stored v' = (d' - w_i E_in(y)) / scale, d' from Eq. lbm-energy with the local
+        // reference R of the stored source value (see the bfloat16 storage note)
+        const float tt =
+            PAUSED ? __fadd_rn(__fsub_rn(t.X[1 + k][1 + j], c.fsc[((1 + k) * 6 + 1 + j) * 32]),
+                               c.fsc[(FR * 6 + FC + j) * 32])
+                   : t.X[SR][SC + j];
+        o[j] = fmaf(t.G[SR][SC + j], v[j], __fmul_rn(c.wi, __fsub_rn(tt, t.eins[k][j])));
+      } else {
+        o[j] = fmaf(t.G[SR][SC + j], v[j], __fmul_rn(c.wi, t.X[FR][FC + j]));
+      }
     }
-  }
-  store4<T>(dst, o, nvalid, s);
+    store4<T>(c.dst + k * c.pitch, o, c.nvalid, s);
 #pragma unroll
-  for (int j = 0; j < 4; ++j) t.acc[j] += s[j];
+    for (int j = 0; j < 4; ++j) t.acc[k][j] += s[j];
+  }
 }
 
-// kase = hop | paused << 3; hop numbering of the host lattice:
-// (1,0) (0,1) (-1,0) (0,-1) (1,1) (-1,1) (-1,-1) (1,-1)
-template <typename T, bool REF>
-__device__ __forceinline__ void dir_kase(int kase, Regs3& t, const T* ring_row, int lane, T* dst,
-                                         float wi, int nvalid) {
-  switch (kase) {
-    case 0: dir_body<T, REF, 1, 0, false>(t, ring_row, lane, dst, wi, nvalid); break;
-    case 1: dir_body<T, REF, 0, 1, false>(t, ring_row, lane, dst, wi, nvalid); break;
-    case 2: dir_body<T, REF, -1, 0, false>(t, ring_row, lane, dst, wi, nvalid); break;
-    case 3: dir_body<T, REF, 0, -1, false>(t, ring_row, lane, dst, wi, nvalid); break;
-    case 4: dir_body<T, REF, 1, 1, false>(t, ring_row, lane, dst, wi, nvalid); break;
-    case 5: dir_body<T, REF, -1, 1, false>(t, ring_row, lane, dst, wi, nvalid); break;
-    case 6: dir_body<T, REF, -1, -1, false>(t, ring_row, lane, dst, wi, nvalid); break;
-    case 7: dir_body<T, REF, 1, -1, false>(t, ring_row, lane, dst, wi, nvalid); break;
-    case 8: dir_body<T, REF, 1, 0, true>(t, ring_row, lane, dst, wi, nvalid); break;
-    case 9: dir_body<T, REF, 0, 1, true>(t, ring_row, lane, dst, wi, nvalid); break;
-    case 10: dir_body<T, REF, -1, 0, true>(t, ring_row, lane, dst, wi, nvalid); break;
-    case 11: dir_body<T, REF, 0, -1, true>(t, ring_row, lane, dst, wi, nvalid); break;
-    case 12: dir_body<T, REF, 1, 1, true>(t, ring_row, lane, dst, wi, nvalid); break;
-    case 13: dir_body<T, REF, -1, 1, true>(t, ring_row, lane, dst, wi, nvalid); break;
-    case 14: dir_body<T, REF, -1, -1, true>(t, ring_row, lane, dst, wi, nvalid); break;
-    default: dir_body<T, REF, 1, -1, true>(t, ring_row, lane, dst, wi, nvalid); break;
+// All directions of one kind (hop (CX, CY), paused or not): entries j .. end-1 of the
+// kind-sorted table.  Returns false when a bounded wait gave up.
+template <typename T, int S, bool REF, int CX, int CY, bool PAUSED>
+__device__ __forceinline__ bool run_kind(int& j, int end, Regs3& t, DirCtx<T>& c, float& accw,
+                                         const Dir3* table, const unsigned char* smem,
+                                         uint64_t* full, uint64_t* empty, T* obase, int ty,
+                                         int* status) {
+  using LY = TmaLayout<T, S>;
+  for (; j < end; ++j) {
+    const int st = j % S;
+    if (!mbar_wait(&full[st], uint32_t(j / S) & 1u, kWaitCycles)) {
+      if (c.lane == 0) atomicOr(status, 1);
+      return false;
+    }
+    const Dir3 d = table[j];
+    c.ring_row = reinterpret_cast<const T*>(smem + st * LY::kStage) + kRPW * ty * LY::BW;
+    c.dst = obase + d.dst_off;
+    c.wi = d.wi;
+    if (REF) accw += d.wi;
+    if (c.nvalid > 0) dir_body<T, REF, CX, CY, PAUSED>(t, c);
+    __syncwarp();
+    if (c.lane == 0) mbar_arrive(&empty[st]);
   }
+  return true;
 }
 
 template <typename T, int S, bool FIELD_W, bool REF>
 __global__ void __maxnreg__(128)
     k_step_tma(const StepArgs a, const __grid_constant__ CUtensorMap tmap) {
   using LY = TmaLayout<T, S>;
-  constexpr int V = LY::V, BW = LY::BW;
+  constexpr int V = LY::V;
   extern __shared__ __align__(128) unsigned char smem[];
-  // smem: S ring stages of [kTY3][BW] elements (stride kStage), then the barriers
+  // smem: S ring stages of [kRows3][BW] elements (stride kStage), the bfloat16 W E
+  // scratch, the barriers, the direction table
+  float* fscr = reinterpret_cast<float*>(smem + LY::off_f);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + LY::off_bar);      // [S]
   uint64_t* empty = full + S;                                            // [S]
   Dir3* table = reinterpret_cast<Dir3*>(smem + LY::off_table);           // [q]
 
   const int lane = threadIdx.x, ty = threadIdx.y;
-  const int tid = ty * 32 + lane, nthr = 32 * (kTY3 + 1);
+  const int tid = ty * 32 + lane, nthr = 32 * (kWarps3 + 1);
   const int col0 = kGhostCol + int(blockIdx.x) * kTW3;
-  const int row0 = 1 + int(blockIdx.y) * kTY3;
-  const int nrows = min(kTY3, a.ny + 2 - row0 + 1);   // rows row0 .. ny+2 are computed
+  const int row0 = 1 + int(blockIdx.y) * kRows3;
+  const int nrows = min(kRows3, a.ny + 2 - row0 + 1);   // rows row0 .. ny+2 are computed
+  const int nwarps = (nrows + kRPW - 1) / kRPW;         // consumer warps with rows
 
-  for (int i = tid; i < a.q; i += nthr) {
+  int* kind_start = reinterpret_cast<int*>(smem + LY::off_kind);         // [17]
+  for (int k = tid; k <= 16; k += nthr) kind_start[k] = a.order[a.q + k];
+  for (int j = tid; j < a.q; j += nthr) {
+    const int i = a.order[j];
     const int code = a.codes[i];
     const int hop = code & 7, paused = (code >> 3) & 1, par = (code >> 4) & 1;
     Dir3 d;
@@ -207,19 +242,19 @@ __global__ void __maxnreg__(128)
     d.z = uint16_t(par * a.q + i);
     d.kase = uint8_t(hop | (paused << 3));
     d.dy = int8_t(paused ? 0 : -c_hop_y[hop]);
-    table[i] = d;
+    table[j] = d;
   }
   if (tid == 0) {
     for (int st = 0; st < S; ++st) {
       mbar_init(&full[st], 1);
-      mbar_init(&empty[st], nrows > 0 ? nrows : 1);
+      mbar_init(&empty[st], nwarps > 0 ? nwarps : 1);
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
   if (nrows <= 0) return;
 
-  if (ty == kTY3) {
+  if (ty == kWarps3) {
     // ------------------------------------------------------------- producer thread
     if (lane != 0) return;
     for (int i = 0; i < a.q; ++i) {
@@ -238,19 +273,21 @@ __global__ void __maxnreg__(128)
   }
 
   // ---------------------------------------------------------------- consumer warps
-  const int r = row0 + ty;
-  if (ty >= nrows) return;
+  if (ty >= nwarps) return;
+  const int r = row0 + kRPW * ty;                      // first row of this warp
+  const int nrw = min(kRPW, a.ny + 2 - r + 1);         // 1 or 2 computed rows
   const int c0 = col0 + 4 * lane;
   const int nvalid = max(0, min(4, kX0 + a.nx - c0 + 1));   // cells c0.. up to the ghost
+  float* fsc = fscr + size_t(ty) * kTR * 6 * 32 + lane;
   Regs3 t;
 #pragma unroll
-  for (int rr = 0; rr < 3; ++rr) {
-    const int row = r - 1 + rr;                 // 0 <= row < rows for computed rows
+  for (int rr = 0; rr < kTR; ++rr) {
+    const int row = r - 1 + rr;
 #pragma unroll
     for (int cc = 0; cc < 6; ++cc) {
       const int c = c0 - 1 + cc;
       float wv = 0.f, ev = 0.f, rv = 0.f;
-      if (c < a.pitch) {
+      if (row < a.rows && c < a.pitch) {
         const int64_t o = int64_t(row) * a.pitch + c;
         ev = a.e_in[o];
         wv = FIELD_W ? a.wfield[o] : uniform_w(a, row, c);
@@ -259,50 +296,74 @@ __global__ void __maxnreg__(128)
       const float fv = __fmul_rn(wv, ev), gv = __fsub_rn(1.f, wv);
       t.G[rr][cc] = gv;
       if (REF) {
-        t.F[rr][cc] = __fmul_rn(fv, a.inv_scale);
-        t.R[rr][cc] = __fmul_rn(fmaf(gv, rv, fv), a.inv_scale);
+        const float fs = __fmul_rn(fv, a.inv_scale);
+        const float xs = __fmul_rn(fmaf(gv, rv, fv), a.inv_scale);
+        t.X[rr][cc] = xs;
+        fsc[(rr * 6 + cc) * 32] = fs;
+        if (rr >= 1 && rr <= kRPW && cc >= 1 && cc <= 4)
+          t.eins[rr - 1][cc - 1] = cc - 1 < nvalid ? __fmul_rn(ev, a.inv_scale) : 0.f;
       } else {
-        t.F[rr][cc] = fv;
-        t.R[rr][cc] = 0.f;
+        t.X[rr][cc] = fv;
       }
-      if (rr == 1 && cc >= 1 && cc <= 4)
-        t.eins[cc - 1] = REF && cc - 1 < nvalid ? __fmul_rn(ev, a.inv_scale) : 0.f;
     }
   }
 #pragma unroll
-  for (int j = 0; j < 4; ++j) t.acc[j] = 0.f;
+  for (int k = 0; k < kRPW; ++k)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) t.acc[k][j] = 0.f;
   float accw = 0.f;
+  DirCtx<T> ctx;
+  ctx.fsc = fsc;
+  ctx.pitch = a.pitch;
+  ctx.lane = lane;
+  ctx.nvalid = nvalid;
+  ctx.nrw = nrw;
   T* obase = static_cast<T*>(a.planes) + int64_t(r) * a.pitch + c0;
 
-  for (int i = 0; i < a.q; ++i) {
-    const int st = i % S;
-    if (!mbar_wait(&full[st], uint32_t(i / S) & 1u, kWaitCycles)) {
-      if (lane == 0) atomicOr(a.status, 1);
-      return;
-    }
-    const Dir3 d = table[i];
-    const T* ring_row = reinterpret_cast<const T*>(smem + st * LY::kStage) + ty * BW;
-    T* dst = obase + d.dst_off;
-    if (REF) accw += d.wi;
-    if (nvalid > 0) dir_kase<T, REF>(d.kase, t, ring_row, lane, dst, d.wi, nvalid);
-    __syncwarp();
-    if (lane == 0) mbar_arrive(&empty[st]);
-  }
+  // kind = hop | paused << 3; hop numbering of the host lattice:
+  // (1,0) (0,1) (-1,0) (0,-1) (1,1) (-1,1) (-1,-1) (1,-1)
+  int j = 0;
+  bool ok = true;
+#define WLBM_KIND(K, CX, CY, P)                                                            \
+  ok = ok && run_kind<T, S, REF, CX, CY, P>(j, kind_start[K + 1], t, ctx, accw, table, smem, \
+                                            full, empty, obase, ty, a.status)
+  WLBM_KIND(0, 1, 0, false);
+  WLBM_KIND(1, 0, 1, false);
+  WLBM_KIND(2, -1, 0, false);
+  WLBM_KIND(3, 0, -1, false);
+  WLBM_KIND(4, 1, 1, false);
+  WLBM_KIND(5, -1, 1, false);
+  WLBM_KIND(6, -1, -1, false);
+  WLBM_KIND(7, 1, -1, false);
+  WLBM_KIND(8, 1, 0, true);
+  WLBM_KIND(9, 0, 1, true);
+  WLBM_KIND(10, -1, 0, true);
+  WLBM_KIND(11, 0, -1, true);
+  WLBM_KIND(12, 1, 1, true);
+  WLBM_KIND(13, -1, 1, true);
+  WLBM_KIND(14, -1, -1, true);
+  WLBM_KIND(15, 1, -1, true);
+#undef WLBM_KIND
+  if (!ok) return;
   // E'(y) = sum_i d_i'(y) (Eq. lbm-energy-density); bfloat16: d' = scale v' + w_i E_in(y)
-  const int64_t own = int64_t(r) * a.pitch + c0;
-  float eo[4];
 #pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    const float ein = REF && j < nvalid ? a.e_in[own + j] : 0.f;
-    eo[j] = REF ? fmaf(t.acc[j], a.scale, __fmul_rn(ein, accw)) : t.acc[j];
-  }
-  float* e_out = a.e_out + own;
-  if (nvalid == 4) {
-    *reinterpret_cast<float4*>(e_out) = make_float4(eo[0], eo[1], eo[2], eo[3]);
-  } else {
+  for (int k = 0; k < kRPW; ++k) {
+    if (k >= nrw) break;
+    const int64_t own = int64_t(r + k) * a.pitch + c0;
+    float eo[4];
 #pragma unroll
-    for (int j = 0; j < 4; ++j)
-      if (j < nvalid) e_out[j] = eo[j];
+    for (int j = 0; j < 4; ++j) {
+      const float ein = REF && j < nvalid ? a.e_in[own + j] : 0.f;
+      eo[j] = REF ? fmaf(t.acc[k][j], a.scale, __fmul_rn(ein, accw)) : t.acc[k][j];
+    }
+    float* e_out = a.e_out + own;
+    if (nvalid == 4) {
+      *reinterpret_cast<float4*>(e_out) = make_float4(eo[0], eo[1], eo[2], eo[3]);
+    } else {
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (j < nvalid) e_out[j] = eo[j];
+    }
   }
 }
 
@@ -325,8 +386,8 @@ cudaError_t configure_tma_t() {
 template <typename T, int S>
 cudaError_t launch_tma_t(const StepArgs& a, const CUtensorMap& tm, cudaStream_t s) {
   using LY = TmaLayout<T, S>;
-  const dim3 block(32, kTY3 + 1);
-  const dim3 grid((a.nx + 2 + kTW3 - 1) / kTW3, (a.ny + 2 + kTY3 - 1) / kTY3);
+  const dim3 block(32, kWarps3 + 1);
+  const dim3 grid((a.nx + 2 + kTW3 - 1) / kTW3, (a.ny + 2 + kRows3 - 1) / kRows3);
   const size_t bytes = LY::bytes(a.q);
   constexpr bool REF = sizeof(T) == 2;
   if (a.wfield) k_step_tma<T, S, true, REF><<<grid, block, bytes, s>>>(a, tm);
@@ -334,8 +395,8 @@ cudaError_t launch_tma_t(const StepArgs& a, const CUtensorMap& tm, cudaStream_t 
   return cudaGetLastError();
 }
 
-constexpr int kStagesF32 = 8;    // 8 x 4352 B of boxes in flight per block
-constexpr int kStagesBF16 = 16;  // 16 x 2304 B
+constexpr int kStagesF32 = 6;    // 6 x 7.4 KB of boxes in flight per block
+constexpr int kStagesBF16 = 8;   // 8 x 4 KB
 
 }  // namespace
 
@@ -378,7 +439,7 @@ bool make_plane_tensor_map(void* out, void* planes, int storage, const Geom& g,
   const cuuint32_t V = cuuint32_t(16 / es);
   const cuuint64_t dims[3] = {cuuint64_t(g.pitch), cuuint64_t(g.rows), cuuint64_t(2 * g.q)};
   const cuuint64_t strides[2] = {cuuint64_t(g.pitch) * es, cuuint64_t(g.plane) * es};
-  const cuuint32_t box[3] = {cuuint32_t(kTW3) + 2 * V, cuuint32_t(kTY3), 1};
+  const cuuint32_t box[3] = {cuuint32_t(kTW3) + 2 * V, cuuint32_t(kRows3), 1};
   const cuuint32_t estr[3] = {1, 1, 1};
   const CUresult r = encode(static_cast<CUtensorMap*>(out),
                             bf ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,

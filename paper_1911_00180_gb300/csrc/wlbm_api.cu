@@ -50,6 +50,7 @@ struct wlbm_handle {
   float* wfield = nullptr;    // framed W_corr (per-cell MFP only)
   float* consts = nullptr;    // w[q], sx[q], sy[q], rho[8][q]
   uint8_t* d_codes = nullptr; // [kChunk][q]
+  uint16_t* d_order = nullptr; // [kChunk][q + 17] kind-sorted directions (variant 3)
   double* d_red = nullptr;    // [4]
   int* d_status = nullptr;    // bit 0: a bounded device wait gave up
   int step_variant = 1;       // 0 register-pipelined, 1 per-warp bulk-copy ring,
@@ -64,6 +65,7 @@ struct wlbm_handle {
   std::vector<void*> owned;
   // host staging
   uint8_t* h_codes[2] = {nullptr, nullptr};
+  uint16_t* h_order[2] = {nullptr, nullptr};
   cudaEvent_t ev[2] = {nullptr, nullptr};
   int slot = 0;
   WallArgs walls{};
@@ -152,6 +154,8 @@ struct wlbm_handle {
     prof_ev.clear();
     for (int k = 0; k < 2; ++k) {
       if (h_codes[k]) cudaFreeHost(h_codes[k]);
+      if (h_order[k]) cudaFreeHost(h_order[k]);
+      h_order[k] = nullptr;
       if (ev[k]) cudaEventDestroy(ev[k]);
       h_codes[k] = nullptr;
       ev[k] = nullptr;
@@ -419,12 +423,13 @@ wlbm_status wlbm_create(const wlbm_grid* grid, const float* mfp_cells, double mf
   h->e_ref = h->bf16() ? 2 : -1;
   h->consts = static_cast<float*>(h->dev_alloc(size_t(11) * G.q * 4));
   h->d_codes = static_cast<uint8_t*>(h->dev_alloc(size_t(kChunk) * G.q));
+  h->d_order = static_cast<uint16_t*>(h->dev_alloc(size_t(kChunk) * (G.q + 17) * 2));
   h->d_red = static_cast<double*>(h->dev_alloc(8 * sizeof(double)));
   h->d_status = static_cast<int*>(h->dev_alloc(256));
   if (h->planes) h->has_tmap = make_plane_tensor_map(h->tmap, h->planes, h->storage, g, &h->tmap_why);
   if (h->field_w) h->wfield = static_cast<float*>(h->dev_alloc(size_t(g.plane) * 4));
   if (!h->planes || !h->e[0] || !h->e[1] || (n_e == 3 && !h->e[2]) || !h->consts ||
-      !h->d_codes || !h->d_red || !h->d_status ||
+      !h->d_codes || !h->d_order || !h->d_red || !h->d_status ||
       (h->field_w && !h->wfield))
     return bad(WLBM_ERR_OOM, "wlbm_create: device allocation failed");
 
@@ -448,6 +453,9 @@ wlbm_status wlbm_create(const wlbm_grid* grid, const float* mfp_cells, double mf
   for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
     e = cudaHostAlloc(reinterpret_cast<void**>(&h->h_codes[k]), size_t(kChunk) * G.q,
                       cudaHostAllocDefault);
+    if (e == cudaSuccess)
+      e = cudaHostAlloc(reinterpret_cast<void**>(&h->h_order[k]),
+                        size_t(kChunk) * (G.q + 17) * 2, cudaHostAllocDefault);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev[k], cudaEventDisableTiming);
   }
   if (e == cudaSuccess) e = prepare_step_kernels();
@@ -548,6 +556,7 @@ static wlbm_status enqueue_steps(wlbm_handle* h, int count, bool profile) {
     sa.variant = h->step_variant; sa.status = h->d_status;
     sa.xper = h->xper; sa.yper = h->yper; sa.wrap = wrap;
     sa.tmap = h->has_tmap ? h->tmap : nullptr;
+    sa.order = h->d_order + size_t(t) * (g.q + 17);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (profile) {
       if (h->prof_used + 2 > h->prof_ev.size()) {
@@ -617,9 +626,16 @@ wlbm_status wlbm_step(wlbm_handle* h, int64_t n) {
     wlbm_status st = h->cuda(cudaEventSynchronize(h->ev[slot]), "wlbm_step");
     if (st != WLBM_OK) return st;
     uint8_t* hc = h->h_codes[slot];
-    for (int t = 0; t < ch; ++t) tas_advance(h->lat, &h->tas, hc + size_t(t) * g.q);
+    uint16_t* ho = h->h_order[slot];
+    for (int t = 0; t < ch; ++t) {
+      tas_advance(h->lat, &h->tas, hc + size_t(t) * g.q);
+      sort_by_kind(hc + size_t(t) * g.q, g.q, ho + size_t(t) * (g.q + 17));
+    }
     st = h->cuda(cudaMemcpyAsync(h->d_codes, hc, size_t(ch) * g.q, cudaMemcpyHostToDevice,
                                  h->stream), "wlbm_step: schedule upload");
+    if (st == WLBM_OK)
+      st = h->cuda(cudaMemcpyAsync(h->d_order, ho, size_t(ch) * (g.q + 17) * 2,
+                                   cudaMemcpyHostToDevice, h->stream), "wlbm_step: order upload");
     if (st == WLBM_OK) st = h->cuda(cudaEventRecord(h->ev[slot], h->stream), "wlbm_step");
     if (st != WLBM_OK) return st;
     if (graphs && ch == h->graph_steps)

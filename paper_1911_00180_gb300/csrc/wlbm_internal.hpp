@@ -69,7 +69,22 @@ struct StepArgs {
   // host pointer to the planes' CUtensorMap (128 bytes, variant 3), or nullptr; read by
   // the launcher on the host, never by a kernel
   const void* tmap;
+  // variant 3: this step's directions sorted by kind (hop | paused << 3, stable), q
+  // entries, followed by the 17 starts of the 16 kinds; nullptr selects variant 1
+  const uint16_t* order;
 };
+
+// Stable sort of one step's directions by kind = hop | paused << 3 (16 kinds): writes the
+// sorted direction indices to out[0..q) and the start of every kind to out[q..q+17).
+inline void sort_by_kind(const uint8_t* codes, int q, uint16_t* out) {
+  uint16_t* start = out + q;
+  for (int k = 0; k <= 16; ++k) start[k] = 0;
+  for (int i = 0; i < q; ++i) ++start[(codes[i] & 15) + 1];
+  for (int k = 0; k < 16; ++k) start[k + 1] = uint16_t(start[k + 1] + start[k]);
+  uint16_t next[16];
+  for (int k = 0; k < 16; ++k) next[k] = start[k];
+  for (int i = 0; i < q; ++i) out[next[codes[i] & 15]++] = uint16_t(i);
+}
 
 #ifdef __CUDACC__
 // Uniform W_corr of a frame cell: w0 inside the frame, 0 on pads and on the ghost cells of

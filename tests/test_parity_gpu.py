@@ -86,8 +86,10 @@ def test_step_kernel_variants(variant, storage, tol, stol, kinds):
 @pytest.mark.parametrize("storage", [0, 1])
 @pytest.mark.parametrize("fuse", [0, 1])
 def test_step_kernel_variants_bitwise_equal(storage, fuse):
-    """The variants (and the fused periodic mirrors) compute the same arithmetic: equal
-    states bit for bit."""
+    """Variants 0-2 (and the fused periodic mirrors) compute the same arithmetic in the
+    same order: equal states bit for bit.  Variant 3 sums E' over the directions in
+    kind-sorted order, so it agrees up to float rounding: 1e-5 of the state scale in
+    float32, one bfloat16 rounding step (the bfloat16 state tolerance) in bfloat16."""
     import paper_1911_00180_gb300 as wl
     from tests._pair import gpu_handle
     cfg = W.pulses_c2(seed=2, n=157, q=32, npulse=4)
@@ -101,8 +103,10 @@ def test_step_kernel_variants_bitwise_equal(storage, fuse):
         h.wlbm_check()
         out.append(h.wlbm_get_state().cpu().numpy())
         h.close()
-    for k in range(1, 4):
+    for k in (1, 2):
         assert np.array_equal(out[0], out[k]), k
+    scale = float(np.abs(out[0]).max())
+    assert np.abs(out[3] - out[0]).max() <= (TOL32 if storage == 0 else TOL16_STATE) * scale
 
 
 @pytest.mark.parametrize("storage,tol,stol", [(0, TOL32, None), (1, TOL16, TOL16_STATE)])
