@@ -341,6 +341,7 @@ def main():
             h.wlbm_set_option(wl.wlbm.OPT_GRAPH_STEPS, args.graph)
         if args.fuse is not None:
             h.wlbm_set_option(wl.wlbm.OPT_FUSE_PERIODIC, args.fuse)
+        variant_used = h.wlbm_get_option(wl.wlbm.OPT_STEP_VARIANT)
         dT = torch.as_tensor(cfg["dT"]).to("cuda", non_blocking=False)
         h.wlbm_init_temperature(dT)
         h.wlbm_step(args.warmup)
@@ -429,13 +430,13 @@ def main():
                        "nx": cfg["nx"], "ny": cfg["ny"], "q": cfg["q"],
                        "mfp_cells": cfg["mfp"], "parallelism": "replicas x%d" % world,
                        "step_kernel": {0: "register-pipelined", 1: "bulk-copy ring",
-                                       2: "warp-specialised", 3: "TMA tiles"}[
-                                           1 if args.variant is None else args.variant],
+                                       2: "warp-specialised", 3: "TMA tiles"}[variant_used],
                        "l2": "state %.2f GB > L2 (no flush needed)"
                              % (2 * cfg["q"] * cells * (4 if args.storage == "fp32" else 2) / 1e9)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None,
-                         "kernel": "k_step", "peak_kind": peak_kind,
+                         "kernel": {0: "k_step", 1: "k_step_bulk", 2: "k_step_ws",
+                                    3: "k_step_tma"}[variant_used], "peak_kind": peak_kind,
                          "bytes_per_update": bpu,
                          "kernel_ms_per_launch": per_launch_ms},
             "gpu_launches": int(launches1 - launches0),

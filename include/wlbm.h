@@ -155,10 +155,18 @@ wlbm_status wlbm_adjoint_backward(wlbm_handle* h, const float* dJ_dT, float* dJ_
                                   double* dJ_dTwall, float* dJ_ddT0);
 
 /* wlbm_set_option: tuning knobs that do not change results.
- *   WLBM_OPT_STEP_VARIANT  0: step kernel with register-pipelined loads; 1 (default):
- *                          step kernel with a per-warp ring of bulk async copies; 2:
- *                          warp-specialised step kernel (a producer warp issues the bulk
- *                          copies of all rows, consumer warps compute).
+ *   WLBM_OPT_STEP_VARIANT  0: step kernel with register-pipelined loads; 1: step kernel
+ *                          with a per-warp ring of bulk async copies; 2: warp-specialised
+ *                          step kernel (a producer warp issues the bulk copies of all
+ *                          rows, consumer warps compute); 3 (default where the driver can
+ *                          describe the planes as a TMA tensor, else 1): one tiled tensor
+ *                          copy per direction and 128 x 14 tile, register-resident cell
+ *                          data, directions processed grouped by hop kind.  Variants 0-2
+ *                          give bit-identical results; variant 3 sums E' in another order
+ *                          (equal up to float rounding).  Steps that fuse the periodic
+ *                          mirrors (WLBM_OPT_FUSE_PERIODIC) or record the adjoint's tape
+ *                          run variant 1 when variant 3 is selected; with variant 3 the
+ *                          periodic pass is never fused.
  *   WLBM_OPT_GRAPH_STEPS   0 (default): launch every step's kernels directly; G > 0, a
  *                          multiple of 6: run chunks of G steps as one captured CUDA
  *                          graph (for small, launch-bound grids; not while profiling and
@@ -170,6 +178,8 @@ wlbm_status wlbm_adjoint_backward(wlbm_handle* h, const float* dJ_dT, float* dJ_
  * inside a kernel gave up since the last check (the status is then cleared). */
 enum { WLBM_OPT_STEP_VARIANT = 1, WLBM_OPT_GRAPH_STEPS = 2, WLBM_OPT_FUSE_PERIODIC = 3 };
 wlbm_status wlbm_set_option(wlbm_handle* h, int32_t key, int64_t value);
+/* wlbm_get_option: the current value of a wlbm_set_option key in *value (host). */
+wlbm_status wlbm_get_option(const wlbm_handle* h, int32_t key, int64_t* value);
 wlbm_status wlbm_check(wlbm_handle* h);
 
 /* wlbm_profile: enable (1) or disable (0) CUDA-event timing of every launch of the
@@ -205,7 +215,7 @@ wlbm_status wlbm_profile_read(wlbm_handle* h, double* step_ms, int64_t* step_lau
 wlbm_status wlbm_reduce_state_noalloc(const float* framed, int32_t nx, int32_t ny, int32_t q,
                                       const int32_t* bc_kind, double* out, void* stream);
 
-/* wlbm_autotune: native search over WLBM_OPT_STEP_VARIANT (0, 1, 2) x WLBM_OPT_GRAPH_STEPS
+/* wlbm_autotune: native search over WLBM_OPT_STEP_VARIANT (0 - 3) x WLBM_OPT_GRAPH_STEPS
  * (0 and the largest multiple of 6 <= trial_steps) for this grid: each candidate runs trial_steps (>= 6) steps after a warm-up; the fastest is kept
  * and returned (any output may be NULL).  The trial steps advance the state: call it
  * before wlbm_init_temperature. */
@@ -222,8 +232,8 @@ wlbm_status wlbm_autotune(wlbm_handle* h, int32_t trial_steps, int32_t* variant,
  *   mfp_uniform         host array of n uniform MFPs (used where mfp_cells[k] is NULL)
  * wlbm_batch_instance returns the handle of instance k (owned by the batch) for
  * moments, reductions and state access.  Options (wlbm_batch_set_option) are those of
- * wlbm_set_option, for every instance: WLBM_OPT_STEP_VARIANT 0 or 1, WLBM_OPT_GRAPH_STEPS,
- * WLBM_OPT_FUSE_PERIODIC.  Instances with a periodic axis whose edges the step kernel does
+ * wlbm_set_option, for every instance: WLBM_OPT_STEP_VARIANT 0, 1 or 3 (default 3 when
+ * every instance has a tensor map), WLBM_OPT_GRAPH_STEPS, WLBM_OPT_FUSE_PERIODIC.  Instances with a periodic axis whose edges the step kernel does
  * not mirror get their own periodic pass each step; graph replay then keeps one captured
  * graph per starting energy-plane phase of those instances (at most three). */
 typedef struct wlbm_batch wlbm_batch;
@@ -237,12 +247,13 @@ wlbm_handle* wlbm_batch_instance(wlbm_batch* b, int32_t k);
 /* dT: host array of n device pointers (nx*ny float32 each). */
 wlbm_status wlbm_batch_init_temperature(wlbm_batch* b, const float* const* dT);
 wlbm_status wlbm_batch_set_option(wlbm_batch* b, int32_t key, int64_t value);
+wlbm_status wlbm_batch_get_option(const wlbm_batch* b, int32_t key, int64_t* value);
 wlbm_status wlbm_batch_step(wlbm_batch* b, int64_t n);
 wlbm_status wlbm_batch_profile(wlbm_batch* b, int32_t enable);
 wlbm_status wlbm_batch_profile_read(wlbm_batch* b, double* step_ms, int64_t* step_launches,
                                     int64_t* all_launches);
-/* wlbm_batch_autotune: as wlbm_autotune over variants 0 and 1, for the whole batch (call
- * before init). */
+/* wlbm_batch_autotune: as wlbm_autotune over variants 0, 1 and 3, for the whole batch
+ * (call before init). */
 wlbm_status wlbm_batch_autotune(wlbm_batch* b, int32_t trial_steps, int32_t* variant,
                                 int32_t* graph_steps, double* ms_per_step);
 

@@ -1,6 +1,7 @@
 // Boundary, initialisation, moment and reduction kernels of libwlbm.
 //
-//  k_walls     ghost cells of non-periodic walls (Sec. 2.6): isotropic blackbody walls
+//  k_walls     ghost cells of non-periodic walls (Sec. 2.6), 32 cells a block: isotropic
+//              blackbody walls
 //              overwrite d_i = w_i (e_eq(T_w) - e_ref) (Eq. isotropic); adiabatic diffuse
 //              walls collect the components that do not point into the domain and
 //              re-emit them into the inward ones with fractions w_i (s_i.n) / sum
@@ -40,39 +41,68 @@ __device__ __forceinline__ float dev_store(T* p, float d, float wi, const float*
   return fmaf(Elem<T>::st(p, __fmul_rn(__fsub_rn(d, r), inv_scale)), scale, r);
 }
 
+// Wall pass over chunks of 32 consecutive ghost cells of one segment: a block of
+// kWallWarps warps takes one chunk, lane l the cell l of it (consecutive cells of a
+// horizontal wall are consecutive in memory, so every per-direction access of a warp is
+// one coalesced row piece), and warp w the directions w, w + kWallWarps, ...  Diffuse
+// walls add the collected directions per warp, then over the warps in a fixed order.
+constexpr int kWallWarps = 8;
+
+__host__ __device__ inline int wall_chunks(const WallArgs& a) {
+  int n = 0;
+  for (int s = 0; s < a.nseg; ++s) n += (a.seg[s].count + 31) >> 5;
+  return n;
+}
+
 template <typename T>
-__device__ __forceinline__ void walls_cell(const WallArgs& a, const uint8_t* codes,
-                                           float* e_ref, int warp, int lane) {
-  int s = 0, idx = warp;
-  while (s < a.nseg && idx >= a.seg[s].count) {
-    idx -= a.seg[s].count;
+__device__ __forceinline__ void walls_chunk(const WallArgs& a, const uint8_t* codes,
+                                            float* e_ref, int chunk, float* part_s) {
+  int s = 0, c = chunk;
+  while (s < a.nseg) {
+    const int nch = (a.seg[s].count + 31) >> 5;
+    if (c < nch) break;
+    c -= nch;
     ++s;
   }
-  if (s >= a.nseg) return;
+  if (s >= a.nseg) return;                     // uniform over the block
   const WallSeg g = a.seg[s];
-  const int64_t off = int64_t(g.r0 + idx * g.dr) * a.pitch + (g.c0 + idx * g.dc);
+  const int lane = int(threadIdx.x) & 31, warp = int(threadIdx.x) >> 5;
+  const int idx = c * 32 + lane;
+  const bool on = idx < g.count;
+  const int64_t off = on ? int64_t(g.r0 + idx * g.dr) * a.pitch + (g.c0 + idx * g.dc) : 0;
   T* planes = static_cast<T*>(a.planes);
   auto ptr = [&](int i) {
     const int par = a.tape ? 0 : (codes[i] >> 4) & 1;
     return planes + int64_t(par * a.q + i) * a.plane + off;
   };
   if (g.action == WLBM_BC_ISOTHERMAL) {
+    if (!on) return;
     if (e_ref) {
       // bfloat16: make the wall's own equilibrium the reference of the cell, so the
       // stored values are exactly zero and decode to w_i (e_eq(T_w) - e_ref) unrounded
-      for (int i = lane; i < a.q; i += 32) Elem<T>::st(ptr(i), 0.f);
-      if (lane == 0) e_ref[off] = g.iso;
+      for (int i = warp; i < a.q; i += kWallWarps) Elem<T>::st(ptr(i), 0.f);
+      if (warp == 0) e_ref[off] = g.iso;
     } else {
-      for (int i = lane; i < a.q; i += 32) Elem<T>::st(ptr(i), a.w[i] * g.iso);
+      for (int i = warp; i < a.q; i += kWallWarps) Elem<T>::st(ptr(i), a.w[i] * g.iso);
     }
     return;
   }
   const float* rho = a.rho + int64_t(g.table) * a.q;
   float part = 0.f;
-  for (int i = lane; i < a.q; i += 32)
-    if (rho[i] == 0.f) part += dev_load(ptr(i), a.w[i], e_ref, off, a.scale);
-  const float A = warp_sum(part);
-  for (int i = lane; i < a.q; i += 32) {
+  if (on) {
+#pragma unroll 4
+    for (int i = warp; i < a.q; i += kWallWarps)
+      if (rho[i] == 0.f) part += dev_load(ptr(i), a.w[i], e_ref, off, a.scale);
+  }
+  part_s[warp * 32 + lane] = part;
+  __syncthreads();
+  float A = 0.f;
+#pragma unroll
+  for (int k = 0; k < kWallWarps; ++k) A += part_s[k * 32 + lane];
+  if (!on) return;
+#pragma unroll 4
+  for (int i = warp; i < a.q; i += kWallWarps) {
+    // collected directions are absorbed (0); the others receive their share of A
     const float d = rho[i] == 0.f ? 0.f
                                   : fmaf(A, rho[i], dev_load(ptr(i), a.w[i], e_ref, off, a.scale));
     dev_store(ptr(i), d, a.w[i], e_ref, off, a.scale, a.inv_scale);
@@ -80,26 +110,28 @@ __device__ __forceinline__ void walls_cell(const WallArgs& a, const uint8_t* cod
 }
 
 template <typename T>
-__global__ void k_walls(const WallArgs a) {
-  const int warp = int((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-  walls_cell<T>(a, a.codes, a.e_ref, warp, threadIdx.x & 31);
+__global__ void __launch_bounds__(32 * kWallWarps) k_walls(const WallArgs a) {
+  __shared__ float part_s[kWallWarps * 32];
+  walls_chunk<T>(a, a.codes, a.e_ref, int(blockIdx.x), part_s);
 }
 
-// Batched wall pass: warp w belongs to the instance whose first_warp is the largest one
-// <= w; codes and the reference-energy plane of step t come from the instance record.
+// Batched wall pass: block b belongs to the instance whose first_block is the largest one
+// <= b; codes and the reference-energy plane of step t come from the instance record.
 template <typename T>
-__global__ void k_walls_batch(const BatchWalls* B, int n, int t) {
-  const int gw = int((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+__global__ void __launch_bounds__(32 * kWallWarps) k_walls_batch(const BatchWalls* B, int n,
+                                                                  int t) {
+  __shared__ float part_s[kWallWarps * 32];
+  const int b = int(blockIdx.x);
   int lo = 0, hi = n - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
-    if (B[mid].first_warp <= gw) lo = mid;
+    if (B[mid].first_block <= b) lo = mid;
     else hi = mid - 1;
   }
   const BatchWalls& I = B[lo];
   const int cur = (I.phase + t) % I.n_e;
   float* e_ref = I.n_e == 3 ? I.e[(cur + 2) % 3] : nullptr;
-  walls_cell<T>(I.w, I.codes + size_t(t) * I.w.q, e_ref, gw - I.first_warp, threadIdx.x & 31);
+  walls_chunk<T>(I.w, I.codes + size_t(t) * I.w.q, e_ref, b - I.first_block, part_s);
 }
 
 template <typename T>
@@ -283,10 +315,9 @@ inline unsigned blocks_for(int64_t n, int per) { return unsigned((n + per - 1) /
 
 template <typename T>
 cudaError_t walls_t(const WallArgs& a, cudaStream_t s) {
-  int cells = 0;
-  for (int k = 0; k < a.nseg; ++k) cells += a.seg[k].count;
-  if (cells == 0) return cudaSuccess;
-  k_walls<T><<<blocks_for(int64_t(cells) * 32, 256), 256, 0, s>>>(a);
+  const int chunks = wall_chunks(a);
+  if (chunks == 0) return cudaSuccess;
+  k_walls<T><<<chunks, 32 * kWallWarps, 0, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -302,16 +333,17 @@ cudaError_t periodic_t(const PeriodicArgs& a, cudaStream_t s) {
 
 }  // namespace
 
-cudaError_t launch_walls_batch(int storage, const BatchWalls* b, int n, int total_warps, int t,
+cudaError_t launch_walls_batch(int storage, const BatchWalls* b, int n, int total_blocks, int t,
                                cudaStream_t s) {
-  if (total_warps <= 0) return cudaSuccess;
-  const unsigned g = blocks_for(int64_t(total_warps) * 32, 256);
+  if (total_blocks <= 0) return cudaSuccess;
   if (storage == WLBM_STORE_BF16_DEV)
-    k_walls_batch<__nv_bfloat16><<<g, 256, 0, s>>>(b, n, t);
+    k_walls_batch<__nv_bfloat16><<<total_blocks, 32 * kWallWarps, 0, s>>>(b, n, t);
   else
-    k_walls_batch<float><<<g, 256, 0, s>>>(b, n, t);
+    k_walls_batch<float><<<total_blocks, 32 * kWallWarps, 0, s>>>(b, n, t);
   return cudaGetLastError();
 }
+
+int wall_blocks(const WallArgs& a) { return wall_chunks(a); }
 
 cudaError_t launch_walls(int storage, const WallArgs& a, cudaStream_t s) {
   return storage == WLBM_STORE_BF16_DEV ? walls_t<__nv_bfloat16>(a, s) : walls_t<float>(a, s);

@@ -210,12 +210,13 @@ __device__ __forceinline__ bool run_kind(int& j, int end, Regs3& t, DirCtx<T>& c
   return true;
 }
 
+// One 128 x 14 tile (bx, by) of one grid; `tmap` is the generic address of the planes'
+// tensor map (kernel parameter or global memory), `smem` the block's dynamic shared memory.
 template <typename T, int S, bool FIELD_W, bool REF>
-__global__ void __maxnreg__(128)
-    k_step_tma(const StepArgs a, const __grid_constant__ CUtensorMap tmap) {
+__device__ __forceinline__ void step_tma_tile(const StepArgs& a, const void* tmap, int bx,
+                                              int by, unsigned char* smem) {
   using LY = TmaLayout<T, S>;
   constexpr int V = LY::V;
-  extern __shared__ __align__(128) unsigned char smem[];
   // smem: S ring stages of [kRows3][BW] elements (stride kStage), the bfloat16 W E
   // scratch, the barriers, the direction table
   float* fscr = reinterpret_cast<float*>(smem + LY::off_f);
@@ -225,8 +226,8 @@ __global__ void __maxnreg__(128)
 
   const int lane = threadIdx.x, ty = threadIdx.y;
   const int tid = ty * 32 + lane, nthr = 32 * (kWarps3 + 1);
-  const int col0 = kGhostCol + int(blockIdx.x) * kTW3;
-  const int row0 = 1 + int(blockIdx.y) * kRows3;
+  const int col0 = kGhostCol + bx * kTW3;
+  const int row0 = 1 + by * kRows3;
   const int nrows = min(kRows3, a.ny + 2 - row0 + 1);   // rows row0 .. ny+2 are computed
   const int nwarps = (nrows + kRPW - 1) / kRPW;         // consumer warps with rows
 
@@ -267,7 +268,7 @@ __global__ void __maxnreg__(128)
       }
       const Dir3 d = table[i];
       mbar_expect(&full[st], LY::kBoxBytes);
-      tma_load_3d(smem + st * LY::kStage, &tmap, col0 - V, row0 + d.dy, int(d.z), &full[st]);
+      tma_load_3d(smem + st * LY::kStage, tmap, col0 - V, row0 + d.dy, int(d.z), &full[st]);
     }
     return;
   }
@@ -367,13 +368,55 @@ __global__ void __maxnreg__(128)
   }
 }
 
+template <typename T, int S, bool FIELD_W, bool REF>
+__global__ void __maxnreg__(128)
+    k_step_tma(const StepArgs a, const __grid_constant__ CUtensorMap tmap) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  step_tma_tile<T, S, FIELD_W, REF>(a, &tmap, int(blockIdx.x), int(blockIdx.y), smem);
+}
+
+// Batched form: block b belongs to the instance whose first_tile is the largest one <= b;
+// the instance's tensor map sits in global memory.
+template <typename T, int S, bool REF>
+__global__ void __maxnreg__(128) k_step_tma_batch(const BatchInst* insts, int n, int t) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ StepArgs sa;
+  __shared__ const void* tm;
+  __shared__ int tile[2];
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    int lo = 0, hi = n - 1;
+    const int b = int(blockIdx.x);
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (insts[mid].first_tile <= b) lo = mid;
+      else hi = mid - 1;
+    }
+    const BatchInst& I = insts[lo];
+    sa = I.a;
+    sa.codes = I.codes + size_t(t) * I.a.q;
+    sa.order = I.order + size_t(t) * (I.a.q + 17);
+    const int cur = (I.phase + t) % I.n_e;
+    sa.e_in = I.e[cur];
+    sa.e_out = I.e[(cur + 1) % I.n_e];
+    sa.e_ref = I.n_e == 3 ? I.e[(cur + 2) % 3] : nullptr;
+    tm = I.tmap;
+    const int local = b - I.first_tile;
+    tile[0] = local % I.tiles_x;
+    tile[1] = local / I.tiles_x;
+  }
+  __syncthreads();
+  if (sa.wfield) step_tma_tile<T, S, true, REF>(sa, tm, tile[0], tile[1], smem);
+  else step_tma_tile<T, S, false, REF>(sa, tm, tile[0], tile[1], smem);
+}
+
 template <typename T, int S>
 cudaError_t configure_tma_t() {
   const int bytes = int(TmaLayout<T, S>::bytes(kMaxQ));
-  const void* fns[2] = {(const void*)k_step_tma<T, S, false, sizeof(T) == 2>,
-                        (const void*)k_step_tma<T, S, true, sizeof(T) == 2>};
+  const void* fns[3] = {(const void*)k_step_tma<T, S, false, sizeof(T) == 2>,
+                        (const void*)k_step_tma<T, S, true, sizeof(T) == 2>,
+                        (const void*)k_step_tma_batch<T, S, sizeof(T) == 2>};
   cudaError_t e = cudaSuccess;
-  for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+  for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
     e = cudaFuncSetAttribute(fns[k], cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     // several blocks per SM: ask for the largest shared-memory carveout
     if (e == cudaSuccess)
@@ -405,6 +448,24 @@ cudaError_t configure_step_tma() {
   if (e == cudaSuccess) e = configure_tma_t<__nv_bfloat16, kStagesBF16>();
   return e;
 }
+
+cudaError_t launch_step_tma_batch(int storage, const BatchInst* insts, int n, int max_q,
+                                  int total_tiles, int t, cudaStream_t s) {
+  if (total_tiles <= 0) return cudaSuccess;
+  const dim3 block(32, kWarps3 + 1);
+  if (storage == WLBM_STORE_BF16_DEV) {
+    using LY = TmaLayout<__nv_bfloat16, kStagesBF16>;
+    k_step_tma_batch<__nv_bfloat16, kStagesBF16, true>
+        <<<total_tiles, block, LY::bytes(max_q), s>>>(insts, n, t);
+  } else {
+    using LY = TmaLayout<float, kStagesF32>;
+    k_step_tma_batch<float, kStagesF32, false><<<total_tiles, block, LY::bytes(max_q), s>>>(insts, n, t);
+  }
+  return cudaGetLastError();
+}
+
+int tma_tile_width() { return kTW3; }
+int tma_tile_rows() { return kRows3; }
 
 cudaError_t launch_step_tma(int storage, const StepArgs& a, cudaStream_t s) {
   const CUtensorMap& tm = *static_cast<const CUtensorMap*>(a.tmap);

@@ -427,6 +427,7 @@ wlbm_status wlbm_create(const wlbm_grid* grid, const float* mfp_cells, double mf
   h->d_red = static_cast<double*>(h->dev_alloc(8 * sizeof(double)));
   h->d_status = static_cast<int*>(h->dev_alloc(256));
   if (h->planes) h->has_tmap = make_plane_tensor_map(h->tmap, h->planes, h->storage, g, &h->tmap_why);
+  if (h->has_tmap) h->step_variant = 3;   // the fastest step kernel where it applies
   if (h->field_w) h->wfield = static_cast<float*>(h->dev_alloc(size_t(g.plane) * 4));
   if (!h->planes || !h->e[0] || !h->e[1] || (n_e == 3 && !h->e[2]) || !h->consts ||
       !h->d_codes || !h->d_order || !h->d_red || !h->d_status ||
@@ -524,7 +525,9 @@ static wlbm_status enqueue_steps(wlbm_handle* h, int count, bool profile) {
   const Geom& g = h->g;
   const bool any_wall = h->walls.nseg > 0;
   // both axes periodic: the step kernel mirrors the edges itself (grids of 2+ cells)
-  const bool wrap = h->fuse_periodic && h->xper && h->yper && g.nx >= 2 && g.ny >= 2;
+  // (variant 3 has no mirror stores: there the separate periodic pass runs)
+  const bool wrap = h->fuse_periodic && h->step_variant != 3 && h->xper && h->yper &&
+                    g.nx >= 2 && g.ny >= 2;
   const bool any_per = (h->xper || h->yper) && !wrap;
   wlbm_status st = WLBM_OK;
   for (int t = 0; t < count; ++t) {
@@ -646,6 +649,15 @@ wlbm_status wlbm_step(wlbm_handle* h, int64_t n) {
     h->slot ^= 1;
     n -= ch;
   }
+  return WLBM_OK;
+}
+
+wlbm_status wlbm_get_option(const wlbm_handle* h, int32_t key, int64_t* value) {
+  if (!h || !value) return WLBM_ERR_INVALID_ARG;
+  if (key == WLBM_OPT_STEP_VARIANT) *value = h->step_variant;
+  else if (key == WLBM_OPT_GRAPH_STEPS) *value = h->graph_steps;
+  else if (key == WLBM_OPT_FUSE_PERIODIC) *value = h->fuse_periodic;
+  else return WLBM_ERR_INVALID_ARG;
   return WLBM_OK;
 }
 
@@ -999,13 +1011,18 @@ struct wlbm_batch {
   BatchInst* d_inst = nullptr;
   BatchWalls* d_walls = nullptr;
   uint8_t* d_codes = nullptr;
+  uint16_t* d_order = nullptr;      // [instance][t][q + 17] kind-sorted directions
+  unsigned char* d_tmaps = nullptr; // [instance] 128-byte CUtensorMaps (variant 3)
+  bool all_tmap = false;            // every instance has a tensor map
+  int max_q = 0;
   BatchInst* h_inst = nullptr;      // pinned staging
   BatchWalls* h_walls = nullptr;
   uint8_t* h_codes = nullptr;
+  uint16_t* h_order = nullptr;
   cudaEvent_t ev = nullptr;
-  std::vector<size_t> code_off;
-  size_t code_bytes = 0;
-  int total_tiles = 0, total_wall_warps = 0;
+  std::vector<size_t> code_off, order_off;   // order_off in uint16 elements
+  size_t code_bytes = 0, order_elems = 0;
+  int total_tiles = 0, total_wall_blocks = 0;
   std::vector<int> per;             // instances whose periodic edges need their own launch
   // Captured chunks, keyed by the energy-plane phases of the instances in `per` (their
   // periodic launches bake plane pointers; the batched kernels read phases at run time).
@@ -1062,6 +1079,8 @@ struct wlbm_batch {
     if (h_inst) cudaFreeHost(h_inst);
     if (h_walls) cudaFreeHost(h_walls);
     if (h_codes) cudaFreeHost(h_codes);
+    if (h_order) cudaFreeHost(h_order);
+    h_order = nullptr;
     if (ev) cudaEventDestroy(ev);
     for (cudaEvent_t e : prof_ev) cudaEventDestroy(e);
     h_inst = nullptr; h_walls = nullptr; h_codes = nullptr; ev = nullptr;
@@ -1069,9 +1088,10 @@ struct wlbm_batch {
     for (wlbm_handle* x : h) wlbm_destroy(x);
     h.clear();
   }
-  // Both axes periodic and fused: the step kernel mirrors the edges of that instance.
+  // Both axes periodic and fused: the step kernel mirrors the edges of that instance
+  // (not in variant 3, which has no mirror stores).
   bool wraps(const wlbm_handle* x) const {
-    return fuse_periodic && x->xper && x->yper && x->g.nx >= 2 && x->g.ny >= 2;
+    return fuse_periodic && variant != 3 && x->xper && x->yper && x->g.nx >= 2 && x->g.ny >= 2;
   }
   void classify() {
     per.clear();
@@ -1081,16 +1101,17 @@ struct wlbm_batch {
   // Block and warp offsets of every instance in the batched grids.
   void layout() {
     total_tiles = 0;
-    total_wall_warps = 0;
-    const int tw = step_tile_width(storage, variant);
+    total_wall_blocks = 0;
+    const int tw = variant == 3 ? tma_tile_width() : step_tile_width(storage, variant);
+    const int th = variant == 3 ? tma_tile_rows() : kStepRows;
     for (size_t k = 0; k < h.size(); ++k) {
       const Geom& g = h[k]->g;
-      const int tx = (g.nx + 2 + tw - 1) / tw, ty = (g.ny + 2 + kStepRows - 1) / kStepRows;
+      const int tx = (g.nx + 2 + tw - 1) / tw, ty = (g.ny + 2 + th - 1) / th;
       h_inst[k].tiles_x = tx;
       h_inst[k].first_tile = total_tiles;
       total_tiles += tx * ty;
-      h_walls[k].first_warp = total_wall_warps;
-      for (int s = 0; s < h[k]->walls.nseg; ++s) total_wall_warps += h[k]->walls.seg[s].count;
+      h_walls[k].first_block = total_wall_blocks;
+      total_wall_blocks += wall_blocks(h[k]->walls);
     }
   }
 };
@@ -1127,20 +1148,33 @@ wlbm_status wlbm_batch_create(int32_t n, const wlbm_grid* grids, const float* co
   b->storage = grids[0].storage;
   b->classify();
   b->code_off.resize(n);
+  b->order_off.resize(n);
+  b->all_tmap = true;
   for (int k = 0; k < n; ++k) {
     b->code_off[k] = b->code_bytes;
     b->code_bytes += size_t(kBatchChunk) * grids[k].q;
+    b->order_off[k] = b->order_elems;
+    b->order_elems += size_t(kBatchChunk) * (grids[k].q + 17);
+    b->max_q = std::max(b->max_q, int(grids[k].q));
+    b->all_tmap = b->all_tmap && b->h[k]->has_tmap;
   }
   b->d_codes = static_cast<uint8_t*>(b->dev_alloc(b->code_bytes));
+  b->d_order = static_cast<uint16_t*>(b->dev_alloc(b->order_elems * 2));
+  b->d_tmaps = static_cast<unsigned char*>(b->dev_alloc(size_t(n) * 128));
   b->d_inst = static_cast<BatchInst*>(b->dev_alloc(sizeof(BatchInst) * n));
   b->d_walls = static_cast<BatchWalls*>(b->dev_alloc(sizeof(BatchWalls) * n));
-  if (!b->d_codes || !b->d_inst || !b->d_walls)
+  if (!b->d_codes || !b->d_order || !b->d_tmaps || !b->d_inst || !b->d_walls)
     return bad(WLBM_ERR_OOM, "wlbm_batch_create: device allocation failed");
   cudaError_t e = cudaHostAlloc(reinterpret_cast<void**>(&b->h_codes), b->code_bytes,
                                 cudaHostAllocDefault);
   if (e == cudaSuccess)
+    e = cudaHostAlloc(reinterpret_cast<void**>(&b->h_order), b->order_elems * 2,
+                      cudaHostAllocDefault);
+  if (e == cudaSuccess)
     e = cudaHostAlloc(reinterpret_cast<void**>(&b->h_inst), sizeof(BatchInst) * n,
                       cudaHostAllocDefault);
+  for (int k = 0; k < n && e == cudaSuccess && b->all_tmap; ++k)
+    e = cudaMemcpy(b->d_tmaps + size_t(k) * 128, b->h[k]->tmap, 128, cudaMemcpyHostToDevice);
   if (e == cudaSuccess)
     e = cudaHostAlloc(reinterpret_cast<void**>(&b->h_walls), sizeof(BatchWalls) * n,
                       cudaHostAllocDefault);
@@ -1150,6 +1184,10 @@ wlbm_status wlbm_batch_create(int32_t n, const wlbm_grid* grids, const float* co
     return bad(WLBM_ERR_CUDA, std::string("wlbm_batch_create: ") + cudaGetErrorString(e));
   }
   std::memset(b->h_inst, 0, sizeof(BatchInst) * n);
+  if (b->all_tmap) {
+    b->variant = 3;
+    b->classify();
+  }
   std::memset(b->h_walls, 0, sizeof(BatchWalls) * n);
   b->layout();
   *out = b;
@@ -1183,11 +1221,24 @@ wlbm_status wlbm_batch_init_temperature(wlbm_batch* b, const float* const* dT) {
   return WLBM_OK;
 }
 
+wlbm_status wlbm_batch_get_option(const wlbm_batch* b, int32_t key, int64_t* value) {
+  if (!b || !value) return WLBM_ERR_INVALID_ARG;
+  if (key == WLBM_OPT_STEP_VARIANT) *value = b->variant;
+  else if (key == WLBM_OPT_GRAPH_STEPS) *value = b->graph_steps;
+  else if (key == WLBM_OPT_FUSE_PERIODIC) *value = b->fuse_periodic;
+  else return WLBM_ERR_INVALID_ARG;
+  return WLBM_OK;
+}
+
 wlbm_status wlbm_batch_set_option(wlbm_batch* b, int32_t key, int64_t value) {
   if (!b) return WLBM_ERR_INVALID_ARG;
-  if (key == WLBM_OPT_STEP_VARIANT && (value == 0 || value == 1)) {
+  if (key == WLBM_OPT_STEP_VARIANT && value == 3 && !b->all_tmap)
+    return b->fail(WLBM_ERR_INVALID_ARG,
+                   "wlbm_batch_set_option: step variant 3 needs a tensor map of every instance");
+  if (key == WLBM_OPT_STEP_VARIANT && (value == 0 || value == 1 || value == 3)) {
     b->variant = int(value);
     b->layout();
+    b->classify();
     b->drop_graph();
     return WLBM_OK;
   }
@@ -1212,8 +1263,8 @@ static wlbm_status batch_enqueue(wlbm_batch* b, int count, bool profile) {
   const int n = int(b->h.size());
   wlbm_status st = WLBM_OK;
   for (int t = 0; t < count && st == WLBM_OK; ++t) {
-    if (b->total_wall_warps > 0) {
-      st = b->cuda(launch_walls_batch(b->storage, b->d_walls, n, b->total_wall_warps, t, b->stream),
+    if (b->total_wall_blocks > 0) {
+      st = b->cuda(launch_walls_batch(b->storage, b->d_walls, n, b->total_wall_blocks, t, b->stream),
                    "wlbm_batch_step: walls");
       ++b->launches;
     }
@@ -1247,8 +1298,12 @@ static wlbm_status batch_enqueue(wlbm_batch* b, int count, bool profile) {
       b->prof_used += 2;
     }
     if (st == WLBM_OK)
-      st = b->cuda(launch_step_batch(b->storage, b->variant, b->d_inst, n, b->total_tiles, t,
-                                     b->stream), "wlbm_batch_step: step");
+      st = b->cuda(b->variant == 3
+                       ? launch_step_tma_batch(b->storage, b->d_inst, n, b->max_q,
+                                               b->total_tiles, t, b->stream)
+                       : launch_step_batch(b->storage, b->variant, b->d_inst, n, b->total_tiles,
+                                           t, b->stream),
+                   "wlbm_batch_step: step");
     ++b->launches;
     if (st == WLBM_OK && e1) st = b->cuda(cudaEventRecord(e1, b->stream), "profiling");
   }
@@ -1270,7 +1325,11 @@ wlbm_status wlbm_batch_step(wlbm_batch* b, int64_t n) {
       wlbm_handle* x = b->h[k];
       const Geom& g = x->g;
       uint8_t* hc = b->h_codes + b->code_off[k];
-      for (int t = 0; t < ch; ++t) tas_advance(x->lat, &x->tas, hc + size_t(t) * g.q);
+      uint16_t* ho = b->h_order + b->order_off[k];
+      for (int t = 0; t < ch; ++t) {
+        tas_advance(x->lat, &x->tas, hc + size_t(t) * g.q);
+        sort_by_kind(hc + size_t(t) * g.q, g.q, ho + size_t(t) * (g.q + 17));
+      }
       BatchInst& I = b->h_inst[k];
       StepArgs& a = I.a;
       a = StepArgs{};
@@ -1283,6 +1342,8 @@ wlbm_status wlbm_batch_step(wlbm_batch* b, int64_t n) {
       a.wrap = b->wraps(x);
       for (int j = 0; j < 3; ++j) I.e[j] = x->e[j];
       I.codes = b->d_codes + b->code_off[k];
+      I.order = b->d_order + b->order_off[k];
+      I.tmap = b->d_tmaps + size_t(k) * 128;
       I.n_e = x->bf16() ? 3 : 2;
       I.phase = x->e_cur;
       BatchWalls& Wk = b->h_walls[k];
@@ -1294,6 +1355,9 @@ wlbm_status wlbm_batch_step(wlbm_batch* b, int64_t n) {
     }
     st = b->cuda(cudaMemcpyAsync(b->d_codes, b->h_codes, b->code_bytes, cudaMemcpyHostToDevice,
                                  b->stream), "wlbm_batch_step: upload");
+    if (st == WLBM_OK)
+      st = b->cuda(cudaMemcpyAsync(b->d_order, b->h_order, b->order_elems * 2,
+                                   cudaMemcpyHostToDevice, b->stream), "wlbm_batch_step: upload");
     if (st == WLBM_OK)
       st = b->cuda(cudaMemcpyAsync(b->d_inst, b->h_inst, sizeof(BatchInst) * ni,
                                    cudaMemcpyHostToDevice, b->stream), "wlbm_batch_step: upload");
@@ -1371,14 +1435,15 @@ wlbm_status wlbm_batch_autotune(wlbm_batch* b, int32_t trial_steps, int32_t* var
                                 int32_t* graph_steps, double* ms_per_step) {
   if (!b || trial_steps < 6) return WLBM_ERR_INVALID_ARG;
   const int g = std::min(kBatchChunk, (trial_steps / 6) * 6);
-  const int cand[4][2] = {{1, 0}, {0, 0}, {1, g}, {0, g}};
+  const int cand[6][2] = {{1, 0}, {0, 0}, {3, 0}, {1, g}, {0, g}, {3, g}};
   double best = 1e300;
   int bv = 1, bg = 0;
   cudaEvent_t e0, e1;
   wlbm_status st = b->cuda(cudaEventCreate(&e0), "autotune");
   if (st != WLBM_OK) return st;
   st = b->cuda(cudaEventCreate(&e1), "autotune");
-  for (int c = 0; c < 4 && st == WLBM_OK; ++c) {
+  for (int c = 0; c < 6 && st == WLBM_OK; ++c) {
+    if (cand[c][0] == 3 && !b->all_tmap) continue;
     st = wlbm_batch_set_option(b, WLBM_OPT_STEP_VARIANT, cand[c][0]);
     if (st == WLBM_OK) st = wlbm_batch_set_option(b, WLBM_OPT_GRAPH_STEPS, cand[c][1]);
     if (st == WLBM_OK) st = wlbm_batch_step(b, g > 0 ? g : 6);           // warm-up / capture

@@ -200,6 +200,8 @@ struct BatchInst {
   int phase;              // index of the current energy plane at the start of the chunk
   int tiles_x;            // step-kernel tiles per row
   int first_tile;         // first block of this instance in the batched grid
+  const uint16_t* order;  // variant 3: kind-sorted directions of the chunk, [t][q + 17]
+  const void* tmap;       // variant 3: device address of the instance's CUtensorMap
 };
 
 struct BatchWalls {
@@ -207,7 +209,7 @@ struct BatchWalls {
   float* e[3];
   const uint8_t* codes;
   int n_e, phase;
-  int first_warp;         // first warp of this instance in the batched wall grid
+  int first_block;        // first block of this instance in the batched wall grid
 };
 
 // Reverse-step arguments (float32 storage only).
@@ -235,13 +237,19 @@ cudaError_t prepare_step_kernels();   // per-device kernel attributes; call befo
 // `out`, 128 bytes, 64-byte aligned; false with a reason when it cannot be made).
 cudaError_t configure_step_tma();
 cudaError_t launch_step_tma(int storage, const StepArgs& a, cudaStream_t s);
+// Batched variant 3 (one block per 128 x 14 tile of every instance) and its tile shape.
+cudaError_t launch_step_tma_batch(int storage, const BatchInst* insts, int n, int max_q,
+                                  int total_tiles, int t, cudaStream_t s);
+int tma_tile_width();
+int tma_tile_rows();
 bool make_plane_tensor_map(void* out, void* planes, int storage, const Geom& g,
                            std::string* why);
 // Batched launches (one launch per step for all instances of a batch).
 int step_tile_width(int storage, int variant);
 cudaError_t launch_step_batch(int storage, int variant, const BatchInst* insts, int n,
                               int total_tiles, int t, cudaStream_t s);
-cudaError_t launch_walls_batch(int storage, const BatchWalls* b, int n, int total_warps, int t,
+int wall_blocks(const WallArgs& a);   // blocks of the wall pass of one grid (32 cells each)
+cudaError_t launch_walls_batch(int storage, const BatchWalls* b, int n, int total_blocks, int t,
                                cudaStream_t s);
 cudaError_t launch_walls(int storage, const WallArgs& a, cudaStream_t s);
 cudaError_t launch_periodic(int storage, const PeriodicArgs& a, cudaStream_t s);

@@ -67,6 +67,7 @@ def _load():
         "wlbm_adjoint_forward": (C.c_int, [vp, vp, i64, i32]),
         "wlbm_adjoint_backward": (C.c_int, [vp, vp, vp, C.POINTER(dbl), vp]),
         "wlbm_set_option": (C.c_int, [vp, i32, i64]),
+        "wlbm_get_option": (C.c_int, [vp, i32, C.POINTER(C.c_int64)]),
         "wlbm_autotune": (C.c_int, [vp, i32, C.POINTER(i32), C.POINTER(i32), C.POINTER(dbl)]),
         "wlbm_batch_create": (C.c_int, [i32, C.POINTER(wlbm_grid), C.POINTER(vp), C.POINTER(dbl),
                                         C.POINTER(wlbm_boundary), C.POINTER(wlbm_allocator), vp,
@@ -77,6 +78,7 @@ def _load():
         "wlbm_batch_instance": (vp, [vp, i32]),
         "wlbm_batch_init_temperature": (C.c_int, [vp, C.POINTER(vp)]),
         "wlbm_batch_set_option": (C.c_int, [vp, i32, i64]),
+        "wlbm_batch_get_option": (C.c_int, [vp, i32, C.POINTER(C.c_int64)]),
         "wlbm_batch_step": (C.c_int, [vp, i64]),
         "wlbm_batch_profile": (C.c_int, [vp, i32]),
         "wlbm_batch_profile_read": (C.c_int, [vp, C.POINTER(dbl), C.POINTER(i64),
@@ -235,6 +237,11 @@ class WormLBM:
     def wlbm_set_option(self, key, value):
         _check(lib.wlbm_set_option(self.h, int(key), int(value)), self.h)
 
+    def wlbm_get_option(self, key):
+        v = C.c_int64()
+        _check(lib.wlbm_get_option(self.h, int(key), C.byref(v)), self.h)
+        return v.value
+
     def wlbm_autotune(self, trial_steps=48):
         """Native search over step-kernel variant x CUDA-graph replay (advances the state:
         call before wlbm_init_temperature).  Returns (variant, graph_steps, ms/step)."""
@@ -358,6 +365,11 @@ class WormLBMBatch:
 
     def wlbm_batch_set_option(self, key, value):
         _batch_check(lib.wlbm_batch_set_option(self.b, int(key), int(value)), self.b)
+
+    def wlbm_batch_get_option(self, key):
+        v = C.c_int64()
+        _batch_check(lib.wlbm_batch_get_option(self.b, int(key), C.byref(v)), self.b)
+        return v.value
 
     def wlbm_batch_profile(self, enable=True):
         _batch_check(lib.wlbm_batch_profile(self.b, 1 if enable else 0), self.b)

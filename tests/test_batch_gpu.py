@@ -1,7 +1,8 @@
 """Batched launches: a batch of uneven grids (different sizes, Q, walls, MFP fields)
 stepped by one wall launch and one step launch per step must give, bit for bit, the
-states of the same grids stepped one by one (same tile code, same arithmetic), for both
-step-kernel variants, with and without CUDA-graph replay, in float32 and bfloat16."""
+states of the same grids stepped one by one with the same step-kernel variant (same tile
+code, same arithmetic), for every batched variant, with and without CUDA-graph replay, in
+float32 and bfloat16."""
 import numpy as np
 import pytest
 
@@ -34,11 +35,12 @@ def _dTs(specs):
     return [W.random_dT(s["nx"], s["ny"], seed=11 + k, scale=0.5) for k, s in enumerate(specs)]
 
 
-def _single(spec, dT, steps, storage, fuse=0):
+def _single(spec, dT, steps, storage, fuse=0, variant=3):
     import paper_1911_00180_gb300 as wl
     h = wl.WormLBM(spec["nx"], spec["ny"], spec["q"], mfp=spec.get("mfp"),
                    mfp_field=spec.get("mfp_field"), bc=spec["bc"], t_wall=spec["t_wall"],
                    storage=storage)
+    h.wlbm_set_option(wl.wlbm.OPT_STEP_VARIANT, variant)
     h.wlbm_set_option(wl.wlbm.OPT_FUSE_PERIODIC, fuse)
     h.wlbm_init_temperature(dT)
     h.wlbm_step(steps)
@@ -49,7 +51,8 @@ def _single(spec, dT, steps, storage, fuse=0):
 
 @pytest.mark.parametrize("storage", [0, 1])
 @pytest.mark.parametrize("variant,graph,fuse", [(1, 0, 0), (0, 0, 0), (1, 12, 0), (0, 12, 0),
-                                                (1, 0, 1), (1, 12, 1)])
+                                                (1, 0, 1), (1, 12, 1), (3, 0, 0), (3, 12, 0),
+                                                (3, 0, 1)])
 def test_batch_equals_single_grids_bitwise(storage, variant, graph, fuse):
     """37 steps = three 12-step graph replays and one single step; the second call starts
     the graph chunks on another energy-plane phase (a second captured graph)."""
@@ -66,7 +69,7 @@ def test_batch_equals_single_grids_bitwise(storage, variant, graph, fuse):
     got = [v.wlbm_get_state().cpu().numpy() for v in b.instances]
     b.close()
     for k, (spec, dT) in enumerate(zip(specs, dTs)):
-        want = _single(spec, dT, 61, storage, fuse)
+        want = _single(spec, dT, 61, storage, fuse, variant)
         assert np.array_equal(got[k], want), k
 
 
@@ -77,13 +80,13 @@ def test_batch_autotune_then_run():
     dTs = _dTs(specs)
     b = wl.WormLBMBatch(specs, storage=1)
     rec = autotune.tune_batch(b, 1, trial_steps=12, use_cache=False)
-    assert rec["variant"] in (0, 1) and rec["graph_steps"] in (0, 12)
+    assert rec["variant"] in (0, 1, 3) and rec["graph_steps"] in (0, 12)
     b.wlbm_batch_init_temperature(dTs)
     b.wlbm_batch_step(20)
     got = [v.wlbm_get_state().cpu().numpy() for v in b.instances]
     b.close()
     for k, (spec, dT) in enumerate(zip(specs, dTs)):
-        assert np.array_equal(got[k], _single(spec, dT, 20, 1)), k
+        assert np.array_equal(got[k], _single(spec, dT, 20, 1, 0, rec["variant"])), k
 
 
 def test_single_grid_autotune_keeps_results():
@@ -100,4 +103,4 @@ def test_single_grid_autotune_keeps_results():
     h.wlbm_step(30)
     got = h.wlbm_get_state().cpu().numpy()
     h.close()
-    assert np.array_equal(got, _single(spec, dT, 30, 1))
+    assert np.array_equal(got, _single(spec, dT, 30, 1, 0, v))

@@ -105,8 +105,14 @@ def test_step_kernel_variants_bitwise_equal(storage, fuse):
         h.close()
     for k in (1, 2):
         assert np.array_equal(out[0], out[k]), k
+    # Variant 3 never fuses the mirrors: it runs the periodic pass before each step, so
+    # after a step its periodic ghost ring holds the step's own outputs where the fused
+    # variants hold mirror images.  Ghost cells of periodic axes are copies (rewritten
+    # before the next step), not state: with fusion on, compare the interior.
+    sl = (slice(None), slice(1, -1), slice(1, -1)) if fuse else (slice(None),) * 3
     scale = float(np.abs(out[0]).max())
-    assert np.abs(out[3] - out[0]).max() <= (TOL32 if storage == 0 else TOL16_STATE) * scale
+    tol = (TOL32 if storage == 0 else TOL16_STATE) * scale
+    assert np.abs(out[3][sl] - out[0][sl]).max() <= tol
 
 
 @pytest.mark.parametrize("storage,tol,stol", [(0, TOL32, None), (1, TOL16, TOL16_STATE)])
