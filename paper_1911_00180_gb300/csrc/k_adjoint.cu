@@ -19,7 +19,6 @@ namespace wlbm {
 
 namespace {
 
-constexpr int kAdjTY = 8;   // rows (warps) per block, one cell per lane
 
 __device__ __forceinline__ float w_at(const AdjArgs& a, int r, int c) {
   if (a.wfield) return a.wfield[int64_t(r) * a.pitch + c];
@@ -30,53 +29,166 @@ __device__ __forceinline__ float w_at(const AdjArgs& a, int r, int c) {
   return a.w0;
 }
 
-// Two passes over the Q adjoint planes per cell: sigma first, then l~ and dJ/dW.  The
-// second pass re-reads what the first one read moments earlier (an L2 hit for a tile of
-// 32 x 8 cells).
-__global__ void __launch_bounds__(32 * kAdjTY) k_adj_step(const AdjArgs a) {
+// One pass over the Q adjoint planes.  A thread owns 4 consecutive cells of a row (a warp
+// 128 cells, a block 8 rows).  With the output adjoint l' = lh' + s' (s' of the 3 x 6 cells
+// around the thread's cells in registers) it reads b_k = l'_k(x + c_k), u_k = l'_k(x) for
+// paused k and d~_k(x) with 16-byte loads (a shifted row piece from two aligned ones), writes
+// lh_k = (1 - W) a_k at once and, after the directions, s = W sigma: no plane is read
+// twice and nothing waits for sigma.  dJ/dW = sum_k d~_k (sigma - a_k) is accumulated
+// shifted by a_0 (the first direction's a), as (sigma - a_0) sum_k d~_k -
+// sum_k d~_k (a_k - a_0): near an isotropic adjoint every a_k is close to sigma and to a_0,
+// so neither term is much larger than the result.  Cells past the right ghost column are
+// neither read for output nor written (their pads stay zero).
+constexpr int kAdjRows = 8;
+constexpr int kAdjTW = 128;   // cells of a row per warp
+
+__device__ __forceinline__ float4 ld4(const float* p) {
+  return __ldcs(reinterpret_cast<const float4*>(p));
+}
+
+// l'_k at the 4 cells shifted by DX (-1, 0, +1) from a 16-byte aligned row position p.
+template <int DX>
+__device__ __forceinline__ void row4(const float* p, float (&v)[4]) {
+  if constexpr (DX == 0) {
+    const float4 m = ld4(p);
+    v[0] = m.x; v[1] = m.y; v[2] = m.z; v[3] = m.w;
+  } else if constexpr (DX < 0) {
+    const float4 l = ld4(p - 4), m = ld4(p);
+    v[0] = l.w; v[1] = m.x; v[2] = m.y; v[3] = m.z;
+  } else {
+    const float4 m = ld4(p), r = ld4(p + 4);
+    v[0] = m.y; v[1] = m.z; v[2] = m.w; v[3] = r.x;
+  }
+}
+
+struct AdjAcc {
+  float sigma[4], a0[4], ed[4], pd[4], h[4];
+};
+
+// Wall index of an isothermal wall cell (r, c), or -1.
+__device__ __forceinline__ int iso_wall_of(const AdjArgs& a, int r, int c) {
+  const bool xl = c == kGhostCol, xr = c == kX0 + a.nx, yb = r == 1, yt = r == a.ny + 2;
+  if ((xl || xr) && (yb || yt)) return a.iso_corner[(yt ? 2 : 0) + (xr ? 1 : 0)];
+  if (xl) return a.iso_side[0];
+  if (xr) return a.iso_side[1];
+  if (yb) return a.iso_side[2];
+  if (yt) return a.iso_side[3];
+  return -1;
+}
+
+// One direction with hop (CX, CY) for the thread's 4 cells.
+template <int CX, int CY>
+__device__ __forceinline__ void adj_dir(AdjAcc& t, const float (&sr)[3][6], const float (&keep)[4],
+                                        const float* pl, const float* pdt, float* po,
+                                        int pitch, float wk, bool paused, bool first,
+                                        int nvalid, bool harvest) {
+  float b[4], av[4];
+  row4<CX>(pl + int64_t(CY) * pitch, b);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) b[j] += sr[1 + CY][1 + CX + j];
+  if (paused) {
+    row4<0>(pl, av);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) av[j] += sr[1][1 + j];
+  } else {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) av[j] = b[j];
+  }
+  const float4 d = ld4(pdt);
+  const float dv[4] = {d.x, d.y, d.z, d.w};
+  float o[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    t.sigma[j] = fmaf(wk, b[j], t.sigma[j]);
+    if (first) t.a0[j] = av[j];
+    t.ed[j] += dv[j];
+    t.pd[j] = fmaf(dv[j], av[j] - t.a0[j], t.pd[j]);
+    o[j] = keep[j] * av[j];
+    if (harvest) t.h[j] = fmaf(wk, av[j], t.h[j]);   // isothermal wall cells: W = 0, l = a
+  }
+  if (nvalid == 4) {
+    __stcs(reinterpret_cast<float4*>(po), make_float4(o[0], o[1], o[2], o[3]));
+  } else {
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (j < nvalid) po[j] = o[j];
+  }
+}
+
+__global__ void __launch_bounds__(32 * kAdjRows) k_adj_step(const AdjArgs a) {
   __shared__ float sw[kMaxQ];
   __shared__ uint8_t scode[kMaxQ];
-  const int tid = threadIdx.y * 32 + threadIdx.x;
-  for (int i = tid; i < a.q; i += 32 * kAdjTY) {
+  __shared__ float hwall[4];   // isothermal harvest of this block per wall
+  const int tid = threadIdx.y * 32 + threadIdx.x, nthr = 32 * kAdjRows;
+  for (int i = tid; i < a.q; i += nthr) {
     sw[i] = a.w[i];
     scode[i] = a.codes[i];
   }
+  if (tid < 4) hwall[tid] = 0.f;
   __syncthreads();
-  const int c = kGhostCol + blockIdx.x * 32 + threadIdx.x;
-  const int r = 1 + blockIdx.y * kAdjTY + threadIdx.y;
-  if (r > a.ny + 2 || c > kX0 + a.nx) return;
-  const int64_t off = int64_t(r) * a.pitch + c;
-  const float W = w_at(a, r, c);
-  constexpr int U = 8;
-  float sigma = 0.f;
-  for (int k0 = 0; k0 < a.q; k0 += U) {
-    float v[U];
+  const int c0 = kGhostCol + blockIdx.x * kAdjTW + 4 * threadIdx.x;
+  const int r = 1 + blockIdx.y * kAdjRows + threadIdx.y;
+  const int clast = kX0 + a.nx;
+  bool any_iso = false;
+  if (r <= a.ny + 2 && c0 <= clast) {
+    const int nvalid = min(4, clast - c0 + 1);
+    const int rows = a.ny + 4;
+    // s' around the cells (pads and past-the-frame cells read 0)
+    float sr[3][6];
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int k = k0 + u, hop = scode[k] & 7;
-      v[u] = a.lam_in[int64_t(k) * a.plane + off + int64_t(c_hop_y[hop]) * a.pitch + c_hop_x[hop]];
+    for (int rr = 0; rr < 3; ++rr)
+#pragma unroll
+      for (int cc = 0; cc < 6; ++cc) {
+        const int rw = r - 1 + rr, c = c0 - 1 + cc;
+        sr[rr][cc] = (rw < rows && c < a.pitch) ? a.s_in[int64_t(rw) * a.pitch + c] : 0.f;
+      }
+    // isothermal wall cells are transposed here: their new adjoint is 0 (keep = 0) and
+    // sum_k w_k a_k is harvested for the wall temperature
+    float W[4], keep[4];
+    int iso[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      W[j] = j < nvalid ? w_at(a, r, c0 + j) : 0.f;
+      iso[j] = j < nvalid ? iso_wall_of(a, r, c0 + j) : -1;
+      any_iso = any_iso || iso[j] >= 0;
+      keep[j] = iso[j] >= 0 ? 0.f : 1.f - W[j];
+    }
+    const int64_t off = int64_t(r) * a.pitch + c0;
+    AdjAcc t;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      t.sigma[j] = 0.f; t.a0[j] = 0.f; t.ed[j] = 0.f; t.pd[j] = 0.f; t.h[j] = 0.f;
+    }
+    for (int k = 0; k < a.q; ++k) {
+      const int code = scode[k];
+      const bool paused = code & 8;
+      const float* pl = a.lam_in + int64_t(k) * a.plane + off;
+      const float* pdt = a.dtil + int64_t(k) * a.plane + off;
+      float* po = a.lam_out + int64_t(k) * a.plane + off;
+      const float wk = sw[k];
+      const bool f = k == 0;
+      switch (code & 7) {   // hop numbering of the host lattice
+        case 0: adj_dir<1, 0>(t, sr, keep, pl, pdt, po, a.pitch, wk, paused, f, nvalid, any_iso); break;
+        case 1: adj_dir<0, 1>(t, sr, keep, pl, pdt, po, a.pitch, wk, paused, f, nvalid, any_iso); break;
+        case 2: adj_dir<-1, 0>(t, sr, keep, pl, pdt, po, a.pitch, wk, paused, f, nvalid, any_iso); break;
+        case 3: adj_dir<0, -1>(t, sr, keep, pl, pdt, po, a.pitch, wk, paused, f, nvalid, any_iso); break;
+        case 4: adj_dir<1, 1>(t, sr, keep, pl, pdt, po, a.pitch, wk, paused, f, nvalid, any_iso); break;
+        case 5: adj_dir<-1, 1>(t, sr, keep, pl, pdt, po, a.pitch, wk, paused, f, nvalid, any_iso); break;
+        case 6: adj_dir<-1, -1>(t, sr, keep, pl, pdt, po, a.pitch, wk, paused, f, nvalid, any_iso); break;
+        default: adj_dir<1, -1>(t, sr, keep, pl, pdt, po, a.pitch, wk, paused, f, nvalid, any_iso); break;
+      }
     }
 #pragma unroll
-    for (int u = 0; u < U; ++u) sigma = fmaf(sw[k0 + u], v[u], sigma);
+    for (int j = 0; j < 4; ++j) {
+      if (j >= nvalid) break;
+      a.s_out[off + j] = W[j] * t.sigma[j];
+      a.gw[off + j] += fmaf(t.sigma[j] - t.a0[j], t.ed[j], -t.pd[j]);
+      if (iso[j] >= 0) atomicAdd(&hwall[iso[j]], t.h[j]);
+    }
   }
-  float g = 0.f;
-  const float keep = 1.f - W, ws = W * sigma;
-  for (int k0 = 0; k0 < a.q; k0 += U) {
-    float av[U], dv[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int k = k0 + u, code = scode[k], hop = code & 7;
-      const int64_t sh = (code & 8) ? 0 : int64_t(c_hop_y[hop]) * a.pitch + c_hop_x[hop];
-      av[u] = a.lam_in[int64_t(k) * a.plane + off + sh];
-      dv[u] = a.dtil[int64_t(k) * a.plane + off];
-    }
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      a.lam_out[int64_t(k0 + u) * a.plane + off] = fmaf(keep, av[u], ws);
-      g = fmaf(dv[u], sigma - av[u], g);
-    }
-  }
-  a.gw[off] += g;
+  // one global atomic per wall and block
+  if (__syncthreads_or(any_iso) && tid < 4 && hwall[tid] != 0.f)
+    atomicAdd(a.gtw + tid, double(hwall[tid]));
 }
 
 // Transpose of the periodic x link (all frame rows), then of the y link.
@@ -107,17 +219,18 @@ __global__ void k_periodic_T_y(float* planes, int64_t plane, int pitch, int nx, 
   base[int64_t(ny + 2) * pitch] = 0.f;
 }
 
-// Transpose of the wall pass: one warp per ghost cell, same segments as k_walls.
-__global__ void k_walls_T(const WallArgs wa, float* lam, double* gtw) {
-  const int warp = int((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-  const int lane = threadIdx.x & 31;
-  int s = 0, idx = warp;
-  while (s < wa.nseg && idx >= wa.seg[s].count) {
-    idx -= wa.seg[s].count;
-    ++s;
-  }
-  if (s >= wa.nseg) return;
-  const WallSeg g = wa.seg[s];
+// Transpose of the wall pass, on the same blocks as k_walls: along horizontal walls lane =
+// ghost cell and warp w = directions w, w + kWallWarpsT, ..., per-cell sums combining over
+// the warps in a fixed order; vertical walls and corners one warp per cell.  Isothermal
+// cells send sum_i w_i l_i to the wall temperature and zero l; diffuse cells give every
+// collected direction sum_k rho_k l_k.
+constexpr int kWallWarpsT = 8;
+static_assert(kWallCellsPerBlock == kWallWarpsT, "one warp per cell of a block");
+
+// One ghost cell by one warp, lanes over the directions; returns sum_i w_i l_i of an
+// isothermal cell (0 for diffuse cells) for the wall-temperature gradient.
+__device__ __forceinline__ float walls_T_cell(const WallArgs& wa, const WallSeg& g, int idx,
+                                              int lane, float* lam) {
   const int64_t off = int64_t(g.r0 + idx * g.dr) * wa.pitch + (g.c0 + idx * g.dc);
   if (g.action == WLBM_BC_ISOTHERMAL) {
     float part = 0.f;
@@ -126,9 +239,7 @@ __global__ void k_walls_T(const WallArgs wa, float* lam, double* gtw) {
       part = fmaf(wa.w[i], *p, part);
       *p = 0.f;
     }
-    const float S = warp_sum(part);
-    if (lane == 0) atomicAdd(gtw + g.wall, double(S));
-    return;
+    return warp_sum(part);
   }
   const float* rho = wa.rho + int64_t(g.table) * wa.q;
   float part = 0.f;
@@ -136,6 +247,69 @@ __global__ void k_walls_T(const WallArgs wa, float* lam, double* gtw) {
     if (rho[i] != 0.f) part = fmaf(rho[i], lam[int64_t(i) * wa.plane + off], part);
   const float S = warp_sum(part);
   for (int i = lane; i < wa.q; i += 32)
+    if (rho[i] == 0.f) lam[int64_t(i) * wa.plane + off] = S;
+  return 0.f;
+}
+
+__global__ void __launch_bounds__(32 * kWallWarpsT) k_walls_T(const WallArgs wa, float* lam,
+                                                               double* gtw) {
+  __shared__ float part_s[kWallWarpsT * 32];
+  int c = 0;
+  const int s = wall_chunk_segment(wa.nseg, wa.seg, int(blockIdx.x), &c);
+  if (s >= wa.nseg) return;
+  const WallSeg g = wa.seg[s];
+  const int lane = int(threadIdx.x) & 31, warp = int(threadIdx.x) >> 5;
+  const bool iso = g.action == WLBM_BC_ISOTHERMAL;
+  // isothermal cells were transposed by the reverse step; only the segment's end cells
+  // may have received corner images from the periodic transpose since
+  auto wanted = [&](int cell) {
+    return cell < g.count && (!iso || cell == 0 || cell == g.count - 1);
+  };
+  if (!wall_seg_rowwise(g)) {   // vertical walls and corners: one warp per cell
+    const int cell = c * kWallCellsPerBlock + warp;
+    const float S = wanted(cell) ? walls_T_cell(wa, g, cell, lane, lam) : 0.f;
+    if (g.action != WLBM_BC_ISOTHERMAL) return;
+    // one atomic per block: the wall temperature's accumulator is a single address
+    if (lane == 0) part_s[warp] = S;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float tot = 0.f;
+      for (int k = 0; k < kWallWarpsT; ++k) tot += part_s[k];
+      atomicAdd(gtw + g.wall, double(tot));
+    }
+    return;
+  }
+  const int idx = c * 32 + lane;
+  const bool on = wanted(idx);
+  const int64_t off = on ? int64_t(g.r0 + idx * g.dr) * wa.pitch + (g.c0 + idx * g.dc) : 0;
+  const float* rho = wa.rho + int64_t(g.table) * wa.q;
+  float part = 0.f;
+  if (on) {
+#pragma unroll 4
+    for (int i = warp; i < wa.q; i += kWallWarpsT) {
+      float* p = lam + int64_t(i) * wa.plane + off;
+      if (iso) {
+        part = fmaf(wa.w[i], *p, part);
+        *p = 0.f;
+      } else if (rho[i] != 0.f) {
+        part = fmaf(rho[i], *p, part);
+      }
+    }
+  }
+  part_s[warp * 32 + lane] = part;
+  __syncthreads();
+  float S = 0.f;
+#pragma unroll
+  for (int k = 0; k < kWallWarpsT; ++k) S += part_s[k * 32 + lane];
+  if (iso) {
+    if (warp == 0) {
+      const float tot = warp_sum(on ? S : 0.f);
+      if (lane == 0) atomicAdd(gtw + g.wall, double(tot));
+    }
+    return;
+  }
+  if (!on) return;
+  for (int i = warp; i < wa.q; i += kWallWarpsT)
     if (rho[i] == 0.f) lam[int64_t(i) * wa.plane + off] = S;
 }
 
@@ -155,8 +329,8 @@ __global__ void k_adj_seed(const AdjArgs a, const float* dJ_dT, const float* e_f
 // dJ/dMFP = dJ/dW_corr * dW_corr/dMFP on interior cells; dJ/d(dT0) from l^0 through the
 // initial condition e_i = w_i e_eq(T_ref + dT0) (ghost cells copy the nearest cell).
 __global__ void k_adj_final(const AdjArgs a, const float* dwc, float* dJ_dmfp,
-                            const float* lam0, const float* dT0, float* dJ_ddT0,
-                            double t_ref, double theta) {
+                            const float* lam0, const float* s0, const float* dT0,
+                            float* dJ_ddT0, double t_ref, double theta) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= a.nx * a.ny) return;
   const int y = t / a.nx, x = t - y * a.nx;
@@ -170,9 +344,13 @@ __global__ void k_adj_final(const AdjArgs a, const float* dwc, float* dJ_dmfp,
       for (int jx = 0; jx < 3; ++jx) {
         if (jx > 0 && fx[jx] == x) continue;
         const int64_t off = int64_t(fy[jy] + 2) * a.pitch + (fx[jx] + kX0);
-        double s = 0.0;
-        for (int i = 0; i < a.q; ++i) s += double(a.w[i]) * lam0[int64_t(i) * a.plane + off];
-        acc += s;
+        // l^0_i = lh_i + s, so sum_i w_i l^0_i = sum_i w_i lh_i + s sum_i w_i
+        double s = 0.0, wsum = 0.0;
+        for (int i = 0; i < a.q; ++i) {
+          s += double(a.w[i]) * lam0[int64_t(i) * a.plane + off];
+          wsum += double(a.w[i]);
+        }
+        acc += s + wsum * double(s0[off]);
       }
     }
     const double T = t_ref + double(dT0[t]);
@@ -186,8 +364,8 @@ inline unsigned nblk(int64_t n, int per) { return unsigned((n + per - 1) / per);
 }  // namespace
 
 cudaError_t launch_adj_step(const AdjArgs& a, cudaStream_t s) {
-  const dim3 block(32, kAdjTY);
-  const dim3 grid((a.nx + 2 + 31) / 32, (a.ny + 2 + kAdjTY - 1) / kAdjTY);
+  const dim3 block(32, kAdjRows);
+  const dim3 grid((a.nx + 2 + kAdjTW - 1) / kAdjTW, (a.ny + 2 + kAdjRows - 1) / kAdjRows);
   k_adj_step<<<grid, block, 0, s>>>(a);
   return cudaGetLastError();
 }
@@ -204,10 +382,9 @@ cudaError_t launch_periodic_T(float* planes, int64_t plane, int pitch, int nx, i
 }
 
 cudaError_t launch_walls_T(const WallArgs& wa, float* lam, double* gtw, cudaStream_t s) {
-  int cells = 0;
-  for (int k = 0; k < wa.nseg; ++k) cells += wa.seg[k].count;
-  if (cells == 0) return cudaSuccess;
-  k_walls_T<<<nblk(int64_t(cells) * 32, 256), 256, 0, s>>>(wa, lam, gtw);
+  const int chunks = wall_chunk_count(wa.nseg, wa.seg);
+  if (chunks == 0) return cudaSuccess;
+  k_walls_T<<<chunks, 32 * kWallWarpsT, 0, s>>>(wa, lam, gtw);
   return cudaGetLastError();
 }
 
@@ -218,9 +395,9 @@ cudaError_t launch_adj_seed(const AdjArgs& a, const float* dJ_dT, const float* e
 }
 
 cudaError_t launch_adj_final(const AdjArgs& a, const float* dwc, float* dJ_dmfp,
-                             const float* lam0, const float* dT0, float* dJ_ddT0,
-                             double t_ref, double theta, cudaStream_t s) {
-  k_adj_final<<<nblk(int64_t(a.nx) * a.ny, 256), 256, 0, s>>>(a, dwc, dJ_dmfp, lam0, dT0,
+                             const float* lam0, const float* s0, const float* dT0,
+                             float* dJ_ddT0, double t_ref, double theta, cudaStream_t s) {
+  k_adj_final<<<nblk(int64_t(a.nx) * a.ny, 256), 256, 0, s>>>(a, dwc, dJ_dmfp, lam0, s0, dT0,
                                                                dJ_ddT0, t_ref, theta);
   return cudaGetLastError();
 }

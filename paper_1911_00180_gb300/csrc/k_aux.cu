@@ -41,32 +41,60 @@ __device__ __forceinline__ float dev_store(T* p, float d, float wi, const float*
   return fmaf(Elem<T>::st(p, __fmul_rn(__fsub_rn(d, r), inv_scale)), scale, r);
 }
 
-// Wall pass over chunks of 32 consecutive ghost cells of one segment: a block of
-// kWallWarps warps takes one chunk, lane l the cell l of it (consecutive cells of a
-// horizontal wall are consecutive in memory, so every per-direction access of a warp is
-// one coalesced row piece), and warp w the directions w, w + kWallWarps, ...  Diffuse
-// walls add the collected directions per warp, then over the warps in a fixed order.
+// Wall pass.  Horizontal walls: a block of kWallWarps warps takes a chunk of 32
+// consecutive ghost cells, lane l the cell l of it (consecutive cells are consecutive in
+// memory, so every per-direction access of a warp is one coalesced row piece), and warp w
+// the directions w, w + kWallWarps, ...; diffuse walls add the collected directions per
+// warp, then over the warps in a fixed order.  Vertical walls and corners: one warp per
+// cell (walls_cell), which keeps many warps busy on the few, strided cells.
 constexpr int kWallWarps = 8;
+static_assert(kWallChunk == 32, "one lane per ghost cell of a chunk");
+static_assert(kWallCellsPerBlock == kWallWarps, "one warp per cell of a block");
 
-__host__ __device__ inline int wall_chunks(const WallArgs& a) {
-  int n = 0;
-  for (int s = 0; s < a.nseg; ++s) n += (a.seg[s].count + 31) >> 5;
-  return n;
+// One ghost cell by one warp, lanes over the directions (vertical walls and corners).
+template <typename T>
+__device__ __forceinline__ void walls_cell(const WallArgs& a, const uint8_t* codes,
+                                           float* e_ref, const WallSeg& g, int idx, int lane) {
+  const int64_t off = int64_t(g.r0 + idx * g.dr) * a.pitch + (g.c0 + idx * g.dc);
+  T* planes = static_cast<T*>(a.planes);
+  auto ptr = [&](int i) {
+    const int par = a.tape ? 0 : (codes[i] >> 4) & 1;
+    return planes + int64_t(par * a.q + i) * a.plane + off;
+  };
+  if (g.action == WLBM_BC_ISOTHERMAL) {
+    if (e_ref) {
+      for (int i = lane; i < a.q; i += 32) Elem<T>::st(ptr(i), 0.f);
+      if (lane == 0) e_ref[off] = g.iso;
+    } else {
+      for (int i = lane; i < a.q; i += 32) Elem<T>::st(ptr(i), a.w[i] * g.iso);
+    }
+    return;
+  }
+  const float* rho = a.rho + int64_t(g.table) * a.q;
+  float part = 0.f;
+  for (int i = lane; i < a.q; i += 32)
+    if (rho[i] == 0.f) part += dev_load(ptr(i), a.w[i], e_ref, off, a.scale);
+  const float A = warp_sum(part);
+  for (int i = lane; i < a.q; i += 32) {
+    const float d = rho[i] == 0.f ? 0.f
+                                  : fmaf(A, rho[i], dev_load(ptr(i), a.w[i], e_ref, off, a.scale));
+    dev_store(ptr(i), d, a.w[i], e_ref, off, a.scale, a.inv_scale);
+  }
 }
 
 template <typename T>
 __device__ __forceinline__ void walls_chunk(const WallArgs& a, const uint8_t* codes,
                                             float* e_ref, int chunk, float* part_s) {
-  int s = 0, c = chunk;
-  while (s < a.nseg) {
-    const int nch = (a.seg[s].count + 31) >> 5;
-    if (c < nch) break;
-    c -= nch;
-    ++s;
-  }
+  int c = 0;
+  const int s = wall_chunk_segment(a.nseg, a.seg, chunk, &c);
   if (s >= a.nseg) return;                     // uniform over the block
   const WallSeg g = a.seg[s];
   const int lane = int(threadIdx.x) & 31, warp = int(threadIdx.x) >> 5;
+  if (!wall_seg_rowwise(g)) {                  // one warp per cell, lanes over directions
+    const int cell = c * kWallCellsPerBlock + warp;
+    if (cell < g.count) walls_cell<T>(a, codes, e_ref, g, cell, lane);
+    return;
+  }
   const int idx = c * 32 + lane;
   const bool on = idx < g.count;
   const int64_t off = on ? int64_t(g.r0 + idx * g.dr) * a.pitch + (g.c0 + idx * g.dc) : 0;
@@ -315,7 +343,7 @@ inline unsigned blocks_for(int64_t n, int per) { return unsigned((n + per - 1) /
 
 template <typename T>
 cudaError_t walls_t(const WallArgs& a, cudaStream_t s) {
-  const int chunks = wall_chunks(a);
+  const int chunks = wall_chunk_count(a.nseg, a.seg);
   if (chunks == 0) return cudaSuccess;
   k_walls<T><<<chunks, 32 * kWallWarps, 0, s>>>(a);
   return cudaGetLastError();
@@ -343,7 +371,7 @@ cudaError_t launch_walls_batch(int storage, const BatchWalls* b, int n, int tota
   return cudaGetLastError();
 }
 
-int wall_blocks(const WallArgs& a) { return wall_chunks(a); }
+int wall_blocks(const WallArgs& a) { return wall_chunk_count(a.nseg, a.seg); }
 
 cudaError_t launch_walls(int storage, const WallArgs& a, cudaStream_t s) {
   return storage == WLBM_STORE_BF16_DEV ? walls_t<__nv_bfloat16>(a, s) : walls_t<float>(a, s);

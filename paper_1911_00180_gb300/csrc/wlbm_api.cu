@@ -81,7 +81,8 @@ struct wlbm_handle {
     float* ckpt = nullptr;     // [nck][q][plane] states before the boundary pass
     float* ckpt_e = nullptr;   // [nck][plane] their local energy
     float* tape = nullptr;     // [k][q][plane] recomputed step inputs of one segment
-    float* lam[2] = {nullptr, nullptr};
+    float* lam[2] = {nullptr, nullptr};   // per-direction part lh of the adjoint
+    float* sh[2] = {nullptr, nullptr};    // shared part s (one plane)
     float* erec[2] = {nullptr, nullptr};
     float* gw = nullptr;       // framed dJ/dW_corr
     float* dwc = nullptr;      // nx*ny dW_corr/dMFP
@@ -810,8 +811,12 @@ static wlbm_status adj_alloc(wlbm_handle* h, int64_t n, int k) {
   A.ckpt = static_cast<float*>(get(size_t(nck) * state));
   A.ckpt_e = static_cast<float*>(get(size_t(nck) * size_t(g.plane) * 4));
   A.tape = static_cast<float*>(get(size_t(k) * state + 1024));
-  A.lam[0] = static_cast<float*>(get(state));
-  A.lam[1] = static_cast<float*>(get(state));
+  // slack after the adjoint planes: the reverse step's shifted 16-byte row reads of the
+  // last tile may run a few elements past the last row
+  A.lam[0] = static_cast<float*>(get(state + 1024));
+  A.lam[1] = static_cast<float*>(get(state + 1024));
+  A.sh[0] = static_cast<float*>(get(size_t(g.plane) * 4));
+  A.sh[1] = static_cast<float*>(get(size_t(g.plane) * 4));
   A.erec[0] = static_cast<float*>(get(size_t(g.plane) * 4));
   A.erec[1] = static_cast<float*>(get(size_t(g.plane) * 4));
   A.gw = static_cast<float*>(get(size_t(g.plane) * 4));
@@ -819,7 +824,8 @@ static wlbm_status adj_alloc(wlbm_handle* h, int64_t n, int k) {
   A.dT0 = static_cast<float*>(get(cells));
   A.gtw = static_cast<double*>(get(4 * sizeof(double)));
   A.codes = static_cast<uint8_t*>(get(size_t(n) * g.q));
-  if (!A.ckpt || !A.ckpt_e || !A.tape || !A.lam[0] || !A.lam[1] || !A.erec[0] || !A.erec[1] ||
+  if (!A.ckpt || !A.ckpt_e || !A.tape || !A.lam[0] || !A.lam[1] || !A.sh[0] || !A.sh[1] ||
+      !A.erec[0] || !A.erec[1] ||
       !A.gw || !A.dwc || !A.dT0 || !A.gtw || !A.codes)
     return h->fail(WLBM_ERR_OOM, "wlbm_adjoint_forward: device allocation failed");
   A.n = n;
@@ -908,12 +914,27 @@ wlbm_status wlbm_adjoint_backward(wlbm_handle* h, const float* dJ_dT, float* dJ_
   };
   ok(cudaMemsetAsync(A.lam[0], 0, state * 4, s), "adjoint");
   ok(cudaMemsetAsync(A.lam[1], 0, state * 4, s), "adjoint");
+  ok(cudaMemsetAsync(A.sh[0], 0, size_t(g.plane) * 4, s), "adjoint");   // pads stay zero
+  ok(cudaMemsetAsync(A.sh[1], 0, size_t(g.plane) * 4, s), "adjoint");
   ok(cudaMemsetAsync(A.gw, 0, size_t(g.plane) * 4, s), "adjoint");
   ok(cudaMemsetAsync(A.gtw, 0, 4 * sizeof(double), s), "adjoint");
   AdjArgs aa{};
   aa.w = h->w_dev(); aa.wfield = h->field_w ? h->wfield : nullptr; aa.w0 = h->w0;
   aa.xper = h->xper; aa.yper = h->yper; aa.gw = A.gw;
   aa.nx = g.nx; aa.ny = g.ny; aa.q = g.q; aa.pitch = g.pitch; aa.plane = g.plane;
+  aa.gtw = A.gtw;
+  // isothermal wall cells, by side and corner, from the wall segments
+  for (int k = 0; k < 4; ++k) aa.iso_side[k] = aa.iso_corner[k] = -1;
+  for (int k = 0; k < h->walls.nseg; ++k) {
+    const WallSeg& sg = h->walls.seg[k];
+    if (sg.action != WLBM_BC_ISOTHERMAL) continue;
+    const bool right = sg.c0 == kX0 + g.nx, top = sg.r0 == g.ny + 2;
+    if (sg.count == 1 && sg.dr == 0 && sg.dc == 0)
+      aa.iso_corner[(top ? 2 : 0) + (right ? 1 : 0)] = sg.wall;
+    else if (sg.dr != 0)
+      aa.iso_side[right ? 1 : 0] = sg.wall;
+    else aa.iso_side[top ? 3 : 2] = sg.wall;
+  }
   aa.lam_out = A.lam[0];
   ok(launch_adj_seed(aa, dJ_dT, h->e[h->e_cur], h->e_eq_ref, h->theta, s), "adjoint: seed");
   int cur = 0;
@@ -959,11 +980,17 @@ wlbm_status wlbm_adjoint_backward(wlbm_handle* h, const float* dJ_dT, float* dJ_
     for (int j = kc - 1; j >= 0 && st == WLBM_OK; --j) {
       aa.lam_in = A.lam[cur];
       aa.lam_out = A.lam[cur ^ 1];
+      aa.s_in = A.sh[cur];
+      aa.s_out = A.sh[cur ^ 1];
       aa.dtil = A.tape + size_t(j) * state;
       aa.codes = A.codes + size_t(s0 + j) * g.q;
       ok(launch_adj_step(aa, s), "adjoint: reverse step");
+      // the periodic transpose is the same on every direction: it acts on lh and on s
       ok(launch_periodic_T(A.lam[cur ^ 1], g.plane, g.pitch, g.nx, g.ny, g.q, h->xper, h->yper, s),
          "adjoint: periodic transpose");
+      ok(launch_periodic_T(A.sh[cur ^ 1], g.plane, g.pitch, g.nx, g.ny, 1, h->xper, h->yper, s),
+         "adjoint: periodic transpose");
+      // s is zero on wall ghost cells (W = 0 there), so the wall transpose sees l = lh
       if (h->walls.nseg > 0) {
         WallArgs wa = h->walls;
         wa.codes = aa.codes;
@@ -975,7 +1002,8 @@ wlbm_status wlbm_adjoint_backward(wlbm_handle* h, const float* dJ_dT, float* dJ_
   // periodic ghosts of W_corr copy interior cells: send their gradient back
   ok(launch_periodic_T(A.gw, g.plane, g.pitch, g.nx, g.ny, 1, h->xper, h->yper, s),
      "adjoint: W transpose");
-  ok(launch_adj_final(aa, A.dwc, dJ_dmfp, A.lam[cur], A.dT0, dJ_ddT0, h->t_ref, h->theta, s),
+  ok(launch_adj_final(aa, A.dwc, dJ_dmfp, A.lam[cur], A.sh[cur], A.dT0, dJ_ddT0, h->t_ref,
+                      h->theta, s),
      "adjoint: final");
   double gt[4] = {0, 0, 0, 0};
   ok(cudaMemcpyAsync(gt, A.gtw, sizeof(gt), cudaMemcpyDeviceToHost, s), "adjoint");

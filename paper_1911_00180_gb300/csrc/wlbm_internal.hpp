@@ -122,6 +122,41 @@ struct WallArgs {
   WallSeg seg[kMaxSeg];
 };
 
+// Wall passes: a segment along a row (horizontal wall) is cut into chunks of
+// kWallChunk consecutive cells, one block each, lane = cell (consecutive cells are
+// consecutive in memory); other segments (vertical walls, corners) give every cell one
+// warp, lanes over the directions, kWallCellsPerBlock cells a block.
+constexpr int kWallChunk = 32;
+constexpr int kWallCellsPerBlock = 8;
+#ifdef __CUDACC__
+__host__ __device__ inline bool wall_seg_rowwise(const WallSeg& g) {
+  return g.dr == 0 && g.dc != 0 && g.count > 1;
+}
+__host__ __device__ inline int wall_seg_blocks(const WallSeg& g) {
+  const int per = wall_seg_rowwise(g) ? kWallChunk : kWallCellsPerBlock;
+  return (g.count + per - 1) / per;
+}
+__host__ __device__ inline int wall_chunk_count(int nseg, const WallSeg* seg) {
+  int n = 0;
+  for (int s = 0; s < nseg; ++s) n += wall_seg_blocks(seg[s]);
+  return n;
+}
+// Segment of block `chunk` (nseg when out of range) and the block's index within it.
+__host__ __device__ inline int wall_chunk_segment(int nseg, const WallSeg* seg, int chunk,
+                                                  int* local) {
+  int s = 0;
+  while (s < nseg) {
+    const int nb = wall_seg_blocks(seg[s]);
+    if (chunk < nb) break;
+    chunk -= nb;
+    ++s;
+  }
+  *local = chunk;
+  return s;
+}
+#endif
+
+
 struct PeriodicArgs {
   void* planes;
   int64_t plane;
@@ -213,9 +248,14 @@ struct BatchWalls {
 };
 
 // Reverse-step arguments (float32 storage only).
+// The adjoint of a state is kept factored as l_k(x) = lh_k(x) + s(x): per-direction planes
+// lh plus one plane s shared by all directions (the reverse relaxation adds the same
+// W sigma to every direction of a cell, so it lands in s instead of in q planes).
 struct AdjArgs {
-  const float* lam_in;   // adjoint of the step's output, [q][plane]
-  float* lam_out;        // adjoint of the step's input (before the boundary transposes)
+  const float* lam_in;   // lh of the step's output, [q][plane]
+  float* lam_out;        // lh of the step's input (before the boundary transposes)
+  const float* s_in;     // s of the step's output (framed plane)
+  float* s_out;          // s of the step's input
   const float* dtil;     // recorded step input (after the boundary pass), [q][plane]
   const uint8_t* codes;  // the step's codes
   const float* w;
@@ -225,6 +265,11 @@ struct AdjArgs {
   float* gw;             // framed dJ/dW_corr accumulator
   int nx, ny, q, pitch;
   int64_t plane;
+  // isothermal wall cells, transposed inside the reverse step: wall index (0..3) of the
+  // edge cells of side k (x-, x+, y-, y+; corners excluded) and of corner k ((1, x-),
+  // (1, x+), (ny+2, x-), (ny+2, x+)), or -1; their sum_i w_i l_i goes to gtw[wall]
+  int iso_side[4], iso_corner[4];
+  double* gtw;
 };
 
 // Sets the message returned by wlbm_last_error(NULL).
@@ -262,11 +307,14 @@ cudaError_t launch_set_state(int storage, const StateArgs& a, cudaStream_t s);
 cudaError_t launch_adj_step(const AdjArgs& a, cudaStream_t s);
 cudaError_t launch_periodic_T(float* planes, int64_t plane, int pitch, int nx, int ny,
                               int nplanes, int xper, int yper, cudaStream_t s);
+// Transposed wall pass after the periodic transpose.  Isothermal cells were transposed by
+// the reverse step: only the two end cells of each isothermal segment (where the periodic
+// transpose of the other axis may have added corner images) are transposed again.
 cudaError_t launch_walls_T(const WallArgs& wa, float* lam, double* gtw, cudaStream_t s);
 cudaError_t launch_adj_seed(const AdjArgs& a, const float* dJ_dT, const float* e_final,
                             double e_ref, double theta, cudaStream_t s);
 cudaError_t launch_adj_final(const AdjArgs& a, const float* dwc, float* dJ_dmfp,
-                             const float* lam0, const float* dT0, float* dJ_ddT0,
-                             double t_ref, double theta, cudaStream_t s);
+                             const float* lam0, const float* s0, const float* dT0,
+                             float* dJ_ddT0, double t_ref, double theta, cudaStream_t s);
 
 }  // namespace wlbm
