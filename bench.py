@@ -52,15 +52,47 @@ def parse():
                         "film, Q=128, isothermal x walls, diffuse y walls (Kn = 1)")
     p.add_argument("--e2e-steps", type=int, default=3)
     p.add_argument("--fuse", type=int, default=None,
-                   help="1: step kernel mirrors periodic edges (library default), 0: separate pass")
+                   help="1: step kernel mirrors periodic edges, 0: separate pass (library "
+                        "default)")
     p.add_argument("--graph", type=int, default=0,
                    help="replay chunks of this many steps as one CUDA graph (multiple of 6)")
     p.add_argument("--variant", type=int, default=None,
-                   help="step kernel: 0 register-pipelined, 1 bulk-copy ring (library default)")
+                   help="step kernel: 0 register-pipelined, 1 bulk-copy ring, 2 warp-specialised, "
+                        "3 TMA tiles (library default where available)")
     p.add_argument("--no-extras", action="store_true",
                    help="skip e2e, cpu baseline, adjoint and clock sampling (profiling runs)")
     p.add_argument("--no-adjoint", action="store_true", help="skip the adjoint ratio")
+    p.add_argument("--adjoint-only", type=int, default=0, metavar="STEPS",
+                   help="profiling aid: run only the adjoint workload for STEPS steps and print "
+                        "its timings (no bench line)")
     return p.parse_args()
+
+
+def measured_traffic(workload, storage, nx, q):
+    """DRAM bytes per step-kernel launch from the committed ncu launch lists, if they were
+    taken on the kernel sources of this tree (else None)."""
+    import glob
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "k_step_tma_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_1911_00180_gb300", "csrc", "*"))):
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    digest = None
+    table = {}
+    for line in open(path):
+        parts = line.split()
+        if not parts or parts[0].startswith("#"):
+            continue
+        if parts[0] == "sources":
+            digest = parts[1]
+        elif len(parts) == 6:
+            table[(parts[0], parts[1], int(parts[2]), int(parts[3]))] = float(parts[5])
+    if digest != h.hexdigest():
+        return None
+    return table.get((workload, storage, nx, q))
 
 
 def peaks():
@@ -312,8 +344,20 @@ def run_reference(args):
     return 0
 
 
+def adjoint_only(args):
+    """Profiling aid: the adjoint workload alone (forward, checkpointed forward, backward)."""
+    import torch
+    import paper_1911_00180_gb300 as wl
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        print(json.dumps(adjoint_ratio(wl, torch, stream, steps=args.adjoint_only)), flush=True)
+    return 0
+
+
 def main():
     args = parse()
+    if args.adjoint_only:
+        return adjoint_only(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batch":
@@ -434,7 +478,11 @@ def main():
                        "l2": "state %.2f GB > L2 (no flush needed)"
                              % (2 * cfg["q"] * cells * (4 if args.storage == "fp32" else 2) / 1e9)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak,
+                         "traffic": (measured_traffic(args.workload, args.storage, cfg["nx"],
+                                                      cfg["q"]) if variant_used == 3 else None),
+                         "traffic_unit": "DRAM bytes per launch (ncu, profiles/)",
+                         "algorithmic_bytes_per_launch": bpu * cells * cfg["q"],
                          "kernel": {0: "k_step", 1: "k_step_bulk", 2: "k_step_ws",
                                     3: "k_step_tma"}[variant_used], "peak_kind": peak_kind,
                          "bytes_per_update": bpu,
