@@ -20,14 +20,6 @@ namespace wlbm {
 namespace {
 
 
-__device__ __forceinline__ float w_at(const AdjArgs& a, int r, int c) {
-  if (a.wfield) return a.wfield[int64_t(r) * a.pitch + c];
-  if (r < 1 || r > a.ny + 2 || c < kGhostCol || c > kX0 + a.nx) return 0.f;
-  const bool gx = (c == kGhostCol) || (c == kX0 + a.nx);
-  const bool gy = (r == 1) || (r == a.ny + 2);
-  if ((gx && !a.xper) || (gy && !a.yper)) return 0.f;
-  return a.w0;
-}
 
 // One pass over the Q adjoint planes.  A thread owns 4 consecutive cells of a row (a warp
 // 128 cells, a block 8 rows).  With the output adjoint l' = lh' + s' (s' of the 3 x 6 cells
@@ -40,7 +32,8 @@ __device__ __forceinline__ float w_at(const AdjArgs& a, int r, int c) {
 // so neither term is much larger than the result.  Cells past the right ghost column are
 // neither read for output nor written (their pads stay zero).
 constexpr int kAdjRows = 8;
-constexpr int kAdjTW = 128;   // cells of a row per warp
+constexpr int kAdjTW = 128;                 // cells of a row per warp
+constexpr int kAdjC0 = kGhostCol & ~3;      // first column of the first group
 
 __device__ __forceinline__ float4 ld4(const float* p) {
   return __ldcs(reinterpret_cast<const float4*>(p));
@@ -65,23 +58,13 @@ struct AdjAcc {
   float sigma[4], a0[4], ed[4], pd[4], h[4];
 };
 
-// Wall index of an isothermal wall cell (r, c), or -1.
-__device__ __forceinline__ int iso_wall_of(const AdjArgs& a, int r, int c) {
-  const bool xl = c == kGhostCol, xr = c == kX0 + a.nx, yb = r == 1, yt = r == a.ny + 2;
-  if ((xl || xr) && (yb || yt)) return a.iso_corner[(yt ? 2 : 0) + (xr ? 1 : 0)];
-  if (xl) return a.iso_side[0];
-  if (xr) return a.iso_side[1];
-  if (yb) return a.iso_side[2];
-  if (yt) return a.iso_side[3];
-  return -1;
-}
 
 // One direction with hop (CX, CY) for the thread's 4 cells.
 template <int CX, int CY>
 __device__ __forceinline__ void adj_dir(AdjAcc& t, const float (&sr)[3][6], const float (&keep)[4],
                                         const float* pl, const float* pdt, float* po,
                                         int pitch, float wk, bool paused, bool first,
-                                        int nvalid, bool harvest) {
+                                        unsigned vm, bool harvest) {
   float b[4], av[4];
   row4<CX>(pl + int64_t(CY) * pitch, b);
 #pragma unroll
@@ -106,12 +89,12 @@ __device__ __forceinline__ void adj_dir(AdjAcc& t, const float (&sr)[3][6], cons
     o[j] = keep[j] * av[j];
     if (harvest) t.h[j] = fmaf(wk, av[j], t.h[j]);   // isothermal wall cells: W = 0, l = a
   }
-  if (nvalid == 4) {
+  if (vm == 0xFu) {
     __stcs(reinterpret_cast<float4*>(po), make_float4(o[0], o[1], o[2], o[3]));
   } else {
 #pragma unroll
     for (int j = 0; j < 4; ++j)
-      if (j < nvalid) po[j] = o[j];
+      if ((vm >> j) & 1u) po[j] = o[j];
   }
 }
 
@@ -126,12 +109,15 @@ __global__ void __launch_bounds__(32 * kAdjRows) k_adj_step(const AdjArgs a) {
   }
   if (tid < 4) hwall[tid] = 0.f;
   __syncthreads();
-  const int c0 = kGhostCol + blockIdx.x * kAdjTW + 4 * threadIdx.x;
+  // 16-byte aligned groups of 4 from the aligned column at or below the left ghost
+  const int c0 = kAdjC0 + blockIdx.x * kAdjTW + 4 * threadIdx.x;
   const int r = 1 + blockIdx.y * kAdjRows + threadIdx.y;
   const int clast = kX0 + a.nx;
   bool any_iso = false;
   if (r <= a.ny + 2 && c0 <= clast) {
-    const int nvalid = min(4, clast - c0 + 1);
+    unsigned vm = 0;   // frame cells of the group
+#pragma unroll
+    for (int j = 0; j < 4; ++j) vm |= (c0 + j >= kGhostCol && c0 + j <= clast) ? 1u << j : 0u;
     const int rows = a.ny + 4;
     // s' around the cells (pads and past-the-frame cells read 0)
     float sr[3][6];
@@ -148,8 +134,8 @@ __global__ void __launch_bounds__(32 * kAdjRows) k_adj_step(const AdjArgs a) {
     int iso[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      W[j] = j < nvalid ? w_at(a, r, c0 + j) : 0.f;
-      iso[j] = j < nvalid ? iso_wall_of(a, r, c0 + j) : -1;
+      W[j] = ((vm >> j) & 1u) ? w_at(a, r, c0 + j) : 0.f;
+      iso[j] = ((vm >> j) & 1u) ? iso_wall_of(a, r, c0 + j) : -1;
       any_iso = any_iso || iso[j] >= 0;
       keep[j] = iso[j] >= 0 ? 0.f : 1.f - W[j];
     }
@@ -168,19 +154,19 @@ __global__ void __launch_bounds__(32 * kAdjRows) k_adj_step(const AdjArgs a) {
       const float wk = sw[k];
       const bool f = k == 0;
       switch (code & 7) {   // hop numbering of the host lattice
-        case 0: adj_dir<1, 0>(t, sr, keep, pl, pdt, po, a.pitch, wk, paused, f, nvalid, any_iso); break;
-        case 1: adj_dir<0, 1>(t, sr, keep, pl, pdt, po, a.pitch, wk, paused, f, nvalid, any_iso); break;
-        case 2: adj_dir<-1, 0>(t, sr, keep, pl, pdt, po, a.pitch, wk, paused, f, nvalid, any_iso); break;
-        case 3: adj_dir<0, -1>(t, sr, keep, pl, pdt, po, a.pitch, wk, paused, f, nvalid, any_iso); break;
-        case 4: adj_dir<1, 1>(t, sr, keep, pl, pdt, po, a.pitch, wk, paused, f, nvalid, any_iso); break;
-        case 5: adj_dir<-1, 1>(t, sr, keep, pl, pdt, po, a.pitch, wk, paused, f, nvalid, any_iso); break;
-        case 6: adj_dir<-1, -1>(t, sr, keep, pl, pdt, po, a.pitch, wk, paused, f, nvalid, any_iso); break;
-        default: adj_dir<1, -1>(t, sr, keep, pl, pdt, po, a.pitch, wk, paused, f, nvalid, any_iso); break;
+        case 0: adj_dir<1, 0>(t, sr, keep, pl, pdt, po, a.pitch, wk, paused, f, vm, any_iso); break;
+        case 1: adj_dir<0, 1>(t, sr, keep, pl, pdt, po, a.pitch, wk, paused, f, vm, any_iso); break;
+        case 2: adj_dir<-1, 0>(t, sr, keep, pl, pdt, po, a.pitch, wk, paused, f, vm, any_iso); break;
+        case 3: adj_dir<0, -1>(t, sr, keep, pl, pdt, po, a.pitch, wk, paused, f, vm, any_iso); break;
+        case 4: adj_dir<1, 1>(t, sr, keep, pl, pdt, po, a.pitch, wk, paused, f, vm, any_iso); break;
+        case 5: adj_dir<-1, 1>(t, sr, keep, pl, pdt, po, a.pitch, wk, paused, f, vm, any_iso); break;
+        case 6: adj_dir<-1, -1>(t, sr, keep, pl, pdt, po, a.pitch, wk, paused, f, vm, any_iso); break;
+        default: adj_dir<1, -1>(t, sr, keep, pl, pdt, po, a.pitch, wk, paused, f, vm, any_iso); break;
       }
     }
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      if (j >= nvalid) break;
+      if (!((vm >> j) & 1u)) continue;
       a.s_out[off + j] = W[j] * t.sigma[j];
       a.gw[off + j] += fmaf(t.sigma[j] - t.a0[j], t.ed[j], -t.pd[j]);
       if (iso[j] >= 0) atomicAdd(&hwall[iso[j]], t.h[j]);
@@ -365,7 +351,7 @@ inline unsigned nblk(int64_t n, int per) { return unsigned((n + per - 1) / per);
 
 cudaError_t launch_adj_step(const AdjArgs& a, cudaStream_t s) {
   const dim3 block(32, kAdjRows);
-  const dim3 grid((a.nx + 2 + kAdjTW - 1) / kAdjTW, (a.ny + 2 + kAdjRows - 1) / kAdjRows);
+  const dim3 grid((kX0 + a.nx - kAdjC0) / kAdjTW + 1, (a.ny + 2 + kAdjRows - 1) / kAdjRows);
   k_adj_step<<<grid, block, 0, s>>>(a);
   return cudaGetLastError();
 }

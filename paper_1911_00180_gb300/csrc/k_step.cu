@@ -854,14 +854,14 @@ cudaError_t prepare_step_kernels() {
   if (e == cudaSuccess) e = configure_ws<__nv_bfloat16, 8, 8, true>();
   if (e == cudaSuccess) e = configure_ws<float, 4, 8, false>();
   if (e == cudaSuccess) e = configure_step_tma();
+  if (e == cudaSuccess) e = configure_adj_tma();
   return e;
 }
 
 cudaError_t launch_step(int storage, const StepArgs& a, cudaStream_t s) {
-  // variant 3 covers plain steps (no fused periodic mirrors, no adjoint tape) of grids
-  // that have a tensor map; the others run variant 1
-  if (a.variant == 3 && !a.wrap && !a.tape && a.tmap && a.order)
-    return launch_step_tma(storage, a, s);
+  // variant 3 covers steps without fused periodic mirrors of grids (or adjoint tapes) that
+  // have a tensor map; the others run variant 1
+  if (a.variant == 3 && !a.wrap && a.tmap && a.order) return launch_step_tma(storage, a, s);
   if (a.variant == 2) {
     if (storage == WLBM_STORE_BF16_DEV) return launch_ws<__nv_bfloat16, 8, 8, true>(a, s);
     return launch_ws<float, 4, 8, false>(a, s);

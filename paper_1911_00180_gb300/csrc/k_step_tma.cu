@@ -41,12 +41,13 @@ constexpr int kTR = kRPW + 2;           // register-tile rows (one halo row each
 
 // Per-direction record built once per block (16 bytes, one shared-memory vector load).
 struct alignas(16) Dir3 {
-  int64_t dst_off;   // element offset of the destination plane
+  int32_t dst;       // destination plane index (from the output base)
   float wi;          // angular weight w_i
-  uint16_t z;        // source plane index par*q + i (tensor-map z coordinate)
+  int32_t z;         // source plane index (tensor-map z coordinate)
   uint8_t kase;      // hop | paused << 3
   int8_t dy;         // source row shift of the box (0 when paused)
 };
+static_assert(sizeof(Dir3) == 16, "one 16-byte shared-memory load per direction");
 
 template <typename T, int S>
 struct TmaLayout {
@@ -104,17 +105,18 @@ __device__ __forceinline__ void ring_values(const T* row, int lane, float (&v)[4
   }
 }
 
-// Store the 4 new values (nvalid of them when the group crosses the right edge) and
-// return what was stored (bfloat16: the rounded values).
+// Store the new values of the cells in mask vm (bit j: cell j is computed; a group at the
+// edge of the covered cells stores element by element) and return what was stored
+// (bfloat16: the rounded values).
 template <typename T>
-__device__ __forceinline__ void store4(T* dst, const float (&o)[4], int nvalid, float (&s)[4]) {
+__device__ __forceinline__ void store4(T* dst, const float (&o)[4], unsigned vm, float (&s)[4]) {
   if constexpr (sizeof(T) == 4) {
-    if (nvalid == 4) {
+    if (vm == 0xFu) {
       __stcs(reinterpret_cast<float4*>(dst), make_float4(o[0], o[1], o[2], o[3]));
     } else {
 #pragma unroll
       for (int j = 0; j < 4; ++j)
-        if (j < nvalid) __stcs(reinterpret_cast<float*>(dst) + j, o[j]);
+        if ((vm >> j) & 1u) __stcs(reinterpret_cast<float*>(dst) + j, o[j]);
     }
 #pragma unroll
     for (int j = 0; j < 4; ++j) s[j] = o[j];
@@ -123,7 +125,7 @@ __device__ __forceinline__ void store4(T* dst, const float (&o)[4], int nvalid, 
     const __nv_bfloat162 p1 = __floats2bfloat162_rn(o[2], o[3]);
     const uint32_t w0 = *reinterpret_cast<const uint32_t*>(&p0);
     const uint32_t w1 = *reinterpret_cast<const uint32_t*>(&p1);
-    if (nvalid == 4) {
+    if (vm == 0xFu) {
       __stcs(reinterpret_cast<uint2*>(dst), make_uint2(w0, w1));
     } else {
       unsigned short* d = reinterpret_cast<unsigned short*>(dst);
@@ -133,7 +135,7 @@ __device__ __forceinline__ void store4(T* dst, const float (&o)[4], int nvalid, 
                                    static_cast<unsigned short>(w1 >> 16)};
 #pragma unroll
       for (int j = 0; j < 4; ++j)
-        if (j < nvalid) __stcs(d + j, h[j]);
+        if ((vm >> j) & 1u) __stcs(d + j, h[j]);
     }
     s[0] = bf_lo(w0); s[1] = bf_hi(w0); s[2] = bf_lo(w1); s[3] = bf_hi(w1);
   }
@@ -145,9 +147,10 @@ struct DirCtx {
   const T* ring_row;   // first of the warp's rows in the stage
   T* dst;              // destination of the lane's first cell in the warp's first row
   const float* fsc;    // bfloat16: this lane's W E / scale scratch (stride 32 floats)
-  int64_t pitch;
+  int64_t pitch, plane;
   float wi;
-  int lane, nvalid, nrw;   // nrw: computed rows of this warp (1 or 2)
+  int lane, nrw;   // nrw: computed rows of this warp (1 or 2)
+  unsigned vm;     // bit j: the lane's cell j is computed
 };
 
 // One direction for the lane's cells; hop (CX, CY), paused or propagating.
@@ -178,7 +181,7 @@ __device__ __forceinline__ void dir_body(Regs3& t, const DirCtx<T>& c) {
         o[j] = fmaf(t.G[SR][SC + j], v[j], __fmul_rn(c.wi, t.X[FR][FC + j]));
       }
     }
-    store4<T>(c.dst + k * c.pitch, o, c.nvalid, s);
+    store4<T>(c.dst + k * c.pitch, o, c.vm, s);
 #pragma unroll
     for (int j = 0; j < 4; ++j) t.acc[k][j] += s[j];
   }
@@ -200,10 +203,10 @@ __device__ __forceinline__ bool run_kind(int& j, int end, Regs3& t, DirCtx<T>& c
     }
     const Dir3 d = table[j];
     c.ring_row = reinterpret_cast<const T*>(smem + st * LY::kStage) + kRPW * ty * LY::BW;
-    c.dst = obase + d.dst_off;
+    c.dst = obase + int64_t(d.dst) * c.plane;
     c.wi = d.wi;
     if (REF) accw += d.wi;
-    if (c.nvalid > 0) dir_body<T, REF, CX, CY, PAUSED>(t, c);
+    if (c.vm) dir_body<T, REF, CX, CY, PAUSED>(t, c);
     __syncwarp();
     if (c.lane == 0) mbar_arrive(&empty[st]);
   }
@@ -226,9 +229,9 @@ __device__ __forceinline__ void step_tma_tile(const StepArgs& a, const void* tma
 
   const int lane = threadIdx.x, ty = threadIdx.y;
   const int tid = ty * 32 + lane, nthr = 32 * (kWarps3 + 1);
-  const int col0 = kGhostCol + bx * kTW3;
-  const int row0 = 1 + by * kRows3;
-  const int nrows = min(kRows3, a.ny + 2 - row0 + 1);   // rows row0 .. ny+2 are computed
+  const int col0 = a.cbase + bx * kTW3;
+  const int row0 = a.rmin + by * kRows3;
+  const int nrows = min(kRows3, a.rmax - row0 + 1);     // rows row0 .. rmax are computed
   const int nwarps = (nrows + kRPW - 1) / kRPW;         // consumer warps with rows
 
   int* kind_start = reinterpret_cast<int*>(smem + LY::off_kind);         // [17]
@@ -238,9 +241,10 @@ __device__ __forceinline__ void step_tma_tile(const StepArgs& a, const void* tma
     const int code = a.codes[i];
     const int hop = code & 7, paused = (code >> 3) & 1, par = (code >> 4) & 1;
     Dir3 d;
-    d.dst_off = int64_t((paused ? par : 1 - par) * a.q + i) * a.plane;
+    // tape mode (adjoint recompute): plane i of the source slot to plane i of the next slot
+    d.dst = a.tape ? i : (paused ? par : 1 - par) * a.q + i;
     d.wi = a.w[i];
-    d.z = uint16_t(par * a.q + i);
+    d.z = a.tape ? a.tape_z0 + i : par * a.q + i;
     d.kase = uint8_t(hop | (paused << 3));
     d.dy = int8_t(paused ? 0 : -c_hop_y[hop]);
     table[j] = d;
@@ -276,9 +280,11 @@ __device__ __forceinline__ void step_tma_tile(const StepArgs& a, const void* tma
   // ---------------------------------------------------------------- consumer warps
   if (ty >= nwarps) return;
   const int r = row0 + kRPW * ty;                      // first row of this warp
-  const int nrw = min(kRPW, a.ny + 2 - r + 1);         // 1 or 2 computed rows
+  const int nrw = min(kRPW, a.rmax - r + 1);           // 1 or 2 computed rows
   const int c0 = col0 + 4 * lane;
-  const int nvalid = max(0, min(4, kX0 + a.nx - c0 + 1));   // cells c0.. up to the ghost
+  unsigned vm = 0;                                     // computed cells of the lane
+#pragma unroll
+  for (int j = 0; j < 4; ++j) vm |= (c0 + j >= a.cmin && c0 + j <= a.cmax) ? 1u << j : 0u;
   float* fsc = fscr + size_t(ty) * kTR * 6 * 32 + lane;
   Regs3 t;
 #pragma unroll
@@ -288,7 +294,7 @@ __device__ __forceinline__ void step_tma_tile(const StepArgs& a, const void* tma
     for (int cc = 0; cc < 6; ++cc) {
       const int c = c0 - 1 + cc;
       float wv = 0.f, ev = 0.f, rv = 0.f;
-      if (row < a.rows && c < a.pitch) {
+      if (row < a.rows && c >= 0 && c < a.pitch) {
         const int64_t o = int64_t(row) * a.pitch + c;
         ev = a.e_in[o];
         wv = FIELD_W ? a.wfield[o] : uniform_w(a, row, c);
@@ -302,7 +308,7 @@ __device__ __forceinline__ void step_tma_tile(const StepArgs& a, const void* tma
         t.X[rr][cc] = xs;
         fsc[(rr * 6 + cc) * 32] = fs;
         if (rr >= 1 && rr <= kRPW && cc >= 1 && cc <= 4)
-          t.eins[rr - 1][cc - 1] = cc - 1 < nvalid ? __fmul_rn(ev, a.inv_scale) : 0.f;
+          t.eins[rr - 1][cc - 1] = ((vm >> (cc - 1)) & 1u) ? __fmul_rn(ev, a.inv_scale) : 0.f;
       } else {
         t.X[rr][cc] = fv;
       }
@@ -316,10 +322,11 @@ __device__ __forceinline__ void step_tma_tile(const StepArgs& a, const void* tma
   DirCtx<T> ctx;
   ctx.fsc = fsc;
   ctx.pitch = a.pitch;
+  ctx.plane = a.plane;
   ctx.lane = lane;
-  ctx.nvalid = nvalid;
+  ctx.vm = vm;
   ctx.nrw = nrw;
-  T* obase = static_cast<T*>(a.planes) + int64_t(r) * a.pitch + c0;
+  T* obase = static_cast<T*>(a.tape ? a.tape_dst : a.planes) + int64_t(r) * a.pitch + c0;
 
   // kind = hop | paused << 3; hop numbering of the host lattice:
   // (1,0) (0,1) (-1,0) (0,-1) (1,1) (-1,1) (-1,-1) (1,-1)
@@ -354,16 +361,16 @@ __device__ __forceinline__ void step_tma_tile(const StepArgs& a, const void* tma
     float eo[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      const float ein = REF && j < nvalid ? a.e_in[own + j] : 0.f;
+      const float ein = REF && ((vm >> j) & 1u) ? a.e_in[own + j] : 0.f;
       eo[j] = REF ? fmaf(t.acc[k][j], a.scale, __fmul_rn(ein, accw)) : t.acc[k][j];
     }
     float* e_out = a.e_out + own;
-    if (nvalid == 4) {
+    if (vm == 0xFu) {
       *reinterpret_cast<float4*>(e_out) = make_float4(eo[0], eo[1], eo[2], eo[3]);
     } else {
 #pragma unroll
       for (int j = 0; j < 4; ++j)
-        if (j < nvalid) e_out[j] = eo[j];
+        if ((vm >> j) & 1u) e_out[j] = eo[j];
     }
   }
 }
@@ -430,7 +437,7 @@ template <typename T, int S>
 cudaError_t launch_tma_t(const StepArgs& a, const CUtensorMap& tm, cudaStream_t s) {
   using LY = TmaLayout<T, S>;
   const dim3 block(32, kWarps3 + 1);
-  const dim3 grid((a.nx + 2 + kTW3 - 1) / kTW3, (a.ny + 2 + kRows3 - 1) / kRows3);
+  const dim3 grid((a.cmax - a.cbase) / kTW3 + 1, (a.rmax - a.rmin + kRows3) / kRows3);
   const size_t bytes = LY::bytes(a.q);
   constexpr bool REF = sizeof(T) == 2;
   if (a.wfield) k_step_tma<T, S, true, REF><<<grid, block, bytes, s>>>(a, tm);
@@ -467,6 +474,22 @@ cudaError_t launch_step_tma_batch(int storage, const BatchInst* insts, int n, in
 int tma_tile_width() { return kTW3; }
 int tma_tile_rows() { return kRows3; }
 
+void tma_cover(const int bc_kind[4], int nx, int ny, StepArgs* a, int* tiles_x, int* tiles_y) {
+  // ghost outputs are read only by the adiabatic-diffuse wall pass; periodic and isothermal
+  // passes overwrite their ghost cells before the next step reads them
+  const bool gl = bc_kind[0] == WLBM_BC_ADIABATIC_DIFFUSE;
+  const bool gr = bc_kind[1] == WLBM_BC_ADIABATIC_DIFFUSE;
+  const bool gb = bc_kind[2] == WLBM_BC_ADIABATIC_DIFFUSE;
+  const bool gt = bc_kind[3] == WLBM_BC_ADIABATIC_DIFFUSE;
+  a->cmin = gl ? kGhostCol : kX0;
+  a->cmax = gr ? kX0 + nx : kX0 + nx - 1;
+  a->rmin = gb ? 1 : 2;
+  a->rmax = gt ? ny + 2 : ny + 1;
+  a->cbase = gl ? kX0 - kTW3 : kX0;   // a left ghost column gets a tile of its own
+  *tiles_x = (a->cmax - a->cbase) / kTW3 + 1;
+  *tiles_y = (a->rmax - a->rmin + kRows3) / kRows3;
+}
+
 cudaError_t launch_step_tma(int storage, const StepArgs& a, cudaStream_t s) {
   const CUtensorMap& tm = *static_cast<const CUtensorMap*>(a.tmap);
   if (storage == WLBM_STORE_BF16_DEV) return launch_tma_t<__nv_bfloat16, kStagesBF16>(a, tm, s);
@@ -476,8 +499,13 @@ cudaError_t launch_step_tma(int storage, const StepArgs& a, cudaStream_t s) {
 // Tensor map of the 2q direction planes as a 3-D tensor (columns, rows, planes) with the
 // box of one TMA stage.  The encoder comes from the driver through the runtime's entry
 // point query, so the library does not link the driver library directly.
-bool make_plane_tensor_map(void* out, void* planes, int storage, const Geom& g,
+bool make_plane_tensor_map(void* out, void* planes, int storage, const Geom& g, int nplanes,
                            std::string* why) {
+  return make_box_tensor_map(out, planes, storage, g, nplanes, kRows3, why);
+}
+
+bool make_box_tensor_map(void* out, void* planes, int storage, const Geom& g, int nplanes,
+                         int box_rows, std::string* why) {
   using Encode = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
                               const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
                               const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
@@ -498,9 +526,9 @@ bool make_plane_tensor_map(void* out, void* planes, int storage, const Geom& g,
   const bool bf = storage == WLBM_STORE_BF16_DEV;
   const cuuint64_t es = bf ? 2 : 4;
   const cuuint32_t V = cuuint32_t(16 / es);
-  const cuuint64_t dims[3] = {cuuint64_t(g.pitch), cuuint64_t(g.rows), cuuint64_t(2 * g.q)};
+  const cuuint64_t dims[3] = {cuuint64_t(g.pitch), cuuint64_t(g.rows), cuuint64_t(nplanes)};
   const cuuint64_t strides[2] = {cuuint64_t(g.pitch) * es, cuuint64_t(g.plane) * es};
-  const cuuint32_t box[3] = {cuuint32_t(kTW3) + 2 * V, cuuint32_t(kRows3), 1};
+  const cuuint32_t box[3] = {cuuint32_t(kTW3) + 2 * V, cuuint32_t(box_rows), 1};
   const cuuint32_t estr[3] = {1, 1, 1};
   const CUresult r = encode(static_cast<CUtensorMap*>(out),
                             bf ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,

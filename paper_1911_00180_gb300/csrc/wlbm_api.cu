@@ -89,6 +89,11 @@ struct wlbm_handle {
     float* dT0 = nullptr;      // nx*ny start field
     double* gtw = nullptr;     // [4] sum_i w_i lambda_i at isothermal ghosts
     uint8_t* codes = nullptr;  // [n][q] schedule of the run
+    uint16_t* order = nullptr; // [n][q + 17] kind-sorted directions of every step
+    alignas(64) unsigned char tape_tmap[128] = {};   // CUtensorMap of the k x q tape planes
+    bool has_tape_tmap = false;
+    alignas(64) unsigned char lam_tmap[2][128] = {}; // CUtensorMaps of the lh planes (16 rows)
+    bool has_lam_tmap = false;
     std::vector<void*> bufs;
   } adj;
   // launch accounting and optional per-launch timing of the step kernel
@@ -427,7 +432,8 @@ wlbm_status wlbm_create(const wlbm_grid* grid, const float* mfp_cells, double mf
   h->d_order = static_cast<uint16_t*>(h->dev_alloc(size_t(kChunk) * (G.q + 17) * 2));
   h->d_red = static_cast<double*>(h->dev_alloc(8 * sizeof(double)));
   h->d_status = static_cast<int*>(h->dev_alloc(256));
-  if (h->planes) h->has_tmap = make_plane_tensor_map(h->tmap, h->planes, h->storage, g, &h->tmap_why);
+  if (h->planes)
+    h->has_tmap = make_plane_tensor_map(h->tmap, h->planes, h->storage, g, 2 * G.q, &h->tmap_why);
   if (h->has_tmap) h->step_variant = 3;   // the fastest step kernel where it applies
   if (h->field_w) h->wfield = static_cast<float*>(h->dev_alloc(size_t(g.plane) * 4));
   if (!h->planes || !h->e[0] || !h->e[1] || (n_e == 3 && !h->e[2]) || !h->consts ||
@@ -561,6 +567,8 @@ static wlbm_status enqueue_steps(wlbm_handle* h, int count, bool profile) {
     sa.xper = h->xper; sa.yper = h->yper; sa.wrap = wrap;
     sa.tmap = h->has_tmap ? h->tmap : nullptr;
     sa.order = h->d_order + size_t(t) * (g.q + 17);
+    int tx_unused = 0, ty_unused = 0;
+    tma_cover(h->bc_kind, g.nx, g.ny, &sa, &tx_unused, &ty_unused);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (profile) {
       if (h->prof_used + 2 > h->prof_ev.size()) {
@@ -824,13 +832,22 @@ static wlbm_status adj_alloc(wlbm_handle* h, int64_t n, int k) {
   A.dT0 = static_cast<float*>(get(cells));
   A.gtw = static_cast<double*>(get(4 * sizeof(double)));
   A.codes = static_cast<uint8_t*>(get(size_t(n) * g.q));
+  A.order = static_cast<uint16_t*>(get(size_t(n) * (g.q + 17) * 2));
   if (!A.ckpt || !A.ckpt_e || !A.tape || !A.lam[0] || !A.lam[1] || !A.sh[0] || !A.sh[1] ||
       !A.erec[0] || !A.erec[1] ||
-      !A.gw || !A.dwc || !A.dT0 || !A.gtw || !A.codes)
+      !A.gw || !A.dwc || !A.dT0 || !A.gtw || !A.codes || !A.order)
     return h->fail(WLBM_ERR_OOM, "wlbm_adjoint_forward: device allocation failed");
   A.n = n;
   A.k = k;
   A.nck = nck;
+  std::string why;
+  A.has_tape_tmap = make_plane_tensor_map(A.tape_tmap, A.tape, WLBM_STORE_FP32_DEV, g, k * g.q,
+                                          &why);
+  A.has_lam_tmap = true;
+  for (int b = 0; b < 2; ++b)
+    A.has_lam_tmap = A.has_lam_tmap &&
+                     make_box_tensor_map(A.lam_tmap[b], A.lam[b], WLBM_STORE_FP32_DEV, g, g.q,
+                                         kAdjTmaBoxRows, &why);
   // tape slots and energy planes: pads must read zero
   cudaError_t e = cudaMemsetAsync(A.tape, 0, size_t(k) * state + 1024, h->stream);
   for (int j = 0; j < 2 && e == cudaSuccess; ++j)
@@ -863,15 +880,22 @@ wlbm_status wlbm_adjoint_forward(wlbm_handle* h, const float* dT0, int64_t n_ste
     dwc[c] = float(d);
   }
   std::vector<uint8_t> codes(size_t(n_steps) * g.q);
+  std::vector<uint16_t> order(size_t(n_steps) * (g.q + 17));
   TasState ts;
   ts.reset(g.q);
-  for (int64_t t = 0; t < n_steps; ++t) tas_advance(h->lat, &ts, codes.data() + t * g.q);
+  for (int64_t t = 0; t < n_steps; ++t) {
+    tas_advance(h->lat, &ts, codes.data() + t * g.q);
+    sort_by_kind(codes.data() + t * g.q, g.q, order.data() + t * (g.q + 17));
+  }
   cudaStream_t s = h->stream;
   st = h->cuda(cudaMemcpyAsync(A.dwc, dwc.data(), dwc.size() * 4, cudaMemcpyHostToDevice, s),
                "wlbm_adjoint_forward");
   if (st == WLBM_OK)
     st = h->cuda(cudaMemcpyAsync(A.codes, codes.data(), codes.size(), cudaMemcpyHostToDevice, s),
                  "wlbm_adjoint_forward");
+  if (st == WLBM_OK)
+    st = h->cuda(cudaMemcpyAsync(A.order, order.data(), order.size() * 2, cudaMemcpyHostToDevice,
+                                 s), "wlbm_adjoint_forward");
   if (st == WLBM_OK)
     st = h->cuda(cudaMemcpyAsync(A.dT0, dT0, size_t(g.nx) * g.ny * 4, cudaMemcpyDeviceToDevice, s),
                  "wlbm_adjoint_forward");
@@ -972,6 +996,14 @@ wlbm_status wlbm_adjoint_backward(wlbm_handle* h, const float* dJ_dT, float* dJ_
         sa.variant = h->step_variant; sa.status = h->d_status;
         sa.tape = 1; sa.tape_dst = slot + state;
         sa.wrap = h->xper && h->yper && g.nx >= 2 && g.ny >= 2;
+        if (h->step_variant == 3 && A.has_tape_tmap) {   // TMA tiles read the tape's slots
+          sa.wrap = 0;                                     // (the periodic pass ran above)
+          sa.tmap = A.tape_tmap;
+          sa.order = A.order + size_t(s0 + j) * (g.q + 17);
+          sa.tape_z0 = j * g.q;
+          int tx_unused = 0, ty_unused = 0;
+          tma_cover(h->bc_kind, g.nx, g.ny, &sa, &tx_unused, &ty_unused);
+        }
         ok(launch_step(h->storage, sa, s), "adjoint: recompute");
         ec ^= 1;
       }
@@ -984,7 +1016,12 @@ wlbm_status wlbm_adjoint_backward(wlbm_handle* h, const float* dJ_dT, float* dJ_
       aa.s_out = A.sh[cur ^ 1];
       aa.dtil = A.tape + size_t(j) * state;
       aa.codes = A.codes + size_t(s0 + j) * g.q;
-      ok(launch_adj_step(aa, s), "adjoint: reverse step");
+      if (h->step_variant == 3 && A.has_tape_tmap && A.has_lam_tmap)
+        ok(launch_adj_tma(aa, A.lam_tmap[cur], A.tape_tmap, j * g.q,
+                          A.order + size_t(s0 + j) * (g.q + 17), h->d_status, s),
+           "adjoint: reverse step");
+      else
+        ok(launch_adj_step(aa, s), "adjoint: reverse step");
       // the periodic transpose is the same on every direction: it acts on lh and on s
       ok(launch_periodic_T(A.lam[cur ^ 1], g.plane, g.pitch, g.nx, g.ny, g.q, h->xper, h->yper, s),
          "adjoint: periodic transpose");
@@ -1130,11 +1167,14 @@ struct wlbm_batch {
   void layout() {
     total_tiles = 0;
     total_wall_blocks = 0;
-    const int tw = variant == 3 ? tma_tile_width() : step_tile_width(storage, variant);
-    const int th = variant == 3 ? tma_tile_rows() : kStepRows;
+    const int tw = step_tile_width(storage, variant);
     for (size_t k = 0; k < h.size(); ++k) {
       const Geom& g = h[k]->g;
-      const int tx = (g.nx + 2 + tw - 1) / tw, ty = (g.ny + 2 + th - 1) / th;
+      int tx = (g.nx + 2 + tw - 1) / tw, ty = (g.ny + 2 + kStepRows - 1) / kStepRows;
+      if (variant == 3) {   // tiles of the cells variant 3 computes
+        StepArgs cover{};
+        tma_cover(h[k]->bc_kind, g.nx, g.ny, &cover, &tx, &ty);
+      }
       h_inst[k].tiles_x = tx;
       h_inst[k].first_tile = total_tiles;
       total_tiles += tx * ty;
@@ -1368,6 +1408,8 @@ wlbm_status wlbm_batch_step(wlbm_batch* b, int64_t n) {
       a.variant = b->variant; a.status = x->d_status;
       a.xper = x->xper; a.yper = x->yper;
       a.wrap = b->wraps(x);
+      int tx_unused = 0, ty_unused = 0;
+      tma_cover(x->bc_kind, g.nx, g.ny, &a, &tx_unused, &ty_unused);
       for (int j = 0; j < 3; ++j) I.e[j] = x->e[j];
       I.codes = b->d_codes + b->code_off[k];
       I.order = b->d_order + b->order_off[k];

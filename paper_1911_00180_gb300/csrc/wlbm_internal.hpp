@@ -14,12 +14,13 @@ namespace wlbm {
 // Framed geometry of every plane (in cells, any element type).
 //   rows: 0 = zero pad, 1 = ghost, 2..ny+1 = interior y = 0..ny-1, ny+2 = ghost,
 //         ny+3 = zero pad.
-//   cols: kGhostCol = ghost x = -1, kGhostCol+1.. = interior, kGhostCol+nx+1 = ghost,
-//         the column after it is a zero pad; columns before kGhostCol are zero pads.
-// The left ghost column sits on a 32-element boundary so that unshifted warp accesses
-// are aligned.  Pads are never written, so shifted reads past the frame read zero.
-constexpr int kGhostCol = 32;
-constexpr int kX0 = kGhostCol + 1;
+//   cols: kGhostCol = ghost x = -1, kX0 = kGhostCol+1.. = interior, kX0+nx = ghost, the
+//         column after it is a zero pad; columns before kGhostCol are zero pads.
+// The interior starts on a 32-element boundary, so tiles of interior cells start 128-byte
+// aligned (and tensor-copy boxes 16-byte aligned).  Pads are never written, so shifted
+// reads past the frame read zero.
+constexpr int kX0 = 32;
+constexpr int kGhostCol = kX0 - 1;
 constexpr int kMaxQ = 1024;
 constexpr int kStepRows = 8;   // rows (warps) per block of the step kernels
 
@@ -72,6 +73,12 @@ struct StepArgs {
   // variant 3: this step's directions sorted by kind (hop | paused << 3, stable), q
   // entries, followed by the 17 starts of the 16 kinds; nullptr selects variant 1
   const uint16_t* order;
+  // variant 3: the frame cells the step computes, columns cmin..cmax and rows rmin..rmax
+  // (ghost cells only on adiabatic-diffuse sides: the other boundary passes overwrite
+  // theirs before the next step), and the first column of the first tile
+  int cmin, cmax, rmin, rmax, cbase;
+  // variant 3 in tape mode: tensor-map plane index of plane 0 of the source slot
+  int tape_z0;
 };
 
 // Stable sort of one step's directions by kind = hop | paused << 3 (16 kinds): writes the
@@ -272,6 +279,30 @@ struct AdjArgs {
   double* gtw;
 };
 
+#ifdef __CUDACC__
+// W_corr of frame cell (r, c) for the reverse step: the framed field, or w0 by the frame
+// rule (pads and wall ghosts 0).
+__device__ __forceinline__ float w_at(const AdjArgs& a, int r, int c) {
+  if (a.wfield) return a.wfield[int64_t(r) * a.pitch + c];
+  if (r < 1 || r > a.ny + 2 || c < kGhostCol || c > kX0 + a.nx) return 0.f;
+  const bool gx = (c == kGhostCol) || (c == kX0 + a.nx);
+  const bool gy = (r == 1) || (r == a.ny + 2);
+  if ((gx && !a.xper) || (gy && !a.yper)) return 0.f;
+  return a.w0;
+}
+
+// Wall index of an isothermal wall cell (r, c), or -1.
+__device__ __forceinline__ int iso_wall_of(const AdjArgs& a, int r, int c) {
+  const bool xl = c == kGhostCol, xr = c == kX0 + a.nx, yb = r == 1, yt = r == a.ny + 2;
+  if ((xl || xr) && (yb || yt)) return a.iso_corner[(yt ? 2 : 0) + (xr ? 1 : 0)];
+  if (xl) return a.iso_side[0];
+  if (xr) return a.iso_side[1];
+  if (yb) return a.iso_side[2];
+  if (yt) return a.iso_side[3];
+  return -1;
+}
+#endif
+
 // Sets the message returned by wlbm_last_error(NULL).
 void set_global_error_msg(const std::string& m);
 
@@ -287,8 +318,21 @@ cudaError_t launch_step_tma_batch(int storage, const BatchInst* insts, int n, in
                                   int total_tiles, int t, cudaStream_t s);
 int tma_tile_width();
 int tma_tile_rows();
-bool make_plane_tensor_map(void* out, void* planes, int storage, const Geom& g,
+// Cells and tiles of a variant-3 step for sides of the given kinds (x-, x+, y-, y+):
+// sets a->cmin..cbase, returns the tile counts along x and y.
+void tma_cover(const int bc_kind[4], int nx, int ny, StepArgs* a, int* tiles_x, int* tiles_y);
+bool make_plane_tensor_map(void* out, void* planes, int storage, const Geom& g, int nplanes,
                            std::string* why);
+// The same with a box of box_rows rows (the 128 + 2V columns of a tile).
+bool make_box_tensor_map(void* out, void* planes, int storage, const Geom& g, int nplanes,
+                         int box_rows, std::string* why);
+// Reverse step with TMA tiles (float32): lam_map describes the q planes of a.lam_in (box
+// of kAdjTmaBoxRows rows), tape_map the adjoint tape (the forward map's box); tape_z0 is the
+// plane index of the step's slot in the tape, order the step's kind-sorted directions.
+constexpr int kAdjTmaBoxRows = 16;
+cudaError_t configure_adj_tma();
+cudaError_t launch_adj_tma(const AdjArgs& a, const void* lam_map, const void* tape_map,
+                           int tape_z0, const uint16_t* order, int* status, cudaStream_t s);
 // Batched launches (one launch per step for all instances of a batch).
 int step_tile_width(int storage, int variant);
 cudaError_t launch_step_batch(int storage, int variant, const BatchInst* insts, int n,
