@@ -163,10 +163,12 @@ wlbm_status wlbm_adjoint_backward(wlbm_handle* h, const float* dJ_dT, float* dJ_
  *                          copy per direction and 128 x 14 tile, register-resident cell
  *                          data, directions processed grouped by hop kind.  Variants 0-2
  *                          give bit-identical results; variant 3 sums E' in another order
- *                          (equal up to float rounding).  Steps that fuse the periodic
- *                          mirrors (WLBM_OPT_FUSE_PERIODIC) or record the adjoint's tape
- *                          run variant 1 when variant 3 is selected; with variant 3 the
- *                          periodic pass is never fused.
+ *                          (equal up to float rounding).  Variant 3 computes ghost cells
+ *                          only where an adiabatic-diffuse wall reads them: after a step
+ *                          the ghost cells of periodic and isothermal sides hold what the
+ *                          last boundary pass wrote (copies or wall values, not state).
+ *                          Variant 3 never fuses the periodic mirrors: with
+ *                          WLBM_OPT_FUSE_PERIODIC set it still runs the periodic pass.
  *   WLBM_OPT_GRAPH_STEPS   0 (default): launch every step's kernels directly; G > 0, a
  *                          multiple of 6: run chunks of G steps as one captured CUDA
  *                          graph (for small, launch-bound grids; not while profiling and
