@@ -7,7 +7,8 @@
 //              re-emit them into the inward ones with fractions w_i (s_i.n) / sum
 //              (Eq. adiabatic-diffuse, normalised so that energy is conserved).
 //  k_periodic  periodic links (Sec. 2.6): ghost rows copy the opposite interior rows,
-//              then ghost columns copy the opposite columns (corners via the diagonal).
+//              then ghost columns copy the opposite columns (corners via the diagonal);
+//              before a step, per plane only the side that step's hop pulls from.
 //  k_init      local equilibrium start e_i = w_i e_eq(T) (Sec. 2.4) in float64.
 //  k_moments   T - T_ref by Eq. pseudo-T in a cancellation-free form, q by Eq. q_corr.
 //  k_reduce    float64 sums: energy (interior, + wall cells), mean heat flux.
@@ -48,62 +49,117 @@ __device__ __forceinline__ float dev_store(T* p, float d, float wi, const float*
 // warp, then over the warps in a fixed order.  Vertical walls and corners: one warp per
 // cell (walls_cell), which keeps many warps busy on the few, strided cells.
 constexpr int kWallWarps = 8;
+constexpr int kHoldChunk = 16;   // values per lane held at once along horizontal walls
+constexpr int kHoldCell = 8;     // values per lane held at once by a warp on one cell
 static_assert(kWallChunk == 32, "one lane per ghost cell of a chunk");
 static_assert(kWallCellsPerBlock == kWallWarps, "one warp per cell of a block");
 
+// Per-direction data of a wall block in shared memory: plane parity of the step, w_i and
+// the segment's re-emission fractions, staged once so that no value load waits on them.
+struct WallSmem {
+  float part[kWallWarps * 32];
+  float w[kMaxQ];
+  float rho[kMaxQ];
+  uint8_t par[kMaxQ];
+};
+
+// Deviation of a stored value (bfloat16: scale * v + w_i R with the cell's reference R) and
+// its inverse for a store; the same rounded operations as dev_load / dev_store.
+template <typename T>
+__device__ __forceinline__ float wall_load(const T* p, float wi, bool ref, float R, float scale) {
+  const float v = Elem<T>::ld(p);
+  return ref ? fmaf(v, scale, __fmul_rn(wi, R)) : v;
+}
+template <typename T>
+__device__ __forceinline__ void wall_store(T* p, float d, float wi, bool ref, float R,
+                                           float inv_scale) {
+  if (!ref) {
+    Elem<T>::st(p, d);
+    return;
+  }
+  Elem<T>::st(p, __fmul_rn(__fsub_rn(d, __fmul_rn(wi, R)), inv_scale));
+}
+
 // One ghost cell by one warp, lanes over the directions (vertical walls and corners).
 template <typename T>
-__device__ __forceinline__ void walls_cell(const WallArgs& a, const uint8_t* codes,
+__device__ __forceinline__ void walls_cell(const WallArgs& a, const WallSmem& sm,
                                            float* e_ref, const WallSeg& g, int idx, int lane) {
   const int64_t off = int64_t(g.r0 + idx * g.dr) * a.pitch + (g.c0 + idx * g.dc);
   T* planes = static_cast<T*>(a.planes);
-  auto ptr = [&](int i) {
-    const int par = a.tape ? 0 : (codes[i] >> 4) & 1;
-    return planes + int64_t(par * a.q + i) * a.plane + off;
-  };
+  auto ptr = [&](int i) { return planes + int64_t(sm.par[i] * a.q + i) * a.plane + off; };
   if (g.action == WLBM_BC_ISOTHERMAL) {
     if (e_ref) {
       for (int i = lane; i < a.q; i += 32) Elem<T>::st(ptr(i), 0.f);
       if (lane == 0) e_ref[off] = g.iso;
     } else {
-      for (int i = lane; i < a.q; i += 32) Elem<T>::st(ptr(i), a.w[i] * g.iso);
+      for (int i = lane; i < a.q; i += 32) Elem<T>::st(ptr(i), sm.w[i] * g.iso);
     }
     return;
   }
-  const float* rho = a.rho + int64_t(g.table) * a.q;
+  const bool ref = e_ref != nullptr;
+  const float R = ref ? e_ref[off] : 0.f;
+  if (a.q <= 32 * kHoldCell) {
+    // every value of the cell in flight at once: one load round, one store round
+    float val[kHoldCell];
+#pragma unroll
+    for (int u = 0; u < kHoldCell; ++u) {
+      const int i = lane + 32 * u;
+      val[u] = i < a.q ? wall_load(ptr(i), sm.w[i], ref, R, a.scale) : 0.f;
+    }
+    float part = 0.f;
+#pragma unroll
+    for (int u = 0; u < kHoldCell; ++u) {
+      const int i = lane + 32 * u;
+      if (i < a.q && sm.rho[i] == 0.f) part += val[u];
+    }
+    const float A = warp_sum(part);
+#pragma unroll
+    for (int u = 0; u < kHoldCell; ++u) {
+      const int i = lane + 32 * u;
+      if (i >= a.q) continue;
+      const float d = sm.rho[i] == 0.f ? 0.f : fmaf(A, sm.rho[i], val[u]);
+      wall_store(ptr(i), d, sm.w[i], ref, R, a.inv_scale);
+    }
+    return;
+  }
   float part = 0.f;
   for (int i = lane; i < a.q; i += 32)
-    if (rho[i] == 0.f) part += dev_load(ptr(i), a.w[i], e_ref, off, a.scale);
+    if (sm.rho[i] == 0.f) part += wall_load(ptr(i), sm.w[i], ref, R, a.scale);
   const float A = warp_sum(part);
   for (int i = lane; i < a.q; i += 32) {
-    const float d = rho[i] == 0.f ? 0.f
-                                  : fmaf(A, rho[i], dev_load(ptr(i), a.w[i], e_ref, off, a.scale));
-    dev_store(ptr(i), d, a.w[i], e_ref, off, a.scale, a.inv_scale);
+    const float d = sm.rho[i] == 0.f
+                        ? 0.f : fmaf(A, sm.rho[i], wall_load(ptr(i), sm.w[i], ref, R, a.scale));
+    wall_store(ptr(i), d, sm.w[i], ref, R, a.inv_scale);
   }
 }
 
 template <typename T>
 __device__ __forceinline__ void walls_chunk(const WallArgs& a, const uint8_t* codes,
-                                            float* e_ref, int chunk, float* part_s) {
+                                            float* e_ref, int chunk, WallSmem& sm) {
   int c = 0;
   const int s = wall_chunk_segment(a.nseg, a.seg, chunk, &c);
   if (s >= a.nseg) return;                     // uniform over the block
   const WallSeg g = a.seg[s];
   const int lane = int(threadIdx.x) & 31, warp = int(threadIdx.x) >> 5;
+  const bool diffuse = g.action != WLBM_BC_ISOTHERMAL;
+  const float* rho = a.rho + int64_t(g.table) * a.q;
+  for (int i = int(threadIdx.x); i < a.q; i += int(blockDim.x)) {
+    sm.par[i] = uint8_t(a.tape ? 0 : (codes[i] >> 4) & 1);
+    sm.w[i] = a.w[i];
+    sm.rho[i] = diffuse ? rho[i] : 0.f;
+  }
+  __syncthreads();
   if (!wall_seg_rowwise(g)) {                  // one warp per cell, lanes over directions
     const int cell = c * kWallCellsPerBlock + warp;
-    if (cell < g.count) walls_cell<T>(a, codes, e_ref, g, cell, lane);
+    if (cell < g.count) walls_cell<T>(a, sm, e_ref, g, cell, lane);
     return;
   }
   const int idx = c * 32 + lane;
   const bool on = idx < g.count;
   const int64_t off = on ? int64_t(g.r0 + idx * g.dr) * a.pitch + (g.c0 + idx * g.dc) : 0;
   T* planes = static_cast<T*>(a.planes);
-  auto ptr = [&](int i) {
-    const int par = a.tape ? 0 : (codes[i] >> 4) & 1;
-    return planes + int64_t(par * a.q + i) * a.plane + off;
-  };
-  if (g.action == WLBM_BC_ISOTHERMAL) {
+  auto ptr = [&](int i) { return planes + int64_t(sm.par[i] * a.q + i) * a.plane + off; };
+  if (!diffuse) {
     if (!on) return;
     if (e_ref) {
       // bfloat16: make the wall's own equilibrium the reference of the cell, so the
@@ -111,36 +167,66 @@ __device__ __forceinline__ void walls_chunk(const WallArgs& a, const uint8_t* co
       for (int i = warp; i < a.q; i += kWallWarps) Elem<T>::st(ptr(i), 0.f);
       if (warp == 0) e_ref[off] = g.iso;
     } else {
-      for (int i = warp; i < a.q; i += kWallWarps) Elem<T>::st(ptr(i), a.w[i] * g.iso);
+      for (int i = warp; i < a.q; i += kWallWarps) Elem<T>::st(ptr(i), sm.w[i] * g.iso);
     }
     return;
   }
-  const float* rho = a.rho + int64_t(g.table) * a.q;
+  const bool ref = e_ref != nullptr;
+  const float R = ref && on ? e_ref[off] : 0.f;
+  if (a.q <= kWallWarps * kHoldChunk) {
+    // every value of the warp's directions in flight at once: one load round, one store
+    float val[kHoldChunk];
+#pragma unroll
+    for (int u = 0; u < kHoldChunk; ++u) {
+      const int i = warp + kWallWarps * u;
+      val[u] = on && i < a.q ? wall_load(ptr(i), sm.w[i], ref, R, a.scale) : 0.f;
+    }
+    float part = 0.f;
+#pragma unroll
+    for (int u = 0; u < kHoldChunk; ++u) {
+      const int i = warp + kWallWarps * u;
+      if (i < a.q && sm.rho[i] == 0.f) part += val[u];
+    }
+    sm.part[warp * 32 + lane] = part;
+    __syncthreads();
+    float A = 0.f;
+#pragma unroll
+    for (int k = 0; k < kWallWarps; ++k) A += sm.part[k * 32 + lane];
+    if (!on) return;
+#pragma unroll
+    for (int u = 0; u < kHoldChunk; ++u) {
+      const int i = warp + kWallWarps * u;
+      if (i >= a.q) continue;
+      const float d = sm.rho[i] == 0.f ? 0.f : fmaf(A, sm.rho[i], val[u]);
+      wall_store(ptr(i), d, sm.w[i], ref, R, a.inv_scale);
+    }
+    return;
+  }
   float part = 0.f;
   if (on) {
 #pragma unroll 4
     for (int i = warp; i < a.q; i += kWallWarps)
-      if (rho[i] == 0.f) part += dev_load(ptr(i), a.w[i], e_ref, off, a.scale);
+      if (sm.rho[i] == 0.f) part += wall_load(ptr(i), sm.w[i], ref, R, a.scale);
   }
-  part_s[warp * 32 + lane] = part;
+  sm.part[warp * 32 + lane] = part;
   __syncthreads();
   float A = 0.f;
 #pragma unroll
-  for (int k = 0; k < kWallWarps; ++k) A += part_s[k * 32 + lane];
+  for (int k = 0; k < kWallWarps; ++k) A += sm.part[k * 32 + lane];
   if (!on) return;
 #pragma unroll 4
   for (int i = warp; i < a.q; i += kWallWarps) {
     // collected directions are absorbed (0); the others receive their share of A
-    const float d = rho[i] == 0.f ? 0.f
-                                  : fmaf(A, rho[i], dev_load(ptr(i), a.w[i], e_ref, off, a.scale));
-    dev_store(ptr(i), d, a.w[i], e_ref, off, a.scale, a.inv_scale);
+    const float d = sm.rho[i] == 0.f
+                        ? 0.f : fmaf(A, sm.rho[i], wall_load(ptr(i), sm.w[i], ref, R, a.scale));
+    wall_store(ptr(i), d, sm.w[i], ref, R, a.inv_scale);
   }
 }
 
 template <typename T>
 __global__ void __launch_bounds__(32 * kWallWarps) k_walls(const WallArgs a) {
-  __shared__ float part_s[kWallWarps * 32];
-  walls_chunk<T>(a, a.codes, a.e_ref, int(blockIdx.x), part_s);
+  __shared__ WallSmem sm;
+  walls_chunk<T>(a, a.codes, a.e_ref, int(blockIdx.x), sm);
 }
 
 // Batched wall pass: block b belongs to the instance whose first_block is the largest one
@@ -148,7 +234,7 @@ __global__ void __launch_bounds__(32 * kWallWarps) k_walls(const WallArgs a) {
 template <typename T>
 __global__ void __launch_bounds__(32 * kWallWarps) k_walls_batch(const BatchWalls* B, int n,
                                                                   int t) {
-  __shared__ float part_s[kWallWarps * 32];
+  __shared__ WallSmem sm;
   const int b = int(blockIdx.x);
   int lo = 0, hi = n - 1;
   while (lo < hi) {
@@ -159,7 +245,7 @@ __global__ void __launch_bounds__(32 * kWallWarps) k_walls_batch(const BatchWall
   const BatchWalls& I = B[lo];
   const int cur = (I.phase + t) % I.n_e;
   float* e_ref = I.n_e == 3 ? I.e[(cur + 2) % 3] : nullptr;
-  walls_chunk<T>(I.w, I.codes + size_t(t) * I.w.q, e_ref, b - I.first_block, part_s);
+  walls_chunk<T>(I.w, I.codes + size_t(t) * I.w.q, e_ref, b - I.first_block, sm);
 }
 
 template <typename T>
@@ -169,15 +255,30 @@ __global__ void k_periodic(const PeriodicArgs a) {
   const int ncx = a.xper ? 2 * (a.ny + 2) : 0;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= 2 * ncy + ncx) return;
+  const int p = blockIdx.y;
+  // Before a step with known codes, a direction plane gets only the ghost cells that step
+  // pulls from: the bottom (top) ghost row if its hop has c_y = +1 (-1), the left (right)
+  // ghost column if c_x = +1 (-1), nothing if it pauses.  Energy planes, the adjoint's tape
+  // and refreshes outside the step loop (a parity mask, no codes) copy everything.
+  const bool partial = p < a.q && !a.tape && !a.par && a.codes;
+  int hx = 0, hy = 0;
+  if (partial) {
+    const int code = a.codes[p];
+    if (code & 8) return;
+    hx = c_hop_x[code & 7];
+    hy = c_hop_y[code & 7];
+  }
   int rd, cd, rs, cs;
   if (t < 2 * ncy) {
     const int side = t / ncy, k = t - side * ncy;
+    if (partial && hy != (side == 0 ? 1 : -1)) return;
     cd = cs = cy0 + k;
     rd = side == 0 ? 1 : a.ny + 2;
     rs = side == 0 ? a.ny + 1 : 2;
   } else {
     const int k = t - 2 * ncy;
     const int side = k / (a.ny + 2);
+    if (partial && hx != (side == 0 ? 1 : -1)) return;
     rd = 1 + (k - side * (a.ny + 2));
     rs = rd;
     if (a.yper) {
@@ -188,7 +289,6 @@ __global__ void k_periodic(const PeriodicArgs a) {
     cs = side == 0 ? kX0 + a.nx - 1 : kX0;
   }
   const int64_t od = int64_t(rd) * a.pitch + cd, os = int64_t(rs) * a.pitch + cs;
-  const int p = blockIdx.y;
   if (p == a.q) {
     a.e_cur[od] = a.e_cur[os];
   } else if (p == a.q + 1) {

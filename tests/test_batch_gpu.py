@@ -31,6 +31,28 @@ def _specs():
     ]
 
 
+def _state(spec, frame):
+    """The framed state without the ghost cells of periodic and isothermal sides: those are
+    copies or fixed wall values that the boundary passes rewrite before a step reads them
+    (before a step, a periodic plane gets only the ghost side its hop pulls from), not
+    state.  Ghost cells of adiabatic-diffuse walls (and corners between two of them) hold
+    energy waiting to re-enter and are kept."""
+    f = np.array(frame, copy=True)
+    d = [k == A for k in spec["bc"]]            # x-, x+, y-, y+
+    if not d[0]:
+        f[:, :, 0] = 0
+    if not d[1]:
+        f[:, :, -1] = 0
+    if not d[2]:
+        f[:, 0, :] = 0
+    if not d[3]:
+        f[:, -1, :] = 0
+    for (r, c, sx, sy) in ((0, 0, 0, 2), (0, -1, 1, 2), (-1, 0, 0, 3), (-1, -1, 1, 3)):
+        if not (d[sx] and d[sy]):
+            f[:, r, c] = 0
+    return f
+
+
 def _dTs(specs):
     return [W.random_dT(s["nx"], s["ny"], seed=11 + k, scale=0.5) for k, s in enumerate(specs)]
 
@@ -70,7 +92,7 @@ def test_batch_equals_single_grids_bitwise(storage, variant, graph, fuse):
     b.close()
     for k, (spec, dT) in enumerate(zip(specs, dTs)):
         want = _single(spec, dT, 61, storage, fuse, variant)
-        assert np.array_equal(got[k], want), k
+        assert np.array_equal(_state(spec, got[k]), _state(spec, want)), k
 
 
 def test_batch_autotune_then_run():
@@ -86,7 +108,8 @@ def test_batch_autotune_then_run():
     got = [v.wlbm_get_state().cpu().numpy() for v in b.instances]
     b.close()
     for k, (spec, dT) in enumerate(zip(specs, dTs)):
-        assert np.array_equal(got[k], _single(spec, dT, 20, 1, 0, rec["variant"])), k
+        want = _single(spec, dT, 20, 1, 0, rec["variant"])
+        assert np.array_equal(_state(spec, got[k]), _state(spec, want)), k
 
 
 def test_single_grid_autotune_keeps_results():
@@ -103,4 +126,4 @@ def test_single_grid_autotune_keeps_results():
     h.wlbm_step(30)
     got = h.wlbm_get_state().cpu().numpy()
     h.close()
-    assert np.array_equal(got, _single(spec, dT, 30, 1, 0, v))
+    assert np.array_equal(_state(spec, got), _state(spec, _single(spec, dT, 30, 1, 0, v)))
