@@ -167,23 +167,50 @@ __device__ __forceinline__ void dir_body(Regs3& t, const DirCtx<T>& c) {
     const int FR = 1 + k - CY;                    // tile row of the EED source
     float v[4], o[4], s[4];
     ring_values<T, DX>(c.ring_row + k * BW, c.lane, v);
+    if constexpr (!PAUSED && SC % 2 == 0) {
+      // source columns start on an even register: the per-element arithmetic runs on
+      // pairs (same rounded operations; x - y as fma(y, -1, x))
+      const float2 wi2 = make_float2(c.wi, c.wi);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      if constexpr (REF) {
-        // stored v' = (d' - w_i E_in(y)) / scale, d' from Eq. lbm-energy with the local
-        // reference R of the stored source value (see the bfloat16 storage note)
-        const float tt =
-            PAUSED ? __fadd_rn(__fsub_rn(t.X[1 + k][1 + j], c.fsc[((1 + k) * 6 + 1 + j) * 32]),
-                               c.fsc[(FR * 6 + FC + j) * 32])
-                   : t.X[SR][SC + j];
-        o[j] = fmaf(t.G[SR][SC + j], v[j], __fmul_rn(c.wi, __fsub_rn(tt, t.eins[k][j])));
-      } else {
-        o[j] = fmaf(t.G[SR][SC + j], v[j], __fmul_rn(c.wi, t.X[FR][FC + j]));
+      for (int jp = 0; jp < 4; jp += 2) {
+        const float2 g2 = make_float2(t.G[SR][SC + jp], t.G[SR][SC + jp + 1]);
+        const float2 v2 = make_float2(v[jp], v[jp + 1]);
+        float2 m2;
+        if constexpr (REF) {
+          const float2 x2 = make_float2(t.X[SR][SC + jp], t.X[SR][SC + jp + 1]);
+          const float2 e2 = make_float2(t.eins[k][jp], t.eins[k][jp + 1]);
+          m2 = __fmul2_rn(wi2, __ffma2_rn(e2, make_float2(-1.f, -1.f), x2));
+        } else {
+          m2 = __fmul2_rn(wi2, make_float2(t.X[FR][FC + jp], t.X[FR][FC + jp + 1]));
+        }
+        const float2 o2 = __ffma2_rn(g2, v2, m2);
+        o[jp] = o2.x;
+        o[jp + 1] = o2.y;
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        if constexpr (REF) {
+          // stored v' = (d' - w_i E_in(y)) / scale, d' from Eq. lbm-energy with the local
+          // reference R of the stored source value (see the bfloat16 storage note)
+          const float tt =
+              PAUSED ? __fadd_rn(__fsub_rn(t.X[1 + k][1 + j], c.fsc[((1 + k) * 6 + 1 + j) * 32]),
+                                 c.fsc[(FR * 6 + FC + j) * 32])
+                     : t.X[SR][SC + j];
+          o[j] = fmaf(t.G[SR][SC + j], v[j], __fmul_rn(c.wi, __fsub_rn(tt, t.eins[k][j])));
+        } else {
+          o[j] = fmaf(t.G[SR][SC + j], v[j], __fmul_rn(c.wi, t.X[FR][FC + j]));
+        }
       }
     }
     store4<T>(c.dst + k * c.pitch, o, c.vm, s);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) t.acc[k][j] += s[j];
+    for (int jp = 0; jp < 4; jp += 2) {
+      const float2 a2 = __fadd2_rn(make_float2(t.acc[k][jp], t.acc[k][jp + 1]),
+                                   make_float2(s[jp], s[jp + 1]));
+      t.acc[k][jp] = a2.x;
+      t.acc[k][jp + 1] = a2.y;
+    }
   }
 }
 
