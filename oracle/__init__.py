@@ -12,6 +12,8 @@ lattice   directions, angular weights, worm paths, Lambda_corr, W_corr, TAS sche
           (Sec. 2.3-2.5: Eqs. algorithm, W-correction, weight, worm-paths).
 stepper   framed-grid state, boundary conditions (Sec. 2.6), the step (Eqs. lbm-energy
           and algorithm), moments (Eqs. pseudo-T and q_corr) and FP64 reductions.
+transport effective conductivity (apparent and central-band), steady-state temperature
+          residual, Fuchs-Sondheimer reference ratios (Sec. 4.5).
 adjoint   the exact transpose of one step and its reverse sweep (derived from Eq.
           lbm-energy; the paper has no adjoint), plus central finite differences.
 

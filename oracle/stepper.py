@@ -152,10 +152,14 @@ class WormLBM:
         return inward, rho
 
     def _diffuse_cell(self, yy, xx, normal, strict):
+        """One diffuse ghost cell, or (yy, xx) index arrays of a wall's ghost cells
+        that share the normal; each cell is handled on its own."""
         inward, rho = self.diffuse_split(normal, strict)
-        a = self.d[~inward, yy, xx].sum()
-        self.d[~inward, yy, xx] = 0.0
-        self.d[inward, yy, xx] += a * rho[inward]
+        yy, xx = np.atleast_1d(yy)[None, :], np.atleast_1d(xx)[None, :]
+        out_i, in_i = np.flatnonzero(~inward)[:, None], np.flatnonzero(inward)[:, None]
+        a = self.d[out_i, yy, xx].sum(axis=0)           # collected energy per cell
+        self.d[out_i, yy, xx] = 0.0
+        self.d[in_i, yy, xx] += rho[in_i] * a[None, :]
 
     def delta_e(self, t):
         """e_eq(T) - e_ref in float64."""
@@ -166,8 +170,8 @@ class WormLBM:
         # 1. adiabatic diffuse walls (edges), then diffuse-diffuse corners
         for wall in (XM, XP, YM, YP):
             if k[wall] == ADIABATIC_DIFFUSE:
-                for (yy, xx) in self._edge_cells(wall):
-                    self._diffuse_cell(yy, xx, INWARD_NORMAL[wall], False)
+                cells = np.array(self._edge_cells(wall))
+                self._diffuse_cell(cells[:, 0], cells[:, 1], INWARD_NORMAL[wall], False)
         for (yy, xx, xw, yw) in self._corners():
             if k[xw] == ADIABATIC_DIFFUSE and k[yw] == ADIABATIC_DIFFUSE:
                 n = (INWARD_NORMAL[xw][0], INWARD_NORMAL[yw][1])
