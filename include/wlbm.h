@@ -117,13 +117,54 @@ int64_t wlbm_step_count(const wlbm_handle* h);
  * current state.  Each output is device nx*ny float32, or NULL to skip it. */
 wlbm_status wlbm_moments(wlbm_handle* h, float* dT, float* qx, float* qy);
 
-/* wlbm_reduce: float64 reductions over the current state, written to host out[4]:
- *   out[0] sum over interior cells of E - e_ref      (energy conservation, Eq.
- *          lbm-energy-density; the paper's energy with its unit prefactor set to 1)
- *   out[1] the same plus wall ghost cells (energy held by adiabatic walls)
+/* wlbm_reduce: float64 reductions over the current state (computed on the GPU in float64
+ * from the stored values), written to host out[WLBM_REDUCE_N].  Lattice units: cell =
+ * step = v_g = 1, energy as E - e_ref with the paper's unit prefactor set to 1.
+ *   out[0] sum over interior cells of E - e_ref   (energy conservation, Eq.
+ *          lbm-energy-density)
+ *   out[1] the same plus the ghost cells of adiabatic-diffuse walls (energy they hold;
+ *          a corner counts when both its walls are adiabatic-diffuse).  Periodic ghosts
+ *          are copies and isothermal ghosts the imposed reservoir, so neither counts.
  *   out[2] mean of q_x over interior cells, out[3] mean of q_y  (Eq. q_corr)
+ *   out[4] mean of q_x over the central band of columns x0 <= x < x0 + m, x0 = nx / 4,
+ *          m = nx / 2 (integer division; NaN if m < 1)
+ *   out[5] least-squares slope dE/dx of the y-averaged E over that band (NaN if m < 2)
+ *   out[6] apparent effective conductivity over the bulk one (Sec. 4.5; the paper calls
+ *          it apparent, Sec. 1): out[2] * nx / (D (e(T_x-) - e(T_x+))), where D = MFP/3
+ *          (grid.emulate_3d) or MFP/2 is the bulk diffusivity and e(T) = 1/(exp(theta/T)
+ *          - 1); NaN unless both x walls are isothermal at different temperatures, and
+ *          NaN for a per-cell MFP field
+ *   out[7] band effective conductivity over the bulk one: out[4] / (-D out[5]), free of
+ *          the temperature jumps at the x walls; NaN where out[5] is 0 or NaN, or for a
+ *          per-cell MFP field
+ *   out[8] steady-state residual: max over interior cells of |T^n - T^m| / (n - m) in
+ *          K per step, n the current step and m the step of the previous wlbm_reduce on
+ *          this handle (temperatures by Eq. pseudo-T in float64); NaN on the first call
+ *          after wlbm_init_temperature / wlbm_set_state / wlbm_adjoint_backward and when
+ *          no step ran since the previous call.  Each call takes the next snapshot
+ *          (library memory: nx*ny float64).
  * Synchronous. */
+#define WLBM_REDUCE_N 9
 wlbm_status wlbm_reduce(wlbm_handle* h, double* out);
+
+/* wlbm_run_steady: run to steady state.  The TAS pauses (Eq. algorithm) make the field,
+ * and above all the heat flux, fluctuate from step to step (Sec. 4.3: up to ~10 % of the
+ * flux on coarse grids, less on finer ones), so the test compares window means: each
+ * check runs check_every steps, the last avg_steps of them each followed by a reduction
+ * (10 steps in Sec. 4.3) that adds T - T_ref of every interior cell to a float64 window
+ * sum.  The residual of a check is max over interior cells of |mean of this window -
+ * mean of the previous window| / check_every (K per step; NaN for the first window).
+ * Checks repeat until the residual is <= tol or the next check would pass max_steps.
+ *   steps_run  host int64 (may be NULL): steps taken (a multiple of check_every)
+ *   converged  host int32 (may be NULL): 1 if the last residual was <= tol
+ *   out        host double[WLBM_REDUCE_N] (may be NULL): out[2..5] are the means of the
+ *              last window's avg_steps reductions, out[6..7] follow from those means,
+ *              out[0..1] are those of the last step, out[8] is the last window residual.
+ * Library memory: two nx*ny float64 planes, allocated on the first call.  Synchronous;
+ * WLBM_ERR_INVALID_ARG unless max_steps >= check_every >= avg_steps >= 1 and tol >= 0. */
+wlbm_status wlbm_run_steady(wlbm_handle* h, int64_t max_steps, int64_t check_every, double tol,
+                            int32_t avg_steps, int64_t* steps_run, int32_t* converged,
+                            double* out);
 
 /* wlbm_get_state / wlbm_set_state: the deviations e_i - w_i e_ref of the current state,
  * unscaled float32, layout [Q][ny+2][nx+2] including the one-cell ghost frame (index
@@ -194,8 +235,8 @@ wlbm_status wlbm_profile(wlbm_handle* h, int32_t enable);
 wlbm_status wlbm_profile_read(wlbm_handle* h, double* step_ms, int64_t* step_launches,
                               int64_t* all_launches);
 
-/* wlbm_reduce_state_noalloc: the four float64 sums of wlbm_reduce (same meaning and
- * order), computed from a caller-owned state instead of a handle, without allocating any
+/* wlbm_reduce_state_noalloc: the first four float64 values of wlbm_reduce (same meaning
+ * and order), computed from a caller-owned state instead of a handle, without allocating any
  * device memory.  The paper has no counterpart; this entry point exists for callers that
  * cannot allocate device memory where they call it: code running inside a host
  * application that has reserved the device memory for its own pool, or a monitoring
@@ -203,8 +244,8 @@ wlbm_status wlbm_profile_read(wlbm_handle* h, double* step_ms, int64_t* step_lau
  * may imply) is not acceptable.
  *   framed   device float32 [q][ny+2][nx+2]: deviations e_i - w_i e_ref including the
  *            ghost frame, as written by wlbm_get_state
- *   bc_kind  host int32[4] wall kinds x-, x+, y-, y+ (decides which ghost cells count as
- *            wall cells in out[1])
+ *   bc_kind  host int32[4] wall kinds x-, x+, y-, y+ (decides which ghost cells count
+ *            towards out[1])
  *   out      device double[4], written on the stream
  *   stream   cudaStream_t (NULL = legacy default stream)
  * Scratch: a file-scope device array of 1 MiB that every device loading the library keeps

@@ -251,9 +251,21 @@ class WormLBM:
 
     def total_energy(self, include_frame=False):
         """Sum of E - e_ref over the interior, or over the interior plus the ghost cells
-        that hold energy of their own (wall cells; periodic ghosts are copies)."""
+        that hold energy of the system: those of adiabatic-diffuse walls (a corner only
+        between two of them).  Periodic ghosts are copies; isothermal ghosts are the
+        imposed reservoir, reset by every boundary pass (Sec. 2.6)."""
         if not include_frame:
             return float(self.d[:, 1:-1, 1:-1].sum())
-        xs = slice(1, -1) if self.bc_kind[XM] == PERIODIC else slice(None)
-        ys = slice(1, -1) if self.bc_kind[YM] == PERIODIC else slice(None)
-        return float(self.d[:, ys, xs].sum())
+        k = self.bc_kind
+        fh, fw = self.ny + 2, self.nx + 2
+        side_x = np.full(fw, -1)
+        side_x[0], side_x[-1] = XM, XP
+        side_y = np.full(fh, -1)
+        side_y[0], side_y[-1] = YM, YP
+        total = float(self.d[:, 1:-1, 1:-1].sum())
+        for yy in range(fh):
+            for xx in range(fw):
+                sides = [s for s in (side_x[xx], side_y[yy]) if s >= 0]
+                if sides and all(k[s] == ADIABATIC_DIFFUSE for s in sides):
+                    total += float(self.d[:, yy, xx].sum())
+        return total

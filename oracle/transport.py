@@ -18,6 +18,11 @@ These functions fix one reading each, in lattice units (cell = step = v_g = 1):
                        central band of columns x0 <= x < x0 + m, x0 = floor(N_x/4),
                        m = floor(N_x/2); free of the wall jumps of the apparent value.
   residual             max over interior cells of |T^n(x) - T^m(x)| / (n - m), K/step.
+  steady run           the TAS pauses make the field fluctuate from step to step (Sec.
+                       4.3), so a steady-state check compares window means: every check
+                       runs C steps, the last K of them averaged; the residual is the
+                       largest change of the window-mean temperature per step between
+                       consecutive checks, and the flux outputs are window means.
 
 Reference ratios (Sec. 4.5):
   fuchs_sondheimer_3d  the textbook diffuse-wall (specularity 0) film ratio
@@ -117,3 +122,36 @@ def fuchs_sondheimer_2d(q, kn):
         if a > 0:
             g[i] = 1.0 - a * (-math.expm1(-1.0 / a))
     return float((w * c2 * g).sum() / (w * c2).sum())
+
+
+def run_steady(m, max_steps, check_every, tol, avg_steps, mfp, emulate_3d=True):
+    """Steady-state run of a WormLBM model by window means (reading above).  Returns
+    (steps, converged, residual, means) with means = (<q_x>, <q_y>, <q_x>_band, slope,
+    kappa_app, kappa_band) from the window means of the last check."""
+    steps, conv, residual, prev = 0, False, float("nan"), None
+    means = None
+    while steps + check_every <= max_steps and not conv:
+        m.step(check_every - avg_steps)
+        t_sum, vals = 0.0, []
+        for _ in range(avg_steps):
+            m.step(1)
+            t_sum = t_sum + m.temperature_dev()
+            qx, qy = m.heat_flux()
+            vals.append((float(qx.mean()), float(qy.mean())) + band_flux_and_slope(m))
+        steps += check_every
+        t_mean = t_sum / avg_steps
+        residual = temperature_residual(t_mean, prev, check_every) if prev is not None \
+            else float("nan")
+        prev = t_mean
+        conv = residual <= tol
+        means = tuple(float(np.mean([v[k] for v in vals])) for k in range(4))
+    qx_m, qy_m, qb, slope = means
+    d = bulk_diffusivity(mfp, emulate_3d)
+    k = m.bc_kind
+    if k[XM] == ISOTHERMAL and k[XP] == ISOTHERMAL and m.t_wall[XM] != m.t_wall[XP]:
+        de = float(L.e_eq(m.t_wall[XM], m.theta) - L.e_eq(m.t_wall[XP], m.theta))
+        k_app = qx_m * m.nx / (d * de)
+    else:
+        k_app = float("nan")
+    k_band = qb / (-d * slope) if slope != 0.0 else float("nan")
+    return steps, conv, residual, (qx_m, qy_m, qb, slope, k_app, k_band)

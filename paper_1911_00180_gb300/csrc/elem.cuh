@@ -62,6 +62,17 @@ struct Elem<__nv_bfloat16> {
   }
 };
 
+// Whether framed cell (fx, fy) of an fw x fh frame counts towards the energy held by the
+// walls: interior cells do not; a ghost cell does when every side it lies on is an
+// adiabatic-diffuse wall (bit k of diff_mask for side k = x-, x+, y-, y+).  Periodic
+// ghosts are copies and isothermal ghosts a reservoir reset by every wall pass.
+__device__ __forceinline__ bool wall_energy_cell(int fx, int fy, int fw, int fh, int diff_mask) {
+  const int sx = fx == 0 ? 0 : (fx == fw - 1 ? 1 : -1);
+  const int sy = fy == 0 ? 2 : (fy == fh - 1 ? 3 : -1);
+  if (sx < 0 && sy < 0) return false;
+  return (sx < 0 || ((diff_mask >> sx) & 1)) && (sy < 0 || ((diff_mask >> sy) & 1));
+}
+
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

@@ -11,7 +11,10 @@
 //              before a step, per plane only the side that step's hop pulls from.
 //  k_init      local equilibrium start e_i = w_i e_eq(T) (Sec. 2.4) in float64.
 //  k_moments   T - T_ref by Eq. pseudo-T in a cancellation-free form, q by Eq. q_corr.
-//  k_reduce    float64 sums: energy (interior, + wall cells), mean heat flux.
+//  k_reduce    float64 sums: energy (interior, + adiabatic-wall ghost cells), heat flux
+//              (all cells and the central band of columns), band energy moment for the
+//              conductivity fit, and the largest temperature change since the previous
+//              reduction (and between window means, for the steady-state run).
 #include "elem.cuh"
 #include "wlbm_internal.hpp"
 
@@ -350,19 +353,38 @@ __global__ void k_moments(const MomentArgs a) {
   }
 }
 
+// T - T_ref of a local-energy deviation de in float64 (Eq. pseudo-T, the same
+// cancellation-free form as k_moments).
+__device__ __forceinline__ double temperature_dev64(double de, const ReduceArgs& a) {
+  const double dl = log1p(de / a.e_ref1) - log1p(de / a.e_ref);
+  return -a.theta * dl / (a.l_ref * (a.l_ref + dl));
+}
+
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long u = __shfl_xor_sync(0xffffffffu, v, o);
+    v = u > v ? u : v;
+  }
+  return v;
+}
+
 template <typename T>
 __global__ void k_reduce(const ReduceArgs a) {
   const int fw = a.nx + 2, fh = a.ny + 2;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  double v[4] = {0.0, 0.0, 0.0, 0.0};
+  double v[kReduceSums] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  double res = 0.0;   // |T - T_snap| of this cell (non-negative or NaN)
+  double resw = 0.0;  // |window mean - previous window mean|
   if (t < fw * fh) {
     const int fy = t / fw, fx = t - fy * fw;
     const bool gx = fx == 0 || fx == fw - 1, gy = fy == 0 || fy == fh - 1;
     const int64_t off = int64_t(fy + 1) * a.pitch + (kGhostCol + fx);
     const T* planes = static_cast<const T*>(a.planes);
     if (!gx && !gy) {
-      v[0] = double(a.e_cur[off]);
-      v[1] = v[0];
+      const double e = double(a.e_cur[off]);
+      v[0] = e;
+      v[1] = e;
       double qx = 0.0, qy = 0.0;
       for (int i = 0; i < a.q; ++i) {
         const double u = dev_load(planes + int64_t(parity_of(a.par, i) * a.q + i) * a.plane + off,
@@ -372,7 +394,26 @@ __global__ void k_reduce(const ReduceArgs a) {
       }
       v[2] = qx;
       v[3] = qy;
-    } else if (!(gx && a.xper) && !(gy && a.yper)) {
+      const int x = fx - 1;
+      if (x >= a.band_x0 && x < a.band_x0 + a.band_w) {
+        v[4] = qx;
+        v[5] = (double(x) - a.band_xbar) * e;
+      }
+      const int64_t c = int64_t(fy - 1) * a.nx + x;
+      const double tn = temperature_dev64(e, a);
+      if (a.has_snap) res = fabs(tn - a.snap[c]);
+      a.snap[c] = tn;
+      if (a.win) {
+        const double acc = a.win_first ? tn : a.win[c] + tn;
+        if (a.win_last) {
+          const double mean = acc * a.win_inv;
+          if (a.win_has_prev) resw = fabs(mean - a.win_prev[c]);
+          a.win_prev[c] = mean;
+        } else {
+          a.win[c] = acc;
+        }
+      }
+    } else if (wall_energy_cell(fx, fy, fw, fh, a.diff_mask)) {
       double e = 0.0;
       for (int i = 0; i < a.q; ++i)
         e += dev_load(planes + int64_t(parity_of(a.par, i) * a.q + i) * a.plane + off, a.w[i],
@@ -380,21 +421,35 @@ __global__ void k_reduce(const ReduceArgs a) {
       v[1] = e;
     }
   }
-  __shared__ double red[4][32];
+  __shared__ double red[kReduceSums][32];
+  __shared__ unsigned long long redm[2][32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
-  for (int k = 0; k < 4; ++k) {
+  for (int k = 0; k < kReduceSums; ++k) {
     const double s = warp_sum(v[k]);
     if (lane == 0) red[k][wid] = s;
+  }
+  // |.| is non-negative, so its bit pattern orders like its value (NaN above all)
+  const unsigned long long m0 = warp_max_u64(static_cast<unsigned long long>(__double_as_longlong(res)));
+  const unsigned long long m1 = warp_max_u64(static_cast<unsigned long long>(__double_as_longlong(resw)));
+  if (lane == 0) {
+    redm[0][wid] = m0;
+    redm[1][wid] = m1;
   }
   __syncthreads();
   if (wid == 0) {
     const int nw = blockDim.x >> 5;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < kReduceSums; ++k) {
       double s = lane < nw ? red[k][lane] : 0.0;
       s = warp_sum(s);
       if (lane == 0 && s != 0.0) atomicAdd(a.out + k, s);
+    }
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const unsigned long long mm = warp_max_u64(lane < nw ? redm[k][lane] : 0ull);
+      if (lane == 0 && mm != 0ull)
+        atomicMax(reinterpret_cast<unsigned long long*>(a.out + kReduceSums + k), mm);
     }
   }
 }

@@ -40,9 +40,9 @@ __device__ __forceinline__ void ring_unit(int i, int m, double* sx, double* sy) 
   *sy = y / len;
 }
 
-// One block per kThreads framed cells: (sum E interior, sum E interior + wall cells,
-// sum q_x, sum q_y) of its cells into partials[block].
-__global__ void k_partials(const float* framed, int nx, int ny, int q, int xper, int yper,
+// One block per kThreads framed cells: (sum E interior, sum E interior + adiabatic-wall
+// ghost cells, sum q_x, sum q_y) of its cells into partials[block].
+__global__ void k_partials(const float* framed, int nx, int ny, int q, int diff_mask,
                            double* partials) {
   const int fw = nx + 2, fh = ny + 2;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -65,7 +65,7 @@ __global__ void k_partials(const float* framed, int nx, int ny, int q, int xper,
       v[1] = e;
       v[2] = qx;
       v[3] = qy;
-    } else if (!(gx && xper) && !(gy && yper)) {
+    } else if (wlbm::wall_energy_cell(fx, fy, fw, fh, diff_mask)) {
       double e = 0.0;
       for (int i = 0; i < q; ++i) e += framed[int64_t(i) * plane + t];
       v[1] = e;
@@ -150,9 +150,10 @@ extern "C" wlbm_status wlbm_reduce_state_noalloc(const float* framed, int32_t nx
     return WLBM_ERR_CUDA;
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  k_partials<<<unsigned(nblocks), kThreads, 0, s>>>(framed, nx, ny, q,
-                                                     bc_kind[0] == WLBM_BC_PERIODIC,
-                                                     bc_kind[2] == WLBM_BC_PERIODIC, partials);
+  int diff_mask = 0;
+  for (int k = 0; k < 4; ++k)
+    if (bc_kind[k] == WLBM_BC_ADIABATIC_DIFFUSE) diff_mask |= 1 << k;
+  k_partials<<<unsigned(nblocks), kThreads, 0, s>>>(framed, nx, ny, q, diff_mask, partials);
   k_finish<<<1, kThreads, 0, s>>>(partials, int(nblocks), 1.0 / (double(nx) * ny), out);
   const cudaError_t le = cudaGetLastError();
   if (le != cudaSuccess) {

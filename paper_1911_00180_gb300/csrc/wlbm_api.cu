@@ -3,6 +3,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <limits>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -51,7 +52,11 @@ struct wlbm_handle {
   float* consts = nullptr;    // w[q], sx[q], sy[q], rho[8][q]
   uint8_t* d_codes = nullptr; // [kChunk][q]
   uint16_t* d_order = nullptr; // [kChunk][q + 17] kind-sorted directions (variant 3)
-  double* d_red = nullptr;    // [4]
+  double* d_red = nullptr;    // [kReduceOut]
+  double* d_snap = nullptr;   // nx*ny float64 T - T_ref at the last reduction
+  int64_t snap_step = -1;     // step of that snapshot (-1: none since the state was set)
+  double* d_win = nullptr;    // nx*ny float64 window sum and previous window mean of
+  double* d_win_prev = nullptr;   // T - T_ref (wlbm_run_steady; allocated on first use)
   int* d_status = nullptr;    // bit 0: a bounded device wait gave up
   int step_variant = 1;       // 0 register-pipelined, 1 per-warp bulk-copy ring,
                               // 2 warp-specialised ring, 3 TMA tiles
@@ -431,13 +436,14 @@ wlbm_status wlbm_create(const wlbm_grid* grid, const float* mfp_cells, double mf
   h->d_codes = static_cast<uint8_t*>(h->dev_alloc(size_t(kChunk) * G.q));
   h->d_order = static_cast<uint16_t*>(h->dev_alloc(size_t(kChunk) * (G.q + 17) * 2));
   h->d_red = static_cast<double*>(h->dev_alloc(8 * sizeof(double)));
+  h->d_snap = static_cast<double*>(h->dev_alloc(size_t(g.nx) * g.ny * sizeof(double)));
   h->d_status = static_cast<int*>(h->dev_alloc(256));
   if (h->planes)
     h->has_tmap = make_plane_tensor_map(h->tmap, h->planes, h->storage, g, 2 * G.q, &h->tmap_why);
   if (h->has_tmap) h->step_variant = 3;   // the fastest step kernel where it applies
   if (h->field_w) h->wfield = static_cast<float*>(h->dev_alloc(size_t(g.plane) * 4));
   if (!h->planes || !h->e[0] || !h->e[1] || (n_e == 3 && !h->e[2]) || !h->consts ||
-      !h->d_codes || !h->d_order || !h->d_red || !h->d_status ||
+      !h->d_codes || !h->d_order || !h->d_red || !h->d_snap || !h->d_status ||
       (h->field_w && !h->wfield))
     return bad(WLBM_ERR_OOM, "wlbm_create: device allocation failed");
 
@@ -517,6 +523,7 @@ wlbm_status wlbm_init_temperature(wlbm_handle* h, const float* dT) {
   h->build_wall_segments();
   h->drop_graphs();
   h->tas.reset(g.q);
+  h->snap_step = -1;
   InitArgs a{};
   a.planes = h->planes; a.plane = g.plane; a.pitch = g.pitch; a.nx = g.nx; a.ny = g.ny; a.q = g.q;
   a.dT = dT; a.w = h->w_dev(); a.e_cur = h->e[h->e_cur]; a.e_refp = h->ref_plane();
@@ -749,29 +756,132 @@ wlbm_status wlbm_moments(wlbm_handle* h, float* dT, float* qx, float* qy) {
   return h->cuda(launch_moments(h->storage, a, h->stream), "wlbm_moments");
 }
 
-wlbm_status wlbm_reduce(wlbm_handle* h, double* out) {
-  if (!h) return WLBM_ERR_INVALID_ARG;
-  if (!out) return h->fail(WLBM_ERR_INVALID_ARG, "wlbm_reduce: NULL output");
+// Derived outputs 6 and 7 of wlbm_reduce from outputs 2, 4 and 5.
+static void reduce_conductivities(const wlbm_handle* h, double* out) {
+  const double nan = std::numeric_limits<double>::quiet_NaN();
+  // bulk diffusivity v_g Lambda / 3 (3D emulation) or / 2; defined for a uniform MFP only
+  const double D = h->field_w ? nan : h->mfp_uniform / (h->emulate_3d ? 3.0 : 2.0);
+  const bool iso_x = h->bc_kind[0] == WLBM_BC_ISOTHERMAL && h->bc_kind[1] == WLBM_BC_ISOTHERMAL &&
+                     h->t_wall[0] != h->t_wall[1];
+  out[6] = iso_x ? out[2] * h->g.nx / (D * (h->delta_e(h->t_wall[0]) - h->delta_e(h->t_wall[1])))
+                 : nan;
+  out[7] = out[5] != 0.0 ? out[4] / (-D * out[5]) : nan;
+}
+
+// Window control of one reduction inside wlbm_run_steady.
+struct WindowCtl {
+  bool first, last, has_prev;
+  int32_t count;
+};
+
+static wlbm_status reduce_impl(wlbm_handle* h, double* out, const WindowCtl* win,
+                               double* win_res) {
   const Geom& g = h->g;
-  wlbm_status st = h->cuda(cudaMemsetAsync(h->d_red, 0, 4 * sizeof(double), h->stream), "reduce");
+  wlbm_status st = h->cuda(
+      cudaMemsetAsync(h->d_red, 0, kReduceOut * sizeof(double), h->stream), "wlbm_reduce");
   if (st != WLBM_OK) return st;
   ReduceArgs a{};
   a.planes = h->planes; a.plane = g.plane; a.pitch = g.pitch; a.nx = g.nx; a.ny = g.ny;
   a.q = g.q; a.par = h->parity_mask(); a.e_cur = h->e[h->e_cur]; a.e_refp = h->ref_plane();
   a.w = h->w_dev(); a.sx = h->sx_dev(); a.sy = h->sy_dev(); a.out = h->d_red; a.scale = h->scale;
-  a.xper = h->xper; a.yper = h->yper;
+  a.diff_mask = 0;
+  for (int k = 0; k < 4; ++k)
+    if (h->bc_kind[k] == WLBM_BC_ADIABATIC_DIFFUSE) a.diff_mask |= 1 << k;
+  a.band_x0 = g.nx / 4;
+  a.band_w = g.nx / 2;
+  a.band_xbar = a.band_x0 + 0.5 * (a.band_w - 1);
+  a.snap = h->d_snap;
+  a.has_snap = h->snap_step >= 0 ? 1 : 0;
+  a.e_ref = h->e_eq_ref;
+  a.e_ref1 = h->e_eq_ref + 1.0;
+  a.l_ref = std::log1p(1.0 / h->e_eq_ref);
+  a.theta = h->theta;
+  if (win) {
+    a.win = h->d_win;
+    a.win_prev = h->d_win_prev;
+    a.win_first = win->first ? 1 : 0;
+    a.win_last = win->last ? 1 : 0;
+    a.win_has_prev = win->has_prev ? 1 : 0;
+    a.win_inv = 1.0 / win->count;
+  }
+  ++h->launches;
   st = h->cuda(launch_reduce(h->storage, a, h->stream), "wlbm_reduce");
-  double tmp[4];
+  double tmp[kReduceOut];
   if (st == WLBM_OK)
     st = h->cuda(cudaMemcpyAsync(tmp, h->d_red, sizeof(tmp), cudaMemcpyDeviceToHost, h->stream),
                  "wlbm_reduce");
   if (st == WLBM_OK) st = h->cuda(cudaStreamSynchronize(h->stream), "wlbm_reduce");
   if (st != WLBM_OK) return st;
+  const double nan = std::numeric_limits<double>::quiet_NaN();
   const double cells = double(g.nx) * g.ny;
+  const double bw = a.band_w;
   out[0] = tmp[0];
   out[1] = tmp[1];
   out[2] = tmp[2] / cells;
   out[3] = tmp[3] / cells;
+  out[4] = a.band_w >= 1 ? tmp[4] / (bw * g.ny) : nan;
+  // least-squares slope of the y-averaged E over the band: sum (x - xbar)^2 = w (w^2 - 1) / 12
+  out[5] = a.band_w >= 2 ? tmp[5] / (double(g.ny) * bw * (bw * bw - 1.0) / 12.0) : nan;
+  reduce_conductivities(h, out);
+  double rmax;
+  std::memcpy(&rmax, &tmp[6], sizeof(rmax));
+  const int64_t n = h->tas.n;
+  out[8] = h->snap_step >= 0 && n > h->snap_step ? rmax / double(n - h->snap_step) : nan;
+  h->snap_step = n;
+  if (win_res) std::memcpy(win_res, &tmp[7], sizeof(double));
+  return WLBM_OK;
+}
+
+wlbm_status wlbm_reduce(wlbm_handle* h, double* out) {
+  if (!h) return WLBM_ERR_INVALID_ARG;
+  if (!out) return h->fail(WLBM_ERR_INVALID_ARG, "wlbm_reduce: NULL output");
+  return reduce_impl(h, out, nullptr, nullptr);
+}
+
+wlbm_status wlbm_run_steady(wlbm_handle* h, int64_t max_steps, int64_t check_every, double tol,
+                            int32_t avg_steps, int64_t* steps_run, int32_t* converged,
+                            double* out) {
+  if (!h) return WLBM_ERR_INVALID_ARG;
+  if (avg_steps < 1 || check_every < avg_steps || max_steps < check_every || !(tol >= 0.0))
+    return h->fail(WLBM_ERR_INVALID_ARG, "wlbm_run_steady: need max_steps >= check_every >= "
+                                         "avg_steps >= 1 and tol >= 0");
+  const size_t cells = size_t(h->g.nx) * h->g.ny;
+  if (!h->d_win) h->d_win = static_cast<double*>(h->dev_alloc(cells * sizeof(double)));
+  if (!h->d_win_prev) h->d_win_prev = static_cast<double*>(h->dev_alloc(cells * sizeof(double)));
+  if (!h->d_win || !h->d_win_prev)
+    return h->fail(WLBM_ERR_OOM, "wlbm_run_steady: device allocation failed");
+  double r[WLBM_REDUCE_N];
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  double residual = std::numeric_limits<double>::quiet_NaN();
+  int64_t done = 0;
+  int32_t conv = 0;
+  bool has_prev = false;
+  wlbm_status st = WLBM_OK;
+  while (st == WLBM_OK && done + check_every <= max_steps && !conv) {
+    st = wlbm_step(h, check_every - avg_steps);
+    for (int k = 0; k < 4; ++k) acc[k] = 0.0;
+    double wres = 0.0;
+    for (int32_t t = 0; t < avg_steps && st == WLBM_OK; ++t) {
+      st = wlbm_step(h, 1);
+      const WindowCtl w{t == 0, t == avg_steps - 1, has_prev, avg_steps};
+      if (st == WLBM_OK) st = reduce_impl(h, r, &w, &wres);
+      if (st == WLBM_OK)
+        for (int k = 0; k < 4; ++k) acc[k] += r[2 + k];
+    }
+    if (st != WLBM_OK) break;
+    done += check_every;
+    // window centres are check_every steps apart
+    residual = has_prev ? wres / double(check_every) : std::numeric_limits<double>::quiet_NaN();
+    has_prev = true;
+    conv = residual <= tol ? 1 : 0;
+  }
+  if (steps_run) *steps_run = done;
+  if (converged) *converged = conv;
+  if (st != WLBM_OK) return st;
+  for (int k = 0; k < 4; ++k) r[2 + k] = acc[k] / avg_steps;
+  reduce_conductivities(h, r);
+  r[8] = residual;
+  if (out) std::memcpy(out, r, sizeof(r));
   return WLBM_OK;
 }
 
@@ -794,6 +904,7 @@ wlbm_status wlbm_get_state(wlbm_handle* h, float* framed) {
 wlbm_status wlbm_set_state(wlbm_handle* h, const float* framed) {
   if (!h) return WLBM_ERR_INVALID_ARG;
   if (!framed) return h->fail(WLBM_ERR_INVALID_ARG, "wlbm_set_state: NULL input");
+  h->snap_step = -1;
   const wlbm_status st = h->cuda(
       launch_set_state(h->storage, state_args(h, const_cast<float*>(framed)), h->stream),
       "wlbm_set_state");
@@ -928,6 +1039,7 @@ wlbm_status wlbm_adjoint_backward(wlbm_handle* h, const float* dJ_dT, float* dJ_
     return h->fail(WLBM_ERR_STATE, "wlbm_adjoint_backward: no checkpointed forward run ends "
                                    "at the current state");
   if (!dJ_dT) return h->fail(WLBM_ERR_INVALID_ARG, "wlbm_adjoint_backward: NULL dJ_dT");
+  h->snap_step = -1;   // the sweep reuses the state buffers
   const Geom& g = h->g;
   cudaStream_t s = h->stream;
   const size_t state = size_t(g.q) * size_t(g.plane);

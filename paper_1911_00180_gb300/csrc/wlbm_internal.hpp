@@ -215,10 +215,31 @@ struct ReduceArgs {
   const float* w;
   const float* sx;
   const float* sy;
-  double* out;           // [4], zeroed before launch
+  double* out;           // [kReduceOut], zeroed before launch
   double scale;
-  int xper, yper;
+  int diff_mask;         // bit k: side k (x-, x+, y-, y+) is an adiabatic-diffuse wall
+  // central band of columns band_x0 <= x < band_x0 + band_w (conductivity fit)
+  int band_x0, band_w;
+  double band_xbar;      // mean column of the band
+  // temperature residual: snap[y * nx + x] holds T - T_ref (float64) of the previous
+  // reduction; read where has_snap, always overwritten with the current field
+  double* snap;
+  int has_snap;
+  double e_ref, e_ref1, l_ref, theta;   // e_ref, e_ref + 1, ln(1 + 1/e_ref), theta
+  // window means of T - T_ref (steady-state test): win accumulates T over the reductions
+  // of a window (set on its first, added on the others); on its last the mean win * win_inv
+  // is compared with win_prev (where win_has_prev) and replaces it.  win == nullptr: off.
+  double* win;
+  double* win_prev;
+  int win_first, win_last, win_has_prev;
+  double win_inv;
 };
+// k_reduce outputs: [0] sum E interior, [1] + adiabatic-wall ghost cells, [2] sum q_x, [3] sum q_y,
+// [4] sum q_x over the band, [5] sum (x - xbar) E over the band, [6] max |dT - dT_snap|,
+// [7] max |window mean - previous window mean| (6, 7: bits of non-negative doubles,
+// combined with an unsigned max).
+constexpr int kReduceSums = 6;
+constexpr int kReduceOut = 8;
 
 struct StateArgs {
   void* planes;

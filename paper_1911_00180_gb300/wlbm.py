@@ -17,6 +17,7 @@ WLBM_ERR_CUDA, WLBM_ERR_TIMEOUT, WLBM_ERR_STATE = 4, 5, 6
 BC_PERIODIC, BC_ISOTHERMAL, BC_ADIABATIC_DIFFUSE = 0, 1, 2
 STORE_FP32_DEV, STORE_BF16_DEV = 0, 1
 OPT_STEP_VARIANT, OPT_GRAPH_STEPS, OPT_FUSE_PERIODIC = 1, 2, 3
+REDUCE_N = 9          # WLBM_REDUCE_N
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "UNSTABLE", 3: "OOM", 4: "CUDA", 5: "TIMEOUT",
                 6: "STATE"}
 
@@ -62,6 +63,8 @@ def _load():
         "wlbm_step_count": (i64, [vp]),
         "wlbm_moments": (C.c_int, [vp, vp, vp, vp]),
         "wlbm_reduce": (C.c_int, [vp, C.POINTER(dbl)]),
+        "wlbm_run_steady": (C.c_int, [vp, i64, i64, dbl, i32, C.POINTER(C.c_int64),
+                                      C.POINTER(i32), C.POINTER(dbl)]),
         "wlbm_get_state": (C.c_int, [vp, vp]),
         "wlbm_set_state": (C.c_int, [vp, vp]),
         "wlbm_adjoint_forward": (C.c_int, [vp, vp, i64, i32]),
@@ -215,9 +218,20 @@ class WormLBM:
         return dT, qx, qy
 
     def wlbm_reduce(self):
-        out = (C.c_double * 4)()
+        """The WLBM_REDUCE_N float64 reductions of include/wlbm.h, as a list."""
+        out = (C.c_double * REDUCE_N)()
         _check(lib.wlbm_reduce(self.h, out), self.h)
         return list(out)
+
+    def wlbm_run_steady(self, max_steps, check_every, tol, avg_steps=10):
+        """Steps until the temperature residual is <= tol K/step or max_steps ran, then
+        averages the flux outputs over avg_steps steps: returns (steps_run, converged,
+        reductions)."""
+        out = (C.c_double * REDUCE_N)()
+        steps, conv = C.c_int64(0), C.c_int32(0)
+        _check(lib.wlbm_run_steady(self.h, int(max_steps), int(check_every), float(tol),
+                                   int(avg_steps), C.byref(steps), C.byref(conv), out), self.h)
+        return steps.value, bool(conv.value), list(out)
 
     def wlbm_adjoint_forward(self, dT0, n_steps, ckpt_every):
         t = self._torch.as_tensor(dT0, dtype=self._torch.float32, device=self.device).contiguous()

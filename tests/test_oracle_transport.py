@@ -207,3 +207,34 @@ def test_temperature_residual():
     b = m.temperature_dev()
     want = np.abs(t9 - t5).max() / 4
     assert T.temperature_residual(b, a, 4) == pytest.approx(want, rel=1e-9)
+
+
+def test_run_steady_windows():
+    """Window means: a uniform equilibrium is steady at the second check (residual 0);
+    for a ballistic periodic run the residual of the second check is the largest change
+    per step of the exactly translated temperature averaged over steps 10-12 against
+    steps 4-6 (checks of 6 steps, windows of 3)."""
+    m = WormLBM(12, 10, 16, 4.0)
+    m.init_temperature(np.full((10, 12), -0.2))
+    steps, conv, res, _ = T.run_steady(m, 400, 100, 0.0, 10, 4.0)
+    assert (steps, conv, res) == (200, True, 0.0)
+
+    nx = ny = 20
+    q = 16
+    yy, xx = np.mgrid[0:ny, 0:nx]
+    dT0 = np.exp(-((xx - 9.4) ** 2 + (yy - 10.2) ** 2) / (2 * 2.5 ** 2))
+    m = WormLBM(nx, ny, q, 1.0, w_field=0.0)
+    m.init_temperature(dT0)
+    e0 = L.e_eq(300.0 + dT0, m.theta) - m.e_ref
+    sched = L.TasSchedule(q)
+    temps = []
+    for _ in range(12):
+        sched.advance()
+        disp = sched.displacement()
+        e = sum(m.w[i] * np.roll(e0, (disp[i][1], disp[i][0]), axis=(0, 1)) for i in range(q))
+        temps.append(L.temperature(m.e_ref + e, m.theta) - 300.0)
+    w1 = (temps[3] + temps[4] + temps[5]) / 3.0
+    w2 = (temps[9] + temps[10] + temps[11]) / 3.0
+    steps, conv, res, _ = T.run_steady(m, 12, 6, 0.0, 3, 1.0)
+    assert steps == 12 and not conv
+    assert res == pytest.approx(np.abs(w2 - w1).max() / 6, rel=1e-9)

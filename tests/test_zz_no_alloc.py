@@ -27,7 +27,7 @@ def test_noalloc_reduction_matches_handle_reduction_twice():
     out = torch.empty(4, dtype=torch.float64, device="cuda")
     for call in range(2):
         h.wlbm_step(25)
-        want = np.array(h.wlbm_reduce())
+        want = np.array(h.wlbm_reduce())[:4]
         framed = h.wlbm_get_state()
         out.fill_(float("nan"))
         wl.wlbm_reduce_state_noalloc(framed, nx, ny, q, kinds, out, stream=h.stream)
