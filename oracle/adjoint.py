@@ -129,13 +129,19 @@ def _diffuse_T(m, lam, yy, xx, normal, strict):
 class AdjointRun:
     """Forward run with recording, then the reverse sweep.
 
-    probe: boolean (ny, nx) mask of the interior cells averaged in J."""
+    probe: boolean (ny, nx) mask of the interior cells averaged in J.
+    objective: "temperature" (J = mean of T - T_ref over the probe) or "flux_x" (J = mean
+    of q_x over the probe, Eq. q_corr; the effective conductivity of a film is this mean
+    over the interior times N_x / (D (e(T_h) - e(T_c))))."""
 
-    def __init__(self, model_kwargs, dT0, steps, probe):
+    def __init__(self, model_kwargs, dT0, steps, probe, objective="temperature"):
         self.kw = dict(model_kwargs)
         self.dT0 = np.asarray(dT0, np.float64)
         self.steps = steps
         self.probe = np.asarray(probe, bool)
+        if objective not in ("temperature", "flux_x"):
+            raise ValueError("objective is 'temperature' or 'flux_x'")
+        self.objective_kind = objective
 
     def model(self, **over):
         kw = dict(self.kw)
@@ -143,6 +149,8 @@ class AdjointRun:
         return WormLBM(**kw)
 
     def objective(self, m):
+        if self.objective_kind == "flux_x":
+            return float(m.heat_flux()[0][self.probe].mean())
         t = m.temperature_dev()
         return float(t[self.probe].mean())
 
@@ -164,9 +172,14 @@ class AdjointRun:
             m.n = n
         J = self.objective(m)
         lam = np.zeros_like(m.d)
-        e_abs = m.e_ref + m.energy_dev()
-        g = np.where(self.probe, dT_dE(e_abs, m.theta), 0.0) / self.probe.sum()
-        lam[:, 1:-1, 1:-1] = g[None]
+        if self.objective_kind == "flux_x":
+            # q_x(x) = sum_i s_ix d_i(x): dJ/dd_i(x) = s_ix over the probe cells
+            g = self.probe / self.probe.sum()
+            lam[:, 1:-1, 1:-1] = m.s_hat[:, 0][:, None, None] * g[None]
+        else:
+            e_abs = m.e_ref + m.energy_dev()
+            g = np.where(self.probe, dT_dE(e_abs, m.theta), 0.0) / self.probe.sum()
+            lam[:, 1:-1, 1:-1] = g[None]
         gW = np.zeros_like(m.wf)
         g_t = np.zeros(4)
         for d_in, hops, paused in reversed(rec):

@@ -67,10 +67,13 @@ def _fd(fun, h):
     return (fun(h) - fun(-h)) / (2 * h)
 
 
-@pytest.mark.parametrize("kinds", [(I, I, P, P), (I, I, D, D)])
-def test_gradients_match_central_differences(kinds):
-    """Gradients of J (mean T - T_ref on a probe column) with respect to the per-cell MFP
-    and the wall temperatures, against central differences of the forward oracle."""
+@pytest.mark.parametrize("kinds,objective", [((I, I, P, P), "temperature"),
+                                             ((I, I, D, D), "temperature"),
+                                             ((I, I, D, D), "flux_x")])
+def test_gradients_match_central_differences(kinds, objective):
+    """Gradients of J (mean T - T_ref, or mean q_x, on a probe column) with respect to the
+    per-cell MFP, the wall temperatures and the start field, against central differences
+    of the forward oracle."""
     nx, ny, q, steps = 20, 14, 16, 40
     rng = np.random.default_rng(11)
     mfp = np.exp(np.log(3.0) + 0.3 * rng.standard_normal((ny, nx)))
@@ -80,7 +83,7 @@ def test_gradients_match_central_differences(kinds):
     probe[:, 14] = True
     tw = (300.5, 299.8, 300.0, 300.0)
     kw = dict(nx=nx, ny=ny, q=q, mfp=mfp, bc_kind=kinds, t_wall=tw, emulate_3d=True)
-    run = A.AdjointRun(kw, dT0, steps, probe)
+    run = A.AdjointRun(kw, dT0, steps, probe, objective)
     g = run.gradients()
     assert g["J"] == pytest.approx(run.forward(), rel=1e-14)
     for (cy, cx) in [(7, 10), (3, 13), (12, 2), (7, 14)]:
@@ -100,6 +103,6 @@ def test_gradients_match_central_differences(kinds):
         def f(h, cy=cy, cx=cx):
             d2 = dT0.copy()
             d2[cy, cx] += h
-            r2 = A.AdjointRun(kw, d2, steps, probe)
+            r2 = A.AdjointRun(kw, d2, steps, probe, objective)
             return r2.forward()
         assert g["dJ_ddT0"][cy, cx] == pytest.approx(_fd(f, 1e-3), rel=1e-6, abs=1e-14)
