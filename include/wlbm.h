@@ -183,7 +183,14 @@ wlbm_status wlbm_set_state(wlbm_handle* h, const float* framed);
  * states of recompute tape).  The handle's state afterwards is the final state.
  *   dT0  device nx*ny float32 start field (K), copied.
  *
- * wlbm_adjoint_backward: given dJ/dT of the final temperature field, returns
+ * wlbm_adjoint_backward: for an objective J of the final temperature field and heat flux
+ * (Eq. pseudo-T, Eq. q_corr), given as its derivatives
+ *   dJ_dT, dJ_dqx, dJ_dqy  device nx*ny float32 each: dJ/dT, dJ/dq_x, dJ/dq_y per interior
+ *             cell (NULL: zero; at least one is needed).  The apparent conductivity of a
+ *             film, mean q_x * nx / (D (e(T_x-) - e(T_x+))), has dJ_dqx = nx / (D de cells)
+ *             everywhere; its explicit dependence on the wall temperatures through de
+ *             is the caller's to add.
+ * returns
  *   dJ_dmfp   device nx*ny float32: dJ / dMFP per cell (through W_corr, Eq. W-correction)
  *   dJ_dTwall host double[4]: dJ / dT_wall for isothermal walls (0 for other walls)
  *   dJ_ddT0   device nx*ny float32: dJ / d(start field)
@@ -192,8 +199,9 @@ wlbm_status wlbm_set_state(wlbm_handle* h, const float* framed);
  * checkpointed forward run (WLBM_ERR_STATE otherwise).  Synchronous. */
 wlbm_status wlbm_adjoint_forward(wlbm_handle* h, const float* dT0, int64_t n_steps,
                                  int32_t ckpt_every);
-wlbm_status wlbm_adjoint_backward(wlbm_handle* h, const float* dJ_dT, float* dJ_dmfp,
-                                  double* dJ_dTwall, float* dJ_ddT0);
+wlbm_status wlbm_adjoint_backward(wlbm_handle* h, const float* dJ_dT, const float* dJ_dqx,
+                                  const float* dJ_dqy, float* dJ_dmfp, double* dJ_dTwall,
+                                  float* dJ_ddT0);
 
 /* wlbm_set_option: tuning knobs that do not change results.
  *   WLBM_OPT_STEP_VARIANT  0: step kernel with register-pipelined loads; 1: step kernel

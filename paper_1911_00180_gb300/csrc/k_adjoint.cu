@@ -299,17 +299,24 @@ __global__ void __launch_bounds__(32 * kWallWarpsT) k_walls_T(const WallArgs wa,
     if (rho[i] == 0.f) lam[int64_t(i) * wa.plane + off] = S;
 }
 
-// l^N: dJ/dT(x) * dT/dE at the final local energy, for every direction (E = sum_i d_i).
-__global__ void k_adj_seed(const AdjArgs a, const float* dJ_dT, const float* e_final,
-                           double e_ref, double theta) {
+// l^N_i(x) = dJ/dT(x) * dT/dE at the final local energy (E = sum_i d_i, Eq. pseudo-T)
+// + dJ/dq_x(x) s_ix + dJ/dq_y(x) s_iy (q = sum_i d_i s_i, Eq. q_corr); NULL seeds are 0.
+__global__ void k_adj_seed(const AdjArgs a, const float* dJ_dT, const float* dJ_dqx,
+                           const float* dJ_dqy, const float* sx, const float* sy,
+                           const float* e_final, double e_ref, double theta) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= a.nx * a.ny) return;
   const int y = t / a.nx, x = t - y * a.nx;
   const int64_t off = int64_t(y + 2) * a.pitch + (x + kX0);
-  const double e = e_ref + double(e_final[off]);
-  const double lg = log1p(1.0 / e);
-  const float g = float(double(dJ_dT[t]) * theta / (lg * lg * e * (1.0 + e)));
-  for (int i = 0; i < a.q; ++i) a.lam_out[int64_t(i) * a.plane + off] = g;
+  float g = 0.f;
+  if (dJ_dT) {
+    const double e = e_ref + double(e_final[off]);
+    const double lg = log1p(1.0 / e);
+    g = float(double(dJ_dT[t]) * theta / (lg * lg * e * (1.0 + e)));
+  }
+  const float gx = dJ_dqx ? dJ_dqx[t] : 0.f, gy = dJ_dqy ? dJ_dqy[t] : 0.f;
+  for (int i = 0; i < a.q; ++i)
+    a.lam_out[int64_t(i) * a.plane + off] = fmaf(gy, sy[i], fmaf(gx, sx[i], g));
 }
 
 // dJ/dMFP = dJ/dW_corr * dW_corr/dMFP on interior cells; dJ/d(dT0) from l^0 through the
@@ -374,9 +381,11 @@ cudaError_t launch_walls_T(const WallArgs& wa, float* lam, double* gtw, cudaStre
   return cudaGetLastError();
 }
 
-cudaError_t launch_adj_seed(const AdjArgs& a, const float* dJ_dT, const float* e_final,
-                            double e_ref, double theta, cudaStream_t s) {
-  k_adj_seed<<<nblk(int64_t(a.nx) * a.ny, 256), 256, 0, s>>>(a, dJ_dT, e_final, e_ref, theta);
+cudaError_t launch_adj_seed(const AdjArgs& a, const float* dJ_dT, const float* dJ_dqx,
+                            const float* dJ_dqy, const float* sx, const float* sy,
+                            const float* e_final, double e_ref, double theta, cudaStream_t s) {
+  k_adj_seed<<<nblk(int64_t(a.nx) * a.ny, 256), 256, 0, s>>>(a, dJ_dT, dJ_dqx, dJ_dqy, sx, sy,
+                                                              e_final, e_ref, theta);
   return cudaGetLastError();
 }
 

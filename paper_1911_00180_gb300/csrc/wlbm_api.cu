@@ -1031,14 +1031,16 @@ wlbm_status wlbm_adjoint_forward(wlbm_handle* h, const float* dT0, int64_t n_ste
   return st;
 }
 
-wlbm_status wlbm_adjoint_backward(wlbm_handle* h, const float* dJ_dT, float* dJ_dmfp,
+wlbm_status wlbm_adjoint_backward(wlbm_handle* h, const float* dJ_dT, const float* dJ_dqx,
+                                  const float* dJ_dqy, float* dJ_dmfp,
                                   double* dJ_dTwall, float* dJ_ddT0) {
   if (!h) return WLBM_ERR_INVALID_ARG;
   auto& A = h->adj;
   if (!A.ready || h->tas.n != A.n)
     return h->fail(WLBM_ERR_STATE, "wlbm_adjoint_backward: no checkpointed forward run ends "
                                    "at the current state");
-  if (!dJ_dT) return h->fail(WLBM_ERR_INVALID_ARG, "wlbm_adjoint_backward: NULL dJ_dT");
+  if (!dJ_dT && !dJ_dqx && !dJ_dqy)
+    return h->fail(WLBM_ERR_INVALID_ARG, "wlbm_adjoint_backward: no seed (dJ_dT, dJ_dqx, dJ_dqy)");
   h->snap_step = -1;   // the sweep reuses the state buffers
   const Geom& g = h->g;
   cudaStream_t s = h->stream;
@@ -1072,7 +1074,9 @@ wlbm_status wlbm_adjoint_backward(wlbm_handle* h, const float* dJ_dT, float* dJ_
     else aa.iso_side[top ? 3 : 2] = sg.wall;
   }
   aa.lam_out = A.lam[0];
-  ok(launch_adj_seed(aa, dJ_dT, h->e[h->e_cur], h->e_eq_ref, h->theta, s), "adjoint: seed");
+  ok(launch_adj_seed(aa, dJ_dT, dJ_dqx, dJ_dqy, h->sx_dev(), h->sy_dev(), h->e[h->e_cur],
+                     h->e_eq_ref, h->theta, s),
+     "adjoint: seed");
   int cur = 0;
   for (int c = A.nck - 1; c >= 0 && st == WLBM_OK; --c) {
     const int64_t s0 = int64_t(c) * A.k;

@@ -376,8 +376,9 @@ cudaError_t launch_periodic_T(float* planes, int64_t plane, int pitch, int nx, i
 // the reverse step: only the two end cells of each isothermal segment (where the periodic
 // transpose of the other axis may have added corner images) are transposed again.
 cudaError_t launch_walls_T(const WallArgs& wa, float* lam, double* gtw, cudaStream_t s);
-cudaError_t launch_adj_seed(const AdjArgs& a, const float* dJ_dT, const float* e_final,
-                            double e_ref, double theta, cudaStream_t s);
+cudaError_t launch_adj_seed(const AdjArgs& a, const float* dJ_dT, const float* dJ_dqx,
+                            const float* dJ_dqy, const float* sx, const float* sy,
+                            const float* e_final, double e_ref, double theta, cudaStream_t s);
 cudaError_t launch_adj_final(const AdjArgs& a, const float* dwc, float* dJ_dmfp,
                              const float* lam0, const float* s0, const float* dT0,
                              float* dJ_ddT0, double t_ref, double theta, cudaStream_t s);

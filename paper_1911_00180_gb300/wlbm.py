@@ -68,7 +68,7 @@ def _load():
         "wlbm_get_state": (C.c_int, [vp, vp]),
         "wlbm_set_state": (C.c_int, [vp, vp]),
         "wlbm_adjoint_forward": (C.c_int, [vp, vp, i64, i32]),
-        "wlbm_adjoint_backward": (C.c_int, [vp, vp, vp, C.POINTER(dbl), vp]),
+        "wlbm_adjoint_backward": (C.c_int, [vp, vp, vp, vp, vp, C.POINTER(dbl), vp]),
         "wlbm_set_option": (C.c_int, [vp, i32, i64]),
         "wlbm_get_option": (C.c_int, [vp, i32, C.POINTER(C.c_int64)]),
         "wlbm_autotune": (C.c_int, [vp, i32, C.POINTER(i32), C.POINTER(i32), C.POINTER(dbl)]),
@@ -237,15 +237,20 @@ class WormLBM:
         t = self._torch.as_tensor(dT0, dtype=self._torch.float32, device=self.device).contiguous()
         _check(lib.wlbm_adjoint_forward(self.h, _ptr(t), int(n_steps), int(ckpt_every)), self.h)
 
-    def wlbm_adjoint_backward(self, dJ_dT, want_mfp=True, want_dT0=True):
-        """(dJ/dMFP (ny, nx), dJ/dT_wall [4], dJ/d dT0 (ny, nx)) for the checkpointed run."""
+    def wlbm_adjoint_backward(self, dJ_dT=None, want_mfp=True, want_dT0=True, dJ_dqx=None,
+                              dJ_dqy=None):
+        """(dJ/dMFP (ny, nx), dJ/dT_wall [4], dJ/d dT0 (ny, nx)) for the checkpointed run,
+        J given by its derivatives with respect to the final T, q_x and q_y (None: 0)."""
         torch = self._torch
-        g = torch.as_tensor(dJ_dT, dtype=torch.float32, device=self.device).contiguous()
+        dev = lambda a: None if a is None else torch.as_tensor(
+            a, dtype=torch.float32, device=self.device).contiguous()
+        seeds = [dev(a) for a in (dJ_dT, dJ_dqx, dJ_dqy)]
         mk = lambda f: torch.empty((self.ny, self.nx), dtype=torch.float32,
                                    device=self.device) if f else None
         g_mfp, g_dT0 = mk(want_mfp), mk(want_dT0)
         g_tw = (C.c_double * 4)()
-        _check(lib.wlbm_adjoint_backward(self.h, _ptr(g), _ptr(g_mfp), g_tw, _ptr(g_dT0)), self.h)
+        _check(lib.wlbm_adjoint_backward(self.h, *[_ptr(a) for a in seeds], _ptr(g_mfp), g_tw,
+                                         _ptr(g_dT0)), self.h)
         return g_mfp, list(g_tw), g_dT0
 
     def wlbm_set_option(self, key, value):
