@@ -173,6 +173,24 @@ wlbm_status wlbm_run_steady(wlbm_handle* h, int64_t max_steps, int64_t check_eve
 wlbm_status wlbm_get_state(wlbm_handle* h, float* framed);
 wlbm_status wlbm_set_state(wlbm_handle* h, const float* framed);
 
+/* wlbm_save / wlbm_load: checkpoint and resume.  A checkpoint holds the current state
+ * planes as stored (framed, float32 or bfloat16), the local-energy plane (and, with
+ * bfloat16 storage, the reference-energy plane), the storage scale and the schedule
+ * cursor of Eq. algorithm (step n, per-direction displacement p_i and worm-hop counter,
+ * plane buffer parity), so that stepping a loaded handle gives bit-for-bit the states of
+ * the uninterrupted run.
+ *   wlbm_save  dst: host buffer of capacity bytes, or NULL to only query the size;
+ *              *written (host, may be NULL) receives the checkpoint size.  Synchronous.
+ *              WLBM_ERR_INVALID_ARG if capacity is too small.
+ *   wlbm_load  src: host buffer of size bytes written by wlbm_save for a handle of the same
+ *              nx, ny, Q, storage and wall kinds (WLBM_ERR_INVALID_ARG otherwise, or for a
+ *              truncated or corrupt header).  The handle's MFP field, wall temperatures and
+ *              options are its own: load into a handle created with the same arguments.
+ *              Clears the residual snapshot of wlbm_reduce and any adjoint forward run.
+ *              Synchronous.  Handles owned by a batch are not supported. */
+wlbm_status wlbm_save(wlbm_handle* h, void* dst, size_t capacity, size_t* written);
+wlbm_status wlbm_load(wlbm_handle* h, const void* src, size_t size);
+
 /* ------------------------------------------------------------------------ adjoint --
  * Reverse-mode gradients of a run (the paper has no adjoint; the reverse step is the
  * exact transpose of Eq. lbm-energy / Eq. algorithm and of the wall passes of Sec. 2.6).

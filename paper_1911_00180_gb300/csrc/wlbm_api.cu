@@ -55,6 +55,7 @@ struct wlbm_handle {
   double* d_red = nullptr;    // [kReduceOut]
   double* d_snap = nullptr;   // nx*ny float64 T - T_ref at the last reduction
   int64_t snap_step = -1;     // step of that snapshot (-1: none since the state was set)
+  bool batch_owned = false;   // instance of a wlbm_batch (its records cache plane roles)
   double* d_win = nullptr;    // nx*ny float64 window sum and previous window mean of
   double* d_win_prev = nullptr;   // T - T_ref (wlbm_run_steady; allocated on first use)
   int* d_status = nullptr;    // bit 0: a bounded device wait gave up
@@ -911,6 +912,144 @@ wlbm_status wlbm_set_state(wlbm_handle* h, const float* framed) {
   return st == WLBM_OK ? refresh_periodic(h) : st;
 }
 
+// ---------------------------------------------------------------- checkpoint / resume
+// Blob: CkptHeader, the schedule cursor (px, py, h as int64[q] each, parity as uint8[q]
+// padded to 8 bytes), the q current state planes as stored (framed, pitch included), the
+// current local-energy plane and, with bfloat16 storage, the reference-energy plane.
+namespace {
+struct CkptHeader {
+  char magic[8];
+  int32_t version, nx, ny, q, storage, pitch;
+  int32_t bc_kind[4];
+  int32_t e_cur, e_ref, e_spare, n_energy;
+  int64_t n, plane_bytes, energy_bytes, total;
+  float scale, inv_scale;
+};
+constexpr char kCkptMagic[8] = {'W', 'L', 'B', 'M', 'C', 'K', 'P', 'T'};
+constexpr int32_t kCkptVersion = 1;
+
+size_t ckpt_cursor_bytes(int q) { return size_t(q) * 24 + ((size_t(q) + 7) & ~size_t(7)); }
+}  // namespace
+
+static size_t ckpt_size(const wlbm_handle* h) {
+  const Geom& g = h->g;
+  const size_t plane_bytes = size_t(g.plane) * h->elem();
+  const size_t energy_bytes = size_t(g.plane) * 4;
+  return sizeof(CkptHeader) + ckpt_cursor_bytes(g.q) + size_t(g.q) * plane_bytes +
+         (h->e_ref >= 0 ? 2 : 1) * energy_bytes;
+}
+
+wlbm_status wlbm_save(wlbm_handle* h, void* dst, size_t capacity, size_t* written) {
+  if (!h) return WLBM_ERR_INVALID_ARG;
+  const size_t total = ckpt_size(h);
+  if (written) *written = total;
+  if (!dst) return WLBM_OK;
+  if (capacity < total) return h->fail(WLBM_ERR_INVALID_ARG, "wlbm_save: buffer too small");
+  const Geom& g = h->g;
+  CkptHeader hd{};
+  std::memcpy(hd.magic, kCkptMagic, 8);
+  hd.version = kCkptVersion;
+  hd.nx = g.nx; hd.ny = g.ny; hd.q = g.q; hd.storage = h->storage; hd.pitch = g.pitch;
+  for (int k = 0; k < 4; ++k) hd.bc_kind[k] = h->bc_kind[k];
+  hd.e_cur = h->e_cur; hd.e_ref = h->e_ref; hd.e_spare = h->e_spare;
+  hd.n_energy = h->e_ref >= 0 ? 2 : 1;
+  hd.n = h->tas.n;
+  hd.plane_bytes = int64_t(g.plane) * int64_t(h->elem());
+  hd.energy_bytes = int64_t(g.plane) * 4;
+  hd.total = int64_t(total);
+  hd.scale = h->scale; hd.inv_scale = h->inv_scale;
+  unsigned char* out = static_cast<unsigned char*>(dst);
+  std::memcpy(out, &hd, sizeof(hd));
+  unsigned char* cur = out + sizeof(hd);
+  std::memcpy(cur, h->tas.px.data(), size_t(g.q) * 8);
+  std::memcpy(cur + size_t(g.q) * 8, h->tas.py.data(), size_t(g.q) * 8);
+  std::memcpy(cur + size_t(g.q) * 16, h->tas.h.data(), size_t(g.q) * 8);
+  std::memset(cur + size_t(g.q) * 24, 0, ckpt_cursor_bytes(g.q) - size_t(g.q) * 24);
+  std::memcpy(cur + size_t(g.q) * 24, h->tas.parity.data(), size_t(g.q));
+  unsigned char* p = cur + ckpt_cursor_bytes(g.q);
+  const unsigned char* planes = static_cast<const unsigned char*>(h->planes);
+  wlbm_status st = WLBM_OK;
+  for (int i = 0; i < g.q && st == WLBM_OK; ++i) {
+    const size_t src = (size_t(h->tas.parity[i]) * g.q + i) * size_t(hd.plane_bytes);
+    st = h->cuda(cudaMemcpyAsync(p, planes + src, size_t(hd.plane_bytes), cudaMemcpyDeviceToHost,
+                                 h->stream), "wlbm_save");
+    p += hd.plane_bytes;
+  }
+  if (st == WLBM_OK)
+    st = h->cuda(cudaMemcpyAsync(p, h->e[h->e_cur], size_t(hd.energy_bytes),
+                                 cudaMemcpyDeviceToHost, h->stream), "wlbm_save");
+  p += hd.energy_bytes;
+  if (st == WLBM_OK && h->e_ref >= 0)
+    st = h->cuda(cudaMemcpyAsync(p, h->e[h->e_ref], size_t(hd.energy_bytes),
+                                 cudaMemcpyDeviceToHost, h->stream), "wlbm_save");
+  if (st == WLBM_OK) st = h->cuda(cudaStreamSynchronize(h->stream), "wlbm_save");
+  return st;
+}
+
+wlbm_status wlbm_load(wlbm_handle* h, const void* src, size_t size) {
+  if (!h) return WLBM_ERR_INVALID_ARG;
+  if (h->batch_owned)
+    return h->fail(WLBM_ERR_STATE, "wlbm_load: handles owned by a batch are not supported");
+  if (!src || size < sizeof(CkptHeader))
+    return h->fail(WLBM_ERR_INVALID_ARG, "wlbm_load: NULL or truncated checkpoint");
+  const Geom& g = h->g;
+  CkptHeader hd;
+  std::memcpy(&hd, src, sizeof(hd));
+  bool same_walls = true;
+  for (int k = 0; k < 4; ++k) same_walls = same_walls && hd.bc_kind[k] == h->bc_kind[k];
+  if (std::memcmp(hd.magic, kCkptMagic, 8) != 0 || hd.version != kCkptVersion)
+    return h->fail(WLBM_ERR_INVALID_ARG, "wlbm_load: not a checkpoint of this library version");
+  if (hd.nx != g.nx || hd.ny != g.ny || hd.q != g.q || hd.storage != h->storage ||
+      hd.pitch != g.pitch || !same_walls)
+    return h->fail(WLBM_ERR_INVALID_ARG,
+                   "wlbm_load: checkpoint of another grid, Q, storage or wall set");
+  if (hd.total != int64_t(ckpt_size(h)) || size < ckpt_size(h) || hd.n < 0 ||
+      hd.n_energy != (h->e_ref >= 0 ? 2 : 1))
+    return h->fail(WLBM_ERR_INVALID_ARG, "wlbm_load: checkpoint size does not match");
+  const int n_e = h->bf16() ? 3 : 2;
+  const bool roles_ok = hd.e_cur >= 0 && hd.e_cur < n_e && hd.e_spare >= 0 && hd.e_spare < n_e &&
+                        hd.e_cur != hd.e_spare &&
+                        (h->bf16() ? (hd.e_ref >= 0 && hd.e_ref < n_e && hd.e_ref != hd.e_cur &&
+                                      hd.e_ref != hd.e_spare)
+                                   : hd.e_ref == -1);
+  const unsigned char* in = static_cast<const unsigned char*>(src) + sizeof(hd);
+  const uint8_t* parity = in + size_t(g.q) * 24;
+  bool parity_ok = true;
+  for (int i = 0; i < g.q; ++i) parity_ok = parity_ok && parity[i] <= 1;
+  if (!roles_ok || !parity_ok || !(hd.scale > 0.f))
+    return h->fail(WLBM_ERR_INVALID_ARG, "wlbm_load: corrupt checkpoint header");
+  h->tas.reset(g.q);
+  h->tas.n = hd.n;
+  std::memcpy(h->tas.px.data(), in, size_t(g.q) * 8);
+  std::memcpy(h->tas.py.data(), in + size_t(g.q) * 8, size_t(g.q) * 8);
+  std::memcpy(h->tas.h.data(), in + size_t(g.q) * 16, size_t(g.q) * 8);
+  std::memcpy(h->tas.parity.data(), parity, size_t(g.q));
+  h->e_cur = hd.e_cur; h->e_ref = hd.e_ref; h->e_spare = hd.e_spare;
+  h->scale = hd.scale; h->inv_scale = hd.inv_scale;
+  h->build_wall_segments();
+  h->drop_graphs();
+  h->snap_step = -1;
+  h->adj.ready = false;
+  const unsigned char* p = in + ckpt_cursor_bytes(g.q);
+  unsigned char* planes = static_cast<unsigned char*>(h->planes);
+  wlbm_status st = WLBM_OK;
+  for (int i = 0; i < g.q && st == WLBM_OK; ++i) {
+    const size_t dst = (size_t(h->tas.parity[i]) * g.q + i) * size_t(hd.plane_bytes);
+    st = h->cuda(cudaMemcpyAsync(planes + dst, p, size_t(hd.plane_bytes), cudaMemcpyHostToDevice,
+                                 h->stream), "wlbm_load");
+    p += hd.plane_bytes;
+  }
+  if (st == WLBM_OK)
+    st = h->cuda(cudaMemcpyAsync(h->e[h->e_cur], p, size_t(hd.energy_bytes),
+                                 cudaMemcpyHostToDevice, h->stream), "wlbm_load");
+  p += hd.energy_bytes;
+  if (st == WLBM_OK && h->e_ref >= 0)
+    st = h->cuda(cudaMemcpyAsync(h->e[h->e_ref], p, size_t(hd.energy_bytes),
+                                 cudaMemcpyHostToDevice, h->stream), "wlbm_load");
+  if (st == WLBM_OK) st = h->cuda(cudaStreamSynchronize(h->stream), "wlbm_load");
+  return st;
+}
+
 
 // ------------------------------------------------------------------------- adjoint
 static wlbm_status adj_alloc(wlbm_handle* h, int64_t n, int k) {
@@ -1325,6 +1464,7 @@ wlbm_status wlbm_batch_create(int32_t n, const wlbm_grid* grids, const float* co
                                        mfp_uniform ? mfp_uniform[k] : 0.0, &bcs[k], alloc, stream,
                                        &x);
     if (st != WLBM_OK) return bad(st, "");   // message of wlbm_create stays in place
+    x->batch_owned = true;
     b->h.push_back(x);
     if (grids[k].storage != grids[0].storage)
       return bad(WLBM_ERR_INVALID_ARG, "wlbm_batch_create: all instances need one storage type");

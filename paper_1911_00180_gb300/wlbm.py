@@ -66,6 +66,8 @@ def _load():
         "wlbm_run_steady": (C.c_int, [vp, i64, i64, dbl, i32, C.POINTER(C.c_int64),
                                       C.POINTER(i32), C.POINTER(dbl)]),
         "wlbm_get_state": (C.c_int, [vp, vp]),
+        "wlbm_save": (C.c_int, [vp, vp, C.c_size_t, C.POINTER(C.c_size_t)]),
+        "wlbm_load": (C.c_int, [vp, vp, C.c_size_t]),
         "wlbm_set_state": (C.c_int, [vp, vp]),
         "wlbm_adjoint_forward": (C.c_int, [vp, vp, i64, i32]),
         "wlbm_adjoint_backward": (C.c_int, [vp, vp, vp, vp, vp, C.POINTER(dbl), vp]),
@@ -232,6 +234,21 @@ class WormLBM:
         _check(lib.wlbm_run_steady(self.h, int(max_steps), int(check_every), float(tol),
                                    int(avg_steps), C.byref(steps), C.byref(conv), out), self.h)
         return steps.value, bool(conv.value), list(out)
+
+    def wlbm_save(self):
+        """Checkpoint of the current state and schedule cursor as a numpy uint8 array."""
+        import numpy as np
+        size = C.c_size_t(0)
+        _check(lib.wlbm_save(self.h, None, 0, C.byref(size)), self.h)
+        buf = np.empty(size.value, np.uint8)
+        _check(lib.wlbm_save(self.h, buf.ctypes.data_as(C.c_void_p), buf.nbytes, C.byref(size)),
+               self.h)
+        return buf
+
+    def wlbm_load(self, blob):
+        import numpy as np
+        buf = np.ascontiguousarray(blob, dtype=np.uint8)
+        _check(lib.wlbm_load(self.h, buf.ctypes.data_as(C.c_void_p), buf.nbytes), self.h)
 
     def wlbm_adjoint_forward(self, dT0, n_steps, ckpt_every):
         t = self._torch.as_tensor(dT0, dtype=self._torch.float32, device=self.device).contiguous()
