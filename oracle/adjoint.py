@@ -26,7 +26,7 @@ gradients equal central finite differences of the forward oracle.
 import numpy as np
 
 from . import lattice as L
-from .stepper import (WormLBM, shift, PERIODIC, ISOTHERMAL, ADIABATIC_DIFFUSE,
+from .stepper import (WormLBM, shift, PERIODIC, ISOTHERMAL, ADIABATIC_DIFFUSE, ADIABATIC,
                       XM, XP, YM, YP, INWARD_NORMAL)
 
 
@@ -110,20 +110,31 @@ def bc_transpose(m, lam):
                 lam[:, yy, xx] = 0.0
     # diffuse walls (forward pass 1): collected directions receive sum rho_k lam_k
     for (yy, xx, xw, yw) in reversed(m._corners()):
-        if k[xw] == ADIABATIC_DIFFUSE and k[yw] == ADIABATIC_DIFFUSE:
+        if k[xw] in ADIABATIC and k[yw] in ADIABATIC:
             n = (INWARD_NORMAL[xw][0], INWARD_NORMAL[yw][1])
             _diffuse_T(m, lam, yy, xx, n, True)
     for wall in (YP, YM, XP, XM):
-        if k[wall] == ADIABATIC_DIFFUSE:
+        if k[wall] in ADIABATIC:
             for (yy, xx) in m._edge_cells(wall):
-                _diffuse_T(m, lam, yy, xx, INWARD_NORMAL[wall], False)
+                _diffuse_T(m, lam, yy, xx, INWARD_NORMAL[wall], False, m.spec[wall])
     return g_t
 
 
-def _diffuse_T(m, lam, yy, xx, normal, strict):
+def _diffuse_T(m, lam, yy, xx, normal, strict, p=0.0):
+    """Transpose of the adiabatic ghost-cell rule: inward components keep their adjoint;
+    an outward one takes p lam_mirror + (1 - p) S, a parallel one p lam + (1 - p) S, with
+    S = sum over inward of rho_i lam_i."""
     inward, rho = m.diffuse_split(normal, strict)
     s = float((lam[inward, yy, xx] * rho[inward]).sum())
-    lam[~inward, yy, xx] = s
+    if p == 0.0:
+        lam[~inward, yy, xx] = s
+        return
+    mirror = m.mirror_index(normal)
+    dots = np.array(m.dirs) @ np.array(normal)
+    old = lam[:, yy, xx].copy()
+    for j in np.flatnonzero(~inward):
+        own = old[mirror[j]] if dots[j] < 0 else old[j]
+        lam[j, yy, xx] = p * own + (1.0 - p) * s
 
 
 class AdjointRun:

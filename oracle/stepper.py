@@ -30,8 +30,18 @@ Readings of passages the paper leaves open (each is also listed in the design doc):
     and adds A * w_i (s_i . n) / sum_k w_k (s_k . n) to each inward component i;
     a corner between two diffuse walls uses n = the quadrant diagonal and counts as
     inward only directions strictly inside the quadrant;
+  * adiabatic specular and specular-diffusive walls (Eq. adiabatic-specular and the
+    linear combination the paper names): with specularity p (1 for a specular wall,
+    the wall's `specularity` for a diffuse one, 0 by default), each outward component j
+    (s_j . n < 0) gives p d_j to its mirror direction (the normal component flipped) and
+    (1 - p) d_j to the diffuse collection; a component parallel to the wall keeps p of
+    its value and gives the rest to the collection; inward components receive
+    p d_mirror + (1 - p) rho_i A on top of what they hold.  Exactly conserving; p = 0 is
+    the diffuse rule;
   * corner ghost cells: a periodic link fills them; otherwise an isothermal x-wall,
-    then an isothermal y-wall, decides; two diffuse walls use the corner rule above;
+    then an isothermal y-wall, decides; two adiabatic walls (diffuse or specular) use the
+    diffuse corner rule above (a specular corner would map up to three directions onto
+    one);
   * heat flux (Eq. q_corr) uses the nominal unit vector s_i of each direction, v_g = 1.
 
 Pins: tests/test_oracle_stepper.py (energy conservation on periodic and adiabatic
@@ -44,7 +54,8 @@ import numpy as np
 
 from . import lattice as L
 
-PERIODIC, ISOTHERMAL, ADIABATIC_DIFFUSE = 0, 1, 2
+PERIODIC, ISOTHERMAL, ADIABATIC_DIFFUSE, ADIABATIC_SPECULAR = 0, 1, 2, 3
+ADIABATIC = (ADIABATIC_DIFFUSE, ADIABATIC_SPECULAR)
 XM, XP, YM, YP = 0, 1, 2, 3           # wall order: x-, x+, y-, y+
 INWARD_NORMAL = {XM: (1, 0), XP: (-1, 0), YM: (0, 1), YP: (0, -1)}
 
@@ -67,10 +78,17 @@ class WormLBM:
 
     def __init__(self, nx, ny, q, mfp, bc_kind=(0, 0, 0, 0), t_wall=(300.0,) * 4,
                  emulate_3d=True, relax_mode=0, t_ref=300.0, theta=L.THETA_DEFAULT,
-                 w_field=None):
+                 w_field=None, specularity=(0.0,) * 4):
         self.nx, self.ny, self.q = nx, ny, q
         self.bc_kind = tuple(int(k) for k in bc_kind)
         self.t_wall = tuple(float(t) for t in t_wall)
+        # specularity of each adiabatic wall: 1 for specular walls, the given fraction
+        # for diffuse ones
+        self.spec = tuple(1.0 if k == ADIABATIC_SPECULAR else
+                          (float(p) if k == ADIABATIC_DIFFUSE else 0.0)
+                          for k, p in zip(self.bc_kind, specularity))
+        if any(not (0.0 <= p <= 1.0) for p in self.spec):
+            raise ValueError("specularity must lie in [0, 1]")
         if (self.bc_kind[XM] == PERIODIC) != (self.bc_kind[XP] == PERIODIC) or \
            (self.bc_kind[YM] == PERIODIC) != (self.bc_kind[YP] == PERIODIC):
             raise ValueError("periodic walls come in opposite pairs")
@@ -151,15 +169,30 @@ class WormLBM:
         rho /= rho.sum()
         return inward, rho
 
-    def _diffuse_cell(self, yy, xx, normal, strict):
-        """One diffuse ghost cell, or (yy, xx) index arrays of a wall's ghost cells
-        that share the normal; each cell is handled on its own."""
+    def mirror_index(self, normal):
+        """Index of each direction reflected at a wall with an axis-aligned normal."""
+        index = {tuple(v): i for i, v in enumerate(self.dirs)}
+        fx, fy = (-1, 1) if normal[0] != 0 else (1, -1)
+        return np.array([index[(fx * a, fy * b)] for (a, b) in self.dirs])
+
+    def _diffuse_cell(self, yy, xx, normal, strict, p=0.0):
+        """One adiabatic ghost cell, or (yy, xx) index arrays of a wall's ghost cells
+        that share the normal; each cell is handled on its own.  p: specularity (edges
+        only)."""
         inward, rho = self.diffuse_split(normal, strict)
         yy, xx = np.atleast_1d(yy)[None, :], np.atleast_1d(xx)[None, :]
         out_i, in_i = np.flatnonzero(~inward)[:, None], np.flatnonzero(inward)[:, None]
         a = self.d[out_i, yy, xx].sum(axis=0)           # collected energy per cell
-        self.d[out_i, yy, xx] = 0.0
-        self.d[in_i, yy, xx] += rho[in_i] * a[None, :]
+        if p == 0.0:
+            self.d[out_i, yy, xx] = 0.0
+            self.d[in_i, yy, xx] += rho[in_i] * a[None, :]
+            return
+        mirror = self.mirror_index(normal)
+        old = self.d[:, yy[0], xx[0]]                   # (q, cells), a copy
+        dots = np.array(self.dirs) @ np.array(normal)
+        o, i = out_i[:, 0], in_i[:, 0]
+        self.d[out_i, yy, xx] = np.where((dots[o] == 0)[:, None], p * old[o], 0.0)
+        self.d[in_i, yy, xx] = old[i] + p * old[mirror[i]] + (1.0 - p) * rho[i][:, None] * a[None, :]
 
     def delta_e(self, t):
         """e_eq(T) - e_ref in float64."""
@@ -169,11 +202,12 @@ class WormLBM:
         k = self.bc_kind
         # 1. adiabatic diffuse walls (edges), then diffuse-diffuse corners
         for wall in (XM, XP, YM, YP):
-            if k[wall] == ADIABATIC_DIFFUSE:
+            if k[wall] in ADIABATIC:
                 cells = np.array(self._edge_cells(wall))
-                self._diffuse_cell(cells[:, 0], cells[:, 1], INWARD_NORMAL[wall], False)
+                self._diffuse_cell(cells[:, 0], cells[:, 1], INWARD_NORMAL[wall], False,
+                                   self.spec[wall])
         for (yy, xx, xw, yw) in self._corners():
-            if k[xw] == ADIABATIC_DIFFUSE and k[yw] == ADIABATIC_DIFFUSE:
+            if k[xw] in ADIABATIC and k[yw] in ADIABATIC:
                 n = (INWARD_NORMAL[xw][0], INWARD_NORMAL[yw][1])
                 self._diffuse_cell(yy, xx, n, True)
         # 2. isotropic blackbody walls (Eq. isotropic): d_i = w_i (e_eq(T_w) - e_ref)
@@ -251,8 +285,8 @@ class WormLBM:
 
     def total_energy(self, include_frame=False):
         """Sum of E - e_ref over the interior, or over the interior plus the ghost cells
-        that hold energy of the system: those of adiabatic-diffuse walls (a corner only
-        between two of them).  Periodic ghosts are copies; isothermal ghosts are the
+        that hold energy of the system: those of adiabatic (diffuse or specular) walls (a
+        corner only between two of them).  Periodic ghosts are copies; isothermal ghosts are the
         imposed reservoir, reset by every boundary pass (Sec. 2.6)."""
         if not include_frame:
             return float(self.d[:, 1:-1, 1:-1].sum())
@@ -266,6 +300,6 @@ class WormLBM:
         for yy in range(fh):
             for xx in range(fw):
                 sides = [s for s in (side_x[xx], side_y[yy]) if s >= 0]
-                if sides and all(k[s] == ADIABATIC_DIFFUSE for s in sides):
+                if sides and all(k[s] in ADIABATIC for s in sides):
                     total += float(self.d[:, yy, xx].sum())
         return total

@@ -107,11 +107,13 @@ def fuchs_sondheimer_3d(kn):
     return 1.0 - 1.5 * kn * val
 
 
-def fuchs_sondheimer_2d(q, kn):
+def fuchs_sondheimer_2d(q, kn, p=0.0):
     """Fuchs-Sondheimer ratio of a 2D film for the Q lattice directions and weights:
     sum_i w_i c_i^2 g(Kn |s_i|) / sum_i w_i c_i^2 with (c_i, s_i) = (cos, sin) of
-    direction i and g(a) = 1 - a (1 - exp(-1/a)), g(0) = 1 (directions along the film
-    never meet a wall)."""
+    direction i and, for walls of specularity p,
+    g(a) = 1 - a (1 - p)(1 - exp(-1/a)) / (1 - p exp(-1/a)), g(0) = 1 (directions along
+    the film never meet a wall): the deviation carried across the film by a direction
+    restarts from p times its mirror image at each wall."""
     dirs = L.ring_directions(q)
     u = L.unit_vectors(dirs)
     w = L.angular_weights(dirs)
@@ -120,7 +122,8 @@ def fuchs_sondheimer_2d(q, kn):
     for i in range(q):
         a = kn * s[i]
         if a > 0:
-            g[i] = 1.0 - a * (-math.expm1(-1.0 / a))
+            u = -math.expm1(-1.0 / a)             # 1 - exp(-1/a), also for large a
+            g[i] = 1.0 - a * (1.0 - p) * u / ((1.0 - p) + p * u)
     return float((w * c2 * g).sum() / (w * c2).sum())
 
 

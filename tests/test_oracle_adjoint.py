@@ -5,17 +5,22 @@ import numpy as np
 import pytest
 
 from oracle import adjoint as A
-from oracle.stepper import WormLBM, PERIODIC as P, ISOTHERMAL as I, ADIABATIC_DIFFUSE as D
+from oracle.stepper import (WormLBM, PERIODIC as P, ISOTHERMAL as I, ADIABATIC_DIFFUSE as D,
+                            ADIABATIC_SPECULAR as S)
 
-BC_CASES = [((P, P, P, P), (300.0,) * 4),
-            ((I, I, D, D), (300.7, 299.6, 300.0, 300.0)),
-            ((D, D, D, D), (300.0,) * 4),
-            ((P, P, I, D), (300.0, 300.0, 300.4, 300.0)),
-            ((D, I, P, P), (300.0, 300.3, 300.0, 300.0))]
+NO_SPEC = (0.0,) * 4
+BC_CASES = [((P, P, P, P), (300.0,) * 4, NO_SPEC),
+            ((I, I, D, D), (300.7, 299.6, 300.0, 300.0), NO_SPEC),
+            ((D, D, D, D), (300.0,) * 4, NO_SPEC),
+            ((P, P, I, D), (300.0, 300.0, 300.4, 300.0), NO_SPEC),
+            ((D, I, P, P), (300.0, 300.3, 300.0, 300.0), NO_SPEC),
+            ((I, I, S, S), (300.7, 299.6, 300.0, 300.0), NO_SPEC),
+            ((D, S, D, D), (300.0,) * 4, (0.35, 0.0, 0.6, 0.0))]
 
 
-def _model(kinds, tw, mfp, q=16, nx=5, ny=4):
-    return WormLBM(nx, ny, q, mfp, bc_kind=kinds, t_wall=tw, emulate_3d=True)
+def _model(kinds, tw, mfp, q=16, nx=5, ny=4, spec=NO_SPEC):
+    return WormLBM(nx, ny, q, mfp, bc_kind=kinds, t_wall=tw, emulate_3d=True,
+                   specularity=spec)
 
 
 def _one_step(m, d, hops, paused):
@@ -24,12 +29,12 @@ def _one_step(m, d, hops, paused):
     return m.collide_stream(m.d, hops, paused)
 
 
-@pytest.mark.parametrize("kinds,tw", BC_CASES)
-def test_reverse_step_is_exact_transpose(kinds, tw):
+@pytest.mark.parametrize("kinds,tw,spec", BC_CASES)
+def test_reverse_step_is_exact_transpose(kinds, tw, spec):
     rng = np.random.default_rng(3)
     nx, ny, q = 5, 4, 16
     mfp = 1.6 + 3 * rng.random((ny, nx))
-    m = _model(kinds, tw, mfp, q, nx, ny)
+    m = _model(kinds, tw, mfp, q, nx, ny, spec)
     for n in range(1, 4):                  # step 3 has paused diagonals
         hops, paused = m.sched.advance(n)
     assert any(paused)
@@ -55,7 +60,7 @@ def test_reverse_step_is_exact_transpose(kinds, tw):
     A._periodic_links_T(m, gW[None])
     base = float((lam_p * _one_step(m, d_in, hops, paused)).sum())
     for (y, x) in [(0, 0), (1, 3), (3, 4), (2, 2)]:
-        m2 = _model(kinds, tw, mfp, q, nx, ny)
+        m2 = _model(kinds, tw, mfp, q, nx, ny, spec)
         wi = m.w_int.copy()
         wi[y, x] += 1.0
         m2.wf = m2._frame_scalar(wi)
@@ -67,10 +72,11 @@ def _fd(fun, h):
     return (fun(h) - fun(-h)) / (2 * h)
 
 
-@pytest.mark.parametrize("kinds,objective", [((I, I, P, P), "temperature"),
-                                             ((I, I, D, D), "temperature"),
-                                             ((I, I, D, D), "flux_x")])
-def test_gradients_match_central_differences(kinds, objective):
+@pytest.mark.parametrize("kinds,objective,spec", [((I, I, P, P), "temperature", NO_SPEC),
+                                                  ((I, I, D, D), "temperature", NO_SPEC),
+                                                  ((I, I, D, D), "flux_x", NO_SPEC),
+                                                  ((I, I, D, S), "flux_x", (0, 0, 0.5, 0))])
+def test_gradients_match_central_differences(kinds, objective, spec):
     """Gradients of J (mean T - T_ref, or mean q_x, on a probe column) with respect to the
     per-cell MFP, the wall temperatures and the start field, against central differences
     of the forward oracle."""
@@ -82,7 +88,8 @@ def test_gradients_match_central_differences(kinds, objective):
     probe = np.zeros((ny, nx), bool)
     probe[:, 14] = True
     tw = (300.5, 299.8, 300.0, 300.0)
-    kw = dict(nx=nx, ny=ny, q=q, mfp=mfp, bc_kind=kinds, t_wall=tw, emulate_3d=True)
+    kw = dict(nx=nx, ny=ny, q=q, mfp=mfp, bc_kind=kinds, t_wall=tw, emulate_3d=True,
+              specularity=spec)
     run = A.AdjointRun(kw, dT0, steps, probe, objective)
     g = run.gradients()
     assert g["J"] == pytest.approx(run.forward(), rel=1e-14)

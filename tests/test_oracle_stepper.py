@@ -7,9 +7,9 @@ import numpy as np
 import pytest
 
 from oracle import lattice as L
-from oracle.stepper import WormLBM, PERIODIC, ISOTHERMAL, ADIABATIC_DIFFUSE
+from oracle.stepper import WormLBM, PERIODIC, ISOTHERMAL, ADIABATIC_DIFFUSE, ADIABATIC_SPECULAR
 
-P, I, A = PERIODIC, ISOTHERMAL, ADIABATIC_DIFFUSE
+P, I, A, S = PERIODIC, ISOTHERMAL, ADIABATIC_DIFFUSE, ADIABATIC_SPECULAR
 
 
 def _rand(ny, nx, seed):
@@ -28,11 +28,17 @@ def test_energy_conserved_on_periodic_grid():
         assert abs(m.total_energy() - e0) <= 1e-13 * scale
 
 
-@pytest.mark.parametrize("kinds", [(A, A, A, A), (P, P, A, A), (A, A, P, P)])
-def test_energy_conserved_with_adiabatic_walls(kinds):
-    """Adiabatic walls (Sec. 2.6) neither add nor remove energy: the total over the
-    interior plus the wall cells stays constant."""
-    m = WormLBM(21, 17, 32, 2.5, bc_kind=kinds)
+@pytest.mark.parametrize("kinds,spec", [((A, A, A, A), (0, 0, 0, 0)),
+                                       ((P, P, A, A), (0, 0, 0, 0)),
+                                       ((A, A, P, P), (0, 0, 0, 0)),
+                                       ((S, S, S, S), (0, 0, 0, 0)),
+                                       ((A, S, A, A), (0.3, 0, 0.7, 1.0)),
+                                       ((P, P, S, A), (0, 0, 0, 0.5))])
+def test_energy_conserved_with_adiabatic_walls(kinds, spec):
+    """Adiabatic walls (Sec. 2.6: diffuse, specular and their linear combinations) neither
+    add nor remove energy: the total over the interior plus the wall cells stays
+    constant."""
+    m = WormLBM(21, 17, 32, 2.5, bc_kind=kinds, specularity=spec)
     m.init_temperature(_rand(17, 21, 2))
     m.apply_bc()
     e0 = m.total_energy(include_frame=True)
@@ -204,3 +210,21 @@ def test_cross_plane_fourier_steady_profile_is_linear():
     assert np.abs(np.polyval(fit, x) - e)[6:-6].max() < 1e-4 * np.ptp(e)
     assert fit[0] < 0 and q.mean() > 0
     assert np.ptp(q[2:-2]) < 0.03 * q.mean()
+
+
+def test_specular_mirror_and_zero_specularity():
+    """The mirror of a direction at a wall flips the normal component and is an
+    involution; a specularity of 0 gives the diffuse wall exactly (same arithmetic, so
+    bit for bit)."""
+    m = WormLBM(9, 7, 24, 3.0)
+    for normal in ((1, 0), (0, 1)):
+        mi = m.mirror_index(normal)
+        assert np.array_equal(mi[mi], np.arange(24))
+        for i, (a, b) in enumerate(m.dirs):
+            assert m.dirs[mi[i]] == ((-a, b) if normal[0] else (a, -b))
+    x = WormLBM(13, 9, 16, 2.0, bc_kind=(A, A, A, A))
+    y = WormLBM(13, 9, 16, 2.0, bc_kind=(A, A, A, A), specularity=(0.0,) * 4)
+    for z in (x, y):
+        z.init_temperature(_rand(9, 13, 4))
+        z.step(30)
+    assert np.array_equal(x.d, y.d)

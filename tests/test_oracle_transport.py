@@ -10,7 +10,7 @@ import pytest
 
 from oracle import lattice as L
 from oracle import transport as T
-from oracle.stepper import WormLBM, PERIODIC, ISOTHERMAL, ADIABATIC_DIFFUSE
+from oracle.stepper import WormLBM, PERIODIC, ISOTHERMAL, ADIABATIC_DIFFUSE, ADIABATIC_SPECULAR
 
 P, I, A = PERIODIC, ISOTHERMAL, ADIABATIC_DIFFUSE
 GOLDEN = pathlib.Path(__file__).parent / "golden"
@@ -238,3 +238,36 @@ def test_run_steady_windows():
     steps, conv, res, _ = T.run_steady(m, 12, 6, 0.0, 3, 1.0)
     assert steps == 12 and not conv
     assert res == pytest.approx(np.abs(w2 - w1).max() / 6, rel=1e-9)
+
+
+@pytest.mark.parametrize("p,kind", [(0.5, ADIABATIC_DIFFUSE), (1.0, ADIABATIC_SPECULAR)])
+def test_specular_film_converges_to_fuchs_sondheimer(p, kind):
+    """Partly specular walls (Sec. 2.6, the linear combination of the diffuse and specular
+    rules) with specularity p: the film-to-bulk band conductivity converges to first order
+    in 1/N_y to the discrete-ordinate ratio with specularity p; fully specular walls do
+    not reduce the in-plane conductivity (ratio 1)."""
+    q, kn = 32, 1.0
+    ratio = {}
+    for ny in (8, 16):
+        mfp, nx = kn * ny, 8 * ny
+        k = {}
+        for name, bc in (("bulk", (I, I, P, P)), ("film", (I, I, kind, kind))):
+            m = WormLBM(nx, ny, q, mfp, bc_kind=bc, t_wall=(300.5, 299.5, 300, 300),
+                        specularity=(0.0, 0.0, p, p))
+            _linear_start(m)
+            m.step(600)
+            k[name] = _band_kappa_mean(m, mfp, 400, 10)
+        ratio[ny] = k["film"] / k["bulk"]
+    fs = T.fuchs_sondheimer_2d(q, kn * 2.0 / 3.0, p)
+    assert abs(ratio[16] - fs) < abs(ratio[8] - fs)
+    assert 2 * ratio[16] - ratio[8] == pytest.approx(fs, rel=0.01)
+
+
+def test_fuchs_sondheimer_2d_specularity_limits():
+    """Specular walls leave every direction's conductivity intact (ratio 1); the
+    thick-film slope scales with 1 - p."""
+    for kn in (0.1, 1.0, 20.0):
+        assert T.fuchs_sondheimer_2d(64, kn, 1.0) == pytest.approx(1.0, abs=1e-14)
+    base = 1 - T.fuchs_sondheimer_2d(256, 1e-3)
+    for p in (0.25, 0.5, 0.9):
+        assert (1 - T.fuchs_sondheimer_2d(256, 1e-3, p)) == pytest.approx((1 - p) * base, rel=1e-6)
