@@ -3,7 +3,8 @@
 Workload (default): 2048 x 2048 periodic grid, Q = 64 worm directions, float32
 deviation storage, uniform MFP drawn log-uniform in [1, 1000] cells from the seed, 16
 seeded Gaussian pulses.  One bench step = one worm-LBM time step over the whole grid:
-the periodic ghost-frame refresh plus the fused relax-and-stream kernel.
+the periodic ghost-frame refresh plus the fused relax-and-stream kernel, with the FP64
+reductions (energy, heat flux, conductivity, steady-state residual) every R = 500 steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
                   [--storage fp32|bf16] [--nx N] [--q Q]
@@ -51,6 +52,9 @@ def parse():
                    help="pulses: 2048^2 periodic Q=64 (default); film: 4096x256 in-plane "
                         "film, Q=128, isothermal x walls, diffuse y walls (Kn = 1)")
     p.add_argument("--e2e-steps", type=int, default=3)
+    p.add_argument("--reduce-every", type=int, default=500, metavar="R",
+                   help="FP64 reductions (energy, flux, conductivity, residual) every R steps "
+                        "inside the timed region and the e2e run (0: none)")
     p.add_argument("--fuse", type=int, default=None,
                    help="1: step kernel mirrors periodic edges, 0: separate pass (library "
                         "default)")
@@ -193,6 +197,19 @@ def run_batch(args):
     if world > 1:
         tdist.destroy_process_group()
     return 0
+
+
+def run_with_reductions(h, steps, every):
+    """`steps` time steps with wlbm_reduce (float64 energy, flux, conductivity and
+    residual, read back to the host) after every `every` steps; returns the readings."""
+    reds, done = [], 0
+    while done < steps:
+        k = steps - done if every <= 0 else min(every, steps - done)
+        h.wlbm_step(k)
+        done += k
+        if every > 0 and done % every == 0:
+            reds.append(h.wlbm_reduce())
+    return reds
 
 
 def bytes_per_update(storage, q):
@@ -389,6 +406,7 @@ def main():
         dT = torch.as_tensor(cfg["dT"]).to("cuda", non_blocking=False)
         h.wlbm_init_temperature(dT)
         h.wlbm_step(args.warmup)
+        e_start = h.wlbm_reduce()[0] if args.reduce_every else None
         stream.synchronize()
         _, _, launches0 = h.wlbm_profile_read()
 
@@ -402,7 +420,7 @@ def main():
         barrier()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
-        h.wlbm_step(args.steps)
+        reds = run_with_reductions(h, args.steps, args.reduce_every)
         ev1.record(stream)
         barrier()
         h.wlbm_profile(False)
@@ -437,7 +455,7 @@ def main():
                 t0 = time.perf_counter()
                 dev_in.copy_(host_in, non_blocking=True)
                 h.wlbm_init_temperature(dev_in)
-                h.wlbm_step(run_steps)
+                e2e_reds = run_with_reductions(h, run_steps, args.reduce_every)
                 dTo, _, _ = h.wlbm_moments(want_q=False)
                 host_out.copy_(dTo, non_blocking=True)
                 stream.synchronize()
@@ -448,7 +466,7 @@ def main():
                 dist.all_reduce(tt, op=dist.ReduceOp.MAX)
             e2e = {"value": cfg["q"] * cells * run_steps * world / (sum(times) / len(times)),
                    "unit": UNIT, "h2d_bytes_per_step": int(host_in.numel() * 4),
-                   "d2h_bytes_per_step": int(host_out.numel() * 4),
+                   "d2h_bytes_per_step": int(host_out.numel() * 4 + 8 * 9 * len(e2e_reds)),
                    "lbm_steps_per_e2e_step": run_steps}
         h.close()
         adj = None
@@ -490,6 +508,14 @@ def main():
             "gpu_launches": int(launches1 - launches0),
             "hbm_roofline_pct_of_measured": 100.0 * achieved / peak,
         }
+        if reds:
+            line["fp64_reductions"] = {
+                "every_steps": args.reduce_every, "count_in_timed_region": len(reds),
+                "energy_interior_last": reds[-1][0],
+                "energy_rel_change_over_timed_region":
+                    (reds[-1][0] - e_start) / abs(e_start) if e_start else None,
+                "mean_qx_last": reds[-1][2], "kappa_apparent_last": reds[-1][6],
+                "kappa_band_last": reds[-1][7], "residual_K_per_step_last": reds[-1][8]}
         if e2e is not None:
             line["e2e"] = e2e
         if adj is not None:

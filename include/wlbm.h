@@ -41,7 +41,9 @@ typedef enum wlbm_status {
 enum {
   WLBM_BC_PERIODIC = 0,          /* periodic link to the opposite wall (must be paired) */
   WLBM_BC_ISOTHERMAL = 1,        /* isotropic blackbody wall, Eq. isotropic            */
-  WLBM_BC_ADIABATIC_DIFFUSE = 2  /* adiabatic diffuse wall, Eq. adiabatic-diffuse      */
+  WLBM_BC_ADIABATIC_DIFFUSE = 2, /* adiabatic diffuse wall, Eq. adiabatic-diffuse;     *
+                                  * partly specular with wlbm_boundary.specularity     */
+  WLBM_BC_ADIABATIC_SPECULAR = 3 /* adiabatic specular wall, Eq. adiabatic-specular     */
 };
 
 /* Storage of the direction planes.  Both store the deviation of e_i from the reference
@@ -62,9 +64,19 @@ typedef struct wlbm_grid {
   double theta;        /* hbar omega0 / k_B, K (624.8 for the paper's 81.8e12 rad/s)   */
 } wlbm_grid;
 
+/* Adiabatic walls (Sec. 2.6).  A ghost cell of a wall with specularity p in [0, 1] (1 for
+ * WLBM_BC_ADIABATIC_SPECULAR, specularity[k] for WLBM_BC_ADIABATIC_DIFFUSE; the paper's
+ * specular-diffusive wall is their linear combination) moves p of each outward component
+ * to its mirror direction (normal component flipped, Eq. adiabatic-specular) and 1 - p to
+ * the diffuse collection, which it re-emits into the inward directions with fractions
+ * w_i (s_i . n) / sum_k w_k (s_k . n) (Eq. adiabatic-diffuse, normalised to conserve
+ * energy); components parallel to the wall keep p of their value.  A corner between two
+ * adiabatic walls uses the diffuse rule about the quadrant diagonal. */
 typedef struct wlbm_boundary {
   int32_t kind[4];     /* WLBM_BC_* for the walls x-, x+, y-, y+                        */
   double t_wall[4];    /* wall temperature (K) of isothermal walls; ignored otherwise   */
+  double specularity[4]; /* specular fraction of WLBM_BC_ADIABATIC_DIFFUSE walls, [0, 1]
+                            (0: fully diffuse); ignored for other kinds                */
 } wlbm_boundary;
 
 /* Device-memory provider.  alloc returns a device pointer of at least `bytes` bytes
@@ -122,9 +134,10 @@ wlbm_status wlbm_moments(wlbm_handle* h, float* dT, float* qx, float* qy);
  * step = v_g = 1, energy as E - e_ref with the paper's unit prefactor set to 1.
  *   out[0] sum over interior cells of E - e_ref   (energy conservation, Eq.
  *          lbm-energy-density)
- *   out[1] the same plus the ghost cells of adiabatic-diffuse walls (energy they hold;
- *          a corner counts when both its walls are adiabatic-diffuse).  Periodic ghosts
- *          are copies and isothermal ghosts the imposed reservoir, so neither counts.
+ *   out[1] the same plus the ghost cells of adiabatic (diffuse or specular) walls
+ *          (energy they hold; a corner counts when both its walls are adiabatic).
+ *          Periodic ghosts are copies and isothermal ghosts the imposed reservoir, so
+ *          neither counts.
  *   out[2] mean of q_x over interior cells, out[3] mean of q_y  (Eq. q_corr)
  *   out[4] mean of q_x over the central band of columns x0 <= x < x0 + m, x0 = nx / 4,
  *          m = nx / 2 (integer division; NaN if m < 1)

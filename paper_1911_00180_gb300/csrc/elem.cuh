@@ -64,7 +64,7 @@ struct Elem<__nv_bfloat16> {
 
 // Whether framed cell (fx, fy) of an fw x fh frame counts towards the energy held by the
 // walls: interior cells do not; a ghost cell does when every side it lies on is an
-// adiabatic-diffuse wall (bit k of diff_mask for side k = x-, x+, y-, y+).  Periodic
+// adiabatic wall (bit k of diff_mask for side k = x-, x+, y-, y+).  Periodic
 // ghosts are copies and isothermal ghosts a reservoir reset by every wall pass.
 __device__ __forceinline__ bool wall_energy_cell(int fx, int fy, int fw, int fh, int diff_mask) {
   const int sx = fx == 0 ? 0 : (fx == fw - 1 ? 1 : -1);

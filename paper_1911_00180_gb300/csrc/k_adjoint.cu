@@ -213,6 +213,18 @@ __global__ void k_periodic_T_y(float* planes, int64_t plane, int pitch, int nx, 
 constexpr int kWallWarpsT = 8;
 static_assert(kWallCellsPerBlock == kWallWarpsT, "one warp per cell of a block");
 
+// New adjoint of a collected (outward or parallel) direction i of an adiabatic ghost cell
+// with specularity p: p l_mirror(i) + (1 - p) S (a parallel direction is its own mirror);
+// S = sum_k rho_k l_k over the inward directions.  Mirrors of collected directions are
+// inward, so no value read here is written by the same pass.
+__device__ __forceinline__ float collected_T(const WallArgs& wa, const WallSeg& g,
+                                             const int16_t* mir, const float* lam, int64_t off,
+                                             int i, float S) {
+  if (g.spec == 0.f) return S;
+  const float own = lam[int64_t(mir[i]) * wa.plane + off];
+  return fmaf(g.spec, own, (1.f - g.spec) * S);
+}
+
 // One ghost cell by one warp, lanes over the directions; returns sum_i w_i l_i of an
 // isothermal cell (0 for diffuse cells) for the wall-temperature gradient.
 __device__ __forceinline__ float walls_T_cell(const WallArgs& wa, const WallSeg& g, int idx,
@@ -232,8 +244,9 @@ __device__ __forceinline__ float walls_T_cell(const WallArgs& wa, const WallSeg&
   for (int i = lane; i < wa.q; i += 32)
     if (rho[i] != 0.f) part = fmaf(rho[i], lam[int64_t(i) * wa.plane + off], part);
   const float S = warp_sum(part);
+  const int16_t* mir = wa.mirror + int64_t(g.mirror) * wa.q;
   for (int i = lane; i < wa.q; i += 32)
-    if (rho[i] == 0.f) lam[int64_t(i) * wa.plane + off] = S;
+    if (rho[i] == 0.f) lam[int64_t(i) * wa.plane + off] = collected_T(wa, g, mir, lam, off, i, S);
   return 0.f;
 }
 
@@ -295,8 +308,9 @@ __global__ void __launch_bounds__(32 * kWallWarpsT) k_walls_T(const WallArgs wa,
     return;
   }
   if (!on) return;
+  const int16_t* mir = wa.mirror + int64_t(g.mirror) * wa.q;
   for (int i = warp; i < wa.q; i += kWallWarpsT)
-    if (rho[i] == 0.f) lam[int64_t(i) * wa.plane + off] = S;
+    if (rho[i] == 0.f) lam[int64_t(i) * wa.plane + off] = collected_T(wa, g, mir, lam, off, i, S);
 }
 
 // l^N_i(x) = dJ/dT(x) * dT/dE at the final local energy (E = sum_i d_i, Eq. pseudo-T)

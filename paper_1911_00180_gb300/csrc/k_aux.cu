@@ -63,6 +63,7 @@ struct WallSmem {
   float part[kWallWarps * 32];
   float w[kMaxQ];
   float rho[kMaxQ];
+  int16_t src[kMaxQ];    // mirror direction at this wall (specular segments)
   uint8_t par[kMaxQ];
 };
 
@@ -116,6 +117,27 @@ __device__ __forceinline__ void walls_cell(const WallArgs& a, const WallSmem& sm
       if (i < a.q && sm.rho[i] == 0.f) part += val[u];
     }
     const float A = warp_sum(part);
+    if (g.spec > 0.f) {
+      // inward directions first (they read their mirrors' outward values), then the rest
+      const float p = g.spec, Ad = (1.f - g.spec) * A;
+#pragma unroll
+      for (int u = 0; u < kHoldCell; ++u) {
+        const int i = lane + 32 * u;
+        if (i >= a.q || sm.rho[i] == 0.f) continue;
+        const int j = sm.src[i];
+        const float m = wall_load(ptr(j), sm.w[j], ref, R, a.scale);
+        wall_store(ptr(i), fmaf(Ad, sm.rho[i], fmaf(p, m, val[u])), sm.w[i], ref, R,
+                   a.inv_scale);
+      }
+      __syncwarp();
+#pragma unroll
+      for (int u = 0; u < kHoldCell; ++u) {
+        const int i = lane + 32 * u;
+        if (i >= a.q || sm.rho[i] != 0.f) continue;
+        wall_store(ptr(i), sm.src[i] == i ? p * val[u] : 0.f, sm.w[i], ref, R, a.inv_scale);
+      }
+      return;
+    }
 #pragma unroll
     for (int u = 0; u < kHoldCell; ++u) {
       const int i = lane + 32 * u;
@@ -129,6 +151,23 @@ __device__ __forceinline__ void walls_cell(const WallArgs& a, const WallSmem& sm
   for (int i = lane; i < a.q; i += 32)
     if (sm.rho[i] == 0.f) part += wall_load(ptr(i), sm.w[i], ref, R, a.scale);
   const float A = warp_sum(part);
+  if (g.spec > 0.f) {
+    const float p = g.spec, Ad = (1.f - g.spec) * A;
+    for (int i = lane; i < a.q; i += 32) {
+      if (sm.rho[i] == 0.f) continue;
+      const int j = sm.src[i];
+      const float m = wall_load(ptr(j), sm.w[j], ref, R, a.scale);
+      const float v = wall_load(ptr(i), sm.w[i], ref, R, a.scale);
+      wall_store(ptr(i), fmaf(Ad, sm.rho[i], fmaf(p, m, v)), sm.w[i], ref, R, a.inv_scale);
+    }
+    __syncwarp();
+    for (int i = lane; i < a.q; i += 32) {
+      if (sm.rho[i] != 0.f) continue;
+      const float d = sm.src[i] == i ? p * wall_load(ptr(i), sm.w[i], ref, R, a.scale) : 0.f;
+      wall_store(ptr(i), d, sm.w[i], ref, R, a.inv_scale);
+    }
+    return;
+  }
   for (int i = lane; i < a.q; i += 32) {
     const float d = sm.rho[i] == 0.f
                         ? 0.f : fmaf(A, sm.rho[i], wall_load(ptr(i), sm.w[i], ref, R, a.scale));
@@ -146,10 +185,12 @@ __device__ __forceinline__ void walls_chunk(const WallArgs& a, const uint8_t* co
   const int lane = int(threadIdx.x) & 31, warp = int(threadIdx.x) >> 5;
   const bool diffuse = g.action != WLBM_BC_ISOTHERMAL;
   const float* rho = a.rho + int64_t(g.table) * a.q;
+  const int16_t* mir = a.mirror + int64_t(g.mirror) * a.q;
   for (int i = int(threadIdx.x); i < a.q; i += int(blockDim.x)) {
     sm.par[i] = uint8_t(a.tape ? 0 : (codes[i] >> 4) & 1);
     sm.w[i] = a.w[i];
     sm.rho[i] = diffuse ? rho[i] : 0.f;
+    sm.src[i] = diffuse && g.spec > 0.f ? mir[i] : int16_t(i);
   }
   __syncthreads();
   if (!wall_seg_rowwise(g)) {                  // one warp per cell, lanes over directions
@@ -195,6 +236,30 @@ __device__ __forceinline__ void walls_chunk(const WallArgs& a, const uint8_t* co
     float A = 0.f;
 #pragma unroll
     for (int k = 0; k < kWallWarps; ++k) A += sm.part[k * 32 + lane];
+    if (g.spec > 0.f) {            // uniform over the block (one segment)
+      // inward directions first (they read their mirrors' outward values), then the rest
+      const float p = g.spec, Ad = (1.f - g.spec) * A;
+      if (on) {
+#pragma unroll
+        for (int u = 0; u < kHoldChunk; ++u) {
+          const int i = warp + kWallWarps * u;
+          if (i >= a.q || sm.rho[i] == 0.f) continue;
+          const int j = sm.src[i];
+          const float m = wall_load(ptr(j), sm.w[j], ref, R, a.scale);
+          wall_store(ptr(i), fmaf(Ad, sm.rho[i], fmaf(p, m, val[u])), sm.w[i], ref, R,
+                     a.inv_scale);
+        }
+      }
+      __syncthreads();
+      if (!on) return;
+#pragma unroll
+      for (int u = 0; u < kHoldChunk; ++u) {
+        const int i = warp + kWallWarps * u;
+        if (i >= a.q || sm.rho[i] != 0.f) continue;
+        wall_store(ptr(i), sm.src[i] == i ? p * val[u] : 0.f, sm.w[i], ref, R, a.inv_scale);
+      }
+      return;
+    }
     if (!on) return;
 #pragma unroll
     for (int u = 0; u < kHoldChunk; ++u) {
@@ -216,6 +281,26 @@ __device__ __forceinline__ void walls_chunk(const WallArgs& a, const uint8_t* co
   float A = 0.f;
 #pragma unroll
   for (int k = 0; k < kWallWarps; ++k) A += sm.part[k * 32 + lane];
+  if (g.spec > 0.f) {
+    const float p = g.spec, Ad = (1.f - g.spec) * A;
+    if (on) {
+      for (int i = warp; i < a.q; i += kWallWarps) {
+        if (sm.rho[i] == 0.f) continue;
+        const int j = sm.src[i];
+        const float m = wall_load(ptr(j), sm.w[j], ref, R, a.scale);
+        const float v = wall_load(ptr(i), sm.w[i], ref, R, a.scale);
+        wall_store(ptr(i), fmaf(Ad, sm.rho[i], fmaf(p, m, v)), sm.w[i], ref, R, a.inv_scale);
+      }
+    }
+    __syncthreads();
+    if (!on) return;
+    for (int i = warp; i < a.q; i += kWallWarps) {
+      if (sm.rho[i] != 0.f) continue;
+      const float d = sm.src[i] == i ? p * wall_load(ptr(i), sm.w[i], ref, R, a.scale) : 0.f;
+      wall_store(ptr(i), d, sm.w[i], ref, R, a.inv_scale);
+    }
+    return;
+  }
   if (!on) return;
 #pragma unroll 4
   for (int i = warp; i < a.q; i += kWallWarps) {

@@ -152,7 +152,8 @@ extern "C" wlbm_status wlbm_reduce_state_noalloc(const float* framed, int32_t nx
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   int diff_mask = 0;
   for (int k = 0; k < 4; ++k)
-    if (bc_kind[k] == WLBM_BC_ADIABATIC_DIFFUSE) diff_mask |= 1 << k;
+    if (bc_kind[k] == WLBM_BC_ADIABATIC_DIFFUSE || bc_kind[k] == WLBM_BC_ADIABATIC_SPECULAR)
+      diff_mask |= 1 << k;
   k_partials<<<unsigned(nblocks), kThreads, 0, s>>>(framed, nx, ny, q, diff_mask, partials);
   k_finish<<<1, kThreads, 0, s>>>(partials, int(nblocks), 1.0 / (double(nx) * ny), out);
   const cudaError_t le = cudaGetLastError();

@@ -37,6 +37,7 @@ struct wlbm_handle {
   float scale = 1.f, inv_scale = 1.f;
   int bc_kind[4] = {0, 0, 0, 0};
   double t_wall[4] = {0, 0, 0, 0};
+  float spec[4] = {0.f, 0.f, 0.f, 0.f};   // specularity of adiabatic walls
   int xper = 1, yper = 1;
   Lattice lat;
   TasState tas;
@@ -50,6 +51,7 @@ struct wlbm_handle {
   int e_cur = 0, e_ref = -1, e_spare = 1;      // roles of the energy planes
   float* wfield = nullptr;    // framed W_corr (per-cell MFP only)
   float* consts = nullptr;    // w[q], sx[q], sy[q], rho[8][q]
+  int16_t* mirror = nullptr;  // [2][q] mirror directions (c_x flipped, c_y flipped)
   uint8_t* d_codes = nullptr; // [kChunk][q]
   uint16_t* d_order = nullptr; // [kChunk][q + 17] kind-sorted directions (variant 3)
   double* d_red = nullptr;    // [kReduceOut]
@@ -213,6 +215,10 @@ void wlbm_handle::build_wall_segments() {
     s.table = table;
     s.wall = wall;
     s.iso = kind == WLBM_BC_ISOTHERMAL ? float(delta_e(t_wall[wall])) : 0.f;
+    // edges of adiabatic walls: specularity and mirror table (x walls flip c_x, y walls
+    // c_y); corners keep the diffuse rule
+    s.spec = kind == WLBM_BC_ADIABATIC_DIFFUSE && table < 4 ? spec[wall] : 0.f;
+    s.mirror = table < 2 ? 0 : 1;
   };
   for (int k = 0; k < 4; ++k) {
     if (bc_kind[k] == WLBM_BC_PERIODIC) continue;
@@ -236,6 +242,7 @@ void wlbm_handle::build_wall_segments() {
   a.q = g.q;
   a.w = w_dev();
   a.rho = rho_dev();
+  a.mirror = mirror;
   a.scale = scale;
   a.inv_scale = inv_scale;
 }
@@ -282,6 +289,19 @@ static std::vector<float> rho_tables(const Lattice& L) {
     for (int i = 0; i < q; ++i) rho[size_t(t) * q + i] = float(r[i] / sum);
   }
   return rho;
+}
+
+// Index of every direction with c_x flipped (row 0) and with c_y flipped (row 1): the
+// mirror images at x and y walls (Eq. adiabatic-specular).
+static std::vector<int16_t> mirror_tables(const Lattice& L) {
+  const int q = L.q;
+  std::vector<int16_t> m(size_t(2) * q, 0);
+  for (int i = 0; i < q; ++i)
+    for (int j = 0; j < q; ++j) {
+      if (L.dx[j] == -L.dx[i] && L.dy[j] == L.dy[i]) m[i] = int16_t(j);
+      if (L.dx[j] == L.dx[i] && L.dy[j] == -L.dy[i]) m[size_t(q) + i] = int16_t(j);
+    }
+  return m;
 }
 
 extern "C" {
@@ -339,8 +359,10 @@ wlbm_status wlbm_create(const wlbm_grid* grid, const float* mfp_cells, double mf
     return WLBM_ERR_INVALID_ARG;
   }
   for (int k = 0; k < 4; ++k) {
-    if (bc->kind[k] < 0 || bc->kind[k] > 2 ||
-        (bc->kind[k] == WLBM_BC_ISOTHERMAL && !(bc->t_wall[k] > 0))) {
+    if (bc->kind[k] < 0 || bc->kind[k] > 3 ||
+        (bc->kind[k] == WLBM_BC_ISOTHERMAL && !(bc->t_wall[k] > 0)) ||
+        (bc->kind[k] == WLBM_BC_ADIABATIC_DIFFUSE &&
+         !(bc->specularity[k] >= 0.0 && bc->specularity[k] <= 1.0))) {
       set_global_error("wlbm_create: invalid boundary kind or wall temperature");
       return WLBM_ERR_INVALID_ARG;
     }
@@ -357,7 +379,14 @@ wlbm_status wlbm_create(const wlbm_grid* grid, const float* mfp_cells, double mf
   h->t_ref = G.t_ref;
   h->theta = G.theta;
   h->e_eq_ref = 1.0 / std::expm1(G.theta / G.t_ref);
-  for (int k = 0; k < 4; ++k) { h->bc_kind[k] = bc->kind[k]; h->t_wall[k] = bc->t_wall[k]; }
+  for (int k = 0; k < 4; ++k) {
+    // a specular wall is the adiabatic wall with specularity 1 (one wall path for both)
+    h->bc_kind[k] = bc->kind[k] == WLBM_BC_ADIABATIC_SPECULAR ? WLBM_BC_ADIABATIC_DIFFUSE
+                                                              : bc->kind[k];
+    h->spec[k] = bc->kind[k] == WLBM_BC_ADIABATIC_SPECULAR ? 1.f
+                 : bc->kind[k] == WLBM_BC_ADIABATIC_DIFFUSE ? float(bc->specularity[k]) : 0.f;
+    h->t_wall[k] = bc->t_wall[k];
+  }
   h->xper = bc->kind[0] == WLBM_BC_PERIODIC;
   h->yper = bc->kind[2] == WLBM_BC_PERIODIC;
   if (!build_lattice(G.q, &h->lat)) {
@@ -434,6 +463,7 @@ wlbm_status wlbm_create(const wlbm_grid* grid, const float* mfp_cells, double mf
   h->e_spare = 1;
   h->e_ref = h->bf16() ? 2 : -1;
   h->consts = static_cast<float*>(h->dev_alloc(size_t(11) * G.q * 4));
+  h->mirror = static_cast<int16_t*>(h->dev_alloc(size_t(2) * G.q * 2));
   h->d_codes = static_cast<uint8_t*>(h->dev_alloc(size_t(kChunk) * G.q));
   h->d_order = static_cast<uint16_t*>(h->dev_alloc(size_t(kChunk) * (G.q + 17) * 2));
   h->d_red = static_cast<double*>(h->dev_alloc(8 * sizeof(double)));
@@ -444,7 +474,7 @@ wlbm_status wlbm_create(const wlbm_grid* grid, const float* mfp_cells, double mf
   if (h->has_tmap) h->step_variant = 3;   // the fastest step kernel where it applies
   if (h->field_w) h->wfield = static_cast<float*>(h->dev_alloc(size_t(g.plane) * 4));
   if (!h->planes || !h->e[0] || !h->e[1] || (n_e == 3 && !h->e[2]) || !h->consts ||
-      !h->d_codes || !h->d_order || !h->d_red || !h->d_snap || !h->d_status ||
+      !h->d_codes || !h->d_order || !h->d_red || !h->d_snap || !h->d_status || !h->mirror ||
       (h->field_w && !h->wfield))
     return bad(WLBM_ERR_OOM, "wlbm_create: device allocation failed");
 
@@ -463,6 +493,9 @@ wlbm_status wlbm_create(const wlbm_grid* grid, const float* mfp_cells, double mf
     e = cudaMemsetAsync(h->e[k], 0, size_t(g.plane) * 4, s);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(h->consts, consts.data(), consts.size() * 4, cudaMemcpyHostToDevice, s);
+  const std::vector<int16_t> mirror = mirror_tables(h->lat);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->mirror, mirror.data(), mirror.size() * 2, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess && h->field_w)
     e = cudaMemcpyAsync(h->wfield, wframe.data(), wframe.size() * 4, cudaMemcpyHostToDevice, s);
   for (int k = 0; k < 2 && e == cudaSuccess; ++k) {

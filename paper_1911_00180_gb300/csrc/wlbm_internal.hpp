@@ -114,6 +114,8 @@ struct WallSeg {
   int table;             // diffuse re-emission table index into rho[]
   float iso;             // isothermal e_eq(T_w) - e_ref (times w_i per direction)
   int wall;              // wall (0..3) whose temperature an isothermal cell takes
+  float spec;            // specularity p of an adiabatic edge (0: diffuse)
+  int mirror;            // mirror table: 0 flips c_x (x walls), 1 flips c_y (y walls)
 };
 constexpr int kMaxSeg = 8;
 struct WallArgs {
@@ -125,6 +127,7 @@ struct WallArgs {
   const uint8_t* codes;  // current parity from the next step's codes
   const float* w;
   const float* rho;      // [8][q] re-emission fractions (0 = collected direction)
+  const int16_t* mirror; // [2][q] direction index with c_x (row 0) or c_y (row 1) flipped
   int tape;              // 1: all planes at `planes` (parity ignored)
   WallSeg seg[kMaxSeg];
 };

@@ -14,7 +14,7 @@ LIB_PATH = os.path.join(PKG, "_lib", "libwlbm.so")
 
 WLBM_OK, WLBM_ERR_INVALID_ARG, WLBM_ERR_UNSTABLE, WLBM_ERR_OOM = 0, 1, 2, 3
 WLBM_ERR_CUDA, WLBM_ERR_TIMEOUT, WLBM_ERR_STATE = 4, 5, 6
-BC_PERIODIC, BC_ISOTHERMAL, BC_ADIABATIC_DIFFUSE = 0, 1, 2
+BC_PERIODIC, BC_ISOTHERMAL, BC_ADIABATIC_DIFFUSE, BC_ADIABATIC_SPECULAR = 0, 1, 2, 3
 STORE_FP32_DEV, STORE_BF16_DEV = 0, 1
 OPT_STEP_VARIANT, OPT_GRAPH_STEPS, OPT_FUSE_PERIODIC = 1, 2, 3
 REDUCE_N = 9          # WLBM_REDUCE_N
@@ -29,7 +29,8 @@ class wlbm_grid(C.Structure):
 
 
 class wlbm_boundary(C.Structure):
-    _fields_ = [("kind", C.c_int32 * 4), ("t_wall", C.c_double * 4)]
+    _fields_ = [("kind", C.c_int32 * 4), ("t_wall", C.c_double * 4),
+                ("specularity", C.c_double * 4)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
@@ -157,14 +158,15 @@ class WormLBM:
     def __init__(self, nx, ny, q, mfp=None, mfp_field=None, bc=(0, 0, 0, 0),
                  t_wall=(300.0,) * 4, storage=STORE_FP32_DEV, emulate_3d=True,
                  relax_mode=0, t_ref=300.0, theta=624.8074248458514, stream=None,
-                 allocator=None):
+                 allocator=None, specularity=(0.0,) * 4):
         import torch
         self._torch = torch
         self.nx, self.ny, self.q = nx, ny, q
         self.device = torch.device("cuda", torch.cuda.current_device())
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         g = wlbm_grid(nx, ny, q, storage, 1 if emulate_3d else 0, relax_mode, t_ref, theta)
-        b = wlbm_boundary((C.c_int32 * 4)(*bc), (C.c_double * 4)(*t_wall))
+        b = wlbm_boundary((C.c_int32 * 4)(*bc), (C.c_double * 4)(*t_wall),
+                          (C.c_double * 4)(*specularity))
         if allocator is None:
             dev, strm = self.device.index, self.stream.cuda_stream
 
@@ -353,7 +355,8 @@ class WormLBMBatch:
             grids[k] = wlbm_grid(sp["nx"], sp["ny"], sp["q"], storage,
                                  1 if sp.get("emulate_3d", True) else 0, sp.get("relax_mode", 0),
                                  t_ref, theta)
-            bcs[k] = wlbm_boundary((C.c_int32 * 4)(*sp["bc"]), (C.c_double * 4)(*sp["t_wall"]))
+            bcs[k] = wlbm_boundary((C.c_int32 * 4)(*sp["bc"]), (C.c_double * 4)(*sp["t_wall"]),
+                                   (C.c_double * 4)(*sp.get("specularity", (0.0,) * 4)))
             if sp.get("mfp_field") is not None:
                 t = torch.as_tensor(sp["mfp_field"], dtype=torch.float32,
                                     device=self.device).contiguous()

@@ -37,12 +37,12 @@ def _case(kinds, nx=26, ny=18, q=16, steps=60, seed=3, field=True):
 
 
 def _gpu(kinds, mfp, dT0, probe, tw, steps, ckpt, q, mfp_uniform=3.0, variant=None,
-         objective="temperature"):
+         objective="temperature", spec=(0.0,) * 4):
     import torch
     import paper_1911_00180_gb300 as wl
     ny, nx = dT0.shape
     h = wl.WormLBM(nx, ny, q, mfp=mfp_uniform if mfp is None else None, mfp_field=mfp,
-                   bc=kinds, t_wall=tw, emulate_3d=True, theta=THETA)
+                   bc=kinds, t_wall=tw, emulate_3d=True, theta=THETA, specularity=spec)
     if variant is not None:
         h.wlbm_set_option(wl.wlbm.OPT_STEP_VARIANT, variant)
     h.wlbm_adjoint_forward(dT0, steps, ckpt)
@@ -62,11 +62,12 @@ def _gpu(kinds, mfp, dT0, probe, tw, steps, ckpt, q, mfp_uniform=3.0, variant=No
     return out
 
 
-def _oracle(kinds, mfp, dT0, probe, tw, steps, q, mfp_uniform=3.0, objective="temperature"):
+def _oracle(kinds, mfp, dT0, probe, tw, steps, q, mfp_uniform=3.0, objective="temperature",
+            spec=(0.0,) * 4):
     ny, nx = dT0.shape
     kw = dict(nx=nx, ny=ny, q=q,
               mfp=(np.full((ny, nx), mfp_uniform) if mfp is None else mfp.astype(np.float64)),
-              bc_kind=kinds, t_wall=tw, emulate_3d=True, theta=THETA)
+              bc_kind=kinds, t_wall=tw, emulate_3d=True, theta=THETA, specularity=spec)
     return A.AdjointRun(kw, dT0.astype(np.float64), steps, probe, objective).gradients()
 
 
@@ -88,6 +89,22 @@ def test_adjoint_gradients_match_oracle(kinds):
     if iso:
         assert _rel(g_tw[iso], ref["dJ_dTwall"][iso]) <= TOL
     assert np.all(g_tw[[k for k in range(4) if kinds[k] != I]] == 0.0)
+
+
+@pytest.mark.parametrize("kinds,spec", [((I, I, 3, D), (0.0, 0.0, 0.0, 0.45)),
+                                       ((D, 3, I, D), (0.7, 0.0, 0.0, 0.0))])
+def test_adjoint_specular_walls_match_oracle(kinds, spec):
+    """Specular and partly specular walls: the transposed wall pass (an outward direction
+    takes p l_mirror + (1 - p) S) against the oracle's transpose."""
+    steps, ckpt, q = 50, 9, 16
+    mfp, dT0, probe, tw = _case(kinds)
+    J, g_mfp, g_tw, g_dT0 = _gpu(kinds, mfp, dT0, probe, tw, steps, ckpt, q, spec=spec)
+    ref = _oracle(kinds, mfp, dT0, probe, tw, steps, q, spec=spec)
+    assert abs(J - ref["J"]) <= 1e-5
+    assert _rel(g_mfp, ref["dJ_dmfp"]) <= TOL
+    assert _rel(g_dT0, ref["dJ_ddT0"]) <= TOL
+    iso = [k for k in range(4) if kinds[k] == I]
+    assert _rel(g_tw[iso], ref["dJ_dTwall"][iso]) <= TOL
 
 
 @pytest.mark.parametrize("kinds", [(I, I, D, D), (I, I, P, P)])

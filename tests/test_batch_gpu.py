@@ -9,7 +9,7 @@ import pytest
 import workloads as W
 
 pytestmark = pytest.mark.gpu
-P, I, A = W.PERIODIC, W.ISOTHERMAL, W.ADIABATIC_DIFFUSE
+P, I, A, S = W.PERIODIC, W.ISOTHERMAL, W.ADIABATIC_DIFFUSE, W.ADIABATIC_SPECULAR
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -28,6 +28,8 @@ def _specs():
         dict(nx=90, ny=17, q=8, bc=(I, I, P, P), t_wall=(300.4, 299.8, 300.0, 300.0),
              mfp_field=W.lognormal_mfp(90, 17, seed=3, corr=4.0)),
         dict(nx=33, ny=260, q=64, bc=(P, P, I, A), t_wall=(300.0, 300.0, 300.7, 300.0), mfp=30.0),
+        dict(nx=70, ny=29, q=40, bc=(A, S, S, A), t_wall=(300.0,) * 4, mfp=5.0,
+             specularity=(0.6, 0.0, 0.0, 0.25)),
     ]
 
 
@@ -35,10 +37,10 @@ def _state(spec, frame):
     """The framed state without the ghost cells of periodic and isothermal sides: those are
     copies or fixed wall values that the boundary passes rewrite before a step reads them
     (before a step, a periodic plane gets only the ghost side its hop pulls from), not
-    state.  Ghost cells of adiabatic-diffuse walls (and corners between two of them) hold
-    energy waiting to re-enter and are kept."""
+    state.  Ghost cells of adiabatic walls (and corners between two of them) hold energy
+    waiting to re-enter and are kept."""
     f = np.array(frame, copy=True)
-    d = [k == A for k in spec["bc"]]            # x-, x+, y-, y+
+    d = [k in (A, S) for k in spec["bc"]]       # x-, x+, y-, y+
     if not d[0]:
         f[:, :, 0] = 0
     if not d[1]:
@@ -61,7 +63,7 @@ def _single(spec, dT, steps, storage, fuse=0, variant=3):
     import paper_1911_00180_gb300 as wl
     h = wl.WormLBM(spec["nx"], spec["ny"], spec["q"], mfp=spec.get("mfp"),
                    mfp_field=spec.get("mfp_field"), bc=spec["bc"], t_wall=spec["t_wall"],
-                   storage=storage)
+                   storage=storage, specularity=spec.get("specularity", (0.0,) * 4))
     h.wlbm_set_option(wl.wlbm.OPT_STEP_VARIANT, variant)
     h.wlbm_set_option(wl.wlbm.OPT_FUSE_PERIODIC, fuse)
     h.wlbm_init_temperature(dT)

@@ -29,7 +29,7 @@ import math
 
 import numpy as np
 
-PERIODIC, ISOTHERMAL, ADIABATIC_DIFFUSE = 0, 1, 2
+PERIODIC, ISOTHERMAL, ADIABATIC_DIFFUSE, ADIABATIC_SPECULAR = 0, 1, 2, 3
 
 
 def _rng(seed):
