@@ -1,0 +1,116 @@
+"""The paper's validation cases on the GPU path against their analytic solutions (the
+oracle's `analytic` module, itself pinned on the CPU): the transient cross-plane Fourier
+profile (Sec. 4.4), the ballistic cross-plane front (Sec. 4.4; exact for the worm
+lattice, and close to the 2D continuum front for Q = 512) and the steady one-hot /
+three-cold square (Sec. 4.6)."""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import analytic as AN
+from oracle import lattice as OL
+from tests._pair import THETA, gpu_handle
+
+pytestmark = pytest.mark.gpu
+P, I = W.PERIODIC, W.ISOTHERMAL
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1911_00180_gb300  # noqa: F401  (fails loudly if the library is missing)
+
+
+def _temperature(h, avg=1):
+    """Mean over `avg` consecutive steps of T - T_ref (the TAS fluctuation, Sec. 4.3)."""
+    acc = 0.0
+    for k in range(avg):
+        if k:
+            h.wlbm_step(1)
+        dT, _, _ = h.wlbm_moments(want_q=False)
+        acc = acc + dT.double().cpu().numpy()
+    return acc / avg
+
+
+def test_cross_plane_fourier_transient():
+    """Hot wall 300.5 K at x = -1, cold 300 K at x = N_x, start at 300 K, periodic y;
+    MFP 16 cells over N_x = 1600 (Kn = 0.01), 3D emulation (D = Lambda / 3).  Theta at the
+    diffusion times s = D t / N_x^2 = 0.02, 0.1, 0.5 against the Fourier series for
+    0.1 <= X <= 0.9, within 0.04, 0.03 and 0.025 (measured 0.031, 0.025 and 0.020, largest
+    next to the hot wall, where its temperature jump sits; 0.2-1.4 % at the centre; the
+    first-order grid-MFP error of D is ~2.5 % at Lambda = 16)."""
+    nx, ny, q, mfp = 1600, 1, 16, 16.0
+    cfg = dict(nx=nx, ny=ny, q=q, mfp=mfp, bc=(I, I, P, P), t_wall=(300.5, 300.0, 300.0, 300.0),
+               emulate_3d=True)
+    h = gpu_handle(cfg)
+    h.wlbm_init_temperature(np.zeros((ny, nx), np.float32))
+    D = mfp / 3.0
+    X = (np.arange(nx) + 0.5) / nx
+    inner = slice(nx // 10, nx - nx // 10)
+    done = 0
+    for s, tol in ((0.02, 0.04), (0.1, 0.03), (0.5, 0.025)):
+        n = int(round(s * nx * nx / D))
+        h.wlbm_step(n - done)
+        done = n
+        theta = _temperature(h, 10)[0] / 0.5
+        done += 9
+        want = AN.cross_plane_fourier(X, D * done / nx ** 2)
+        err = float(np.abs(theta - want)[inner].max())
+        assert err <= tol, (s, err)
+    h.close()
+
+
+def test_cross_plane_ballistic_front():
+    """W = 0 (infinite MFP), Q = 512, N_x = 510, N_y = 1 (the paper's ballistic case):
+    the GPU field equals the worm lattice's exact front from the TAS displacements, and
+    that front follows the 2D continuum front e_0 + (arccos(x / t) / pi)(e_w - e_0)."""
+    nx, q = 510, 512
+    cfg = dict(nx=nx, ny=1, q=q, mfp=math.inf, bc=(I, I, P, P),
+               t_wall=(300.5, 300.0, 300.0, 300.0), emulate_3d=True)
+    h = gpu_handle(cfg)
+    h.wlbm_init_temperature(np.zeros((1, nx), np.float32))
+    e_ref = 1.0 / math.expm1(THETA / 300.0)
+    de_w = 1.0 / math.expm1(THETA / 300.5) - e_ref
+    done = 0
+    for n in (100, 300):
+        h.wlbm_step(n - done)
+        done = n
+        got = _temperature(h)[0]
+        de = AN.ballistic_cross_plane_worm(q, n, nx, de_w)
+        want = OL.temperature(e_ref + de, THETA) - 300.0
+        assert float(np.abs(got - want).max()) <= 1e-5 * 0.5, n
+        x = np.arange(nx) + 1.0                      # distance from the wall's ghost cell
+        cont = AN.ballistic_cross_plane_2d(x, float(n), de_w, 0.0)
+        assert float(np.abs(de - cont).max()) <= 0.06 * de_w, n
+    h.close()
+
+
+def test_one_hot_three_cold_steady():
+    """Isothermal walls, hot (300.5 K) at y = N_y and cold (299.5 K) elsewhere, MFP 8 cells
+    on 512 x 512 (Kn = 0.016, about the paper's cells per MFP), 12 decay times of the
+    slowest mode from 299.5 K: Theta along Y = 0.5 and 0.75 within 0.025 of the steady
+    Fourier solution for 0.1 <= X <= 0.9 (measured 0.018 and 0.017, +0.8 % at the
+    centre).  The steady profile does not depend on D; the
+    walls' temperature jump is first order in 1/Lambda (measured at Lambda = 2.56 cells:
+    ~4.4 % of Delta T next to every wall and +2.3 % at the centre, for N = 256 and 512
+    alike; half that at Lambda = 5.12)."""
+    n, q, mfp = 512, 16, 8.0
+    cfg = dict(nx=n, ny=n, q=q, mfp=mfp, bc=(I, I, I, I),
+               t_wall=(299.5, 299.5, 299.5, 300.5), emulate_3d=True)
+    h = gpu_handle(cfg)
+    h.wlbm_init_temperature(np.full((n, n), -0.5, np.float32))
+    tau = n * n / (2 * math.pi ** 2 * (mfp / 3.0))
+    h.wlbm_step(int(12 * tau))
+    theta = (_temperature(h, 10) + 0.5) / 1.0
+    h.close()
+    X = (np.arange(n) + 0.5) / n
+    inner = slice(n // 10, n - n // 10)
+    for Yc in (0.5, 0.75):
+        row = int(round(Yc * n - 0.5))
+        want = AN.one_hot_three_cold(X, (row + 0.5) / n)
+        err = float(np.abs(theta[row] - want)[inner].max())
+        assert err <= 0.025, (Yc, err)
