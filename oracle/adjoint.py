@@ -184,9 +184,9 @@ class AdjointRun:
         J = self.objective(m)
         lam = np.zeros_like(m.d)
         if self.objective_kind == "flux_x":
-            # q_x(x) = sum_i s_ix d_i(x): dJ/dd_i(x) = s_ix over the probe cells
+            # q_x(x) = v sum_i s_ix d_i(x): dJ/dd_i(x) = v s_ix over the probe cells
             g = self.probe / self.probe.sum()
-            lam[:, 1:-1, 1:-1] = m.s_hat[:, 0][:, None, None] * g[None]
+            lam[:, 1:-1, 1:-1] = m.speed * m.s_hat[:, 0][:, None, None] * g[None]
         else:
             e_abs = m.e_ref + m.energy_dev()
             g = np.where(self.probe, dT_dE(e_abs, m.theta), 0.0) / self.probe.sum()
@@ -210,6 +210,9 @@ class AdjointRun:
         out = dict(J=J, dJ_dWcorr=g_wc, dJ_dTwall=g_t, dJ_ddT0=g_dT0)
         if self.kw.get("w_field") is None:
             mfp = np.broadcast_to(np.asarray(self.kw["mfp"], np.float64), (m.ny, m.nx))
-            out["dJ_dmfp"] = g_wc * dwcorr_dmfp(mfp, m.lam_corr, self.kw.get("emulate_3d", True),
-                                                self.kw.get("relax_mode", 0))
+            # W = speed / MFP: the weight is a function of MFP / speed
+            v = m.speed
+            out["dJ_dmfp"] = g_wc * dwcorr_dmfp(mfp / v, m.lam_corr,
+                                                self.kw.get("emulate_3d", True),
+                                                self.kw.get("relax_mode", 0)) / v
         return out

@@ -160,15 +160,23 @@ def temperature(e, theta):
 class TasSchedule:
     """Eq. algorithm + worm paths: per-direction displacement p_i, executed-hop counter
     h_i.  ``advance(n)`` performs step n (n = 1, 2, ...) and returns, for every direction,
-    the due basic hop index and whether the DDED is paused at this step."""
+    the due basic hop index and whether the DDED is paused at this step.
 
-    def __init__(self, q):
+    speed v in (0, 1]: the propagation speed in cells per step (the TAS extended to other
+    speeds, Sec. 1): the axial reference distance after step n is v n, so the hop test
+    reads |p + c|^2 <= (v n + 1)^2, evaluated in float64 as written (v = 1 gives the exact
+    integer test of the unit speed)."""
+
+    def __init__(self, q, speed=1.0):
         self.dirs = ring_directions(q)
         self.paths = worm_table(self.dirs)
         self.m = q // 8
         self.p = [[0, 0] for _ in range(q)]
         self.h = [0] * q
         self.n = 0
+        self.speed = float(speed)
+        if not (0.0 < self.speed <= 1.0):
+            raise ValueError("speed must lie in (0, 1]")
 
     def advance(self, n=None):
         n = self.n + 1 if n is None else n
@@ -178,7 +186,8 @@ class TasSchedule:
             k = self.paths[i][self.h[i] % self.m]
             cx, cy = BASIC_HOPS[k]
             nx_, ny_ = self.p[i][0] + cx, self.p[i][1] + cy
-            if nx_ * nx_ + ny_ * ny_ <= (n + 1) * (n + 1):
+            r = self.speed * n + 1.0
+            if nx_ * nx_ + ny_ * ny_ <= r * r:
                 self.p[i] = [nx_, ny_]
                 self.h[i] += 1
                 paused.append(False)

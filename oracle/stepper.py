@@ -42,7 +42,11 @@ Readings of passages the paper leaves open (each is also listed in the design doc):
     then an isothermal y-wall, decides; two adiabatic walls (diffuse or specular) use the
     diffuse corner rule above (a specular corner would map up to three directions onto
     one);
-  * heat flux (Eq. q_corr) uses the nominal unit vector s_i of each direction, v_g = 1.
+  * heat flux (Eq. q_corr) uses the nominal unit vector s_i of each direction and
+    v_g = the propagation speed (1 cell per step unless a band is slower);
+  * propagation speed v <= 1 (TAS beyond the unit speed, Sec. 1; one band of a multigray
+    run, Sec. 2.1): the hop test compares with v n instead of n, and the relaxation per
+    step is W = v / MFP before Eq. W-correction.
 
 Pins: tests/test_oracle_stepper.py (energy conservation on periodic and adiabatic
 grids, exact ballistic translation, reduction to standard D2Q8 at W = 1, the moment
@@ -78,8 +82,11 @@ class WormLBM:
 
     def __init__(self, nx, ny, q, mfp, bc_kind=(0, 0, 0, 0), t_wall=(300.0,) * 4,
                  emulate_3d=True, relax_mode=0, t_ref=300.0, theta=L.THETA_DEFAULT,
-                 w_field=None, specularity=(0.0,) * 4):
+                 w_field=None, specularity=(0.0,) * 4, speed=1.0):
         self.nx, self.ny, self.q = nx, ny, q
+        # propagation speed in cells per step (TAS beyond the unit speed, Sec. 1): one
+        # band of a multigray run; its relaxation per step is W = speed / MFP
+        self.speed = float(speed)
         self.bc_kind = tuple(int(k) for k in bc_kind)
         self.t_wall = tuple(float(t) for t in t_wall)
         # specularity of each adiabatic wall: 1 for specular walls, the given fraction
@@ -97,7 +104,7 @@ class WormLBM:
         self.s_hat = L.unit_vectors(self.dirs)
         self.w = L.angular_weights(self.dirs)
         self.lam_corr = L.lambda_corr(self.dirs)
-        self.sched = L.TasSchedule(q)
+        self.sched = L.TasSchedule(q, self.speed)
         self.e_ref = float(L.e_eq(self.t_ref, self.theta))
         if w_field is not None:            # direct W (tests of the W = 1 limit, adjoint)
             wc = np.broadcast_to(np.asarray(w_field, np.float64), (ny, nx)).copy()
@@ -105,7 +112,7 @@ class WormLBM:
             mfp = np.broadcast_to(np.asarray(mfp, np.float64), (ny, nx))
             if np.any(mfp <= 0):
                 raise ValueError("MFP must be positive")
-            wc = L.relax_weight(mfp, self.lam_corr, emulate_3d, relax_mode)
+            wc = L.relax_weight(mfp / self.speed, self.lam_corr, emulate_3d, relax_mode)
         if wc.max() > 1.0:
             # Appendix A: the paused step is stable only for W <= 1.
             raise ValueError("unstable: max W_corr = %g > 1" % wc.max())
@@ -277,10 +284,12 @@ class WormLBM:
         return L.temperature(e, self.theta) - self.t_ref
 
     def heat_flux(self):
-        """(q_x, q_y) by Eq. q_corr with v_g = 1 and c_i/|c_i| = s_i."""
+        """(q_x, q_y) by Eq. q_corr with v_g = speed (1 by default) and c_i/|c_i| = s_i."""
         di = self.d[:, 1:-1, 1:-1]
         qx = np.tensordot(self.s_hat[:, 0], di, axes=(0, 0))
         qy = np.tensordot(self.s_hat[:, 1], di, axes=(0, 0))
+        if self.speed != 1.0:
+            qx, qy = self.speed * qx, self.speed * qy
         return qx, qy
 
     def total_energy(self, include_frame=False):

@@ -45,9 +45,9 @@ from . import lattice as L
 from .stepper import ISOTHERMAL, XM, XP
 
 
-def bulk_diffusivity(mfp, emulate_3d=True):
-    """D = v_g Lambda / 3 (3D) or v_g Lambda / 2 (2D), lattice units."""
-    return float(mfp) / (3.0 if emulate_3d else 2.0)
+def bulk_diffusivity(mfp, emulate_3d=True, speed=1.0):
+    """D = v_g Lambda / 3 (3D) or v_g Lambda / 2 (2D), lattice units (v_g = speed)."""
+    return float(speed) * float(mfp) / (3.0 if emulate_3d else 2.0)
 
 
 def band_columns(nx):
@@ -79,7 +79,7 @@ def kappa_apparent(m, mfp, emulate_3d=True):
         return float("nan")
     de = float(L.e_eq(m.t_wall[XM], m.theta) - L.e_eq(m.t_wall[XP], m.theta))
     qx, _ = m.heat_flux()
-    return float(qx.mean()) * m.nx / (bulk_diffusivity(mfp, emulate_3d) * de)
+    return float(qx.mean()) * m.nx / (bulk_diffusivity(mfp, emulate_3d, m.speed) * de)
 
 
 def kappa_band(m, mfp, emulate_3d=True):
@@ -87,7 +87,7 @@ def kappa_band(m, mfp, emulate_3d=True):
     q_band, slope = band_flux_and_slope(m)
     if not (slope != 0.0):
         return float("nan")
-    return q_band / (-bulk_diffusivity(mfp, emulate_3d) * slope)
+    return q_band / (-bulk_diffusivity(mfp, emulate_3d, m.speed) * slope)
 
 
 def temperature_residual(dT_now, dT_then, steps):
@@ -149,7 +149,7 @@ def run_steady(m, max_steps, check_every, tol, avg_steps, mfp, emulate_3d=True):
         conv = residual <= tol
         means = tuple(float(np.mean([v[k] for v in vals])) for k in range(4))
     qx_m, qy_m, qb, slope = means
-    d = bulk_diffusivity(mfp, emulate_3d)
+    d = bulk_diffusivity(mfp, emulate_3d, m.speed)
     k = m.bc_kind
     if k[XM] == ISOTHERMAL and k[XP] == ISOTHERMAL and m.t_wall[XM] != m.t_wall[XP]:
         de = float(L.e_eq(m.t_wall[XM], m.theta) - L.e_eq(m.t_wall[XP], m.theta))

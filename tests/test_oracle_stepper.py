@@ -93,14 +93,14 @@ def test_w_equal_one_reduces_to_standard_d2q8():
         assert np.allclose(m.energy_dev(), e, rtol=0, atol=1e-15)
 
 
-def _moment_recursion(q, w_uniform, steps, m0, m1x, m1y, m2x):
+def _moment_recursion(q, w_uniform, steps, m0, m1x, m1y, m2x, speed=1.0):
     """Per-direction spatial moments propagated in moment space: sum_x d_i, sum_x x d_i,
     sum_x y d_i, sum_x x^2 d_i.  Translation by c shifts moments; scattering mixes
     directions through the totals.  Independent of the field code."""
     dirs = L.ring_directions(q)
     w = L.angular_weights(dirs)
     W = w_uniform
-    sched = L.TasSchedule(q)
+    sched = L.TasSchedule(q, speed)
     out = []
     for n in range(1, steps + 1):
         hops, paused = sched.advance(n)
@@ -147,12 +147,12 @@ def test_field_step_matches_moment_recursion():
             assert np.allclose(a, b, rtol=1e-11, atol=1e-9)
 
 
-def _diffusivity(q, mfp, emulate_3d, steps):
+def _diffusivity(q, mfp, emulate_3d, steps, speed=1.0):
     dirs = L.ring_directions(q)
-    W = float(L.relax_weight(mfp, L.lambda_corr(dirs), emulate_3d))
+    W = float(L.relax_weight(mfp / speed, L.lambda_corr(dirs), emulate_3d))
     w = L.angular_weights(dirs)
     z = np.zeros(q)
-    hist = _moment_recursion(q, W, steps, w.copy(), z.copy(), z.copy(), z.copy())
+    hist = _moment_recursion(q, W, steps, w.copy(), z.copy(), z.copy(), z.copy(), speed)
 
     def var(t):
         m0, m1x, _, m2x = hist[t]
@@ -228,3 +228,37 @@ def test_specular_mirror_and_zero_specularity():
         z.init_temperature(_rand(9, 13, 4))
         z.step(30)
     assert np.array_equal(x.d, y.d)
+
+
+@pytest.mark.parametrize("speed", [0.5, 0.3])
+def test_tas_at_lower_speed_keeps_every_direction_within_one_cell(speed):
+    """TAS beyond the unit speed (Sec. 1): with the reference distance v n every direction
+    stays within one cell of v n along its ray (the unit-speed bound of Sec. 3.1 carried
+    over), and now the axial directions pause too, at the rate 1 - v."""
+    q = 32
+    sched = L.TasSchedule(q, speed)
+    dirs = np.array(L.ring_directions(q), np.float64)
+    u = dirs / np.linalg.norm(dirs, axis=1)[:, None]
+    axial_pauses = 0
+    steps = 400
+    for n in range(1, steps + 1):
+        _, paused = sched.advance(n)
+        axial_pauses += sum(paused[i] for i in (0, q // 4, q // 2, 3 * q // 4))
+        p = sched.displacement().astype(np.float64)
+        along = (p * u).sum(axis=1)
+        across = p[:, 0] * u[:, 1] - p[:, 1] * u[:, 0]
+        assert np.all(np.abs(along - speed * n) <= 1.0 + 1e-12)
+        assert np.all(np.abs(across) <= 1.0 + 1e-12)
+    assert axial_pauses / (4 * steps) == pytest.approx(1 - speed, abs=0.01)
+
+
+@pytest.mark.parametrize("speed", [0.5, 0.25])
+def test_diffusive_limit_at_lower_speed(speed):
+    """A band with speed v relaxes with W = v / Lambda per step and diffuses with
+    D = v Lambda / 3 (3D emulation), up to a first-order error in 1/Lambda."""
+    d16 = _diffusivity(16, 16.0, True, int(1400 / speed), speed)
+    d32 = _diffusivity(16, 32.0, True, int(2400 / speed), speed)
+    assert (d32 - d16) / 16.0 == pytest.approx(speed / 3.0, rel=0.01)
+    e16 = d16 / (16 * speed / 3) - 1
+    e32 = d32 / (32 * speed / 3) - 1
+    assert 0.3 < e32 / e16 < 0.7                       # first order in 1/Lambda
