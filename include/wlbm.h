@@ -62,6 +62,11 @@ typedef struct wlbm_grid {
                           1 - exp(-W_corr), stable for MFP < 1 cell (not in the paper)  */
   double t_ref;        /* reference temperature, K (e.g. 300)                          */
   double theta;        /* hbar omega0 / k_B, K (624.8 for the paper's 81.8e12 rad/s)   */
+  double speed;        /* propagation speed v in (0, 1] cells per step (0 means 1): the
+                          TAS extended beyond the unit speed (Sec. 1) for one band of a
+                          multigray run (Sec. 2.1).  The hop test of Eq. algorithm uses
+                          v n in place of n, the relaxation per step is W = v / MFP
+                          before Eq. W-correction, and the heat flux carries v_g = v.     */
 } wlbm_grid;
 
 /* Adiabatic walls (Sec. 2.6).  A ghost cell of a wall with specularity p in [0, 1] (1 for
@@ -349,9 +354,10 @@ wlbm_status wlbm_batch_autotune(wlbm_batch* b, int32_t trial_steps, int32_t* var
 wlbm_status wlbm_lattice(int32_t q, int32_t* dirs, double* weights, int8_t* worm,
                          double* lam_corr);
 
-/* wlbm_schedule: the TAS schedule (Eq. algorithm) of steps 1..n_steps: host
- * uint8[n_steps*Q]; entry [t][i] = hop index (bits 0-2) | paused << 3. */
-wlbm_status wlbm_schedule(int32_t q, int64_t n_steps, uint8_t* codes);
+/* wlbm_schedule: the TAS schedule (Eq. algorithm) of steps 1..n_steps at propagation
+ * speed v (wlbm_grid.speed; 0 means 1): host uint8[n_steps*Q]; entry [t][i] = hop index
+ * (bits 0-2) | paused << 3. */
+wlbm_status wlbm_schedule(int32_t q, int64_t n_steps, double speed, uint8_t* codes);
 
 #ifdef __cplusplus
 }

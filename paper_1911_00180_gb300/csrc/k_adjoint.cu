@@ -314,9 +314,9 @@ __global__ void __launch_bounds__(32 * kWallWarpsT) k_walls_T(const WallArgs wa,
 }
 
 // l^N_i(x) = dJ/dT(x) * dT/dE at the final local energy (E = sum_i d_i, Eq. pseudo-T)
-// + dJ/dq_x(x) s_ix + dJ/dq_y(x) s_iy (q = sum_i d_i s_i, Eq. q_corr); NULL seeds are 0.
+// + v (dJ/dq_x(x) s_ix + dJ/dq_y(x) s_iy) (q = v sum_i d_i s_i, Eq. q_corr); NULL seeds are 0.
 __global__ void k_adj_seed(const AdjArgs a, const float* dJ_dT, const float* dJ_dqx,
-                           const float* dJ_dqy, const float* sx, const float* sy,
+                           const float* dJ_dqy, const float* sx, const float* sy, float vg,
                            const float* e_final, double e_ref, double theta) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= a.nx * a.ny) return;
@@ -328,7 +328,8 @@ __global__ void k_adj_seed(const AdjArgs a, const float* dJ_dT, const float* dJ_
     const double lg = log1p(1.0 / e);
     g = float(double(dJ_dT[t]) * theta / (lg * lg * e * (1.0 + e)));
   }
-  const float gx = dJ_dqx ? dJ_dqx[t] : 0.f, gy = dJ_dqy ? dJ_dqy[t] : 0.f;
+  // q = v_g sum_i d_i s_i (Eq. q_corr)
+  const float gx = dJ_dqx ? dJ_dqx[t] * vg : 0.f, gy = dJ_dqy ? dJ_dqy[t] * vg : 0.f;
   for (int i = 0; i < a.q; ++i)
     a.lam_out[int64_t(i) * a.plane + off] = fmaf(gy, sy[i], fmaf(gx, sx[i], g));
 }
@@ -396,10 +397,10 @@ cudaError_t launch_walls_T(const WallArgs& wa, float* lam, double* gtw, cudaStre
 }
 
 cudaError_t launch_adj_seed(const AdjArgs& a, const float* dJ_dT, const float* dJ_dqx,
-                            const float* dJ_dqy, const float* sx, const float* sy,
+                            const float* dJ_dqy, const float* sx, const float* sy, float vg,
                             const float* e_final, double e_ref, double theta, cudaStream_t s) {
   k_adj_seed<<<nblk(int64_t(a.nx) * a.ny, 256), 256, 0, s>>>(a, dJ_dT, dJ_dqx, dJ_dqy, sx, sy,
-                                                              e_final, e_ref, theta);
+                                                              vg, e_final, e_ref, theta);
   return cudaGetLastError();
 }
 

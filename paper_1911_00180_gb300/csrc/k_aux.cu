@@ -433,8 +433,8 @@ __global__ void k_moments(const MomentArgs a) {
       qx = fmaf(v, a.sx[i], qx);
       qy = fmaf(v, a.sy[i], qy);
     }
-    if (a.qx) a.qx[t] = qx;
-    if (a.qy) a.qy[t] = qy;
+    if (a.qx) a.qx[t] = qx * a.vg;
+    if (a.qy) a.qy[t] = qy * a.vg;
   }
 }
 

@@ -95,10 +95,16 @@ void TasState::reset(int q) {
 void tas_advance(const Lattice& L, TasState* st, uint8_t* codes) {
   const int64_t n = st->n + 1;
   const int64_t lim = (n + 1) * (n + 1);
+  // below the unit speed the reference distance is v n: |p + c|^2 <= (v n + 1)^2 in
+  // float64, two roundings (v n, + 1) and the square (host code is built without
+  // contraction into fused multiply-adds)
+  const bool unit = L.speed == 1.0;
+  const double r = L.speed * double(n) + 1.0;
+  const double r2 = r * r;
   for (int i = 0; i < L.q; ++i) {
     const int k = L.worm[size_t(i) * L.m + size_t(st->h[i] % L.m)];
     const int64_t x = st->px[i] + kHopX[k], y = st->py[i] + kHopY[k];
-    const bool hop = x * x + y * y <= lim;
+    const bool hop = unit ? x * x + y * y <= lim : double(x * x + y * y) <= r2;
     codes[i] = uint8_t(k | (hop ? 0 : 8) | (st->parity[i] << 4));
     if (hop) {
       st->px[i] = x;

@@ -16,6 +16,7 @@ struct Lattice {
   std::vector<double> w;              // angular weights, Eq. weight
   std::vector<int8_t> worm;           // [q][m] basic-hop index per worm sub-step
   double lam_corr = 0.0;              // Eq. W-correction-factor-generalized
+  double speed = 1.0;                 // propagation speed v in (0, 1], cells per step
 };
 
 // Returns false if q is not a multiple of 8 in [8, 1024].

@@ -328,12 +328,15 @@ wlbm_status wlbm_lattice(int32_t q, int32_t* dirs, double* weights, int8_t* worm
   return WLBM_OK;
 }
 
-wlbm_status wlbm_schedule(int32_t q, int64_t n_steps, uint8_t* codes) {
+wlbm_status wlbm_schedule(int32_t q, int64_t n_steps, double speed, uint8_t* codes) {
   Lattice L;
-  if (!build_lattice(q, &L) || n_steps < 0 || (n_steps > 0 && !codes)) {
-    set_global_error("wlbm_schedule: invalid Q, step count or output");
+  if (speed == 0.0) speed = 1.0;
+  if (!build_lattice(q, &L) || n_steps < 0 || (n_steps > 0 && !codes) ||
+      !(speed > 0.0 && speed <= 1.0)) {
+    set_global_error("wlbm_schedule: invalid Q, step count, speed or output");
     return WLBM_ERR_INVALID_ARG;
   }
+  L.speed = speed;
   TasState st;
   st.reset(q);
   for (int64_t t = 0; t < n_steps; ++t) {
@@ -354,10 +357,13 @@ wlbm_status wlbm_create(const wlbm_grid* grid, const float* mfp_cells, double mf
   const wlbm_grid& G = *grid;
   if (G.nx < 1 || G.ny < 1 || int64_t(G.nx) * G.ny > (int64_t(1) << 31) ||
       (G.storage != WLBM_STORE_FP32_DEV && G.storage != WLBM_STORE_BF16_DEV) ||
-      (G.relax_mode != 0 && G.relax_mode != 1) || !(G.t_ref > 0) || !(G.theta > 0)) {
-    set_global_error("wlbm_create: invalid grid (sizes, storage, relax_mode, t_ref, theta)");
+      (G.relax_mode != 0 && G.relax_mode != 1) || !(G.t_ref > 0) || !(G.theta > 0) ||
+      !(G.speed == 0.0 || (G.speed > 0.0 && G.speed <= 1.0))) {
+    set_global_error("wlbm_create: invalid grid (sizes, storage, relax_mode, t_ref, theta, "
+                     "speed)");
     return WLBM_ERR_INVALID_ARG;
   }
+  const double speed = G.speed == 0.0 ? 1.0 : G.speed;
   for (int k = 0; k < 4; ++k) {
     if (bc->kind[k] < 0 || bc->kind[k] > 3 ||
         (bc->kind[k] == WLBM_BC_ISOTHERMAL && !(bc->t_wall[k] > 0)) ||
@@ -394,6 +400,7 @@ wlbm_status wlbm_create(const wlbm_grid* grid, const float* mfp_cells, double mf
     set_global_error("wlbm_create: Q must be a multiple of 8 in [8, 1024]");
     return WLBM_ERR_INVALID_ARG;
   }
+  h->lat.speed = speed;
   h->tas.reset(G.q);
   Geom& g = h->g;
   g.nx = G.nx; g.ny = G.ny; g.q = G.q;
@@ -425,7 +432,8 @@ wlbm_status wlbm_create(const wlbm_grid* grid, const float* mfp_cells, double mf
       for (int x = 0; x < G.nx; ++x) {
         const double m = mfp[size_t(y) * G.nx + x];
         if (!(m > 0)) return bad(WLBM_ERR_INVALID_ARG, "wlbm_create: MFP must be positive");
-        const double wc = corrected_weight(m, h->lat.lam_corr, h->emulate_3d, h->relax_mode);
+        const double wc = corrected_weight(m / speed, h->lat.lam_corr, h->emulate_3d,
+                                           h->relax_mode);
         wmax = std::max(wmax, wc);
         wframe[size_t(g.cell(x, y))] = float(wc);
       }
@@ -446,7 +454,8 @@ wlbm_status wlbm_create(const wlbm_grid* grid, const float* mfp_cells, double mf
   } else {
     if (!(mfp_uniform > 0))
       return bad(WLBM_ERR_INVALID_ARG, "wlbm_create: MFP must be positive");
-    const double wc = corrected_weight(mfp_uniform, h->lat.lam_corr, h->emulate_3d, h->relax_mode);
+    const double wc = corrected_weight(mfp_uniform / speed, h->lat.lam_corr, h->emulate_3d,
+                                       h->relax_mode);
     if (wc > 1.0)
       return bad(WLBM_ERR_UNSTABLE, "wlbm_create: W_corr > 1, unstable (use a larger MFP)");
     h->w0 = float(wc);
@@ -782,6 +791,7 @@ wlbm_status wlbm_moments(wlbm_handle* h, float* dT, float* qx, float* qy) {
   a.q = g.q; a.par = h->parity_mask(); a.e_cur = h->e[h->e_cur]; a.e_refp = h->ref_plane();
   a.w = h->w_dev(); a.sx = h->sx_dev(); a.sy = h->sy_dev(); a.dT = dT; a.qx = qx; a.qy = qy;
   a.scale = h->scale;
+  a.vg = float(h->lat.speed);
   a.e_ref = float(h->e_eq_ref);
   a.e_ref1 = float(h->e_eq_ref + 1.0);
   a.l_ref = float(std::log1p(1.0 / h->e_eq_ref));
@@ -794,7 +804,8 @@ wlbm_status wlbm_moments(wlbm_handle* h, float* dT, float* qx, float* qy) {
 static void reduce_conductivities(const wlbm_handle* h, double* out) {
   const double nan = std::numeric_limits<double>::quiet_NaN();
   // bulk diffusivity v_g Lambda / 3 (3D emulation) or / 2; defined for a uniform MFP only
-  const double D = h->field_w ? nan : h->mfp_uniform / (h->emulate_3d ? 3.0 : 2.0);
+  const double D =
+      h->field_w ? nan : h->lat.speed * h->mfp_uniform / (h->emulate_3d ? 3.0 : 2.0);
   const bool iso_x = h->bc_kind[0] == WLBM_BC_ISOTHERMAL && h->bc_kind[1] == WLBM_BC_ISOTHERMAL &&
                      h->t_wall[0] != h->t_wall[1];
   out[6] = iso_x ? out[2] * h->g.nx / (D * (h->delta_e(h->t_wall[0]) - h->delta_e(h->t_wall[1])))
@@ -849,11 +860,12 @@ static wlbm_status reduce_impl(wlbm_handle* h, double* out, const WindowCtl* win
   const double nan = std::numeric_limits<double>::quiet_NaN();
   const double cells = double(g.nx) * g.ny;
   const double bw = a.band_w;
+  const double vg = h->lat.speed;        // Eq. q_corr: q = v_g sum_i e_i s_i
   out[0] = tmp[0];
   out[1] = tmp[1];
-  out[2] = tmp[2] / cells;
-  out[3] = tmp[3] / cells;
-  out[4] = a.band_w >= 1 ? tmp[4] / (bw * g.ny) : nan;
+  out[2] = vg * tmp[2] / cells;
+  out[3] = vg * tmp[3] / cells;
+  out[4] = a.band_w >= 1 ? vg * tmp[4] / (bw * g.ny) : nan;
   // least-squares slope of the y-averaged E over the band: sum (x - xbar)^2 = w (w^2 - 1) / 12
   out[5] = a.band_w >= 2 ? tmp[5] / (double(g.ny) * bw * (bw * bw - 1.0) / 12.0) : nan;
   reduce_conductivities(h, out);
@@ -1151,16 +1163,17 @@ wlbm_status wlbm_adjoint_forward(wlbm_handle* h, const float* dT0, int64_t n_ste
   if (!(A.n == n_steps && A.k == ckpt_every && A.ckpt)) st = adj_alloc(h, n_steps, ckpt_every);
   if (st != WLBM_OK) return st;
   A.ready = false;
-  // dW_corr/dMFP per interior cell (Eq. W-correction with W = 1/MFP)
+  // dW_corr/dMFP per interior cell (Eq. W-correction with W = v/MFP: a function of
+  // m = MFP/v, so dW_corr/dMFP = (dW_corr/dm) / v)
   std::vector<float> dwc(size_t(g.nx) * g.ny);
-  const double f = h->emulate_3d ? 1.5 : 1.0, lc = h->lat.lam_corr;
+  const double f = h->emulate_3d ? 1.5 : 1.0, lc = h->lat.lam_corr, v = h->lat.speed;
   for (size_t c = 0; c < dwc.size(); ++c) {
-    const double m = h->field_w ? double(h->mfp_host[c]) : h->mfp_uniform;
+    const double m = (h->field_w ? double(h->mfp_host[c]) : h->mfp_uniform) / v;
     if (std::isinf(m)) { dwc[c] = 0.f; continue; }
     const double W = 1.0 / m;
     double d = -f * (1.0 + 2.0 * W * (lc - 1.0)) / (m * m);
     if (h->relax_mode == 1) d *= std::exp(-f * (W + W * W * (lc - 1.0)));
-    dwc[c] = float(d);
+    dwc[c] = float(d / v);
   }
   std::vector<uint8_t> codes(size_t(n_steps) * g.q);
   std::vector<uint16_t> order(size_t(n_steps) * (g.q + 17));
@@ -1246,8 +1259,8 @@ wlbm_status wlbm_adjoint_backward(wlbm_handle* h, const float* dJ_dT, const floa
     else aa.iso_side[top ? 3 : 2] = sg.wall;
   }
   aa.lam_out = A.lam[0];
-  ok(launch_adj_seed(aa, dJ_dT, dJ_dqx, dJ_dqy, h->sx_dev(), h->sy_dev(), h->e[h->e_cur],
-                     h->e_eq_ref, h->theta, s),
+  ok(launch_adj_seed(aa, dJ_dT, dJ_dqx, dJ_dqy, h->sx_dev(), h->sy_dev(), float(h->lat.speed),
+                     h->e[h->e_cur], h->e_eq_ref, h->theta, s),
      "adjoint: seed");
   int cur = 0;
   for (int c = A.nck - 1; c >= 0 && st == WLBM_OK; --c) {

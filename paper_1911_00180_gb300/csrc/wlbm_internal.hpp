@@ -205,6 +205,7 @@ struct MomentArgs {
   float* qx;
   float* qy;
   float scale;
+  float vg;              // propagation speed: q = v_g sum_i e_i s_i (Eq. q_corr)
   float e_ref, e_ref1, l_ref, theta;   // e_ref, e_ref + 1, ln(1 + 1/e_ref), theta
 };
 
@@ -380,7 +381,7 @@ cudaError_t launch_periodic_T(float* planes, int64_t plane, int pitch, int nx, i
 // transpose of the other axis may have added corner images) are transposed again.
 cudaError_t launch_walls_T(const WallArgs& wa, float* lam, double* gtw, cudaStream_t s);
 cudaError_t launch_adj_seed(const AdjArgs& a, const float* dJ_dT, const float* dJ_dqx,
-                            const float* dJ_dqy, const float* sx, const float* sy,
+                            const float* dJ_dqy, const float* sx, const float* sy, float vg,
                             const float* e_final, double e_ref, double theta, cudaStream_t s);
 cudaError_t launch_adj_final(const AdjArgs& a, const float* dwc, float* dJ_dmfp,
                              const float* lam0, const float* s0, const float* dT0,

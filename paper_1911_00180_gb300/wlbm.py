@@ -25,7 +25,8 @@ STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "UNSTABLE", 3: "OOM", 4: "CUDA", 5
 class wlbm_grid(C.Structure):
     _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("q", C.c_int32),
                 ("storage", C.c_int32), ("emulate_3d", C.c_int32),
-                ("relax_mode", C.c_int32), ("t_ref", C.c_double), ("theta", C.c_double)]
+                ("relax_mode", C.c_int32), ("t_ref", C.c_double), ("theta", C.c_double),
+                ("speed", C.c_double)]
 
 
 class wlbm_boundary(C.Structure):
@@ -97,7 +98,7 @@ def _load():
         "wlbm_reduce_state_noalloc": (C.c_int, [vp, i32, i32, i32, C.POINTER(i32), vp, vp]),
         "wlbm_lattice": (C.c_int, [i32, C.POINTER(i32), C.POINTER(dbl), C.POINTER(C.c_int8),
                                    C.POINTER(dbl)]),
-        "wlbm_schedule": (C.c_int, [i32, i64, C.POINTER(C.c_uint8)]),
+        "wlbm_schedule": (C.c_int, [i32, i64, dbl, C.POINTER(C.c_uint8)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -134,11 +135,13 @@ def wlbm_lattice(q):
     return dirs.reshape(q, 2), w, worm.reshape(q, q // 8), lam.value
 
 
-def wlbm_schedule(q, n_steps):
-    """TAS codes (n_steps, Q) uint8: hop index | paused << 3 (Eq. algorithm)."""
+def wlbm_schedule(q, n_steps, speed=1.0):
+    """TAS codes (n_steps, Q) uint8: hop index | paused << 3 (Eq. algorithm) at the given
+    propagation speed."""
     import numpy as np
     out = np.zeros(max(n_steps, 1) * q, np.uint8)
-    _check(lib.wlbm_schedule(q, n_steps, out.ctypes.data_as(C.POINTER(C.c_uint8))))
+    _check(lib.wlbm_schedule(q, n_steps, float(speed),
+                             out.ctypes.data_as(C.POINTER(C.c_uint8))))
     return out[:n_steps * q].reshape(n_steps, q)
 
 
@@ -158,13 +161,14 @@ class WormLBM:
     def __init__(self, nx, ny, q, mfp=None, mfp_field=None, bc=(0, 0, 0, 0),
                  t_wall=(300.0,) * 4, storage=STORE_FP32_DEV, emulate_3d=True,
                  relax_mode=0, t_ref=300.0, theta=624.8074248458514, stream=None,
-                 allocator=None, specularity=(0.0,) * 4):
+                 allocator=None, specularity=(0.0,) * 4, speed=1.0):
         import torch
         self._torch = torch
         self.nx, self.ny, self.q = nx, ny, q
         self.device = torch.device("cuda", torch.cuda.current_device())
         self.stream = stream if stream is not None else torch.cuda.current_stream()
-        g = wlbm_grid(nx, ny, q, storage, 1 if emulate_3d else 0, relax_mode, t_ref, theta)
+        g = wlbm_grid(nx, ny, q, storage, 1 if emulate_3d else 0, relax_mode, t_ref, theta,
+                      float(speed))
         b = wlbm_boundary((C.c_int32 * 4)(*bc), (C.c_double * 4)(*t_wall),
                           (C.c_double * 4)(*specularity))
         if allocator is None:
@@ -354,7 +358,7 @@ class WormLBMBatch:
         for k, sp in enumerate(specs):
             grids[k] = wlbm_grid(sp["nx"], sp["ny"], sp["q"], storage,
                                  1 if sp.get("emulate_3d", True) else 0, sp.get("relax_mode", 0),
-                                 t_ref, theta)
+                                 t_ref, theta, float(sp.get("speed", 1.0)))
             bcs[k] = wlbm_boundary((C.c_int32 * 4)(*sp["bc"]), (C.c_double * 4)(*sp["t_wall"]),
                                    (C.c_double * 4)(*sp.get("specularity", (0.0,) * 4)))
             if sp.get("mfp_field") is not None:

@@ -12,7 +12,8 @@ def oracle_run(cfg, steps, state=None):
                   cfg["mfp"] if cfg.get("mfp_field") is None else cfg["mfp_field"],
                   bc_kind=cfg["bc"], t_wall=cfg["t_wall"], emulate_3d=cfg["emulate_3d"],
                   relax_mode=cfg.get("relax_mode", 0), theta=THETA,
-                  w_field=cfg.get("w_field"), specularity=cfg.get("specularity", (0.0,) * 4))
+                  w_field=cfg.get("w_field"), specularity=cfg.get("specularity", (0.0,) * 4),
+                  speed=cfg.get("speed", 1.0))
     if state is None:
         m.init_temperature(cfg["dT"].astype(np.float64))
     else:
@@ -30,7 +31,8 @@ def gpu_handle(cfg, storage=0, variant=None):
                    mfp_field=cfg.get("mfp_field"), bc=cfg["bc"], t_wall=cfg["t_wall"],
                    storage=storage, emulate_3d=cfg["emulate_3d"],
                    relax_mode=cfg.get("relax_mode", 0), theta=THETA,
-                   specularity=cfg.get("specularity", (0.0,) * 4))
+                   specularity=cfg.get("specularity", (0.0,) * 4),
+                   speed=cfg.get("speed", 1.0))
     if variant is not None:
         h.wlbm_set_option(wl.wlbm.OPT_STEP_VARIANT, variant)
     return h

@@ -36,10 +36,14 @@ def test_library_lattice_equals_oracle(wl, q):
     assert lam == pytest.approx(L.lambda_corr(L.ring_directions(q)), abs=1e-14)
 
 
-@pytest.mark.parametrize("q,steps", [(8, 3000), (16, 2000), (64, 1500), (256, 600)])
-def test_library_schedule_equals_oracle_byte_for_byte(wl, q, steps):
-    codes = wl.wlbm_schedule(q, steps)
-    sched = L.TasSchedule(q)
+@pytest.mark.parametrize("q,steps,speed", [(8, 3000, 1.0), (16, 2000, 1.0), (64, 1500, 1.0),
+                                           (256, 600, 1.0), (16, 2000, 0.5), (64, 900, 0.37),
+                                           (128, 600, 0.8125)])
+def test_library_schedule_equals_oracle_byte_for_byte(wl, q, steps, speed):
+    """The host schedule of the library and the oracle's, also below the unit speed (the
+    float64 hop test, evaluated identically on both sides)."""
+    codes = wl.wlbm_schedule(q, steps, speed)
+    sched = L.TasSchedule(q, speed)
     for n in range(1, steps + 1):
         hops, paused = sched.advance(n)
         want = np.array(hops, np.uint8) | (np.array(paused, np.uint8) << 3)
@@ -48,7 +52,7 @@ def test_library_schedule_equals_oracle_byte_for_byte(wl, q, steps):
 
 def _create(wl, nx=16, ny=16, q=16, mfp=4.0, kinds=(0, 0, 0, 0), relax=0, alloc=None,
             storage=0):
-    g = wl.wlbm.wlbm_grid(nx, ny, q, storage, 1, relax, 300.0, 624.8)
+    g = wl.wlbm.wlbm_grid(nx, ny, q, storage, 1, relax, 300.0, 624.8, 1.0)
     b = wl.wlbm.wlbm_boundary((C.c_int32 * 4)(*kinds), (C.c_double * 4)(300.0, 301.0, 300.0, 300.0))
     if alloc is None:
         fns = (wl.wlbm.ALLOC_FN(lambda n, ctx: None), wl.wlbm.FREE_FN(lambda p, ctx: None))

@@ -30,6 +30,8 @@ def _specs():
         dict(nx=33, ny=260, q=64, bc=(P, P, I, A), t_wall=(300.0, 300.0, 300.7, 300.0), mfp=30.0),
         dict(nx=70, ny=29, q=40, bc=(A, S, S, A), t_wall=(300.0,) * 4, mfp=5.0,
              specularity=(0.6, 0.0, 0.0, 0.25)),
+        dict(nx=58, ny=31, q=24, bc=(I, I, A, A), t_wall=(300.5, 300.0, 300.0, 300.0), mfp=6.0,
+             speed=0.55),
     ]
 
 
@@ -63,7 +65,8 @@ def _single(spec, dT, steps, storage, fuse=0, variant=3):
     import paper_1911_00180_gb300 as wl
     h = wl.WormLBM(spec["nx"], spec["ny"], spec["q"], mfp=spec.get("mfp"),
                    mfp_field=spec.get("mfp_field"), bc=spec["bc"], t_wall=spec["t_wall"],
-                   storage=storage, specularity=spec.get("specularity", (0.0,) * 4))
+                   storage=storage, specularity=spec.get("specularity", (0.0,) * 4),
+                   speed=spec.get("speed", 1.0))
     h.wlbm_set_option(wl.wlbm.OPT_STEP_VARIANT, variant)
     h.wlbm_set_option(wl.wlbm.OPT_FUSE_PERIODIC, fuse)
     h.wlbm_init_temperature(dT)
