@@ -13,12 +13,20 @@ float64.  TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
                         (W = 0): direction i carries the wall's w_i e(T_w) to x once its
                         worm displacement along x exceeds x (a pure function of the TAS
                         schedule of Eq. algorithm).
+  one_pixel_worm        the "one-pixel source" of Sec. 4.2 at W = 0 on a periodic grid: a
+                        direction carries the source's value at x exactly when its path
+                        back in time passes the source cell at a step before n, i.e.
+                        x - s = p_i(n) - p_i(k) (mod the grid) for some 0 <= k < n.
+  disk_ballistic_2d     2D ballistic spreading of a uniform disk (Sec. 4.2, the circular
+                        initial condition): the angular fraction of the circle of radius
+                        v t around a point that lies inside the disk.
   one_hot_three_cold    2D steady heat conduction on the unit square, Theta = 1 on the hot
                         edge Y = 1 and 0 on the other three (Sec. 4.6, Eq. 2DT): Fourier
                         sine series in X with sinh profiles in Y.
 
 Pins: tests/test_oracle_analytic.py (boundary values, steady limits, harmonicity by finite
-differences, the discrete ballistic profile against the oracle stepper at W = 0).
+differences, the discrete ballistic and one-pixel profiles against the oracle stepper at
+W = 0, the small-disk limit of the disk front).
 """
 import math
 
@@ -73,4 +81,41 @@ def one_hot_three_cold(X, Y, terms=400):
         k = l * math.pi
         ratio = np.exp(-k * (1.0 - Y)) * (-np.expm1(-2.0 * k * Y)) / (-math.expm1(-2.0 * k))
         out = out + 4.0 / k * np.sin(k * X) * ratio
+    return out
+
+
+def one_pixel_worm(q, n, nx, ny, src, de_src, de_init=0.0):
+    """E(x, y) - e_ref after n steps, array (ny, nx): source cell src = (x, y) kept at the
+    isotropic deviation de_src, the rest starting at de_init, W = 0, periodic grid."""
+    dirs = L.ring_directions(q)
+    w = L.angular_weights(dirs)
+    sched = L.TasSchedule(q)
+    path = [sched.displacement().copy()]
+    for _ in range(n):
+        sched.advance()
+        path.append(sched.displacement().copy())
+    pn = path[-1]
+    e = np.zeros((ny, nx))
+    for i in range(q):
+        hit = np.zeros((ny, nx), bool)
+        for k in range(n):
+            dx, dy = pn[i] - path[k][i]
+            hit[(src[1] + dy) % ny, (src[0] + dx) % nx] = True
+        e += w[i] * np.where(hit, de_src, de_init)
+    return e
+
+
+def disk_ballistic_2d(r, t, radius, v=1.0):
+    """Fraction of the directions from a point at distance r from the disk centre whose
+    point at distance v t lies inside the disk of the given radius (the ballistic
+    temperature rise over the disk's, as a fraction)."""
+    r = np.asarray(r, np.float64)
+    s = v * t
+    if s == 0:
+        return (r < radius).astype(np.float64)
+    full = (r + s <= radius)
+    part = (np.abs(r - s) < radius) & ~full
+    with np.errstate(invalid="ignore", divide="ignore"):
+        c = (r * r + s * s - radius * radius) / (2.0 * r * s)
+    out = np.where(full, 1.0, np.where(part, np.arccos(np.clip(c, -1.0, 1.0)) / math.pi, 0.0))
     return out

@@ -38,6 +38,12 @@ Readings of passages the paper leaves open (each is also listed in the design doc):
     its value and gives the rest to the collection; inward components receive
     p d_mirror + (1 - p) rho_i A on top of what they hold.  Exactly conserving; p = 0 is
     the diffuse rule;
+  * internal sources (Sec. 2.6: isotropic blackbody and anisotropic radiation conditions
+    "or, equivalently", internal temperature and radiation sources): listed cells of the
+    interior or of a non-periodic wall's ghost frame whose DDEDs are overwritten at every
+    step, after the wall conditions and before the periodic links, with w_i e_eq(T_s)
+    (Eq. isotropic) or imposed values (Eq. anisotropic); on a wall's ghost cells they make
+    an anisotropic radiation wall;
   * corner ghost cells: a periodic link fills them; otherwise an isothermal x-wall,
     then an isothermal y-wall, decides; two adiabatic walls (diffuse or specular) use the
     diffuse corner rule above (a specular corner would map up to three directions onto
@@ -120,6 +126,7 @@ class WormLBM:
         self.wf = self._frame_scalar(wc)
         self.d = np.zeros((q, ny + 2, nx + 2))
         self.n = 0
+        self.sources = []                  # (Y, X, deviations (q,)) in framed indices
 
     # ----------------------------------------------------------------- geometry
     def _frame_scalar(self, interior):
@@ -230,8 +237,31 @@ class WormLBM:
                 self.d[:, yy, xx] = self.w * self.delta_e(self.t_wall[xw])
             elif k[yw] == ISOTHERMAL:
                 self.d[:, yy, xx] = self.w * self.delta_e(self.t_wall[yw])
-        # 3. periodic links
+        # 3. internal sources and radiation cells (Eq. isotropic / Eq. anisotropic)
+        for (yy, xx, v) in self.sources:
+            self.d[:, yy, xx] = v
+        # 4. periodic links
         self._periodic_links(self.d)
+
+    def set_sources(self, cells, temps=None, imposed=None):
+        """Cells (x, y) with -1 <= x <= nx, -1 <= y <= ny (not on a periodic side's ghost
+        frame) kept at temperature temps[k] (isotropic: e_i = w_i e_eq(T)) or at the
+        imposed absolute DDEDs imposed[k] (Q values each).  An empty list removes them."""
+        per = [self.bc_kind[s] == PERIODIC for s in (XM, XP, YM, YP)]
+        out = []
+        for k, (x, y) in enumerate(cells):
+            if not (-1 <= x <= self.nx and -1 <= y <= self.ny):
+                raise ValueError("source outside the frame")
+            sides = [s for s, hit in ((XM, x == -1), (XP, x == self.nx), (YM, y == -1),
+                                      (YP, y == self.ny)) if hit]
+            if any(per[s] for s in sides):
+                raise ValueError("source on a periodic ghost cell")
+            if imposed is not None:
+                v = np.asarray(imposed[k], np.float64) - self.w * self.e_ref
+            else:
+                v = self.w * self.delta_e(float(temps[k]))
+            out.append((y + 1, x + 1, v))
+        self.sources = out
 
     # ------------------------------------------------------------------- state
     def init_temperature(self, dT):
