@@ -191,6 +191,19 @@ wlbm_status wlbm_run_steady(wlbm_handle* h, int64_t max_steps, int64_t check_eve
 wlbm_status wlbm_get_state(wlbm_handle* h, float* framed);
 wlbm_status wlbm_set_state(wlbm_handle* h, const float* framed);
 
+/* wlbm_set_sources: internal temperature and radiation sources (Sec. 2.6: the isotropic
+ * blackbody and anisotropic radiation conditions are "equivalently" internal sources).
+ * n cells (host int32 xy[2n]: x in [-1, nx], y in [-1, ny], not on the ghost frame of a
+ * periodic side) whose DDEDs are overwritten at every step, after the wall pass and
+ * before the periodic links, either with w_i e_eq(t[k]) (host double t[n], K; Eq.
+ * isotropic) or, when e_imposed is given, with the imposed absolute DDEDs e_imposed[k][i]
+ * (host double [n][Q]; Eq. anisotropic).  Sources on a wall's ghost cells make an
+ * anisotropic radiation wall.  n = 0 removes all sources.  Each call replaces the previous
+ * set (library memory).  Not for batch-owned handles (WLBM_ERR_STATE); the adjoint refuses
+ * handles with sources (WLBM_ERR_STATE).  Synchronous. */
+wlbm_status wlbm_set_sources(wlbm_handle* h, int32_t n, const int32_t* xy, const double* t,
+                             const double* e_imposed);
+
 /* wlbm_save / wlbm_load: checkpoint and resume.  A checkpoint holds the current state
  * planes as stored (framed, float32 or bfloat16), the local-energy plane (and, with
  * bfloat16 storage, the reference-energy plane), the storage scale and the schedule

@@ -9,6 +9,8 @@
 //  k_periodic  periodic links (Sec. 2.6): ghost rows copy the opposite interior rows,
 //              then ghost columns copy the opposite columns (corners via the diagonal);
 //              before a step, per plane only the side that step's hop pulls from.
+//  k_sources   internal temperature / radiation sources (Sec. 2.6): listed cells take fixed
+//              values every step.
 //  k_init      local equilibrium start e_i = w_i e_eq(T) (Sec. 2.4) in float64.
 //  k_moments   T - T_ref by Eq. pseudo-T in a cancellation-free form, q by Eq. q_corr.
 //  k_reduce    float64 sums: energy (interior, + adiabatic-wall ghost cells), heat flux
@@ -336,6 +338,27 @@ __global__ void __launch_bounds__(32 * kWallWarps) k_walls_batch(const BatchWall
   walls_chunk<T>(I.w, I.codes + size_t(t) * I.w.q, e_ref, b - I.first_block, sm);
 }
 
+// Internal sources / radiation cells: one warp per cell, lanes over the directions.  With
+// bfloat16 storage the cell's reference energy becomes the imposed total, so the stored
+// values are the imposed ones relative to it (as for isothermal walls).
+template <typename T>
+__global__ void __launch_bounds__(256) k_sources(const SourceArgs a) {
+  const int s = int(blockIdx.x) * 8 + (int(threadIdx.x) >> 5);
+  const int lane = int(threadIdx.x) & 31;
+  if (s >= a.n) return;
+  const int64_t off = a.off[s];
+  const float R = a.esum[s];
+  T* planes = static_cast<T*>(a.planes);
+  for (int i = lane; i < a.q; i += 32) {
+    T* p = planes + int64_t(((a.codes[i] >> 4) & 1) * a.q + i) * a.plane + off;
+    wall_store(p, a.val[int64_t(s) * a.q + i], a.w[i], a.e_ref != nullptr, R, a.inv_scale);
+  }
+  if (lane == 0) {
+    a.e_cur[off] = R;
+    if (a.e_ref) a.e_ref[off] = R;
+  }
+}
+
 template <typename T>
 __global__ void k_periodic(const PeriodicArgs a) {
   const int ncy = a.yper ? (a.xper ? a.nx : a.nx + 2) : 0;
@@ -637,6 +660,16 @@ cudaError_t launch_moments(int storage, const MomentArgs& a, cudaStream_t s) {
     k_moments<__nv_bfloat16><<<g, 256, 0, s>>>(a);
   else
     k_moments<float><<<g, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sources(int storage, const SourceArgs& a, cudaStream_t s) {
+  if (a.n == 0) return cudaSuccess;
+  const unsigned g = unsigned((a.n + 7) / 8);
+  if (storage == WLBM_STORE_BF16_DEV)
+    k_sources<__nv_bfloat16><<<g, 256, 0, s>>>(a);
+  else
+    k_sources<float><<<g, 256, 0, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -58,6 +58,11 @@ struct wlbm_handle {
   double* d_snap = nullptr;   // nx*ny float64 T - T_ref at the last reduction
   int64_t snap_step = -1;     // step of that snapshot (-1: none since the state was set)
   bool batch_owned = false;   // instance of a wlbm_batch (its records cache plane roles)
+  // internal sources / radiation cells (wlbm_set_sources)
+  int n_src = 0;
+  int64_t* d_src_off = nullptr;
+  float* d_src_val = nullptr;   // [n_src][q] deviations
+  float* d_src_e = nullptr;     // [n_src] sums
   double* d_win = nullptr;    // nx*ny float64 window sum and previous window mean of
   double* d_win_prev = nullptr;   // T - T_ref (wlbm_run_steady; allocated on first use)
   int* d_status = nullptr;    // bit 0: a bounded device wait gave up
@@ -583,8 +588,9 @@ static wlbm_status enqueue_steps(wlbm_handle* h, int count, bool profile) {
   const bool any_wall = h->walls.nseg > 0;
   // both axes periodic: the step kernel mirrors the edges itself (grids of 2+ cells)
   // (variant 3 has no mirror stores: there the separate periodic pass runs)
+  // (sources must reach the ghost copies through the periodic pass: no mirrors with them)
   const bool wrap = h->fuse_periodic && h->step_variant != 3 && h->xper && h->yper &&
-                    g.nx >= 2 && g.ny >= 2;
+                    g.nx >= 2 && g.ny >= 2 && h->n_src == 0;
   const bool any_per = (h->xper || h->yper) && !wrap;
   wlbm_status st = WLBM_OK;
   for (int t = 0; t < count; ++t) {
@@ -594,6 +600,16 @@ static wlbm_status enqueue_steps(wlbm_handle* h, int count, bool profile) {
       wa.codes = codes;
       wa.e_ref = h->ref_plane();
       st = h->cuda(launch_walls(h->storage, wa, h->stream), "wlbm_step: walls");
+      if (st != WLBM_OK) return st;
+      ++h->launches;
+    }
+    if (h->n_src > 0) {
+      SourceArgs ca{};
+      ca.planes = h->planes; ca.plane = g.plane; ca.q = g.q; ca.n = h->n_src;
+      ca.off = h->d_src_off; ca.val = h->d_src_val; ca.esum = h->d_src_e;
+      ca.e_cur = h->e[h->e_cur]; ca.e_ref = h->ref_plane(); ca.w = h->w_dev();
+      ca.codes = codes; ca.inv_scale = h->inv_scale;
+      st = h->cuda(launch_sources(h->storage, ca, h->stream), "wlbm_step: sources");
       if (st != WLBM_OK) return st;
       ++h->launches;
     }
@@ -957,6 +973,66 @@ wlbm_status wlbm_set_state(wlbm_handle* h, const float* framed) {
   return st == WLBM_OK ? refresh_periodic(h) : st;
 }
 
+wlbm_status wlbm_set_sources(wlbm_handle* h, int32_t n, const int32_t* xy, const double* t,
+                             const double* e_imposed) {
+  if (!h) return WLBM_ERR_INVALID_ARG;
+  if (h->batch_owned)
+    return h->fail(WLBM_ERR_STATE, "wlbm_set_sources: handles owned by a batch are not supported");
+  if (n < 0 || (n > 0 && (!xy || (!t && !e_imposed))))
+    return h->fail(WLBM_ERR_INVALID_ARG, "wlbm_set_sources: need cells and temperatures or "
+                                         "imposed values");
+  const Geom& g = h->g;
+  const size_t ns = static_cast<size_t>(n);
+  std::vector<int64_t> off(ns);
+  std::vector<float> val(ns * g.q), esum(ns);
+  for (int k = 0; k < n; ++k) {
+    const int x = xy[2 * k], y = xy[2 * k + 1];
+    if (x < -1 || x > g.nx || y < -1 || y > g.ny)
+      return h->fail(WLBM_ERR_INVALID_ARG, "wlbm_set_sources: cell outside the frame");
+    const bool per = ((x == -1 || x == g.nx) && h->xper) || ((y == -1 || y == g.ny) && h->yper);
+    if (per)
+      return h->fail(WLBM_ERR_INVALID_ARG, "wlbm_set_sources: cell on a periodic ghost frame");
+    off[size_t(k)] = int64_t(y + 2) * g.pitch + (kX0 + x);
+    double sum = 0.0;
+    for (int i = 0; i < g.q; ++i) {
+      double d;
+      if (e_imposed) {
+        d = e_imposed[size_t(k) * g.q + i] - h->lat.w[i] * h->e_eq_ref;
+      } else {
+        if (!(t[k] > 0))
+          return h->fail(WLBM_ERR_INVALID_ARG, "wlbm_set_sources: temperatures must be > 0");
+        d = h->lat.w[i] * h->delta_e(t[k]);
+      }
+      val[size_t(k) * g.q + i] = float(d);
+      sum += double(float(d));
+    }
+    esum[size_t(k)] = float(sum);
+  }
+  for (void* p : {static_cast<void*>(h->d_src_off), static_cast<void*>(h->d_src_val),
+                  static_cast<void*>(h->d_src_e)})
+    if (p) h->dev_free(p);
+  h->d_src_off = nullptr; h->d_src_val = nullptr; h->d_src_e = nullptr;
+  h->n_src = 0;
+  h->drop_graphs();
+  if (n == 0) return WLBM_OK;
+  h->d_src_off = static_cast<int64_t*>(h->dev_alloc(off.size() * 8));
+  h->d_src_val = static_cast<float*>(h->dev_alloc(val.size() * 4));
+  h->d_src_e = static_cast<float*>(h->dev_alloc(esum.size() * 4));
+  if (!h->d_src_off || !h->d_src_val || !h->d_src_e)
+    return h->fail(WLBM_ERR_OOM, "wlbm_set_sources: device allocation failed");
+  wlbm_status st = h->cuda(cudaMemcpyAsync(h->d_src_off, off.data(), off.size() * 8,
+                                           cudaMemcpyHostToDevice, h->stream), "wlbm_set_sources");
+  if (st == WLBM_OK)
+    st = h->cuda(cudaMemcpyAsync(h->d_src_val, val.data(), val.size() * 4,
+                                 cudaMemcpyHostToDevice, h->stream), "wlbm_set_sources");
+  if (st == WLBM_OK)
+    st = h->cuda(cudaMemcpyAsync(h->d_src_e, esum.data(), esum.size() * 4,
+                                 cudaMemcpyHostToDevice, h->stream), "wlbm_set_sources");
+  if (st == WLBM_OK) st = h->cuda(cudaStreamSynchronize(h->stream), "wlbm_set_sources");
+  if (st == WLBM_OK) h->n_src = n;
+  return st;
+}
+
 // ---------------------------------------------------------------- checkpoint / resume
 // Blob: CkptHeader, the schedule cursor (px, py, h as int64[q] each, parity as uint8[q]
 // padded to 8 bytes), the q current state planes as stored (framed, pitch included), the
@@ -1155,6 +1231,8 @@ wlbm_status wlbm_adjoint_forward(wlbm_handle* h, const float* dT0, int64_t n_ste
   if (!h) return WLBM_ERR_INVALID_ARG;
   if (h->bf16())
     return h->fail(WLBM_ERR_INVALID_ARG, "wlbm_adjoint_forward: needs float32 storage");
+  if (h->n_src > 0)
+    return h->fail(WLBM_ERR_STATE, "wlbm_adjoint_forward: internal sources are not supported");
   if (!dT0 || n_steps < 1 || ckpt_every < 1)
     return h->fail(WLBM_ERR_INVALID_ARG, "wlbm_adjoint_forward: bad start field or counts");
   const Geom& g = h->g;

@@ -380,6 +380,23 @@ cudaError_t launch_periodic_T(float* planes, int64_t plane, int pitch, int nx, i
 // the reverse step: only the two end cells of each isothermal segment (where the periodic
 // transpose of the other axis may have added corner images) are transposed again.
 cudaError_t launch_walls_T(const WallArgs& wa, float* lam, double* gtw, cudaStream_t s);
+// Internal sources and radiation cells: framed cells whose deviations are overwritten
+// every step (after the wall pass, before the periodic pass) with fixed values.
+struct SourceArgs {
+  void* planes;
+  int64_t plane;
+  int q, n;
+  const int64_t* off;    // [n] framed offsets within a plane
+  const float* val;      // [n][q] deviations d_i to impose
+  const float* esum;     // [n] their sum (the cell's local energy deviation)
+  float* e_cur;          // local-energy plane of the current state
+  float* e_ref;          // reference-energy plane (bfloat16 only)
+  const float* w;
+  const uint8_t* codes;  // current parity from the next step's codes
+  float inv_scale;
+};
+cudaError_t launch_sources(int storage, const SourceArgs& a, cudaStream_t s);
+
 cudaError_t launch_adj_seed(const AdjArgs& a, const float* dJ_dT, const float* dJ_dqx,
                             const float* dJ_dqy, const float* sx, const float* sy, float vg,
                             const float* e_final, double e_ref, double theta, cudaStream_t s);

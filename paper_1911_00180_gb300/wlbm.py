@@ -69,6 +69,7 @@ def _load():
                                       C.POINTER(i32), C.POINTER(dbl)]),
         "wlbm_get_state": (C.c_int, [vp, vp]),
         "wlbm_save": (C.c_int, [vp, vp, C.c_size_t, C.POINTER(C.c_size_t)]),
+        "wlbm_set_sources": (C.c_int, [vp, i32, C.POINTER(i32), C.POINTER(dbl), C.POINTER(dbl)]),
         "wlbm_load": (C.c_int, [vp, vp, C.c_size_t]),
         "wlbm_set_state": (C.c_int, [vp, vp]),
         "wlbm_adjoint_forward": (C.c_int, [vp, vp, i64, i32]),
@@ -240,6 +241,19 @@ class WormLBM:
         _check(lib.wlbm_run_steady(self.h, int(max_steps), int(check_every), float(tol),
                                    int(avg_steps), C.byref(steps), C.byref(conv), out), self.h)
         return steps.value, bool(conv.value), list(out)
+
+    def wlbm_set_sources(self, cells, temps=None, imposed=None):
+        """Cells [(x, y), ...] kept at temperatures `temps` (K) or at the imposed absolute
+        DDEDs `imposed` (n x Q); an empty list removes the sources."""
+        import numpy as np
+        n = len(cells)
+        xy = np.ascontiguousarray(np.asarray(cells, np.int32).reshape(-1))
+        t = None if temps is None else np.ascontiguousarray(np.asarray(temps, np.float64))
+        e = None if imposed is None else np.ascontiguousarray(
+            np.asarray(imposed, np.float64).reshape(n, self.q))
+        ptr = lambda a, ty: None if a is None else a.ctypes.data_as(C.POINTER(ty))
+        _check(lib.wlbm_set_sources(self.h, n, ptr(xy, C.c_int32) if n else None,
+                                    ptr(t, C.c_double), ptr(e, C.c_double)), self.h)
 
     def wlbm_save(self):
         """Checkpoint of the current state and schedule cursor as a numpy uint8 array."""
