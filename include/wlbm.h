@@ -134,8 +134,11 @@ int64_t wlbm_step_count(const wlbm_handle* h);
  * current state.  Each output is device nx*ny float32, or NULL to skip it. */
 wlbm_status wlbm_moments(wlbm_handle* h, float* dT, float* qx, float* qy);
 
-/* wlbm_reduce: float64 reductions over the current state (computed on the GPU in float64
- * from the stored values), written to host out[WLBM_REDUCE_N].  Lattice units: cell =
+/* wlbm_reduce: float64 reductions over the current state, written to host
+ * out[WLBM_REDUCE_N].  On the GPU each cell's sums over its directions and its temperature
+ * are float32 (as in wlbm_moments: the stored values are float32 or coarser); the sums and
+ * the maximum over cells are float64, combined in a fixed order (the same bits on every
+ * call for the same state).  Lattice units: cell =
  * step = v_g = 1, energy as E - e_ref with the paper's unit prefactor set to 1.
  *   out[0] sum over interior cells of E - e_ref   (energy conservation, Eq.
  *          lbm-energy-density)
@@ -157,7 +160,7 @@ wlbm_status wlbm_moments(wlbm_handle* h, float* dT, float* qx, float* qy);
  *          per-cell MFP field
  *   out[8] steady-state residual: max over interior cells of |T^n - T^m| / (n - m) in
  *          K per step, n the current step and m the step of the previous wlbm_reduce on
- *          this handle (temperatures by Eq. pseudo-T in float64); NaN on the first call
+ *          this handle (temperatures by Eq. pseudo-T); NaN on the first call
  *          after wlbm_init_temperature / wlbm_set_state / wlbm_adjoint_backward and when
  *          no step ran since the previous call.  Each call takes the next snapshot
  *          (library memory: nx*ny float64).

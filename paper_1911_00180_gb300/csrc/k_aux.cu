@@ -17,6 +17,8 @@
 //              (all cells and the central band of columns), band energy moment for the
 //              conductivity fit, and the largest temperature change since the previous
 //              reduction (and between window means, for the steady-state run).
+#include <algorithm>
+
 #include "elem.cuh"
 #include "wlbm_internal.hpp"
 
@@ -461,11 +463,19 @@ __global__ void k_moments(const MomentArgs a) {
   }
 }
 
-// T - T_ref of a local-energy deviation de in float64 (Eq. pseudo-T, the same
-// cancellation-free form as k_moments).
-__device__ __forceinline__ double temperature_dev64(double de, const ReduceArgs& a) {
-  const double dl = log1p(de / a.e_ref1) - log1p(de / a.e_ref);
-  return -a.theta * dl / (a.l_ref * (a.l_ref + dl));
+// T - T_ref of a cell's float32 local-energy deviation (Eq. pseudo-T in the same
+// cancellation-free float32 form as k_moments; float64 per cell would cost more than the
+// rest of the reduction on this GPU's float64 rate).  The reductions over cells that use
+// it stay in float64.
+__device__ __forceinline__ float temperature_dev32(float de, float e_ref, float e_ref1,
+                                                   float l_ref, float theta) {
+  const float dl = log1pf(de / e_ref1) - log1pf(de / e_ref);
+  return -theta * dl / (l_ref * (l_ref + dl));
+}
+
+// max that keeps NaN (a NaN temperature must show in the residual)
+__device__ __forceinline__ double fmax_nan(double a, double b) {
+  return (a != a || b != b) ? __longlong_as_double(0x7ff8000000000000ll) : (a > b ? a : b);
 }
 
 __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
@@ -477,60 +487,85 @@ __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v)
   return v;
 }
 
+// Per-direction data of a reduction block, staged once in shared memory.
+struct ReduceSmem {
+  float w[kMaxQ], sx[kMaxQ], sy[kMaxQ];
+  uint8_t par[kMaxQ];
+};
+
+// Per-cell contributions of k_reduce at framed index t: the sums v[] and the residual.
 template <typename T>
-__global__ void k_reduce(const ReduceArgs a) {
+__device__ __forceinline__ void reduce_cell(const ReduceArgs& a, const ReduceSmem& sm, int t,
+                                            double* v, double* res, double* resw) {
   const int fw = a.nx + 2, fh = a.ny + 2;
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  double v[kReduceSums] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-  double res = 0.0;   // |T - T_snap| of this cell (non-negative or NaN)
-  double resw = 0.0;  // |window mean - previous window mean|
-  if (t < fw * fh) {
-    const int fy = t / fw, fx = t - fy * fw;
-    const bool gx = fx == 0 || fx == fw - 1, gy = fy == 0 || fy == fh - 1;
-    const int64_t off = int64_t(fy + 1) * a.pitch + (kGhostCol + fx);
-    const T* planes = static_cast<const T*>(a.planes);
-    if (!gx && !gy) {
-      const double e = double(a.e_cur[off]);
-      v[0] = e;
-      v[1] = e;
-      double qx = 0.0, qy = 0.0;
-      for (int i = 0; i < a.q; ++i) {
-        const double u = dev_load(planes + int64_t(parity_of(a.par, i) * a.q + i) * a.plane + off,
-                                  a.w[i], a.e_refp, off, float(a.scale));
-        qx += u * a.sx[i];
-        qy += u * a.sy[i];
-      }
-      v[2] = qx;
-      v[3] = qy;
-      const int x = fx - 1;
-      if (x >= a.band_x0 && x < a.band_x0 + a.band_w) {
-        v[4] = qx;
-        v[5] = (double(x) - a.band_xbar) * e;
-      }
-      const int64_t c = int64_t(fy - 1) * a.nx + x;
-      const double tn = temperature_dev64(e, a);
-      if (a.has_snap) res = fabs(tn - a.snap[c]);
-      a.snap[c] = tn;
-      if (a.win) {
-        const double acc = a.win_first ? tn : a.win[c] + tn;
-        if (a.win_last) {
-          const double mean = acc * a.win_inv;
-          if (a.win_has_prev) resw = fabs(mean - a.win_prev[c]);
-          a.win_prev[c] = mean;
-        } else {
-          a.win[c] = acc;
-        }
-      }
-    } else if (wall_energy_cell(fx, fy, fw, fh, a.diff_mask)) {
-      double e = 0.0;
-      for (int i = 0; i < a.q; ++i)
-        e += dev_load(planes + int64_t(parity_of(a.par, i) * a.q + i) * a.plane + off, a.w[i],
-                      a.e_refp, off, float(a.scale));
-      v[1] = e;
+  const int fy = t / fw, fx = t - fy * fw;
+  const bool gx = fx == 0 || fx == fw - 1, gy = fy == 0 || fy == fh - 1;
+  const int64_t off = int64_t(fy + 1) * a.pitch + (kGhostCol + fx);
+  const T* planes = static_cast<const T*>(a.planes);
+  if (!gx && !gy) {
+    const double e = double(a.e_cur[off]);
+    v[0] += e;
+    v[1] += e;
+    // a cell's flux over its Q directions in float32 (as in k_moments: the stored values
+    // are float32 or coarser), the sums over cells in float64
+    float qx = 0.f, qy = 0.f;
+#pragma unroll 8
+    for (int i = 0; i < a.q; ++i) {
+      const float u = dev_load(planes + int64_t(sm.par[i] * a.q + i) * a.plane + off, sm.w[i],
+                               a.e_refp, off, float(a.scale));
+      qx = fmaf(u, sm.sx[i], qx);
+      qy = fmaf(u, sm.sy[i], qy);
     }
+    v[2] += qx;
+    v[3] += qy;
+    const int x = fx - 1;
+    if (x >= a.band_x0 && x < a.band_x0 + a.band_w) {
+      v[4] += qx;
+      v[5] += (double(x) - a.band_xbar) * e;
+    }
+    const int64_t c = int64_t(fy - 1) * a.nx + x;
+    const double tn = double(temperature_dev32(a.e_cur[off], float(a.e_ref), float(a.e_ref1),
+                                               float(a.l_ref), float(a.theta)));
+    if (a.has_snap) *res = fmax_nan(*res, fabs(tn - a.snap[c]));
+    a.snap[c] = tn;
+    if (a.win) {
+      const double acc = a.win_first ? tn : a.win[c] + tn;
+      if (a.win_last) {
+        const double mean = acc * a.win_inv;
+        if (a.win_has_prev) *resw = fmax_nan(*resw, fabs(mean - a.win_prev[c]));
+        a.win_prev[c] = mean;
+      } else {
+        a.win[c] = acc;
+      }
+    }
+  } else if (wall_energy_cell(fx, fy, fw, fh, a.diff_mask)) {
+    double e = 0.0;            // wall cells are few: float64 over the directions
+    for (int i = 0; i < a.q; ++i)
+      e += dev_load(planes + int64_t(sm.par[i] * a.q + i) * a.plane + off, sm.w[i], a.e_refp,
+                    off, float(a.scale));
+    v[1] += e;
   }
-  __shared__ double red[kReduceSums][32];
-  __shared__ unsigned long long redm[2][32];
+}
+
+// Stage 1: a grid-stride pass; block b writes its kReduceOut partial results to
+// a.part[b] (no atomics: a second kernel combines the blocks in a fixed order).
+template <typename T>
+__global__ void __launch_bounds__(256) k_reduce(const ReduceArgs a) {
+  const int cells = (a.nx + 2) * (a.ny + 2);
+  __shared__ ReduceSmem sm;
+  for (int i = int(threadIdx.x); i < a.q; i += 256) {
+    sm.w[i] = a.w[i];
+    sm.sx[i] = a.sx[i];
+    sm.sy[i] = a.sy[i];
+    sm.par[i] = uint8_t(parity_of(a.par, i));
+  }
+  __syncthreads();
+  double v[kReduceSums] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  double res = 0.0, resw = 0.0;   // largest |T - T_snap| and window change (>= 0 or NaN)
+  for (int t = int(blockIdx.x) * 256 + int(threadIdx.x); t < cells; t += int(gridDim.x) * 256)
+    reduce_cell<T>(a, sm, t, v, &res, &resw);
+  __shared__ double red[kReduceSums][8];
+  __shared__ unsigned long long redm[2][8];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
   for (int k = 0; k < kReduceSums; ++k) {
@@ -545,20 +580,57 @@ __global__ void k_reduce(const ReduceArgs a) {
     redm[1][wid] = m1;
   }
   __syncthreads();
-  if (wid == 0) {
-    const int nw = blockDim.x >> 5;
+  if (threadIdx.x < kReduceSums) {
+    double s = 0.0;
+    for (int w = 0; w < 8; ++w) s += red[threadIdx.x][w];
+    a.part[int64_t(blockIdx.x) * kReduceOut + threadIdx.x] = s;
+  } else if (threadIdx.x < kReduceOut) {
+    unsigned long long m = 0ull;
+    for (int w = 0; w < 8; ++w) m = redm[threadIdx.x - kReduceSums][w] > m
+                                        ? redm[threadIdx.x - kReduceSums][w] : m;
+    a.part[int64_t(blockIdx.x) * kReduceOut + threadIdx.x] = __longlong_as_double(
+        static_cast<long long>(m));
+  }
+}
+
+// Stage 2, one block: the blocks' partials combined in a fixed order into a.out.
+__global__ void __launch_bounds__(256) k_reduce_finish(const ReduceArgs a, int nblocks) {
+  double v[kReduceSums] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  unsigned long long m[2] = {0ull, 0ull};
+  for (int b = int(threadIdx.x); b < nblocks; b += 256) {
+    const double* p = a.part + int64_t(b) * kReduceOut;
 #pragma unroll
-    for (int k = 0; k < kReduceSums; ++k) {
-      double s = lane < nw ? red[k][lane] : 0.0;
-      s = warp_sum(s);
-      if (lane == 0 && s != 0.0) atomicAdd(a.out + k, s);
-    }
+    for (int k = 0; k < kReduceSums; ++k) v[k] += p[k];
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
-      const unsigned long long mm = warp_max_u64(lane < nw ? redm[k][lane] : 0ull);
-      if (lane == 0 && mm != 0ull)
-        atomicMax(reinterpret_cast<unsigned long long*>(a.out + kReduceSums + k), mm);
+      const unsigned long long u =
+          static_cast<unsigned long long>(__double_as_longlong(p[kReduceSums + k]));
+      m[k] = u > m[k] ? u : m[k];
     }
+  }
+  __shared__ double red[kReduceSums][8];
+  __shared__ unsigned long long redm[2][8];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < kReduceSums; ++k) {
+    const double s = warp_sum(v[k]);
+    if (lane == 0) red[k][wid] = s;
+  }
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const unsigned long long u = warp_max_u64(m[k]);
+    if (lane == 0) redm[k][wid] = u;
+  }
+  __syncthreads();
+  if (threadIdx.x < kReduceSums) {
+    double s = 0.0;
+    for (int w = 0; w < 8; ++w) s += red[threadIdx.x][w];
+    a.out[threadIdx.x] = s;
+  } else if (threadIdx.x < kReduceOut) {
+    unsigned long long u = 0ull;
+    for (int w = 0; w < 8; ++w) u = redm[threadIdx.x - kReduceSums][w] > u
+                                        ? redm[threadIdx.x - kReduceSums][w] : u;
+    a.out[threadIdx.x] = __longlong_as_double(static_cast<long long>(u));
   }
 }
 
@@ -674,11 +746,13 @@ cudaError_t launch_sources(int storage, const SourceArgs& a, cudaStream_t s) {
 }
 
 cudaError_t launch_reduce(int storage, const ReduceArgs& a, cudaStream_t s) {
-  const unsigned g = blocks_for(int64_t(a.nx + 2) * (a.ny + 2), 256);
+  const int cells = (a.nx + 2) * (a.ny + 2);
+  const int nb = std::max(1, std::min(kReduceBlocks, (cells + 255) / 256));
   if (storage == WLBM_STORE_BF16_DEV)
-    k_reduce<__nv_bfloat16><<<g, 256, 0, s>>>(a);
+    k_reduce<__nv_bfloat16><<<nb, 256, 0, s>>>(a);
   else
-    k_reduce<float><<<g, 256, 0, s>>>(a);
+    k_reduce<float><<<nb, 256, 0, s>>>(a);
+  k_reduce_finish<<<1, 256, 0, s>>>(a, nb);
   return cudaGetLastError();
 }
 

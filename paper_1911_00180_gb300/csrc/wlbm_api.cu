@@ -55,6 +55,7 @@ struct wlbm_handle {
   uint8_t* d_codes = nullptr; // [kChunk][q]
   uint16_t* d_order = nullptr; // [kChunk][q + 17] kind-sorted directions (variant 3)
   double* d_red = nullptr;    // [kReduceOut]
+  double* d_red_part = nullptr;   // [kReduceBlocks][kReduceOut] reduction partials
   double* d_snap = nullptr;   // nx*ny float64 T - T_ref at the last reduction
   int64_t snap_step = -1;     // step of that snapshot (-1: none since the state was set)
   bool batch_owned = false;   // instance of a wlbm_batch (its records cache plane roles)
@@ -481,6 +482,8 @@ wlbm_status wlbm_create(const wlbm_grid* grid, const float* mfp_cells, double mf
   h->d_codes = static_cast<uint8_t*>(h->dev_alloc(size_t(kChunk) * G.q));
   h->d_order = static_cast<uint16_t*>(h->dev_alloc(size_t(kChunk) * (G.q + 17) * 2));
   h->d_red = static_cast<double*>(h->dev_alloc(8 * sizeof(double)));
+  h->d_red_part = static_cast<double*>(
+      h->dev_alloc(size_t(kReduceBlocks) * kReduceOut * sizeof(double)));
   h->d_snap = static_cast<double*>(h->dev_alloc(size_t(g.nx) * g.ny * sizeof(double)));
   h->d_status = static_cast<int*>(h->dev_alloc(256));
   if (h->planes)
@@ -488,7 +491,8 @@ wlbm_status wlbm_create(const wlbm_grid* grid, const float* mfp_cells, double mf
   if (h->has_tmap) h->step_variant = 3;   // the fastest step kernel where it applies
   if (h->field_w) h->wfield = static_cast<float*>(h->dev_alloc(size_t(g.plane) * 4));
   if (!h->planes || !h->e[0] || !h->e[1] || (n_e == 3 && !h->e[2]) || !h->consts ||
-      !h->d_codes || !h->d_order || !h->d_red || !h->d_snap || !h->d_status || !h->mirror ||
+      !h->d_codes || !h->d_order || !h->d_red || !h->d_red_part || !h->d_snap || !h->d_status ||
+      !h->mirror ||
       (h->field_w && !h->wfield))
     return bad(WLBM_ERR_OOM, "wlbm_create: device allocation failed");
 
@@ -838,13 +842,12 @@ struct WindowCtl {
 static wlbm_status reduce_impl(wlbm_handle* h, double* out, const WindowCtl* win,
                                double* win_res) {
   const Geom& g = h->g;
-  wlbm_status st = h->cuda(
-      cudaMemsetAsync(h->d_red, 0, kReduceOut * sizeof(double), h->stream), "wlbm_reduce");
-  if (st != WLBM_OK) return st;
+  wlbm_status st = WLBM_OK;
   ReduceArgs a{};
   a.planes = h->planes; a.plane = g.plane; a.pitch = g.pitch; a.nx = g.nx; a.ny = g.ny;
   a.q = g.q; a.par = h->parity_mask(); a.e_cur = h->e[h->e_cur]; a.e_refp = h->ref_plane();
   a.w = h->w_dev(); a.sx = h->sx_dev(); a.sy = h->sy_dev(); a.out = h->d_red; a.scale = h->scale;
+  a.part = h->d_red_part;
   a.diff_mask = 0;
   for (int k = 0; k < 4; ++k)
     if (h->bc_kind[k] == WLBM_BC_ADIABATIC_DIFFUSE) a.diff_mask |= 1 << k;
@@ -865,7 +868,7 @@ static wlbm_status reduce_impl(wlbm_handle* h, double* out, const WindowCtl* win
     a.win_has_prev = win->has_prev ? 1 : 0;
     a.win_inv = 1.0 / win->count;
   }
-  ++h->launches;
+  h->launches += 2;
   st = h->cuda(launch_reduce(h->storage, a, h->stream), "wlbm_reduce");
   double tmp[kReduceOut];
   if (st == WLBM_OK)

@@ -219,14 +219,15 @@ struct ReduceArgs {
   const float* w;
   const float* sx;
   const float* sy;
-  double* out;           // [kReduceOut], zeroed before launch
+  double* out;           // [kReduceOut], written by the second stage
+  double* part;          // [kReduceBlocks][kReduceOut] per-block partials (scratch)
   double scale;
   int diff_mask;         // bit k: side k (x-, x+, y-, y+) is an adiabatic-diffuse wall
   // central band of columns band_x0 <= x < band_x0 + band_w (conductivity fit)
   int band_x0, band_w;
   double band_xbar;      // mean column of the band
-  // temperature residual: snap[y * nx + x] holds T - T_ref (float64) of the previous
-  // reduction; read where has_snap, always overwritten with the current field
+  // temperature residual: snap[y * nx + x] holds T - T_ref of the previous reduction (a
+  // float32 per-cell value kept in float64); read where has_snap, always overwritten
   double* snap;
   int has_snap;
   double e_ref, e_ref1, l_ref, theta;   // e_ref, e_ref + 1, ln(1 + 1/e_ref), theta
@@ -244,6 +245,7 @@ struct ReduceArgs {
 // combined with an unsigned max).
 constexpr int kReduceSums = 6;
 constexpr int kReduceOut = 8;
+constexpr int kReduceBlocks = 152 * 8;   // grid-stride blocks of the first stage
 
 struct StateArgs {
   void* planes;
