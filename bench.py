@@ -193,10 +193,21 @@ def run_batch(args):
                          "frac": achieved / peak, "traffic": None, "kernel": "k_step_*_batch",
                          "peak_kind": kind, "kernel_ms_per_launch": per_launch},
             "gpu_launches": int(l1 - l0)}
-    print(json.dumps(line), flush=True)
+    print(json.dumps(finite_or_none(line)), flush=True)
     if world > 1:
         tdist.destroy_process_group()
     return 0
+
+
+def finite_or_none(x):
+    """The JSON line carries no NaN or infinity (not JSON): such values become null."""
+    if isinstance(x, float) and not math.isfinite(x):
+        return None
+    if isinstance(x, dict):
+        return {k: finite_or_none(v) for k, v in x.items()}
+    if isinstance(x, (list, tuple)):
+        return [finite_or_none(v) for v in x]
+    return x
 
 
 def run_with_reductions(h, steps, every):
@@ -357,7 +368,7 @@ def run_reference(args):
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
-    print(json.dumps(line), flush=True)
+    print(json.dumps(finite_or_none(line)), flush=True)
     return 0
 
 
@@ -524,7 +535,7 @@ def main():
             line["clocks"] = clk
         if not args.no_extras:
             line["cpu_baseline"] = cpu_baseline(cfg)
-        print(json.dumps(line), flush=True)
+        print(json.dumps(finite_or_none(line)), flush=True)
     if world > 1:
         dist.destroy_process_group()
     return 0

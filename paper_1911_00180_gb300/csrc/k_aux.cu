@@ -89,7 +89,8 @@ __device__ __forceinline__ void wall_store(T* p, float d, float wi, bool ref, fl
 }
 
 // One ghost cell by one warp, lanes over the directions (vertical walls and corners).
-template <typename T>
+// SPEC: the launch has a segment with specularity > 0 (else that code is not compiled in).
+template <typename T, bool SPEC>
 __device__ __forceinline__ void walls_cell(const WallArgs& a, const WallSmem& sm,
                                            float* e_ref, const WallSeg& g, int idx, int lane) {
   const int64_t off = int64_t(g.r0 + idx * g.dr) * a.pitch + (g.c0 + idx * g.dc);
@@ -121,7 +122,7 @@ __device__ __forceinline__ void walls_cell(const WallArgs& a, const WallSmem& sm
       if (i < a.q && sm.rho[i] == 0.f) part += val[u];
     }
     const float A = warp_sum(part);
-    if (g.spec > 0.f) {
+    if (SPEC && g.spec > 0.f) {
       // inward directions first (they read their mirrors' outward values), then the rest
       const float p = g.spec, Ad = (1.f - g.spec) * A;
 #pragma unroll
@@ -155,7 +156,7 @@ __device__ __forceinline__ void walls_cell(const WallArgs& a, const WallSmem& sm
   for (int i = lane; i < a.q; i += 32)
     if (sm.rho[i] == 0.f) part += wall_load(ptr(i), sm.w[i], ref, R, a.scale);
   const float A = warp_sum(part);
-  if (g.spec > 0.f) {
+  if (SPEC && g.spec > 0.f) {
     const float p = g.spec, Ad = (1.f - g.spec) * A;
     for (int i = lane; i < a.q; i += 32) {
       if (sm.rho[i] == 0.f) continue;
@@ -179,7 +180,7 @@ __device__ __forceinline__ void walls_cell(const WallArgs& a, const WallSmem& sm
   }
 }
 
-template <typename T>
+template <typename T, bool SPEC>
 __device__ __forceinline__ void walls_chunk(const WallArgs& a, const uint8_t* codes,
                                             float* e_ref, int chunk, WallSmem& sm) {
   int c = 0;
@@ -194,12 +195,12 @@ __device__ __forceinline__ void walls_chunk(const WallArgs& a, const uint8_t* co
     sm.par[i] = uint8_t(a.tape ? 0 : (codes[i] >> 4) & 1);
     sm.w[i] = a.w[i];
     sm.rho[i] = diffuse ? rho[i] : 0.f;
-    sm.src[i] = diffuse && g.spec > 0.f ? mir[i] : int16_t(i);
+    if (SPEC) sm.src[i] = diffuse && g.spec > 0.f ? mir[i] : int16_t(i);
   }
   __syncthreads();
   if (!wall_seg_rowwise(g)) {                  // one warp per cell, lanes over directions
     const int cell = c * kWallCellsPerBlock + warp;
-    if (cell < g.count) walls_cell<T>(a, sm, e_ref, g, cell, lane);
+    if (cell < g.count) walls_cell<T, SPEC>(a, sm, e_ref, g, cell, lane);
     return;
   }
   const int idx = c * 32 + lane;
@@ -240,7 +241,7 @@ __device__ __forceinline__ void walls_chunk(const WallArgs& a, const uint8_t* co
     float A = 0.f;
 #pragma unroll
     for (int k = 0; k < kWallWarps; ++k) A += sm.part[k * 32 + lane];
-    if (g.spec > 0.f) {            // uniform over the block (one segment)
+    if (SPEC && g.spec > 0.f) {    // uniform over the block (one segment)
       // inward directions first (they read their mirrors' outward values), then the rest
       const float p = g.spec, Ad = (1.f - g.spec) * A;
       if (on) {
@@ -285,7 +286,7 @@ __device__ __forceinline__ void walls_chunk(const WallArgs& a, const uint8_t* co
   float A = 0.f;
 #pragma unroll
   for (int k = 0; k < kWallWarps; ++k) A += sm.part[k * 32 + lane];
-  if (g.spec > 0.f) {
+  if (SPEC && g.spec > 0.f) {
     const float p = g.spec, Ad = (1.f - g.spec) * A;
     if (on) {
       for (int i = warp; i < a.q; i += kWallWarps) {
@@ -315,15 +316,15 @@ __device__ __forceinline__ void walls_chunk(const WallArgs& a, const uint8_t* co
   }
 }
 
-template <typename T>
+template <typename T, bool SPEC>
 __global__ void __launch_bounds__(32 * kWallWarps) k_walls(const WallArgs a) {
   __shared__ WallSmem sm;
-  walls_chunk<T>(a, a.codes, a.e_ref, int(blockIdx.x), sm);
+  walls_chunk<T, SPEC>(a, a.codes, a.e_ref, int(blockIdx.x), sm);
 }
 
 // Batched wall pass: block b belongs to the instance whose first_block is the largest one
 // <= b; codes and the reference-energy plane of step t come from the instance record.
-template <typename T>
+template <typename T, bool SPEC>
 __global__ void __launch_bounds__(32 * kWallWarps) k_walls_batch(const BatchWalls* B, int n,
                                                                   int t) {
   __shared__ WallSmem sm;
@@ -337,7 +338,7 @@ __global__ void __launch_bounds__(32 * kWallWarps) k_walls_batch(const BatchWall
   const BatchWalls& I = B[lo];
   const int cur = (I.phase + t) % I.n_e;
   float* e_ref = I.n_e == 3 ? I.e[(cur + 2) % 3] : nullptr;
-  walls_chunk<T>(I.w, I.codes + size_t(t) * I.w.q, e_ref, b - I.first_block, sm);
+  walls_chunk<T, SPEC>(I.w, I.codes + size_t(t) * I.w.q, e_ref, b - I.first_block, sm);
 }
 
 // Internal sources / radiation cells: one warp per cell, lanes over the directions.  With
@@ -680,7 +681,10 @@ template <typename T>
 cudaError_t walls_t(const WallArgs& a, cudaStream_t s) {
   const int chunks = wall_chunk_count(a.nseg, a.seg);
   if (chunks == 0) return cudaSuccess;
-  k_walls<T><<<chunks, 32 * kWallWarps, 0, s>>>(a);
+  if (a.any_spec)
+    k_walls<T, true><<<chunks, 32 * kWallWarps, 0, s>>>(a);
+  else
+    k_walls<T, false><<<chunks, 32 * kWallWarps, 0, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -697,12 +701,16 @@ cudaError_t periodic_t(const PeriodicArgs& a, cudaStream_t s) {
 }  // namespace
 
 cudaError_t launch_walls_batch(int storage, const BatchWalls* b, int n, int total_blocks, int t,
-                               cudaStream_t s) {
+                               bool any_spec, cudaStream_t s) {
   if (total_blocks <= 0) return cudaSuccess;
-  if (storage == WLBM_STORE_BF16_DEV)
-    k_walls_batch<__nv_bfloat16><<<total_blocks, 32 * kWallWarps, 0, s>>>(b, n, t);
-  else
-    k_walls_batch<float><<<total_blocks, 32 * kWallWarps, 0, s>>>(b, n, t);
+  const dim3 g{unsigned(total_blocks)}, blk{32 * kWallWarps};
+  if (storage == WLBM_STORE_BF16_DEV) {
+    if (any_spec) k_walls_batch<__nv_bfloat16, true><<<g, blk, 0, s>>>(b, n, t);
+    else k_walls_batch<__nv_bfloat16, false><<<g, blk, 0, s>>>(b, n, t);
+  } else {
+    if (any_spec) k_walls_batch<float, true><<<g, blk, 0, s>>>(b, n, t);
+    else k_walls_batch<float, false><<<g, blk, 0, s>>>(b, n, t);
+  }
   return cudaGetLastError();
 }
 

@@ -242,6 +242,9 @@ void wlbm_handle::build_wall_segments() {
     else
       push(1, cr[k], cc[k], 0, 0, WLBM_BC_ADIABATIC_DIFFUSE, 4 + k, xw);
   }
+  a.any_spec = 0;
+  for (int k = 0; k < a.nseg; ++k)
+    if (a.seg[k].spec > 0.f) a.any_spec = 1;
   a.planes = planes;
   a.plane = g.plane;
   a.pitch = g.pitch;
@@ -1713,9 +1716,12 @@ wlbm_status wlbm_batch_set_option(wlbm_batch* b, int32_t key, int64_t value) {
 static wlbm_status batch_enqueue(wlbm_batch* b, int count, bool profile) {
   const int n = int(b->h.size());
   wlbm_status st = WLBM_OK;
+  bool any_spec = false;
+  for (const wlbm_handle* x : b->h) any_spec = any_spec || x->walls.any_spec;
   for (int t = 0; t < count && st == WLBM_OK; ++t) {
     if (b->total_wall_blocks > 0) {
-      st = b->cuda(launch_walls_batch(b->storage, b->d_walls, n, b->total_wall_blocks, t, b->stream),
+      st = b->cuda(launch_walls_batch(b->storage, b->d_walls, n, b->total_wall_blocks, t,
+                                      any_spec, b->stream),
                    "wlbm_batch_step: walls");
       ++b->launches;
     }

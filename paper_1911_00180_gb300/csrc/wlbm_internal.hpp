@@ -129,6 +129,7 @@ struct WallArgs {
   const float* rho;      // [8][q] re-emission fractions (0 = collected direction)
   const int16_t* mirror; // [2][q] direction index with c_x (row 0) or c_y (row 1) flipped
   int tape;              // 1: all planes at `planes` (parity ignored)
+  int any_spec;          // a segment has specularity > 0 (selects the kernel with that path)
   WallSeg seg[kMaxSeg];
 };
 
@@ -366,7 +367,7 @@ cudaError_t launch_step_batch(int storage, int variant, const BatchInst* insts, 
                               int total_tiles, int t, cudaStream_t s);
 int wall_blocks(const WallArgs& a);   // blocks of the wall pass of one grid (32 cells each)
 cudaError_t launch_walls_batch(int storage, const BatchWalls* b, int n, int total_blocks, int t,
-                               cudaStream_t s);
+                               bool any_spec, cudaStream_t s);
 cudaError_t launch_walls(int storage, const WallArgs& a, cudaStream_t s);
 cudaError_t launch_periodic(int storage, const PeriodicArgs& a, cudaStream_t s);
 cudaError_t launch_init(int storage, const InitArgs& a, cudaStream_t s);
