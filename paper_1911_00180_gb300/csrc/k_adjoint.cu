@@ -205,9 +205,9 @@ __global__ void k_periodic_T_y(float* planes, int64_t plane, int pitch, int nx, 
   base[int64_t(ny + 2) * pitch] = 0.f;
 }
 
-// Transpose of the wall pass, on the same blocks as k_walls: along horizontal walls lane =
-// ghost cell and warp w = directions w, w + kWallWarpsT, ..., per-cell sums combining over
-// the warps in a fixed order; vertical walls and corners one warp per cell.  Isothermal
+// Transpose of the wall pass, on the same blocks as k_walls: along horizontal walls lane l =
+// ghost cells 4l .. 4l+3 of a 128-cell chunk and warp w = directions w, w + kWallWarpsT,
+// ..., per-cell sums combining over the warps in a fixed order; vertical walls and corners one warp per cell.  Isothermal
 // cells send sum_i w_i l_i to the wall temperature and zero l; diffuse cells give every
 // collected direction sum_k rho_k l_k.
 constexpr int kWallWarpsT = 8;
@@ -252,7 +252,7 @@ __device__ __forceinline__ float walls_T_cell(const WallArgs& wa, const WallSeg&
 
 __global__ void __launch_bounds__(32 * kWallWarpsT) k_walls_T(const WallArgs wa, float* lam,
                                                                double* gtw) {
-  __shared__ float part_s[kWallWarpsT * 32];
+  __shared__ float part_s[kWallWarpsT * 32 * 4];
   int c = 0;
   const int s = wall_chunk_segment(wa.nseg, wa.seg, int(blockIdx.x), &c);
   if (s >= wa.nseg) return;
@@ -278,39 +278,58 @@ __global__ void __launch_bounds__(32 * kWallWarpsT) k_walls_T(const WallArgs wa,
     }
     return;
   }
-  const int idx = c * 32 + lane;
-  const bool on = wanted(idx);
-  const int64_t off = on ? int64_t(g.r0 + idx * g.dr) * wa.pitch + (g.c0 + idx * g.dc) : 0;
+  // horizontal walls: four consecutive cells per lane (the blocks of k_walls)
+  const int idx0 = c * kWallChunk + 4 * lane;
+  bool on[4];
+  int64_t off[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int idx = idx0 + j;
+    on[j] = wanted(idx);
+    off[j] = on[j] ? int64_t(g.r0 + idx * g.dr) * wa.pitch + (g.c0 + idx * g.dc) : 0;
+  }
   const float* rho = wa.rho + int64_t(g.table) * wa.q;
-  float part = 0.f;
-  if (on) {
-#pragma unroll 4
+  float part[4] = {0.f, 0.f, 0.f, 0.f};
+  if (on[0] || on[1] || on[2] || on[3]) {
     for (int i = warp; i < wa.q; i += kWallWarpsT) {
-      float* p = lam + int64_t(i) * wa.plane + off;
-      if (iso) {
-        part = fmaf(wa.w[i], *p, part);
-        *p = 0.f;
-      } else if (rho[i] != 0.f) {
-        part = fmaf(rho[i], *p, part);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        if (!on[j]) continue;
+        float* p = lam + int64_t(i) * wa.plane + off[j];
+        if (iso) {
+          part[j] = fmaf(wa.w[i], *p, part[j]);
+          *p = 0.f;
+        } else if (rho[i] != 0.f) {
+          part[j] = fmaf(rho[i], *p, part[j]);
+        }
       }
     }
   }
-  part_s[warp * 32 + lane] = part;
-  __syncthreads();
-  float S = 0.f;
 #pragma unroll
-  for (int k = 0; k < kWallWarpsT; ++k) S += part_s[k * 32 + lane];
+  for (int j = 0; j < 4; ++j) part_s[(warp * 32 + lane) * 4 + j] = part[j];
+  __syncthreads();
+  float S[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+  for (int k = 0; k < kWallWarpsT; ++k)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) S[j] += part_s[(k * 32 + lane) * 4 + j];
   if (iso) {
     if (warp == 0) {
-      const float tot = warp_sum(on ? S : 0.f);
+      float mine = 0.f;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) mine += on[j] ? S[j] : 0.f;
+      const float tot = warp_sum(mine);
       if (lane == 0) atomicAdd(gtw + g.wall, double(tot));
     }
     return;
   }
-  if (!on) return;
   const int16_t* mir = wa.mirror + int64_t(g.mirror) * wa.q;
-  for (int i = warp; i < wa.q; i += kWallWarpsT)
-    if (rho[i] == 0.f) lam[int64_t(i) * wa.plane + off] = collected_T(wa, g, mir, lam, off, i, S);
+  for (int i = warp; i < wa.q; i += kWallWarpsT) {
+    if (rho[i] != 0.f) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (on[j]) lam[int64_t(i) * wa.plane + off[j]] = collected_T(wa, g, mir, lam, off[j], i, S[j]);
+  }
 }
 
 // l^N_i(x) = dJ/dT(x) * dT/dE at the final local energy (E = sum_i d_i, Eq. pseudo-T)

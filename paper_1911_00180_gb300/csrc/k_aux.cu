@@ -49,22 +49,22 @@ __device__ __forceinline__ float dev_store(T* p, float d, float wi, const float*
   return fmaf(Elem<T>::st(p, __fmul_rn(__fsub_rn(d, r), inv_scale)), scale, r);
 }
 
-// Wall pass.  Horizontal walls: a block of kWallWarps warps takes a chunk of 32
-// consecutive ghost cells, lane l the cell l of it (consecutive cells are consecutive in
-// memory, so every per-direction access of a warp is one coalesced row piece), and warp w
-// the directions w, w + kWallWarps, ...; diffuse walls add the collected directions per
-// warp, then over the warps in a fixed order.  Vertical walls and corners: one warp per
-// cell (walls_cell), which keeps many warps busy on the few, strided cells.
+// Wall pass.  Horizontal walls: a block of kWallWarps warps takes a chunk of 128
+// consecutive ghost cells, lane l the four cells 4l .. 4l+3 of it (one 16-byte float32 or
+// 8-byte bfloat16 access per direction: a warp moves 512 or 256 contiguous bytes of a row
+// at once), and warp w the directions w, w + kWallWarps, ...; diffuse walls add the
+// collected directions per warp, then over the warps in a fixed order, and re-read the
+// values (from L2) to store them.  Vertical walls and corners: one warp per cell
+// (walls_cell), which keeps many warps busy on the few, strided cells.
 constexpr int kWallWarps = 8;
-constexpr int kHoldChunk = 16;   // values per lane held at once along horizontal walls
 constexpr int kHoldCell = 8;     // values per lane held at once by a warp on one cell
-static_assert(kWallChunk == 32, "one lane per ghost cell of a chunk");
+static_assert(kWallChunk == 128, "four consecutive ghost cells per lane of a chunk");
 static_assert(kWallCellsPerBlock == kWallWarps, "one warp per cell of a block");
 
 // Per-direction data of a wall block in shared memory: plane parity of the step, w_i and
 // the segment's re-emission fractions, staged once so that no value load waits on them.
 struct WallSmem {
-  float part[kWallWarps * 32];
+  float part[kWallWarps * 32 * 4];   // per warp, lane and lane cell: collected energy
   float w[kMaxQ];
   float rho[kMaxQ];
   int16_t src[kMaxQ];    // mirror direction at this wall (specular segments)
@@ -86,6 +86,56 @@ __device__ __forceinline__ void wall_store(T* p, float d, float wi, bool ref, fl
     return;
   }
   Elem<T>::st(p, __fmul_rn(__fsub_rn(d, __fmul_rn(wi, R)), inv_scale));
+}
+
+// Four consecutive stored values of a horizontal wall (one 16-byte float32 or 8-byte
+// bfloat16 access; the frame's pitch keeps such groups aligned and inside the row).
+__device__ __forceinline__ void ld4_raw(const float* p, float (&v)[4]) {
+  const float4 f = *reinterpret_cast<const float4*>(p);
+  v[0] = f.x; v[1] = f.y; v[2] = f.z; v[3] = f.w;
+}
+__device__ __forceinline__ void ld4_raw(const __nv_bfloat16* p, float (&v)[4]) {
+  const uint2 u = *reinterpret_cast<const uint2*>(p);
+  v[0] = __uint_as_float(u.x << 16); v[1] = __uint_as_float(u.x & 0xffff0000u);
+  v[2] = __uint_as_float(u.y << 16); v[3] = __uint_as_float(u.y & 0xffff0000u);
+}
+// Store the first nv of four raw values (all four in one access when nv == 4).
+__device__ __forceinline__ void st4_raw(float* p, const float (&v)[4], int nv) {
+  if (nv == 4) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  } else {
+    for (int j = 0; j < nv; ++j) p[j] = v[j];
+  }
+}
+__device__ __forceinline__ void st4_raw(__nv_bfloat16* p, const float (&v)[4], int nv) {
+  if (nv == 4) {
+    const __nv_bfloat162 a = __floats2bfloat162_rn(v[0], v[1]);
+    const __nv_bfloat162 b = __floats2bfloat162_rn(v[2], v[3]);
+    *reinterpret_cast<uint2*>(p) = make_uint2(*reinterpret_cast<const uint32_t*>(&a),
+                                              *reinterpret_cast<const uint32_t*>(&b));
+  } else {
+    for (int j = 0; j < nv; ++j) Elem<__nv_bfloat16>::st(p + j, v[j]);
+  }
+}
+// Deviations of four cells (cell references R) and the raw values that store deviations d:
+// the same rounded operations as wall_load / wall_store.
+template <typename T>
+__device__ __forceinline__ void ld4_dev(const T* p, float wi, bool ref, const float (&R)[4],
+                                        float scale, float (&d)[4]) {
+  ld4_raw(p, d);
+  if (ref) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) d[j] = fmaf(d[j], scale, __fmul_rn(wi, R[j]));
+  }
+}
+template <typename T>
+__device__ __forceinline__ void st4_dev(T* p, const float (&d)[4], float wi, bool ref,
+                                        const float (&R)[4], float inv_scale, int nv) {
+  float v[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+    v[j] = ref ? __fmul_rn(__fsub_rn(d[j], __fmul_rn(wi, R[j])), inv_scale) : d[j];
+  st4_raw(p, v, nv);
 }
 
 // One ghost cell by one warp, lanes over the directions (vertical walls and corners).
@@ -203,106 +253,84 @@ __device__ __forceinline__ void walls_chunk(const WallArgs& a, const uint8_t* co
     if (cell < g.count) walls_cell<T, SPEC>(a, sm, e_ref, g, cell, lane);
     return;
   }
-  const int idx = c * 32 + lane;
-  const bool on = idx < g.count;
-  const int64_t off = on ? int64_t(g.r0 + idx * g.dr) * a.pitch + (g.c0 + idx * g.dc) : 0;
+  // horizontal wall (dr = 0, dc = 1): the block takes cells c*128 .. c*128+127 of the
+  // segment; lane owns four consecutive cells, warp w the directions w, w + kWallWarps, ...
+  const int idx0 = c * kWallChunk + 4 * lane;
+  const int nv = min(4, g.count - idx0);          // this lane's valid cells (<= 0: none)
+  const bool on = nv > 0;
+  const int64_t off = on ? int64_t(g.r0) * a.pitch + (g.c0 + idx0) : 0;
   T* planes = static_cast<T*>(a.planes);
   auto ptr = [&](int i) { return planes + int64_t(sm.par[i] * a.q + i) * a.plane + off; };
+  const bool ref = e_ref != nullptr;
+  float R[4] = {0.f, 0.f, 0.f, 0.f};
   if (!diffuse) {
     if (!on) return;
-    if (e_ref) {
+    float v[4];
+    if (ref) {
       // bfloat16: make the wall's own equilibrium the reference of the cell, so the
       // stored values are exactly zero and decode to w_i (e_eq(T_w) - e_ref) unrounded
-      for (int i = warp; i < a.q; i += kWallWarps) Elem<T>::st(ptr(i), 0.f);
-      if (warp == 0) e_ref[off] = g.iso;
+      const float z[4] = {0.f, 0.f, 0.f, 0.f};
+      for (int i = warp; i < a.q; i += kWallWarps) st4_raw(ptr(i), z, nv);
+      if (warp == 0)
+        for (int j = 0; j < nv; ++j) e_ref[off + j] = g.iso;
     } else {
-      for (int i = warp; i < a.q; i += kWallWarps) Elem<T>::st(ptr(i), sm.w[i] * g.iso);
+      for (int i = warp; i < a.q; i += kWallWarps) {
+        const float x = sm.w[i] * g.iso;
+        v[0] = x; v[1] = x; v[2] = x; v[3] = x;
+        st4_raw(ptr(i), v, nv);
+      }
     }
     return;
   }
-  const bool ref = e_ref != nullptr;
-  const float R = ref && on ? e_ref[off] : 0.f;
-  if (a.q <= kWallWarps * kHoldChunk) {
-    // every value of the warp's directions in flight at once: one load round, one store
-    float val[kHoldChunk];
-#pragma unroll
-    for (int u = 0; u < kHoldChunk; ++u) {
-      const int i = warp + kWallWarps * u;
-      val[u] = on && i < a.q ? wall_load(ptr(i), sm.w[i], ref, R, a.scale) : 0.f;
-    }
-    float part = 0.f;
-#pragma unroll
-    for (int u = 0; u < kHoldChunk; ++u) {
-      const int i = warp + kWallWarps * u;
-      if (i < a.q && sm.rho[i] == 0.f) part += val[u];
-    }
-    sm.part[warp * 32 + lane] = part;
-    __syncthreads();
-    float A = 0.f;
-#pragma unroll
-    for (int k = 0; k < kWallWarps; ++k) A += sm.part[k * 32 + lane];
-    if (SPEC && g.spec > 0.f) {    // uniform over the block (one segment)
-      // inward directions first (they read their mirrors' outward values), then the rest
-      const float p = g.spec, Ad = (1.f - g.spec) * A;
-      if (on) {
-#pragma unroll
-        for (int u = 0; u < kHoldChunk; ++u) {
-          const int i = warp + kWallWarps * u;
-          if (i >= a.q || sm.rho[i] == 0.f) continue;
-          const int j = sm.src[i];
-          const float m = wall_load(ptr(j), sm.w[j], ref, R, a.scale);
-          wall_store(ptr(i), fmaf(Ad, sm.rho[i], fmaf(p, m, val[u])), sm.w[i], ref, R,
-                     a.inv_scale);
-        }
-      }
-      __syncthreads();
-      if (!on) return;
-#pragma unroll
-      for (int u = 0; u < kHoldChunk; ++u) {
-        const int i = warp + kWallWarps * u;
-        if (i >= a.q || sm.rho[i] != 0.f) continue;
-        wall_store(ptr(i), sm.src[i] == i ? p * val[u] : 0.f, sm.w[i], ref, R, a.inv_scale);
-      }
-      return;
-    }
-    if (!on) return;
-#pragma unroll
-    for (int u = 0; u < kHoldChunk; ++u) {
-      const int i = warp + kWallWarps * u;
-      if (i >= a.q) continue;
-      const float d = sm.rho[i] == 0.f ? 0.f : fmaf(A, sm.rho[i], val[u]);
-      wall_store(ptr(i), d, sm.w[i], ref, R, a.inv_scale);
-    }
-    return;
+  if (ref && on) {
+    const float4 r = *reinterpret_cast<const float4*>(e_ref + off);
+    R[0] = r.x; R[1] = r.y; R[2] = r.z; R[3] = r.w;
   }
-  float part = 0.f;
+  // collected energy per cell: the non-inward directions of this warp, then all warps
+  float part[4] = {0.f, 0.f, 0.f, 0.f};
   if (on) {
 #pragma unroll 4
-    for (int i = warp; i < a.q; i += kWallWarps)
-      if (sm.rho[i] == 0.f) part += wall_load(ptr(i), sm.w[i], ref, R, a.scale);
-  }
-  sm.part[warp * 32 + lane] = part;
-  __syncthreads();
-  float A = 0.f;
+    for (int i = warp; i < a.q; i += kWallWarps) {
+      if (sm.rho[i] != 0.f) continue;
+      float d[4];
+      ld4_dev(ptr(i), sm.w[i], ref, R, a.scale, d);
 #pragma unroll
-  for (int k = 0; k < kWallWarps; ++k) A += sm.part[k * 32 + lane];
-  if (SPEC && g.spec > 0.f) {
-    const float p = g.spec, Ad = (1.f - g.spec) * A;
+      for (int j = 0; j < 4; ++j) part[j] += d[j];
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) sm.part[(warp * 32 + lane) * 4 + j] = part[j];
+  __syncthreads();
+  float A[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+  for (int k = 0; k < kWallWarps; ++k)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) A[j] += sm.part[(k * 32 + lane) * 4 + j];
+  if (SPEC && g.spec > 0.f) {      // uniform over the block (one segment)
+    // inward directions first (they read their mirrors' outward values), then the rest
+    const float p = g.spec;
     if (on) {
       for (int i = warp; i < a.q; i += kWallWarps) {
         if (sm.rho[i] == 0.f) continue;
-        const int j = sm.src[i];
-        const float m = wall_load(ptr(j), sm.w[j], ref, R, a.scale);
-        const float v = wall_load(ptr(i), sm.w[i], ref, R, a.scale);
-        wall_store(ptr(i), fmaf(Ad, sm.rho[i], fmaf(p, m, v)), sm.w[i], ref, R, a.inv_scale);
+        float v[4], m[4], d[4];
+        ld4_dev(ptr(i), sm.w[i], ref, R, a.scale, v);
+        ld4_dev(ptr(sm.src[i]), sm.w[sm.src[i]], ref, R, a.scale, m);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) d[j] = fmaf((1.f - p) * A[j], sm.rho[i], fmaf(p, m[j], v[j]));
+        st4_dev(ptr(i), d, sm.w[i], ref, R, a.inv_scale, nv);
       }
     }
     __syncthreads();
     if (!on) return;
     for (int i = warp; i < a.q; i += kWallWarps) {
       if (sm.rho[i] != 0.f) continue;
-      const float d = sm.src[i] == i ? p * wall_load(ptr(i), sm.w[i], ref, R, a.scale) : 0.f;
-      wall_store(ptr(i), d, sm.w[i], ref, R, a.inv_scale);
+      float d[4] = {0.f, 0.f, 0.f, 0.f};
+      if (sm.src[i] == i) {
+        ld4_dev(ptr(i), sm.w[i], ref, R, a.scale, d);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) d[j] = p * d[j];
+      }
+      st4_dev(ptr(i), d, sm.w[i], ref, R, a.inv_scale, nv);
     }
     return;
   }
@@ -310,9 +338,13 @@ __device__ __forceinline__ void walls_chunk(const WallArgs& a, const uint8_t* co
 #pragma unroll 4
   for (int i = warp; i < a.q; i += kWallWarps) {
     // collected directions are absorbed (0); the others receive their share of A
-    const float d = sm.rho[i] == 0.f
-                        ? 0.f : fmaf(A, sm.rho[i], wall_load(ptr(i), sm.w[i], ref, R, a.scale));
-    wall_store(ptr(i), d, sm.w[i], ref, R, a.inv_scale);
+    float d[4] = {0.f, 0.f, 0.f, 0.f};
+    if (sm.rho[i] != 0.f) {
+      ld4_dev(ptr(i), sm.w[i], ref, R, a.scale, d);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) d[j] = fmaf(A[j], sm.rho[i], d[j]);
+    }
+    st4_dev(ptr(i), d, sm.w[i], ref, R, a.inv_scale, nv);
   }
 }
 
@@ -322,23 +354,28 @@ __global__ void __launch_bounds__(32 * kWallWarps) k_walls(const WallArgs a) {
   walls_chunk<T, SPEC>(a, a.codes, a.e_ref, int(blockIdx.x), sm);
 }
 
-// Batched wall pass: block b belongs to the instance whose first_block is the largest one
-// <= b; codes and the reference-energy plane of step t come from the instance record.
+// Batched wall pass: block b belongs to instance block_inst[b] (a host-built table: one
+// load instead of a search); the instance's wall arguments are copied to shared memory
+// once, so the segment lookup and the per-direction staging read no global memory chain.
+// Codes and the reference-energy plane of step t come from the instance record.
 template <typename T, bool SPEC>
-__global__ void __launch_bounds__(32 * kWallWarps) k_walls_batch(const BatchWalls* B, int n,
-                                                                  int t) {
+__global__ void __launch_bounds__(32 * kWallWarps) k_walls_batch(const BatchWalls* B,
+                                                                  const int* block_inst, int t) {
   __shared__ WallSmem sm;
+  __shared__ __align__(16) WallArgs wa;
   const int b = int(blockIdx.x);
-  int lo = 0, hi = n - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (B[mid].first_block <= b) lo = mid;
-    else hi = mid - 1;
-  }
-  const BatchWalls& I = B[lo];
+  const BatchWalls& I = B[block_inst[b]];
+  static_assert(sizeof(WallArgs) % 4 == 0, "copied as 32-bit words");
+  const int* src = reinterpret_cast<const int*>(&I.w);
+  int* dst = reinterpret_cast<int*>(&wa);
+  for (int i = int(threadIdx.x); i < int(sizeof(WallArgs) / 4); i += int(blockDim.x))
+    dst[i] = src[i];
   const int cur = (I.phase + t) % I.n_e;
   float* e_ref = I.n_e == 3 ? I.e[(cur + 2) % 3] : nullptr;
-  walls_chunk<T, SPEC>(I.w, I.codes + size_t(t) * I.w.q, e_ref, b - I.first_block, sm);
+  const uint8_t* codes = I.codes + size_t(t) * I.w.q;
+  const int chunk = b - I.first_block;
+  __syncthreads();
+  walls_chunk<T, SPEC>(wa, codes, e_ref, chunk, sm);
 }
 
 // Internal sources / radiation cells: one warp per cell, lanes over the directions.  With
@@ -700,16 +737,16 @@ cudaError_t periodic_t(const PeriodicArgs& a, cudaStream_t s) {
 
 }  // namespace
 
-cudaError_t launch_walls_batch(int storage, const BatchWalls* b, int n, int total_blocks, int t,
-                               bool any_spec, cudaStream_t s) {
+cudaError_t launch_walls_batch(int storage, const BatchWalls* b, const int* block_inst,
+                               int total_blocks, int t, bool any_spec, cudaStream_t s) {
   if (total_blocks <= 0) return cudaSuccess;
   const dim3 g{unsigned(total_blocks)}, blk{32 * kWallWarps};
   if (storage == WLBM_STORE_BF16_DEV) {
-    if (any_spec) k_walls_batch<__nv_bfloat16, true><<<g, blk, 0, s>>>(b, n, t);
-    else k_walls_batch<__nv_bfloat16, false><<<g, blk, 0, s>>>(b, n, t);
+    if (any_spec) k_walls_batch<__nv_bfloat16, true><<<g, blk, 0, s>>>(b, block_inst, t);
+    else k_walls_batch<__nv_bfloat16, false><<<g, blk, 0, s>>>(b, block_inst, t);
   } else {
-    if (any_spec) k_walls_batch<float, true><<<g, blk, 0, s>>>(b, n, t);
-    else k_walls_batch<float, false><<<g, blk, 0, s>>>(b, n, t);
+    if (any_spec) k_walls_batch<float, true><<<g, blk, 0, s>>>(b, block_inst, t);
+    else k_walls_batch<float, false><<<g, blk, 0, s>>>(b, block_inst, t);
   }
   return cudaGetLastError();
 }

@@ -1460,6 +1460,7 @@ struct wlbm_batch {
   std::vector<void*> owned;
   BatchInst* d_inst = nullptr;
   BatchWalls* d_walls = nullptr;
+  int* d_wall_inst = nullptr;   // [total_wall_blocks] instance of every wall block
   uint8_t* d_codes = nullptr;
   uint16_t* d_order = nullptr;      // [instance][t][q + 17] kind-sorted directions
   unsigned char* d_tmaps = nullptr; // [instance] 128-byte CUtensorMaps (variant 3)
@@ -1617,8 +1618,19 @@ wlbm_status wlbm_batch_create(int32_t n, const wlbm_grid* grids, const float* co
   b->d_tmaps = static_cast<unsigned char*>(b->dev_alloc(size_t(n) * 128));
   b->d_inst = static_cast<BatchInst*>(b->dev_alloc(sizeof(BatchInst) * n));
   b->d_walls = static_cast<BatchWalls*>(b->dev_alloc(sizeof(BatchWalls) * n));
-  if (!b->d_codes || !b->d_order || !b->d_tmaps || !b->d_inst || !b->d_walls)
+  // the wall segments of every instance are fixed: the block -> instance table once
+  std::vector<int> wall_inst;
+  for (int k = 0; k < n; ++k)
+    wall_inst.insert(wall_inst.end(), size_t(wall_blocks(b->h[k]->walls)), k);
+  if (!wall_inst.empty())
+    b->d_wall_inst = static_cast<int*>(b->dev_alloc(wall_inst.size() * sizeof(int)));
+  if (!b->d_codes || !b->d_order || !b->d_tmaps || !b->d_inst || !b->d_walls ||
+      (!wall_inst.empty() && !b->d_wall_inst))
     return bad(WLBM_ERR_OOM, "wlbm_batch_create: device allocation failed");
+  if (!wall_inst.empty() &&
+      cudaMemcpy(b->d_wall_inst, wall_inst.data(), wall_inst.size() * sizeof(int),
+                 cudaMemcpyHostToDevice) != cudaSuccess)
+    return bad(WLBM_ERR_CUDA, "wlbm_batch_create: upload of the wall block table failed");
   cudaError_t e = cudaHostAlloc(reinterpret_cast<void**>(&b->h_codes), b->code_bytes,
                                 cudaHostAllocDefault);
   if (e == cudaSuccess)
@@ -1720,8 +1732,8 @@ static wlbm_status batch_enqueue(wlbm_batch* b, int count, bool profile) {
   for (const wlbm_handle* x : b->h) any_spec = any_spec || x->walls.any_spec;
   for (int t = 0; t < count && st == WLBM_OK; ++t) {
     if (b->total_wall_blocks > 0) {
-      st = b->cuda(launch_walls_batch(b->storage, b->d_walls, n, b->total_wall_blocks, t,
-                                      any_spec, b->stream),
+      st = b->cuda(launch_walls_batch(b->storage, b->d_walls, b->d_wall_inst,
+                                      b->total_wall_blocks, t, any_spec, b->stream),
                    "wlbm_batch_step: walls");
       ++b->launches;
     }

@@ -134,10 +134,10 @@ struct WallArgs {
 };
 
 // Wall passes: a segment along a row (horizontal wall) is cut into chunks of
-// kWallChunk consecutive cells, one block each, lane = cell (consecutive cells are
-// consecutive in memory); other segments (vertical walls, corners) give every cell one
-// warp, lanes over the directions, kWallCellsPerBlock cells a block.
-constexpr int kWallChunk = 32;
+// kWallChunk consecutive cells, one block each, four consecutive cells per lane (one
+// vector access per direction); other segments (vertical walls, corners) give every cell
+// one warp, lanes over the directions, kWallCellsPerBlock cells a block.
+constexpr int kWallChunk = 128;
 constexpr int kWallCellsPerBlock = 8;
 #ifdef __CUDACC__
 __host__ __device__ inline bool wall_seg_rowwise(const WallSeg& g) {
@@ -366,8 +366,8 @@ int step_tile_width(int storage, int variant);
 cudaError_t launch_step_batch(int storage, int variant, const BatchInst* insts, int n,
                               int total_tiles, int t, cudaStream_t s);
 int wall_blocks(const WallArgs& a);   // blocks of the wall pass of one grid (32 cells each)
-cudaError_t launch_walls_batch(int storage, const BatchWalls* b, int n, int total_blocks, int t,
-                               bool any_spec, cudaStream_t s);
+cudaError_t launch_walls_batch(int storage, const BatchWalls* b, const int* block_inst,
+                               int total_blocks, int t, bool any_spec, cudaStream_t s);
 cudaError_t launch_walls(int storage, const WallArgs& a, cudaStream_t s);
 cudaError_t launch_periodic(int storage, const PeriodicArgs& a, cudaStream_t s);
 cudaError_t launch_init(int storage, const InitArgs& a, cudaStream_t s);
