@@ -322,6 +322,19 @@ class WormLBM:
             qx, qy = self.speed * qx, self.speed * qy
         return qx, qy
 
+    def mean_moments(self, nsteps):
+        """Advance nsteps steps and return the means of T - T_ref, q_x and q_y over the
+        nsteps states reached (the running average of the flux over 10 steps of Sec. 4.3,
+        which smooths the TAS fluctuations)."""
+        acc_t = acc_x = acc_y = 0.0
+        for _ in range(nsteps):
+            self.step()
+            qx, qy = self.heat_flux()
+            acc_t = acc_t + self.temperature_dev()
+            acc_x = acc_x + qx
+            acc_y = acc_y + qy
+        return acc_t / nsteps, acc_x / nsteps, acc_y / nsteps
+
     def total_energy(self, include_frame=False):
         """Sum of E - e_ref over the interior, or over the interior plus the ghost cells
         that hold energy of the system: those of adiabatic (diffuse or specular) walls (a

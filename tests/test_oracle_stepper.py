@@ -262,3 +262,32 @@ def test_diffusive_limit_at_lower_speed(speed):
     e16 = d16 / (16 * speed / 3) - 1
     e32 = d32 / (32 * speed / 3) - 1
     assert 0.3 < e32 / e16 < 0.7                       # first order in 1/Lambda
+
+
+def test_mean_moments_of_a_ballistic_run():
+    """Sec. 4.3 averages the flux over 10 steps: at W = 0 on a periodic grid the mean over
+    the next n states equals the mean of the exactly translated fields."""
+    nx = ny = 18
+    q, n0, n = 16, 3, 10
+    yy, xx = np.mgrid[0:ny, 0:nx]
+    dT0 = np.exp(-((xx - 8.3) ** 2 + (yy - 9.1) ** 2) / 8.0)
+    m = WormLBM(nx, ny, q, 1.0, w_field=0.0)
+    m.init_temperature(dT0)
+    m.step(n0)
+    mt, mqx, mqy = m.mean_moments(n)
+    e0 = L.e_eq(300.0 + dT0, m.theta) - m.e_ref
+    sched = L.TasSchedule(q)
+    u = L.unit_vectors(L.ring_directions(q))
+    st = sx = sy = 0.0
+    for k in range(1, n0 + n + 1):
+        sched.advance()
+        if k <= n0:
+            continue
+        p = sched.displacement()
+        planes = [m.w[i] * np.roll(e0, (p[i][1], p[i][0]), axis=(0, 1)) for i in range(q)]
+        st = st + L.temperature(m.e_ref + sum(planes), m.theta) - 300.0
+        sx = sx + sum(u[i, 0] * planes[i] for i in range(q))
+        sy = sy + sum(u[i, 1] * planes[i] for i in range(q))
+    np.testing.assert_allclose(mt, st / n, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(mqx, sx / n, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(mqy, sy / n, rtol=0, atol=1e-15)
