@@ -134,6 +134,13 @@ int64_t wlbm_step_count(const wlbm_handle* h);
  * current state.  Each output is device nx*ny float32, or NULL to skip it. */
 wlbm_status wlbm_moments(wlbm_handle* h, float* dT, float* qx, float* qy);
 
+/* wlbm_moments_mean: advance n >= 1 steps and write the means of the moments of
+ * wlbm_moments over the n states reached (the running average over 10 steps of Sec. 4.3,
+ * which smooths the step-to-step fluctuations of the TAS pauses).  Same outputs as
+ * wlbm_moments (device nx*ny float32 each, or NULL); each term is weighted by 1/n and
+ * added in float32 in step order. */
+wlbm_status wlbm_moments_mean(wlbm_handle* h, int32_t n, float* dT, float* qx, float* qy);
+
 /* wlbm_reduce: float64 reductions over the current state, written to host
  * out[WLBM_REDUCE_N].  On the GPU each cell's sums over its directions and its temperature
  * are float32 (as in wlbm_moments: the stored values are float32 or coarser); the sums and

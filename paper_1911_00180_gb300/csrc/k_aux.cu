@@ -485,7 +485,8 @@ __global__ void k_moments(const MomentArgs a) {
     // T - T_ref = theta/L - theta/L_ref = -theta dL / (L_ref (L_ref + dL)).
     const float de = a.e_cur[off];
     const float dl = log1pf(de / a.e_ref1) - log1pf(de / a.e_ref);
-    a.dT[t] = -a.theta * dl / (a.l_ref * (a.l_ref + dl));
+    const float v = a.weight * (-a.theta * dl / (a.l_ref * (a.l_ref + dl)));
+    a.dT[t] = a.accumulate ? a.dT[t] + v : v;
   }
   if (a.qx || a.qy) {
     const T* planes = static_cast<const T*>(a.planes);
@@ -496,8 +497,9 @@ __global__ void k_moments(const MomentArgs a) {
       qx = fmaf(v, a.sx[i], qx);
       qy = fmaf(v, a.sy[i], qy);
     }
-    if (a.qx) a.qx[t] = qx * a.vg;
-    if (a.qy) a.qy[t] = qy * a.vg;
+    const float wx = a.weight * (qx * a.vg), wy = a.weight * (qy * a.vg);
+    if (a.qx) a.qx[t] = a.accumulate ? a.qx[t] + wx : wx;
+    if (a.qy) a.qy[t] = a.accumulate ? a.qy[t] + wy : wy;
   }
 }
 

@@ -805,9 +805,8 @@ wlbm_status wlbm_profile_read(wlbm_handle* h, double* step_ms, int64_t* step_lau
   return WLBM_OK;
 }
 
-wlbm_status wlbm_moments(wlbm_handle* h, float* dT, float* qx, float* qy) {
-  if (!h) return WLBM_ERR_INVALID_ARG;
-  if (!dT && !qx && !qy) return WLBM_OK;
+static wlbm_status moments_impl(wlbm_handle* h, float* dT, float* qx, float* qy, float weight,
+                                int accumulate) {
   const Geom& g = h->g;
   MomentArgs a{};
   a.planes = h->planes; a.plane = g.plane; a.pitch = g.pitch; a.nx = g.nx; a.ny = g.ny;
@@ -819,8 +818,28 @@ wlbm_status wlbm_moments(wlbm_handle* h, float* dT, float* qx, float* qy) {
   a.e_ref1 = float(h->e_eq_ref + 1.0);
   a.l_ref = float(std::log1p(1.0 / h->e_eq_ref));
   a.theta = float(h->theta);
+  a.weight = weight;
+  a.accumulate = accumulate;
   ++h->launches;
   return h->cuda(launch_moments(h->storage, a, h->stream), "wlbm_moments");
+}
+
+wlbm_status wlbm_moments(wlbm_handle* h, float* dT, float* qx, float* qy) {
+  if (!h) return WLBM_ERR_INVALID_ARG;
+  if (!dT && !qx && !qy) return WLBM_OK;
+  return moments_impl(h, dT, qx, qy, 1.f, 0);
+}
+
+wlbm_status wlbm_moments_mean(wlbm_handle* h, int32_t n, float* dT, float* qx, float* qy) {
+  if (!h) return WLBM_ERR_INVALID_ARG;
+  if (n < 1) return h->fail(WLBM_ERR_INVALID_ARG, "wlbm_moments_mean: need n >= 1 steps");
+  wlbm_status st = WLBM_OK;
+  const float weight = 1.f / float(n);
+  for (int32_t k = 0; k < n && st == WLBM_OK; ++k) {
+    st = wlbm_step(h, 1);
+    if (st == WLBM_OK && (dT || qx || qy)) st = moments_impl(h, dT, qx, qy, weight, k > 0);
+  }
+  return st;
 }
 
 // Derived outputs 6 and 7 of wlbm_reduce from outputs 2, 4 and 5.

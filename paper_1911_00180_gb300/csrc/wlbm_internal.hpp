@@ -207,6 +207,8 @@ struct MomentArgs {
   float* qy;
   float scale;
   float vg;              // propagation speed: q = v_g sum_i e_i s_i (Eq. q_corr)
+  float weight;          // outputs take weight * moment (1 for plain moments)
+  int accumulate;        // 1: add to the outputs instead of overwriting them
   float e_ref, e_ref1, l_ref, theta;   // e_ref, e_ref + 1, ln(1 + 1/e_ref), theta
 };
 

@@ -65,6 +65,7 @@ def _load():
         "wlbm_step_count": (i64, [vp]),
         "wlbm_moments": (C.c_int, [vp, vp, vp, vp]),
         "wlbm_reduce": (C.c_int, [vp, C.POINTER(dbl)]),
+        "wlbm_moments_mean": (C.c_int, [vp, i32, vp, vp, vp]),
         "wlbm_run_steady": (C.c_int, [vp, i64, i64, dbl, i32, C.POINTER(C.c_int64),
                                       C.POINTER(i32), C.POINTER(dbl)]),
         "wlbm_get_state": (C.c_int, [vp, vp]),
@@ -224,6 +225,15 @@ class WormLBM:
             out = (mk(want_t), mk(want_q), mk(want_q))
         dT, qx, qy = out
         _check(lib.wlbm_moments(self.h, _ptr(dT), _ptr(qx), _ptr(qy)), self.h)
+        return dT, qx, qy
+
+    def wlbm_moments_mean(self, n, want_t=True, want_q=True):
+        """Advance n steps; means of (dT, q_x, q_y) over the n states reached."""
+        torch = self._torch
+        mk = lambda f: torch.empty((self.ny, self.nx), dtype=torch.float32,
+                                   device=self.device) if f else None
+        dT, qx, qy = mk(want_t), mk(want_q), mk(want_q)
+        _check(lib.wlbm_moments_mean(self.h, int(n), _ptr(dT), _ptr(qx), _ptr(qy)), self.h)
         return dT, qx, qy
 
     def wlbm_reduce(self):

@@ -206,3 +206,26 @@ def test_full_size_film_conductivity():
     assert k32[1] / k32[0] == pytest.approx(fs, rel=0.015)
     for a, b in zip(k16, k32):
         assert a == pytest.approx(b, rel=0.025)
+
+
+@pytest.mark.parametrize("storage", [0, 1])
+def test_moments_mean_matches_oracle(storage):
+    """wlbm_moments_mean: means of T, q_x and q_y over the next 10 states (Sec. 4.3's
+    10-step flux average) against the oracle's, on the film recipe (120 x 24, Q = 32)."""
+    cfg = W.film_c3(kn=1.0, nx=120, ny=24, q=32)
+    n0, n = 40, 10
+    m = oracle_run(cfg, n0)
+    mt, mqx, mqy = m.mean_moments(n)
+    dscale = float(np.abs(oracle_run(cfg, 0).d).max())
+    h = gpu_handle(cfg, storage)
+    h.wlbm_init_temperature(cfg["dT"])
+    h.wlbm_step(n0)
+    dT, qx, qy = h.wlbm_moments_mean(n)
+    assert h.wlbm_step_count() == n0 + n
+    got = [x.double().cpu().numpy() for x in (dT, qx, qy)]
+    h.close()
+    tol, stol = (TOL32, TOL32) if storage == 0 else (TOL16, TOL16_STATE)
+    qscale = dscale * float(np.abs(m.s_hat[:, 0]).sum())
+    assert np.abs(got[0] - mt).max() <= tol * cfg["amp"]
+    assert np.abs(got[1] - mqx).max() <= stol * qscale
+    assert np.abs(got[2] - mqy).max() <= stol * qscale
