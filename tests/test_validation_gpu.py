@@ -114,3 +114,48 @@ def test_one_hot_three_cold_steady():
         want = AN.one_hot_three_cold(X, (row + 0.5) / n)
         err = float(np.abs(theta[row] - want)[inner].max())
         assert err <= 0.025, (Yc, err)
+
+
+def test_gaussian_spreading_matches_lattice_diffusivity():
+    """Diffusive limit on the GPU (Sec. 4.3, a Gaussian in the Fourier limit): 512^2,
+    periodic, MFP 4 cells, Q = 16, 3D emulation.  The start is an equilibrium, so the field
+    is the initial Gaussian convolved with the lattice's response to a point source, and
+    variances add: the GPU's energy variance grows between steps 600 and 1400 exactly as
+    the point source's variance in the oracle's moment recursion (an independent
+    computation in moment space), i.e. at 2 D with the lattice's own D (-> Lambda / 3 up
+    to a first-order error in 1/Lambda)."""
+    from oracle import lattice as L
+    from tests.test_oracle_stepper import _moment_recursion
+    n, q, mfp, sigma0 = 512, 16, 4.0, 12.0
+    t1, t2 = 600, 1400
+    yy, xx = np.mgrid[0:n, 0:n]
+    c = n / 2.0
+    dT0 = np.exp(-((xx - c) ** 2 + (yy - c) ** 2) / (2 * sigma0 ** 2)).astype(np.float32)
+    cfg = dict(nx=n, ny=n, q=q, mfp=mfp, bc=(P,) * 4, t_wall=(300.0,) * 4, emulate_3d=True)
+    h = gpu_handle(cfg)
+    h.wlbm_init_temperature(dT0)
+    e_ref = 1.0 / math.expm1(THETA / 300.0)
+
+    def variance():
+        t = _temperature(h)
+        e = 1.0 / np.expm1(THETA / (300.0 + t)) - e_ref
+        w = e.sum()
+        mx = (e * xx).sum() / w
+        return (e * (xx - mx) ** 2).sum() / w
+    h.wlbm_step(t1)
+    v1 = variance()
+    h.wlbm_step(t2 - t1)
+    v2 = variance()
+    h.close()
+    dirs = L.ring_directions(q)
+    W = float(L.relax_weight(mfp, L.lambda_corr(dirs), True))
+    w = L.angular_weights(dirs)
+    z = np.zeros(q)
+    hist = _moment_recursion(q, W, t2, w.copy(), z.copy(), z.copy(), z.copy())
+
+    def var_point(t):
+        m0, m1x, _, m2x = hist[t - 1]
+        return m2x.sum() / m0.sum() - (m1x.sum() / m0.sum()) ** 2
+    grow = var_point(t2) - var_point(t1)
+    assert (v2 - v1) == pytest.approx(grow, rel=1e-3), (v2 - v1, grow)
+    assert grow / (2.0 * (t2 - t1)) == pytest.approx(mfp / 3.0, rel=0.1)
