@@ -525,8 +525,10 @@ def main():
                 "energy_interior_last": reds[-1][0],
                 "energy_rel_change_over_timed_region":
                     (reds[-1][0] - e_start) / abs(e_start) if e_start else None,
-                "mean_qx_last": reds[-1][2], "kappa_apparent_last": reds[-1][6],
-                "kappa_band_last": reds[-1][7], "residual_K_per_step_last": reds[-1][8]}
+                "mean_qx_last": reds[-1][2], "residual_K_per_step_last": reds[-1][8]}
+            if cfg["bc"][0] == cfg["bc"][1] == wl.BC_ISOTHERMAL:   # a film between walls
+                line["fp64_reductions"].update(kappa_apparent_last=reds[-1][6],
+                                               kappa_band_last=reds[-1][7])
         if e2e is not None:
             line["e2e"] = e2e
         if adj is not None:
