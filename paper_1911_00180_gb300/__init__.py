@@ -8,7 +8,8 @@ module (``paper_1911_00180_gb300.build``) imports without the library.
 """
 _EXPORTS = ("WormLBM", "WlbmError", "wlbm_lattice", "wlbm_schedule", "lib", "LIB_PATH",
             "wlbm_reduce_state_noalloc", "WormLBMBatch",
-            "BC_PERIODIC", "BC_ISOTHERMAL", "BC_ADIABATIC_DIFFUSE",
+            "BC_PERIODIC", "BC_ISOTHERMAL", "BC_ADIABATIC_DIFFUSE", "BC_ADIABATIC_SPECULAR",
+            "REDUCE_N",
             "STORE_FP32_DEV", "STORE_BF16_DEV")
 
 
