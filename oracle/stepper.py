@@ -23,7 +23,7 @@ One step n (n = 1, 2, ...), in the order the paper applies it:
      W is the corrected weight W_corr of Eq. W-correction; ghost cells of walls have
      W = 0 (no scattering inside a wall), periodic ghost cells copy W across the link.
 
-Readings of passages the paper leaves open (each is also listed in the design doc):
+Readings of passages the paper leaves open:
   * per-cell W in the paused branch: the loss uses W(y), the gain uses W(s);
   * adiabatic diffuse wall (Eq. adiabatic-diffuse, normalisation garbled): a ghost cell
     collects A = sum of its components that do not point into the domain, zeroes them,
