@@ -93,3 +93,13 @@ def test_failing_allocator_reports_oom(wl):
     st, h, _ = _create(wl, alloc=fns)
     assert st == wl.wlbm.WLBM_ERR_OOM and not h.value
     assert calls and max(calls) >= 2 * 16 * 16 * 16 * 4
+
+
+def test_schedule_speed_arguments(wl):
+    """wlbm_schedule: speed 0 means the unit speed; speeds outside (0, 1] are refused."""
+    import numpy as np
+    assert np.array_equal(wl.wlbm_schedule(16, 40, 0.0), wl.wlbm_schedule(16, 40, 1.0))
+    for bad in (1.5, -0.25, float("nan")):
+        with pytest.raises(wl.WlbmError) as e:
+            wl.wlbm_schedule(16, 10, bad)
+        assert e.value.status == wl.wlbm.WLBM_ERR_INVALID_ARG
