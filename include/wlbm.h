@@ -99,12 +99,14 @@ typedef struct wlbm_handle wlbm_handle;
  * wlbm_create: build the lattice for one grid (Sec. 2.2-2.5): the Q ring directions,
  * the angular weights (Eq. weight), the worm paths (Eq. worm-paths), Lambda_corr
  * (Eq. W-correction-factor-generalized) and the per-cell corrected relaxation weight
- * W_corr = f W (1 - W + W Lambda_corr), W = 1 / MFP (Eq. W-Kn and Eq. W-correction).
+ * W_corr = f W (1 - W + W Lambda_corr), W = v / MFP (Eq. W-Kn and Eq. W-correction; v the
+ * grid's propagation speed, 1 unless set).
  *   mfp_cells    device, nx*ny float32 mean free path in cells (row-major), or NULL to
  *                use mfp_uniform for every cell.  +inf gives W = 0 (ballistic).
  *   stream       cudaStream_t used for every later call (NULL = legacy default stream).
  * Fails with WLBM_ERR_UNSTABLE if any W_corr > 1 (relax_mode 0), WLBM_ERR_INVALID_ARG
- * for an unpaired periodic wall, Q not a multiple of 8, non-positive MFP or sizes.
+ * for an unpaired periodic wall, Q not a multiple of 8, non-positive MFP or sizes, a
+ * speed outside (0, 1] or a specularity outside [0, 1].
  * Synchronous (copies the MFP field to the host once).  The state starts at zero
  * deviation (uniform t_ref) and must be set by wlbm_init_temperature or wlbm_set_state.
  */
@@ -123,15 +125,17 @@ wlbm_status wlbm_set_stream(wlbm_handle* h, void* stream);
 wlbm_status wlbm_init_temperature(wlbm_handle* h, const float* dT);
 
 /* wlbm_step: advance n >= 0 time steps.  Each step applies the wall conditions to the
- * ghost frame (Sec. 2.6), then the fused update of every cell and direction (Eq.
+ * ghost frame (Sec. 2.6), the internal sources (wlbm_set_sources) and the periodic links,
+ * then the fused update of every cell and direction (Eq.
  * lbm-energy with e_i^eq = w_i E, Eq. lbm-energy-density, and the TAS rule of Eq.
  * algorithm along the worm paths of Eq. worm-paths). */
 wlbm_status wlbm_step(wlbm_handle* h, int64_t n);
 int64_t wlbm_step_count(const wlbm_handle* h);
 
 /* wlbm_moments: temperature deviation T - t_ref by Eq. pseudo-T (computed in a
- * cancellation-free form) and heat flux q = sum_i e_i s_i (Eq. q_corr, v_g = 1) of the
- * current state.  Each output is device nx*ny float32, or NULL to skip it. */
+ * cancellation-free form) and heat flux q = v_g sum_i e_i s_i (Eq. q_corr, v_g the grid's
+ * propagation speed) of the current state.  Each output is device nx*ny float32, or NULL
+ * to skip it. */
 wlbm_status wlbm_moments(wlbm_handle* h, float* dT, float* qx, float* qy);
 
 /* wlbm_moments_mean: advance n >= 1 steps and write the means of the moments of
