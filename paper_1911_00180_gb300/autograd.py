@@ -2,7 +2,9 @@
 
 `wlbm_run(mfp_field, t_wall, dT0, spec)` runs `spec["steps"]` steps from the start field
 dT0 (K above T_ref) with per-cell mean free paths `mfp_field` (cells) and wall
-temperatures `t_wall` (4, K) and returns the final temperature deviation field.
+temperatures `t_wall` (4, K) and returns the final temperature deviation field.  `spec`
+holds nx, ny, q, bc, steps, ckpt and optionally emulate_3d, relax_mode, specularity (4)
+and speed (the band's propagation speed, cells per step).
 `wlbm_run_moments(...)` returns the final (dT, q_x, q_y) fields instead, so that an
 objective can use the heat flux (Eq. q_corr), e.g. the apparent conductivity of a film
 mean(q_x) * nx / (D (e(T_h) - e(T_c))), whose explicit dependence on t_wall torch then
@@ -21,7 +23,9 @@ class _WormLBMRun(torch.autograd.Function):
         h = WormLBM(spec["nx"], spec["ny"], spec["q"], mfp_field=mfp_field.detach(),
                     bc=spec["bc"], t_wall=tuple(float(t) for t in t_wall.detach().cpu()),
                     emulate_3d=spec.get("emulate_3d", True),
-                    relax_mode=spec.get("relax_mode", 0))
+                    relax_mode=spec.get("relax_mode", 0),
+                    specularity=spec.get("specularity", (0.0,) * 4),
+                    speed=spec.get("speed", 1.0))
         h.wlbm_adjoint_forward(dT0.detach(), spec["steps"], spec["ckpt"])
         dT, qx, qy = h.wlbm_moments()
         ctx.h = h

@@ -37,12 +37,13 @@ def _case(kinds, nx=26, ny=18, q=16, steps=60, seed=3, field=True):
 
 
 def _gpu(kinds, mfp, dT0, probe, tw, steps, ckpt, q, mfp_uniform=3.0, variant=None,
-         objective="temperature", spec=(0.0,) * 4):
+         objective="temperature", spec=(0.0,) * 4, speed=1.0):
     import torch
     import paper_1911_00180_gb300 as wl
     ny, nx = dT0.shape
     h = wl.WormLBM(nx, ny, q, mfp=mfp_uniform if mfp is None else None, mfp_field=mfp,
-                   bc=kinds, t_wall=tw, emulate_3d=True, theta=THETA, specularity=spec)
+                   bc=kinds, t_wall=tw, emulate_3d=True, theta=THETA, specularity=spec,
+                   speed=speed)
     if variant is not None:
         h.wlbm_set_option(wl.wlbm.OPT_STEP_VARIANT, variant)
     h.wlbm_adjoint_forward(dT0, steps, ckpt)
@@ -63,11 +64,12 @@ def _gpu(kinds, mfp, dT0, probe, tw, steps, ckpt, q, mfp_uniform=3.0, variant=No
 
 
 def _oracle(kinds, mfp, dT0, probe, tw, steps, q, mfp_uniform=3.0, objective="temperature",
-            spec=(0.0,) * 4):
+            spec=(0.0,) * 4, speed=1.0):
     ny, nx = dT0.shape
     kw = dict(nx=nx, ny=ny, q=q,
               mfp=(np.full((ny, nx), mfp_uniform) if mfp is None else mfp.astype(np.float64)),
-              bc_kind=kinds, t_wall=tw, emulate_3d=True, theta=THETA, specularity=spec)
+              bc_kind=kinds, t_wall=tw, emulate_3d=True, theta=THETA, specularity=spec,
+              speed=speed)
     return A.AdjointRun(kw, dT0.astype(np.float64), steps, probe, objective).gradients()
 
 
@@ -105,6 +107,24 @@ def test_adjoint_specular_walls_match_oracle(kinds, spec):
     assert _rel(g_dT0, ref["dJ_ddT0"]) <= TOL
     iso = [k for k in range(4) if kinds[k] == I]
     assert _rel(g_tw[iso], ref["dJ_dTwall"][iso]) <= TOL
+
+
+@pytest.mark.parametrize("objective,kinds,spec", [
+    ("temperature", (I, I, D, D), (0.0,) * 4),
+    ("flux_x", (I, I, D, 3), (0.0, 0.0, 0.0, 0.6))])
+def test_adjoint_band_speed_matches_oracle(objective, kinds, spec):
+    """A band of speed v = 0.6 cells/step (W = v / MFP, the hop test against (v n + 1)^2,
+    the flux seed scaled by v): the GPU reverse sweep against the oracle's transpose."""
+    steps, ckpt, q, v = 56, 9, 16, 0.6
+    mfp, dT0, probe, tw = _case(kinds, seed=5)
+    J, g_mfp, g_tw, g_dT0 = _gpu(kinds, mfp, dT0, probe, tw, steps, ckpt, q,
+                                 objective=objective, spec=spec, speed=v)
+    ref = _oracle(kinds, mfp, dT0, probe, tw, steps, q, objective=objective, spec=spec,
+                  speed=v)
+    assert abs(J - ref["J"]) <= (1e-5 * 1.2e-3 * q if objective == "flux_x" else 1e-5)
+    assert _rel(g_mfp, ref["dJ_dmfp"]) <= TOL
+    assert _rel(g_dT0, ref["dJ_ddT0"]) <= TOL
+    assert _rel(g_tw[:2], ref["dJ_dTwall"][:2]) <= TOL
 
 
 @pytest.mark.parametrize("kinds", [(I, I, D, D), (I, I, P, P)])
@@ -167,19 +187,20 @@ def test_adjoint_uniform_mfp_and_register_variant():
     assert _rel(g_tw[:2], ref["dJ_dTwall"][:2]) <= TOL
 
 
-def test_autograd_function_matches_direct_backward():
+@pytest.mark.parametrize("kinds,p,v", [((I, I, P, P), (0.0,) * 4, 1.0),
+                                       ((I, I, 3, D), (0.0, 0.0, 0.8, 0.0), 0.7)])
+def test_autograd_function_matches_direct_backward(kinds, p, v):
     import torch
     from paper_1911_00180_gb300.autograd import wlbm_run
-    kinds = (I, I, P, P)
     mfp, dT0, probe, tw = _case(kinds, nx=20, ny=14)
-    spec = dict(nx=20, ny=14, q=16, bc=kinds, steps=30, ckpt=8)
+    spec = dict(nx=20, ny=14, q=16, bc=kinds, steps=30, ckpt=8, specularity=p, speed=v)
     m = torch.tensor(mfp, device="cuda", requires_grad=True)
     t = torch.tensor(tw, dtype=torch.float64, device="cuda", requires_grad=True)
     d0 = torch.tensor(dT0, device="cuda", requires_grad=True)
     out = wlbm_run(m, t, d0, spec)
     J = out[torch.as_tensor(probe, device="cuda")].mean()
     J.backward()
-    ref = _oracle(kinds, mfp, dT0, probe, tw, 30, 16)
+    ref = _oracle(kinds, mfp, dT0, probe, tw, 30, 16, spec=p, speed=v)
     assert _rel(m.grad.double().cpu().numpy(), ref["dJ_dmfp"]) <= TOL
     assert _rel(d0.grad.double().cpu().numpy(), ref["dJ_ddT0"]) <= TOL
     assert _rel(t.grad.cpu().numpy()[:2], ref["dJ_dTwall"][:2]) <= TOL
