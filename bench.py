@@ -16,6 +16,8 @@ e2e       the same metric through the public API with host buffers: per e2e step
 roofline  the fused step kernel: algorithmic bytes per launch (8 B per site-direction for
           float32, 4 B for bfloat16, plus 8 B per cell for the local-energy read and
           write) over its CUDA-event duration, against the measured HBM copy bandwidth.
+          The events bracket every S-th step-kernel launch of the timed region
+          (--profile-every, default 8), so most steps run without event records.
 cpu_baseline  the FP64 oracle on the host cores, on a bounded sample of the same grid.
 
 Under torchrun (N > 1) every rank runs an independent replica of the workload (the grid
@@ -58,6 +60,9 @@ def parse():
     p.add_argument("--fuse", type=int, default=None,
                    help="1: step kernel mirrors periodic edges, 0: separate pass (library "
                         "default)")
+    p.add_argument("--profile-every", type=int, default=8, metavar="S",
+                   help="CUDA-event pair around every S-th step-kernel launch of the timed "
+                        "region (the roofline's kernel duration; 1: every launch)")
     p.add_argument("--graph", type=int, default=0,
                    help="replay chunks of this many steps as one CUDA graph (multiple of 6)")
     p.add_argument("--variant", type=int, default=None,
@@ -72,17 +77,23 @@ def parse():
     return p.parse_args()
 
 
+# the TMA step kernel's translation unit within the package (device code and argument
+# structs), sorted by name
+STEP_KERNEL_SOURCES = ("elem.cuh", "k_step_tma.cu", "lattice.hpp", "mbar.cuh",
+                       "wlbm_internal.hpp")
+
+
 def measured_traffic(workload, storage, nx, q):
     """DRAM bytes per step-kernel launch from the committed ncu launch lists, if they were
-    taken on the kernel sources of this tree (else None)."""
-    import glob
+    taken on the step kernel's sources of this tree (else None): the digest covers
+    k_step_tma.cu and the headers it compiles with (STEP_KERNEL_SOURCES)."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "k_step_tma_traffic.txt")
     if not os.path.exists(path):
         return None
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_1911_00180_gb300", "csrc", "*"))):
-        with open(f, "rb") as fh:
+    for f in STEP_KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1911_00180_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     digest = None
     table = {}
@@ -153,7 +164,7 @@ def run_batch(args):
         stream.synchronize()
         _, _, l0 = b.wlbm_batch_profile_read()
         graphs = tuned["graph_steps"] > 0
-        b.wlbm_batch_profile(not graphs)
+        b.wlbm_batch_profile(0 if graphs else args.profile_every)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         if world > 1:
@@ -191,7 +202,8 @@ def run_batch(args):
                        "autotune": tuned},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None, "kernel": "k_step_*_batch",
-                         "peak_kind": kind, "kernel_ms_per_launch": per_launch},
+                         "peak_kind": kind, "kernel_ms_per_launch": per_launch,
+                         "kernel_launches_timed": nlaunch},
             "gpu_launches": int(l1 - l0)}
     print(json.dumps(finite_or_none(line)), flush=True)
     if world > 1:
@@ -427,7 +439,7 @@ def main():
             torch.cuda.synchronize()
 
         clocks = None if args.no_extras else Clocks(local)
-        h.wlbm_profile(not args.graph)
+        h.wlbm_profile(0 if args.graph else args.profile_every)
         barrier()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
@@ -515,7 +527,8 @@ def main():
                          "kernel": {0: "k_step", 1: "k_step_bulk", 2: "k_step_ws",
                                     3: "k_step_tma"}[variant_used], "peak_kind": peak_kind,
                          "bytes_per_update": bpu,
-                         "kernel_ms_per_launch": per_launch_ms},
+                         "kernel_ms_per_launch": per_launch_ms,
+                         "kernel_launches_timed": step_launches},
             "gpu_launches": int(launches1 - launches0),
             "hbm_roofline_pct_of_measured": 100.0 * achieved / peak,
         }

@@ -296,13 +296,17 @@ wlbm_status wlbm_set_option(wlbm_handle* h, int32_t key, int64_t value);
 wlbm_status wlbm_get_option(const wlbm_handle* h, int32_t key, int64_t* value);
 wlbm_status wlbm_check(wlbm_handle* h);
 
-/* wlbm_profile: enable (1) or disable (0) CUDA-event timing of every launch of the
- * fused step kernel on the handle's stream (an event pair around each launch).
+/* wlbm_profile: CUDA-event timing of the fused step kernel on the handle's stream: an
+ * event pair around every `every`-th step-kernel launch from this call on (1: every
+ * launch; 0: off).  A stride above 1 keeps the event records off most steps, so the
+ * steps between timed launches run as they do without profiling.  While it is on, steps
+ * are launched directly (WLBM_OPT_GRAPH_STEPS is ignored).  WLBM_ERR_INVALID_ARG for
+ * every < 0.
  * wlbm_profile_read: synchronises the stream, returns the summed duration (ms) and count
  * of the timed step-kernel launches since the last read (then resets them), and the
  * number of kernels this handle has launched since it was created.  Any output may be
  * NULL. */
-wlbm_status wlbm_profile(wlbm_handle* h, int32_t enable);
+wlbm_status wlbm_profile(wlbm_handle* h, int32_t every);
 wlbm_status wlbm_profile_read(wlbm_handle* h, double* step_ms, int64_t* step_launches,
                               int64_t* all_launches);
 
@@ -363,7 +367,7 @@ wlbm_status wlbm_batch_init_temperature(wlbm_batch* b, const float* const* dT);
 wlbm_status wlbm_batch_set_option(wlbm_batch* b, int32_t key, int64_t value);
 wlbm_status wlbm_batch_get_option(const wlbm_batch* b, int32_t key, int64_t* value);
 wlbm_status wlbm_batch_step(wlbm_batch* b, int64_t n);
-wlbm_status wlbm_batch_profile(wlbm_batch* b, int32_t enable);
+wlbm_status wlbm_batch_profile(wlbm_batch* b, int32_t every);   /* as wlbm_profile */
 wlbm_status wlbm_batch_profile_read(wlbm_batch* b, double* step_ms, int64_t* step_launches,
                                     int64_t* all_launches);
 /* wlbm_batch_autotune: as wlbm_autotune over variants 0, 1 and 3, for the whole batch

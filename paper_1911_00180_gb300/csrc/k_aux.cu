@@ -1,7 +1,6 @@
 // Boundary, initialisation, moment and reduction kernels of libwlbm.
 //
-//  k_walls     ghost cells of non-periodic walls (Sec. 2.6), 32 cells a block: isotropic
-//              blackbody walls
+//  k_walls     ghost cells of non-periodic walls (Sec. 2.6): isotropic blackbody walls
 //              overwrite d_i = w_i (e_eq(T_w) - e_ref) (Eq. isotropic); adiabatic diffuse
 //              walls collect the components that do not point into the domain and
 //              re-emit them into the inward ones with fractions w_i (s_i.n) / sum
@@ -230,14 +229,80 @@ __device__ __forceinline__ void walls_cell(const WallArgs& a, const WallSmem& sm
   }
 }
 
+// Diffuse (or specular-diffuse) horizontal chunk with every value staged in shared memory
+// (vals[i][lane] = the deviations of the lane's four cells in direction i): the block's
+// warps load all directions at once (nw warps, directions warp, warp + nw, ...), then
+// warps 0 .. kWallWarps-1 add the collected directions in exactly the order of the
+// streaming path below (group g: directions g, g + kWallWarps, ... in turn; then the
+// groups in turn), so both paths give the same bits, and every output is computed from
+// the staged values: one global load and one store per value.
+template <typename T, bool SPEC>
+__device__ __forceinline__ void walls_staged(const WallArgs& a, const WallSeg& g,
+                                             WallSmem& sm, float4* vals, T* const planes,
+                                             int64_t off, bool on, int nv, bool ref,
+                                             const float (&R)[4], int lane, int warp, int nw) {
+  auto ptr = [&](int i) { return planes + int64_t(sm.par[i] * a.q + i) * a.plane + off; };
+#pragma unroll 4
+  for (int i = warp; i < a.q; i += nw) {
+    float d[4] = {0.f, 0.f, 0.f, 0.f};
+    if (on) ld4_dev(ptr(i), sm.w[i], ref, R, a.scale, d);
+    vals[i * 32 + lane] = make_float4(d[0], d[1], d[2], d[3]);
+  }
+  __syncthreads();
+  if (warp < kWallWarps) {
+    float part[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int i = warp; i < a.q; i += kWallWarps) {
+      if (sm.rho[i] != 0.f) continue;
+      const float4 v = vals[i * 32 + lane];
+      part[0] += v.x; part[1] += v.y; part[2] += v.z; part[3] += v.w;
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) sm.part[(warp * 32 + lane) * 4 + j] = part[j];
+  }
+  __syncthreads();
+  if (!on) return;
+  float A[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+  for (int k = 0; k < kWallWarps; ++k)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) A[j] += sm.part[(k * 32 + lane) * 4 + j];
+  const float p = SPEC ? g.spec : 0.f;
+#pragma unroll 4
+  for (int i = warp; i < a.q; i += nw) {
+    const float4 f = vals[i * 32 + lane];
+    const float v[4] = {f.x, f.y, f.z, f.w};
+    float d[4] = {0.f, 0.f, 0.f, 0.f};
+    if (SPEC && p > 0.f) {       // uniform over the block (one segment)
+      if (sm.rho[i] != 0.f) {
+        const float4 mf = vals[sm.src[i] * 32 + lane];
+        const float m[4] = {mf.x, mf.y, mf.z, mf.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) d[j] = fmaf((1.f - p) * A[j], sm.rho[i], fmaf(p, m[j], v[j]));
+      } else if (sm.src[i] == i) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) d[j] = p * v[j];
+      }
+    } else if (sm.rho[i] != 0.f) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) d[j] = fmaf(A[j], sm.rho[i], v[j]);
+    }
+    st4_dev(ptr(i), d, sm.w[i], ref, R, a.inv_scale, nv);
+  }
+}
+
+// One block of a wall pass.  vals: the staging buffer of walls_staged (q * 32 float4 of
+// dynamic shared memory), or nullptr for the streaming path, which keeps no values
+// between its passes and runs with kWallWarps warps.
 template <typename T, bool SPEC>
 __device__ __forceinline__ void walls_chunk(const WallArgs& a, const uint8_t* codes,
-                                            float* e_ref, int chunk, WallSmem& sm) {
+                                            float* e_ref, int chunk, WallSmem& sm,
+                                            float4* vals) {
   int c = 0;
   const int s = wall_chunk_segment(a.nseg, a.seg, chunk, &c);
   if (s >= a.nseg) return;                     // uniform over the block
   const WallSeg g = a.seg[s];
   const int lane = int(threadIdx.x) & 31, warp = int(threadIdx.x) >> 5;
+  const int nw = int(blockDim.x) >> 5;
   const bool diffuse = g.action != WLBM_BC_ISOTHERMAL;
   const float* rho = a.rho + int64_t(g.table) * a.q;
   const int16_t* mir = a.mirror + int64_t(g.mirror) * a.q;
@@ -250,11 +315,12 @@ __device__ __forceinline__ void walls_chunk(const WallArgs& a, const uint8_t* co
   __syncthreads();
   if (!wall_seg_rowwise(g)) {                  // one warp per cell, lanes over directions
     const int cell = c * kWallCellsPerBlock + warp;
-    if (cell < g.count) walls_cell<T, SPEC>(a, sm, e_ref, g, cell, lane);
+    if (warp < kWallCellsPerBlock && cell < g.count)
+      walls_cell<T, SPEC>(a, sm, e_ref, g, cell, lane);
     return;
   }
   // horizontal wall (dr = 0, dc = 1): the block takes cells c*128 .. c*128+127 of the
-  // segment; lane owns four consecutive cells, warp w the directions w, w + kWallWarps, ...
+  // segment; lane owns four consecutive cells, warp w the directions w, w + nw, ...
   const int idx0 = c * kWallChunk + 4 * lane;
   const int nv = min(4, g.count - idx0);          // this lane's valid cells (<= 0: none)
   const bool on = nv > 0;
@@ -270,11 +336,11 @@ __device__ __forceinline__ void walls_chunk(const WallArgs& a, const uint8_t* co
       // bfloat16: make the wall's own equilibrium the reference of the cell, so the
       // stored values are exactly zero and decode to w_i (e_eq(T_w) - e_ref) unrounded
       const float z[4] = {0.f, 0.f, 0.f, 0.f};
-      for (int i = warp; i < a.q; i += kWallWarps) st4_raw(ptr(i), z, nv);
+      for (int i = warp; i < a.q; i += nw) st4_raw(ptr(i), z, nv);
       if (warp == 0)
         for (int j = 0; j < nv; ++j) e_ref[off + j] = g.iso;
     } else {
-      for (int i = warp; i < a.q; i += kWallWarps) {
+      for (int i = warp; i < a.q; i += nw) {
         const float x = sm.w[i] * g.iso;
         v[0] = x; v[1] = x; v[2] = x; v[3] = x;
         st4_raw(ptr(i), v, nv);
@@ -286,6 +352,11 @@ __device__ __forceinline__ void walls_chunk(const WallArgs& a, const uint8_t* co
     const float4 r = *reinterpret_cast<const float4*>(e_ref + off);
     R[0] = r.x; R[1] = r.y; R[2] = r.z; R[3] = r.w;
   }
+  if (vals) {
+    walls_staged<T, SPEC>(a, g, sm, vals, planes, off, on, nv, ref, R, lane, warp, nw);
+    return;
+  }
+  // streaming path (nw == kWallWarps)
   // collected energy per cell: the non-inward directions of this warp, then all warps
   float part[4] = {0.f, 0.f, 0.f, 0.f};
   if (on) {
@@ -348,10 +419,18 @@ __device__ __forceinline__ void walls_chunk(const WallArgs& a, const uint8_t* co
   }
 }
 
+// Single-grid wall pass: kStagedWarps(q) warps and staged values for q <= kStagedMaxQ,
+// else the streaming path with kWallWarps warps.
+constexpr int kStagedMaxQ = 256;
+constexpr int kMaxWallWarps = 32;
+inline int staged_warps(int q) { return std::min(kMaxWallWarps, std::max(kWallWarps, q / 4)); }
+
 template <typename T, bool SPEC>
-__global__ void __launch_bounds__(32 * kWallWarps) k_walls(const WallArgs a) {
+__global__ void __launch_bounds__(32 * kMaxWallWarps) k_walls(const WallArgs a) {
   __shared__ WallSmem sm;
-  walls_chunk<T, SPEC>(a, a.codes, a.e_ref, int(blockIdx.x), sm);
+  extern __shared__ float4 wall_vals[];
+  walls_chunk<T, SPEC>(a, a.codes, a.e_ref, int(blockIdx.x), sm,
+                       a.q <= kStagedMaxQ ? wall_vals : nullptr);
 }
 
 // Batched wall pass: block b belongs to instance block_inst[b] (a host-built table: one
@@ -375,7 +454,7 @@ __global__ void __launch_bounds__(32 * kWallWarps) k_walls_batch(const BatchWall
   const uint8_t* codes = I.codes + size_t(t) * I.w.q;
   const int chunk = b - I.first_block;
   __syncthreads();
-  walls_chunk<T, SPEC>(wa, codes, e_ref, chunk, sm);
+  walls_chunk<T, SPEC>(wa, codes, e_ref, chunk, sm, nullptr);
 }
 
 // Internal sources / radiation cells: one warp per cell, lanes over the directions.  With
@@ -720,10 +799,13 @@ template <typename T>
 cudaError_t walls_t(const WallArgs& a, cudaStream_t s) {
   const int chunks = wall_chunk_count(a.nseg, a.seg);
   if (chunks == 0) return cudaSuccess;
+  const bool staged = a.q <= kStagedMaxQ;
+  const int warps = staged ? staged_warps(a.q) : kWallWarps;
+  const size_t bytes = staged ? size_t(a.q) * 32 * sizeof(float4) : 0;
   if (a.any_spec)
-    k_walls<T, true><<<chunks, 32 * kWallWarps, 0, s>>>(a);
+    k_walls<T, true><<<chunks, 32 * warps, bytes, s>>>(a);
   else
-    k_walls<T, false><<<chunks, 32 * kWallWarps, 0, s>>>(a);
+    k_walls<T, false><<<chunks, 32 * warps, bytes, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -754,6 +836,17 @@ cudaError_t launch_walls_batch(int storage, const BatchWalls* b, const int* bloc
 }
 
 int wall_blocks(const WallArgs& a) { return wall_chunk_count(a.nseg, a.seg); }
+
+cudaError_t configure_walls() {
+  const int bytes = kStagedMaxQ * 32 * int(sizeof(float4));
+  const void* fns[4] = {(const void*)k_walls<float, false>, (const void*)k_walls<float, true>,
+                        (const void*)k_walls<__nv_bfloat16, false>,
+                        (const void*)k_walls<__nv_bfloat16, true>};
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < 4 && e == cudaSuccess; ++k)
+    e = cudaFuncSetAttribute(fns[k], cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  return e;
+}
 
 cudaError_t launch_walls(int storage, const WallArgs& a, cudaStream_t s) {
   return storage == WLBM_STORE_BF16_DEV ? walls_t<__nv_bfloat16>(a, s) : walls_t<float>(a, s);

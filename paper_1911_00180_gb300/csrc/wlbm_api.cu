@@ -112,7 +112,8 @@ struct wlbm_handle {
   } adj;
   // launch accounting and optional per-launch timing of the step kernel
   int64_t launches = 0;
-  bool profiling = false;
+  int prof_every = 0;                 // time every prof_every-th step launch (0: none)
+  int64_t prof_tick = 0;              // step launches seen while profiling
   std::vector<cudaEvent_t> prof_ev;   // pairs (start, stop)
   size_t prof_used = 0;
 
@@ -528,6 +529,7 @@ wlbm_status wlbm_create(const wlbm_grid* grid, const float* mfp_cells, double mf
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev[k], cudaEventDisableTiming);
   }
   if (e == cudaSuccess) e = prepare_step_kernels();
+  if (e == cudaSuccess) e = configure_walls();
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // host vectors die here
   if (e != cudaSuccess) {
     const std::string m = std::string("wlbm_create: ") + cudaGetErrorString(e);
@@ -590,7 +592,8 @@ wlbm_status wlbm_init_temperature(wlbm_handle* h, const float* dT) {
 }
 
 // Launch the kernels of `count` steps whose codes sit at d_codes[t][q], t < count.
-static wlbm_status enqueue_steps(wlbm_handle* h, int count, bool profile) {
+// every > 0: an event pair around every every-th step-kernel launch (counted across calls)
+static wlbm_status enqueue_steps(wlbm_handle* h, int count, int every) {
   const Geom& g = h->g;
   const bool any_wall = h->walls.nseg > 0;
   // both axes periodic: the step kernel mirrors the edges itself (grids of 2+ cells)
@@ -643,7 +646,7 @@ static wlbm_status enqueue_steps(wlbm_handle* h, int count, bool profile) {
     int tx_unused = 0, ty_unused = 0;
     tma_cover(h->bc_kind, g.nx, g.ny, &sa, &tx_unused, &ty_unused);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
-    if (profile) {
+    if (every > 0 && h->prof_tick++ % every == 0) {
       if (h->prof_used + 2 > h->prof_ev.size()) {
         for (int k = 0; k < 2; ++k) {
           cudaEvent_t ev;
@@ -681,7 +684,7 @@ static wlbm_status run_graph(wlbm_handle* h) {
     wlbm_status st = h->cuda(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal),
                              "wlbm_step: graph capture");
     if (st != WLBM_OK) return st;
-    const wlbm_status est = enqueue_steps(h, G, false);
+    const wlbm_status est = enqueue_steps(h, G, 0);
     cudaGraph_t graph = nullptr;
     const cudaError_t ce = cudaStreamEndCapture(h->stream, &graph);
     if (est != WLBM_OK) {
@@ -704,7 +707,7 @@ wlbm_status wlbm_step(wlbm_handle* h, int64_t n) {
   if (!h) return WLBM_ERR_INVALID_ARG;
   if (n < 0) return h->fail(WLBM_ERR_INVALID_ARG, "wlbm_step: negative step count");
   const Geom& g = h->g;
-  const bool graphs = h->graph_steps > 0 && !h->profiling && h->stream != nullptr;
+  const bool graphs = h->graph_steps > 0 && h->prof_every == 0 && h->stream != nullptr;
   while (n > 0) {
     const int ch = int(std::min<int64_t>(n, graphs ? h->graph_steps : kChunk));
     const int slot = h->slot;
@@ -726,7 +729,7 @@ wlbm_status wlbm_step(wlbm_handle* h, int64_t n) {
     if (graphs && ch == h->graph_steps)
       st = run_graph(h);
     else
-      st = enqueue_steps(h, ch, h->profiling);
+      st = enqueue_steps(h, ch, h->prof_every);
     if (st != WLBM_OK) return st;
     h->slot ^= 1;
     n -= ch;
@@ -780,9 +783,11 @@ wlbm_status wlbm_check(wlbm_handle* h) {
   return WLBM_OK;
 }
 
-wlbm_status wlbm_profile(wlbm_handle* h, int32_t enable) {
+wlbm_status wlbm_profile(wlbm_handle* h, int32_t every) {
   if (!h) return WLBM_ERR_INVALID_ARG;
-  h->profiling = enable != 0;
+  if (every < 0) return h->fail(WLBM_ERR_INVALID_ARG, "wlbm_profile: negative stride");
+  h->prof_every = every;
+  h->prof_tick = 0;
   return WLBM_OK;
 }
 
@@ -1502,7 +1507,8 @@ struct wlbm_batch {
   };
   std::vector<Graph> graphs;
   int64_t graph_launches = 0, launches = 0;
-  bool profiling = false;
+  int prof_every = 0;
+  int64_t prof_tick = 0;
   std::vector<cudaEvent_t> prof_ev;
   size_t prof_used = 0;
   std::string err;
@@ -1744,7 +1750,7 @@ wlbm_status wlbm_batch_set_option(wlbm_batch* b, int32_t key, int64_t value) {
 }  // extern "C"
 
 // Kernels of `count` steps for the whole batch, instance records already on the device.
-static wlbm_status batch_enqueue(wlbm_batch* b, int count, bool profile) {
+static wlbm_status batch_enqueue(wlbm_batch* b, int count, int every) {
   const int n = int(b->h.size());
   wlbm_status st = WLBM_OK;
   bool any_spec = false;
@@ -1772,7 +1778,7 @@ static wlbm_status batch_enqueue(wlbm_batch* b, int count, bool profile) {
     }
     if (st != WLBM_OK) break;
     cudaEvent_t e1 = nullptr;
-    if (profile) {
+    if (every > 0 && b->prof_tick++ % every == 0) {
       if (b->prof_used + 2 > b->prof_ev.size()) {
         for (int j = 0; j < 2; ++j) {
           cudaEvent_t ev;
@@ -1804,7 +1810,7 @@ wlbm_status wlbm_batch_step(wlbm_batch* b, int64_t n) {
   if (!b) return WLBM_ERR_INVALID_ARG;
   if (n < 0) return b->fail(WLBM_ERR_INVALID_ARG, "wlbm_batch_step: negative step count");
   const int ni = int(b->h.size());
-  const bool graphs = b->graph_steps > 0 && !b->profiling && b->stream;
+  const bool graphs = b->graph_steps > 0 && b->prof_every == 0 && b->stream;
   while (n > 0) {
     const int ch = int(std::min<int64_t>(n, graphs ? b->graph_steps : kBatchChunk));
     wlbm_status st = b->cuda(cudaEventSynchronize(b->ev), "wlbm_batch_step");
@@ -1867,7 +1873,7 @@ wlbm_status wlbm_batch_step(wlbm_batch* b, int64_t n) {
         st = b->cuda(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal),
                      "wlbm_batch_step: capture");
         if (st != WLBM_OK) return st;
-        const wlbm_status est = batch_enqueue(b, ch, false);
+        const wlbm_status est = batch_enqueue(b, ch, 0);
         cudaGraph_t gr = nullptr;
         const cudaError_t ce = cudaStreamEndCapture(b->stream, &gr);
         if (est == WLBM_OK) st = b->cuda(ce, "wlbm_batch_step: capture");
@@ -1883,7 +1889,7 @@ wlbm_status wlbm_batch_step(wlbm_batch* b, int64_t n) {
       b->launches += b->graph_launches;
       st = b->cuda(cudaGraphLaunch(exec, b->stream), "wlbm_batch_step: graph launch");
     } else {
-      st = batch_enqueue(b, ch, b->profiling);
+      st = batch_enqueue(b, ch, b->prof_every);
     }
     if (st != WLBM_OK) return st;
     for (wlbm_handle* x : b->h)
@@ -1893,9 +1899,11 @@ wlbm_status wlbm_batch_step(wlbm_batch* b, int64_t n) {
   return WLBM_OK;
 }
 
-wlbm_status wlbm_batch_profile(wlbm_batch* b, int32_t enable) {
+wlbm_status wlbm_batch_profile(wlbm_batch* b, int32_t every) {
   if (!b) return WLBM_ERR_INVALID_ARG;
-  b->profiling = enable != 0;
+  if (every < 0) return b->fail(WLBM_ERR_INVALID_ARG, "wlbm_batch_profile: negative stride");
+  b->prof_every = every;
+  b->prof_tick = 0;
   return WLBM_OK;
 }
 

@@ -339,6 +339,7 @@ void set_global_error_msg(const std::string& m);
 // Kernel launchers (k_step.cu, k_aux.cu).  Return cudaGetLastError().
 cudaError_t launch_step(int storage, const StepArgs& a, cudaStream_t s);
 cudaError_t prepare_step_kernels();   // per-device kernel attributes; call before capture
+cudaError_t configure_walls();        // the same for the single-grid wall pass
 // Variant 3 (TMA tiles): kernel attributes, launch, and the planes' tensor map (written to
 // `out`, 128 bytes, 64-byte aligned; false with a reason when it cannot be made).
 cudaError_t configure_step_tma();

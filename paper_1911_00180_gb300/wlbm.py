@@ -319,8 +319,9 @@ class WormLBM:
     def wlbm_check(self):
         _check(lib.wlbm_check(self.h), self.h)
 
-    def wlbm_profile(self, enable=True):
-        _check(lib.wlbm_profile(self.h, 1 if enable else 0), self.h)
+    def wlbm_profile(self, every=1):
+        """Time every `every`-th step-kernel launch (True: every launch; False or 0: off)."""
+        _check(lib.wlbm_profile(self.h, int(every)), self.h)
 
     def wlbm_profile_read(self):
         """(summed step-kernel ms, timed step launches, all kernel launches so far)."""
@@ -438,8 +439,8 @@ class WormLBMBatch:
         _batch_check(lib.wlbm_batch_get_option(self.b, int(key), C.byref(v)), self.b)
         return v.value
 
-    def wlbm_batch_profile(self, enable=True):
-        _batch_check(lib.wlbm_batch_profile(self.b, 1 if enable else 0), self.b)
+    def wlbm_batch_profile(self, every=1):
+        _batch_check(lib.wlbm_batch_profile(self.b, int(every)), self.b)
 
     def wlbm_batch_profile_read(self):
         ms, n, alln = C.c_double(), C.c_int64(), C.c_int64()
