@@ -4,7 +4,9 @@ Workload (default): 2048 x 2048 periodic grid, Q = 64 worm directions, float32
 deviation storage, uniform MFP drawn log-uniform in [1, 1000] cells from the seed, 16
 seeded Gaussian pulses.  One bench step = one worm-LBM time step over the whole grid:
 the periodic ghost-frame refresh plus the fused relax-and-stream kernel, with the FP64
-reductions (energy, heat flux, conductivity, steady-state residual) every R = 500 steps.
+reductions (energy, heat flux, conductivity, steady-state residual) every R = 480 steps.
+Steps run as CUDA-graph replays of 48-step chunks (--graph; R a multiple of it, so every
+chunk is a replay).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
                   [--storage fp32|bf16] [--nx N] [--q Q]
@@ -17,7 +19,9 @@ roofline  the fused step kernel: algorithmic bytes per launch (8 B per site-dire
           float32, 4 B for bfloat16, plus 8 B per cell for the local-energy read and
           write) over its CUDA-event duration, against the measured HBM copy bandwidth.
           The events bracket every S-th step-kernel launch of the timed region
-          (--profile-every, default 8), so most steps run without event records.
+          (--profile-every, default 8; under graph replay the steps t of each chunk with
+          t % S == 0, recorded by the graph's event nodes), so most steps run without
+          event records.
 cpu_baseline  the FP64 oracle on the host cores, on a bounded sample of the same grid.
 
 Under torchrun (N > 1) every rank runs an independent replica of the workload (the grid
@@ -54,7 +58,7 @@ def parse():
                    help="pulses: 2048^2 periodic Q=64 (default); film: 4096x256 in-plane "
                         "film, Q=128, isothermal x walls, diffuse y walls (Kn = 1)")
     p.add_argument("--e2e-steps", type=int, default=3)
-    p.add_argument("--reduce-every", type=int, default=500, metavar="R",
+    p.add_argument("--reduce-every", type=int, default=480, metavar="R",
                    help="FP64 reductions (energy, flux, conductivity, residual) every R steps "
                         "inside the timed region and the e2e run (0: none)")
     p.add_argument("--fuse", type=int, default=None,
@@ -63,8 +67,9 @@ def parse():
     p.add_argument("--profile-every", type=int, default=8, metavar="S",
                    help="CUDA-event pair around every S-th step-kernel launch of the timed "
                         "region (the roofline's kernel duration; 1: every launch)")
-    p.add_argument("--graph", type=int, default=0,
-                   help="replay chunks of this many steps as one CUDA graph (multiple of 6)")
+    p.add_argument("--graph", type=int, default=48,
+                   help="replay chunks of this many steps as one CUDA graph (multiple of 6; "
+                        "0: launch every step directly)")
     p.add_argument("--variant", type=int, default=None,
                    help="step kernel: 0 register-pipelined, 1 bulk-copy ring, 2 warp-specialised, "
                         "3 TMA tiles (library default where available)")
@@ -163,8 +168,7 @@ def run_batch(args):
         b.wlbm_batch_step(args.warmup)
         stream.synchronize()
         _, _, l0 = b.wlbm_batch_profile_read()
-        graphs = tuned["graph_steps"] > 0
-        b.wlbm_batch_profile(0 if graphs else args.profile_every)
+        b.wlbm_batch_profile(args.profile_every)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         if world > 1:
@@ -439,7 +443,7 @@ def main():
             torch.cuda.synchronize()
 
         clocks = None if args.no_extras else Clocks(local)
-        h.wlbm_profile(0 if args.graph else args.profile_every)
+        h.wlbm_profile(args.profile_every)
         barrier()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
@@ -514,6 +518,7 @@ def main():
                            % (cfg["nx"], cfg["ny"], cfg["q"], args.storage, cfg["mfp"])),
                        "nx": cfg["nx"], "ny": cfg["ny"], "q": cfg["q"],
                        "mfp_cells": cfg["mfp"], "parallelism": "replicas x%d" % world,
+                       "graph_steps": args.graph,
                        "step_kernel": {0: "register-pipelined", 1: "bulk-copy ring",
                                        2: "warp-specialised", 3: "TMA tiles"}[variant_used],
                        "l2": "state %.2f GB > L2 (no flush needed)"

@@ -283,8 +283,7 @@ wlbm_status wlbm_adjoint_backward(wlbm_handle* h, const float* dJ_dT, const floa
  *                          WLBM_OPT_FUSE_PERIODIC set it still runs the periodic pass.
  *   WLBM_OPT_GRAPH_STEPS   0 (default): launch every step's kernels directly; G > 0, a
  *                          multiple of 6: run chunks of G steps as one captured CUDA
- *                          graph (for small, launch-bound grids; not while profiling and
- *                          not on the legacy default stream).
+ *                          graph (fewer launch gaps; not on the legacy default stream).
  *   WLBM_OPT_FUSE_PERIODIC 0 (default): a separate periodic pass before every step; 1:
  *                          when both axes are periodic the step kernel also writes the
  *                          ghost cells mirroring each edge cell (no separate pass).
@@ -299,9 +298,11 @@ wlbm_status wlbm_check(wlbm_handle* h);
 /* wlbm_profile: CUDA-event timing of the fused step kernel on the handle's stream: an
  * event pair around every `every`-th step-kernel launch from this call on (1: every
  * launch; 0: off).  A stride above 1 keeps the event records off most steps, so the
- * steps between timed launches run as they do without profiling.  While it is on, steps
- * are launched directly (WLBM_OPT_GRAPH_STEPS is ignored).  WLBM_ERR_INVALID_ARG for
- * every < 0.
+ * steps between timed launches run as they do without profiling.  Under graph replay
+ * (WLBM_OPT_GRAPH_STEPS = G) the timed launches are the steps t of each replayed chunk
+ * with t % every == 0, recorded by event nodes of the graph; a graph's pairs are read
+ * before it replays again (two chunks later: the host may wait for that replay to end).
+ * Changing the stride drops the captured graphs.  WLBM_ERR_INVALID_ARG for every < 0.
  * wlbm_profile_read: synchronises the stream, returns the summed duration (ms) and count
  * of the timed step-kernel launches since the last read (then resets them), and the
  * number of kernels this handle has launched since it was created.  Any output may be

@@ -26,6 +26,64 @@ void set_global_error(const std::string& m) {
 
 int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
 
+// An event record on stream s; `node`: the stream is being captured and the record becomes
+// an event node of the graph (timed each time the graph replays).
+cudaError_t record_event(cudaEvent_t e, cudaStream_t s, bool node) {
+  return node ? cudaEventRecordWithFlags(e, s, cudaEventRecordExternal) : cudaEventRecord(e, s);
+}
+
+// One instantiated CUDA graph of a chunk of steps.  Captured while profiling, its timed
+// step-kernel launches record event pairs through event nodes; a replay overwrites them,
+// so they are read (waiting for that replay) before the graph replays again.
+struct TimedGraph {
+  cudaGraphExec_t exec = nullptr;
+  std::vector<cudaEvent_t> ev;   // (start, stop) pairs
+  cudaEvent_t done = nullptr;    // recorded after every replay when there are pairs
+  bool pending = false;          // replayed since the pairs were last read
+
+  // Events for `pairs` timed launches (before the capture).
+  cudaError_t make_events(int pairs) {
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < 2 * pairs && e == cudaSuccess; ++k) {
+      cudaEvent_t x = nullptr;
+      e = cudaEventCreate(&x);
+      if (e == cudaSuccess) ev.push_back(x);
+    }
+    if (pairs > 0 && e == cudaSuccess) e = cudaEventCreateWithFlags(&done, cudaEventDisableTiming);
+    return e;
+  }
+  // Adds the latest replay's durations (ms) and pair count to *ms and *n.
+  cudaError_t harvest(double* ms, int64_t* n) {
+    if (!pending) return cudaSuccess;
+    pending = false;
+    cudaError_t e = cudaEventSynchronize(done);
+    for (size_t k = 0; e == cudaSuccess && k + 1 < ev.size(); k += 2) {
+      float t = 0.f;
+      e = cudaEventElapsedTime(&t, ev[k], ev[k + 1]);
+      *ms += t;
+      ++*n;
+    }
+    return e;
+  }
+  cudaError_t launch(cudaStream_t s) {
+    cudaError_t e = cudaGraphLaunch(exec, s);
+    if (e == cudaSuccess && done) {
+      e = cudaEventRecord(done, s);
+      pending = e == cudaSuccess;
+    }
+    return e;
+  }
+  void destroy() {
+    if (exec) cudaGraphExecDestroy(exec);
+    for (cudaEvent_t x : ev) cudaEventDestroy(x);
+    if (done) cudaEventDestroy(done);
+    exec = nullptr;
+    ev.clear();
+    done = nullptr;
+    pending = false;
+  }
+};
+
 }  // namespace
 
 void wlbm::set_global_error_msg(const std::string& m) { set_global_error(m); }
@@ -74,7 +132,10 @@ struct wlbm_handle {
   std::string tmap_why;       // why there is no tensor map
   int graph_steps = 0;        // >0: replay chunks of this many steps as one CUDA graph
   int fuse_periodic = 0;      // 1: both axes periodic, the step kernel mirrors the edges
-  cudaGraphExec_t graphs[3] = {nullptr, nullptr, nullptr};   // per energy-plane role
+  // per energy-plane role and replay parity (consecutive replays alternate, so a graph's
+  // event pairs are read while the other one runs)
+  TimedGraph graphs[3][2];
+  int graph_parity = 0;
   int64_t graph_launches = 0; // kernels per graph replay
   std::vector<void*> owned;
   // host staging
@@ -116,6 +177,8 @@ struct wlbm_handle {
   int64_t prof_tick = 0;              // step launches seen while profiling
   std::vector<cudaEvent_t> prof_ev;   // pairs (start, stop)
   size_t prof_used = 0;
+  double prof_graph_ms = 0.0;         // read from replayed graphs, not yet reported
+  int64_t prof_graph_n = 0;
 
   size_t elem() const { return storage == WLBM_STORE_BF16_DEV ? 2 : 4; }
   float* w_dev() const { return consts; }
@@ -155,11 +218,13 @@ struct wlbm_handle {
       return;
     }
   }
+  // Destroys the graphs, keeping the timings of their latest replays for the next read.
   void drop_graphs() {
-    for (auto& gx : graphs) {
-      if (gx) cudaGraphExecDestroy(gx);
-      gx = nullptr;
-    }
+    for (auto& role : graphs)
+      for (TimedGraph& tg : role) {
+        tg.harvest(&prof_graph_ms, &prof_graph_n);
+        tg.destroy();
+      }
   }
   void release() {
     drop_graphs();
@@ -592,8 +657,12 @@ wlbm_status wlbm_init_temperature(wlbm_handle* h, const float* dT) {
 }
 
 // Launch the kernels of `count` steps whose codes sit at d_codes[t][q], t < count.
-// every > 0: an event pair around every every-th step-kernel launch (counted across calls)
-static wlbm_status enqueue_steps(wlbm_handle* h, int count, int every) {
+// every > 0: an event pair around every every-th step-kernel launch (counted across calls;
+// while capturing a graph, `cap` holds the graph's pairs and the steps t with t % every == 0
+// of the chunk are timed)
+static wlbm_status enqueue_steps(wlbm_handle* h, int count, int every,
+                                 const std::vector<cudaEvent_t>* cap = nullptr) {
+  size_t cap_used = 0;
   const Geom& g = h->g;
   const bool any_wall = h->walls.nseg > 0;
   // both axes periodic: the step kernel mirrors the edges itself (grids of 2+ cells)
@@ -646,26 +715,32 @@ static wlbm_status enqueue_steps(wlbm_handle* h, int count, int every) {
     int tx_unused = 0, ty_unused = 0;
     tma_cover(h->bc_kind, g.nx, g.ny, &sa, &tx_unused, &ty_unused);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
-    if (every > 0 && h->prof_tick++ % every == 0) {
-      if (h->prof_used + 2 > h->prof_ev.size()) {
-        for (int k = 0; k < 2; ++k) {
-          cudaEvent_t ev;
-          st = h->cuda(cudaEventCreate(&ev), "wlbm_step: profiling event");
-          if (st != WLBM_OK) return st;
-          h->prof_ev.push_back(ev);
+    if (every > 0 && (cap ? t % every == 0 : h->prof_tick++ % every == 0)) {
+      if (cap) {
+        e0 = (*cap)[cap_used];
+        e1 = (*cap)[cap_used + 1];
+        cap_used += 2;
+      } else {
+        if (h->prof_used + 2 > h->prof_ev.size()) {
+          for (int k = 0; k < 2; ++k) {
+            cudaEvent_t ev;
+            st = h->cuda(cudaEventCreate(&ev), "wlbm_step: profiling event");
+            if (st != WLBM_OK) return st;
+            h->prof_ev.push_back(ev);
+          }
         }
+        e0 = h->prof_ev[h->prof_used];
+        e1 = h->prof_ev[h->prof_used + 1];
+        h->prof_used += 2;
       }
-      e0 = h->prof_ev[h->prof_used];
-      e1 = h->prof_ev[h->prof_used + 1];
-      h->prof_used += 2;
-      st = h->cuda(cudaEventRecord(e0, h->stream), "wlbm_step: profiling");
+      st = h->cuda(record_event(e0, h->stream, cap != nullptr), "wlbm_step: profiling");
       if (st != WLBM_OK) return st;
     }
     st = h->cuda(launch_step(h->storage, sa, h->stream), "wlbm_step: step");
     if (st != WLBM_OK) return st;
     ++h->launches;
     if (e1) {
-      st = h->cuda(cudaEventRecord(e1, h->stream), "wlbm_step: profiling");
+      st = h->cuda(record_event(e1, h->stream, cap != nullptr), "wlbm_step: profiling");
       if (st != WLBM_OK) return st;
     }
     h->rotate_energy();
@@ -675,39 +750,60 @@ static wlbm_status enqueue_steps(wlbm_handle* h, int count, int every) {
 
 // Replay (capturing on first use) a CUDA graph of graph_steps steps.  The energy-plane
 // roles return to the same state after a multiple of 6 steps, so one graph per starting
-// role serves every chunk.
+// role (and replay parity) serves every chunk.  While profiling, the graph times the steps
+// t % prof_every == 0 of its chunk; the pairs of its previous replay, two chunks back, are
+// read before it replays again.
 static wlbm_status run_graph(wlbm_handle* h) {
   const int G = h->graph_steps;
-  const int phase = h->e_cur;
-  if (!h->graphs[phase]) {
+  TimedGraph& tg = h->graphs[h->e_cur][h->graph_parity];
+  h->graph_parity ^= 1;
+  if (!tg.exec) {
+    const int every = h->prof_every;
+    wlbm_status st = h->cuda(tg.make_events(every > 0 ? (G + every - 1) / every : 0),
+                             "wlbm_step: graph events");
+    if (st != WLBM_OK) {
+      tg.destroy();
+      return st;
+    }
     const int64_t launches0 = h->launches;
-    wlbm_status st = h->cuda(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal),
-                             "wlbm_step: graph capture");
-    if (st != WLBM_OK) return st;
-    const wlbm_status est = enqueue_steps(h, G, 0);
+    st = h->cuda(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal),
+                 "wlbm_step: graph capture");
+    if (st != WLBM_OK) {
+      tg.destroy();
+      return st;
+    }
+    const wlbm_status est = enqueue_steps(h, G, every, &tg.ev);
     cudaGraph_t graph = nullptr;
     const cudaError_t ce = cudaStreamEndCapture(h->stream, &graph);
     if (est != WLBM_OK) {
       if (graph) cudaGraphDestroy(graph);
+      tg.destroy();
       return est;
     }
     st = h->cuda(ce, "wlbm_step: graph capture");
     if (st == WLBM_OK)
-      st = h->cuda(cudaGraphInstantiate(&h->graphs[phase], graph, 0), "wlbm_step: graph");
+      st = h->cuda(cudaGraphInstantiate(&tg.exec, graph, 0), "wlbm_step: graph");
     if (graph) cudaGraphDestroy(graph);
-    if (st != WLBM_OK) return st;
+    if (st != WLBM_OK) {
+      tg.destroy();
+      return st;
+    }
     h->graph_launches = h->launches - launches0;
     h->launches = launches0;
+  } else {
+    const wlbm_status st =
+        h->cuda(tg.harvest(&h->prof_graph_ms, &h->prof_graph_n), "wlbm_step: graph timing");
+    if (st != WLBM_OK) return st;
   }
   h->launches += h->graph_launches;
-  return h->cuda(cudaGraphLaunch(h->graphs[phase], h->stream), "wlbm_step: graph launch");
+  return h->cuda(tg.launch(h->stream), "wlbm_step: graph launch");
 }
 
 wlbm_status wlbm_step(wlbm_handle* h, int64_t n) {
   if (!h) return WLBM_ERR_INVALID_ARG;
   if (n < 0) return h->fail(WLBM_ERR_INVALID_ARG, "wlbm_step: negative step count");
   const Geom& g = h->g;
-  const bool graphs = h->graph_steps > 0 && h->prof_every == 0 && h->stream != nullptr;
+  const bool graphs = h->graph_steps > 0 && h->stream != nullptr;
   while (n > 0) {
     const int ch = int(std::min<int64_t>(n, graphs ? h->graph_steps : kChunk));
     const int slot = h->slot;
@@ -786,6 +882,7 @@ wlbm_status wlbm_check(wlbm_handle* h) {
 wlbm_status wlbm_profile(wlbm_handle* h, int32_t every) {
   if (!h) return WLBM_ERR_INVALID_ARG;
   if (every < 0) return h->fail(WLBM_ERR_INVALID_ARG, "wlbm_profile: negative stride");
+  if (every != h->prof_every) h->drop_graphs();   // their event nodes follow the stride
   h->prof_every = every;
   h->prof_tick = 0;
   return WLBM_OK;
@@ -796,7 +893,12 @@ wlbm_status wlbm_profile_read(wlbm_handle* h, double* step_ms, int64_t* step_lau
   if (!h) return WLBM_ERR_INVALID_ARG;
   wlbm_status st = h->cuda(cudaStreamSynchronize(h->stream), "wlbm_profile_read");
   if (st != WLBM_OK) return st;
-  double total = 0.0;
+  for (auto& role : h->graphs)
+    for (TimedGraph& tg : role) {
+      st = h->cuda(tg.harvest(&h->prof_graph_ms, &h->prof_graph_n), "wlbm_profile_read");
+      if (st != WLBM_OK) return st;
+    }
+  double total = h->prof_graph_ms;
   for (size_t k = 0; k + 1 < h->prof_used; k += 2) {
     float ms = 0.f;
     st = h->cuda(cudaEventElapsedTime(&ms, h->prof_ev[k], h->prof_ev[k + 1]), "wlbm_profile_read");
@@ -804,9 +906,11 @@ wlbm_status wlbm_profile_read(wlbm_handle* h, double* step_ms, int64_t* step_lau
     total += ms;
   }
   if (step_ms) *step_ms = total;
-  if (step_launches) *step_launches = int64_t(h->prof_used / 2);
+  if (step_launches) *step_launches = h->prof_graph_n + int64_t(h->prof_used / 2);
   if (all_launches) *all_launches = h->launches;
   h->prof_used = 0;
+  h->prof_graph_ms = 0.0;
+  h->prof_graph_n = 0;
   return WLBM_OK;
 }
 
@@ -1501,16 +1605,21 @@ struct wlbm_batch {
   std::vector<int> per;             // instances whose periodic edges need their own launch
   // Captured chunks, keyed by the energy-plane phases of the instances in `per` (their
   // periodic launches bake plane pointers; the batched kernels read phases at run time).
+  // Two per key (replay parity), as for a single grid.
   struct Graph {
     std::vector<int> key;
-    cudaGraphExec_t exec = nullptr;
+    int parity = 0;
+    TimedGraph tg;
   };
   std::vector<Graph> graphs;
+  int graph_parity = 0;
   int64_t graph_launches = 0, launches = 0;
   int prof_every = 0;
   int64_t prof_tick = 0;
   std::vector<cudaEvent_t> prof_ev;
   size_t prof_used = 0;
+  double prof_graph_ms = 0.0;
+  int64_t prof_graph_n = 0;
   std::string err;
 
   wlbm_status fail(wlbm_status s, const std::string& m) {
@@ -1534,7 +1643,10 @@ struct wlbm_batch {
     return p;
   }
   void drop_graph() {
-    for (Graph& gr : graphs) cudaGraphExecDestroy(gr.exec);
+    for (Graph& gr : graphs) {
+      gr.tg.harvest(&prof_graph_ms, &prof_graph_n);
+      gr.tg.destroy();
+    }
     graphs.clear();
   }
   std::vector<int> phase_key() const {
@@ -1750,7 +1862,9 @@ wlbm_status wlbm_batch_set_option(wlbm_batch* b, int32_t key, int64_t value) {
 }  // extern "C"
 
 // Kernels of `count` steps for the whole batch, instance records already on the device.
-static wlbm_status batch_enqueue(wlbm_batch* b, int count, int every) {
+static wlbm_status batch_enqueue(wlbm_batch* b, int count, int every,
+                                 const std::vector<cudaEvent_t>* cap = nullptr) {
+  size_t cap_used = 0;
   const int n = int(b->h.size());
   wlbm_status st = WLBM_OK;
   bool any_spec = false;
@@ -1778,18 +1892,26 @@ static wlbm_status batch_enqueue(wlbm_batch* b, int count, int every) {
     }
     if (st != WLBM_OK) break;
     cudaEvent_t e1 = nullptr;
-    if (every > 0 && b->prof_tick++ % every == 0) {
-      if (b->prof_used + 2 > b->prof_ev.size()) {
-        for (int j = 0; j < 2; ++j) {
-          cudaEvent_t ev;
-          st = b->cuda(cudaEventCreate(&ev), "wlbm_batch_step: profiling");
-          if (st != WLBM_OK) return st;
-          b->prof_ev.push_back(ev);
+    if (every > 0 && (cap ? t % every == 0 : b->prof_tick++ % every == 0)) {
+      cudaEvent_t e0 = nullptr;
+      if (cap) {
+        e0 = (*cap)[cap_used];
+        e1 = (*cap)[cap_used + 1];
+        cap_used += 2;
+      } else {
+        if (b->prof_used + 2 > b->prof_ev.size()) {
+          for (int j = 0; j < 2; ++j) {
+            cudaEvent_t ev;
+            st = b->cuda(cudaEventCreate(&ev), "wlbm_batch_step: profiling");
+            if (st != WLBM_OK) return st;
+            b->prof_ev.push_back(ev);
+          }
         }
+        e0 = b->prof_ev[b->prof_used];
+        e1 = b->prof_ev[b->prof_used + 1];
+        b->prof_used += 2;
       }
-      st = b->cuda(cudaEventRecord(b->prof_ev[b->prof_used], b->stream), "profiling");
-      e1 = b->prof_ev[b->prof_used + 1];
-      b->prof_used += 2;
+      st = b->cuda(record_event(e0, b->stream, cap != nullptr), "profiling");
     }
     if (st == WLBM_OK)
       st = b->cuda(b->variant == 3
@@ -1799,7 +1921,7 @@ static wlbm_status batch_enqueue(wlbm_batch* b, int count, int every) {
                                            t, b->stream),
                    "wlbm_batch_step: step");
     ++b->launches;
-    if (st == WLBM_OK && e1) st = b->cuda(cudaEventRecord(e1, b->stream), "profiling");
+    if (st == WLBM_OK && e1) st = b->cuda(record_event(e1, b->stream, cap != nullptr), "profiling");
   }
   return st;
 }
@@ -1810,7 +1932,7 @@ wlbm_status wlbm_batch_step(wlbm_batch* b, int64_t n) {
   if (!b) return WLBM_ERR_INVALID_ARG;
   if (n < 0) return b->fail(WLBM_ERR_INVALID_ARG, "wlbm_batch_step: negative step count");
   const int ni = int(b->h.size());
-  const bool graphs = b->graph_steps > 0 && b->prof_every == 0 && b->stream;
+  const bool graphs = b->graph_steps > 0 && b->stream;
   while (n > 0) {
     const int ch = int(std::min<int64_t>(n, graphs ? b->graph_steps : kBatchChunk));
     wlbm_status st = b->cuda(cudaEventSynchronize(b->ev), "wlbm_batch_step");
@@ -1864,30 +1986,47 @@ wlbm_status wlbm_batch_step(wlbm_batch* b, int64_t n) {
     if (st != WLBM_OK) return st;
     if (graphs && ch == b->graph_steps) {
       const std::vector<int> key = b->phase_key();
-      cudaGraphExec_t exec = nullptr;
-      for (const wlbm_batch::Graph& gr : b->graphs)
-        if (gr.key == key) exec = gr.exec;
-      if (!exec) {
-        if (b->graphs.size() >= 3) b->drop_graph();
+      const int parity = b->graph_parity;
+      b->graph_parity ^= 1;
+      TimedGraph* tg = nullptr;
+      for (wlbm_batch::Graph& gr : b->graphs)
+        if (gr.key == key && gr.parity == parity) tg = &gr.tg;
+      if (!tg) {
+        if (b->graphs.size() >= 6) b->drop_graph();
+        TimedGraph fresh;
+        const int every = b->prof_every;
+        st = b->cuda(fresh.make_events(every > 0 ? (ch + every - 1) / every : 0),
+                     "wlbm_batch_step: graph events");
         const int64_t l0 = b->launches;
-        st = b->cuda(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal),
-                     "wlbm_batch_step: capture");
-        if (st != WLBM_OK) return st;
-        const wlbm_status est = batch_enqueue(b, ch, 0);
+        if (st == WLBM_OK)
+          st = b->cuda(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal),
+                       "wlbm_batch_step: capture");
+        if (st != WLBM_OK) {
+          fresh.destroy();
+          return st;
+        }
+        const wlbm_status est = batch_enqueue(b, ch, every, &fresh.ev);
         cudaGraph_t gr = nullptr;
         const cudaError_t ce = cudaStreamEndCapture(b->stream, &gr);
         if (est == WLBM_OK) st = b->cuda(ce, "wlbm_batch_step: capture");
         else st = est;
         if (st == WLBM_OK)
-          st = b->cuda(cudaGraphInstantiate(&exec, gr, 0), "wlbm_batch_step: graph");
+          st = b->cuda(cudaGraphInstantiate(&fresh.exec, gr, 0), "wlbm_batch_step: graph");
         if (gr) cudaGraphDestroy(gr);
-        if (st != WLBM_OK) return st;
-        b->graphs.push_back({key, exec});
+        if (st != WLBM_OK) {
+          fresh.destroy();
+          return st;
+        }
+        b->graphs.push_back({key, parity, fresh});
+        tg = &b->graphs.back().tg;
         b->graph_launches = b->launches - l0;
         b->launches = l0;
+      } else {
+        st = b->cuda(tg->harvest(&b->prof_graph_ms, &b->prof_graph_n), "wlbm_batch_step: timing");
+        if (st != WLBM_OK) return st;
       }
       b->launches += b->graph_launches;
-      st = b->cuda(cudaGraphLaunch(exec, b->stream), "wlbm_batch_step: graph launch");
+      st = b->cuda(tg->launch(b->stream), "wlbm_batch_step: graph launch");
     } else {
       st = batch_enqueue(b, ch, b->prof_every);
     }
@@ -1902,6 +2041,7 @@ wlbm_status wlbm_batch_step(wlbm_batch* b, int64_t n) {
 wlbm_status wlbm_batch_profile(wlbm_batch* b, int32_t every) {
   if (!b) return WLBM_ERR_INVALID_ARG;
   if (every < 0) return b->fail(WLBM_ERR_INVALID_ARG, "wlbm_batch_profile: negative stride");
+  if (every != b->prof_every) b->drop_graph();   // their event nodes follow the stride
   b->prof_every = every;
   b->prof_tick = 0;
   return WLBM_OK;
@@ -1912,7 +2052,11 @@ wlbm_status wlbm_batch_profile_read(wlbm_batch* b, double* step_ms, int64_t* ste
   if (!b) return WLBM_ERR_INVALID_ARG;
   wlbm_status st = b->cuda(cudaStreamSynchronize(b->stream), "wlbm_batch_profile_read");
   if (st != WLBM_OK) return st;
-  double total = 0.0;
+  for (wlbm_batch::Graph& gr : b->graphs) {
+    st = b->cuda(gr.tg.harvest(&b->prof_graph_ms, &b->prof_graph_n), "profile_read");
+    if (st != WLBM_OK) return st;
+  }
+  double total = b->prof_graph_ms;
   for (size_t k = 0; k + 1 < b->prof_used; k += 2) {
     float ms = 0.f;
     st = b->cuda(cudaEventElapsedTime(&ms, b->prof_ev[k], b->prof_ev[k + 1]), "profile_read");
@@ -1920,9 +2064,11 @@ wlbm_status wlbm_batch_profile_read(wlbm_batch* b, double* step_ms, int64_t* ste
     total += ms;
   }
   if (step_ms) *step_ms = total;
-  if (step_launches) *step_launches = int64_t(b->prof_used / 2);
+  if (step_launches) *step_launches = b->prof_graph_n + int64_t(b->prof_used / 2);
   if (all_launches) *all_launches = b->launches;
   b->prof_used = 0;
+  b->prof_graph_ms = 0.0;
+  b->prof_graph_n = 0;
   return WLBM_OK;
 }
 

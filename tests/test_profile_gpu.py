@@ -1,7 +1,7 @@
 """Step-kernel timing through the C ABI (wlbm_profile / wlbm_profile_read and the batch
-forms): an event pair around every S-th step-kernel launch, counted across calls; a
-negative stride is refused; profiling changes no result, also where it turns graph replay
-off."""
+forms): an event pair around every S-th step-kernel launch, counted across calls, or,
+under graph replay, the steps of each chunk that the stride selects, recorded by the
+graph's event nodes; a negative stride is refused; profiling changes no result."""
 import numpy as np
 import pytest
 
@@ -51,36 +51,63 @@ def test_stride_counts_launches_across_calls():
     h.close()
 
 
-def test_profiling_changes_no_result():
+def _streamed(cfg, storage, stream):
+    import paper_1911_00180_gb300 as wl
+    from tests._pair import THETA
+    return wl.WormLBM(cfg["nx"], cfg["ny"], cfg["q"], mfp=cfg["mfp"], bc=cfg["bc"],
+                      t_wall=cfg["t_wall"], storage=storage, emulate_3d=cfg["emulate_3d"],
+                      theta=THETA, stream=stream)
+
+
+def test_graph_replay_is_timed_and_changes_no_result():
+    """Graph replay of 12-step chunks with stride 4: every replay times its steps 0, 4 and 8
+    through event nodes of the graph, the direct steps after the last whole chunk count on
+    from the stride's start; the states equal those of an untimed run launched step by
+    step, bit for bit."""
+    import torch
     import paper_1911_00180_gb300 as wl
     cfg = W.film_c3(kn=0.5, nx=96, ny=24, q=24)
-    a = gpu_handle(cfg, 1)
-    b = gpu_handle(cfg, 1)
-    b.wlbm_set_option(wl.wlbm.OPT_GRAPH_STEPS, 12)
-    b.wlbm_profile(5)                    # graph replay is off while profiling
-    for h in (a, b):
-        h.wlbm_init_temperature(cfg["dT"])
-        h.wlbm_step(31)
-    b.wlbm_profile(0)                    # and back on for the rest
-    for h in (a, b):
-        h.wlbm_step(24)
-    assert np.array_equal(_state(a), _state(b))
-    assert b.wlbm_profile_read()[1] == 7  # launches 0, 5, ..., 30
-    a.close()
-    b.close()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        a = _streamed(cfg, 1, s)
+        b = _streamed(cfg, 1, s)
+        b.wlbm_set_option(wl.wlbm.OPT_GRAPH_STEPS, 12)
+        b.wlbm_profile(4)
+        for h in (a, b):
+            h.wlbm_init_temperature(cfg["dT"])
+            h.wlbm_step(24)
+        ms, n, _ = b.wlbm_profile_read()
+        assert n == 6 and ms > 0.0            # two replays x steps 0, 4, 8
+        for h in (a, b):
+            h.wlbm_step(3 * 12 + 5)
+        assert b.wlbm_profile_read()[1] == 3 * 3 + 2   # + direct steps 0 and 4 of 5
+        b.wlbm_profile(0)                     # drops the timed graphs; untimed replay on
+        for h in (a, b):
+            h.wlbm_step(24)
+        assert b.wlbm_profile_read()[1] == 0
+        assert np.array_equal(_state(a), _state(b))
+        a.close()
+        b.close()
 
 
-def test_batch_stride():
+@pytest.mark.parametrize("graph", [0, 6])
+def test_batch_stride(graph):
+    import torch
     import paper_1911_00180_gb300 as wl
     cfg = W.film_c3(kn=1.0, nx=40, ny=12, q=16)
     spec = dict(nx=40, ny=12, q=16, bc=cfg["bc"], t_wall=cfg["t_wall"], mfp=12.0,
                 emulate_3d=True)
-    b = wl.WormLBMBatch([spec, dict(spec, q=24)])
-    b.wlbm_batch_init_temperature([cfg["dT"], cfg["dT"]])
-    b.wlbm_batch_profile(2)
-    b.wlbm_batch_step(5)                 # launches 0, 2, 4
-    ms, n, _ = b.wlbm_batch_profile_read()
-    assert n == 3 and ms > 0.0
-    with pytest.raises(wl.WlbmError):
-        b.wlbm_batch_profile(-1)
-    b.close()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        b = wl.WormLBMBatch([spec, dict(spec, q=24)], stream=s)
+        b.wlbm_batch_set_option(wl.wlbm.OPT_GRAPH_STEPS, graph)
+        b.wlbm_batch_init_temperature([cfg["dT"], cfg["dT"]])
+        b.wlbm_batch_profile(2)
+        b.wlbm_batch_step(6)             # launches 0, 2, 4 (directly or in one replay)
+        ms, n, _ = b.wlbm_batch_profile_read()
+        assert n == 3 and ms > 0.0
+        b.wlbm_batch_step(18)            # three more chunks of 6
+        assert b.wlbm_batch_profile_read()[1] == 9
+        with pytest.raises(wl.WlbmError):
+            b.wlbm_batch_profile(-1)
+        b.close()
