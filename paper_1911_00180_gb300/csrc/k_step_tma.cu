@@ -443,14 +443,15 @@ __global__ void __maxnreg__(128) k_step_tma_batch(const BatchInst* insts, int n,
   else step_tma_tile<T, S, false, REF>(sa, tm, tile[0], tile[1], smem);
 }
 
-template <typename T, int S>
+// BATCH: also the batched form of the same storage and ring depth.
+template <typename T, int S, bool BATCH>
 cudaError_t configure_tma_t() {
   const int bytes = int(TmaLayout<T, S>::bytes(kMaxQ));
   const void* fns[3] = {(const void*)k_step_tma<T, S, false, sizeof(T) == 2>,
                         (const void*)k_step_tma<T, S, true, sizeof(T) == 2>,
-                        (const void*)k_step_tma_batch<T, S, sizeof(T) == 2>};
+                        BATCH ? (const void*)k_step_tma_batch<T, S, sizeof(T) == 2> : nullptr};
   cudaError_t e = cudaSuccess;
-  for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
+  for (int k = 0; k < 3 && fns[k] && e == cudaSuccess; ++k) {
     e = cudaFuncSetAttribute(fns[k], cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     // several blocks per SM: ask for the largest shared-memory carveout
     if (e == cudaSuccess)
@@ -474,12 +475,18 @@ cudaError_t launch_tma_t(const StepArgs& a, const CUtensorMap& tm, cudaStream_t 
 
 constexpr int kStagesF32 = 6;    // 6 x 7.4 KB of boxes in flight per block
 constexpr int kStagesBF16 = 8;   // 8 x 4 KB
+// Single grids with Q <= kDeepMaxQ: 16 bfloat16 stages.  Measured: 2048^2 x Q64 0.223 ->
+// 0.217 ms a launch (8 -> 16 stages), while the 4096 x 256 x Q128 film slowed from 0.108
+// to 0.114 ms (and 6 stages were slower on both).
+constexpr int kStagesBF16Deep = 16;
+constexpr int kDeepMaxQ = 64;
 
 }  // namespace
 
 cudaError_t configure_step_tma() {
-  cudaError_t e = configure_tma_t<float, kStagesF32>();
-  if (e == cudaSuccess) e = configure_tma_t<__nv_bfloat16, kStagesBF16>();
+  cudaError_t e = configure_tma_t<float, kStagesF32, true>();
+  if (e == cudaSuccess) e = configure_tma_t<__nv_bfloat16, kStagesBF16, true>();
+  if (e == cudaSuccess) e = configure_tma_t<__nv_bfloat16, kStagesBF16Deep, false>();
   return e;
 }
 
@@ -519,7 +526,9 @@ void tma_cover(const int bc_kind[4], int nx, int ny, StepArgs* a, int* tiles_x, 
 
 cudaError_t launch_step_tma(int storage, const StepArgs& a, cudaStream_t s) {
   const CUtensorMap& tm = *static_cast<const CUtensorMap*>(a.tmap);
-  if (storage == WLBM_STORE_BF16_DEV) return launch_tma_t<__nv_bfloat16, kStagesBF16>(a, tm, s);
+  if (storage == WLBM_STORE_BF16_DEV)
+    return a.q <= kDeepMaxQ ? launch_tma_t<__nv_bfloat16, kStagesBF16Deep>(a, tm, s)
+                            : launch_tma_t<__nv_bfloat16, kStagesBF16>(a, tm, s);
   return launch_tma_t<float, kStagesF32>(a, tm, s);
 }
 
