@@ -475,10 +475,13 @@ cudaError_t launch_tma_t(const StepArgs& a, const CUtensorMap& tm, cudaStream_t 
 
 constexpr int kStagesF32 = 6;    // 6 x 7.4 KB of boxes in flight per block
 constexpr int kStagesBF16 = 8;   // 8 x 4 KB
-// Single grids with Q <= kDeepMaxQ: 16 bfloat16 stages.  Measured: 2048^2 x Q64 0.223 ->
-// 0.217 ms a launch (8 -> 16 stages), while the 4096 x 256 x Q128 film slowed from 0.108
-// to 0.114 ms (and 6 stages were slower on both).
+// Ring depth by Q for single grids, from sweeps on 2048^2 x Q64 and 4096 x 256 x Q128:
+// bfloat16 Q <= kDeepMaxQ takes 16 stages (Q64 0.223 -> 0.217 ms a launch against 8, while
+// the Q128 film slowed from 0.108 to 0.114 ms); float32 Q > kDeepMaxQ takes 4 (Q128 film
+// 0.181 -> 0.175 ms against 6, while Q64 slowed from 0.337 to 0.343 ms).  Batches keep
+// kStagesF32 / kStagesBF16.
 constexpr int kStagesBF16Deep = 16;
+constexpr int kStagesF32Shallow = 4;
 constexpr int kDeepMaxQ = 64;
 
 }  // namespace
@@ -487,6 +490,7 @@ cudaError_t configure_step_tma() {
   cudaError_t e = configure_tma_t<float, kStagesF32, true>();
   if (e == cudaSuccess) e = configure_tma_t<__nv_bfloat16, kStagesBF16, true>();
   if (e == cudaSuccess) e = configure_tma_t<__nv_bfloat16, kStagesBF16Deep, false>();
+  if (e == cudaSuccess) e = configure_tma_t<float, kStagesF32Shallow, false>();
   return e;
 }
 
@@ -529,7 +533,8 @@ cudaError_t launch_step_tma(int storage, const StepArgs& a, cudaStream_t s) {
   if (storage == WLBM_STORE_BF16_DEV)
     return a.q <= kDeepMaxQ ? launch_tma_t<__nv_bfloat16, kStagesBF16Deep>(a, tm, s)
                             : launch_tma_t<__nv_bfloat16, kStagesBF16>(a, tm, s);
-  return launch_tma_t<float, kStagesF32>(a, tm, s);
+  return a.q <= kDeepMaxQ ? launch_tma_t<float, kStagesF32>(a, tm, s)
+                          : launch_tma_t<float, kStagesF32Shallow>(a, tm, s);
 }
 
 // Tensor map of the 2q direction planes as a 3-D tensor (columns, rows, planes) with the
