@@ -234,18 +234,30 @@ def _window_oracle(cfg, cx, cy, steps, pad):
     return oracle_run(sub, steps)
 
 
+BENCH_GRAPH, BENCH_PROFILE = 48, 8     # the benchmark's graph chunk and timing stride
+
+
 def _sampled_full_size(cfg, steps, samples, window_fn):
-    """Run the full-size grid on the GPU (the benchmark launch path), then check sampled
-    cells one by one against the oracle on a window around each."""
+    """Run the full-size grid on the GPU in the benchmark's launch configuration (its own
+    stream, 48-step CUDA-graph replays, event timing of every 8th step kernel), then
+    check sampled cells one by one against the oracle on a window around each."""
     import torch
+    import paper_1911_00180_gb300 as wl
     from oracle import lattice as L
-    from tests._pair import gpu_handle
-    h = gpu_handle(cfg)
-    h.wlbm_init_temperature(cfg["dT"])
-    h.wlbm_step(steps)
-    dT, _, _ = h.wlbm_moments(want_q=False)
-    state = h.wlbm_get_state()
-    torch.cuda.synchronize()
+    from tests._pair import THETA
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        h = wl.WormLBM(cfg["nx"], cfg["ny"], cfg["q"], mfp=cfg["mfp"], bc=cfg["bc"],
+                       t_wall=cfg["t_wall"], storage=0, emulate_3d=cfg["emulate_3d"],
+                       relax_mode=cfg.get("relax_mode", 0), theta=THETA, stream=stream)
+        h.wlbm_set_option(wl.wlbm.OPT_GRAPH_STEPS, BENCH_GRAPH)
+        h.wlbm_profile(BENCH_PROFILE)
+        h.wlbm_init_temperature(cfg["dT"])
+        h.wlbm_step(steps)
+        dT, _, _ = h.wlbm_moments(want_q=False)
+        state = h.wlbm_get_state()
+        stream.synchronize()
+        assert h.wlbm_profile_read()[1] == steps // BENCH_PROFILE
     w = L.angular_weights(L.ring_directions(cfg["q"]))
     dscale = float(w.max() * (L.e_eq(301.0, 624.8074248458514) - L.e_eq(300.0, 624.8074248458514)))
     for (cx, cy) in samples:
@@ -258,9 +270,10 @@ def _sampled_full_size(cfg, steps, samples, window_fn):
 
 
 def test_full_size_c2_sampled_cells():
-    """2048 x 2048, Q = 64, periodic, 16 pulses (the benchmark workload)."""
+    """2048 x 2048, Q = 64, periodic, 16 pulses (the benchmark workload), one 48-step
+    graph replay."""
     cfg = W.pulses_c2(seed=2)
-    steps, pad = 16, 18
+    steps, pad = BENCH_GRAPH, BENCH_GRAPH + 2
     rng = np.random.default_rng(0)
     samples = [tuple(int(v) for v in rng.integers(0, 2048, size=2)) for _ in range(5)]
     # plus the hottest cell, where the pulse signal is largest
@@ -275,9 +288,9 @@ def test_full_size_c2_sampled_cells():
 def test_full_size_c3_film_sampled_cells():
     """4096 x 256 film, Q = 128, isothermal x walls, diffuse y walls: sampled cells
     (including ones next to the diffuse walls) against the oracle on an x-window that
-    keeps the full film thickness and its walls."""
+    keeps the full film thickness and its walls; one 48-step graph replay."""
     cfg = W.film_c3(kn=1.0)
-    steps, pad = 12, 14
+    steps, pad = BENCH_GRAPH, BENCH_GRAPH + 2
     samples = [(1000, 0), (2500, 255), (3100, 128), (7, 40), (4090, 200)]
 
     def window(cfg, cx, cy, steps):
