@@ -130,6 +130,26 @@ def workload(args):
     return W.pulses_c2(seed=args.seed, n=args.nx, q=args.q)
 
 
+def batch_config(args, n_all):
+    """The `config` keys that name the batched workload (both arms print them)."""
+    return {"workload": "batch_c4: 96 films, thickness 16-512, aspect 8-32, Kn 0.01-100, "
+                        "Q in {16..256}, %s storage" % args.storage, "instances": n_all}
+
+
+def workload_config(args, cfg):
+    """The `config` keys that name a single-grid workload (both arms print them)."""
+    if args.workload == "pulses":
+        name = ("pulses_c2 %dx%d periodic, Q=%d, %s deviation storage, uniform MFP %.4g "
+                "cells, 16 Gaussian pulses" % (cfg["nx"], cfg["ny"], cfg["q"], args.storage,
+                                               cfg["mfp"]))
+    else:
+        name = ("film_c3 %dx%d, Q=%d, %s deviation storage, isothermal x walls 301/300 K, "
+                "adiabatic-diffuse y walls, Kn=1 (MFP %.4g cells)"
+                % (cfg["nx"], cfg["ny"], cfg["q"], args.storage, cfg["mfp"]))
+    return {"workload": name, "nx": cfg["nx"], "ny": cfg["ny"], "q": cfg["q"],
+            "mfp_cells": cfg["mfp"]}
+
+
 def run_batch(args):
     """96 in-plane films of uneven thickness (16-512 cells), aspect (8-32), Kn (0.01-100)
     and Q (16-256), bfloat16 storage by default, one wall launch and one step launch per
@@ -199,9 +219,7 @@ def run_batch(args):
             "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "bf16-storage/f32-math" if elem == 2 else "f32",
             "data": "synthetic",
-            "config": {"workload": "batch_c4: 96 films, thickness 16-512, aspect 8-32, "
-                                   "Kn 0.01-100, Q in {16..256}, %s storage" % args.storage,
-                       "instances": n_all, "instances_rank0": len(specs),
+            "config": {**batch_config(args, n_all), "instances_rank0": len(specs),
                        "site_directions": upd, "parallelism": "instances sharded x%d" % world,
                        "autotune": tuned},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -359,27 +377,38 @@ def run_reference(args):
         return 0
     import numpy as np
     from oracle.stepper import WormLBM as Oracle
-    cfg = workload(args)
-    n = 128                                  # bounded sample per bench step
-    m = Oracle(n, n, cfg["q"], cfg["mfp"], emulate_3d=cfg["emulate_3d"],
-               relax_mode=cfg["relax_mode"], theta=624.8074248458514)
-    m.init_temperature(cfg["dT"][:n, :n].astype(np.float64))
+    if args.workload == "batch":
+        import workloads as W
+        insts = W.batch_c4(seed=4)
+        cfg = dict(insts[0], relax_mode=0, mfp=max(insts[0]["mfp"], 1.5))
+        config = batch_config(args, len(insts))
+    else:
+        cfg = workload(args)
+        config = workload_config(args, cfg)
+    # bounded sample per bench step: a 128-column window, 128 rows of the periodic grid or
+    # a film's full thickness (at most 256 rows) with its walls
+    n = min(128, cfg["nx"])
+    rows = min(n, cfg["ny"]) if args.workload == "pulses" else min(256, cfg["ny"])
+    m = Oracle(n, rows, cfg["q"], cfg["mfp"], bc_kind=cfg["bc"], t_wall=cfg["t_wall"],
+               emulate_3d=cfg["emulate_3d"], relax_mode=cfg["relax_mode"],
+               theta=624.8074248458514)
+    m.init_temperature(cfg["dT"][:rows, :n].astype(np.float64))
     for _ in range(args.warmup):
         m.step()
     t0 = time.perf_counter()
     for _ in range(args.steps):
         m.step()
     dt = time.perf_counter() - t0
-    value = cfg["q"] * n * n * args.steps / dt
-    sample = ("each step: one time step of a %dx%d window of the %dx%d workload (Q=%d), "
-              "numpy float64 oracle, single thread" % (n, n, cfg["nx"], cfg["ny"], cfg["q"]))
+    value = cfg["q"] * n * rows * args.steps / dt
+    of = ("instance 0 (%dx%d, Q=%d) of the batch" if args.workload == "batch"
+          else "the %dx%d workload (Q=%d)") % (cfg["nx"], cfg["ny"], cfg["q"])
+    sample = ("each step: one time step of a %dx%d window of %s, numpy float64 oracle, "
+              "single thread" % (n, rows, of))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "pulses_c2 window %dx%d of %dx%d, Q=%d, periodic"
-                       % (n, n, cfg["nx"], cfg["ny"], cfg["q"]), "q": cfg["q"],
-                       "mfp_cells": cfg["mfp"]},
+            "config": config,
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
@@ -508,16 +537,7 @@ def main():
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if args.storage == "fp32" else "bf16-storage/f32-math",
             "data": "synthetic",
-            "config": {"workload": (
-                           "pulses_c2 %dx%d periodic, Q=%d, %s deviation storage, "
-                           "uniform MFP %.4g cells, 16 Gaussian pulses"
-                           % (cfg["nx"], cfg["ny"], cfg["q"], args.storage, cfg["mfp"]))
-                       if args.workload == "pulses" else (
-                           "film_c3 %dx%d, Q=%d, %s deviation storage, isothermal x walls "
-                           "301/300 K, adiabatic-diffuse y walls, Kn=1 (MFP %.4g cells)"
-                           % (cfg["nx"], cfg["ny"], cfg["q"], args.storage, cfg["mfp"])),
-                       "nx": cfg["nx"], "ny": cfg["ny"], "q": cfg["q"],
-                       "mfp_cells": cfg["mfp"], "parallelism": "replicas x%d" % world,
+            "config": {**workload_config(args, cfg), "parallelism": "replicas x%d" % world,
                        "graph_steps": args.graph,
                        "step_kernel": {0: "register-pipelined", 1: "bulk-copy ring",
                                        2: "warp-specialised", 3: "TMA tiles"}[variant_used],
