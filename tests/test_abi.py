@@ -103,3 +103,19 @@ def test_schedule_speed_arguments(wl):
         with pytest.raises(wl.WlbmError) as e:
             wl.wlbm_schedule(16, 10, bad)
         assert e.value.status == wl.wlbm.WLBM_ERR_INVALID_ARG
+
+
+def test_header_is_plain_c(tmp_path):
+    """include/wlbm.h is a C header: a C99 translation unit that includes it compiles with
+    every warning on (no C++ types, no default arguments, no overloads)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "t.c"
+    src.write_text('#include "wlbm.h"\nint main(void) { return (int)WLBM_OK; }\n')
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror",
+                        "-I", os.path.join(ROOT, "include"), "-fsyntax-only", str(src)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
