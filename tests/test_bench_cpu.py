@@ -1,7 +1,8 @@
 """Host logic of bench.py (no GPU): the defaults keep every timed chunk a graph replay and
-the reductions on chunk boundaries, the algorithmic bytes per update are the scope table's,
-and the reference arm (the oracle on the host) prints the native arm's workload config
-with the contract's keys."""
+the reductions on chunk boundaries, the algorithmic bytes per update are one read and one
+write of the stored value plus the local-energy read and write per cell, and the reference
+arm (the oracle on the host) prints the native arm's workload config with the bench line's
+keys."""
 import json
 import os
 import subprocess
