@@ -3,14 +3,16 @@
 The search itself is native (wlbm_autotune / wlbm_batch_autotune time every candidate of
 step-kernel variant x CUDA-graph replay on the real grid).  This module only remembers
 the winner per workload signature in a JSON file, so a later run with the same shapes
-skips the search.  Cache file: $WLBM_AUTOTUNE_CACHE, else _autotune_cache.json next to this
-module.
+skips the search.  The signature covers the GPU model, the storage type, the grids' shapes,
+walls and MFP kind, and the build of libwlbm.so (its size and modification time), so a
+rebuilt library searches again.  Cache file: $WLBM_AUTOTUNE_CACHE, else
+_autotune_cache.json next to this module.
 """
 import hashlib
 import json
 import os
 
-from .wlbm import OPT_GRAPH_STEPS, OPT_STEP_VARIANT
+from .wlbm import LIB_PATH, OPT_GRAPH_STEPS, OPT_STEP_VARIANT
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 
@@ -19,11 +21,19 @@ def _cache_path():
     return os.environ.get("WLBM_AUTOTUNE_CACHE", os.path.join(_HERE, "_autotune_cache.json"))
 
 
+def _build_identity():
+    try:
+        st = os.stat(LIB_PATH)
+        return [st.st_size, st.st_mtime_ns]
+    except OSError:
+        return None
+
+
 def signature(specs, storage):
     import torch
     shapes = sorted((int(s["nx"]), int(s["ny"]), int(s["q"]), tuple(int(k) for k in s["bc"]),
                      s.get("mfp_field") is not None) for s in specs)
-    key = json.dumps([torch.cuda.get_device_name(), int(storage), shapes])
+    key = json.dumps([torch.cuda.get_device_name(), int(storage), shapes, _build_identity()])
     return hashlib.sha1(key.encode()).hexdigest()
 
 

@@ -126,3 +126,25 @@ def test_y_strip_decomposition_with_halo_exchange():
         assert p.exitcode == 0
     got = np.concatenate([res[0], res[1]], axis=1)
     np.testing.assert_array_equal(got, ref.d[:, 1:-1, 1:-1])
+
+
+def test_autotune_cache_signature_and_store(tmp_path, monkeypatch):
+    """The autotuning cache (host logic, no GPU): the signature ignores the order of the
+    grids, separates storage types, shapes and builds of the library, and a stored pick
+    is read back; a damaged cache file reads as empty."""
+    import torch
+    from paper_1911_00180_gb300 import autotune as AT
+    monkeypatch.setattr(torch.cuda, "get_device_name", lambda *a: "GB300 (test)")
+    monkeypatch.setenv("WLBM_AUTOTUNE_CACHE", str(tmp_path / "cache.json"))
+    a = dict(nx=64, ny=16, q=32, bc=(1, 1, 2, 2))
+    b = dict(nx=40, ny=40, q=16, bc=(0, 0, 0, 0), mfp_field=object())
+    s0 = AT.signature([a, b], 0)
+    assert AT.signature([b, a], 0) == s0
+    assert AT.signature([a, b], 1) != s0
+    assert AT.signature([a, dict(b, q=24)], 0) != s0
+    monkeypatch.setattr(AT, "_build_identity", lambda: [1, 2])
+    assert AT.signature([a, b], 0) != s0                  # another build of the library
+    AT._store("k", {"variant": 3, "graph_steps": 48, "ms_per_step": 0.5})
+    assert AT._load()["k"]["graph_steps"] == 48
+    (tmp_path / "cache.json").write_text("{not json")
+    assert AT._load() == {}
