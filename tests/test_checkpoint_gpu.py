@@ -69,22 +69,33 @@ def test_resume_is_bitwise(name, cfg, storage):
 
 
 def test_resume_under_graph_replay():
+    """Graph replay needs a stream of its own (not the legacy default stream): both
+    handles run on one, so their 12-step chunks are captured graphs."""
+    import torch
     import paper_1911_00180_gb300 as wl
+    from tests._pair import THETA
     cfg = W.film_c3(kn=2.0, nx=64, ny=20, q=16)
-    h = gpu_handle(cfg, 1)
-    h.wlbm_set_option(wl.wlbm.OPT_GRAPH_STEPS, 12)
-    h.wlbm_init_temperature(cfg["dT"])
-    h.wlbm_step(29)
-    blob = h.wlbm_save()
-    h.wlbm_step(40)
-    want = _snapshot(h)
-    g = gpu_handle(cfg, 1)
-    g.wlbm_set_option(wl.wlbm.OPT_GRAPH_STEPS, 12)
-    g.wlbm_load(blob)
-    g.wlbm_step(40)
-    _same(_snapshot(g), want)
-    g.close()
-    h.close()
+
+    def make(stream):
+        x = wl.WormLBM(cfg["nx"], cfg["ny"], cfg["q"], mfp=cfg["mfp"], bc=cfg["bc"],
+                       t_wall=cfg["t_wall"], storage=1, emulate_3d=cfg["emulate_3d"],
+                       theta=THETA, stream=stream)
+        x.wlbm_set_option(wl.wlbm.OPT_GRAPH_STEPS, 12)
+        return x
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        h = make(stream)
+        h.wlbm_init_temperature(cfg["dT"])
+        h.wlbm_step(29)
+        blob = h.wlbm_save()
+        h.wlbm_step(40)
+        want = _snapshot(h)
+        g = make(stream)
+        g.wlbm_load(blob)
+        g.wlbm_step(40)
+        _same(_snapshot(g), want)
+        g.close()
+        h.close()
 
 
 def test_load_refuses_mismatches():
