@@ -82,19 +82,23 @@ def _single(spec, dT, steps, storage, fuse=0, variant=3):
                                                 (3, 0, 1)])
 def test_batch_equals_single_grids_bitwise(storage, variant, graph, fuse):
     """37 steps = three 12-step graph replays and one single step; the second call starts
-    the graph chunks on another energy-plane phase (a second captured graph)."""
+    the graph chunks on another energy-plane phase (a second captured graph).  The batch
+    runs on a stream of its own (graph replay is off on the legacy default stream)."""
+    import torch
     import paper_1911_00180_gb300 as wl
     specs = _specs()
     dTs = _dTs(specs)
-    b = wl.WormLBMBatch(specs, storage=storage)
-    b.wlbm_batch_set_option(wl.wlbm.OPT_STEP_VARIANT, variant)
-    b.wlbm_batch_set_option(wl.wlbm.OPT_GRAPH_STEPS, graph)
-    b.wlbm_batch_set_option(wl.wlbm.OPT_FUSE_PERIODIC, fuse)
-    b.wlbm_batch_init_temperature(dTs)
-    b.wlbm_batch_step(37)
-    b.wlbm_batch_step(24)
-    got = [v.wlbm_get_state().cpu().numpy() for v in b.instances]
-    b.close()
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        b = wl.WormLBMBatch(specs, storage=storage, stream=stream)
+        b.wlbm_batch_set_option(wl.wlbm.OPT_STEP_VARIANT, variant)
+        b.wlbm_batch_set_option(wl.wlbm.OPT_GRAPH_STEPS, graph)
+        b.wlbm_batch_set_option(wl.wlbm.OPT_FUSE_PERIODIC, fuse)
+        b.wlbm_batch_init_temperature(dTs)
+        b.wlbm_batch_step(37)
+        b.wlbm_batch_step(24)
+        got = [v.wlbm_get_state().cpu().numpy() for v in b.instances]
+        b.close()
     for k, (spec, dT) in enumerate(zip(specs, dTs)):
         want = _single(spec, dT, 61, storage, fuse, variant)
         assert np.array_equal(_state(spec, got[k]), _state(spec, want)), k
