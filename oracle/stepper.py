@@ -56,7 +56,9 @@ Readings of passages the paper leaves open:
 
 Pins: tests/test_oracle_stepper.py (energy conservation on periodic and adiabatic
 grids, exact ballistic translation, reduction to standard D2Q8 at W = 1, the moment
-recursion, the diffusive Gaussian limit, isothermal steady profile).
+recursion, the diffusive Gaussian limit, isothermal steady profile; for a per-cell W
+field: conservation through paused steps, which every other placement of W(y) and W(s)
+breaks, one step written out term by term, and the uniform field equal to the scalar).
 """
 import math
 

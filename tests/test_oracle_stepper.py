@@ -291,3 +291,92 @@ def test_mean_moments_of_a_ballistic_run():
     np.testing.assert_allclose(mt, st / n, rtol=0, atol=1e-12)
     np.testing.assert_allclose(mqx, sx / n, rtol=0, atol=1e-15)
     np.testing.assert_allclose(mqy, sy / n, rtol=0, atol=1e-15)
+
+
+# ---------------------------------------------------------------------------------------
+# Per-cell relaxation weight.  Eq. lbm-energy and Eq. algorithm print one W; with a field
+# W(x) the oracle takes the loss of a paused DDED at its own cell y and every gain (the
+# EED, which always hops) at the source cell s = y - c.  The pins below fix that reading
+# from outside the step: global conservation (which any other placement of W breaks), one
+# step written out by hand, and the uniform field.
+
+def _lognormal_w(ny, nx, seed):
+    """A rough log-normal MFP field (cells), every W_corr well inside (0, 1)."""
+    g = np.random.default_rng(seed).standard_normal((ny, nx))
+    return np.maximum(np.exp(math.log(4.0) + 0.6 * g), 1.5)
+
+
+def test_energy_conserved_with_per_cell_mfp_field():
+    """Eq. lbm-energy-density with a non-uniform W: the loss (1 - W(y)) d_i(y) of a paused
+    DDED and the gains w_i W(s) E(s) sum to the scattered energy of every cell, so a
+    periodic grid keeps its total to round-off through propagating and paused steps."""
+    ny, nx, q = 19, 23, 16
+    m = WormLBM(nx, ny, q, _lognormal_w(ny, nx, 11))
+    assert np.ptp(m.w_int) > 0.2                       # the field really varies
+    m.init_temperature(_rand(ny, nx, 12))
+    e0 = m.total_energy()
+    scale = np.abs(m.d).sum()
+    sched = L.TasSchedule(q)
+    n_paused = 0
+    for n in range(1, 61):
+        _, paused = sched.advance(n)
+        n_paused += int(np.sum(paused))
+        m.step()
+        assert abs(m.total_energy() - e0) <= 1e-13 * scale
+    assert n_paused > 0                                # paused steps were exercised
+
+
+@pytest.mark.parametrize("q", [8, 16])
+def test_one_step_with_per_cell_w_written_out_by_hand(q):
+    """Two populated directions of one cell y0 (one paused, one propagating at the first
+    step that pauses anything), a distinct W in every cell, one update.  Expected values
+    from Eq. algorithm with the loss of a paused DDED at its own cell and every gain at the
+    source cell, written out term by term:
+        every direction i:      d_i'(y0 + c_i)  gains w_i W(y0) E(y0);
+        propagating b:          d_b'(y0 + c_b) += (1 - W(y0)) b;
+        paused a:               d_a'(y0)        = (1 - W(y0)) a."""
+    nx = ny = 7
+    rng = np.random.default_rng(5 + q)
+    wf = 0.05 + 0.9 * rng.random((ny, nx))             # distinct W in every cell
+    m = WormLBM(nx, ny, q, None, w_field=wf, bc_kind=(P, P, P, P))
+    sched = L.TasSchedule(q)
+    for n in range(1, 200):
+        hops, paused = sched.advance(n)
+        if any(paused):
+            break
+    assert any(paused) and not all(paused)
+    ia = int(np.flatnonzero(paused)[0])
+    ib = int(np.flatnonzero(~np.asarray(paused, bool))[0])
+    Y0, X0 = 4, 3                                       # framed indices of y0
+    a, b = 0.7, -1.3
+    d = np.zeros((q, ny + 2, nx + 2))
+    d[ia, Y0, X0] = a
+    d[ib, Y0, X0] = b
+    E0 = a + b
+    W0 = wf[Y0 - 1, X0 - 1]
+    want = np.zeros_like(d)
+    for i in range(q):
+        cx, cy = L.BASIC_HOPS[hops[i]]
+        want[i, Y0 + cy, X0 + cx] += m.w[i] * W0 * E0
+    cbx, cby = L.BASIC_HOPS[hops[ib]]
+    want[ib, Y0 + cby, X0 + cbx] += (1.0 - W0) * b
+    want[ia, Y0, X0] += (1.0 - W0) * a
+    got = m.collide_stream(d, hops, paused)
+    np.testing.assert_allclose(got, want, rtol=0, atol=1e-15)
+    # the two placements of W the reading rules out give other values here
+    cax, cay = L.BASIC_HOPS[hops[ia]]
+    assert abs(wf[Y0 - 1 - cay, X0 - 1 - cax] - W0) > 1e-3     # W(s) of the paused loss
+    assert abs(wf[Y0 - 1 + cby, X0 - 1 + cbx] - W0) > 1e-3     # W(y) of the propagating one
+
+
+def test_uniform_w_field_equals_scalar_mfp():
+    """A field whose every cell carries the same MFP is the scalar-MFP run, bit for bit."""
+    ny, nx, q = 13, 17, 16
+    dT = _rand(ny, nx, 21)
+    runs = []
+    for mfp in (3.5, np.full((ny, nx), 3.5)):
+        m = WormLBM(nx, ny, q, mfp, bc_kind=(I, I, A, A), t_wall=(301.0, 300.0, 0, 0))
+        m.init_temperature(dT)
+        m.step(25)
+        runs.append(m.d.copy())
+    assert np.array_equal(runs[0], runs[1])
