@@ -22,7 +22,18 @@ roofline  the fused step kernel: algorithmic bytes per launch (8 B per site-dire
           (--profile-every, default 8; under graph replay the steps t of each chunk with
           t % S == 0, recorded by the graph's event nodes), so most steps run without
           event records.
-cpu_baseline  the FP64 oracle on the host cores, on a bounded sample of the same grid.
+cpu_baseline  the FP64 oracle on the host cores, on a bounded sample of the same grid: one
+          thread, and one process per host core each stepping its own window (all cores).
+workloads the other headline workloads, measured in the same run after the timed region
+          (default run only; --no-workloads skips them): pulses with bfloat16 storage, the
+          4096 x 256 film (Q = 128) with float32 and bfloat16 storage, and the 96-film
+          batch with bfloat16 and float32 storage: step-kernel ms per launch from the
+          library's event timing, its fraction of the measured HBM bandwidth, and
+          whole-step updates/s.
+adjoint   the adjoint workload: backward / forward and (checkpointed forward + backward)
+          / forward, the whole gradient's cost against a plain forward run.
+clocks    nvidia-smi samples over the whole native run (warm-up, timed region, e2e and
+          the other workloads), so a short timed region still has a record.
 
 Under torchrun (N > 1) every rank runs an independent replica of the workload (the grid
 does not shard without a halo exchange; replicas only) and the time is the max over
@@ -76,6 +87,10 @@ def parse():
     p.add_argument("--no-extras", action="store_true",
                    help="skip e2e, cpu baseline, adjoint and clock sampling (profiling runs)")
     p.add_argument("--no-adjoint", action="store_true", help="skip the adjoint ratio")
+    p.add_argument("--no-workloads", action="store_true",
+                   help="skip the other headline workloads (bf16 pulses, film, batch)")
+    p.add_argument("--cpu-seconds", type=float, default=10.0,
+                   help="seconds of oracle work per cpu_baseline leg (one thread, all cores)")
     p.add_argument("--adjoint-only", type=int, default=0, metavar="STEPS",
                    help="profiling aid: run only the adjoint workload for STEPS steps and print "
                         "its timings (no bench line)")
@@ -219,8 +234,9 @@ def run_batch(args):
             "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "bf16-storage/f32-math" if elem == 2 else "f32",
             "data": "synthetic",
-            "config": {**batch_config(args, n_all), "instances_rank0": len(specs),
-                       "site_directions": upd, "parallelism": "instances sharded x%d" % world,
+            "config": {**batch_config(args, n_all),
+                       "parallelism": "instances sharded x%d" % world},
+            "launch": {"instances_rank0": len(specs), "site_directions": upd,
                        "autotune": tuned},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None, "kernel": "k_step_*_batch",
@@ -308,27 +324,89 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(cfg, seconds=12.0):
-    """Oracle (numpy float64, one thread) on a bounded sample: a square window of the
-    benchmark grid with the same Q and MFP, stepped until ~`seconds` of work."""
-    import numpy as np
+def _oracle_window_rate(job):
+    """Worker of the host baseline: the oracle on one window of the workload (a dict of the
+    window's start field and the workload's parameters), stepped for about `seconds`;
+    returns (site-direction updates, seconds, steps)."""
+    w, seconds, start_at = job
     from oracle.stepper import WormLBM as Oracle
-    nx, ny = min(512, cfg["nx"]), min(512, cfg["ny"])
-    sub = cfg["dT"][:ny, :nx].astype(np.float64)
-    m = Oracle(nx, ny, cfg["q"], cfg["mfp"], bc_kind=cfg["bc"], t_wall=cfg["t_wall"],
-               emulate_3d=cfg["emulate_3d"], relax_mode=cfg["relax_mode"],
-               theta=624.8074248458514)
-    m.init_temperature(sub)
+    ny, nx = w["dT"].shape
+    m = Oracle(nx, ny, w["q"], w["mfp"], bc_kind=w["bc"], t_wall=w["t_wall"],
+               emulate_3d=w["emulate_3d"], relax_mode=w["relax_mode"], theta=624.8074248458514)
+    m.init_temperature(w["dT"])
+    m.step()                                # first-touch allocations outside the timing
+    while time.time() < start_at:           # all workers start their timing together
+        time.sleep(0.01)
     t0 = time.perf_counter()
     steps = 0
     while time.perf_counter() - t0 < seconds:
         m.step()
         steps += 1
     dt = time.perf_counter() - t0
-    return {"value": cfg["q"] * nx * ny * steps / dt, "unit": UNIT, "cores": 1,
-            "kind": "oracle",
-            "sample": "%d steps of a %dx%d window of the workload (Q=%d, MFP=%.3g), numpy "
-                      "float64 single thread" % (steps, nx, ny, cfg["q"], cfg["mfp"])}
+    return w["q"] * nx * ny * steps, dt, steps
+
+
+def _window(cfg, x0, y0, n):
+    """A periodic window of at most n x n cells of the workload's start field."""
+    import numpy as np
+    nx, ny = min(n, cfg["nx"]), min(n, cfg["ny"])
+    xs = (np.arange(x0, x0 + nx)) % cfg["nx"]
+    ys = (np.arange(y0, y0 + ny)) % cfg["ny"]
+    w = {k: cfg[k] for k in ("q", "mfp", "bc", "t_wall", "emulate_3d", "relax_mode")}
+    w["dT"] = cfg["dT"][np.ix_(ys, xs)].astype(np.float64)
+    return w
+
+
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), or None."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() == "Model name":
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.split(":")[0].strip() in ("model name", "Model", "CPU part"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return None
+
+
+def cpu_baseline(cfg, seconds=10.0, window=256):
+    """The FP64 oracle (numpy, as it stands) on bounded samples of the workload: one
+    thread on one window, then one process per host core (spawned, so no process forks
+    after CUDA is up), each on its own window of the same grid, all at once."""
+    import multiprocessing as mp
+    n = window
+    upd1, dt1, steps1 = _oracle_window_rate((_window(cfg, 0, 0, n), seconds, 0.0))
+    one = upd1 / dt1
+    cores = os.cpu_count() or 1
+    start_at = time.time() + 5.0 + 0.2 * cores     # after every worker has spawned
+    jobs = [(_window(cfg, (k * 997) % cfg["nx"], (k * 613) % cfg["ny"], n), seconds, start_at)
+            for k in range(cores)]
+    env_keep = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS")}
+    os.environ["OMP_NUM_THREADS"] = os.environ["OPENBLAS_NUM_THREADS"] = "1"
+    try:
+        with mp.get_context("spawn").Pool(cores) as pool:
+            res = pool.map(_oracle_window_rate, jobs)
+    finally:
+        for k, v in env_keep.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    allc = sum(u / dt for u, dt, _ in res)
+    rows = min(n, cfg["ny"])
+    return {"value": allc, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "value_one_thread": one, "cpu_model": cpu_model(),
+            "sample": "numpy float64 oracle on %dx%d windows of the workload (Q=%d, MFP=%.3g): "
+                      "one thread %d steps in %.1f s; all cores: %d spawned processes, one "
+                      "window each, timed together for ~%.0f s (%d steps in total)"
+                      % (min(n, cfg["nx"]), rows, cfg["q"], cfg["mfp"], steps1, dt1, cores,
+                         seconds, sum(st for _, _, st in res))}
 
 
 def adjoint_ratio(wl, torch, stream, steps=None):
@@ -368,7 +446,132 @@ def adjoint_ratio(wl, torch, stream, steps=None):
                         "periodic y, %d steps, checkpoints every %d"
                         % (cfg["nx"], cfg["ny"], cfg["q"], n, cfg["ckpt"]),
             "forward_ms": fwd, "checkpointed_forward_ms": fwd_ck, "backward_ms": bwd,
-            "ratio_backward_over_forward": bwd / fwd}
+            "ratio_backward_over_forward": bwd / fwd,
+            "ratio_gradient_over_forward": (fwd_ck + bwd) / fwd,
+            "ratio_note": "backward = segment recompute + reverse sweep (the <= 3x target); "
+                          "gradient = checkpointed forward + backward"}
+
+
+def kernel_fraction(ms_per_launch, algo_bytes):
+    """(achieved GB/s, fraction of the HBM peak, peak, peak kind) of one step-kernel launch."""
+    peak, kind = peaks()
+    achieved = algo_bytes / (ms_per_launch * 1e-3) / 1e9
+    return achieved, achieved / peak, peak, kind
+
+
+def measure_single(wl, torch, cfg, storage, steps, warmup=48, graph=48, every=8):
+    """One single-grid workload in the bench's launch configuration (own stream, graph
+    replay of `graph`-step chunks, event timing of every `every`-th step kernel): whole-step
+    updates/s over `steps` steps and the step kernel's ms per launch and HBM fraction."""
+    st = wl.STORE_BF16_DEV if storage == "bf16" else wl.STORE_FP32_DEV
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        h = wl.WormLBM(cfg["nx"], cfg["ny"], cfg["q"], mfp=cfg["mfp"], bc=cfg["bc"],
+                       t_wall=cfg["t_wall"], storage=st, emulate_3d=cfg["emulate_3d"],
+                       relax_mode=cfg["relax_mode"], stream=stream)
+        h.wlbm_set_option(wl.wlbm.OPT_GRAPH_STEPS, graph)
+        h.wlbm_init_temperature(torch.as_tensor(cfg["dT"]).to("cuda"))
+        h.wlbm_step(warmup)
+        stream.synchronize()
+        h.wlbm_profile_read()
+        h.wlbm_profile(every)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        h.wlbm_step(steps)
+        e1.record(stream)
+        stream.synchronize()
+        h.wlbm_profile(0)
+        ms = e0.elapsed_time(e1)
+        kms, kn, _ = h.wlbm_profile_read()
+        h.wlbm_check()
+        h.close()
+    cells = cfg["nx"] * cfg["ny"]
+    per = kms / kn
+    algo = bytes_per_update(storage, cfg["q"]) * cfg["q"] * cells
+    ach, frac, peak, kind = kernel_fraction(per, algo)
+    return {"updates_per_s": cfg["q"] * cells * steps / (ms * 1e-3),
+            "ms_per_step": ms / steps, "kernel": "k_step_tma", "kernel_ms_per_launch": per,
+            "kernel_launches_timed": kn, "achieved_gbs": ach, "frac": frac, "peak": peak,
+            "peak_kind": kind, "algorithmic_bytes_per_launch": algo,
+            "bytes_per_update": bytes_per_update(storage, cfg["q"]), "steps": steps,
+            "dtype": "f32" if storage == "fp32" else "bf16-storage/f32-math"}
+
+
+def measure_batch(wl, torch, storage, steps, warmup=48, graph=48, every=8):
+    """The 96-film batch (fixed TMA-tile variant, graph replay): whole-step updates/s and
+    the batched step kernel's ms per launch and HBM fraction.  One step streams every
+    instance's planes once, tens of GB in all, so no instance stays in the 129 MB L2
+    from one step to the next: every instance's algorithmic bytes are DRAM bytes."""
+    import workloads as W
+    insts = W.batch_c4(seed=4)
+    specs = [dict(nx=c["nx"], ny=c["ny"], q=c["q"], bc=c["bc"], t_wall=c["t_wall"],
+                  mfp=max(c["mfp"], 1.5), emulate_3d=True) for c in insts]
+    st = wl.STORE_BF16_DEV if storage == "bf16" else wl.STORE_FP32_DEV
+    elem = 2 if storage == "bf16" else 4
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        b = wl.WormLBMBatch(specs, storage=st, stream=stream)
+        b.wlbm_batch_set_option(wl.wlbm.OPT_STEP_VARIANT, 3)
+        b.wlbm_batch_set_option(wl.wlbm.OPT_GRAPH_STEPS, graph)
+        b.wlbm_batch_init_temperature([c["dT"] for c in insts])
+        b.wlbm_batch_step(warmup)
+        stream.synchronize()
+        b.wlbm_batch_profile_read()
+        b.wlbm_batch_profile(every)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.wlbm_batch_step(steps)
+        e1.record(stream)
+        stream.synchronize()
+        b.wlbm_batch_profile(0)
+        ms = e0.elapsed_time(e1)
+        kms, kn, _ = b.wlbm_batch_profile_read()
+        b.close()
+    upd = sum(sp["q"] * sp["nx"] * sp["ny"] for sp in specs)
+    algo = sum(sp["q"] * sp["nx"] * sp["ny"] * (2 * elem + (12.0 if elem == 2 else 8.0) / sp["q"])
+               for sp in specs)
+    per = kms / kn
+    ach, frac, peak, kind = kernel_fraction(per, algo)
+    state_gb = sum(2 * sp["q"] * (sp["nx"] + 2) * (sp["ny"] + 2) * elem for sp in specs) / 1e9
+    return {"updates_per_s": upd * steps / (ms * 1e-3), "ms_per_step": ms / steps,
+            "kernel": "k_step_tma_batch", "kernel_ms_per_launch": per,
+            "kernel_launches_timed": kn, "achieved_gbs": ach, "frac": frac, "peak": peak,
+            "peak_kind": kind, "algorithmic_bytes_per_launch": algo, "steps": steps,
+            "instances": len(specs), "state_gb": state_gb,
+            "l2_resident_instances": 0,
+            "l2_note": "each step streams %.1f GB of planes > 129 MB of L2: no instance's "
+                       "planes survive in L2 between its steps" % state_gb,
+            "dtype": "f32" if storage == "fp32" else "bf16-storage/f32-math"}
+
+
+def other_workloads(wl, torch, args):
+    """The headline workloads besides the bench line's own, measured one after another."""
+    import workloads as W
+    out = {}
+    runs = [("bf16_pulses", lambda: measure_single(wl, torch, W.pulses_c2(seed=args.seed),
+                                                   "bf16", 480)),
+            ("film_fp32", lambda: measure_single(wl, torch, W.film_c3(kn=1.0), "fp32", 480)),
+            ("film_bf16", lambda: measure_single(wl, torch, W.film_c3(kn=1.0), "bf16", 480)),
+            ("batch_bf16", lambda: measure_batch(wl, torch, "bf16", 96)),
+            ("batch_fp32", lambda: measure_batch(wl, torch, "fp32", 96))]
+    for name, fn in runs:
+        try:
+            out[name] = fn()
+        except Exception as exc:             # keep the bench line; record what failed
+            out[name] = {"error": "%s: %s" % (type(exc).__name__, exc)}
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+    cfgs = {"bf16_pulses": workload_config(argparse.Namespace(workload="pulses", storage="bf16"),
+                                           W.pulses_c2(seed=args.seed)),
+            "film_fp32": workload_config(argparse.Namespace(workload="film", storage="fp32"),
+                                         W.film_c3(kn=1.0)),
+            "film_bf16": workload_config(argparse.Namespace(workload="film", storage="bf16"),
+                                         W.film_c3(kn=1.0)),
+            "batch_bf16": batch_config(argparse.Namespace(storage="bf16"), 96),
+            "batch_fp32": batch_config(argparse.Namespace(storage="fp32"), 96)}
+    for k in out:
+        out[k]["config"] = cfgs[k]
+    return out
 
 
 def run_reference(args):
@@ -381,10 +584,12 @@ def run_reference(args):
         import workloads as W
         insts = W.batch_c4(seed=4)
         cfg = dict(insts[0], relax_mode=0, mfp=max(insts[0]["mfp"], 1.5))
-        config = batch_config(args, len(insts))
+        config = {**batch_config(args, len(insts)), "parallelism": "instances sharded x%d"
+                  % int(os.environ.get("WORLD_SIZE", "1"))}
     else:
         cfg = workload(args)
-        config = workload_config(args, cfg)
+        config = {**workload_config(args, cfg),
+                  "parallelism": "replicas x%d" % int(os.environ.get("WORLD_SIZE", "1"))}
     # bounded sample per bench step: a 128-column window, 128 rows of the periodic grid or
     # a film's full thickness (at most 256 rows) with its walls
     n = min(128, cfg["nx"])
@@ -459,6 +664,7 @@ def main():
         if args.fuse is not None:
             h.wlbm_set_option(wl.wlbm.OPT_FUSE_PERIODIC, args.fuse)
         variant_used = h.wlbm_get_option(wl.wlbm.OPT_STEP_VARIANT)
+        clocks = None if args.no_extras else Clocks(local)
         dT = torch.as_tensor(cfg["dT"]).to("cuda", non_blocking=False)
         h.wlbm_init_temperature(dT)
         h.wlbm_step(args.warmup)
@@ -471,7 +677,6 @@ def main():
                 dist.barrier()
             torch.cuda.synchronize()
 
-        clocks = None if args.no_extras else Clocks(local)
         h.wlbm_profile(args.profile_every)
         barrier()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -480,7 +685,6 @@ def main():
         ev1.record(stream)
         barrier()
         h.wlbm_profile(False)
-        clk = clocks.stop() if clocks else None
         elapsed_ms = ev0.elapsed_time(ev1)
         step_ms, step_launches, launches1 = h.wlbm_profile_read()
         h.wlbm_check()
@@ -528,6 +732,13 @@ def main():
         adj = None
         if not args.no_extras and not args.no_adjoint and rank == 0:
             adj = adjoint_ratio(wl, torch, stream)
+        others = None
+        if (not args.no_extras and not args.no_workloads and rank == 0 and
+                args.workload == "pulses" and args.storage == "fp32" and args.nx == 2048 and
+                args.q == 64):
+            torch.cuda.empty_cache()
+            others = other_workloads(wl, torch, args)
+        clk = clocks.stop() if clocks else None
 
     if rank == 0:
         line = {
@@ -537,8 +748,8 @@ def main():
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if args.storage == "fp32" else "bf16-storage/f32-math",
             "data": "synthetic",
-            "config": {**workload_config(args, cfg), "parallelism": "replicas x%d" % world,
-                       "graph_steps": args.graph,
+            "config": {**workload_config(args, cfg), "parallelism": "replicas x%d" % world},
+            "launch": {"graph_steps": args.graph,
                        "step_kernel": {0: "register-pipelined", 1: "bulk-copy ring",
                                        2: "warp-specialised", 3: "TMA tiles"}[variant_used],
                        "l2": "state %.2f GB > L2 (no flush needed)"
@@ -571,10 +782,13 @@ def main():
             line["e2e"] = e2e
         if adj is not None:
             line["adjoint"] = adj
+        if others is not None:
+            line.update(others)
         if clk is not None:
+            clk["window"] = "whole native run: warm-up, timed region, e2e, adjoint, workloads"
             line["clocks"] = clk
         if not args.no_extras:
-            line["cpu_baseline"] = cpu_baseline(cfg)
+            line["cpu_baseline"] = cpu_baseline(cfg, args.cpu_seconds)
         print(json.dumps(finite_or_none(line)), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -283,13 +283,18 @@ wlbm_status wlbm_adjoint_backward(wlbm_handle* h, const float* dJ_dT, const floa
  *                          WLBM_OPT_FUSE_PERIODIC set it still runs the periodic pass.
  *   WLBM_OPT_GRAPH_STEPS   0 (default): launch every step's kernels directly; G > 0, a
  *                          multiple of 6: run chunks of G steps as one captured CUDA
- *                          graph (fewer launch gaps; not on the legacy default stream).
+ *                          graph (fewer launch gaps).  Replay needs a stream of its own:
+ *                          on the legacy default stream (NULL) the steps are launched
+ *                          directly, which WLBM_OPT_GRAPH_REPLAYS shows.
  *   WLBM_OPT_FUSE_PERIODIC 0 (default): a separate periodic pass before every step; 1:
  *                          when both axes are periodic the step kernel also writes the
  *                          ghost cells mirroring each edge cell (no separate pass).
+ *   WLBM_OPT_GRAPH_REPLAYS read only (wlbm_get_option): how many chunks of steps this
+ *                          handle has run as replays of a captured graph.
  * wlbm_check: synchronises the stream and returns WLBM_ERR_TIMEOUT if a bounded wait
  * inside a kernel gave up since the last check (the status is then cleared). */
-enum { WLBM_OPT_STEP_VARIANT = 1, WLBM_OPT_GRAPH_STEPS = 2, WLBM_OPT_FUSE_PERIODIC = 3 };
+enum { WLBM_OPT_STEP_VARIANT = 1, WLBM_OPT_GRAPH_STEPS = 2, WLBM_OPT_FUSE_PERIODIC = 3,
+       WLBM_OPT_GRAPH_REPLAYS = 4 };
 wlbm_status wlbm_set_option(wlbm_handle* h, int32_t key, int64_t value);
 /* wlbm_get_option: the current value of a wlbm_set_option key in *value (host). */
 wlbm_status wlbm_get_option(const wlbm_handle* h, int32_t key, int64_t* value);
@@ -320,19 +325,24 @@ wlbm_status wlbm_profile_read(wlbm_handle* h, double* step_ms, int64_t* step_lau
  * may imply) is not acceptable.
  *   framed   device float32 [q][ny+2][nx+2]: deviations e_i - w_i e_ref including the
  *            ghost frame, as written by wlbm_get_state
+ *   speed    the band's propagation speed v_g in cells per step, (0, 1] (wlbm_grid.speed;
+ *            1 for a single gray band): the mean fluxes out[2], out[3] carry it as
+ *            wlbm_reduce's do (Eq. q_corr)
  *   bc_kind  host int32[4] wall kinds x-, x+, y-, y+ (decides which ghost cells count
  *            towards out[1])
  *   out      device double[4], written on the stream
  *   stream   cudaStream_t (NULL = legacy default stream)
  * Scratch: a file-scope device array of 1 MiB that every device loading the library keeps
  * until the process exits; it covers frames of up to 8,388,608 cells ((nx+2)*(ny+2)), and
- * larger frames are rejected with WLBM_ERR_INVALID_ARG and a message.  The first call on a
+ * larger frames (and a speed outside (0, 1]) are rejected with WLBM_ERR_INVALID_ARG and a
+ * message.  The first call on a
  * device looks up the array's device address (once per device, with that device current);
  * make that first call before any stream capture.  Every call reuses the same array and
  * overwrites each entry it reads before reading it, so nothing needs clearing; calls whose
  * executions overlap on the GPU (other streams, other threads) race on it.  Asynchronous. */
 wlbm_status wlbm_reduce_state_noalloc(const float* framed, int32_t nx, int32_t ny, int32_t q,
-                                      const int32_t* bc_kind, double* out, void* stream);
+                                      double speed, const int32_t* bc_kind, double* out,
+                                      void* stream);
 
 /* wlbm_autotune: native search over WLBM_OPT_STEP_VARIANT (0 - 3) x WLBM_OPT_GRAPH_STEPS
  * (0 and the largest multiple of 6 <= trial_steps) for this grid: each candidate runs trial_steps (>= 6) steps after a warm-up; the fastest is kept

@@ -20,8 +20,9 @@
 //     order, so the result equals the other variants' up to float rounding.
 // A block is 8 warps, so two blocks of up to 128 registers a thread fit on an SM.  Edge
 // groups (columns past the right ghost) store element by element, so pad columns stay
-// zero.  Fully periodic grids with fused mirrors and the adjoint's tape mode are served by
-// variant 1 (the dispatcher routes them there).
+// zero.  This kernel never mirrors periodic edges into the ghost frame (a separate
+// periodic pass does).  It also serves the adjoint's tape mode: the recompute of a segment
+// reads slot j of the tape through the tape's own tensor map and writes slot j + 1.
 #include <cuda.h>
 
 #include "elem.cuh"

@@ -87,7 +87,8 @@ __global__ void k_partials(const float* framed, int nx, int ny, int q, int diff_
 }
 
 // One block: fixed-order sum of the partials, means of q over the interior.
-__global__ void k_finish(const double* partials, int nblocks, double inv_cells, double* out) {
+__global__ void k_finish(const double* partials, int nblocks, double inv_cells, double speed,
+                         double* out) {
   __shared__ double red[kOut][kThreads / 32];
   double v[kOut] = {0.0, 0.0, 0.0, 0.0};
   for (int b = threadIdx.x; b < nblocks; b += kThreads)
@@ -103,7 +104,8 @@ __global__ void k_finish(const double* partials, int nblocks, double inv_cells, 
   if (threadIdx.x < kOut) {
     double s = 0.0;
     for (int w = 0; w < kThreads / 32; ++w) s += red[threadIdx.x][w];
-    out[threadIdx.x] = threadIdx.x >= 2 ? s * inv_cells : s;
+    // heat flux (Eq. q_corr): v_g sum_i e_i s_i, v_g = the band's speed in cells per step
+    out[threadIdx.x] = threadIdx.x >= 2 ? s * inv_cells * speed : s;
   }
 }
 
@@ -127,13 +129,18 @@ cudaError_t set_up(double** ptr) {
 }  // namespace
 
 extern "C" wlbm_status wlbm_reduce_state_noalloc(const float* framed, int32_t nx, int32_t ny,
-                                                 int32_t q, const int32_t* bc_kind,
-                                                 double* out, void* stream) {
+                                                 int32_t q, double speed,
+                                                 const int32_t* bc_kind, double* out,
+                                                 void* stream) {
   if (!framed || !out || !bc_kind || nx < 1 || ny < 1 || q < 8 || q > 1024 || q % 8) {
     wlbm::set_global_error_msg("wlbm_reduce_state_noalloc: invalid pointer, size or Q");
     return WLBM_ERR_INVALID_ARG;
   }
-  const int64_t cells = int64_t(nx + 2) * (ny + 2);
+  if (!(speed > 0.0 && speed <= 1.0)) {
+    wlbm::set_global_error_msg("wlbm_reduce_state_noalloc: speed must lie in (0, 1]");
+    return WLBM_ERR_INVALID_ARG;
+  }
+  const int64_t cells = (int64_t(nx) + 2) * (int64_t(ny) + 2);
   const int64_t nblocks = (cells + kThreads - 1) / kThreads;
   if (nblocks > kMaxBlocks) {
     wlbm::set_global_error_msg(
@@ -154,8 +161,10 @@ extern "C" wlbm_status wlbm_reduce_state_noalloc(const float* framed, int32_t nx
   for (int k = 0; k < 4; ++k)
     if (bc_kind[k] == WLBM_BC_ADIABATIC_DIFFUSE || bc_kind[k] == WLBM_BC_ADIABATIC_SPECULAR)
       diff_mask |= 1 << k;
+  // a launch error of earlier, unrelated work must not be reported as this call's
+  cudaGetLastError();
   k_partials<<<unsigned(nblocks), kThreads, 0, s>>>(framed, nx, ny, q, diff_mask, partials);
-  k_finish<<<1, kThreads, 0, s>>>(partials, int(nblocks), 1.0 / (double(nx) * ny), out);
+  k_finish<<<1, kThreads, 0, s>>>(partials, int(nblocks), 1.0 / (double(nx) * ny), speed, out);
   const cudaError_t le = cudaGetLastError();
   if (le != cudaSuccess) {
     wlbm::set_global_error_msg(std::string("wlbm_reduce_state_noalloc: ") + cudaGetErrorString(le));

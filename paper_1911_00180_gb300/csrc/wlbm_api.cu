@@ -136,6 +136,7 @@ struct wlbm_handle {
   // event pairs are read while the other one runs)
   TimedGraph graphs[3][2];
   int graph_parity = 0;
+  int64_t graph_replays = 0;  // chunks run as graph replays (WLBM_OPT_GRAPH_REPLAYS)
   int64_t graph_launches = 0; // kernels per graph replay
   std::vector<void*> owned;
   // host staging
@@ -796,6 +797,7 @@ static wlbm_status run_graph(wlbm_handle* h) {
     if (st != WLBM_OK) return st;
   }
   h->launches += h->graph_launches;
+  ++h->graph_replays;
   return h->cuda(tg.launch(h->stream), "wlbm_step: graph launch");
 }
 
@@ -838,6 +840,7 @@ wlbm_status wlbm_get_option(const wlbm_handle* h, int32_t key, int64_t* value) {
   if (key == WLBM_OPT_STEP_VARIANT) *value = h->step_variant;
   else if (key == WLBM_OPT_GRAPH_STEPS) *value = h->graph_steps;
   else if (key == WLBM_OPT_FUSE_PERIODIC) *value = h->fuse_periodic;
+  else if (key == WLBM_OPT_GRAPH_REPLAYS) *value = h->graph_replays;
   else return WLBM_ERR_INVALID_ARG;
   return WLBM_OK;
 }
@@ -1613,6 +1616,7 @@ struct wlbm_batch {
   };
   std::vector<Graph> graphs;
   int graph_parity = 0;
+  int64_t graph_replays = 0;
   int64_t graph_launches = 0, launches = 0;
   int prof_every = 0;
   int64_t prof_tick = 0;
@@ -1829,6 +1833,7 @@ wlbm_status wlbm_batch_get_option(const wlbm_batch* b, int32_t key, int64_t* val
   if (key == WLBM_OPT_STEP_VARIANT) *value = b->variant;
   else if (key == WLBM_OPT_GRAPH_STEPS) *value = b->graph_steps;
   else if (key == WLBM_OPT_FUSE_PERIODIC) *value = b->fuse_periodic;
+  else if (key == WLBM_OPT_GRAPH_REPLAYS) *value = b->graph_replays;
   else return WLBM_ERR_INVALID_ARG;
   return WLBM_OK;
 }
@@ -2026,6 +2031,7 @@ wlbm_status wlbm_batch_step(wlbm_batch* b, int64_t n) {
         if (st != WLBM_OK) return st;
       }
       b->launches += b->graph_launches;
+      ++b->graph_replays;
       st = b->cuda(tg->launch(b->stream), "wlbm_batch_step: graph launch");
     } else {
       st = batch_enqueue(b, ch, b->prof_every);

@@ -16,7 +16,7 @@ WLBM_OK, WLBM_ERR_INVALID_ARG, WLBM_ERR_UNSTABLE, WLBM_ERR_OOM = 0, 1, 2, 3
 WLBM_ERR_CUDA, WLBM_ERR_TIMEOUT, WLBM_ERR_STATE = 4, 5, 6
 BC_PERIODIC, BC_ISOTHERMAL, BC_ADIABATIC_DIFFUSE, BC_ADIABATIC_SPECULAR = 0, 1, 2, 3
 STORE_FP32_DEV, STORE_BF16_DEV = 0, 1
-OPT_STEP_VARIANT, OPT_GRAPH_STEPS, OPT_FUSE_PERIODIC = 1, 2, 3
+OPT_STEP_VARIANT, OPT_GRAPH_STEPS, OPT_FUSE_PERIODIC, OPT_GRAPH_REPLAYS = 1, 2, 3, 4
 REDUCE_N = 9          # WLBM_REDUCE_N
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "UNSTABLE", 3: "OOM", 4: "CUDA", 5: "TIMEOUT",
                 6: "STATE"}
@@ -97,7 +97,8 @@ def _load():
         "wlbm_check": (C.c_int, [vp]),
         "wlbm_profile": (C.c_int, [vp, i32]),
         "wlbm_profile_read": (C.c_int, [vp, C.POINTER(dbl), C.POINTER(i64), C.POINTER(i64)]),
-        "wlbm_reduce_state_noalloc": (C.c_int, [vp, i32, i32, i32, C.POINTER(i32), vp, vp]),
+        "wlbm_reduce_state_noalloc": (C.c_int, [vp, i32, i32, i32, C.c_double, C.POINTER(i32),
+                                                vp, vp]),
         "wlbm_lattice": (C.c_int, [i32, C.POINTER(i32), C.POINTER(dbl), C.POINTER(C.c_int8),
                                    C.POINTER(dbl)]),
         "wlbm_schedule": (C.c_int, [i32, i64, dbl, C.POINTER(C.c_uint8)]),
@@ -147,13 +148,32 @@ def wlbm_schedule(q, n_steps, speed=1.0):
     return out[:n_steps * q].reshape(n_steps, q)
 
 
-def wlbm_reduce_state_noalloc(framed, nx, ny, q, bc_kind, out, stream=None):
-    """No-allocation reduction of a framed float32 state (device tensor) into a device
-    float64 tensor `out` of 4 entries (see include/wlbm.h)."""
+def wlbm_reduce_state_noalloc(framed, nx, ny, q, bc_kind, out, stream=None, speed=1.0):
+    """No-allocation reduction of a framed float32 state (contiguous CUDA tensor of at least
+    q * (ny + 2) * (nx + 2) elements) into a contiguous CUDA float64 tensor `out` of at
+    least 4 entries on the same device (see include/wlbm.h); `speed` is the band's v_g.
+    Runs on `stream`, by default torch's current stream.  Tensors of another dtype,
+    device, layout or size raise ValueError before anything is launched."""
+    nx, ny, q = int(nx), int(ny), int(q)
+    need = q * (ny + 2) * (nx + 2)
+    for name, t, dt, n in (("framed", framed, "float32", need), ("out", out, "float64", 4)):
+        if not getattr(t, "is_cuda", False):
+            raise ValueError("wlbm_reduce_state_noalloc: %s must be a CUDA tensor" % name)
+        if str(t.dtype) != "torch." + dt:
+            raise ValueError("wlbm_reduce_state_noalloc: %s must be %s" % (name, dt))
+        if not t.is_contiguous():
+            raise ValueError("wlbm_reduce_state_noalloc: %s must be contiguous" % name)
+        if t.numel() < n:
+            raise ValueError("wlbm_reduce_state_noalloc: %s holds %d elements, needs %d"
+                             % (name, t.numel(), n))
+    if framed.device != out.device:
+        raise ValueError("wlbm_reduce_state_noalloc: framed and out on different devices")
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream(framed.device)
     kinds = (C.c_int32 * 4)(*bc_kind)
-    s = None if stream is None else C.c_void_p(stream.cuda_stream)
-    _check(lib.wlbm_reduce_state_noalloc(_ptr(framed), int(nx), int(ny), int(q), kinds,
-                                         _ptr(out), s))
+    _check(lib.wlbm_reduce_state_noalloc(_ptr(framed), nx, ny, q, float(speed), kinds,
+                                         _ptr(out), C.c_void_p(stream.cuda_stream)))
 
 
 # ------------------------------------------------------------------ device handle

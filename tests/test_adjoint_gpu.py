@@ -237,3 +237,31 @@ def test_adjoint_directional_derivative_mid_size():
     eps = 0.05
     fd = (J_of(dT0 + eps * v) - J_of(dT0 - eps * v)) / (2 * eps)
     assert ad == pytest.approx(fd, rel=2e-3)
+
+
+def test_adjoint_multi_tile_c5_recipe_matches_oracle():
+    """The adjoint workload's recipe beyond one tile: 260 x 30 (three 128-column tiles and
+    three 14-row tile rows of the TMA kernels), Q = 64, log-normal MFP field, isothermal x
+    walls at 300 K, periodic y, central Gaussian pulse, checkpoints every 50 steps over 110
+    steps (three checkpoints, a ragged last segment), on a stream of its own as the
+    benchmark runs it.  J = mean T over the column at 3 nx / 4; dJ/dMFP, dJ/dT_wall and
+    dJ/d(dT0) against the oracle's transpose at 1e-4."""
+    import torch
+    nx, ny, q, steps, ckpt = 260, 30, 64, 110, 50
+    kinds = (I, I, P, P)
+    mfp = np.maximum(W.lognormal_mfp(nx, ny, seed=9, corr=8.0), 1.6).astype(np.float32)
+    dT0 = W.gaussian_field(nx, ny, [(nx / 2.0, ny / 2.0)], [8.0], [1.0],
+                           periodic=False).astype(np.float32)
+    probe = np.zeros((ny, nx), bool)
+    probe[:, (3 * nx) // 4] = True
+    tw = (300.0,) * 4
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        J, g_mfp, g_tw, g_dT0 = _gpu(kinds, mfp, dT0, probe, tw, steps, ckpt, q)
+    ref = _oracle(kinds, mfp, dT0, probe, tw, steps, q)
+    assert abs(J - ref["J"]) <= 1e-5
+    e = (_rel(g_mfp, ref["dJ_dmfp"]), _rel(g_dT0, ref["dJ_ddT0"]),
+         _rel(g_tw[:2], ref["dJ_dTwall"][:2]))
+    print("adjoint 260x30 Q64: dJ/dMFP %.3g  dJ/ddT0 %.3g  dJ/dTwall %.3g" % e)
+    assert max(e) <= TOL
+    assert np.all(g_tw[2:] == 0.0)

@@ -54,4 +54,16 @@ def test_reference_arm_line(bench, workload):
                            "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     a = bench.parse()
     a.workload, a.nx, a.q = workload, 64, 16
-    assert line["config"] == json.loads(json.dumps(bench.workload_config(a, bench.workload(a))))
+    want = dict(bench.workload_config(a, bench.workload(a)), parallelism="replicas x1")
+    assert line["config"] == json.loads(json.dumps(want))
+
+
+def test_cpu_baseline_one_thread_and_all_cores(bench):
+    """The host baseline reports the oracle on one thread and on one spawned process per
+    core, the core count and the CPU model."""
+    import workloads as W
+    cfg = W.pulses_c2(seed=2, n=48, q=16, npulse=2)
+    cb = bench.cpu_baseline(cfg, seconds=0.3, window=32)
+    assert cb["kind"] == "oracle" and cb["cores"] == (os.cpu_count() or 1)
+    assert cb["value"] > 0 and cb["value_one_thread"] > 0
+    assert "cpu_model" in cb and "32x32" in cb["sample"]

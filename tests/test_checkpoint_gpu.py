@@ -94,6 +94,9 @@ def test_resume_under_graph_replay():
         g.wlbm_load(blob)
         g.wlbm_step(40)
         _same(_snapshot(g), want)
+        # 29 + 40 steps = 2 + 3 whole chunks of h, 3 of g, each a graph replay
+        assert h.wlbm_get_option(wl.wlbm.OPT_GRAPH_REPLAYS) == 5
+        assert g.wlbm_get_option(wl.wlbm.OPT_GRAPH_REPLAYS) == 3
         g.close()
         h.close()
 

@@ -7,11 +7,11 @@ relative to the largest initial per-direction deviation, 1e-5 for float32 storag
 With bfloat16 storage every stored value carries a rounding of up to 2^-9 of its
 non-equilibrium part, several times over near walls (ghost values are re-stored by the
 wall pass and by the step), so the state is held to 1e-2 of the largest initial
-per-direction deviation.  The heat flux q_x = sum_i s_ix d_i is a fixed linear map of
-the state, so that state bound implies |dq_x| <= 1e-2 * scale * sum_i |s_ix|, the bound
-q is held to; separately, the flux the library returns must equal the oracle's formula
-applied to the library's own state to 1e-5 of that scale (the moment kernel, free of the
-storage rounding).  The ballistic limit is exact (no arithmetic happens there)."""
+per-direction deviation.  The heat flux with bfloat16 storage is held to TOL16_Q of the
+oracle's flux amplitude (the largest |q_x|, |q_y| of the oracle's field); separately, the
+flux the library returns must equal the oracle's formula applied to the library's own
+state to 1e-5 of the state scale (the moment kernel, free of the storage rounding).  The
+ballistic limit is exact (no arithmetic happens there)."""
 import math
 
 import numpy as np
@@ -34,6 +34,13 @@ def _cuda():
 
 
 TOL16_STATE = 1e-2
+# bfloat16 heat flux, relative to the oracle's flux amplitude: a stored value carries a
+# rounding of up to 2^-9 of its non-equilibrium part, and in a near-steady state
+# round-to-nearest repeats the same rounding step after step (the error of the stored
+# part grows towards 2^-9 / W), so q, a small first moment of those parts, is the least
+# accurate output; the measured figure of every bfloat16 case is stated with the parity
+# results.
+TOL16_Q = 1e-2
 
 
 def _compare(cfg, steps, storage=0, tol=TOL32, state_tol=None, variant=None):
@@ -47,17 +54,21 @@ def _compare(cfg, steps, storage=0, tol=TOL32, state_tol=None, variant=None):
     e_t = rel_linf(gpu["dT"], orc.temperature_dev(), amp)
     e_s = rel_linf(gpu["state"][:, 1:-1, 1:-1], orc.d[:, 1:-1, 1:-1], dscale)
     qx, qy = orc.heat_flux()
-    qscale = dscale
+    qscale, qtol = dscale, tol
     if storage == 1:
-        qscale = dscale * float(max(np.abs(orc.s_hat[:, 0]).sum(), np.abs(orc.s_hat[:, 1]).sum()))
         own = gpu["state"][:, 1:-1, 1:-1]
-        e_m = max(rel_linf(gpu["qx"], np.tensordot(orc.s_hat[:, 0], own, axes=(0, 0)), qscale),
-                  rel_linf(gpu["qy"], np.tensordot(orc.s_hat[:, 1], own, axes=(0, 0)), qscale))
+        e_m = max(rel_linf(gpu["qx"], np.tensordot(orc.s_hat[:, 0], own, axes=(0, 0)), dscale),
+                  rel_linf(gpu["qy"], np.tensordot(orc.s_hat[:, 1], own, axes=(0, 0)), dscale))
         assert e_m <= TOL32, ("q of own state", e_m)
+        qscale = max(float(np.abs(qx).max()), float(np.abs(qy).max()))
+        qtol = TOL16_Q
     e_q = max(rel_linf(gpu["qx"], qx, qscale), rel_linf(gpu["qy"], qy, qscale))
+    print("parity %s: T %.3g  state %.3g  q %.3g (of %s)"
+          % ("bf16" if storage == 1 else "fp32", e_t, e_s, e_q,
+             "flux amplitude" if storage == 1 else "state scale"))
     assert e_t <= tol, ("T", e_t)
     assert e_s <= (state_tol or tol), ("state", e_s)
-    assert e_q <= (state_tol or tol), ("q", e_q)
+    assert e_q <= qtol, ("q", e_q)
     return orc, gpu
 
 
@@ -237,10 +248,12 @@ def _window_oracle(cfg, cx, cy, steps, pad):
 BENCH_GRAPH, BENCH_PROFILE = 48, 8     # the benchmark's graph chunk and timing stride
 
 
-def _sampled_full_size(cfg, steps, samples, window_fn):
+def _sampled_full_size(cfg, steps, samples, window_fn, storage=0):
     """Run the full-size grid on the GPU in the benchmark's launch configuration (its own
     stream, 48-step CUDA-graph replays, event timing of every 8th step kernel), then
-    check sampled cells one by one against the oracle on a window around each."""
+    check sampled cells one by one against the oracle on a window around each
+    (temperature to TOL32 / TOL16 of the amplitude, state to TOL32 / TOL16_STATE of the
+    largest per-direction pulse deviation)."""
     import torch
     import paper_1911_00180_gb300 as wl
     from oracle import lattice as L
@@ -248,7 +261,7 @@ def _sampled_full_size(cfg, steps, samples, window_fn):
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         h = wl.WormLBM(cfg["nx"], cfg["ny"], cfg["q"], mfp=cfg["mfp"], bc=cfg["bc"],
-                       t_wall=cfg["t_wall"], storage=0, emulate_3d=cfg["emulate_3d"],
+                       t_wall=cfg["t_wall"], storage=storage, emulate_3d=cfg["emulate_3d"],
                        relax_mode=cfg.get("relax_mode", 0), theta=THETA, stream=stream)
         h.wlbm_set_option(wl.wlbm.OPT_GRAPH_STEPS, BENCH_GRAPH)
         h.wlbm_profile(BENCH_PROFILE)
@@ -258,20 +271,28 @@ def _sampled_full_size(cfg, steps, samples, window_fn):
         state = h.wlbm_get_state()
         stream.synchronize()
         assert h.wlbm_profile_read()[1] == steps // BENCH_PROFILE
+        assert h.wlbm_get_option(wl.wlbm.OPT_GRAPH_REPLAYS) == steps // BENCH_GRAPH
     w = L.angular_weights(L.ring_directions(cfg["q"]))
     dscale = float(w.max() * (L.e_eq(301.0, 624.8074248458514) - L.e_eq(300.0, 624.8074248458514)))
+    t_tol, s_tol = (TOL32, TOL32) if storage == 0 else (TOL16, TOL16_STATE)
+    worst_t = worst_s = 0.0
     for (cx, cy) in samples:
         orc, (ox, oy) = window_fn(cfg, cx, cy, steps)
-        assert abs(float(dT[cy, cx]) - orc.temperature_dev()[oy, ox]) <= TOL32
+        e_t = abs(float(dT[cy, cx]) - orc.temperature_dev()[oy, ox])
         got = state[:, cy + 1, cx + 1].double().cpu().numpy()
         want = orc.d[:, oy + 1, ox + 1]
-        assert np.abs(got - want).max() <= TOL32 * dscale
+        e_s = float(np.abs(got - want).max()) / dscale
+        worst_t, worst_s = max(worst_t, e_t), max(worst_s, e_s)
+        assert e_t <= t_tol, ((cx, cy), e_t)
+        assert e_s <= s_tol, ((cx, cy), e_s)
+    print("full size %s: T %.3g  state %.3g" % ("bf16" if storage else "fp32", worst_t, worst_s))
     h.close()
 
 
-def test_full_size_c2_sampled_cells():
+@pytest.mark.parametrize("storage", [0, 1])
+def test_full_size_c2_sampled_cells(storage):
     """2048 x 2048, Q = 64, periodic, 16 pulses (the benchmark workload), one 48-step
-    graph replay."""
+    graph replay; float32 and bfloat16 storage (the 16-stage ring of Q <= 64)."""
     cfg = W.pulses_c2(seed=2)
     steps, pad = BENCH_GRAPH, BENCH_GRAPH + 2
     rng = np.random.default_rng(0)
@@ -282,13 +303,15 @@ def test_full_size_c2_sampled_cells():
 
     def window(cfg, cx, cy, steps):
         return _window_oracle(cfg, cx, cy, steps, pad), (pad, pad)
-    _sampled_full_size(cfg, steps, samples, window)
+    _sampled_full_size(cfg, steps, samples, window, storage)
 
 
-def test_full_size_c3_film_sampled_cells():
+@pytest.mark.parametrize("storage", [0, 1])
+def test_full_size_c3_film_sampled_cells(storage):
     """4096 x 256 film, Q = 128, isothermal x walls, diffuse y walls: sampled cells
     (including ones next to the diffuse walls) against the oracle on an x-window that
-    keeps the full film thickness and its walls; one 48-step graph replay."""
+    keeps the full film thickness and its walls; one 48-step graph replay; float32 and
+    bfloat16 storage (the 8-stage ring of Q > 64)."""
     cfg = W.film_c3(kn=1.0)
     steps, pad = BENCH_GRAPH, BENCH_GRAPH + 2
     samples = [(1000, 0), (2500, 255), (3100, 128), (7, 40), (4090, 200)]
@@ -300,4 +323,4 @@ def test_full_size_c3_film_sampled_cells():
         x0, x1 = max(cx - pad, 0), min(cx + pad, cfg["nx"] - 1)
         sub = dict(cfg, nx=x1 - x0 + 1, dT=cfg["dT"][:, x0:x1 + 1])
         return oracle_run(sub, steps), (cx - x0, cy)
-    _sampled_full_size(cfg, steps, samples, window)
+    _sampled_full_size(cfg, steps, samples, window, storage)

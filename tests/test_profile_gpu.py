@@ -85,6 +85,8 @@ def test_graph_replay_is_timed_and_changes_no_result():
         for h in (a, b):
             h.wlbm_step(24)
         assert b.wlbm_profile_read()[1] == 0
+        assert b.wlbm_get_option(wl.wlbm.OPT_GRAPH_REPLAYS) == 2 + 3 + 2
+        assert a.wlbm_get_option(wl.wlbm.OPT_GRAPH_REPLAYS) == 0
         assert np.array_equal(_state(a), _state(b))
         a.close()
         b.close()
