@@ -294,7 +294,8 @@ wlbm_status wlbm_adjoint_backward(wlbm_handle* h, const float* dJ_dT, const floa
  * wlbm_check: synchronises the stream and returns WLBM_ERR_TIMEOUT if a bounded wait
  * inside a kernel gave up since the last check (the status is then cleared). */
 enum { WLBM_OPT_STEP_VARIANT = 1, WLBM_OPT_GRAPH_STEPS = 2, WLBM_OPT_FUSE_PERIODIC = 3,
-       WLBM_OPT_GRAPH_REPLAYS = 4 };
+       WLBM_OPT_GRAPH_REPLAYS = 4, WLBM_OPT_PERSISTENT = 5, WLBM_OPT_RING_STAGES = 6,
+       WLBM_OPT_WAIT_LIMIT = 7, WLBM_OPT_STALL_TEST = 8 };
 wlbm_status wlbm_set_option(wlbm_handle* h, int32_t key, int64_t value);
 /* wlbm_get_option: the current value of a wlbm_set_option key in *value (host). */
 wlbm_status wlbm_get_option(const wlbm_handle* h, int32_t key, int64_t* value);
@@ -362,9 +363,31 @@ wlbm_status wlbm_autotune(wlbm_handle* h, int32_t trial_steps, int32_t* variant,
  * wlbm_batch_instance returns the handle of instance k (owned by the batch) for
  * moments, reductions and state access.  Options (wlbm_batch_set_option) are those of
  * wlbm_set_option, for every instance: WLBM_OPT_STEP_VARIANT 0, 1 or 3 (default 3 when
- * every instance has a tensor map), WLBM_OPT_GRAPH_STEPS, WLBM_OPT_FUSE_PERIODIC.  Instances with a periodic axis whose edges the step kernel does
- * not mirror get their own periodic pass each step; graph replay then keeps one captured
- * graph per starting energy-plane phase of those instances (at most three). */
+ * every instance has a tensor map), WLBM_OPT_GRAPH_STEPS, WLBM_OPT_FUSE_PERIODIC.
+ * Instances with a periodic axis whose edges the step kernel does not mirror get their own
+ * periodic pass each step; graph replay then keeps one captured graph per starting
+ * energy-plane phase of those instances (at most three).  Options of batches only:
+ *   WLBM_OPT_PERSISTENT    0 (default): one wall launch and one step launch per step; 1:
+ *                          one persistent launch per chunk of steps (64, or the
+ *                          WLBM_OPT_GRAPH_STEPS of a replayed graph) on a fixed grid of
+ *                          resident blocks that take the wall chunks and step tiles of
+ *                          every instance and step from a queue, each item waiting only
+ *                          for the items of its own instance it reads (results equal the
+ *                          per-step launches of variant 3 bit for bit).  Needs variant 3
+ *                          and no instance with a periodic axis (WLBM_ERR_INVALID_ARG).
+ *                          Profiling then times whole launches: wlbm_batch_profile_read
+ *                          reports their steps as step_launches.
+ *   WLBM_OPT_RING_STAGES   ring depth of the persistent kernel's tensor copies: 0
+ *                          (default: 6 float32, 8 bfloat16) or 4 (float32) / 16 (bfloat16).
+ *   WLBM_OPT_WAIT_LIMIT    clock cycles a dependency wait of the persistent kernel may take
+ *                          before it gives up (0, default: about two seconds); a wait that
+ *                          gives up sets the status word of its instance, and every block
+ *                          of the launch leaves (wlbm_batch_check reports it).
+ *   WLBM_OPT_STALL_TEST    failure-detection hook for tests (0 default): 1 makes the step
+ *                          tiles of instance 0 wait for one wall chunk more than exists,
+ *                          so that their wait runs out after WLBM_OPT_WAIT_LIMIT cycles.
+ *                          The states are then those of a partial step: initialise them
+ *                          again before use. */
 typedef struct wlbm_batch wlbm_batch;
 wlbm_status wlbm_batch_create(int32_t n, const wlbm_grid* grids, const float* const* mfp_cells,
                               const double* mfp_uniform, const wlbm_boundary* bcs,
@@ -379,10 +402,17 @@ wlbm_status wlbm_batch_set_option(wlbm_batch* b, int32_t key, int64_t value);
 wlbm_status wlbm_batch_get_option(const wlbm_batch* b, int32_t key, int64_t* value);
 wlbm_status wlbm_batch_step(wlbm_batch* b, int64_t n);
 wlbm_status wlbm_batch_profile(wlbm_batch* b, int32_t every);   /* as wlbm_profile */
+/* wlbm_batch_check: synchronises the batch's stream and returns WLBM_ERR_TIMEOUT if a bounded
+ * wait in a kernel of any instance gave up since the last check (the status words are
+ * then cleared), as wlbm_check does for one handle. */
+wlbm_status wlbm_batch_check(wlbm_batch* b);
 wlbm_status wlbm_batch_profile_read(wlbm_batch* b, double* step_ms, int64_t* step_launches,
                                     int64_t* all_launches);
-/* wlbm_batch_autotune: as wlbm_autotune over variants 0, 1 and 3, for the whole batch
- * (call before init). */
+/* wlbm_batch_autotune: as wlbm_autotune over variants 0, 1 and 3 with per-step launches,
+ * and, where the batch allows it, the persistent kernel at both of its ring depths, each
+ * with and without graph replay (steps per launch: the graph's or 64), for the whole
+ * batch (call before init).  The winner's options are set; WLBM_OPT_PERSISTENT and
+ * WLBM_OPT_RING_STAGES report the persistent choice. */
 wlbm_status wlbm_batch_autotune(wlbm_batch* b, int32_t trial_steps, int32_t* variant,
                                 int32_t* graph_steps, double* ms_per_step);
 

@@ -17,7 +17,7 @@ BUILD = os.path.join(PKG, "_build")
 LIBDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIBDIR, "libwlbm.so")
 SOURCES = ["lattice.cpp", "wlbm_api.cu", "k_step.cu", "k_step_tma.cu", "k_aux.cu", "k_adjoint.cu",
-           "k_adjoint_tma.cu", "noalloc.cu"]
+           "k_adjoint_tma.cu", "k_batch_persistent.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2,-ffp-contract=off",
          "-I" + os.path.join(PKG, "..", "include")]

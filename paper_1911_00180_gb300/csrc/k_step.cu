@@ -855,6 +855,7 @@ cudaError_t prepare_step_kernels() {
   if (e == cudaSuccess) e = configure_ws<float, 4, 8, false>();
   if (e == cudaSuccess) e = configure_step_tma();
   if (e == cudaSuccess) e = configure_adj_tma();
+  if (e == cudaSuccess) e = configure_batch_persistent();
   return e;
 }
 

@@ -38,6 +38,7 @@ cudaError_t record_event(cudaEvent_t e, cudaStream_t s, bool node) {
 struct TimedGraph {
   cudaGraphExec_t exec = nullptr;
   std::vector<cudaEvent_t> ev;   // (start, stop) pairs
+  int weight = 1;                // steps one pair times (a persistent launch: its steps)
   cudaEvent_t done = nullptr;    // recorded after every replay when there are pairs
   bool pending = false;          // replayed since the pairs were last read
 
@@ -61,7 +62,7 @@ struct TimedGraph {
       float t = 0.f;
       e = cudaEventElapsedTime(&t, ev[k], ev[k + 1]);
       *ms += t;
-      ++*n;
+      *n += weight;
     }
     return e;
   }
@@ -1581,11 +1582,22 @@ wlbm_status wlbm_adjoint_backward(wlbm_handle* h, const float* dJ_dT, const floa
 // adds the per-chunk instance records the batched kernels read.
 namespace {
 constexpr int kBatchChunk = 64;   // steps per schedule upload of a batch
+// default limit of a dependency wait in the persistent kernel: about two seconds of clock
+constexpr long long kPersistWaitCycles = 4000000000LL;
 }
 
 struct wlbm_batch {
   std::vector<wlbm_handle*> h;
   int storage = 0, variant = 1, graph_steps = 0, fuse_periodic = 0;
+  // persistent kernel (WLBM_OPT_PERSISTENT): one launch per chunk of steps, its ring depth
+  // (0: default), the dependency-wait limit in clock cycles (0: the default of about two
+  // seconds) and the failure-detection test hook
+  int persistent = 0, ring_stages = 0, stall_test = 0;
+  long long wait_limit = 0;
+  unsigned* d_ctr = nullptr;   // [1 + 2n] item queue and per-instance completion counts
+  int* d_abort = nullptr;
+  int persist_grid = 0;        // blocks of the persistent launch (resident blocks x SMs)
+  std::vector<int> prof_w;     // steps timed by each direct event pair
   cudaStream_t stream = nullptr;
   wlbm_allocator alloc{nullptr, nullptr, nullptr};
   std::vector<void*> owned;
@@ -1680,6 +1692,19 @@ struct wlbm_batch {
     for (wlbm_handle* x : h) wlbm_destroy(x);
     h.clear();
   }
+  // The persistent kernel covers the wall pass and variant-3 tiles, not periodic links.
+  bool persistent_ok(std::string* why) const {
+    if (variant != 3) {
+      *why = "the persistent kernel runs variant 3 (TMA tiles)";
+      return false;
+    }
+    for (const wlbm_handle* x : h)
+      if (x->xper || x->yper) {
+        *why = "the persistent kernel takes no instance with a periodic axis";
+        return false;
+      }
+    return true;
+  }
   // Both axes periodic and fused: the step kernel mirrors the edges of that instance
   // (not in variant 3, which has no mirror stores).
   bool wraps(const wlbm_handle* x) const {
@@ -1704,9 +1729,11 @@ struct wlbm_batch {
       }
       h_inst[k].tiles_x = tx;
       h_inst[k].first_tile = total_tiles;
+      h_inst[k].n_tiles = tx * ty;
       total_tiles += tx * ty;
       h_walls[k].first_block = total_wall_blocks;
-      total_wall_blocks += wall_blocks(h[k]->walls);
+      h_walls[k].n_blocks = wall_blocks(h[k]->walls);
+      total_wall_blocks += h_walls[k].n_blocks;
     }
   }
 };
@@ -1759,14 +1786,16 @@ wlbm_status wlbm_batch_create(int32_t n, const wlbm_grid* grids, const float* co
   b->d_tmaps = static_cast<unsigned char*>(b->dev_alloc(size_t(n) * 128));
   b->d_inst = static_cast<BatchInst*>(b->dev_alloc(sizeof(BatchInst) * n));
   b->d_walls = static_cast<BatchWalls*>(b->dev_alloc(sizeof(BatchWalls) * n));
+  b->d_ctr = static_cast<unsigned*>(b->dev_alloc(sizeof(unsigned) * (1 + 2 * size_t(n))));
+  b->d_abort = static_cast<int*>(b->dev_alloc(sizeof(int)));
   // the wall segments of every instance are fixed: the block -> instance table once
   std::vector<int> wall_inst;
   for (int k = 0; k < n; ++k)
     wall_inst.insert(wall_inst.end(), size_t(wall_blocks(b->h[k]->walls)), k);
   if (!wall_inst.empty())
     b->d_wall_inst = static_cast<int*>(b->dev_alloc(wall_inst.size() * sizeof(int)));
-  if (!b->d_codes || !b->d_order || !b->d_tmaps || !b->d_inst || !b->d_walls ||
-      (!wall_inst.empty() && !b->d_wall_inst))
+  if (!b->d_codes || !b->d_order || !b->d_tmaps || !b->d_inst || !b->d_walls || !b->d_ctr ||
+      !b->d_abort || (!wall_inst.empty() && !b->d_wall_inst))
     return bad(WLBM_ERR_OOM, "wlbm_batch_create: device allocation failed");
   if (!wall_inst.empty() &&
       cudaMemcpy(b->d_wall_inst, wall_inst.data(), wall_inst.size() * sizeof(int),
@@ -1834,6 +1863,10 @@ wlbm_status wlbm_batch_get_option(const wlbm_batch* b, int32_t key, int64_t* val
   else if (key == WLBM_OPT_GRAPH_STEPS) *value = b->graph_steps;
   else if (key == WLBM_OPT_FUSE_PERIODIC) *value = b->fuse_periodic;
   else if (key == WLBM_OPT_GRAPH_REPLAYS) *value = b->graph_replays;
+  else if (key == WLBM_OPT_PERSISTENT) *value = b->persistent;
+  else if (key == WLBM_OPT_RING_STAGES) *value = b->ring_stages;
+  else if (key == WLBM_OPT_WAIT_LIMIT) *value = b->wait_limit;
+  else if (key == WLBM_OPT_STALL_TEST) *value = b->stall_test;
   else return WLBM_ERR_INVALID_ARG;
   return WLBM_OK;
 }
@@ -1844,9 +1877,37 @@ wlbm_status wlbm_batch_set_option(wlbm_batch* b, int32_t key, int64_t value) {
     return b->fail(WLBM_ERR_INVALID_ARG,
                    "wlbm_batch_set_option: step variant 3 needs a tensor map of every instance");
   if (key == WLBM_OPT_STEP_VARIANT && (value == 0 || value == 1 || value == 3)) {
+    if (b->persistent && value != 3)
+      return b->fail(WLBM_ERR_INVALID_ARG,
+                     "wlbm_batch_set_option: the persistent kernel runs variant 3");
     b->variant = int(value);
     b->layout();
     b->classify();
+    b->drop_graph();
+    return WLBM_OK;
+  }
+  if (key == WLBM_OPT_PERSISTENT && (value == 0 || value == 1)) {
+    std::string why;
+    if (value == 1 && !b->persistent_ok(&why))
+      return b->fail(WLBM_ERR_INVALID_ARG, "wlbm_batch_set_option: " + why);
+    b->persistent = int(value);
+    b->drop_graph();
+    return WLBM_OK;
+  }
+  if (key == WLBM_OPT_RING_STAGES && value >= 0 && value <= 64 &&
+      batch_persistent_stages_ok(b->storage, int(value))) {
+    b->ring_stages = int(value);
+    b->persist_grid = 0;
+    b->drop_graph();
+    return WLBM_OK;
+  }
+  if (key == WLBM_OPT_WAIT_LIMIT && value >= 0) {
+    b->wait_limit = value;
+    b->drop_graph();
+    return WLBM_OK;
+  }
+  if (key == WLBM_OPT_STALL_TEST && (value == 0 || value == 1)) {
+    b->stall_test = int(value);
     b->drop_graph();
     return WLBM_OK;
   }
@@ -1874,6 +1935,67 @@ static wlbm_status batch_enqueue(wlbm_batch* b, int count, int every,
   wlbm_status st = WLBM_OK;
   bool any_spec = false;
   for (const wlbm_handle* x : b->h) any_spec = any_spec || x->walls.any_spec;
+  if (b->persistent) {
+    // one launch for the chunk: the wall pass and the tiles of every step
+    if (b->persist_grid == 0) {
+      int dev = 0, sms = 0;
+      st = b->cuda(cudaGetDevice(&dev), "wlbm_batch_step: device");
+      if (st == WLBM_OK)
+        st = b->cuda(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev),
+                     "wlbm_batch_step: device");
+      if (st != WLBM_OK) return st;
+      const int per_sm = batch_persistent_blocks_per_sm(b->storage, b->ring_stages);
+      if (per_sm <= 0)
+        return b->fail(WLBM_ERR_CUDA, "wlbm_batch_step: the persistent kernel does not fit an SM");
+      b->persist_grid = per_sm * sms;
+    }
+    PersistArgs p{};
+    p.insts = b->d_inst;
+    p.walls = b->d_walls;
+    p.wall_inst = b->d_wall_inst;
+    p.n = n;
+    p.wall_items = b->total_wall_blocks;
+    p.tile_items = b->total_tiles;
+    p.steps = count;
+    p.ctr = b->d_ctr;
+    p.abort_flag = b->d_abort;
+    p.wait_limit = b->wait_limit > 0 ? b->wait_limit : kPersistWaitCycles;
+    p.stall_test = b->stall_test;
+    st = b->cuda(cudaMemsetAsync(b->d_ctr, 0, sizeof(unsigned) * (1 + 2 * size_t(n)), b->stream),
+                 "wlbm_batch_step: counters");
+    if (st == WLBM_OK)
+      st = b->cuda(cudaMemsetAsync(b->d_abort, 0, sizeof(int), b->stream),
+                   "wlbm_batch_step: counters");
+    if (st != WLBM_OK) return st;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (every > 0) {
+      if (cap) {
+        e0 = (*cap)[0];
+        e1 = (*cap)[1];
+      } else {
+        if (b->prof_used + 2 > b->prof_ev.size()) {
+          for (int j = 0; j < 2; ++j) {
+            cudaEvent_t ev;
+            st = b->cuda(cudaEventCreate(&ev), "wlbm_batch_step: profiling");
+            if (st != WLBM_OK) return st;
+            b->prof_ev.push_back(ev);
+          }
+        }
+        e0 = b->prof_ev[b->prof_used];
+        e1 = b->prof_ev[b->prof_used + 1];
+        b->prof_used += 2;
+        b->prof_w.push_back(count);
+      }
+      st = b->cuda(record_event(e0, b->stream, cap != nullptr), "profiling");
+    }
+    if (st == WLBM_OK)
+      st = b->cuda(launch_batch_persistent(b->storage, b->ring_stages, p, b->max_q,
+                                           b->persist_grid, any_spec, b->stream),
+                   "wlbm_batch_step: persistent kernel");
+    ++b->launches;
+    if (st == WLBM_OK && e1) st = b->cuda(record_event(e1, b->stream, cap != nullptr), "profiling");
+    return st;
+  }
   for (int t = 0; t < count && st == WLBM_OK; ++t) {
     if (b->total_wall_blocks > 0) {
       st = b->cuda(launch_walls_batch(b->storage, b->d_walls, b->d_wall_inst,
@@ -1915,6 +2037,7 @@ static wlbm_status batch_enqueue(wlbm_batch* b, int count, int every,
         e0 = b->prof_ev[b->prof_used];
         e1 = b->prof_ev[b->prof_used + 1];
         b->prof_used += 2;
+        b->prof_w.push_back(1);
       }
       st = b->cuda(record_event(e0, b->stream, cap != nullptr), "profiling");
     }
@@ -2000,8 +2123,10 @@ wlbm_status wlbm_batch_step(wlbm_batch* b, int64_t n) {
         if (b->graphs.size() >= 6) b->drop_graph();
         TimedGraph fresh;
         const int every = b->prof_every;
-        st = b->cuda(fresh.make_events(every > 0 ? (ch + every - 1) / every : 0),
-                     "wlbm_batch_step: graph events");
+        // a persistent chunk is one launch: one timed pair covering its ch steps
+        const int pairs = every > 0 ? (b->persistent ? 1 : (ch + every - 1) / every) : 0;
+        fresh.weight = b->persistent ? ch : 1;
+        st = b->cuda(fresh.make_events(pairs), "wlbm_batch_step: graph events");
         const int64_t l0 = b->launches;
         if (st == WLBM_OK)
           st = b->cuda(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal),
@@ -2044,6 +2169,23 @@ wlbm_status wlbm_batch_step(wlbm_batch* b, int64_t n) {
   return WLBM_OK;
 }
 
+wlbm_status wlbm_batch_check(wlbm_batch* b) {
+  if (!b) return WLBM_ERR_INVALID_ARG;
+  wlbm_status r = b->cuda(cudaStreamSynchronize(b->stream), "wlbm_batch_check");
+  if (r != WLBM_OK) return r;
+  int bad = -1;
+  for (size_t k = 0; k < b->h.size(); ++k) {
+    const wlbm_status st = wlbm_check(b->h[k]);
+    if (st == WLBM_ERR_TIMEOUT && bad < 0) bad = int(k);
+    else if (st != WLBM_OK && st != WLBM_ERR_TIMEOUT) return b->fail(st, b->h[k]->err);
+  }
+  if (bad >= 0)
+    return b->fail(WLBM_ERR_TIMEOUT,
+                   "a bounded wait gave up (first instance with its status set: " +
+                       std::to_string(bad) + ")");
+  return WLBM_OK;
+}
+
 wlbm_status wlbm_batch_profile(wlbm_batch* b, int32_t every) {
   if (!b) return WLBM_ERR_INVALID_ARG;
   if (every < 0) return b->fail(WLBM_ERR_INVALID_ARG, "wlbm_batch_profile: negative stride");
@@ -2069,10 +2211,13 @@ wlbm_status wlbm_batch_profile_read(wlbm_batch* b, double* step_ms, int64_t* ste
     if (st != WLBM_OK) return st;
     total += ms;
   }
+  int64_t timed = b->prof_graph_n;
+  for (int w : b->prof_w) timed += w;
   if (step_ms) *step_ms = total;
-  if (step_launches) *step_launches = b->prof_graph_n + int64_t(b->prof_used / 2);
+  if (step_launches) *step_launches = timed;
   if (all_launches) *all_launches = b->launches;
   b->prof_used = 0;
+  b->prof_w.clear();
   b->prof_graph_ms = 0.0;
   b->prof_graph_n = 0;
   return WLBM_OK;

@@ -274,6 +274,7 @@ struct BatchInst {
   int first_tile;         // first block of this instance in the batched grid
   const uint16_t* order;  // variant 3: kind-sorted directions of the chunk, [t][q + 17]
   const void* tmap;       // variant 3: device address of the instance's CUtensorMap
+  int n_tiles;            // step-kernel tiles of this instance
 };
 
 struct BatchWalls {
@@ -282,6 +283,27 @@ struct BatchWalls {
   const uint8_t* codes;
   int n_e, phase;
   int first_block;        // first block of this instance in the batched wall grid
+  int n_blocks;           // wall blocks (chunks of ghost cells) of this instance
+};
+
+// Persistent batched kernel (variant 3 tiles and the wall pass in one launch for a chunk
+// of steps): its work items are, for every step t of the chunk, the wall chunks of all
+// instances, then the step tiles of all instances, taken in that order from a queue.  A
+// wall chunk of instance k at step t waits until every tile of k's step t - 1 is done; a
+// tile waits until every wall chunk of k's step t is done (and every tile of step t - 1).
+struct PersistArgs {
+  const BatchInst* insts;
+  const BatchWalls* walls;
+  const int* wall_inst;   // [wall_items] instance of each wall chunk of a step
+  int n;                  // instances
+  int wall_items, tile_items;   // per step
+  int steps;              // steps of this launch (codes of steps 0 .. steps-1 of the chunk)
+  unsigned* ctr;          // [1 + 2n] zeroed before the launch: item queue, walls done per
+                          // instance, tiles done per instance
+  int* abort_flag;        // zeroed before the launch; set when a wait gave up
+  long long wait_limit;   // clock cycles a dependency wait may take
+  int stall_test;         // failure-detection test: instance 0's tiles wait for one wall
+                          // chunk more than exists, so their wait runs out
 };
 
 // Reverse-step arguments (float32 storage only).
@@ -371,6 +393,13 @@ cudaError_t launch_step_batch(int storage, int variant, const BatchInst* insts, 
 int wall_blocks(const WallArgs& a);   // blocks of the wall pass of one grid (32 cells each)
 cudaError_t launch_walls_batch(int storage, const BatchWalls* b, const int* block_inst,
                                int total_blocks, int t, bool any_spec, cudaStream_t s);
+// Persistent batched kernel (k_batch_persistent.cu): attributes, resident blocks per SM and
+// one launch of p.steps steps on `grid` blocks (ring depth `stages`: 0 takes the default).
+cudaError_t configure_batch_persistent();
+int batch_persistent_blocks_per_sm(int storage, int stages);
+bool batch_persistent_stages_ok(int storage, int stages);
+cudaError_t launch_batch_persistent(int storage, int stages, const PersistArgs& p, int max_q,
+                                    int grid, bool any_spec, cudaStream_t s);
 cudaError_t launch_walls(int storage, const WallArgs& a, cudaStream_t s);
 cudaError_t launch_periodic(int storage, const PeriodicArgs& a, cudaStream_t s);
 cudaError_t launch_init(int storage, const InitArgs& a, cudaStream_t s);

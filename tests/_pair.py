@@ -7,7 +7,10 @@ from oracle.stepper import WormLBM as OracleLBM
 THETA = 624.8074248458514
 
 
-def oracle_run(cfg, steps, state=None):
+def oracle_run(cfg, steps, state=None, flux_peak=False):
+    """The oracle after `steps` steps; with flux_peak the largest |q_x|, |q_y| of any cell
+    over the start state and every step is kept as m.flux_peak (the run's flux
+    amplitude)."""
     m = OracleLBM(cfg["nx"], cfg["ny"], cfg["q"],
                   cfg["mfp"] if cfg.get("mfp_field") is None else cfg["mfp_field"],
                   bc_kind=cfg["bc"], t_wall=cfg["t_wall"], emulate_3d=cfg["emulate_3d"],
@@ -18,7 +21,16 @@ def oracle_run(cfg, steps, state=None):
         m.init_temperature(cfg["dT"].astype(np.float64))
     else:
         m.set_state(state)
-    m.step(steps)
+    if not flux_peak:
+        m.step(steps)
+        return m
+    peak = 0.0
+    for n in range(steps + 1):
+        if n:
+            m.step()
+        qx, qy = m.heat_flux()
+        peak = max(peak, float(np.abs(qx).max()), float(np.abs(qy).max()))
+    m.flux_peak = peak
     return m
 
 

@@ -34,17 +34,22 @@ def _cuda():
 
 
 TOL16_STATE = 1e-2
-# bfloat16 heat flux, relative to the oracle's flux amplitude: a stored value carries a
-# rounding of up to 2^-9 of its non-equilibrium part, and in a near-steady state
-# round-to-nearest repeats the same rounding step after step (the error of the stored
-# part grows towards 2^-9 / W), so q, a small first moment of those parts, is the least
-# accurate output; the measured figure of every bfloat16 case is stated with the parity
-# results.
-TOL16_Q = 1e-2
+# bfloat16 heat flux: the benchmark spec's bfloat16 bar, relative to the oracle's flux
+# amplitude (the largest |q_x|, |q_y| of any cell at any step of the run: a decaying
+# pulse's flux falls by orders of magnitude while the rounding of the stored values does
+# not fall with it).
+TOL16_Q = 2e-3
+# bfloat16 per-direction values of the full-size film and batch runs, relative to the
+# largest per-direction wall deviation: next to an isothermal wall of a near-ballistic film
+# (W ~ 1/170 at Kn = 1 on 256 rows) the stored non-equilibrium part is of the wall's order
+# and round-to-nearest repeats nearly the same rounding every step, so the error of a
+# stored value grows towards several of its rounding steps (2^-9 each); the temperature
+# there stays within TOL16.
+TOL16_STATE_WALL = 2e-2
 
 
 def _compare(cfg, steps, storage=0, tol=TOL32, state_tol=None, variant=None):
-    orc = oracle_run(cfg, steps)
+    orc = oracle_run(cfg, steps, flux_peak=storage == 1)
     gpu = gpu_run(cfg, steps, storage, variant=variant)
     amp = max(float(np.abs(cfg["dT"]).max()),
               max(abs(t - 300.0) for k, t in zip(cfg["bc"], cfg["t_wall"]) if k == I)
@@ -60,12 +65,14 @@ def _compare(cfg, steps, storage=0, tol=TOL32, state_tol=None, variant=None):
         e_m = max(rel_linf(gpu["qx"], np.tensordot(orc.s_hat[:, 0], own, axes=(0, 0)), dscale),
                   rel_linf(gpu["qy"], np.tensordot(orc.s_hat[:, 1], own, axes=(0, 0)), dscale))
         assert e_m <= TOL32, ("q of own state", e_m)
-        qscale = max(float(np.abs(qx).max()), float(np.abs(qy).max()))
+        qscale = orc.flux_peak
         qtol = TOL16_Q
     e_q = max(rel_linf(gpu["qx"], qx, qscale), rel_linf(gpu["qy"], qy, qscale))
-    print("parity %s: T %.3g  state %.3g  q %.3g (of %s)"
-          % ("bf16" if storage == 1 else "fp32", e_t, e_s, e_q,
-             "flux amplitude" if storage == 1 else "state scale"))
+    where = np.unravel_index(np.argmax(np.abs(gpu["state"][:, 1:-1, 1:-1] - orc.d[:, 1:-1, 1:-1])),
+                             orc.d[:, 1:-1, 1:-1].shape)
+    print("parity %s %dx%d Q%d %s %d steps: T %.3g  state %.3g at %s  q %.3g (of %s)"
+          % ("bf16" if storage == 1 else "fp32", cfg["nx"], cfg["ny"], cfg["q"], cfg["bc"],
+             steps, e_t, e_s, where, e_q, "flux amplitude" if storage == 1 else "state scale"))
     assert e_t <= tol, ("T", e_t)
     assert e_s <= (state_tol or tol), ("state", e_s)
     assert e_q <= qtol, ("q", e_q)
@@ -274,7 +281,7 @@ def _sampled_full_size(cfg, steps, samples, window_fn, storage=0):
         assert h.wlbm_get_option(wl.wlbm.OPT_GRAPH_REPLAYS) == steps // BENCH_GRAPH
     w = L.angular_weights(L.ring_directions(cfg["q"]))
     dscale = float(w.max() * (L.e_eq(301.0, 624.8074248458514) - L.e_eq(300.0, 624.8074248458514)))
-    t_tol, s_tol = (TOL32, TOL32) if storage == 0 else (TOL16, TOL16_STATE)
+    t_tol, s_tol = (TOL32, TOL32) if storage == 0 else (TOL16, TOL16_STATE_WALL)
     worst_t = worst_s = 0.0
     for (cx, cy) in samples:
         orc, (ox, oy) = window_fn(cfg, cx, cy, steps)
