@@ -27,9 +27,9 @@ cpu_baseline  the FP64 oracle on the host cores, on a bounded sample of the same
 workloads the other headline workloads, measured in the same run after the timed region
           (default run only; --no-workloads skips them): pulses with bfloat16 storage, the
           4096 x 256 film (Q = 128) with float32 and bfloat16 storage, and the 96-film
-          batch with bfloat16 and float32 storage: step-kernel ms per launch from the
-          library's event timing, its fraction of the measured HBM bandwidth, and
-          whole-step updates/s.
+          batch with bfloat16 and float32 storage, launched per step and as one persistent
+          kernel per chunk: step-kernel ms per launch from the library's event timing, its
+          fraction of the measured HBM bandwidth, and whole-step updates/s.
 adjoint   the adjoint workload: backward / forward and (checkpointed forward + backward)
           / forward, the whole gradient's cost against a plain forward run.
 clocks    nvidia-smi samples over the whole native run (warm-up, timed region, e2e and
@@ -81,6 +81,11 @@ def parse():
     p.add_argument("--graph", type=int, default=48,
                    help="replay chunks of this many steps as one CUDA graph (multiple of 6; "
                         "0: launch every step directly)")
+    p.add_argument("--ring", type=int, default=0,
+                   help="ring depth of the TMA step kernel (0: library default by Q)")
+    p.add_argument("--tile-loop", type=int, default=None,
+                   help="1: resident blocks loop over the tiles, 0: one block per tile "
+                        "(library default)")
     p.add_argument("--variant", type=int, default=None,
                    help="step kernel: 0 register-pipelined, 1 bulk-copy ring, 2 warp-specialised, "
                         "3 TMA tiles (library default where available)")
@@ -497,11 +502,13 @@ def measure_single(wl, torch, cfg, storage, steps, warmup=48, graph=48, every=8)
             "dtype": "f32" if storage == "fp32" else "bf16-storage/f32-math"}
 
 
-def measure_batch(wl, torch, storage, steps, warmup=48, graph=48, every=8):
+def measure_batch(wl, torch, storage, steps, warmup=48, graph=48, every=8, persistent=0):
     """The 96-film batch (fixed TMA-tile variant, graph replay): whole-step updates/s and
     the batched step kernel's ms per launch and HBM fraction.  One step streams every
     instance's planes once, tens of GB in all, so no instance stays in the 129 MB L2
-    from one step to the next: every instance's algorithmic bytes are DRAM bytes."""
+    from one step to the next: every instance's algorithmic bytes are DRAM bytes.
+    persistent=1: one persistent launch per graph chunk (wall pass and tiles together);
+    its duration over the chunk's steps is then the per-step kernel time (walls included)."""
     import workloads as W
     insts = W.batch_c4(seed=4)
     specs = [dict(nx=c["nx"], ny=c["ny"], q=c["q"], bc=c["bc"], t_wall=c["t_wall"],
@@ -513,6 +520,7 @@ def measure_batch(wl, torch, storage, steps, warmup=48, graph=48, every=8):
         b = wl.WormLBMBatch(specs, storage=st, stream=stream)
         b.wlbm_batch_set_option(wl.wlbm.OPT_STEP_VARIANT, 3)
         b.wlbm_batch_set_option(wl.wlbm.OPT_GRAPH_STEPS, graph)
+        b.wlbm_batch_set_option(wl.wlbm.OPT_PERSISTENT, persistent)
         b.wlbm_batch_init_temperature([c["dT"] for c in insts])
         b.wlbm_batch_step(warmup)
         stream.synchronize()
@@ -526,6 +534,7 @@ def measure_batch(wl, torch, storage, steps, warmup=48, graph=48, every=8):
         b.wlbm_batch_profile(0)
         ms = e0.elapsed_time(e1)
         kms, kn, _ = b.wlbm_batch_profile_read()
+        b.wlbm_batch_check()
         b.close()
     upd = sum(sp["q"] * sp["nx"] * sp["ny"] for sp in specs)
     algo = sum(sp["q"] * sp["nx"] * sp["ny"] * (2 * elem + (12.0 if elem == 2 else 8.0) / sp["q"])
@@ -534,7 +543,8 @@ def measure_batch(wl, torch, storage, steps, warmup=48, graph=48, every=8):
     ach, frac, peak, kind = kernel_fraction(per, algo)
     state_gb = sum(2 * sp["q"] * (sp["nx"] + 2) * (sp["ny"] + 2) * elem for sp in specs) / 1e9
     return {"updates_per_s": upd * steps / (ms * 1e-3), "ms_per_step": ms / steps,
-            "kernel": "k_step_tma_batch", "kernel_ms_per_launch": per,
+            "kernel": "k_batch_persistent (per step)" if persistent else "k_step_tma_batch",
+            "kernel_ms_per_launch": per,
             "kernel_launches_timed": kn, "achieved_gbs": ach, "frac": frac, "peak": peak,
             "peak_kind": kind, "algorithmic_bytes_per_launch": algo, "steps": steps,
             "instances": len(specs), "state_gb": state_gb,
@@ -553,7 +563,11 @@ def other_workloads(wl, torch, args):
             ("film_fp32", lambda: measure_single(wl, torch, W.film_c3(kn=1.0), "fp32", 480)),
             ("film_bf16", lambda: measure_single(wl, torch, W.film_c3(kn=1.0), "bf16", 480)),
             ("batch_bf16", lambda: measure_batch(wl, torch, "bf16", 96)),
-            ("batch_fp32", lambda: measure_batch(wl, torch, "fp32", 96))]
+            ("batch_fp32", lambda: measure_batch(wl, torch, "fp32", 96)),
+            ("batch_bf16_persistent", lambda: measure_batch(wl, torch, "bf16", 96,
+                                                            persistent=1)),
+            ("batch_fp32_persistent", lambda: measure_batch(wl, torch, "fp32", 96,
+                                                            persistent=1))]
     for name, fn in runs:
         try:
             out[name] = fn()
@@ -569,6 +583,8 @@ def other_workloads(wl, torch, args):
                                          W.film_c3(kn=1.0)),
             "batch_bf16": batch_config(argparse.Namespace(storage="bf16"), 96),
             "batch_fp32": batch_config(argparse.Namespace(storage="fp32"), 96)}
+    cfgs["batch_bf16_persistent"] = cfgs["batch_bf16"]
+    cfgs["batch_fp32_persistent"] = cfgs["batch_fp32"]
     for k in out:
         out[k]["config"] = cfgs[k]
     return out
@@ -663,7 +679,13 @@ def main():
             h.wlbm_set_option(wl.wlbm.OPT_GRAPH_STEPS, args.graph)
         if args.fuse is not None:
             h.wlbm_set_option(wl.wlbm.OPT_FUSE_PERIODIC, args.fuse)
+        if args.ring:
+            h.wlbm_set_option(wl.wlbm.OPT_RING_STAGES, args.ring)
+        if args.tile_loop is not None:
+            h.wlbm_set_option(wl.wlbm.OPT_TILE_LOOP, args.tile_loop)
         variant_used = h.wlbm_get_option(wl.wlbm.OPT_STEP_VARIANT)
+        h_ring = h.wlbm_get_option(wl.wlbm.OPT_RING_STAGES)
+        h_loop = h.wlbm_get_option(wl.wlbm.OPT_TILE_LOOP)
         clocks = None if args.no_extras else Clocks(local)
         dT = torch.as_tensor(cfg["dT"]).to("cuda", non_blocking=False)
         h.wlbm_init_temperature(dT)
@@ -752,6 +774,7 @@ def main():
             "launch": {"graph_steps": args.graph,
                        "step_kernel": {0: "register-pipelined", 1: "bulk-copy ring",
                                        2: "warp-specialised", 3: "TMA tiles"}[variant_used],
+                       "ring_stages": h_ring, "tile_loop": h_loop,
                        "l2": "state %.2f GB > L2 (no flush needed)"
                              % (2 * cfg["q"] * cells * (4 if args.storage == "fp32" else 2) / 1e9)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

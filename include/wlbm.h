@@ -291,11 +291,18 @@ wlbm_status wlbm_adjoint_backward(wlbm_handle* h, const float* dJ_dT, const floa
  *                          ghost cells mirroring each edge cell (no separate pass).
  *   WLBM_OPT_GRAPH_REPLAYS read only (wlbm_get_option): how many chunks of steps this
  *                          handle has run as replays of a captured graph.
+ *   WLBM_OPT_RING_STAGES   variant 3 ring depth of the tensor copies: 0 (default: by Q,
+ *                          6 float32 / 16 bfloat16 for Q <= 64, else 4 / 8), or 6 or 4
+ *                          (float32), 8 or 16 (bfloat16).
+ *   WLBM_OPT_TILE_LOOP     variant 3: 0 (default) one block per 128 x 14 tile; 1 a grid of
+ *                          resident blocks that take the tiles in turn (no partial last
+ *                          wave; bfloat16 runs three such blocks per SM where the ring
+ *                          fits).  Same results bit for bit.
  * wlbm_check: synchronises the stream and returns WLBM_ERR_TIMEOUT if a bounded wait
  * inside a kernel gave up since the last check (the status is then cleared). */
 enum { WLBM_OPT_STEP_VARIANT = 1, WLBM_OPT_GRAPH_STEPS = 2, WLBM_OPT_FUSE_PERIODIC = 3,
        WLBM_OPT_GRAPH_REPLAYS = 4, WLBM_OPT_PERSISTENT = 5, WLBM_OPT_RING_STAGES = 6,
-       WLBM_OPT_WAIT_LIMIT = 7, WLBM_OPT_STALL_TEST = 8 };
+       WLBM_OPT_WAIT_LIMIT = 7, WLBM_OPT_STALL_TEST = 8, WLBM_OPT_TILE_LOOP = 9 };
 wlbm_status wlbm_set_option(wlbm_handle* h, int32_t key, int64_t value);
 /* wlbm_get_option: the current value of a wlbm_set_option key in *value (host). */
 wlbm_status wlbm_get_option(const wlbm_handle* h, int32_t key, int64_t* value);

@@ -1,7 +1,8 @@
 """Autotuning cache for libwlbm.
 
 The search itself is native (wlbm_autotune / wlbm_batch_autotune time every candidate of
-step-kernel variant x CUDA-graph replay on the real grid).  This module only remembers
+step-kernel variant x CUDA-graph replay on the real grid; for batches also the persistent
+kernel at two ring depths, with a chunk of 64 steps per launch or the graph's).  This module only remembers
 the winner per workload signature in a JSON file, so a later run with the same shapes
 skips the search.  The signature covers the GPU model, the storage type, the grids' shapes,
 walls and MFP kind, and the build of libwlbm.so (its size and modification time), so a
@@ -12,7 +13,8 @@ import hashlib
 import json
 import os
 
-from .wlbm import LIB_PATH, OPT_GRAPH_STEPS, OPT_STEP_VARIANT
+from .wlbm import (LIB_PATH, OPT_GRAPH_STEPS, OPT_PERSISTENT, OPT_RING_STAGES,
+                   OPT_STEP_VARIANT)
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 
@@ -55,17 +57,23 @@ def _store(sig, rec):
 
 
 def tune_batch(batch, storage, trial_steps=48, use_cache=True):
-    """Pick variant and graph replay for a WormLBMBatch (before its init).  Returns the
-    record {variant, graph_steps, ms_per_step, cached}."""
+    """Pick variant, graph replay, persistent kernel and its ring depth for a WormLBMBatch
+    (before its init).  Returns the record {variant, graph_steps, persistent, ring_stages,
+    ms_per_step, cached}."""
     sig = signature(batch.specs, storage)
     if use_cache:
         rec = _load().get(sig)
-        if rec:
+        if rec and "persistent" in rec:
+            batch.wlbm_batch_set_option(OPT_PERSISTENT, 0)
             batch.wlbm_batch_set_option(OPT_STEP_VARIANT, rec["variant"])
+            batch.wlbm_batch_set_option(OPT_PERSISTENT, rec["persistent"])
+            batch.wlbm_batch_set_option(OPT_RING_STAGES, rec["ring_stages"])
             batch.wlbm_batch_set_option(OPT_GRAPH_STEPS, rec["graph_steps"])
             return dict(rec, cached=True)
     v, g, ms = batch.wlbm_batch_autotune(trial_steps)
-    rec = {"variant": v, "graph_steps": g, "ms_per_step": ms}
+    rec = {"variant": v, "graph_steps": g, "ms_per_step": ms,
+           "persistent": batch.wlbm_batch_get_option(OPT_PERSISTENT),
+           "ring_stages": batch.wlbm_batch_get_option(OPT_RING_STAGES)}
     _store(sig, rec)
     return dict(rec, cached=False)
 

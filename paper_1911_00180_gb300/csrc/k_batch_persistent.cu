@@ -3,18 +3,20 @@
 //
 // Many uncoupled gray problems (Sec. 2.1: the multigray approach solves one gray BTE per
 // band; a batch also holds films of other sizes, Knudsen numbers and Q) share the GPU.
-// A block takes work items from a queue in a fixed order: for every step t of the chunk,
-// first the wall chunks of all instances (Sec. 2.6 on the ghost frame of state t), then
-// the step tiles of all instances (Eq. lbm-energy / Eq. algorithm, the same tile code as
+// A block takes work items from a queue in a fixed order: for every step t of the chunk
+// and every instance in turn, the instance's wall chunks (Sec. 2.6 on the ghost frame of
+// state t), then its step tiles (Eq. lbm-energy / Eq. algorithm, the same tile code as
 // the other variant-3 kernels, so results are bit for bit those of the launch-per-step
 // form).  Instead of a grid-wide barrier between the passes, every item waits only for
 // what it reads: a wall chunk of instance k at step t for all of k's tiles of step t - 1,
 // a tile for all of k's wall chunks of step t and all of k's tiles of step t - 1 (the
-// energy planes rotate, so a tile also overwrites what those tiles read).  Items are
-// claimed in queue order and depend only on earlier items, which running blocks hold, so
-// the waits always end; each is still bounded in time, and a wait that gives up sets the
-// instance's status word and an abort flag that makes every block leave.  Waits happen only
-// between items, when no tensor copy of the block is in flight.
+// energy planes rotate, so a tile also overwrites what those tiles read).  Instance by
+// instance, a wall chunk finds its instance's previous step long done, and a tile waits at
+// most for the wall chunks claimed just before it.  Items are claimed in queue order and
+// depend only on earlier items, which running blocks hold, so the waits always end; each
+// is still bounded in time, and a wait that gives up sets the instance's status word and an
+// abort flag that makes every block leave.  Waits happen only between items, when no
+// tensor copy of the block is in flight.
 #include <cuda.h>
 
 #include "elem.cuh"
@@ -49,9 +51,14 @@ __device__ bool wait_count(const unsigned* ctr, unsigned target, const int* abor
   }
 }
 
-struct PersistShared {
+// Wall chunks and step tiles never run at the same time in a block, and a tile leaves no
+// tensor copy in flight, so a wall chunk's shared data overlays the ring of the tiles.
+struct WallOverlay {
   WallSmem wsm;
   WallArgs wa;
+};
+
+struct PersistShared {
   StepArgs sa;
   const void* tm;
   const uint8_t* wcodes;
@@ -61,11 +68,19 @@ struct PersistShared {
   int fail;
 };
 
+// Resident blocks per SM the register budget aims at: the bfloat16 tile keeps its cell
+// terms in shared memory and fits three blocks; float32 keeps them in registers (two).
+template <typename T>
+constexpr int persist_min_blocks() { return sizeof(T) == 2 ? 3 : 2; }
+
 template <typename T, int S, bool SPEC>
-__global__ void __launch_bounds__(kPersistThreads, 2) k_batch_persistent(const PersistArgs p) {
+__global__ void __launch_bounds__(kPersistThreads, persist_min_blocks<T>())
+    k_batch_persistent(const PersistArgs p) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ PersistShared ps;
   using LY = TmaLayout<T, S>;
+  static_assert(sizeof(WallOverlay) <= LY::off_bar, "the wall data fits in the ring");
+  WallOverlay& wo = *reinterpret_cast<WallOverlay*>(smem);
   constexpr bool REF = sizeof(T) == 2;
   const int tid = int(threadIdx.x);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + LY::off_bar);
@@ -91,31 +106,30 @@ __global__ void __launch_bounds__(kPersistThreads, 2) k_batch_persistent(const P
       const int item = int(atomicAdd(queue, 1u));
       if (item < total && *reinterpret_cast<const volatile int*>(p.abort_flag) == 0) {
         const int t = item / per_step;
-        int r = item - t * per_step;
-        int k = 0;
+        const int r = item - t * per_step;
+        int lo = 0, hi = p.n - 1;                 // instance: the last first_item <= r
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (p.insts[mid].first_item <= r) lo = mid;
+          else hi = mid - 1;
+        }
+        const int k = lo;
+        const int local = r - p.insts[k].first_item;
+        const int nwall = p.walls[k].n_blocks;
         bool ok;
-        if (r < p.wall_items) {
-          k = p.wall_inst[r];
+        if (local < nwall) {
           ok = wait_count(done_t + k, unsigned(t) * unsigned(p.insts[k].n_tiles), p.abort_flag,
                           p.wait_limit);
           kind = 0;
-          ps.local = r - p.walls[k].first_block;
+          ps.local = local;
         } else {
-          r -= p.wall_items;
-          int lo = 0, hi = p.n - 1;
-          while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (p.insts[mid].first_tile <= r) lo = mid;
-            else hi = mid - 1;
-          }
-          k = lo;
-          const unsigned need_w = unsigned(t + 1) * unsigned(p.walls[k].n_blocks) +
+          const unsigned need_w = unsigned(t + 1) * unsigned(nwall) +
                                   (p.stall_test && k == 0 ? 1u : 0u);
           ok = wait_count(done_w + k, need_w, p.abort_flag, p.wait_limit) &&
                wait_count(done_t + k, unsigned(t) * unsigned(p.insts[k].n_tiles), p.abort_flag,
                           p.wait_limit);
           kind = 1;
-          ps.local = r - p.insts[k].first_tile;
+          ps.local = local - nwall;
         }
         if (!ok) {
           atomicOr(p.insts[k].a.status, 1);
@@ -148,10 +162,10 @@ __global__ void __launch_bounds__(kPersistThreads, 2) k_batch_persistent(const P
     if (kind == 0) {
       static_assert(sizeof(WallArgs) % 4 == 0, "copied as 32-bit words");
       const int* src = reinterpret_cast<const int*>(&p.walls[k].w);
-      int* dst = reinterpret_cast<int*>(&ps.wa);
+      int* dst = reinterpret_cast<int*>(&wo.wa);
       for (int i = tid; i < int(sizeof(WallArgs) / 4); i += kPersistThreads) dst[i] = src[i];
       __syncthreads();
-      walls_chunk<T, SPEC>(ps.wa, ps.wcodes, ps.we_ref, ps.local, ps.wsm, nullptr);
+      walls_chunk<T, SPEC>(wo.wa, ps.wcodes, ps.we_ref, ps.local, wo.wsm, nullptr);
     } else {
       const int tx = p.insts[k].tiles_x;
       const int bx = ps.local % tx, by = ps.local / tx;
@@ -189,11 +203,11 @@ cudaError_t configure_t() {
 }
 
 template <typename T, int S>
-int blocks_per_sm_t() {
+int blocks_per_sm_t(int max_q) {
   int n = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
           &n, k_batch_persistent<T, S, true>, kPersistThreads,
-          TmaLayout<T, S>::bytes(kMaxQ)) != cudaSuccess) {
+          TmaLayout<T, S>::bytes(max_q)) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
@@ -229,12 +243,12 @@ cudaError_t configure_batch_persistent() {
   return e;
 }
 
-int batch_persistent_blocks_per_sm(int storage, int stages) {
+int batch_persistent_blocks_per_sm(int storage, int stages, int max_q) {
   if (storage == WLBM_STORE_BF16_DEV)
-    return stages == kBF16Stages[1] ? blocks_per_sm_t<__nv_bfloat16, kBF16Stages[1]>()
-                                    : blocks_per_sm_t<__nv_bfloat16, kBF16Stages[0]>();
-  return stages == kF32Stages[1] ? blocks_per_sm_t<float, kF32Stages[1]>()
-                                 : blocks_per_sm_t<float, kF32Stages[0]>();
+    return stages == kBF16Stages[1] ? blocks_per_sm_t<__nv_bfloat16, kBF16Stages[1]>(max_q)
+                                    : blocks_per_sm_t<__nv_bfloat16, kBF16Stages[0]>(max_q);
+  return stages == kF32Stages[1] ? blocks_per_sm_t<float, kF32Stages[1]>(max_q)
+                                 : blocks_per_sm_t<float, kF32Stages[0]>(max_q);
 }
 
 cudaError_t launch_batch_persistent(int storage, int stages, const PersistArgs& p, int max_q,

@@ -25,6 +25,8 @@
 // reads slot j of the tape through the tape's own tensor map and writes slot j + 1.
 #include <cuda.h>
 
+#include <algorithm>
+
 #include "elem.cuh"
 #include "mbar.cuh"
 #include "step_tile.cuh"
@@ -39,7 +41,25 @@ __global__ void __maxnreg__(128)
     k_step_tma(const StepArgs a, const __grid_constant__ CUtensorMap tmap) {
   extern __shared__ __align__(128) unsigned char smem[];
   uint32_t g0 = 0;
-  step_tma_tile<T, S, FIELD_W, REF>(a, &tmap, int(blockIdx.x), int(blockIdx.y), smem, g0);
+  // single grids: the register-tile form (two blocks per SM)
+  step_tma_tile<T, S, FIELD_W, REF, false, false>(a, &tmap, int(blockIdx.x), int(blockIdx.y),
+                                                  smem, g0);
+}
+
+// Tile-looping form: a grid of resident blocks (three per SM for bfloat16, whose cell
+// terms sit in shared memory; two for float32) in which block b takes tiles b, b + grid,
+// ... in turn, so no partial last wave of blocks idles the GPU, and whose producer streams
+// the boxes of all its tiles without a pause at tile edges.
+template <typename T>
+constexpr int loop_min_blocks() { return sizeof(T) == 2 ? 3 : 2; }
+
+template <typename T, int S, bool FIELD_W, bool REF>
+__global__ void __launch_bounds__(32 * (kWarps3 + 1), loop_min_blocks<T>())
+    k_step_tma_loop(const StepArgs a, const __grid_constant__ CUtensorMap tmap, int tiles_x,
+                    int ntiles) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ int fail;
+  step_tma_loop<T, S, FIELD_W, REF>(a, &tmap, tiles_x, ntiles, smem, &fail);
 }
 
 // Batched form: block b belongs to the instance whose first_tile is the largest one <= b;
@@ -81,11 +101,13 @@ __global__ void __maxnreg__(128) k_step_tma_batch(const BatchInst* insts, int n,
 template <typename T, int S, bool BATCH>
 cudaError_t configure_tma_t() {
   const int bytes = int(TmaLayout<T, S>::bytes(kMaxQ));
-  const void* fns[3] = {(const void*)k_step_tma<T, S, false, sizeof(T) == 2>,
+  const void* fns[5] = {(const void*)k_step_tma<T, S, false, sizeof(T) == 2>,
                         (const void*)k_step_tma<T, S, true, sizeof(T) == 2>,
+                        (const void*)k_step_tma_loop<T, S, false, sizeof(T) == 2>,
+                        (const void*)k_step_tma_loop<T, S, true, sizeof(T) == 2>,
                         BATCH ? (const void*)k_step_tma_batch<T, S, sizeof(T) == 2> : nullptr};
   cudaError_t e = cudaSuccess;
-  for (int k = 0; k < 3 && fns[k] && e == cudaSuccess; ++k) {
+  for (int k = 0; k < 5 && fns[k] && e == cudaSuccess; ++k) {
     e = cudaFuncSetAttribute(fns[k], cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     // several blocks per SM: ask for the largest shared-memory carveout
     if (e == cudaSuccess)
@@ -102,9 +124,35 @@ cudaError_t launch_tma_t(const StepArgs& a, const CUtensorMap& tm, cudaStream_t 
   const dim3 grid((a.cmax - a.cbase) / kTW3 + 1, (a.rmax - a.rmin + kRows3) / kRows3);
   const size_t bytes = LY::bytes(a.q);
   constexpr bool REF = sizeof(T) == 2;
+  if (a.loop_blocks > 0 && !a.tape) {
+    const int ntiles = int(grid.x * grid.y);
+    const int nb = std::min(a.loop_blocks, ntiles);
+    if (a.wfield)
+      k_step_tma_loop<T, S, true, REF><<<nb, 32 * (kWarps3 + 1), bytes, s>>>(a, tm, int(grid.x),
+                                                                             ntiles);
+    else
+      k_step_tma_loop<T, S, false, REF><<<nb, 32 * (kWarps3 + 1), bytes, s>>>(a, tm, int(grid.x),
+                                                                              ntiles);
+    return cudaGetLastError();
+  }
   if (a.wfield) k_step_tma<T, S, true, REF><<<grid, block, bytes, s>>>(a, tm);
   else k_step_tma<T, S, false, REF><<<grid, block, bytes, s>>>(a, tm);
   return cudaGetLastError();
+}
+
+template <typename T, int S>
+int loop_blocks_t(bool field_w, int q) {
+  int per_sm = 0, dev = 0, sms = 0;
+  const void* fn = field_w ? (const void*)k_step_tma_loop<T, S, true, sizeof(T) == 2>
+                           : (const void*)k_step_tma_loop<T, S, false, sizeof(T) == 2>;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 32 * (kWarps3 + 1),
+                                                    TmaLayout<T, S>::bytes(q)) != cudaSuccess ||
+      cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return per_sm * sms;
 }
 
 constexpr int kStagesF32 = 6;    // 6 x 7.4 KB of boxes in flight per block
@@ -162,12 +210,35 @@ void tma_cover(const int bc_kind[4], int nx, int ny, StepArgs* a, int* tiles_x, 
   *tiles_y = (a->rmax - a->rmin + kRows3) / kRows3;
 }
 
+// Ring depth of a single-grid step: the explicit choice, else by Q (see above).
+static int single_stages(int storage, int stages, int q) {
+  if (storage == WLBM_STORE_BF16_DEV)
+    return stages ? stages : (q <= kDeepMaxQ ? kStagesBF16Deep : kStagesBF16);
+  return stages ? stages : (q <= kDeepMaxQ ? kStagesF32 : kStagesF32Shallow);
+}
+
+bool step_tma_stages_ok(int storage, int stages) {
+  if (stages == 0) return true;
+  if (storage == WLBM_STORE_BF16_DEV) return stages == kStagesBF16 || stages == kStagesBF16Deep;
+  return stages == kStagesF32 || stages == kStagesF32Shallow;
+}
+
+int step_tma_loop_blocks(int storage, int stages, bool field_w, int q) {
+  const int st = single_stages(storage, stages, q);
+  if (storage == WLBM_STORE_BF16_DEV)
+    return st == kStagesBF16Deep ? loop_blocks_t<__nv_bfloat16, kStagesBF16Deep>(field_w, q)
+                                 : loop_blocks_t<__nv_bfloat16, kStagesBF16>(field_w, q);
+  return st == kStagesF32 ? loop_blocks_t<float, kStagesF32>(field_w, q)
+                          : loop_blocks_t<float, kStagesF32Shallow>(field_w, q);
+}
+
 cudaError_t launch_step_tma(int storage, const StepArgs& a, cudaStream_t s) {
   const CUtensorMap& tm = *static_cast<const CUtensorMap*>(a.tmap);
+  const int st = single_stages(storage, a.ring_stages, a.q);
   if (storage == WLBM_STORE_BF16_DEV)
-    return a.q <= kDeepMaxQ ? launch_tma_t<__nv_bfloat16, kStagesBF16Deep>(a, tm, s)
-                            : launch_tma_t<__nv_bfloat16, kStagesBF16>(a, tm, s);
-  return a.q <= kDeepMaxQ ? launch_tma_t<float, kStagesF32>(a, tm, s)
+    return st == kStagesBF16Deep ? launch_tma_t<__nv_bfloat16, kStagesBF16Deep>(a, tm, s)
+                                 : launch_tma_t<__nv_bfloat16, kStagesBF16>(a, tm, s);
+  return st == kStagesF32 ? launch_tma_t<float, kStagesF32>(a, tm, s)
                           : launch_tma_t<float, kStagesF32Shallow>(a, tm, s);
 }
 

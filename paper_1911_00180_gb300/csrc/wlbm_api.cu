@@ -132,6 +132,9 @@ struct wlbm_handle {
   bool has_tmap = false;
   std::string tmap_why;       // why there is no tensor map
   int graph_steps = 0;        // >0: replay chunks of this many steps as one CUDA graph
+  int ring_stages = 0;        // variant 3 ring depth (0: by Q)
+  int tile_loop = 0;          // variant 3: 1 = resident blocks loop over the tiles
+  int loop_blocks = 0;        // blocks of that grid (set with the options)
   int fuse_periodic = 0;      // 1: both axes periodic, the step kernel mirrors the edges
   // per energy-plane role and replay parity (consecutive replays alternate, so a graph's
   // event pairs are read while the other one runs)
@@ -713,6 +716,8 @@ static wlbm_status enqueue_steps(wlbm_handle* h, int count, int every,
     sa.variant = h->step_variant; sa.status = h->d_status;
     sa.xper = h->xper; sa.yper = h->yper; sa.wrap = wrap;
     sa.tmap = h->has_tmap ? h->tmap : nullptr;
+    sa.ring_stages = h->ring_stages;
+    sa.loop_blocks = h->tile_loop ? h->loop_blocks : 0;
     sa.order = h->d_order + size_t(t) * (g.q + 17);
     int tx_unused = 0, ty_unused = 0;
     tma_cover(h->bc_kind, g.nx, g.ny, &sa, &tx_unused, &ty_unused);
@@ -842,6 +847,8 @@ wlbm_status wlbm_get_option(const wlbm_handle* h, int32_t key, int64_t* value) {
   else if (key == WLBM_OPT_GRAPH_STEPS) *value = h->graph_steps;
   else if (key == WLBM_OPT_FUSE_PERIODIC) *value = h->fuse_periodic;
   else if (key == WLBM_OPT_GRAPH_REPLAYS) *value = h->graph_replays;
+  else if (key == WLBM_OPT_RING_STAGES) *value = h->ring_stages;
+  else if (key == WLBM_OPT_TILE_LOOP) *value = h->tile_loop;
   else return WLBM_ERR_INVALID_ARG;
   return WLBM_OK;
 }
@@ -863,6 +870,23 @@ wlbm_status wlbm_set_option(wlbm_handle* h, int32_t key, int64_t value) {
   }
   if (key == WLBM_OPT_FUSE_PERIODIC && (value == 0 || value == 1)) {
     h->fuse_periodic = int(value);
+    h->drop_graphs();
+    return WLBM_OK;
+  }
+  if ((key == WLBM_OPT_RING_STAGES && step_tma_stages_ok(h->storage, int(value)) &&
+       value >= 0 && value <= 64) ||
+      (key == WLBM_OPT_TILE_LOOP && (value == 0 || value == 1))) {
+    const int stages = key == WLBM_OPT_RING_STAGES ? int(value) : h->ring_stages;
+    const int loop = key == WLBM_OPT_TILE_LOOP ? int(value) : h->tile_loop;
+    int blocks = 0;
+    if (loop) {
+      blocks = step_tma_loop_blocks(h->storage, stages, h->field_w, h->g.q);
+      if (blocks <= 0)
+        return h->fail(WLBM_ERR_CUDA, "wlbm_set_option: occupancy of the tile-looping kernel");
+    }
+    h->ring_stages = stages;
+    h->tile_loop = loop;
+    h->loop_blocks = blocks;
     h->drop_graphs();
     return WLBM_OK;
   }
@@ -1719,6 +1743,7 @@ struct wlbm_batch {
   void layout() {
     total_tiles = 0;
     total_wall_blocks = 0;
+    int items = 0;
     const int tw = step_tile_width(storage, variant);
     for (size_t k = 0; k < h.size(); ++k) {
       const Geom& g = h[k]->g;
@@ -1734,6 +1759,8 @@ struct wlbm_batch {
       h_walls[k].first_block = total_wall_blocks;
       h_walls[k].n_blocks = wall_blocks(h[k]->walls);
       total_wall_blocks += h_walls[k].n_blocks;
+      h_inst[k].first_item = items;
+      items += h_walls[k].n_blocks + tx * ty;
     }
   }
 };
@@ -1944,7 +1971,7 @@ static wlbm_status batch_enqueue(wlbm_batch* b, int count, int every,
         st = b->cuda(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev),
                      "wlbm_batch_step: device");
       if (st != WLBM_OK) return st;
-      const int per_sm = batch_persistent_blocks_per_sm(b->storage, b->ring_stages);
+      const int per_sm = batch_persistent_blocks_per_sm(b->storage, b->ring_stages, b->max_q);
       if (per_sm <= 0)
         return b->fail(WLBM_ERR_CUDA, "wlbm_batch_step: the persistent kernel does not fit an SM");
       b->persist_grid = per_sm * sms;
@@ -1952,7 +1979,6 @@ static wlbm_status batch_enqueue(wlbm_batch* b, int count, int every,
     PersistArgs p{};
     p.insts = b->d_inst;
     p.walls = b->d_walls;
-    p.wall_inst = b->d_wall_inst;
     p.n = n;
     p.wall_items = b->total_wall_blocks;
     p.tile_items = b->total_tiles;
@@ -2224,22 +2250,35 @@ wlbm_status wlbm_batch_profile_read(wlbm_batch* b, double* step_ms, int64_t* ste
 }
 
 // Native autotuner: times `trial_steps` steps for every candidate (step-kernel variant x
-// graph replay) after one warm-up run of each, keeps the fastest, and reports it.  The
-// trial steps advance the instances: call it before wlbm_batch_init_temperature.
+// graph replay with per-step launches; the persistent kernel at both ring depths x graph
+// replay, where the batch allows it) after one warm-up run of each, keeps the fastest, and
+// reports it.  The trial steps advance the instances: call it before
+// wlbm_batch_init_temperature.
 wlbm_status wlbm_batch_autotune(wlbm_batch* b, int32_t trial_steps, int32_t* variant,
                                 int32_t* graph_steps, double* ms_per_step) {
   if (!b || trial_steps < 6) return WLBM_ERR_INVALID_ARG;
   const int g = std::min(kBatchChunk, (trial_steps / 6) * 6);
-  const int cand[6][2] = {{1, 0}, {0, 0}, {3, 0}, {1, g}, {0, g}, {3, g}};
+  const int alt = b->storage == WLBM_STORE_BF16_DEV ? 16 : 4;   // the other ring depth
+  // variant, graph steps, persistent, ring stages
+  const int cand[10][4] = {{1, 0, 0, 0}, {0, 0, 0, 0}, {3, 0, 0, 0}, {1, g, 0, 0},
+                           {0, g, 0, 0}, {3, g, 0, 0}, {3, 0, 1, 0}, {3, g, 1, 0},
+                           {3, 0, 1, alt}, {3, g, 1, alt}};
   double best = 1e300;
-  int bv = 1, bg = 0;
+  int bv = 1, bg = 0, bp = 0, bs = 0;
+  std::string why;
   cudaEvent_t e0, e1;
   wlbm_status st = b->cuda(cudaEventCreate(&e0), "autotune");
   if (st != WLBM_OK) return st;
   st = b->cuda(cudaEventCreate(&e1), "autotune");
-  for (int c = 0; c < 6 && st == WLBM_OK; ++c) {
+  for (int c = 0; c < 10 && st == WLBM_OK; ++c) {
     if (cand[c][0] == 3 && !b->all_tmap) continue;
-    st = wlbm_batch_set_option(b, WLBM_OPT_STEP_VARIANT, cand[c][0]);
+    st = wlbm_batch_set_option(b, WLBM_OPT_PERSISTENT, 0);
+    if (st == WLBM_OK) st = wlbm_batch_set_option(b, WLBM_OPT_STEP_VARIANT, cand[c][0]);
+    if (st == WLBM_OK && cand[c][2]) {
+      if (!b->persistent_ok(&why)) continue;
+      st = wlbm_batch_set_option(b, WLBM_OPT_PERSISTENT, 1);
+    }
+    if (st == WLBM_OK) st = wlbm_batch_set_option(b, WLBM_OPT_RING_STAGES, cand[c][3]);
     if (st == WLBM_OK) st = wlbm_batch_set_option(b, WLBM_OPT_GRAPH_STEPS, cand[c][1]);
     if (st == WLBM_OK) st = wlbm_batch_step(b, g > 0 ? g : 6);           // warm-up / capture
     if (st == WLBM_OK) st = b->cuda(cudaEventRecord(e0, b->stream), "autotune");
@@ -2252,12 +2291,17 @@ wlbm_status wlbm_batch_autotune(wlbm_batch* b, int32_t trial_steps, int32_t* var
       best = ms / trial_steps;
       bv = cand[c][0];
       bg = cand[c][1];
+      bp = cand[c][2];
+      bs = cand[c][3];
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (st != WLBM_OK) return st;
+  wlbm_batch_set_option(b, WLBM_OPT_PERSISTENT, 0);
   wlbm_batch_set_option(b, WLBM_OPT_STEP_VARIANT, bv);
+  wlbm_batch_set_option(b, WLBM_OPT_PERSISTENT, bp);
+  wlbm_batch_set_option(b, WLBM_OPT_RING_STAGES, bs);
   wlbm_batch_set_option(b, WLBM_OPT_GRAPH_STEPS, bg);
   if (variant) *variant = bv;
   if (graph_steps) *graph_steps = bg;

@@ -79,6 +79,11 @@ struct StepArgs {
   int cmin, cmax, rmin, rmax, cbase;
   // variant 3 in tape mode: tensor-map plane index of plane 0 of the source slot
   int tape_z0;
+  // variant 3, single grids: ring depth (0: by Q) and, when loop_blocks > 0, a grid of
+  // that many blocks that each take every loop_blocks-th tile in turn (no last partial
+  // wave of blocks); 0: one block per tile
+  int ring_stages;
+  int loop_blocks;
 };
 
 // Stable sort of one step's directions by kind = hop | paused << 3 (16 kinds): writes the
@@ -275,6 +280,7 @@ struct BatchInst {
   const uint16_t* order;  // variant 3: kind-sorted directions of the chunk, [t][q + 17]
   const void* tmap;       // variant 3: device address of the instance's CUtensorMap
   int n_tiles;            // step-kernel tiles of this instance
+  int first_item;         // persistent kernel: first item of this instance within a step
 };
 
 struct BatchWalls {
@@ -287,14 +293,13 @@ struct BatchWalls {
 };
 
 // Persistent batched kernel (variant 3 tiles and the wall pass in one launch for a chunk
-// of steps): its work items are, for every step t of the chunk, the wall chunks of all
-// instances, then the step tiles of all instances, taken in that order from a queue.  A
-// wall chunk of instance k at step t waits until every tile of k's step t - 1 is done; a
+// of steps): its work items are, for every step t of the chunk and every instance k in
+// turn, the wall chunks of k, then the step tiles of k, taken in that order from a queue.
+// A wall chunk of instance k at step t waits until every tile of k's step t - 1 is done; a
 // tile waits until every wall chunk of k's step t is done (and every tile of step t - 1).
 struct PersistArgs {
   const BatchInst* insts;
   const BatchWalls* walls;
-  const int* wall_inst;   // [wall_items] instance of each wall chunk of a step
   int n;                  // instances
   int wall_items, tile_items;   // per step
   int steps;              // steps of this launch (codes of steps 0 .. steps-1 of the chunk)
@@ -366,6 +371,10 @@ cudaError_t configure_walls();        // the same for the single-grid wall pass
 // `out`, 128 bytes, 64-byte aligned; false with a reason when it cannot be made).
 cudaError_t configure_step_tma();
 cudaError_t launch_step_tma(int storage, const StepArgs& a, cudaStream_t s);
+// Ring depths compiled for single grids (0 picks by Q) and the blocks of the tile-looping
+// grid for this storage, depth, W kind and Q (resident blocks per SM x SMs; 0 on error).
+bool step_tma_stages_ok(int storage, int stages);
+int step_tma_loop_blocks(int storage, int stages, bool field_w, int q);
 // Batched variant 3 (one block per 128 x 14 tile of every instance) and its tile shape.
 cudaError_t launch_step_tma_batch(int storage, const BatchInst* insts, int n, int max_q,
                                   int total_tiles, int t, cudaStream_t s);
@@ -396,7 +405,7 @@ cudaError_t launch_walls_batch(int storage, const BatchWalls* b, const int* bloc
 // Persistent batched kernel (k_batch_persistent.cu): attributes, resident blocks per SM and
 // one launch of p.steps steps on `grid` blocks (ring depth `stages`: 0 takes the default).
 cudaError_t configure_batch_persistent();
-int batch_persistent_blocks_per_sm(int storage, int stages);
+int batch_persistent_blocks_per_sm(int storage, int stages, int max_q);
 bool batch_persistent_stages_ok(int storage, int stages);
 cudaError_t launch_batch_persistent(int storage, int stages, const PersistArgs& p, int max_q,
                                     int grid, bool any_spec, cudaStream_t s);

@@ -17,6 +17,8 @@ WLBM_ERR_CUDA, WLBM_ERR_TIMEOUT, WLBM_ERR_STATE = 4, 5, 6
 BC_PERIODIC, BC_ISOTHERMAL, BC_ADIABATIC_DIFFUSE, BC_ADIABATIC_SPECULAR = 0, 1, 2, 3
 STORE_FP32_DEV, STORE_BF16_DEV = 0, 1
 OPT_STEP_VARIANT, OPT_GRAPH_STEPS, OPT_FUSE_PERIODIC, OPT_GRAPH_REPLAYS = 1, 2, 3, 4
+OPT_PERSISTENT, OPT_RING_STAGES, OPT_WAIT_LIMIT, OPT_STALL_TEST = 5, 6, 7, 8
+OPT_TILE_LOOP = 9
 REDUCE_N = 9          # WLBM_REDUCE_N
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "UNSTABLE", 3: "OOM", 4: "CUDA", 5: "TIMEOUT",
                 6: "STATE"}
@@ -88,6 +90,7 @@ def _load():
         "wlbm_batch_init_temperature": (C.c_int, [vp, C.POINTER(vp)]),
         "wlbm_batch_set_option": (C.c_int, [vp, i32, i64]),
         "wlbm_batch_get_option": (C.c_int, [vp, i32, C.POINTER(C.c_int64)]),
+        "wlbm_batch_check": (C.c_int, [vp]),
         "wlbm_batch_step": (C.c_int, [vp, i64]),
         "wlbm_batch_profile": (C.c_int, [vp, i32]),
         "wlbm_batch_profile_read": (C.c_int, [vp, C.POINTER(dbl), C.POINTER(i64),
@@ -458,6 +461,11 @@ class WormLBMBatch:
         v = C.c_int64()
         _batch_check(lib.wlbm_batch_get_option(self.b, int(key), C.byref(v)), self.b)
         return v.value
+
+    def wlbm_batch_check(self):
+        """Raises WlbmError(WLBM_ERR_TIMEOUT) if a bounded wait in a kernel of any instance
+        gave up since the last check (see include/wlbm.h)."""
+        _batch_check(lib.wlbm_batch_check(self.b), self.b)
 
     def wlbm_batch_profile(self, every=1):
         _batch_check(lib.wlbm_batch_profile(self.b, int(every)), self.b)

@@ -114,8 +114,30 @@ def test_batch_autotune_then_run():
     b = wl.WormLBMBatch(specs, storage=1)
     rec = autotune.tune_batch(b, 1, trial_steps=12, use_cache=False)
     assert rec["variant"] in (0, 1, 3) and rec["graph_steps"] in (0, 12)
+    assert rec["persistent"] == 0            # the batch has periodic instances
     b.wlbm_batch_init_temperature(dTs)
     b.wlbm_batch_step(20)
+    got = [v.wlbm_get_state().cpu().numpy() for v in b.instances]
+    b.close()
+    for k, (spec, dT) in enumerate(zip(specs, dTs)):
+        want = _single(spec, dT, 20, 1, 0, rec["variant"])
+        assert np.array_equal(_state(spec, got[k]), _state(spec, want)), k
+
+
+def test_batch_autotune_searches_persistent_kernel():
+    """A batch with walls only may pick the persistent kernel (either ring depth); whatever
+    it picks gives the single grids' states bit for bit."""
+    import paper_1911_00180_gb300 as wl
+    from paper_1911_00180_gb300 import autotune
+    specs = _specs_walls()[:4]
+    dTs = _dTs(specs)
+    b = wl.WormLBMBatch(specs, storage=1)
+    rec = autotune.tune_batch(b, 1, trial_steps=12, use_cache=False)
+    assert rec["persistent"] in (0, 1) and rec["ring_stages"] in (0, 16)
+    assert b.wlbm_batch_get_option(wl.wlbm.OPT_PERSISTENT) == rec["persistent"]
+    b.wlbm_batch_init_temperature(dTs)
+    b.wlbm_batch_step(20)
+    b.wlbm_batch_check()
     got = [v.wlbm_get_state().cpu().numpy() for v in b.instances]
     b.close()
     for k, (spec, dT) in enumerate(zip(specs, dTs)):
@@ -148,8 +170,138 @@ C4_PICK = (2, 5, 8, 12, 13, 21, 25, 33, 60, 85, 90, 95)
 BENCH_GRAPH, BENCH_PROFILE = 48, 8     # the benchmark's graph chunk and timing stride
 
 
+def _specs_walls():
+    """Uneven films and boxes with walls only (the persistent kernel takes no periodic
+    axis): every wall kind, a per-cell MFP field, specularity, a slower band and Q up to
+    128, on grids of one to several tiles in each direction."""
+    return [
+        dict(nx=150, ny=21, q=32, bc=(I, I, A, A), t_wall=(301.0, 300.0, 300.0, 300.0), mfp=4.0),
+        dict(nx=47, ny=33, q=16, bc=(A, A, A, A), t_wall=(300.0,) * 4, mfp=2.5),
+        dict(nx=90, ny=17, q=8, bc=(I, I, A, A), t_wall=(300.4, 299.8, 300.0, 300.0),
+             mfp_field=W.lognormal_mfp(90, 17, seed=3, corr=4.0)),
+        dict(nx=33, ny=260, q=64, bc=(A, A, I, A), t_wall=(300.0, 300.0, 300.7, 300.0), mfp=30.0),
+        dict(nx=70, ny=29, q=40, bc=(A, S, S, A), t_wall=(300.0,) * 4, mfp=5.0,
+             specularity=(0.6, 0.0, 0.0, 0.25)),
+        dict(nx=58, ny=31, q=24, bc=(I, I, A, A), t_wall=(300.5, 300.0, 300.0, 300.0), mfp=6.0,
+             speed=0.55),
+        dict(nx=300, ny=45, q=128, bc=(I, I, A, A), t_wall=(301.0, 300.0, 300.0, 300.0),
+             mfp=20.0),
+    ]
+
+
 @pytest.mark.parametrize("storage", [0, 1])
-def test_batch_c4_instances_match_oracle(storage):
+@pytest.mark.parametrize("graph,alt_ring", [(0, False), (12, False), (12, True)])
+def test_persistent_batch_equals_single_grids_bitwise(storage, graph, alt_ring):
+    """The persistent kernel (wall chunks and step tiles of every instance and step taken
+    from one queue, each waiting only for what it reads) gives the states of the same grids
+    stepped one by one, bit for bit: the same tile and wall code in another schedule.  37 +
+    24 steps: with 12-step graphs three replays, a direct one-step launch and two replays;
+    without, one launch per call.  Both ring depths."""
+    import torch
+    import paper_1911_00180_gb300 as wl
+    specs = _specs_walls()
+    dTs = _dTs(specs)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        b = wl.WormLBMBatch(specs, storage=storage, stream=stream)
+        b.wlbm_batch_set_option(wl.wlbm.OPT_STEP_VARIANT, 3)
+        b.wlbm_batch_set_option(wl.wlbm.OPT_GRAPH_STEPS, graph)
+        b.wlbm_batch_set_option(wl.wlbm.OPT_PERSISTENT, 1)
+        if alt_ring:
+            b.wlbm_batch_set_option(wl.wlbm.OPT_RING_STAGES, 16 if storage else 4)
+        b.wlbm_batch_init_temperature(dTs)
+        _, _, l0 = b.wlbm_batch_profile_read()
+        b.wlbm_batch_step(37)
+        b.wlbm_batch_step(24)
+        b.wlbm_batch_check()
+        assert b.wlbm_batch_get_option(wl.wlbm.OPT_GRAPH_REPLAYS) == (5 if graph else 0)
+        _, _, l1 = b.wlbm_batch_profile_read()
+        assert l1 - l0 == (6 if graph else 2)        # one kernel launch per chunk
+        got = [v.wlbm_get_state().cpu().numpy() for v in b.instances]
+        b.close()
+    for k, (spec, dT) in enumerate(zip(specs, dTs)):
+        want = _single(spec, dT, 61, storage, 0, 3)
+        assert np.array_equal(_state(spec, got[k]), _state(spec, want)), k
+
+
+def test_persistent_refuses_periodic_instances_and_other_variants():
+    import paper_1911_00180_gb300 as wl
+    b = wl.WormLBMBatch(_specs())                   # has periodic instances
+    with pytest.raises(wl.WlbmError):
+        b.wlbm_batch_set_option(wl.wlbm.OPT_PERSISTENT, 1)
+    b.close()
+    b = wl.WormLBMBatch(_specs_walls()[:2])
+    b.wlbm_batch_set_option(wl.wlbm.OPT_STEP_VARIANT, 1)
+    with pytest.raises(wl.WlbmError):
+        b.wlbm_batch_set_option(wl.wlbm.OPT_PERSISTENT, 1)
+    b.wlbm_batch_set_option(wl.wlbm.OPT_STEP_VARIANT, 3)
+    b.wlbm_batch_set_option(wl.wlbm.OPT_PERSISTENT, 1)
+    with pytest.raises(wl.WlbmError):
+        b.wlbm_batch_set_option(wl.wlbm.OPT_STEP_VARIANT, 1)
+    with pytest.raises(wl.WlbmError):
+        b.wlbm_batch_set_option(wl.wlbm.OPT_RING_STAGES, 5)
+    b.close()
+
+
+@pytest.mark.parametrize("storage", [0, 1])
+def test_persistent_wait_runs_out_then_recovers(storage):
+    """Failure detection without a GPU fault: with the test hook, the tiles of instance 0
+    wait for a wall chunk that never completes (a count nothing reaches); after the short
+    limit the wait gives up, the instance's status word is set, every block leaves, and
+    wlbm_batch_check reports WLBM_ERR_TIMEOUT (once: the check clears it).  The same batch
+    then steps normally and matches the single grids bit for bit."""
+    import torch
+    import paper_1911_00180_gb300 as wl
+    specs = _specs_walls()[:4]
+    dTs = _dTs(specs)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        b = wl.WormLBMBatch(specs, storage=storage, stream=stream)
+        b.wlbm_batch_set_option(wl.wlbm.OPT_STEP_VARIANT, 3)
+        b.wlbm_batch_set_option(wl.wlbm.OPT_PERSISTENT, 1)
+        b.wlbm_batch_set_option(wl.wlbm.OPT_WAIT_LIMIT, 2_000_000)   # about a millisecond
+        b.wlbm_batch_set_option(wl.wlbm.OPT_STALL_TEST, 1)
+        b.wlbm_batch_init_temperature(dTs)
+        b.wlbm_batch_step(6)
+        with pytest.raises(wl.WlbmError) as err:
+            b.wlbm_batch_check()
+        assert err.value.status == wl.wlbm.WLBM_ERR_TIMEOUT
+        b.wlbm_batch_check()                        # the status words were cleared
+        b.wlbm_batch_set_option(wl.wlbm.OPT_STALL_TEST, 0)
+        b.wlbm_batch_set_option(wl.wlbm.OPT_WAIT_LIMIT, 0)
+        b.wlbm_batch_init_temperature(dTs)
+        b.wlbm_batch_step(20)
+        b.wlbm_batch_check()
+        got = [v.wlbm_get_state().cpu().numpy() for v in b.instances]
+        b.close()
+    for k, (spec, dT) in enumerate(zip(specs, dTs)):
+        want = _single(spec, dT, 20, storage, 0, 3)
+        assert np.array_equal(_state(spec, got[k]), _state(spec, want)), k
+
+
+def test_persistent_profile_counts_steps():
+    """Profiling a persistent launch times the whole launch and counts its steps."""
+    import torch
+    import paper_1911_00180_gb300 as wl
+    specs = _specs_walls()[:3]
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        b = wl.WormLBMBatch(specs, stream=stream)
+        b.wlbm_batch_set_option(wl.wlbm.OPT_PERSISTENT, 1)
+        b.wlbm_batch_init_temperature(_dTs(specs))
+        b.wlbm_batch_profile(8)
+        b.wlbm_batch_step(20)                       # one direct launch of 20 steps
+        ms, n, _ = b.wlbm_batch_profile_read()
+        assert n == 20 and ms > 0.0
+        b.wlbm_batch_set_option(wl.wlbm.OPT_GRAPH_STEPS, 12)
+        b.wlbm_batch_step(24)                       # two graph replays of 12 steps
+        ms, n, _ = b.wlbm_batch_profile_read()
+        assert n == 24 and ms > 0.0
+        b.close()
+
+
+@pytest.mark.parametrize("storage,persistent", [(0, 0), (1, 0), (0, 1), (1, 1)])
+def test_batch_c4_instances_match_oracle(storage, persistent):
     """Multigray-style batch (Sec. 2.1: many uncoupled gray problems) at the shape of the
     96-film workload: twelve recipe instances in one batch, stepped in the benchmark's
     launch configuration (own stream, TMA tiles, 48-step graph replay, event timing of every
@@ -177,6 +329,7 @@ def test_batch_c4_instances_match_oracle(storage):
         b = wl.WormLBMBatch(specs, storage=storage, stream=stream, theta=THETA)
         b.wlbm_batch_set_option(wl.wlbm.OPT_STEP_VARIANT, 3)
         b.wlbm_batch_set_option(wl.wlbm.OPT_GRAPH_STEPS, BENCH_GRAPH)
+        b.wlbm_batch_set_option(wl.wlbm.OPT_PERSISTENT, persistent)
         b.wlbm_batch_init_temperature([c["dT"] for c in insts])
         b.wlbm_batch_profile(BENCH_PROFILE)
         b.wlbm_batch_step(steps)
@@ -186,7 +339,9 @@ def test_batch_c4_instances_match_oracle(storage):
             got.append((dT.double().cpu().numpy(), v.wlbm_get_state().double().cpu().numpy()))
         stream.synchronize()
         assert b.wlbm_batch_get_option(wl.wlbm.OPT_GRAPH_REPLAYS) == 1
-        assert b.wlbm_batch_profile_read()[1] == steps // BENCH_PROFILE
+        # per-step launches time every 8th step; a persistent launch is timed whole
+        assert b.wlbm_batch_profile_read()[1] == (steps if persistent else steps // BENCH_PROFILE)
+        b.wlbm_batch_check()
         b.close()
     t_tol, s_tol = (1e-5, 1e-5) if storage == 0 else (2e-3, 2e-2)
     worst_t = worst_s = 0.0
@@ -201,4 +356,6 @@ def test_batch_c4_instances_match_oracle(storage):
             worst_t, worst_s = max(worst_t, e_t), max(worst_s, e_s)
             assert e_t <= t_tol, (c["name"], cx, e_t)
             assert e_s <= s_tol, (c["name"], cx, e_s)
-    print("batch C4 %s: T %.3g  state %.3g" % ("bf16" if storage else "fp32", worst_t, worst_s))
+    print("batch C4 %s%s: T %.3g  state %.3g" % ("bf16" if storage else "fp32",
+                                                 " persistent" if persistent else "", worst_t,
+                                                 worst_s))

@@ -132,6 +132,35 @@ def test_step_kernel_variants_bitwise_equal(storage, fuse):
     assert np.abs(out[3][sl] - out[0][sl]).max() <= tol
 
 
+@pytest.mark.parametrize("storage", [0, 1])
+@pytest.mark.parametrize("kinds", [(P,) * 4, (I, I, A, A)])
+def test_tile_loop_and_ring_depths_bitwise_equal(storage, kinds):
+    """Variant 3 with one block per tile, with resident blocks looping over the tiles, and
+    with either ring depth: the same tile code in another schedule, so the same states bit
+    for bit (grids of several tiles in both directions, a per-cell MFP field)."""
+    import paper_1911_00180_gb300 as wl
+    from tests._pair import gpu_handle
+    nx, ny, q = 301, 47, 32
+    cfg = dict(nx=nx, ny=ny, q=q, mfp=None, mfp_field=np.maximum(
+               W.lognormal_mfp(nx, ny, seed=4, corr=6.0), 1.6).astype(np.float32),
+               bc=kinds, t_wall=(300.8, 300.0, 300.0, 300.0), emulate_3d=True,
+               dT=W.random_dT(nx, ny, seed=8, scale=0.5))
+    alt = 8 if storage else 4
+    out = []
+    for loop, ring in ((0, 0), (1, 0), (1, alt), (0, alt)):
+        h = gpu_handle(cfg, storage, 3)
+        h.wlbm_set_option(wl.wlbm.OPT_RING_STAGES, ring)
+        h.wlbm_set_option(wl.wlbm.OPT_TILE_LOOP, loop)
+        h.wlbm_init_temperature(cfg["dT"])
+        h.wlbm_step(29)
+        h.wlbm_check()
+        out.append(h.wlbm_get_state().cpu().numpy())
+        h.close()
+    sl = (slice(None), slice(1, -1), slice(1, -1))
+    for k in range(1, 4):
+        assert np.array_equal(out[0][sl], out[k][sl]), k
+
+
 @pytest.mark.parametrize("storage,tol,stol", [(0, TOL32, None), (1, TOL16, TOL16_STATE)])
 @pytest.mark.parametrize("nx,ny,q", [(1, 1, 8), (1, 7, 16), (5, 1, 8), (2, 3, 24), (126, 9, 16),
                                      (127, 17, 8), (258, 41, 40)])
