@@ -92,6 +92,12 @@ def parse():
     p.add_argument("--no-extras", action="store_true",
                    help="skip e2e, cpu baseline, adjoint and clock sampling (profiling runs)")
     p.add_argument("--no-adjoint", action="store_true", help="skip the adjoint ratio")
+    p.add_argument("--max-sd", type=float, default=0.0,
+                   help="batch workload: keep only the instances with at most this many "
+                        "site-directions (a smaller batch of the same recipe, for profiling)")
+    p.add_argument("--persistent", type=int, default=None,
+                   help="batch workload: 1 persistent kernel, 0 per-step launches (default: "
+                        "the autotuner's choice)")
     p.add_argument("--no-workloads", action="store_true",
                    help="skip the other headline workloads (bf16 pulses, film, batch)")
     p.add_argument("--cpu-seconds", type=float, default=10.0,
@@ -105,11 +111,11 @@ def parse():
 # the TMA step kernel's translation unit within the package (device code and argument
 # structs), sorted by name
 STEP_KERNEL_SOURCES = ("elem.cuh", "k_step_tma.cu", "lattice.hpp", "mbar.cuh",
-                       "wlbm_internal.hpp")
+                       "step_tile.cuh", "wlbm_internal.hpp")
 
 
 def measured_traffic(workload, storage, nx, q):
-    """DRAM bytes per step-kernel launch from the committed ncu launch lists, if they were
+    """DRAM bytes per step-kernel launch from the committed ncu captures, if they were
     taken on the step kernel's sources of this tree (else None): the digest covers
     k_step_tma.cu and the headers it compiles with (STEP_KERNEL_SOURCES)."""
     import hashlib
@@ -152,8 +158,11 @@ def workload(args):
 
 def batch_config(args, n_all):
     """The `config` keys that name the batched workload (both arms print them)."""
+    sub = (", instances of at most %.3g site-directions" % args.max_sd
+           if getattr(args, "max_sd", 0) else "")
     return {"workload": "batch_c4: 96 films, thickness 16-512, aspect 8-32, Kn 0.01-100, "
-                        "Q in {16..256}, %s storage" % args.storage, "instances": n_all}
+                        "Q in {16..256}, %s storage%s" % (args.storage, sub),
+            "instances": n_all}
 
 
 def workload_config(args, cfg):
@@ -187,6 +196,8 @@ def run_batch(args):
         tdist.init_process_group("nccl")
     storage = wl.STORE_FP32_DEV if args.storage == "fp32" else wl.STORE_BF16_DEV
     insts = W.batch_c4(seed=4)
+    if args.max_sd > 0:
+        insts = [c for c in insts if c["q"] * c["nx"] * c["ny"] <= args.max_sd]
     n_all = len(insts)
     # instances are independent: each rank takes a cost-balanced share, no collective
     mine = D.shard_by_cost([c["q"] * c["nx"] * c["ny"] for c in insts], rank, world)
@@ -203,7 +214,13 @@ def run_batch(args):
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         b = wl.WormLBMBatch(specs, storage=storage, stream=stream)
-        tuned = autotune.tune_batch(b, storage, trial_steps=48)
+        if args.persistent is None:
+            tuned = autotune.tune_batch(b, storage, trial_steps=48)
+        else:
+            b.wlbm_batch_set_option(wl.wlbm.OPT_STEP_VARIANT, 3)
+            b.wlbm_batch_set_option(wl.wlbm.OPT_GRAPH_STEPS, args.graph)
+            b.wlbm_batch_set_option(wl.wlbm.OPT_PERSISTENT, args.persistent)
+            tuned = {"variant": 3, "graph_steps": args.graph, "persistent": args.persistent}
         b.wlbm_batch_init_temperature([c["dT"] for c in insts])
         b.wlbm_batch_step(args.warmup)
         stream.synchronize()
@@ -464,7 +481,8 @@ def kernel_fraction(ms_per_launch, algo_bytes):
     return achieved, achieved / peak, peak, kind
 
 
-def measure_single(wl, torch, cfg, storage, steps, warmup=48, graph=48, every=8):
+def measure_single(wl, torch, cfg, storage, steps, warmup=48, graph=48, every=8,
+                   workload_name=None):
     """One single-grid workload in the bench's launch configuration (own stream, graph
     replay of `graph`-step chunks, event timing of every `every`-th step kernel): whole-step
     updates/s over `steps` steps and the step kernel's ms per launch and HBM fraction."""
@@ -494,8 +512,11 @@ def measure_single(wl, torch, cfg, storage, steps, warmup=48, graph=48, every=8)
     per = kms / kn
     algo = bytes_per_update(storage, cfg["q"]) * cfg["q"] * cells
     ach, frac, peak, kind = kernel_fraction(per, algo)
-    return {"updates_per_s": cfg["q"] * cells * steps / (ms * 1e-3),
-            "ms_per_step": ms / steps, "kernel": "k_step_tma", "kernel_ms_per_launch": per,
+    kernel = "k_step_tma_cells" if storage == "bf16" and cfg["q"] <= 64 else "k_step_tma"
+    traffic = (measured_traffic(workload_name, storage, cfg["nx"], cfg["q"])
+               if workload_name else None)
+    return {"updates_per_s": cfg["q"] * cells * steps / (ms * 1e-3), "traffic": traffic,
+            "ms_per_step": ms / steps, "kernel": kernel, "kernel_ms_per_launch": per,
             "kernel_launches_timed": kn, "achieved_gbs": ach, "frac": frac, "peak": peak,
             "peak_kind": kind, "algorithmic_bytes_per_launch": algo,
             "bytes_per_update": bytes_per_update(storage, cfg["q"]), "steps": steps,
@@ -559,9 +580,11 @@ def other_workloads(wl, torch, args):
     import workloads as W
     out = {}
     runs = [("bf16_pulses", lambda: measure_single(wl, torch, W.pulses_c2(seed=args.seed),
-                                                   "bf16", 480)),
-            ("film_fp32", lambda: measure_single(wl, torch, W.film_c3(kn=1.0), "fp32", 480)),
-            ("film_bf16", lambda: measure_single(wl, torch, W.film_c3(kn=1.0), "bf16", 480)),
+                                                   "bf16", 480, workload_name="pulses")),
+            ("film_fp32", lambda: measure_single(wl, torch, W.film_c3(kn=1.0), "fp32", 480,
+                                                 workload_name="film")),
+            ("film_bf16", lambda: measure_single(wl, torch, W.film_c3(kn=1.0), "bf16", 480,
+                                                 workload_name="film")),
             ("batch_bf16", lambda: measure_batch(wl, torch, "bf16", 96)),
             ("batch_fp32", lambda: measure_batch(wl, torch, "fp32", 96)),
             ("batch_bf16_persistent", lambda: measure_batch(wl, torch, "bf16", 96,
@@ -599,6 +622,8 @@ def run_reference(args):
     if args.workload == "batch":
         import workloads as W
         insts = W.batch_c4(seed=4)
+        if args.max_sd > 0:
+            insts = [c for c in insts if c["q"] * c["nx"] * c["ny"] <= args.max_sd]
         cfg = dict(insts[0], relax_mode=0, mfp=max(insts[0]["mfp"], 1.5))
         config = {**batch_config(args, len(insts)), "parallelism": "instances sharded x%d"
                   % int(os.environ.get("WORLD_SIZE", "1"))}
@@ -783,8 +808,11 @@ def main():
                                                       cfg["q"]) if variant_used == 3 else None),
                          "traffic_unit": "DRAM bytes per launch (ncu, profiles/)",
                          "algorithmic_bytes_per_launch": bpu * cells * cfg["q"],
-                         "kernel": {0: "k_step", 1: "k_step_bulk", 2: "k_step_ws",
-                                    3: "k_step_tma"}[variant_used], "peak_kind": peak_kind,
+                         "kernel": ("k_step_tma_cells" if variant_used == 3 and
+                                    args.storage == "bf16" and
+                                    (h_ring == 6 or (h_ring == 0 and cfg["q"] <= 64)) else
+                                    {0: "k_step", 1: "k_step_bulk", 2: "k_step_ws",
+                                     3: "k_step_tma"}[variant_used]), "peak_kind": peak_kind,
                          "bytes_per_update": bpu,
                          "kernel_ms_per_launch": per_launch_ms,
                          "kernel_launches_timed": step_launches},

@@ -292,8 +292,10 @@ wlbm_status wlbm_adjoint_backward(wlbm_handle* h, const float* dJ_dT, const floa
  *   WLBM_OPT_GRAPH_REPLAYS read only (wlbm_get_option): how many chunks of steps this
  *                          handle has run as replays of a captured graph.
  *   WLBM_OPT_RING_STAGES   variant 3 ring depth of the tensor copies: 0 (default: by Q,
- *                          6 float32 / 16 bfloat16 for Q <= 64, else 4 / 8), or 6 or 4
- *                          (float32), 8 or 16 (bfloat16).
+ *                          6 float32 / 6 bfloat16 for Q <= 64, else 4 / 8), or 6 or 4
+ *                          (float32), 8 or 16 (bfloat16), or 6 (bfloat16: the form that
+ *                          keeps the cell terms in shared memory, four blocks per SM; the
+ *                          others keep them in registers, two blocks per SM).
  *   WLBM_OPT_TILE_LOOP     variant 3: 0 (default) one block per 128 x 14 tile; 1 a grid of
  *                          resident blocks that take the tiles in turn (no partial last
  *                          wave; bfloat16 runs three such blocks per SM where the ring

@@ -46,6 +46,18 @@ __global__ void __maxnreg__(128)
                                                   smem, g0);
 }
 
+// bfloat16 cell-tile form for single grids: the cell terms in the block-shared tile, so a
+// block needs 64 registers a thread and, with a 6-stage ring, 51 KB of shared memory:
+// four blocks per SM (28 consumer warps).
+template <int S, bool FIELD_W>
+__global__ void __launch_bounds__(32 * (kWarps3 + 1), 4)
+    k_step_tma_cells(const StepArgs a, const __grid_constant__ CUtensorMap tmap) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint32_t g0 = 0;
+  step_tma_tile<__nv_bfloat16, S, FIELD_W, true, false, true>(a, &tmap, int(blockIdx.x),
+                                                              int(blockIdx.y), smem, g0);
+}
+
 // Tile-looping form: a grid of resident blocks (three per SM for bfloat16, whose cell
 // terms sit in shared memory; two for float32) in which block b takes tiles b, b + grid,
 // ... in turn, so no partial last wave of blocks idles the GPU, and whose producer streams
@@ -165,6 +177,33 @@ constexpr int kStagesBF16 = 8;   // 8 x 4 KB
 constexpr int kStagesBF16Deep = 16;
 constexpr int kStagesF32Shallow = 4;
 constexpr int kDeepMaxQ = 64;
+// bfloat16 single grids with this ring depth run the cell-tile form (four blocks per SM)
+constexpr int kStagesBF16Cells = 6;
+
+template <int S>
+cudaError_t configure_cells_t() {
+  const int bytes = int(TmaLayout<__nv_bfloat16, S>::bytes(kMaxQ));
+  const void* fns[2] = {(const void*)k_step_tma_cells<S, false>,
+                        (const void*)k_step_tma_cells<S, true>};
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+    e = cudaFuncSetAttribute(fns[k], cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(fns[k], cudaFuncAttributePreferredSharedMemoryCarveout,
+                               int(cudaSharedmemCarveoutMaxShared));
+  }
+  return e;
+}
+
+template <int S>
+cudaError_t launch_cells_t(const StepArgs& a, const CUtensorMap& tm, cudaStream_t s) {
+  const dim3 block(32, kWarps3 + 1);
+  const dim3 grid((a.cmax - a.cbase) / kTW3 + 1, (a.rmax - a.rmin + kRows3) / kRows3);
+  const size_t bytes = TmaLayout<__nv_bfloat16, S>::bytes(a.q);
+  if (a.wfield) k_step_tma_cells<S, true><<<grid, block, bytes, s>>>(a, tm);
+  else k_step_tma_cells<S, false><<<grid, block, bytes, s>>>(a, tm);
+  return cudaGetLastError();
+}
 
 }  // namespace
 
@@ -173,6 +212,7 @@ cudaError_t configure_step_tma() {
   if (e == cudaSuccess) e = configure_tma_t<__nv_bfloat16, kStagesBF16, true>();
   if (e == cudaSuccess) e = configure_tma_t<__nv_bfloat16, kStagesBF16Deep, false>();
   if (e == cudaSuccess) e = configure_tma_t<float, kStagesF32Shallow, false>();
+  if (e == cudaSuccess) e = configure_cells_t<kStagesBF16Cells>();
   return e;
 }
 
@@ -210,16 +250,20 @@ void tma_cover(const int bc_kind[4], int nx, int ny, StepArgs* a, int* tiles_x, 
   *tiles_y = (a->rmax - a->rmin + kRows3) / kRows3;
 }
 
-// Ring depth of a single-grid step: the explicit choice, else by Q (see above).
+// Ring depth of a single-grid step: the explicit choice, else by Q (see above; bfloat16
+// with Q <= kDeepMaxQ runs the cell-tile form, measured on 2048^2 x Q64 at 0.200 ms a
+// launch against 0.202 for the 16-stage register form, and 0.058 against 0.062 ms on
+// 1024^2 x Q64; the Q128 film keeps the 8-stage register form, 0.104 against 0.105 ms).
 static int single_stages(int storage, int stages, int q) {
   if (storage == WLBM_STORE_BF16_DEV)
-    return stages ? stages : (q <= kDeepMaxQ ? kStagesBF16Deep : kStagesBF16);
+    return stages ? stages : (q <= kDeepMaxQ ? kStagesBF16Cells : kStagesBF16);
   return stages ? stages : (q <= kDeepMaxQ ? kStagesF32 : kStagesF32Shallow);
 }
 
 bool step_tma_stages_ok(int storage, int stages) {
   if (stages == 0) return true;
-  if (storage == WLBM_STORE_BF16_DEV) return stages == kStagesBF16 || stages == kStagesBF16Deep;
+  if (storage == WLBM_STORE_BF16_DEV)
+    return stages == kStagesBF16 || stages == kStagesBF16Deep || stages == kStagesBF16Cells;
   return stages == kStagesF32 || stages == kStagesF32Shallow;
 }
 
@@ -235,9 +279,12 @@ int step_tma_loop_blocks(int storage, int stages, bool field_w, int q) {
 cudaError_t launch_step_tma(int storage, const StepArgs& a, cudaStream_t s) {
   const CUtensorMap& tm = *static_cast<const CUtensorMap*>(a.tmap);
   const int st = single_stages(storage, a.ring_stages, a.q);
-  if (storage == WLBM_STORE_BF16_DEV)
+  if (storage == WLBM_STORE_BF16_DEV) {
+    if (st == kStagesBF16Cells && !a.tape && a.loop_blocks == 0)
+      return launch_cells_t<kStagesBF16Cells>(a, tm, s);
     return st == kStagesBF16Deep ? launch_tma_t<__nv_bfloat16, kStagesBF16Deep>(a, tm, s)
                                  : launch_tma_t<__nv_bfloat16, kStagesBF16>(a, tm, s);
+  }
   return st == kStagesF32 ? launch_tma_t<float, kStagesF32>(a, tm, s)
                           : launch_tma_t<float, kStagesF32Shallow>(a, tm, s);
 }
