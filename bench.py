@@ -105,6 +105,9 @@ def parse():
     p.add_argument("--adjoint-only", type=int, default=0, metavar="STEPS",
                    help="profiling aid: run only the adjoint workload for STEPS steps and print "
                         "its timings (no bench line)")
+    p.add_argument("--adjoint-ckpt", type=int, default=0,
+                   help="with --adjoint-only: checkpoint interval (0: the workload's 50; a "
+                        "smaller one keeps the tape small for profiling)")
     return p.parse_args()
 
 
@@ -431,13 +434,15 @@ def cpu_baseline(cfg, seconds=10.0, window=256):
                          seconds, sum(st for _, _, st in res))}
 
 
-def adjoint_ratio(wl, torch, stream, steps=None):
+def adjoint_ratio(wl, torch, stream, steps=None, ckpt=0):
     """Adjoint workload (1024^2, Q = 64, log-normal per-cell MFP, isothermal x walls,
     periodic y, 1000 steps, checkpoints every 50): wall time of the backward pass (segment
     recompute + reverse sweep) over that of a plain forward run of the same steps."""
     import numpy as np
     import workloads as W
     cfg = W.adjoint_c5()
+    if ckpt:
+        cfg["ckpt"] = ckpt
     n = cfg["steps"] if steps is None else steps
     h = wl.WormLBM(cfg["nx"], cfg["ny"], cfg["q"], mfp_field=cfg["mfp_field"], bc=cfg["bc"],
                    t_wall=cfg["t_wall"], emulate_3d=True, stream=stream)
@@ -669,7 +674,8 @@ def adjoint_only(args):
     import paper_1911_00180_gb300 as wl
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
-        print(json.dumps(adjoint_ratio(wl, torch, stream, steps=args.adjoint_only)), flush=True)
+        print(json.dumps(adjoint_ratio(wl, torch, stream, steps=args.adjoint_only,
+                                       ckpt=args.adjoint_ckpt)), flush=True)
     return 0
 
 

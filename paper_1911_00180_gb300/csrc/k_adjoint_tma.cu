@@ -1,11 +1,12 @@
 // Reverse step with TMA tiles (float32 storage): the transpose of one forward step, as
 // k_adj_step computes it (see k_adjoint.cu for the algebra), organised like the forward
 // step kernel k_step_tma:
-//   * one producer thread per block issues, for direction k, a 16-row tensor box of the
-//     output adjoint's plane k (rows row0-1 .. row0+14, so both l'(x + c_k) and l'(x) of
-//     every cell of the 128 x 14 tile are in it) and a 14-row box of plane k of the
-//     recorded step input d~, into one stage of a 4-stage ring (full/empty mbarriers,
-//     bounded waits);
+//   * one producer thread per block issues, for direction k, a tensor box of the output
+//     adjoint's plane k and a 14 x 128 box (no column halo) of plane k of the recorded step
+//     input d~, into one stage of a 4-stage ring (full/empty mbarriers, bounded waits).  A
+//     propagating direction reads only l'(x + c_k): its adjoint box is the tile's 14 rows
+//     shifted by c_k's row; a paused one also reads l'(x): its box is 16 rows (row0-1 ..
+//     row0+14).  So the halo rows are fetched only where they are needed;
 //   * 7 consumer warps own 2 rows each, a lane 4 consecutive cells; the shared part s' of
 //     the 4 x 6 cells around them sits in registers;
 //   * the step's directions run sorted by kind (hop, paused), as 16 loops with
@@ -31,14 +32,16 @@ constexpr int kAV = 4;                     // floats per 16 bytes
 constexpr int kABW = kATW + 2 * kAV;       // box width
 constexpr int kAC0 = kGhostCol & ~3;       // first column of the first tile
 constexpr int kAS = 4;                     // ring stages
-constexpr uint32_t kBoxL = uint32_t(kAdjTmaBoxRows) * kABW * 4;   // adjoint box bytes
-constexpr uint32_t kBoxD = uint32_t(kARows) * kABW * 4;           // tape box bytes
+constexpr uint32_t kBoxL = uint32_t(kAdjTmaBoxRows) * kABW * 4;   // adjoint box (paused)
+constexpr uint32_t kBoxL14 = uint32_t(kAdjTmaRows) * kABW * 4;    // adjoint box (propagating)
+constexpr uint32_t kBoxD = uint32_t(kARows) * kATW * 4;           // tape box bytes
 constexpr size_t kAStage = (size_t(kBoxL) + kBoxD + 127) / 128 * 128;
 constexpr size_t kAOffBar = kAS * kAStage;
 constexpr size_t kAOffKind = kAOffBar + 2 * kAS * 8;          // 17 ints
 constexpr size_t kAOffWall = kAOffKind + 17 * 4;              // 4 floats
 constexpr size_t kAOffTable = (kAOffWall + 4 * 4 + 127) / 128 * 128;
 static_assert(kAdjTmaBoxRows == kARows + 2, "one halo row above and below the tile");
+static_assert(kAdjTmaRows == kARows && kAdjTmaCols == kATW, "tile-sized boxes");
 static_assert(kBoxL % 128 == 0, "the tape box starts 128-byte aligned in its stage");
 
 struct alignas(16) AdjDir3 {
@@ -86,9 +89,11 @@ __device__ __forceinline__ void adj_body(AdjRegs& t, const AdjCtx& c) {
 #pragma unroll
   for (int k = 0; k < kARPW; ++k) {
     if (k >= c.nrw) break;
-    const int br = 1 + kARPW * c.ty + k;           // box row of cell row r + k
+    const int br = 1 + kARPW * c.ty + k;           // 16-row box: row of cell row r + k
     float b[4], av[4], dv[4], o[4];
-    row_vals<CX>(c.boxl + (br + CY) * kABW, c.lane, b);
+    // l'(x + c_k): row br + CY of a paused direction's 16-row box, row br - 1 of a
+    // propagating direction's 14-row box (which starts c_k's row below the tile)
+    row_vals<CX>(c.boxl + (PAUSED ? br + CY : br - 1) * kABW, c.lane, b);
 #pragma unroll
     for (int j = 0; j < 4; ++j) b[j] += t.sr[1 + k + CY][1 + j + CX];
     if constexpr (PAUSED) {
@@ -99,7 +104,10 @@ __device__ __forceinline__ void adj_body(AdjRegs& t, const AdjCtx& c) {
 #pragma unroll
       for (int j = 0; j < 4; ++j) av[j] = b[j];
     }
-    row_vals<0>(c.boxd + (br - 1) * kABW, c.lane, dv);
+    {
+      const float4 q = *reinterpret_cast<const float4*>(c.boxd + (br - 1) * kATW + 4 * c.lane);
+      dv[0] = q.x; dv[1] = q.y; dv[2] = q.z; dv[3] = q.w;
+    }
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       t.sigma[k][j] = fmaf(c.wk, b[j], t.sigma[k][j]);
@@ -146,6 +154,7 @@ __device__ __forceinline__ bool adj_kind(int& j, int end, AdjRegs& t, AdjCtx& c,
 
 __global__ void __maxnreg__(128)
     k_adj_tma(const AdjArgs a, const __grid_constant__ CUtensorMap lam_map,
+              const __grid_constant__ CUtensorMap lam_map14,
               const __grid_constant__ CUtensorMap tape_map, int tape_z0, const uint16_t* order,
               int* status) {
   extern __shared__ __align__(128) unsigned char smem[];
@@ -196,9 +205,14 @@ __global__ void __maxnreg__(128)
       }
       const AdjDir3 d = table[j];
       unsigned char* stage = smem + st * kAStage;
-      mbar_expect(&full[st], kBoxL + kBoxD);
-      tma_load_3d(stage, &lam_map, col0 - kAV, row0 - 1, d.k, &full[st]);
-      tma_load_3d(stage + kBoxL, &tape_map, col0 - kAV, row0, d.z_tape, &full[st]);
+      if (d.kind & 8) {   // paused: l'(x) and l'(x + c_k)
+        mbar_expect(&full[st], kBoxL + kBoxD);
+        tma_load_3d(stage, &lam_map, col0 - kAV, row0 - 1, d.k, &full[st]);
+      } else {            // propagating: l'(x + c_k) only
+        mbar_expect(&full[st], kBoxL14 + kBoxD);
+        tma_load_3d(stage, &lam_map14, col0 - kAV, row0 + c_hop_y[d.kind & 7], d.k, &full[st]);
+      }
+      tma_load_3d(stage + kBoxL, &tape_map, col0, row0, d.z_tape, &full[st]);
     }
     return;
   }
@@ -295,13 +309,14 @@ cudaError_t configure_adj_tma() {
   return e;
 }
 
-cudaError_t launch_adj_tma(const AdjArgs& a, const void* lam_map, const void* tape_map,
-                           int tape_z0, const uint16_t* order, int* status, cudaStream_t s) {
+cudaError_t launch_adj_tma(const AdjArgs& a, const void* lam_map, const void* lam_map14,
+                           const void* tape_map, int tape_z0, const uint16_t* order,
+                           int* status, cudaStream_t s) {
   const dim3 block(32, kAW + 1);
   const dim3 grid((kX0 + a.nx - kAC0) / kATW + 1, (a.ny + 2 + kARows - 1) / kARows);
   k_adj_tma<<<grid, block, adj_tma_bytes(a.q), s>>>(
-      a, *static_cast<const CUtensorMap*>(lam_map), *static_cast<const CUtensorMap*>(tape_map),
-      tape_z0, order, status);
+      a, *static_cast<const CUtensorMap*>(lam_map), *static_cast<const CUtensorMap*>(lam_map14),
+      *static_cast<const CUtensorMap*>(tape_map), tape_z0, order, status);
   return cudaGetLastError();
 }
 

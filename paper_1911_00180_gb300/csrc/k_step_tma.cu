@@ -298,7 +298,7 @@ bool make_plane_tensor_map(void* out, void* planes, int storage, const Geom& g, 
 }
 
 bool make_box_tensor_map(void* out, void* planes, int storage, const Geom& g, int nplanes,
-                         int box_rows, std::string* why) {
+                         int box_rows, std::string* why, int box_cols) {
   using Encode = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
                               const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
                               const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
@@ -319,9 +319,13 @@ bool make_box_tensor_map(void* out, void* planes, int storage, const Geom& g, in
   const bool bf = storage == WLBM_STORE_BF16_DEV;
   const cuuint64_t es = bf ? 2 : 4;
   const cuuint32_t V = cuuint32_t(16 / es);
-  const cuuint64_t dims[3] = {cuuint64_t(g.pitch), cuuint64_t(g.rows), cuuint64_t(nplanes)};
+  // columns past the right ghost column are zero pads: as out-of-bounds columns of the
+  // tensor the copy engine fills them with zeros without reading them
+  const cuuint64_t dims[3] = {cuuint64_t(kX0 + g.nx + 1), cuuint64_t(g.rows),
+                              cuuint64_t(nplanes)};
   const cuuint64_t strides[2] = {cuuint64_t(g.pitch) * es, cuuint64_t(g.plane) * es};
-  const cuuint32_t box[3] = {cuuint32_t(kTW3) + 2 * V, cuuint32_t(box_rows), 1};
+  const cuuint32_t box[3] = {box_cols > 0 ? cuuint32_t(box_cols) : cuuint32_t(kTW3) + 2 * V,
+                             cuuint32_t(box_rows), 1};
   const cuuint32_t estr[3] = {1, 1, 1};
   const CUresult r = encode(static_cast<CUtensorMap*>(out),
                             bf ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,

@@ -173,6 +173,8 @@ struct wlbm_handle {
     alignas(64) unsigned char tape_tmap[128] = {};   // CUtensorMap of the k x q tape planes
     bool has_tape_tmap = false;
     alignas(64) unsigned char lam_tmap[2][128] = {}; // CUtensorMaps of the lh planes (16 rows)
+    alignas(64) unsigned char lam14_tmap[2][128] = {};   // the same planes, 14-row boxes
+    alignas(64) unsigned char tape_adj_tmap[128] = {};   // the tape, 14 x 128 boxes
     bool has_lam_tmap = false;
     std::vector<void*> bufs;
   } adj;
@@ -1380,7 +1382,12 @@ static wlbm_status adj_alloc(wlbm_handle* h, int64_t n, int k) {
   for (int b = 0; b < 2; ++b)
     A.has_lam_tmap = A.has_lam_tmap &&
                      make_box_tensor_map(A.lam_tmap[b], A.lam[b], WLBM_STORE_FP32_DEV, g, g.q,
-                                         kAdjTmaBoxRows, &why);
+                                         kAdjTmaBoxRows, &why) &&
+                     make_box_tensor_map(A.lam14_tmap[b], A.lam[b], WLBM_STORE_FP32_DEV, g, g.q,
+                                         kAdjTmaRows, &why);
+  A.has_lam_tmap = A.has_lam_tmap &&
+                   make_box_tensor_map(A.tape_adj_tmap, A.tape, WLBM_STORE_FP32_DEV, g, k * g.q,
+                                       kAdjTmaRows, &why, kAdjTmaCols);
   // tape slots and energy planes: pads must read zero
   cudaError_t e = cudaMemsetAsync(A.tape, 0, size_t(k) * state + 1024, h->stream);
   for (int j = 0; j < 2 && e == cudaSuccess; ++j)
@@ -1558,7 +1565,7 @@ wlbm_status wlbm_adjoint_backward(wlbm_handle* h, const float* dJ_dT, const floa
       aa.dtil = A.tape + size_t(j) * state;
       aa.codes = A.codes + size_t(s0 + j) * g.q;
       if (h->step_variant == 3 && A.has_tape_tmap && A.has_lam_tmap)
-        ok(launch_adj_tma(aa, A.lam_tmap[cur], A.tape_tmap, j * g.q,
+        ok(launch_adj_tma(aa, A.lam_tmap[cur], A.lam14_tmap[cur], A.tape_adj_tmap, j * g.q,
                           A.order + size_t(s0 + j) * (g.q + 17), h->d_status, s),
            "adjoint: reverse step");
       else

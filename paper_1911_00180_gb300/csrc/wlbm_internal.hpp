@@ -387,14 +387,20 @@ bool make_plane_tensor_map(void* out, void* planes, int storage, const Geom& g, 
                            std::string* why);
 // The same with a box of box_rows rows (the 128 + 2V columns of a tile).
 bool make_box_tensor_map(void* out, void* planes, int storage, const Geom& g, int nplanes,
-                         int box_rows, std::string* why);
-// Reverse step with TMA tiles (float32): lam_map describes the q planes of a.lam_in (box
-// of kAdjTmaBoxRows rows), tape_map the adjoint tape (the forward map's box); tape_z0 is the
-// plane index of the step's slot in the tape, order the step's kind-sorted directions.
+                         int box_rows, std::string* why, int box_cols = 0);
+// Reverse step with TMA tiles (float32): lam_map describes the q planes of a.lam_in with
+// boxes of kAdjTmaBoxRows rows (paused directions read both x and x + c_k), lam_map14 the
+// same planes with boxes of kAdjTmaRows rows (propagating directions read x + c_k only),
+// tape_map the adjoint tape with boxes of kAdjTmaRows rows of the tile's kAdjTmaCols columns
+// (no column halo); tape_z0 is the plane index of the step's slot in the tape, order the
+// step's kind-sorted directions.
 constexpr int kAdjTmaBoxRows = 16;
+constexpr int kAdjTmaRows = 14;
+constexpr int kAdjTmaCols = 128;
 cudaError_t configure_adj_tma();
-cudaError_t launch_adj_tma(const AdjArgs& a, const void* lam_map, const void* tape_map,
-                           int tape_z0, const uint16_t* order, int* status, cudaStream_t s);
+cudaError_t launch_adj_tma(const AdjArgs& a, const void* lam_map, const void* lam_map14,
+                           const void* tape_map, int tape_z0, const uint16_t* order,
+                           int* status, cudaStream_t s);
 // Batched launches (one launch per step for all instances of a batch).
 int step_tile_width(int storage, int variant);
 cudaError_t launch_step_batch(int storage, int variant, const BatchInst* insts, int n,
