@@ -86,6 +86,9 @@ def parse():
     p.add_argument("--tile-loop", type=int, default=None,
                    help="1: resident blocks loop over the tiles, 0: one block per tile "
                         "(library default)")
+    p.add_argument("--wide", type=int, default=None,
+                   help="bfloat16: 1 = 256-column tiles, 0 = 128-column tiles (library "
+                        "default)")
     p.add_argument("--variant", type=int, default=None,
                    help="step kernel: 0 register-pipelined, 1 bulk-copy ring, 2 warp-specialised, "
                         "3 TMA tiles (library default where available)")
@@ -114,7 +117,7 @@ def parse():
 # the TMA step kernel's translation unit within the package (device code and argument
 # structs), sorted by name
 STEP_KERNEL_SOURCES = ("elem.cuh", "k_step_tma.cu", "lattice.hpp", "mbar.cuh",
-                       "step_tile.cuh", "wlbm_internal.hpp")
+                       "step_tile.cuh", "step_tile_wide.cuh", "wlbm_internal.hpp")
 
 
 def measured_traffic(workload, storage, nx, q):
@@ -714,6 +717,9 @@ def main():
             h.wlbm_set_option(wl.wlbm.OPT_RING_STAGES, args.ring)
         if args.tile_loop is not None:
             h.wlbm_set_option(wl.wlbm.OPT_TILE_LOOP, args.tile_loop)
+        if args.wide is not None and args.storage == "bf16":
+            h.wlbm_set_option(wl.wlbm.OPT_BF16_WIDE, args.wide)
+        h_wide = h.wlbm_get_option(wl.wlbm.OPT_BF16_WIDE)
         variant_used = h.wlbm_get_option(wl.wlbm.OPT_STEP_VARIANT)
         h_ring = h.wlbm_get_option(wl.wlbm.OPT_RING_STAGES)
         h_loop = h.wlbm_get_option(wl.wlbm.OPT_TILE_LOOP)
@@ -805,7 +811,7 @@ def main():
             "launch": {"graph_steps": args.graph,
                        "step_kernel": {0: "register-pipelined", 1: "bulk-copy ring",
                                        2: "warp-specialised", 3: "TMA tiles"}[variant_used],
-                       "ring_stages": h_ring, "tile_loop": h_loop,
+                       "ring_stages": h_ring, "tile_loop": h_loop, "bf16_wide": h_wide,
                        "l2": "state %.2f GB > L2 (no flush needed)"
                              % (2 * cfg["q"] * cells * (4 if args.storage == "fp32" else 2) / 1e9)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -814,7 +820,9 @@ def main():
                                                       cfg["q"]) if variant_used == 3 else None),
                          "traffic_unit": "DRAM bytes per launch (ncu, profiles/)",
                          "algorithmic_bytes_per_launch": bpu * cells * cfg["q"],
-                         "kernel": ("k_step_tma_cells" if variant_used == 3 and
+                         "kernel": ("k_step_tma_wide" if variant_used == 3 and h_wide and
+                                    not h_loop else
+                                    "k_step_tma_cells" if variant_used == 3 and
                                     args.storage == "bf16" and
                                     (h_ring == 6 or (h_ring == 0 and cfg["q"] <= 64)) else
                                     {0: "k_step", 1: "k_step_bulk", 2: "k_step_ws",

@@ -300,11 +300,19 @@ wlbm_status wlbm_adjoint_backward(wlbm_handle* h, const float* dJ_dT, const floa
  *                          resident blocks that take the tiles in turn (no partial last
  *                          wave; bfloat16 runs three such blocks per SM where the ring
  *                          fits).  Same results bit for bit.
+ *   WLBM_OPT_BF16_WIDE     variant 3, bfloat16 storage: 0 (default) tiles of 128 columns;
+ *                          1 tiles of 256 columns read as one box of 32-bit words (pairs of
+ *                          columns) per direction, each lane owning 8 cells of 2 rows, two
+ *                          blocks per SM (one block per tile; the tile-loop option and the
+ *                          adjoint's recompute keep the 128-column kernels).  Same results
+ *                          bit for bit as the cell-tile form.  WLBM_ERR_INVALID_ARG for
+ *                          float32 storage or where the planes have no tensor map.
  * wlbm_check: synchronises the stream and returns WLBM_ERR_TIMEOUT if a bounded wait
  * inside a kernel gave up since the last check (the status is then cleared). */
 enum { WLBM_OPT_STEP_VARIANT = 1, WLBM_OPT_GRAPH_STEPS = 2, WLBM_OPT_FUSE_PERIODIC = 3,
        WLBM_OPT_GRAPH_REPLAYS = 4, WLBM_OPT_PERSISTENT = 5, WLBM_OPT_RING_STAGES = 6,
-       WLBM_OPT_WAIT_LIMIT = 7, WLBM_OPT_STALL_TEST = 8, WLBM_OPT_TILE_LOOP = 9 };
+       WLBM_OPT_WAIT_LIMIT = 7, WLBM_OPT_STALL_TEST = 8, WLBM_OPT_TILE_LOOP = 9,
+       WLBM_OPT_BF16_WIDE = 10 };
 wlbm_status wlbm_set_option(wlbm_handle* h, int32_t key, int64_t value);
 /* wlbm_get_option: the current value of a wlbm_set_option key in *value (host). */
 wlbm_status wlbm_get_option(const wlbm_handle* h, int32_t key, int64_t* value);

@@ -30,6 +30,7 @@
 #include "elem.cuh"
 #include "mbar.cuh"
 #include "step_tile.cuh"
+#include "step_tile_wide.cuh"
 #include "wlbm_internal.hpp"
 
 namespace wlbm {
@@ -56,6 +57,17 @@ __global__ void __launch_bounds__(32 * (kWarps3 + 1), 4)
   uint32_t g0 = 0;
   step_tma_tile<__nv_bfloat16, S, FIELD_W, true, false, true>(a, &tmap, int(blockIdx.x),
                                                               int(blockIdx.y), smem, g0);
+}
+
+// bfloat16 wide-tile form for single grids: 256 x 14 tiles of the planes seen as 32-bit
+// words (one 136-word box per direction), a lane owning 8 cells of 2 rows; the cell terms in
+// the block-shared tile.  Two blocks per SM (a 6-stage ring of 7.6 KB boxes and a 51 KB
+// cell tile).
+template <int S, bool FIELD_W>
+__global__ void __launch_bounds__(32 * (kWarps3 + 1), 2)
+    k_step_tma_wide(const StepArgs a, const __grid_constant__ CUtensorMap tmap, int cbase) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  step_tma_tile_wide<S, FIELD_W>(a, &tmap, cbase, int(blockIdx.x), int(blockIdx.y), smem);
 }
 
 // Tile-looping form: a grid of resident blocks (three per SM for bfloat16, whose cell
@@ -205,6 +217,38 @@ cudaError_t launch_cells_t(const StepArgs& a, const CUtensorMap& tm, cudaStream_
   return cudaGetLastError();
 }
 
+constexpr int kStagesBF16Wide = 6;
+
+template <int S>
+cudaError_t configure_wide_t() {
+  const int bytes = int(WideLayout<S>::bytes(kMaxQ));
+  const void* fns[2] = {(const void*)k_step_tma_wide<S, false>,
+                        (const void*)k_step_tma_wide<S, true>};
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+    e = cudaFuncSetAttribute(fns[k], cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(fns[k], cudaFuncAttributePreferredSharedMemoryCarveout,
+                               int(cudaSharedmemCarveoutMaxShared));
+  }
+  return e;
+}
+
+// First column of the first wide tile: kX0, or with a computed left ghost column kX0 - 8
+// (a multiple of 8 columns, so that every box starts on a 16-byte boundary).
+int wide_cbase(const StepArgs& a) { return a.cmin < kX0 ? kX0 - 8 : kX0; }
+
+template <int S>
+cudaError_t launch_wide_t(const StepArgs& a, const CUtensorMap& tm, cudaStream_t s) {
+  const dim3 block(32, kWarps3 + 1);
+  const int cbase = wide_cbase(a);
+  const dim3 grid((a.cmax - cbase) / kWTW + 1, (a.rmax - a.rmin + kRows3) / kRows3);
+  const size_t bytes = WideLayout<S>::bytes(a.q);
+  if (a.wfield) k_step_tma_wide<S, true><<<grid, block, bytes, s>>>(a, tm, cbase);
+  else k_step_tma_wide<S, false><<<grid, block, bytes, s>>>(a, tm, cbase);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t configure_step_tma() {
@@ -213,6 +257,7 @@ cudaError_t configure_step_tma() {
   if (e == cudaSuccess) e = configure_tma_t<__nv_bfloat16, kStagesBF16Deep, false>();
   if (e == cudaSuccess) e = configure_tma_t<float, kStagesF32Shallow, false>();
   if (e == cudaSuccess) e = configure_cells_t<kStagesBF16Cells>();
+  if (e == cudaSuccess) e = configure_wide_t<kStagesBF16Wide>();
   return e;
 }
 
@@ -280,6 +325,8 @@ cudaError_t launch_step_tma(int storage, const StepArgs& a, cudaStream_t s) {
   const CUtensorMap& tm = *static_cast<const CUtensorMap*>(a.tmap);
   const int st = single_stages(storage, a.ring_stages, a.q);
   if (storage == WLBM_STORE_BF16_DEV) {
+    if (a.wide && a.tmap_w && !a.tape && a.loop_blocks == 0)
+      return launch_wide_t<kStagesBF16Wide>(a, *static_cast<const CUtensorMap*>(a.tmap_w), s);
     if (st == kStagesBF16Cells && !a.tape && a.loop_blocks == 0)
       return launch_cells_t<kStagesBF16Cells>(a, tm, s);
     return st == kStagesBF16Deep ? launch_tma_t<__nv_bfloat16, kStagesBF16Deep>(a, tm, s)
@@ -297,13 +344,13 @@ bool make_plane_tensor_map(void* out, void* planes, int storage, const Geom& g, 
   return make_box_tensor_map(out, planes, storage, g, nplanes, kRows3, why);
 }
 
-bool make_box_tensor_map(void* out, void* planes, int storage, const Geom& g, int nplanes,
-                         int box_rows, std::string* why, int box_cols) {
-  using Encode = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
-                              const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
-                              const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
-                              CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-  static Encode encode = nullptr;
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                 const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                 const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                 CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiled tensor_map_encoder(std::string* why) {
+  static EncodeTiled encode = nullptr;
   if (!encode) {
     void* fn = nullptr;
     cudaDriverEntryPointQueryResult q{};
@@ -312,10 +359,41 @@ bool make_box_tensor_map(void* out, void* planes, int storage, const Geom& g, in
         q != cudaDriverEntryPointSuccess || !fn) {
       cudaGetLastError();
       *why = "cuTensorMapEncodeTiled is not available from the driver";
-      return false;
+      return nullptr;
     }
-    encode = reinterpret_cast<Encode>(fn);
+    encode = reinterpret_cast<EncodeTiled>(fn);
   }
+  return encode;
+}
+
+// The bfloat16 planes as 32-bit words (pairs of columns): boxes of kWBoxWords words x kRows3
+// rows for the wide-tile kernel.  The tensor ends at the word holding the right ghost
+// column; when that word also holds the first pad column, the copy reads the pad from
+// memory, where it is zero (pads are never written).
+bool make_word_tensor_map(void* out, void* planes, const Geom& g, int nplanes,
+                          std::string* why) {
+  const EncodeTiled encode = tensor_map_encoder(why);
+  if (!encode) return false;
+  const cuuint64_t dims[3] = {cuuint64_t(kX0 + g.nx + 2) / 2, cuuint64_t(g.rows),
+                              cuuint64_t(nplanes)};
+  const cuuint64_t strides[2] = {cuuint64_t(g.pitch) * 2, cuuint64_t(g.plane) * 2};
+  const cuuint32_t box[3] = {cuuint32_t(kWBoxWords), cuuint32_t(kRows3), 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  const CUresult r = encode(static_cast<CUtensorMap*>(out), CU_TENSOR_MAP_DATA_TYPE_UINT32, 3,
+                            planes, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    *why = "cuTensorMapEncodeTiled failed with code " + std::to_string(int(r));
+    return false;
+  }
+  return true;
+}
+
+bool make_box_tensor_map(void* out, void* planes, int storage, const Geom& g, int nplanes,
+                         int box_rows, std::string* why, int box_cols) {
+  const EncodeTiled encode = tensor_map_encoder(why);
+  if (!encode) return false;
   const bool bf = storage == WLBM_STORE_BF16_DEV;
   const cuuint64_t es = bf ? 2 : 4;
   const cuuint32_t V = cuuint32_t(16 / es);

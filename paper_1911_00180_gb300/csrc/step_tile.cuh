@@ -697,27 +697,56 @@ __device__ __forceinline__ bool consume_bf16r(const StepArgs& a, int col0, int r
 
 // bfloat16 cell tile of the block's tile at (col0, row0), filled by the consumer threads
 // (tid < 32 kWarps3); the caller synchronises the consumer warps around it.
-template <int S, bool FIELD_W>
+// A thread's positions are idx = tid + k * (32 kWarps3); the loads of a batch of KB of them
+// are all issued before any value is used, so a tile start waits about one memory latency
+// per batch instead of one per position (KB = 0: one position at a time, a rolled loop, for
+// kernels short of registers).
+template <int COLS, int KB, typename Index>
+__device__ __forceinline__ void fill_cell_terms(const StepArgs& a, bool field_w, int col0,
+                                                int row0, int tid, float* cells, int arr,
+                                                Index index) {
+  constexpr int kN = kCellRows * (COLS + 2);          // positions of the tile and its halo
+  constexpr int kT = 32 * kWarps3;                    // consumer threads
+  constexpr int kIt = (kN + kT - 1) / kT;
+  constexpr int kB = KB > 0 ? KB : 1;                 // positions per batch
+#pragma unroll(KB > 0 ? kIt : 1)
+  for (int h = 0; h < kIt; h += kB) {
+    float ev[kB], wv[kB], rv[kB];
+#pragma unroll
+    for (int k = 0; k < kB; ++k) {
+      const int idx = tid + (h + k) * kT;
+      const int rr = idx / (COLS + 2), cc = idx - rr * (COLS + 2);
+      const int row = row0 - 1 + rr, c = col0 - 1 + cc;
+      ev[k] = wv[k] = rv[k] = 0.f;
+      if (h + k < kIt && idx < kN && row < a.rows && c >= 0 && c < a.pitch) {
+        const int64_t o = int64_t(row) * a.pitch + c;
+        ev[k] = a.e_in[o];
+        wv[k] = field_w ? a.wfield[o] : uniform_w(a, row, c);
+        rv[k] = a.e_ref[o];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < kB; ++k) {
+      const int idx = tid + (h + k) * kT;
+      if (h + k < kIt && idx < kN) {
+        const int rr = idx / (COLS + 2), cc = idx - rr * (COLS + 2);
+        const float fv = __fmul_rn(wv[k], ev[k]), gv = __fsub_rn(1.f, wv[k]);
+        const int ci = index(rr, cc);
+        cells[ci] = gv;
+        cells[arr + ci] = __fmul_rn(fmaf(gv, rv[k], fv), a.inv_scale);
+        cells[2 * arr + ci] = __fmul_rn(fv, a.inv_scale);
+      }
+    }
+  }
+}
+
+template <int S, bool FIELD_W, int KB = 5>
 __device__ __forceinline__ void fill_cells(const StepArgs& a, int col0, int row0, int tid,
                                            const TileSmem<__nv_bfloat16, S>& m) {
   using LY = TmaLayout<__nv_bfloat16, S>;
   float* cells = reinterpret_cast<float*>(m.base + LY::off_f);
-  for (int idx = tid; idx < kCellRows * (kTW3 + 2); idx += 32 * kWarps3) {
-    const int rr = idx / (kTW3 + 2), cc = idx - rr * (kTW3 + 2);
-    const int row = row0 - 1 + rr, c = col0 - 1 + cc;
-    float wv = 0.f, ev = 0.f, rv = 0.f;
-    if (row < a.rows && c >= 0 && c < a.pitch) {
-      const int64_t o = int64_t(row) * a.pitch + c;
-      ev = a.e_in[o];
-      wv = FIELD_W ? a.wfield[o] : uniform_w(a, row, c);
-      rv = a.e_ref[o];
-    }
-    const float fv = __fmul_rn(wv, ev), gv = __fsub_rn(1.f, wv);
-    const int ci = cell_index(rr, cc);
-    cells[ci] = gv;
-    cells[kCellArr + ci] = __fmul_rn(fmaf(gv, rv, fv), a.inv_scale);
-    cells[2 * kCellArr + ci] = __fmul_rn(fv, a.inv_scale);
-  }
+  fill_cell_terms<kTW3, KB>(a, FIELD_W, col0, row0, tid, cells, kCellArr,
+                        [](int rr, int cc) { return cell_index(rr, cc); });
 }
 
 // The consumer warps' barrier (barrier 1; the producer warp never takes part).
@@ -820,7 +849,8 @@ __device__ __forceinline__ bool step_tma_tile(const StepArgs& a, const void* tma
   }
   // ---------------------------------------------------------------- consumer warps
   if constexpr (REF && CELLS) {
-    fill_cells<S, FIELD_W>(a, col0, row0, tid, m);
+    // (the persistent kernel, three blocks per SM, has no registers to spare for batches)
+    fill_cells<S, FIELD_W, PERSIST ? 0 : 5>(a, col0, row0, tid, m);
     consumers_sync();
     if (ty >= nwarps) return PERSIST ? drain_tile<T, S>(a, g, lane, m) : true;
     return consume_bf16c<S>(a, col0, row0, ty, lane, g, m);
@@ -892,8 +922,6 @@ __device__ __forceinline__ void step_tma_loop(const StepArgs& a, const void* tma
     if (ty < nwarps) g += uint32_t(a.q);
   }
 }
-
-#undef WLBM_KINDS16
 
 }  // namespace
 

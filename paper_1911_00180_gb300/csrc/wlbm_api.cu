@@ -131,6 +131,9 @@ struct wlbm_handle {
   alignas(64) unsigned char tmap[128] = {};   // CUtensorMap of the planes (variant 3)
   bool has_tmap = false;
   std::string tmap_why;       // why there is no tensor map
+  alignas(64) unsigned char tmap_w[128] = {};  // bfloat16 planes as 32-bit words (wide tiles)
+  bool has_tmap_w = false;
+  int bf16_wide = 0;          // variant 3, bfloat16: 1 = 256-column tiles
   int graph_steps = 0;        // >0: replay chunks of this many steps as one CUDA graph
   int ring_stages = 0;        // variant 3 ring depth (0: by Q)
   int tile_loop = 0;          // variant 3: 1 = resident blocks loop over the tiles
@@ -565,6 +568,9 @@ wlbm_status wlbm_create(const wlbm_grid* grid, const float* mfp_cells, double mf
   if (h->planes)
     h->has_tmap = make_plane_tensor_map(h->tmap, h->planes, h->storage, g, 2 * G.q, &h->tmap_why);
   if (h->has_tmap) h->step_variant = 3;   // the fastest step kernel where it applies
+  std::string why_w;
+  if (h->has_tmap && h->bf16())
+    h->has_tmap_w = make_word_tensor_map(h->tmap_w, h->planes, g, 2 * G.q, &why_w);
   if (h->field_w) h->wfield = static_cast<float*>(h->dev_alloc(size_t(g.plane) * 4));
   if (!h->planes || !h->e[0] || !h->e[1] || (n_e == 3 && !h->e[2]) || !h->consts ||
       !h->d_codes || !h->d_order || !h->d_red || !h->d_red_part || !h->d_snap || !h->d_status ||
@@ -720,6 +726,8 @@ static wlbm_status enqueue_steps(wlbm_handle* h, int count, int every,
     sa.tmap = h->has_tmap ? h->tmap : nullptr;
     sa.ring_stages = h->ring_stages;
     sa.loop_blocks = h->tile_loop ? h->loop_blocks : 0;
+    sa.wide = h->bf16_wide;
+    sa.tmap_w = h->has_tmap_w ? h->tmap_w : nullptr;
     sa.order = h->d_order + size_t(t) * (g.q + 17);
     int tx_unused = 0, ty_unused = 0;
     tma_cover(h->bc_kind, g.nx, g.ny, &sa, &tx_unused, &ty_unused);
@@ -851,6 +859,7 @@ wlbm_status wlbm_get_option(const wlbm_handle* h, int32_t key, int64_t* value) {
   else if (key == WLBM_OPT_GRAPH_REPLAYS) *value = h->graph_replays;
   else if (key == WLBM_OPT_RING_STAGES) *value = h->ring_stages;
   else if (key == WLBM_OPT_TILE_LOOP) *value = h->tile_loop;
+  else if (key == WLBM_OPT_BF16_WIDE) *value = h->bf16_wide;
   else return WLBM_ERR_INVALID_ARG;
   return WLBM_OK;
 }
@@ -889,6 +898,14 @@ wlbm_status wlbm_set_option(wlbm_handle* h, int32_t key, int64_t value) {
     h->ring_stages = stages;
     h->tile_loop = loop;
     h->loop_blocks = blocks;
+    h->drop_graphs();
+    return WLBM_OK;
+  }
+  if (key == WLBM_OPT_BF16_WIDE && (value == 0 || value == 1)) {
+    if (value == 1 && !h->has_tmap_w)
+      return h->fail(WLBM_ERR_INVALID_ARG, "wlbm_set_option: wide tiles need bfloat16 storage "
+                                           "and a tensor map of the planes");
+    h->bf16_wide = int(value);
     h->drop_graphs();
     return WLBM_OK;
   }

@@ -84,6 +84,10 @@ struct StepArgs {
   // wave of blocks); 0: one block per tile
   int ring_stages;
   int loop_blocks;
+  // bfloat16 single grids: 1 = the wide-tile kernel (256-column tiles) through tmap_w, the
+  // host pointer to the planes' 32-bit-word tensor map
+  int wide;
+  const void* tmap_w;
 };
 
 // Stable sort of one step's directions by kind = hop | paused << 3 (16 kinds): writes the
@@ -388,6 +392,9 @@ bool make_plane_tensor_map(void* out, void* planes, int storage, const Geom& g, 
 // The same with a box of box_rows rows (the 128 + 2V columns of a tile).
 bool make_box_tensor_map(void* out, void* planes, int storage, const Geom& g, int nplanes,
                          int box_rows, std::string* why, int box_cols = 0);
+// bfloat16 planes as 32-bit words with the wide-tile kernel's box (136 words x 14 rows).
+bool make_word_tensor_map(void* out, void* planes, const Geom& g, int nplanes,
+                          std::string* why);
 // Reverse step with TMA tiles (float32): lam_map describes the q planes of a.lam_in with
 // boxes of kAdjTmaBoxRows rows (paused directions read both x and x + c_k), lam_map14 the
 // same planes with boxes of kAdjTmaRows rows (propagating directions read x + c_k only),

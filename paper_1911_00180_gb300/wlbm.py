@@ -19,6 +19,7 @@ STORE_FP32_DEV, STORE_BF16_DEV = 0, 1
 OPT_STEP_VARIANT, OPT_GRAPH_STEPS, OPT_FUSE_PERIODIC, OPT_GRAPH_REPLAYS = 1, 2, 3, 4
 OPT_PERSISTENT, OPT_RING_STAGES, OPT_WAIT_LIMIT, OPT_STALL_TEST = 5, 6, 7, 8
 OPT_TILE_LOOP = 9
+OPT_BF16_WIDE = 10
 REDUCE_N = 9          # WLBM_REDUCE_N
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "UNSTABLE", 3: "OOM", 4: "CUDA", 5: "TIMEOUT",
                 6: "STATE"}

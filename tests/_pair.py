@@ -34,7 +34,7 @@ def oracle_run(cfg, steps, state=None, flux_peak=False):
     return m
 
 
-def gpu_handle(cfg, storage=0, variant=None):
+def gpu_handle(cfg, storage=0, variant=None, options=None):
     import paper_1911_00180_gb300 as wl
     mfp = cfg.get("mfp")
     if mfp is None:
@@ -47,12 +47,14 @@ def gpu_handle(cfg, storage=0, variant=None):
                    speed=cfg.get("speed", 1.0))
     if variant is not None:
         h.wlbm_set_option(wl.wlbm.OPT_STEP_VARIANT, variant)
+    for key, value in (options or {}).items():
+        h.wlbm_set_option(key, value)
     return h
 
 
-def gpu_run(cfg, steps, storage=0, state=None, variant=None):
+def gpu_run(cfg, steps, storage=0, state=None, variant=None, options=None):
     import torch
-    h = gpu_handle(cfg, storage, variant)
+    h = gpu_handle(cfg, storage, variant, options)
     if state is None:
         h.wlbm_init_temperature(cfg["dT"])
     else:

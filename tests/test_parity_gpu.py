@@ -48,9 +48,9 @@ TOL16_Q = 2e-3
 TOL16_STATE_WALL = 2e-2
 
 
-def _compare(cfg, steps, storage=0, tol=TOL32, state_tol=None, variant=None):
+def _compare(cfg, steps, storage=0, tol=TOL32, state_tol=None, variant=None, options=None):
     orc = oracle_run(cfg, steps, flux_peak=storage == 1)
-    gpu = gpu_run(cfg, steps, storage, variant=variant)
+    gpu = gpu_run(cfg, steps, storage, variant=variant, options=options)
     amp = max(float(np.abs(cfg["dT"]).max()),
               max(abs(t - 300.0) for k, t in zip(cfg["bc"], cfg["t_wall"]) if k == I)
               if I in cfg["bc"] else 0.0)
@@ -148,11 +148,15 @@ def test_tile_loop_and_ring_depths_bitwise_equal(storage, kinds):
                dT=W.random_dT(nx, ny, seed=8, scale=0.5))
     alt = 8 if storage else 4
     out = []
-    runs = [(0, 0), (1, 0), (1, alt), (0, alt)] + ([(0, 6)] if storage else [])
-    for loop, ring in runs:
+    runs = [(0, 0, 0), (1, 0, 0), (1, alt, 0), (0, alt, 0)]
+    if storage:
+        runs += [(0, 6, 0), (0, 0, 1)]   # cell-tile form; 256-column tiles
+    for loop, ring, wide in runs:
         h = gpu_handle(cfg, storage, 3)
         h.wlbm_set_option(wl.wlbm.OPT_RING_STAGES, ring)
         h.wlbm_set_option(wl.wlbm.OPT_TILE_LOOP, loop)
+        if wide:
+            h.wlbm_set_option(wl.wlbm.OPT_BF16_WIDE, 1)
         h.wlbm_init_temperature(cfg["dT"])
         h.wlbm_step(29)
         h.wlbm_check()
@@ -177,6 +181,37 @@ def test_tma_variant_edges_and_field(storage, tol, stol, nx, ny, q):
                t_wall=(300.6, 300.0, 300.0, 300.0), emulate_3d=True,
                dT=W.random_dT(nx, ny, seed=nx * ny + q, scale=0.5))
     _compare(cfg, 40, storage=storage, tol=tol, state_tol=stol, variant=3)
+
+
+@pytest.mark.parametrize("nx,ny,q,bc", [(1, 1, 8, (I, A, P, P)), (7, 3, 16, (A, A, A, A)),
+                                        (256, 15, 24, (P, P, I, I)), (257, 14, 16, (P, P, A, A)),
+                                        (247, 29, 8, (A, A, P, P)), (248, 9, 40, (A, A, I, I)),
+                                        (600, 31, 64, (P, P, P, P)), (520, 43, 32, (A, I, I, A))])
+def test_wide_tiles_edges_and_field(nx, ny, q, bc):
+    """bfloat16 256-column tiles: widths around one and two tiles (256 interior columns fill
+    one tile, 257 spill one into a second; with diffuse walls on both sides the first tile
+    starts 8 columns left of the interior and covers the ghost columns of 247, while 248
+    spill the right ghost), rows around the 14-row tile, every wall kind, a per-cell MFP
+    field; against the oracle."""
+    import paper_1911_00180_gb300 as wl
+    mfp = (np.full((1, 1), 6.0, np.float32) if nx * ny == 1 else
+           np.maximum(W.lognormal_mfp(nx, ny, seed=nx + ny, corr=3.0), 1.6).astype(np.float32))
+    cfg = dict(nx=nx, ny=ny, q=q, mfp=None, mfp_field=mfp, bc=bc,
+               t_wall=(300.6, 300.0, 300.3, 300.0), emulate_3d=True,
+               dT=W.random_dT(nx, ny, seed=nx * ny + q, scale=0.5))
+    _compare(cfg, 40, storage=1, tol=TOL16, state_tol=TOL16_STATE, variant=3,
+             options={wl.wlbm.OPT_BF16_WIDE: 1})
+
+
+def test_wide_tiles_refused_for_float32():
+    import paper_1911_00180_gb300 as wl
+    from tests._pair import gpu_handle
+    cfg = W.gaussian_c1(seed=1)
+    h = gpu_handle(cfg, 0, 3)
+    with pytest.raises(Exception):
+        h.wlbm_set_option(wl.wlbm.OPT_BF16_WIDE, 1)
+    assert h.wlbm_get_option(wl.wlbm.OPT_BF16_WIDE) == 0
+    h.close()
 
 
 def test_init_roundtrip_temperature():
