@@ -501,6 +501,7 @@ def measure_single(wl, torch, cfg, storage, steps, warmup=48, graph=48, every=8,
                        t_wall=cfg["t_wall"], storage=st, emulate_3d=cfg["emulate_3d"],
                        relax_mode=cfg["relax_mode"], stream=stream)
         h.wlbm_set_option(wl.wlbm.OPT_GRAPH_STEPS, graph)
+        wide = h.wlbm_get_option(wl.wlbm.OPT_BF16_WIDE)
         h.wlbm_init_temperature(torch.as_tensor(cfg["dT"]).to("cuda"))
         h.wlbm_step(warmup)
         stream.synchronize()
@@ -520,7 +521,8 @@ def measure_single(wl, torch, cfg, storage, steps, warmup=48, graph=48, every=8,
     per = kms / kn
     algo = bytes_per_update(storage, cfg["q"]) * cfg["q"] * cells
     ach, frac, peak, kind = kernel_fraction(per, algo)
-    kernel = "k_step_tma_cells" if storage == "bf16" and cfg["q"] <= 64 else "k_step_tma"
+    kernel = ("k_step_tma_wide" if wide else
+              "k_step_tma_cells" if storage == "bf16" and cfg["q"] <= 64 else "k_step_tma")
     traffic = (measured_traffic(workload_name, storage, cfg["nx"], cfg["q"])
                if workload_name else None)
     return {"updates_per_s": cfg["q"] * cells * steps / (ms * 1e-3), "traffic": traffic,
@@ -820,8 +822,8 @@ def main():
                                                       cfg["q"]) if variant_used == 3 else None),
                          "traffic_unit": "DRAM bytes per launch (ncu, profiles/)",
                          "algorithmic_bytes_per_launch": bpu * cells * cfg["q"],
-                         "kernel": ("k_step_tma_wide" if variant_used == 3 and h_wide and
-                                    not h_loop else
+                         "kernel": ("k_step_tma_loop" if variant_used == 3 and h_loop else
+                                    "k_step_tma_wide" if variant_used == 3 and h_wide else
                                     "k_step_tma_cells" if variant_used == 3 and
                                     args.storage == "bf16" and
                                     (h_ring == 6 or (h_ring == 0 and cfg["q"] <= 64)) else

@@ -295,17 +295,20 @@ wlbm_status wlbm_adjoint_backward(wlbm_handle* h, const float* dJ_dT, const floa
  *                          6 float32 / 6 bfloat16 for Q <= 64, else 4 / 8), or 6 or 4
  *                          (float32), 8 or 16 (bfloat16), or 6 (bfloat16: the form that
  *                          keeps the cell terms in shared memory, four blocks per SM; the
- *                          others keep them in registers, two blocks per SM).
+ *                          others keep them in registers, two blocks per SM).  bfloat16
+ *                          single grids take these 128-column forms with
+ *                          WLBM_OPT_BF16_WIDE = 0 or the tile loop; batches always.
  *   WLBM_OPT_TILE_LOOP     variant 3: 0 (default) one block per 128 x 14 tile; 1 a grid of
  *                          resident blocks that take the tiles in turn (no partial last
  *                          wave; bfloat16 runs three such blocks per SM where the ring
  *                          fits).  Same results bit for bit.
- *   WLBM_OPT_BF16_WIDE     variant 3, bfloat16 storage: 0 (default) tiles of 128 columns;
- *                          1 tiles of 256 columns read as one box of 32-bit words (pairs of
- *                          columns) per direction, each lane owning 8 cells of 2 rows, two
- *                          blocks per SM (one block per tile; the tile-loop option and the
- *                          adjoint's recompute keep the 128-column kernels).  Same results
- *                          bit for bit as the cell-tile form.  WLBM_ERR_INVALID_ARG for
+ *   WLBM_OPT_BF16_WIDE     variant 3, bfloat16 storage: 1 (default) tiles of 256 columns
+ *                          read as one box of 32-bit words (pairs of columns) per direction,
+ *                          two consumer warps per row pair, two blocks of 15 warps per SM
+ *                          (one block per tile; the tile-loop option and the adjoint's
+ *                          recompute keep the 128-column kernels); 0 tiles of 128 columns
+ *                          (the forms WLBM_OPT_RING_STAGES selects).  Same results bit for
+ *                          bit either way.  Setting 1 returns WLBM_ERR_INVALID_ARG for
  *                          float32 storage or where the planes have no tensor map.
  * wlbm_check: synchronises the stream and returns WLBM_ERR_TIMEOUT if a bounded wait
  * inside a kernel gave up since the last check (the status is then cleared). */

@@ -60,11 +60,11 @@ __global__ void __launch_bounds__(32 * (kWarps3 + 1), 4)
 }
 
 // bfloat16 wide-tile form for single grids: 256 x 14 tiles of the planes seen as 32-bit
-// words (one 136-word box per direction), a lane owning 8 cells of 2 rows; the cell terms in
-// the block-shared tile.  Two blocks per SM (a 6-stage ring of 7.6 KB boxes and a 51 KB
-// cell tile).
+// words (one 136-word box per direction), two consumer warps per row pair, the cell terms in
+// the block-shared tile.  Two blocks of 15 warps per SM (a 6-stage ring of 7.6 KB boxes
+// and a 50 KB cell tile each).
 template <int S, bool FIELD_W>
-__global__ void __launch_bounds__(32 * (kWarps3 + 1), 2)
+__global__ void __launch_bounds__(kWThreads, 2)
     k_step_tma_wide(const StepArgs a, const __grid_constant__ CUtensorMap tmap, int cbase) {
   extern __shared__ __align__(128) unsigned char smem[];
   step_tma_tile_wide<S, FIELD_W>(a, &tmap, cbase, int(blockIdx.x), int(blockIdx.y), smem);
@@ -217,7 +217,10 @@ cudaError_t launch_cells_t(const StepArgs& a, const CUtensorMap& tm, cudaStream_
   return cudaGetLastError();
 }
 
-constexpr int kStagesBF16Wide = 6;
+// Wide-tile ring depth by Q, from a sweep of 5, 6 and 7 stages: 2048^2 x Q64 0.1918 / 0.1901
+// / 0.1890 ms a launch, the 4096 x 256 x Q128 film 0.0990 / 0.1012 / 0.1020 ms.
+constexpr int kStagesBF16Wide = 7;        // Q <= kDeepMaxQ
+constexpr int kStagesBF16WideHighQ = 5;
 
 template <int S>
 cudaError_t configure_wide_t() {
@@ -240,7 +243,7 @@ int wide_cbase(const StepArgs& a) { return a.cmin < kX0 ? kX0 - 8 : kX0; }
 
 template <int S>
 cudaError_t launch_wide_t(const StepArgs& a, const CUtensorMap& tm, cudaStream_t s) {
-  const dim3 block(32, kWarps3 + 1);
+  const dim3 block(32, kWWarps + 1);
   const int cbase = wide_cbase(a);
   const dim3 grid((a.cmax - cbase) / kWTW + 1, (a.rmax - a.rmin + kRows3) / kRows3);
   const size_t bytes = WideLayout<S>::bytes(a.q);
@@ -258,6 +261,7 @@ cudaError_t configure_step_tma() {
   if (e == cudaSuccess) e = configure_tma_t<float, kStagesF32Shallow, false>();
   if (e == cudaSuccess) e = configure_cells_t<kStagesBF16Cells>();
   if (e == cudaSuccess) e = configure_wide_t<kStagesBF16Wide>();
+  if (e == cudaSuccess) e = configure_wide_t<kStagesBF16WideHighQ>();
   return e;
 }
 
@@ -325,8 +329,11 @@ cudaError_t launch_step_tma(int storage, const StepArgs& a, cudaStream_t s) {
   const CUtensorMap& tm = *static_cast<const CUtensorMap*>(a.tmap);
   const int st = single_stages(storage, a.ring_stages, a.q);
   if (storage == WLBM_STORE_BF16_DEV) {
-    if (a.wide && a.tmap_w && !a.tape && a.loop_blocks == 0)
-      return launch_wide_t<kStagesBF16Wide>(a, *static_cast<const CUtensorMap*>(a.tmap_w), s);
+    if (a.wide && a.tmap_w && !a.tape && a.loop_blocks == 0) {
+      const CUtensorMap& tw = *static_cast<const CUtensorMap*>(a.tmap_w);
+      return a.q <= kDeepMaxQ ? launch_wide_t<kStagesBF16Wide>(a, tw, s)
+                              : launch_wide_t<kStagesBF16WideHighQ>(a, tw, s);
+    }
     if (st == kStagesBF16Cells && !a.tape && a.loop_blocks == 0)
       return launch_cells_t<kStagesBF16Cells>(a, tm, s);
     return st == kStagesBF16Deep ? launch_tma_t<__nv_bfloat16, kStagesBF16Deep>(a, tm, s)

@@ -36,15 +36,18 @@ static_assert(sizeof(Dir3) == 16, "one 16-byte shared-memory load per direction"
 constexpr int kCellRows = kRows3 + 2;
 constexpr int kCellG = kTW3 / 4 + 2;                 // groups -1 .. kTW3 / 4
 constexpr int kCellArr = 4 * kCellRows * kCellG;     // floats per array
+// (CG: groups per row of the tile, kCellG for 128-column tiles.)
+template <int CG = kCellG>
 __device__ __forceinline__ int cell_index(int rr, int cc) {
-  const int x = cc - 1;                              // column - col0, -1 .. kTW3
-  return ((x & 3) * kCellRows + rr) * kCellG + (x >> 2) + 1;
+  const int x = cc - 1;                              // column - col0, -1 .. tile width
+  return ((x & 3) * kCellRows + rr) * CG + (x >> 2) + 1;
 }
-// Offset from a lane's base (cells + 2 ty * kCellG + lane + 1) of its register-tile
-// position (lr, lc): row r - 1 + lr, column c0 - 1 + lc of the warp's first row r and the
-// lane's first cell c0 = col0 + 4 lane.
+// Offset from a lane's base (cells + 2 ty * CG + g + 1, g = the lane's group) of its
+// register-tile position (lr, lc): row r - 1 + lr, column c0 - 1 + lc of the warp's first
+// row r and the lane's first cell c0 = col0 + 4 g.
+template <int CG = kCellG>
 __host__ __device__ constexpr int cell_off(int lr, int lc) {
-  return (((lc + 3) & 3) * kCellRows + lr) * kCellG + (lc == 0 ? -1 : (lc - 1) / 4);
+  return (((lc + 3) & 3) * kCellRows + lr) * CG + (lc == 0 ? -1 : (lc - 1) / 4);
 }
 
 template <typename T, int S>
@@ -271,11 +274,11 @@ __device__ __forceinline__ void ring_pairs(const __nv_bfloat16* row, int lane, f
   }
 }
 
-template <int CX, bool PAUSED, bool FULL, typename R>
+// BW: ring row length (elements).
+template <int CX, bool PAUSED, bool FULL, typename R, int BW = kTW3 + 16>
 __device__ __forceinline__ void dir_body_ref(R& t, const DirCtx<__nv_bfloat16>& c,
                                              const float2 (&Gk)[kRPW][2],
                                              const float2 (&Dk)[kRPW][2]) {
-  constexpr int BW = kTW3 + 2 * (16 / int(sizeof(__nv_bfloat16)));   // ring row length
   constexpr int DX = PAUSED ? 0 : -CX;
   const float2 wi2 = make_float2(c.wi, c.wi);
 #pragma unroll
@@ -381,19 +384,22 @@ __device__ __forceinline__ bool run_kind_bf16r(int& j, int end, RegsR& t,
   return true;
 }
 
-template <int S, int CX, int CY, bool PAUSED, bool FULL>
+// The cell-tile form (CG groups per tile row, ring rows of BW elements, stages STAGE bytes
+// apart; ring_off: the warp's first ring element in a stage).
+template <int S, int CX, int CY, bool PAUSED, bool FULL, int CG = kCellG, int BW = kTW3 + 16,
+          size_t STAGE = TmaLayout<__nv_bfloat16, S>::kStage>
 __device__ __forceinline__ bool run_kind_bf16(int& j, int end, RegsB& t,
                                               DirCtx<__nv_bfloat16>& c, float& accw,
                                               const Dir3* table, const unsigned char* smem,
                                               uint64_t* full, uint64_t* empty,
-                                              __nv_bfloat16* obase, int ty, int* status) {
-  using LY = TmaLayout<__nv_bfloat16, S>;
+                                              __nv_bfloat16* obase, int ring_off, int* status) {
   if (j >= end) return true;
   float2 Gk[kRPW][2], Dk[kRPW][2];
   {
     const float* G = c.cells;
-    const float* X = c.cells + kCellArr;
-    const float* F = c.cells + 2 * kCellArr;
+    constexpr int kArr = 4 * kCellRows * CG;            // floats per array of the tile
+    const float* X = c.cells + kArr;
+    const float* F = c.cells + 2 * kArr;
     constexpr int SC = PAUSED ? 1 : 1 - CX;
     constexpr int FC = 1 - CX;
 #pragma unroll
@@ -403,11 +409,11 @@ __device__ __forceinline__ bool run_kind_bf16(int& j, int end, RegsB& t,
       float g[4], d[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        g[q] = G[cell_off(SR, SC + q)];
+        g[q] = G[cell_off<CG>(SR, SC + q)];
         const float tt =
-            PAUSED ? __fadd_rn(__fsub_rn(X[cell_off(1 + k, 1 + q)], F[cell_off(1 + k, 1 + q)]),
-                               F[cell_off(FR, FC + q)])
-                   : X[cell_off(SR, SC + q)];
+            PAUSED ? __fadd_rn(__fsub_rn(X[cell_off<CG>(1 + k, 1 + q)], F[cell_off<CG>(1 + k, 1 + q)]),
+                               F[cell_off<CG>(FR, FC + q)])
+                   : X[cell_off<CG>(SR, SC + q)];
         d[q] = __fsub_rn(tt, t.eins[k][q]);
       }
       Gk[k][0] = make_float2(g[0], g[1]);
@@ -424,12 +430,11 @@ __device__ __forceinline__ bool run_kind_bf16(int& j, int end, RegsB& t,
       return false;
     }
     const Dir3 d = table[j];
-    c.ring_row =
-        reinterpret_cast<const __nv_bfloat16*>(smem + st * LY::kStage) + kRPW * ty * LY::BW;
+    c.ring_row = reinterpret_cast<const __nv_bfloat16*>(smem + st * STAGE) + ring_off;
     c.dst = obase + d.dst;
     c.wi = d.wi;
     accw += d.wi;
-    if (FULL || c.vm) dir_body_ref<CX, PAUSED, FULL>(t, c, Gk, Dk);
+    if (FULL || c.vm) dir_body_ref<CX, PAUSED, FULL, RegsB, BW>(t, c, Gk, Dk);
     __syncwarp();
     mbar_arrive_if(&empty[st], c.lane == 0);
   }
@@ -701,12 +706,12 @@ __device__ __forceinline__ bool consume_bf16r(const StepArgs& a, int col0, int r
 // are all issued before any value is used, so a tile start waits about one memory latency
 // per batch instead of one per position (KB = 0: one position at a time, a rolled loop, for
 // kernels short of registers).
-template <int COLS, int KB, typename Index>
+template <int COLS, int KB, typename Index, int NT = 32 * kWarps3>
 __device__ __forceinline__ void fill_cell_terms(const StepArgs& a, bool field_w, int col0,
                                                 int row0, int tid, float* cells, int arr,
                                                 Index index) {
   constexpr int kN = kCellRows * (COLS + 2);          // positions of the tile and its halo
-  constexpr int kT = 32 * kWarps3;                    // consumer threads
+  constexpr int kT = NT;                              // consumer threads
   constexpr int kIt = (kN + kT - 1) / kT;
   constexpr int kB = KB > 0 ? KB : 1;                 // positions per batch
 #pragma unroll(KB > 0 ? kIt : 1)
@@ -788,9 +793,11 @@ __device__ __forceinline__ bool consume_bf16c(const StepArgs& a, int col0, int r
       static_cast<__nv_bfloat16*>(a.tape ? a.tape_dst : a.planes) + int64_t(r) * a.pitch + c0;
   int j = 0;
   bool ok = true;
+  const int ring_off = kRPW * ty * LY::BW;
 #define WLBM_KIND(K, CX, CY, P, F)                                                          \
   ok = ok && run_kind_bf16<S, CX, CY, P, F>(j, m.kind_start[K + 1], t, ctx, accw, m.table, \
-                                            m.base, m.full, m.empty, obase, ty, a.status)
+                                            m.base, m.full, m.empty, obase, ring_off,      \
+                                            a.status)
   if (nrw == kRPW && __all_sync(0xffffffffu, vm == 0xFu)) {
     WLBM_KINDS16(WLBM_KIND, true);
   } else {

@@ -133,7 +133,8 @@ struct wlbm_handle {
   std::string tmap_why;       // why there is no tensor map
   alignas(64) unsigned char tmap_w[128] = {};  // bfloat16 planes as 32-bit words (wide tiles)
   bool has_tmap_w = false;
-  int bf16_wide = 0;          // variant 3, bfloat16: 1 = 256-column tiles
+  int bf16_wide = 0;          // variant 3, bfloat16: 1 = 256-column tiles (the default
+                              // where the planes have a 32-bit-word tensor map)
   int graph_steps = 0;        // >0: replay chunks of this many steps as one CUDA graph
   int ring_stages = 0;        // variant 3 ring depth (0: by Q)
   int tile_loop = 0;          // variant 3: 1 = resident blocks loop over the tiles
@@ -571,6 +572,7 @@ wlbm_status wlbm_create(const wlbm_grid* grid, const float* mfp_cells, double mf
   std::string why_w;
   if (h->has_tmap && h->bf16())
     h->has_tmap_w = make_word_tensor_map(h->tmap_w, h->planes, g, 2 * G.q, &why_w);
+  h->bf16_wide = h->has_tmap_w ? 1 : 0;
   if (h->field_w) h->wfield = static_cast<float*>(h->dev_alloc(size_t(g.plane) * 4));
   if (!h->planes || !h->e[0] || !h->e[1] || (n_e == 3 && !h->e[2]) || !h->consts ||
       !h->d_codes || !h->d_order || !h->d_red || !h->d_red_part || !h->d_snap || !h->d_status ||

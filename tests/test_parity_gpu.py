@@ -155,8 +155,8 @@ def test_tile_loop_and_ring_depths_bitwise_equal(storage, kinds):
         h = gpu_handle(cfg, storage, 3)
         h.wlbm_set_option(wl.wlbm.OPT_RING_STAGES, ring)
         h.wlbm_set_option(wl.wlbm.OPT_TILE_LOOP, loop)
-        if wide:
-            h.wlbm_set_option(wl.wlbm.OPT_BF16_WIDE, 1)
+        if storage:
+            h.wlbm_set_option(wl.wlbm.OPT_BF16_WIDE, wide)
         h.wlbm_init_temperature(cfg["dT"])
         h.wlbm_step(29)
         h.wlbm_check()
