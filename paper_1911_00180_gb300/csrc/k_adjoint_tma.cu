@@ -5,8 +5,9 @@
 //     adjoint's plane k and a 14 x 128 box (no column halo) of plane k of the recorded step
 //     input d~, into one stage of a 4-stage ring (full/empty mbarriers, bounded waits).  A
 //     propagating direction reads only l'(x + c_k): its adjoint box is the tile's 14 rows
-//     shifted by c_k's row; a paused one also reads l'(x): its box is 16 rows (row0-1 ..
-//     row0+14).  So the halo rows are fetched only where they are needed;
+//     shifted by c_k's row; a paused one also reads l'(x): its box is the tile's 14 rows
+//     and, for a hop with a vertical component, the one row beyond them on c_k's side (15
+//     rows).  So the halo rows are fetched only where they are needed;
 //   * 7 consumer warps own 2 rows each, a lane 4 consecutive cells; the shared part s' of
 //     the 4 x 6 cells around them sits in registers;
 //   * the step's directions run sorted by kind (hop, paused), as 16 loops with
@@ -33,16 +34,16 @@ constexpr int kABW = kATW + 2 * kAV;       // box width
 constexpr int kAC0 = kGhostCol & ~3;       // first column of the first tile
 constexpr int kAS = 4;                     // ring stages
 constexpr uint32_t kBoxL = uint32_t(kAdjTmaBoxRows) * kABW * 4;   // adjoint box (paused)
-constexpr uint32_t kBoxL14 = uint32_t(kAdjTmaRows) * kABW * 4;    // adjoint box (propagating)
+constexpr uint32_t kBoxL14 = uint32_t(kAdjTmaRows) * kABW * 4;    // adjoint box (14 rows)
+constexpr uint32_t kBoxLSlot = (kBoxL + 127) / 128 * 128;         // tape box offset
 constexpr uint32_t kBoxD = uint32_t(kARows) * kATW * 4;           // tape box bytes
-constexpr size_t kAStage = (size_t(kBoxL) + kBoxD + 127) / 128 * 128;
+constexpr size_t kAStage = (size_t(kBoxLSlot) + kBoxD + 127) / 128 * 128;
 constexpr size_t kAOffBar = kAS * kAStage;
 constexpr size_t kAOffKind = kAOffBar + 2 * kAS * 8;          // 17 ints
 constexpr size_t kAOffWall = kAOffKind + 17 * 4;              // 4 floats
 constexpr size_t kAOffTable = (kAOffWall + 4 * 4 + 127) / 128 * 128;
-static_assert(kAdjTmaBoxRows == kARows + 2, "one halo row above and below the tile");
+static_assert(kAdjTmaBoxRows == kARows + 1, "one halo row on the side of c_k");
 static_assert(kAdjTmaRows == kARows && kAdjTmaCols == kATW, "tile-sized boxes");
-static_assert(kBoxL % 128 == 0, "the tape box starts 128-byte aligned in its stage");
 
 struct alignas(16) AdjDir3 {
   int32_t k;        // direction index
@@ -87,17 +88,21 @@ struct AdjCtx {
 template <int CX, int CY, bool PAUSED>
 __device__ __forceinline__ void adj_body(AdjRegs& t, const AdjCtx& c) {
 #pragma unroll
+  // a paused direction's box starts at tile row OFF (one row above the tile for a hop
+  // downwards), a propagating direction's at c_k's row
+  constexpr int OFF = CY < 0 ? -1 : 0;
+#pragma unroll
   for (int k = 0; k < kARPW; ++k) {
     if (k >= c.nrw) break;
-    const int br = 1 + kARPW * c.ty + k;           // 16-row box: row of cell row r + k
+    const int tr = kARPW * c.ty + k;               // tile row of cell row r + k
     float b[4], av[4], dv[4], o[4];
-    // l'(x + c_k): row br + CY of a paused direction's 16-row box, row br - 1 of a
-    // propagating direction's 14-row box (which starts c_k's row below the tile)
-    row_vals<CX>(c.boxl + (PAUSED ? br + CY : br - 1) * kABW, c.lane, b);
+    // l'(x + c_k): row tr - OFF + CY of a paused direction's box, row tr of a propagating
+    // direction's box
+    row_vals<CX>(c.boxl + (PAUSED ? tr - OFF + CY : tr) * kABW, c.lane, b);
 #pragma unroll
     for (int j = 0; j < 4; ++j) b[j] += t.sr[1 + k + CY][1 + j + CX];
     if constexpr (PAUSED) {
-      row_vals<0>(c.boxl + br * kABW, c.lane, av);
+      row_vals<0>(c.boxl + (tr - OFF) * kABW, c.lane, av);
 #pragma unroll
       for (int j = 0; j < 4; ++j) av[j] += t.sr[1 + k][1 + j];
     } else {
@@ -105,7 +110,7 @@ __device__ __forceinline__ void adj_body(AdjRegs& t, const AdjCtx& c) {
       for (int j = 0; j < 4; ++j) av[j] = b[j];
     }
     {
-      const float4 q = *reinterpret_cast<const float4*>(c.boxd + (br - 1) * kATW + 4 * c.lane);
+      const float4 q = *reinterpret_cast<const float4*>(c.boxd + tr * kATW + 4 * c.lane);
       dv[0] = q.x; dv[1] = q.y; dv[2] = q.z; dv[3] = q.w;
     }
 #pragma unroll
@@ -141,7 +146,7 @@ __device__ __forceinline__ bool adj_kind(int& j, int end, AdjRegs& t, AdjCtx& c,
     }
     const AdjDir3 d = table[j];
     c.boxl = reinterpret_cast<const float*>(smem + st * kAStage);
-    c.boxd = reinterpret_cast<const float*>(smem + st * kAStage + kBoxL);
+    c.boxd = reinterpret_cast<const float*>(smem + st * kAStage + kBoxLSlot);
     c.dst = obase + int64_t(d.k) * plane;
     c.wk = d.wk;
     c.first = j == 0;
@@ -205,14 +210,16 @@ __global__ void __maxnreg__(128)
       }
       const AdjDir3 d = table[j];
       unsigned char* stage = smem + st * kAStage;
-      if (d.kind & 8) {   // paused: l'(x) and l'(x + c_k)
+      const int cy = c_hop_y[d.kind & 7];
+      if ((d.kind & 8) && cy != 0) {   // paused, vertical component: l'(x) and l'(x + c_k)
         mbar_expect(&full[st], kBoxL + kBoxD);
-        tma_load_3d(stage, &lam_map, col0 - kAV, row0 - 1, d.k, &full[st]);
-      } else {            // propagating: l'(x + c_k) only
+        tma_load_3d(stage, &lam_map, col0 - kAV, row0 + (cy < 0 ? -1 : 0), d.k, &full[st]);
+      } else {   // propagating: l'(x + c_k) only; paused horizontal: the tile's rows
         mbar_expect(&full[st], kBoxL14 + kBoxD);
-        tma_load_3d(stage, &lam_map14, col0 - kAV, row0 + c_hop_y[d.kind & 7], d.k, &full[st]);
+        tma_load_3d(stage, &lam_map14, col0 - kAV, row0 + ((d.kind & 8) ? 0 : cy), d.k,
+                    &full[st]);
       }
-      tma_load_3d(stage + kBoxL, &tape_map, col0, row0, d.z_tape, &full[st]);
+      tma_load_3d(stage + kBoxLSlot, &tape_map, col0, row0, d.z_tape, &full[st]);
     }
     return;
   }

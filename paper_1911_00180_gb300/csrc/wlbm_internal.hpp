@@ -396,12 +396,13 @@ bool make_box_tensor_map(void* out, void* planes, int storage, const Geom& g, in
 bool make_word_tensor_map(void* out, void* planes, const Geom& g, int nplanes,
                           std::string* why);
 // Reverse step with TMA tiles (float32): lam_map describes the q planes of a.lam_in with
-// boxes of kAdjTmaBoxRows rows (paused directions read both x and x + c_k), lam_map14 the
-// same planes with boxes of kAdjTmaRows rows (propagating directions read x + c_k only),
+// boxes of kAdjTmaBoxRows rows (paused directions with a vertical hop component read both x
+// and x + c_k), lam_map14 the same planes with boxes of kAdjTmaRows rows (propagating
+// directions read x + c_k only; paused horizontal hops x and x + c_k of the same rows),
 // tape_map the adjoint tape with boxes of kAdjTmaRows rows of the tile's kAdjTmaCols columns
 // (no column halo); tape_z0 is the plane index of the step's slot in the tape, order the
 // step's kind-sorted directions.
-constexpr int kAdjTmaBoxRows = 16;
+constexpr int kAdjTmaBoxRows = 15;
 constexpr int kAdjTmaRows = 14;
 constexpr int kAdjTmaCols = 128;
 cudaError_t configure_adj_tma();
