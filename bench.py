@@ -120,14 +120,15 @@ STEP_KERNEL_SOURCES = ("elem.cuh", "k_step_tma.cu", "lattice.hpp", "mbar.cuh",
                        "step_tile.cuh", "step_tile_wide.cuh", "wlbm_internal.hpp")
 
 
-def measured_traffic(workload, storage, nx, q):
-    """DRAM bytes per step-kernel launch from the committed ncu captures, if they were
-    taken on the step kernel's sources of this tree (else None): the digest covers
-    k_step_tma.cu and the headers it compiles with (STEP_KERNEL_SOURCES)."""
+def _traffic_table():
+    """Rows of the committed ncu traffic captures, if they were taken on the step kernels'
+    sources of this tree (else {}): the digest covers k_step_tma.cu and the headers it
+    compiles with (STEP_KERNEL_SOURCES).  (workload, storage, nx, q) -> (DRAM bytes per
+    launch, algorithmic bytes of the captured launch or None)."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "k_step_tma_traffic.txt")
     if not os.path.exists(path):
-        return None
+        return {}
     h = hashlib.sha256()
     for f in STEP_KERNEL_SOURCES:
         with open(os.path.join(ROOT, "paper_1911_00180_gb300", "csrc", f), "rb") as fh:
@@ -140,11 +141,28 @@ def measured_traffic(workload, storage, nx, q):
             continue
         if parts[0] == "sources":
             digest = parts[1]
-        elif len(parts) == 6:
-            table[(parts[0], parts[1], int(parts[2]), int(parts[3]))] = float(parts[5])
-    if digest != h.hexdigest():
-        return None
-    return table.get((workload, storage, nx, q))
+        elif len(parts) in (6, 7):
+            table[(parts[0], parts[1], int(parts[2]), int(parts[3]))] = (
+                float(parts[5]), float(parts[6]) if len(parts) == 7 else None)
+    return table if digest == h.hexdigest() else {}
+
+
+def measured_traffic(workload, storage, nx, q):
+    """DRAM bytes per step-kernel launch from the committed ncu captures (None if there is
+    no capture of this workload on the current sources)."""
+    row = _traffic_table().get((workload, storage, nx, q))
+    return row[0] if row else None
+
+
+def batch_traffic(storage, algo):
+    """DRAM bytes per launch of the batched step kernel: the full batch is too large to
+    capture under ncu (tens of GB of planes), so its traffic is the captured subset's
+    ratio of DRAM to algorithmic bytes (the instances of at most 2e7 site-directions, every
+    Q of the recipe) times the full batch's algorithmic bytes; None without a capture."""
+    row = _traffic_table().get(("batch", storage, 20000000, 0))
+    if not row or not row[1]:
+        return None, None
+    return row[0] / row[1] * algo, row[0] / row[1]
 
 
 def peaks():
@@ -267,7 +285,12 @@ def run_batch(args):
             "launch": {"instances_rank0": len(specs), "site_directions": upd,
                        "autotune": tuned},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None, "kernel": "k_step_*_batch",
+                         "frac": achieved / peak,
+                         "traffic": batch_traffic(args.storage, algo)[0],
+                         "traffic_note": "scaled from the ncu capture of the 2e7-site-direction "
+                                         "subset (DRAM / algorithmic = %s)"
+                                         % batch_traffic(args.storage, algo)[1],
+                         "kernel": "k_step_*_batch", "algorithmic_bytes_per_launch": algo,
                          "peak_kind": kind, "kernel_ms_per_launch": per_launch,
                          "kernel_launches_timed": nlaunch},
             "gpu_launches": int(l1 - l0)}
@@ -573,9 +596,13 @@ def measure_batch(wl, torch, storage, steps, warmup=48, graph=48, every=8, persi
     per = kms / kn
     ach, frac, peak, kind = kernel_fraction(per, algo)
     state_gb = sum(2 * sp["q"] * (sp["nx"] + 2) * (sp["ny"] + 2) * elem for sp in specs) / 1e9
+    traffic, ratio = (None, None) if persistent else batch_traffic(storage, algo)
     return {"updates_per_s": upd * steps / (ms * 1e-3), "ms_per_step": ms / steps,
             "kernel": "k_batch_persistent (per step)" if persistent else "k_step_tma_batch",
-            "kernel_ms_per_launch": per,
+            "kernel_ms_per_launch": per, "traffic": traffic,
+            "traffic_note": None if traffic is None else
+            "scaled from the ncu capture of the 2e7-site-direction subset (DRAM / algorithmic "
+            "= %.3f)" % ratio,
             "kernel_launches_timed": kn, "achieved_gbs": ach, "frac": frac, "peak": peak,
             "peak_kind": kind, "algorithmic_bytes_per_launch": algo, "steps": steps,
             "instances": len(specs), "state_gb": state_gb,
