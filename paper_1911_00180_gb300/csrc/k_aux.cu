@@ -160,6 +160,47 @@ __global__ void k_init(const InitArgs a) {
   a.e_cur[off] = e;
 }
 
+// e_i - e_j of one cell from their stored values: float32 deviations subtract directly;
+// bfloat16 ones subtract before the scaling, and the reference parts w R leave only
+// (w_i - w_j) R.
+template <typename T>
+__device__ __forceinline__ float dev_diff(const T* pi, const T* pj, float wi, float wj,
+                                          const float* ref, int64_t off, float scale) {
+  const float d = Elem<T>::ld(pi) - Elem<T>::ld(pj);
+  return ref ? fmaf(d, scale, __fmul_rn(wi - wj, ref[off])) : d;
+}
+
+// Heat flux of one cell, q = sum_i e_i s_i (Eq. heat-flux, v = 1 here), taken over the
+// pairs of opposite directions i and i + Q/2 (the ring order puts them Q/2 apart, with
+// s_{i+Q/2} = -s_i exactly): q = sum_{i < Q/2} (e_i - e_{i+Q/2}) s_i, summed with Kahan's
+// compensation (the product's rounding folded into the compensated term by one fma).  So
+// the float32 result is within a few roundings of |q| for any Q, where a plain float32 sum
+// of Q products errs by about Q roundings of the summands' magnitude (at Q = 1024 more than
+// 1e-5 of a direction's amplitude).
+template <typename T, typename Par>
+__device__ __forceinline__ void cell_flux(const T* planes, int64_t plane, int q, Par par,
+                                          const float* w, const float* sx, const float* sy,
+                                          const float* ref, int64_t off, float scale,
+                                          float& qx, float& qy) {
+  const int h = q / 2;
+  float cx = 0.f, cy = 0.f;   // compensations: what the running sums lost
+  qx = 0.f;
+  qy = 0.f;
+#pragma unroll 4
+  for (int i = 0; i < h; ++i) {
+    const int j = i + h;
+    const float d = dev_diff(planes + int64_t(par(i) * q + i) * plane + off,
+                             planes + int64_t(par(j) * q + j) * plane + off, w[i], w[j], ref,
+                             off, scale);
+    const float yx = fmaf(d, sx[i], -cx), yy = fmaf(d, sy[i], -cy);
+    const float tx = qx + yx, ty = qy + yy;
+    cx = (tx - qx) - yx;
+    cy = (ty - qy) - yy;
+    qx = tx;
+    qy = ty;
+  }
+}
+
 template <typename T>
 __global__ void k_moments(const MomentArgs a) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -175,14 +216,10 @@ __global__ void k_moments(const MomentArgs a) {
     a.dT[t] = a.accumulate ? a.dT[t] + v : v;
   }
   if (a.qx || a.qy) {
-    const T* planes = static_cast<const T*>(a.planes);
-    float qx = 0.f, qy = 0.f;
-    for (int i = 0; i < a.q; ++i) {
-      const float v = dev_load(planes + int64_t(parity_of(a.par, i) * a.q + i) * a.plane + off,
-                               a.w[i], a.e_refp, off, a.scale);
-      qx = fmaf(v, a.sx[i], qx);
-      qy = fmaf(v, a.sy[i], qy);
-    }
+    float qx, qy;
+    cell_flux(static_cast<const T*>(a.planes), a.plane, a.q,
+              [&](int i) { return parity_of(a.par, i); }, a.w, a.sx, a.sy, a.e_refp, off,
+              a.scale, qx, qy);
     const float wx = a.weight * (qx * a.vg), wy = a.weight * (qy * a.vg);
     if (a.qx) a.qx[t] = a.accumulate ? a.qx[t] + wx : wx;
     if (a.qy) a.qy[t] = a.accumulate ? a.qy[t] + wy : wy;
@@ -234,14 +271,9 @@ __device__ __forceinline__ void reduce_cell(const ReduceArgs& a, const ReduceSme
     v[1] += e;
     // a cell's flux over its Q directions in float32 (as in k_moments: the stored values
     // are float32 or coarser), the sums over cells in float64
-    float qx = 0.f, qy = 0.f;
-#pragma unroll 8
-    for (int i = 0; i < a.q; ++i) {
-      const float u = dev_load(planes + int64_t(sm.par[i] * a.q + i) * a.plane + off, sm.w[i],
-                               a.e_refp, off, float(a.scale));
-      qx = fmaf(u, sm.sx[i], qx);
-      qy = fmaf(u, sm.sy[i], qy);
-    }
+    float qx, qy;
+    cell_flux(planes, a.plane, a.q, [&](int i) { return int(sm.par[i]); }, sm.w, sm.sx, sm.sy,
+              a.e_refp, off, float(a.scale), qx, qy);
     v[2] += qx;
     v[3] += qy;
     const int x = fx - 1;

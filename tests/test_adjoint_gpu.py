@@ -93,6 +93,22 @@ def test_adjoint_gradients_match_oracle(kinds):
     assert np.all(g_tw[[k for k in range(4) if kinds[k] != I]] == 0.0)
 
 
+@pytest.mark.parametrize("q", [256, 1024])
+def test_adjoint_largest_direction_sets_match_oracle(q):
+    """Q = 256 and the largest Q the library takes (1024): the reverse step's direction
+    table and ring at their largest, with walls of every kind, against the oracle."""
+    kinds = (D, I, P, P)                   # the isothermal wall 7 cells from the probe
+    steps, ckpt = 20, 6
+    mfp, dT0, probe, tw = _case(kinds, nx=30, ny=16, seed=7)
+    J, g_mfp, g_tw, g_dT0 = _gpu(kinds, mfp, dT0, probe, tw, steps, ckpt, q)
+    ref = _oracle(kinds, mfp, dT0, probe, tw, steps, q)
+    assert abs(J - ref["J"]) <= 1e-5
+    assert _rel(g_mfp, ref["dJ_dmfp"]) <= TOL
+    assert _rel(g_dT0, ref["dJ_ddT0"]) <= TOL
+    assert abs(ref["dJ_dTwall"][1]) > 0
+    assert _rel(g_tw[1:2], ref["dJ_dTwall"][1:2]) <= TOL
+
+
 @pytest.mark.parametrize("kinds,spec", [((I, I, 3, D), (0.0, 0.0, 0.0, 0.45)),
                                        ((D, 3, I, D), (0.7, 0.0, 0.0, 0.0))])
 def test_adjoint_specular_walls_match_oracle(kinds, spec):

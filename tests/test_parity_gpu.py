@@ -48,7 +48,8 @@ TOL16_Q = 2e-3
 TOL16_STATE_WALL = 2e-2
 
 
-def _compare(cfg, steps, storage=0, tol=TOL32, state_tol=None, variant=None, options=None):
+def _compare(cfg, steps, storage=0, tol=TOL32, state_tol=None, variant=None, options=None,
+             q_of_flux=False):
     orc = oracle_run(cfg, steps, flux_peak=storage == 1)
     gpu = gpu_run(cfg, steps, storage, variant=variant, options=options)
     amp = max(float(np.abs(cfg["dT"]).max()),
@@ -60,6 +61,8 @@ def _compare(cfg, steps, storage=0, tol=TOL32, state_tol=None, variant=None, opt
     e_s = rel_linf(gpu["state"][:, 1:-1, 1:-1], orc.d[:, 1:-1, 1:-1], dscale)
     qx, qy = orc.heat_flux()
     qscale, qtol = dscale, tol
+    if q_of_flux:   # float32 q against the oracle's flux amplitude at the compared step
+        qscale = float(max(np.abs(qx).max(), np.abs(qy).max()))
     if storage == 1:
         own = gpu["state"][:, 1:-1, 1:-1]
         e_m = max(rel_linf(gpu["qx"], np.tensordot(orc.s_hat[:, 0], own, axes=(0, 0)), dscale),
@@ -72,7 +75,8 @@ def _compare(cfg, steps, storage=0, tol=TOL32, state_tol=None, variant=None, opt
                              orc.d[:, 1:-1, 1:-1].shape)
     print("parity %s %dx%d Q%d %s %d steps: T %.3g  state %.3g at %s  q %.3g (of %s)"
           % ("bf16" if storage == 1 else "fp32", cfg["nx"], cfg["ny"], cfg["q"], cfg["bc"],
-             steps, e_t, e_s, where, e_q, "flux amplitude" if storage == 1 else "state scale"))
+             steps, e_t, e_s, where, e_q,
+             "flux amplitude" if storage == 1 or q_of_flux else "state scale"))
     assert e_t <= tol, ("T", e_t)
     assert e_s <= (state_tol or tol), ("state", e_s)
     assert e_q <= qtol, ("q", e_q)
@@ -201,6 +205,27 @@ def test_wide_tiles_edges_and_field(nx, ny, q, bc):
                dT=W.random_dT(nx, ny, seed=nx * ny + q, scale=0.5))
     _compare(cfg, 40, storage=1, tol=TOL16, state_tol=TOL16_STATE, variant=3,
              options={wl.wlbm.OPT_BF16_WIDE: 1})
+
+
+@pytest.mark.parametrize("storage,tol,stol", [(0, TOL32, None), (1, TOL16, TOL16_STATE)])
+@pytest.mark.parametrize("q", [256, 1024])
+def test_largest_direction_sets(storage, tol, stol, q):
+    """Q = 256 and the largest Q the library takes (1024, M = 128 hops a worm): the
+    direction table and the ring of every step kernel at their largest, on a grid of two
+    tiles and a ragged tail in x (three 128-column tiles, two 256-column ones) and a
+    ragged tile row in y, with mixed walls and a per-cell MFP field; against the oracle.
+    The float32 flux is held to 1e-5 of the flux amplitude (the pulse amplitude of q): q
+    sums Q directions, at Q = 1024 some 60 times one direction's amplitude, and each
+    float32 state value carries about 2e-7 of that amplitude after 24 steps, so the flux
+    measured against one direction's amplitude (1.5e-5 at Q = 1024) reflects the size of
+    the sum, not an error of the method (2.5e-7 of the flux amplitude)."""
+    nx, ny = 300, 17
+    cfg = dict(nx=nx, ny=ny, q=q, mfp=None,
+               mfp_field=np.maximum(W.lognormal_mfp(nx, ny, seed=q, corr=4.0), 1.6)
+               .astype(np.float32),
+               bc=(I, A, P, P), t_wall=(300.7, 300.0, 300.0, 300.0),
+               emulate_3d=True, dT=W.random_dT(nx, ny, seed=q + 1, scale=0.5))
+    _compare(cfg, 24, storage=storage, tol=tol, state_tol=stol, variant=3, q_of_flux=True)
 
 
 def test_wide_tiles_refused_for_float32():
