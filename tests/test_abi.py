@@ -72,6 +72,33 @@ def test_create_rejects_bad_arguments(wl):
     assert _create(wl, mfp=-1.0)[0] == wl.wlbm.WLBM_ERR_INVALID_ARG
 
 
+@pytest.mark.parametrize("nx,ny,q", [(0, 16, 16), (16, 0, 16), (-3, 16, 16), (16, -1, 16),
+                                     (16, 16, 0), (16, 16, 4), (16, 16, 1032), (16, 16, -8),
+                                     (16, 16, 2048)])
+def test_create_rejects_empty_grids_and_out_of_range_q(wl, nx, ny, q):
+    """Empty or negative grids and Q outside 8 <= Q = 8M <= 1024 are refused before any
+    device work (no allocation is asked for: the test allocator returns none)."""
+    st, h, _ = _create(wl, nx=nx, ny=ny, q=q)
+    assert st == wl.wlbm.WLBM_ERR_INVALID_ARG
+    assert not h.value
+
+
+def test_batch_create_rejects_empty_batches_and_null_arguments(wl):
+    """A batch of no instances, or without grids, boundaries or MFP, is refused before any
+    instance is created."""
+    g = (wl.wlbm.wlbm_grid * 1)(wl.wlbm.wlbm_grid(16, 16, 16, 0, 1, 0, 300.0, 624.8, 1.0))
+    b = (wl.wlbm.wlbm_boundary * 1)(wl.wlbm.wlbm_boundary((C.c_int32 * 4)(0, 0, 0, 0),
+                                                         (C.c_double * 4)(300.0, 300.0, 300.0,
+                                                                          300.0)))
+    mfp = (C.c_double * 1)(4.0)
+    out = C.c_void_p()
+    for n, grids, bcs, mu in [(0, g, b, mfp), (-1, g, b, mfp), (1, None, b, mfp),
+                              (1, g, None, mfp), (1, g, b, None)]:
+        st = wl.lib.wlbm_batch_create(n, grids, None, mu, bcs, None, None, C.byref(out))
+        assert st == wl.wlbm.WLBM_ERR_INVALID_ARG, n
+        assert not out.value
+
+
 def test_create_rejects_unstable_relaxation(wl):
     """Appendix A: the paused step is stable only for W <= 1.  MFP = 0.5 cell gives
     W_corr > 1 under the paper's weight; the opt-in exponential mode accepts it."""
