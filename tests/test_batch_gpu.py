@@ -359,3 +359,46 @@ def test_batch_c4_instances_match_oracle(storage, persistent):
     print("batch C4 %s%s: T %.3g  state %.3g" % ("bf16" if storage else "fp32",
                                                  " persistent" if persistent else "", worst_t,
                                                  worst_s))
+
+
+@pytest.mark.parametrize("storage", [0, 1])
+def test_full_c4_batch_equals_single_grids_bitwise(storage):
+    """All 96 films of the batch workload (thickness 16-512, aspect 8-32, Q 16-256; 40 / 20
+    GB of planes) in the benchmark's launch configuration (own stream, TMA tiles, 48-step
+    graph replay, event timing of every 8th step), 48 steps, against each film run as a
+    single grid: the same states bit for bit (compared on the device; the single grids run
+    one at a time next to the batch)."""
+    import torch
+    import paper_1911_00180_gb300 as wl
+    insts = W.batch_c4(seed=4)
+    specs = [dict(nx=c["nx"], ny=c["ny"], q=c["q"], bc=c["bc"], t_wall=c["t_wall"],
+                  mfp=max(c["mfp"], 1.5)) for c in insts]
+    steps = BENCH_GRAPH
+    torch.cuda.empty_cache()             # memory cached by earlier tests back to the device
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        b = wl.WormLBMBatch(specs, storage=storage, stream=stream)
+        b.wlbm_batch_set_option(wl.wlbm.OPT_STEP_VARIANT, 3)
+        b.wlbm_batch_set_option(wl.wlbm.OPT_GRAPH_STEPS, BENCH_GRAPH)
+        b.wlbm_batch_init_temperature([c["dT"] for c in insts])
+        b.wlbm_batch_profile(BENCH_PROFILE)
+        b.wlbm_batch_step(steps)
+        assert b.wlbm_batch_get_option(wl.wlbm.OPT_GRAPH_REPLAYS) == 1
+        b.wlbm_batch_check()
+        for k, (spec, c) in enumerate(zip(specs, insts)):
+            got = b.instances[k].wlbm_get_state()
+            h = wl.WormLBM(spec["nx"], spec["ny"], spec["q"], mfp=spec["mfp"], bc=spec["bc"],
+                           t_wall=spec["t_wall"], storage=storage, stream=stream)
+            h.wlbm_set_option(wl.wlbm.OPT_STEP_VARIANT, 3)
+            h.wlbm_init_temperature(c["dT"])
+            h.wlbm_step(steps)
+            want = h.wlbm_get_state()
+            h.wlbm_check()
+            h.close()
+            # isothermal x walls: their ghost columns are rewritten before every step
+            assert torch.equal(got[:, :, 1:-1], want[:, :, 1:-1]), (k, c["name"])
+            del got, want
+            torch.cuda.empty_cache()     # the films differ in size: keep the cache small
+        b.close()
+    torch.cuda.empty_cache()
+
