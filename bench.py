@@ -238,6 +238,8 @@ def run_batch(args):
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         b = wl.WormLBMBatch(specs, storage=storage, stream=stream)
+        if args.wide is not None and args.storage == "bf16":
+            b.wlbm_batch_set_option(wl.wlbm.OPT_BF16_WIDE, args.wide)
         if args.persistent is None:
             tuned = autotune.tune_batch(b, storage, trial_steps=48)
         else:
@@ -575,6 +577,7 @@ def measure_batch(wl, torch, storage, steps, warmup=48, graph=48, every=8, persi
         b.wlbm_batch_set_option(wl.wlbm.OPT_STEP_VARIANT, 3)
         b.wlbm_batch_set_option(wl.wlbm.OPT_GRAPH_STEPS, graph)
         b.wlbm_batch_set_option(wl.wlbm.OPT_PERSISTENT, persistent)
+        wide = b.wlbm_batch_get_option(wl.wlbm.OPT_BF16_WIDE) and not persistent
         b.wlbm_batch_init_temperature([c["dT"] for c in insts])
         b.wlbm_batch_step(warmup)
         stream.synchronize()
@@ -598,7 +601,8 @@ def measure_batch(wl, torch, storage, steps, warmup=48, graph=48, every=8, persi
     state_gb = sum(2 * sp["q"] * (sp["nx"] + 2) * (sp["ny"] + 2) * elem for sp in specs) / 1e9
     traffic, ratio = (None, None) if persistent else batch_traffic(storage, algo)
     return {"updates_per_s": upd * steps / (ms * 1e-3), "ms_per_step": ms / steps,
-            "kernel": "k_batch_persistent (per step)" if persistent else "k_step_tma_batch",
+            "kernel": ("k_batch_persistent (per step)" if persistent else
+                       "k_step_tma_batch_wide" if wide else "k_step_tma_batch"),
             "kernel_ms_per_launch": per, "traffic": traffic,
             "traffic_note": None if traffic is None else
             "scaled from the ncu capture of the 2e7-site-direction subset (DRAM / algorithmic "

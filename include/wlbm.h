@@ -297,7 +297,8 @@ wlbm_status wlbm_adjoint_backward(wlbm_handle* h, const float* dJ_dT, const floa
  *                          keeps the cell terms in shared memory, four blocks per SM; the
  *                          others keep them in registers, two blocks per SM).  bfloat16
  *                          single grids take these 128-column forms with
- *                          WLBM_OPT_BF16_WIDE = 0 or the tile loop; batches always.
+ *                          WLBM_OPT_BF16_WIDE = 0 or the tile loop; batches with
+ *                          WLBM_OPT_BF16_WIDE = 0 take the cell-tile form with 8 stages.
  *   WLBM_OPT_TILE_LOOP     variant 3: 0 (default) one block per 128 x 14 tile; 1 a grid of
  *                          resident blocks that take the tiles in turn (no partial last
  *                          wave; bfloat16 runs three such blocks per SM where the ring
@@ -383,7 +384,9 @@ wlbm_status wlbm_autotune(wlbm_handle* h, int32_t trial_steps, int32_t* variant,
  * wlbm_batch_instance returns the handle of instance k (owned by the batch) for
  * moments, reductions and state access.  Options (wlbm_batch_set_option) are those of
  * wlbm_set_option, for every instance: WLBM_OPT_STEP_VARIANT 0, 1 or 3 (default 3 when
- * every instance has a tensor map), WLBM_OPT_GRAPH_STEPS, WLBM_OPT_FUSE_PERIODIC.
+ * every instance has a tensor map), WLBM_OPT_GRAPH_STEPS, WLBM_OPT_FUSE_PERIODIC, and
+ * WLBM_OPT_BF16_WIDE (bfloat16 per-step launches of variant 3 in 256-column tiles; default
+ * 1 when every instance has a word tensor map; the persistent kernel keeps 128 columns).
  * Instances with a periodic axis whose edges the step kernel does not mirror get their own
  * periodic pass each step; graph replay then keeps one captured graph per starting
  * energy-plane phase of those instances (at most three).  Options of batches only:

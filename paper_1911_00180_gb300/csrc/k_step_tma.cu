@@ -70,6 +70,42 @@ __global__ void __launch_bounds__(kWThreads, 2)
   step_tma_tile_wide<S, FIELD_W>(a, &tmap, cbase, int(blockIdx.x), int(blockIdx.y), smem);
 }
 
+// Batched wide-tile form: block b belongs to the instance whose first_tile_w is the
+// largest one <= b; the instance's word tensor map sits in global memory.
+template <int S>
+__global__ void __launch_bounds__(kWThreads, 2)
+    k_step_tma_batch_wide(const BatchInst* insts, int n, int t) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ StepArgs sa;
+  __shared__ const void* tm;
+  __shared__ int tile[3];
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    int lo = 0, hi = n - 1;
+    const int b = int(blockIdx.x);
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (insts[mid].first_tile_w <= b) lo = mid;
+      else hi = mid - 1;
+    }
+    const BatchInst& I = insts[lo];
+    sa = I.a;
+    sa.codes = I.codes + size_t(t) * I.a.q;
+    sa.order = I.order + size_t(t) * (I.a.q + 17);
+    const int cur = (I.phase + t) % I.n_e;
+    sa.e_in = I.e[cur];
+    sa.e_out = I.e[(cur + 1) % I.n_e];
+    sa.e_ref = I.e[(cur + 2) % 3];
+    tm = I.tmap_w;
+    const int local = b - I.first_tile_w;
+    tile[0] = local % I.tiles_x_w;
+    tile[1] = local / I.tiles_x_w;
+    tile[2] = I.cbase_w;
+  }
+  __syncthreads();
+  if (sa.wfield) step_tma_tile_wide<S, true>(sa, tm, tile[2], tile[0], tile[1], smem);
+  else step_tma_tile_wide<S, false>(sa, tm, tile[2], tile[0], tile[1], smem);
+}
+
 // Tile-looping form: a grid of resident blocks (three per SM for bfloat16, whose cell
 // terms sit in shared memory; two for float32) in which block b takes tiles b, b + grid,
 // ... in turn, so no partial last wave of blocks idles the GPU, and whose producer streams
@@ -225,10 +261,11 @@ constexpr int kStagesBF16WideHighQ = 5;
 template <int S>
 cudaError_t configure_wide_t() {
   const int bytes = int(WideLayout<S>::bytes(kMaxQ));
-  const void* fns[2] = {(const void*)k_step_tma_wide<S, false>,
-                        (const void*)k_step_tma_wide<S, true>};
+  const void* fns[3] = {(const void*)k_step_tma_wide<S, false>,
+                        (const void*)k_step_tma_wide<S, true>,
+                        (const void*)k_step_tma_batch_wide<S>};
   cudaError_t e = cudaSuccess;
-  for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+  for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
     e = cudaFuncSetAttribute(fns[k], cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(fns[k], cudaFuncAttributePreferredSharedMemoryCarveout,
@@ -240,6 +277,14 @@ cudaError_t configure_wide_t() {
 // First column of the first wide tile: kX0, or with a computed left ghost column kX0 - 8
 // (a multiple of 8 columns, so that every box starts on a 16-byte boundary).
 int wide_cbase(const StepArgs& a) { return a.cmin < kX0 ? kX0 - 8 : kX0; }
+
+template <int S>
+cudaError_t launch_batch_wide_t(const BatchInst* insts, int n, int max_q, int total_tiles, int t,
+                                cudaStream_t s) {
+  k_step_tma_batch_wide<S><<<total_tiles, dim3(32, kWWarps + 1), WideLayout<S>::bytes(max_q),
+                             s>>>(insts, n, t);
+  return cudaGetLastError();
+}
 
 template <int S>
 cudaError_t launch_wide_t(const StepArgs& a, const CUtensorMap& tm, cudaStream_t s) {
@@ -278,6 +323,19 @@ cudaError_t launch_step_tma_batch(int storage, const BatchInst* insts, int n, in
     k_step_tma_batch<float, kStagesF32, false><<<total_tiles, block, LY::bytes(max_q), s>>>(insts, n, t);
   }
   return cudaGetLastError();
+}
+
+void tma_cover_wide(const StepArgs& cover, int* cbase, int* tiles_x) {
+  *cbase = wide_cbase(cover);
+  *tiles_x = (cover.cmax - *cbase) / kWTW + 1;
+}
+
+cudaError_t launch_step_tma_batch_wide(const BatchInst* insts, int n, int max_q,
+                                       int total_tiles, int t, cudaStream_t s) {
+  if (total_tiles <= 0) return cudaSuccess;
+  return max_q <= kDeepMaxQ
+             ? launch_batch_wide_t<kStagesBF16Wide>(insts, n, max_q, total_tiles, t, s)
+             : launch_batch_wide_t<kStagesBF16WideHighQ>(insts, n, max_q, total_tiles, t, s);
 }
 
 int tma_tile_width() { return kTW3; }

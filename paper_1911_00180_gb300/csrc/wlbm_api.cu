@@ -1667,6 +1667,10 @@ struct wlbm_batch {
   uint16_t* d_order = nullptr;      // [instance][t][q + 17] kind-sorted directions
   unsigned char* d_tmaps = nullptr; // [instance] 128-byte CUtensorMaps (variant 3)
   bool all_tmap = false;            // every instance has a tensor map
+  unsigned char* d_tmaps_w = nullptr;  // [instance] 32-bit-word maps (bfloat16 wide tiles)
+  bool all_tmap_w = false;          // every instance has one
+  int wide = 0;                     // per-step launches in 256-column bfloat16 tiles
+  int total_tiles_w = 0;
   int max_q = 0;
   BatchInst* h_inst = nullptr;      // pinned staging
   BatchWalls* h_walls = nullptr;
@@ -1777,6 +1781,7 @@ struct wlbm_batch {
   // Block and warp offsets of every instance in the batched grids.
   void layout() {
     total_tiles = 0;
+    total_tiles_w = 0;
     total_wall_blocks = 0;
     int items = 0;
     const int tw = step_tile_width(storage, variant);
@@ -1786,6 +1791,12 @@ struct wlbm_batch {
       if (variant == 3) {   // tiles of the cells variant 3 computes
         StepArgs cover{};
         tma_cover(h[k]->bc_kind, g.nx, g.ny, &cover, &tx, &ty);
+        int cb = 0, txw = 0;
+        tma_cover_wide(cover, &cb, &txw);
+        h_inst[k].cbase_w = cb;
+        h_inst[k].tiles_x_w = txw;
+        h_inst[k].first_tile_w = total_tiles_w;
+        total_tiles_w += txw * ty;
       }
       h_inst[k].tiles_x = tx;
       h_inst[k].first_tile = total_tiles;
@@ -1835,6 +1846,7 @@ wlbm_status wlbm_batch_create(int32_t n, const wlbm_grid* grids, const float* co
   b->code_off.resize(n);
   b->order_off.resize(n);
   b->all_tmap = true;
+  b->all_tmap_w = true;
   for (int k = 0; k < n; ++k) {
     b->code_off[k] = b->code_bytes;
     b->code_bytes += size_t(kBatchChunk) * grids[k].q;
@@ -1842,10 +1854,12 @@ wlbm_status wlbm_batch_create(int32_t n, const wlbm_grid* grids, const float* co
     b->order_elems += size_t(kBatchChunk) * (grids[k].q + 17);
     b->max_q = std::max(b->max_q, int(grids[k].q));
     b->all_tmap = b->all_tmap && b->h[k]->has_tmap;
+    b->all_tmap_w = b->all_tmap_w && b->h[k]->has_tmap_w;
   }
   b->d_codes = static_cast<uint8_t*>(b->dev_alloc(b->code_bytes));
   b->d_order = static_cast<uint16_t*>(b->dev_alloc(b->order_elems * 2));
   b->d_tmaps = static_cast<unsigned char*>(b->dev_alloc(size_t(n) * 128));
+  if (b->all_tmap_w) b->d_tmaps_w = static_cast<unsigned char*>(b->dev_alloc(size_t(n) * 128));
   b->d_inst = static_cast<BatchInst*>(b->dev_alloc(sizeof(BatchInst) * n));
   b->d_walls = static_cast<BatchWalls*>(b->dev_alloc(sizeof(BatchWalls) * n));
   b->d_ctr = static_cast<unsigned*>(b->dev_alloc(sizeof(unsigned) * (1 + 2 * size_t(n))));
@@ -1857,7 +1871,7 @@ wlbm_status wlbm_batch_create(int32_t n, const wlbm_grid* grids, const float* co
   if (!wall_inst.empty())
     b->d_wall_inst = static_cast<int*>(b->dev_alloc(wall_inst.size() * sizeof(int)));
   if (!b->d_codes || !b->d_order || !b->d_tmaps || !b->d_inst || !b->d_walls || !b->d_ctr ||
-      !b->d_abort || (!wall_inst.empty() && !b->d_wall_inst))
+      !b->d_abort || (!wall_inst.empty() && !b->d_wall_inst) || (b->all_tmap_w && !b->d_tmaps_w))
     return bad(WLBM_ERR_OOM, "wlbm_batch_create: device allocation failed");
   if (!wall_inst.empty() &&
       cudaMemcpy(b->d_wall_inst, wall_inst.data(), wall_inst.size() * sizeof(int),
@@ -1873,6 +1887,8 @@ wlbm_status wlbm_batch_create(int32_t n, const wlbm_grid* grids, const float* co
                       cudaHostAllocDefault);
   for (int k = 0; k < n && e == cudaSuccess && b->all_tmap; ++k)
     e = cudaMemcpy(b->d_tmaps + size_t(k) * 128, b->h[k]->tmap, 128, cudaMemcpyHostToDevice);
+  for (int k = 0; k < n && e == cudaSuccess && b->all_tmap_w; ++k)
+    e = cudaMemcpy(b->d_tmaps_w + size_t(k) * 128, b->h[k]->tmap_w, 128, cudaMemcpyHostToDevice);
   if (e == cudaSuccess)
     e = cudaHostAlloc(reinterpret_cast<void**>(&b->h_walls), sizeof(BatchWalls) * n,
                       cudaHostAllocDefault);
@@ -1886,6 +1902,7 @@ wlbm_status wlbm_batch_create(int32_t n, const wlbm_grid* grids, const float* co
     b->variant = 3;
     b->classify();
   }
+  b->wide = b->all_tmap_w ? 1 : 0;
   std::memset(b->h_walls, 0, sizeof(BatchWalls) * n);
   b->layout();
   *out = b;
@@ -1929,6 +1946,7 @@ wlbm_status wlbm_batch_get_option(const wlbm_batch* b, int32_t key, int64_t* val
   else if (key == WLBM_OPT_RING_STAGES) *value = b->ring_stages;
   else if (key == WLBM_OPT_WAIT_LIMIT) *value = b->wait_limit;
   else if (key == WLBM_OPT_STALL_TEST) *value = b->stall_test;
+  else if (key == WLBM_OPT_BF16_WIDE) *value = b->wide;
   else return WLBM_ERR_INVALID_ARG;
   return WLBM_OK;
 }
@@ -1981,6 +1999,14 @@ wlbm_status wlbm_batch_set_option(wlbm_batch* b, int32_t key, int64_t value) {
   if (key == WLBM_OPT_FUSE_PERIODIC && (value == 0 || value == 1)) {
     b->fuse_periodic = int(value);
     b->classify();
+    b->drop_graph();
+    return WLBM_OK;
+  }
+  if (key == WLBM_OPT_BF16_WIDE && (value == 0 || value == 1)) {
+    if (value == 1 && !b->all_tmap_w)
+      return b->fail(WLBM_ERR_INVALID_ARG, "wlbm_batch_set_option: wide tiles need bfloat16 "
+                                           "storage and a word tensor map of every instance");
+    b->wide = int(value);
     b->drop_graph();
     return WLBM_OK;
   }
@@ -2103,7 +2129,10 @@ static wlbm_status batch_enqueue(wlbm_batch* b, int count, int every,
       st = b->cuda(record_event(e0, b->stream, cap != nullptr), "profiling");
     }
     if (st == WLBM_OK)
-      st = b->cuda(b->variant == 3
+      st = b->cuda(b->variant == 3 && b->wide
+                       ? launch_step_tma_batch_wide(b->d_inst, n, b->max_q, b->total_tiles_w, t,
+                                                    b->stream)
+                   : b->variant == 3
                        ? launch_step_tma_batch(b->storage, b->d_inst, n, b->max_q,
                                                b->total_tiles, t, b->stream)
                        : launch_step_batch(b->storage, b->variant, b->d_inst, n, b->total_tiles,
@@ -2151,6 +2180,7 @@ wlbm_status wlbm_batch_step(wlbm_batch* b, int64_t n) {
       I.codes = b->d_codes + b->code_off[k];
       I.order = b->d_order + b->order_off[k];
       I.tmap = b->d_tmaps + size_t(k) * 128;
+      I.tmap_w = b->d_tmaps_w ? b->d_tmaps_w + size_t(k) * 128 : nullptr;
       I.n_e = x->bf16() ? 3 : 2;
       I.phase = x->e_cur;
       BatchWalls& Wk = b->h_walls[k];

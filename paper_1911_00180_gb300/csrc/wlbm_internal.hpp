@@ -285,6 +285,11 @@ struct BatchInst {
   const void* tmap;       // variant 3: device address of the instance's CUtensorMap
   int n_tiles;            // step-kernel tiles of this instance
   int first_item;         // persistent kernel: first item of this instance within a step
+  // bfloat16 256-column tiles (per-step launches with WLBM_OPT_BF16_WIDE): tiles per row,
+  // first block in that batched grid, first column of the first tile, and the device
+  // address of the instance's 32-bit-word tensor map
+  int tiles_x_w, first_tile_w, cbase_w;
+  const void* tmap_w;
 };
 
 struct BatchWalls {
@@ -395,6 +400,12 @@ bool make_box_tensor_map(void* out, void* planes, int storage, const Geom& g, in
 // bfloat16 planes as 32-bit words with the wide-tile kernel's box (136 words x 14 rows).
 bool make_word_tensor_map(void* out, void* planes, const Geom& g, int nplanes,
                           std::string* why);
+// 256-column tiles of a variant-3 step whose covered cells tma_cover set in `cover`: the
+// first column of the first tile and the tiles per row.
+void tma_cover_wide(const StepArgs& cover, int* cbase, int* tiles_x);
+// One step of every instance of a batch in 256-column bfloat16 tiles (total_tiles of them).
+cudaError_t launch_step_tma_batch_wide(const BatchInst* insts, int n, int max_q,
+                                       int total_tiles, int t, cudaStream_t s);
 // Reverse step with TMA tiles (float32): lam_map describes the q planes of a.lam_in with
 // boxes of kAdjTmaBoxRows rows (paused directions with a vertical hop component read both x
 // and x + c_k), lam_map14 the same planes with boxes of kAdjTmaRows rows (propagating

@@ -106,6 +106,36 @@ def test_batch_equals_single_grids_bitwise(storage, variant, graph, fuse):
         assert np.array_equal(_state(spec, got[k]), _state(spec, want)), k
 
 
+def test_batch_wide_tiles_equal_128_column_tiles_bitwise():
+    """bfloat16 batches step in 256-column tiles by default; with WLBM_OPT_BF16_WIDE = 0 they
+    take the 128-column cell-tile form: the same states bit for bit.  float32 batches refuse
+    the option."""
+    import torch
+    import paper_1911_00180_gb300 as wl
+    specs = _specs()
+    dTs = _dTs(specs)
+    stream = torch.cuda.Stream()
+    out = []
+    with torch.cuda.stream(stream):
+        for wide in (1, 0):
+            b = wl.WormLBMBatch(specs, storage=1, stream=stream)
+            assert b.wlbm_batch_get_option(wl.wlbm.OPT_BF16_WIDE) == 1
+            b.wlbm_batch_set_option(wl.wlbm.OPT_BF16_WIDE, wide)
+            b.wlbm_batch_set_option(wl.wlbm.OPT_GRAPH_STEPS, 12)
+            b.wlbm_batch_init_temperature(dTs)
+            b.wlbm_batch_step(31)
+            b.wlbm_batch_check()
+            out.append([v.wlbm_get_state().cpu().numpy() for v in b.instances])
+            b.close()
+        b = wl.WormLBMBatch(specs, storage=0, stream=stream)
+        assert b.wlbm_batch_get_option(wl.wlbm.OPT_BF16_WIDE) == 0
+        with pytest.raises(Exception):
+            b.wlbm_batch_set_option(wl.wlbm.OPT_BF16_WIDE, 1)
+        b.close()
+    for k, spec in enumerate(specs):
+        assert np.array_equal(_state(spec, out[0][k]), _state(spec, out[1][k])), k
+
+
 def test_batch_autotune_then_run():
     import paper_1911_00180_gb300 as wl
     from paper_1911_00180_gb300 import autotune
