@@ -393,9 +393,10 @@ wlbm_status wlbm_autotune(wlbm_handle* h, int32_t trial_steps, int32_t* variant,
  *   WLBM_OPT_PERSISTENT    0 (default): one wall launch and one step launch per step; 1:
  *                          one persistent launch per chunk of steps (64, or the
  *                          WLBM_OPT_GRAPH_STEPS of a replayed graph) on a fixed grid of
- *                          resident blocks that take the wall chunks and step tiles of
- *                          every instance and step from a queue, each item waiting only
- *                          for the items of its own instance it reads (results equal the
+ *                          resident blocks that take, step by step, the wall chunks of
+ *                          every instance and then the step tiles of every instance from a
+ *                          queue, each item waiting only for the items of its own instance
+ *                          it reads (results equal the
  *                          per-step launches of variant 3 bit for bit).  Needs variant 3
  *                          and no instance with a periodic axis (WLBM_ERR_INVALID_ARG).
  *                          Profiling then times whole launches: wlbm_batch_profile_read

@@ -3,16 +3,16 @@
 //
 // Many uncoupled gray problems (Sec. 2.1: the multigray approach solves one gray BTE per
 // band; a batch also holds films of other sizes, Knudsen numbers and Q) share the GPU.
-// A block takes work items from a queue in a fixed order: for every step t of the chunk
-// and every instance in turn, the instance's wall chunks (Sec. 2.6 on the ghost frame of
-// state t), then its step tiles (Eq. lbm-energy / Eq. algorithm, the same tile code as
+// A block takes work items from a queue in a fixed order: for every step t of the chunk,
+// the wall chunks of every instance (Sec. 2.6 on the ghost frame of state t), then the
+// step tiles of every instance (Eq. lbm-energy / Eq. algorithm, the same tile code as
 // the other variant-3 kernels, so results are bit for bit those of the launch-per-step
 // form).  Instead of a grid-wide barrier between the passes, every item waits only for
 // what it reads: a wall chunk of instance k at step t for all of k's tiles of step t - 1,
 // a tile for all of k's wall chunks of step t and all of k's tiles of step t - 1 (the
-// energy planes rotate, so a tile also overwrites what those tiles read).  Instance by
-// instance, a wall chunk finds its instance's previous step long done, and a tile waits at
-// most for the wall chunks claimed just before it.  Items are claimed in queue order and
+// energy planes rotate, so a tile also overwrites what those tiles read).  A tile's wall
+// chunks were queued a whole wall pass earlier, and a wall chunk's tiles of the previous
+// step a whole tile pass earlier, so waits are rare.  Items are claimed in queue order and
 // depend only on earlier items, which running blocks hold, so the waits always end; each
 // is still bounded in time, and a wait that gives up sets the instance's status word and an
 // abort flag that makes every block leave.  Waits happen only between items, when no
@@ -107,17 +107,21 @@ __global__ void __launch_bounds__(kPersistThreads, persist_min_blocks<T>())
       if (item < total && *reinterpret_cast<const volatile int*>(p.abort_flag) == 0) {
         const int t = item / per_step;
         const int r = item - t * per_step;
-        int lo = 0, hi = p.n - 1;                 // instance: the last first_item <= r
+        // a step's items: the wall chunks of every instance, then the tiles of every
+        // instance (instance: the last first_block / first_tile <= the item's offset)
+        const bool wall = r < p.wall_items;
+        const int rr = wall ? r : r - p.wall_items;
+        int lo = 0, hi = p.n - 1;
         while (lo < hi) {
           const int mid = (lo + hi + 1) >> 1;
-          if (p.insts[mid].first_item <= r) lo = mid;
+          if ((wall ? p.walls[mid].first_block : p.insts[mid].first_tile) <= rr) lo = mid;
           else hi = mid - 1;
         }
         const int k = lo;
-        const int local = r - p.insts[k].first_item;
+        const int local = rr - (wall ? p.walls[k].first_block : p.insts[k].first_tile);
         const int nwall = p.walls[k].n_blocks;
         bool ok;
-        if (local < nwall) {
+        if (wall) {
           ok = wait_count(done_t + k, unsigned(t) * unsigned(p.insts[k].n_tiles), p.abort_flag,
                           p.wait_limit);
           kind = 0;
@@ -129,7 +133,7 @@ __global__ void __launch_bounds__(kPersistThreads, persist_min_blocks<T>())
                wait_count(done_t + k, unsigned(t) * unsigned(p.insts[k].n_tiles), p.abort_flag,
                           p.wait_limit);
           kind = 1;
-          ps.local = local - nwall;
+          ps.local = local;
         }
         if (!ok) {
           atomicOr(p.insts[k].a.status, 1);

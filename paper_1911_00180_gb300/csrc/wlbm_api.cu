@@ -1783,7 +1783,6 @@ struct wlbm_batch {
     total_tiles = 0;
     total_tiles_w = 0;
     total_wall_blocks = 0;
-    int items = 0;
     const int tw = step_tile_width(storage, variant);
     for (size_t k = 0; k < h.size(); ++k) {
       const Geom& g = h[k]->g;
@@ -1805,8 +1804,6 @@ struct wlbm_batch {
       h_walls[k].first_block = total_wall_blocks;
       h_walls[k].n_blocks = wall_blocks(h[k]->walls);
       total_wall_blocks += h_walls[k].n_blocks;
-      h_inst[k].first_item = items;
-      items += h_walls[k].n_blocks + tx * ty;
     }
   }
 };

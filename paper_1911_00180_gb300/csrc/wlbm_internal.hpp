@@ -284,7 +284,6 @@ struct BatchInst {
   const uint16_t* order;  // variant 3: kind-sorted directions of the chunk, [t][q + 17]
   const void* tmap;       // variant 3: device address of the instance's CUtensorMap
   int n_tiles;            // step-kernel tiles of this instance
-  int first_item;         // persistent kernel: first item of this instance within a step
   // bfloat16 256-column tiles (per-step launches with WLBM_OPT_BF16_WIDE): tiles per row,
   // first block in that batched grid, first column of the first tile, and the device
   // address of the instance's 32-bit-word tensor map
@@ -302,8 +301,9 @@ struct BatchWalls {
 };
 
 // Persistent batched kernel (variant 3 tiles and the wall pass in one launch for a chunk
-// of steps): its work items are, for every step t of the chunk and every instance k in
-// turn, the wall chunks of k, then the step tiles of k, taken in that order from a queue.
+// of steps): its work items are, for every step t of the chunk, the wall chunks of every
+// instance (in instance order), then the step tiles of every instance, taken in that order
+// from a queue.
 // A wall chunk of instance k at step t waits until every tile of k's step t - 1 is done; a
 // tile waits until every wall chunk of k's step t is done (and every tile of step t - 1).
 struct PersistArgs {
