@@ -108,16 +108,10 @@ __global__ void __launch_bounds__(kPersistThreads, persist_min_blocks<T>())
         const int t = item / per_step;
         const int r = item - t * per_step;
         // a step's items: the wall chunks of every instance, then the tiles of every
-        // instance (instance: the last first_block / first_tile <= the item's offset)
+        // instance (their instances from host-built tables: one load each)
         const bool wall = r < p.wall_items;
         const int rr = wall ? r : r - p.wall_items;
-        int lo = 0, hi = p.n - 1;
-        while (lo < hi) {
-          const int mid = (lo + hi + 1) >> 1;
-          if ((wall ? p.walls[mid].first_block : p.insts[mid].first_tile) <= rr) lo = mid;
-          else hi = mid - 1;
-        }
-        const int k = lo;
+        const int k = wall ? p.wall_inst[rr] : p.tile_inst[rr];
         const int local = rr - (wall ? p.walls[k].first_block : p.insts[k].first_tile);
         const int nwall = p.walls[k].n_blocks;
         bool ok;

@@ -70,24 +70,18 @@ __global__ void __launch_bounds__(kWThreads, 2)
   step_tma_tile_wide<S, FIELD_W>(a, &tmap, cbase, int(blockIdx.x), int(blockIdx.y), smem);
 }
 
-// Batched wide-tile form: block b belongs to the instance whose first_tile_w is the
-// largest one <= b; the instance's word tensor map sits in global memory.
+// Batched wide-tile form: block b belongs to instance tile_inst[b]; the instance's word
+// tensor map sits in global memory.
 template <int S>
 __global__ void __launch_bounds__(kWThreads, 2)
-    k_step_tma_batch_wide(const BatchInst* insts, int n, int t) {
+    k_step_tma_batch_wide(const BatchInst* insts, const int* tile_inst, int t) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ StepArgs sa;
   __shared__ const void* tm;
   __shared__ int tile[3];
   if (threadIdx.x == 0 && threadIdx.y == 0) {
-    int lo = 0, hi = n - 1;
     const int b = int(blockIdx.x);
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (insts[mid].first_tile_w <= b) lo = mid;
-      else hi = mid - 1;
-    }
-    const BatchInst& I = insts[lo];
+    const BatchInst& I = insts[tile_inst[b]];
     sa = I.a;
     sa.codes = I.codes + size_t(t) * I.a.q;
     sa.order = I.order + size_t(t) * (I.a.q + 17);
@@ -122,23 +116,19 @@ __global__ void __launch_bounds__(32 * (kWarps3 + 1), loop_min_blocks<T>())
   step_tma_loop<T, S, FIELD_W, REF>(a, &tmap, tiles_x, ntiles, smem, &fail);
 }
 
-// Batched form: block b belongs to the instance whose first_tile is the largest one <= b;
-// the instance's tensor map sits in global memory.
+// Batched form: block b belongs to instance tile_inst[b] (a host-built table: one load
+// where a search over the instances' first tiles would take a chain of them); the
+// instance's tensor map sits in global memory.
 template <typename T, int S, bool REF>
-__global__ void __maxnreg__(128) k_step_tma_batch(const BatchInst* insts, int n, int t) {
+__global__ void __maxnreg__(128) k_step_tma_batch(const BatchInst* insts, const int* tile_inst,
+                                                  int t) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ StepArgs sa;
   __shared__ const void* tm;
   __shared__ int tile[2];
   if (threadIdx.x == 0 && threadIdx.y == 0) {
-    int lo = 0, hi = n - 1;
     const int b = int(blockIdx.x);
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (insts[mid].first_tile <= b) lo = mid;
-      else hi = mid - 1;
-    }
-    const BatchInst& I = insts[lo];
+    const BatchInst& I = insts[tile_inst[b]];
     sa = I.a;
     sa.codes = I.codes + size_t(t) * I.a.q;
     sa.order = I.order + size_t(t) * (I.a.q + 17);
@@ -279,10 +269,10 @@ cudaError_t configure_wide_t() {
 int wide_cbase(const StepArgs& a) { return a.cmin < kX0 ? kX0 - 8 : kX0; }
 
 template <int S>
-cudaError_t launch_batch_wide_t(const BatchInst* insts, int n, int max_q, int total_tiles, int t,
-                                cudaStream_t s) {
+cudaError_t launch_batch_wide_t(const BatchInst* insts, const int* tile_inst, int max_q,
+                                int total_tiles, int t, cudaStream_t s) {
   k_step_tma_batch_wide<S><<<total_tiles, dim3(32, kWWarps + 1), WideLayout<S>::bytes(max_q),
-                             s>>>(insts, n, t);
+                             s>>>(insts, tile_inst, t);
   return cudaGetLastError();
 }
 
@@ -310,17 +300,20 @@ cudaError_t configure_step_tma() {
   return e;
 }
 
-cudaError_t launch_step_tma_batch(int storage, const BatchInst* insts, int n, int max_q,
+cudaError_t launch_step_tma_batch(int storage, const BatchInst* insts,
+                                  const int* tile_inst, int n, int max_q,
                                   int total_tiles, int t, cudaStream_t s) {
+  (void)n;
   if (total_tiles <= 0) return cudaSuccess;
   const dim3 block(32, kWarps3 + 1);
   if (storage == WLBM_STORE_BF16_DEV) {
     using LY = TmaLayout<__nv_bfloat16, kStagesBF16>;
     k_step_tma_batch<__nv_bfloat16, kStagesBF16, true>
-        <<<total_tiles, block, LY::bytes(max_q), s>>>(insts, n, t);
+        <<<total_tiles, block, LY::bytes(max_q), s>>>(insts, tile_inst, t);
   } else {
     using LY = TmaLayout<float, kStagesF32>;
-    k_step_tma_batch<float, kStagesF32, false><<<total_tiles, block, LY::bytes(max_q), s>>>(insts, n, t);
+    k_step_tma_batch<float, kStagesF32, false>
+        <<<total_tiles, block, LY::bytes(max_q), s>>>(insts, tile_inst, t);
   }
   return cudaGetLastError();
 }
@@ -330,12 +323,14 @@ void tma_cover_wide(const StepArgs& cover, int* cbase, int* tiles_x) {
   *tiles_x = (cover.cmax - *cbase) / kWTW + 1;
 }
 
-cudaError_t launch_step_tma_batch_wide(const BatchInst* insts, int n, int max_q,
-                                       int total_tiles, int t, cudaStream_t s) {
+cudaError_t launch_step_tma_batch_wide(const BatchInst* insts, const int* tile_inst, int n,
+                                       int max_q, int total_tiles, int t, cudaStream_t s) {
+  (void)n;
   if (total_tiles <= 0) return cudaSuccess;
   return max_q <= kDeepMaxQ
-             ? launch_batch_wide_t<kStagesBF16Wide>(insts, n, max_q, total_tiles, t, s)
-             : launch_batch_wide_t<kStagesBF16WideHighQ>(insts, n, max_q, total_tiles, t, s);
+             ? launch_batch_wide_t<kStagesBF16Wide>(insts, tile_inst, max_q, total_tiles, t, s)
+             : launch_batch_wide_t<kStagesBF16WideHighQ>(insts, tile_inst, max_q, total_tiles,
+                                                          t, s);
 }
 
 int tma_tile_width() { return kTW3; }

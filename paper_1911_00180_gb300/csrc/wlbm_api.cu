@@ -1663,6 +1663,10 @@ struct wlbm_batch {
   BatchInst* d_inst = nullptr;
   BatchWalls* d_walls = nullptr;
   int* d_wall_inst = nullptr;   // [total_wall_blocks] instance of every wall block
+  int* d_tile_inst = nullptr;   // [total_tiles] instance of every variant-3 step tile
+  int* d_tile_inst_w = nullptr; // [total_tiles_w] the same for 256-column tiles
+  int tile_inst_cap = 0, tile_inst_w_cap = 0;
+  bool tables_ok = true;        // the tables match the layout (uploaded by layout())
   uint8_t* d_codes = nullptr;
   uint16_t* d_order = nullptr;      // [instance][t][q + 17] kind-sorted directions
   unsigned char* d_tmaps = nullptr; // [instance] 128-byte CUtensorMaps (variant 3)
@@ -1805,6 +1809,38 @@ struct wlbm_batch {
       h_walls[k].n_blocks = wall_blocks(h[k]->walls);
       total_wall_blocks += h_walls[k].n_blocks;
     }
+    if (variant == 3) upload_tile_tables();
+  }
+  // Block -> instance tables of the variant-3 batched step kernels (both tilings); the
+  // device buffers are sized on the first call and the stream is drained before they are
+  // rewritten.
+  void upload_tile_tables() {
+    std::vector<int> ti(static_cast<size_t>(total_tiles)), tw(static_cast<size_t>(total_tiles_w));
+    for (size_t k = 0; k < h.size(); ++k) {
+      const int n1 = h_inst[k].n_tiles;
+      for (int j = 0; j < n1; ++j) ti[size_t(h_inst[k].first_tile + j)] = int(k);
+      const int n2 = (k + 1 < h.size() ? h_inst[k + 1].first_tile_w : total_tiles_w) -
+                     h_inst[k].first_tile_w;
+      for (int j = 0; j < n2; ++j) tw[size_t(h_inst[k].first_tile_w + j)] = int(k);
+    }
+    tables_ok = false;
+    if (total_tiles > tile_inst_cap) {
+      d_tile_inst = static_cast<int*>(dev_alloc(ti.size() * sizeof(int)));
+      tile_inst_cap = d_tile_inst ? total_tiles : 0;
+    }
+    if (total_tiles_w > tile_inst_w_cap) {
+      d_tile_inst_w = static_cast<int*>(dev_alloc(tw.size() * sizeof(int)));
+      tile_inst_w_cap = d_tile_inst_w ? total_tiles_w : 0;
+    }
+    if (!d_tile_inst || (total_tiles_w > 0 && !d_tile_inst_w)) return;
+    if (stream && cudaStreamSynchronize(stream) != cudaSuccess) return;
+    if (cudaMemcpy(d_tile_inst, ti.data(), ti.size() * sizeof(int), cudaMemcpyHostToDevice) !=
+        cudaSuccess)
+      return;
+    if (!tw.empty() && cudaMemcpy(d_tile_inst_w, tw.data(), tw.size() * sizeof(int),
+                                  cudaMemcpyHostToDevice) != cudaSuccess)
+      return;
+    tables_ok = true;
   }
 };
 
@@ -1902,6 +1938,10 @@ wlbm_status wlbm_batch_create(int32_t n, const wlbm_grid* grids, const float* co
   b->wide = b->all_tmap_w ? 1 : 0;
   std::memset(b->h_walls, 0, sizeof(BatchWalls) * n);
   b->layout();
+  if (!b->tables_ok) {
+    cudaGetLastError();
+    return bad(WLBM_ERR_CUDA, "wlbm_batch_create: upload of the tile tables failed");
+  }
   *out = b;
   return WLBM_OK;
 }
@@ -1961,6 +2001,10 @@ wlbm_status wlbm_batch_set_option(wlbm_batch* b, int32_t key, int64_t value) {
     b->layout();
     b->classify();
     b->drop_graph();
+    if (!b->tables_ok) {
+      cudaGetLastError();
+      return b->fail(WLBM_ERR_CUDA, "wlbm_batch_set_option: upload of the tile tables failed");
+    }
     return WLBM_OK;
   }
   if (key == WLBM_OPT_PERSISTENT && (value == 0 || value == 1)) {
@@ -2037,6 +2081,8 @@ static wlbm_status batch_enqueue(wlbm_batch* b, int count, int every,
     PersistArgs p{};
     p.insts = b->d_inst;
     p.walls = b->d_walls;
+    p.wall_inst = b->d_wall_inst;
+    p.tile_inst = b->d_tile_inst;
     p.n = n;
     p.wall_items = b->total_wall_blocks;
     p.tile_items = b->total_tiles;
@@ -2127,11 +2173,11 @@ static wlbm_status batch_enqueue(wlbm_batch* b, int count, int every,
     }
     if (st == WLBM_OK)
       st = b->cuda(b->variant == 3 && b->wide
-                       ? launch_step_tma_batch_wide(b->d_inst, n, b->max_q, b->total_tiles_w, t,
-                                                    b->stream)
+                       ? launch_step_tma_batch_wide(b->d_inst, b->d_tile_inst_w, n, b->max_q,
+                                                    b->total_tiles_w, t, b->stream)
                    : b->variant == 3
-                       ? launch_step_tma_batch(b->storage, b->d_inst, n, b->max_q,
-                                               b->total_tiles, t, b->stream)
+                       ? launch_step_tma_batch(b->storage, b->d_inst, b->d_tile_inst, n,
+                                               b->max_q, b->total_tiles, t, b->stream)
                        : launch_step_batch(b->storage, b->variant, b->d_inst, n, b->total_tiles,
                                            t, b->stream),
                    "wlbm_batch_step: step");

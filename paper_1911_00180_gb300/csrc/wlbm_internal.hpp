@@ -309,6 +309,8 @@ struct BatchWalls {
 struct PersistArgs {
   const BatchInst* insts;
   const BatchWalls* walls;
+  const int* wall_inst;   // [wall_items] instance of every wall chunk of a step
+  const int* tile_inst;   // [tile_items] instance of every step tile of a step
   int n;                  // instances
   int wall_items, tile_items;   // per step
   int steps;              // steps of this launch (codes of steps 0 .. steps-1 of the chunk)
@@ -385,7 +387,8 @@ cudaError_t launch_step_tma(int storage, const StepArgs& a, cudaStream_t s);
 bool step_tma_stages_ok(int storage, int stages);
 int step_tma_loop_blocks(int storage, int stages, bool field_w, int q);
 // Batched variant 3 (one block per 128 x 14 tile of every instance) and its tile shape.
-cudaError_t launch_step_tma_batch(int storage, const BatchInst* insts, int n, int max_q,
+cudaError_t launch_step_tma_batch(int storage, const BatchInst* insts,
+                                  const int* tile_inst, int n, int max_q,
                                   int total_tiles, int t, cudaStream_t s);
 int tma_tile_width();
 int tma_tile_rows();
@@ -404,8 +407,8 @@ bool make_word_tensor_map(void* out, void* planes, const Geom& g, int nplanes,
 // first column of the first tile and the tiles per row.
 void tma_cover_wide(const StepArgs& cover, int* cbase, int* tiles_x);
 // One step of every instance of a batch in 256-column bfloat16 tiles (total_tiles of them).
-cudaError_t launch_step_tma_batch_wide(const BatchInst* insts, int n, int max_q,
-                                       int total_tiles, int t, cudaStream_t s);
+cudaError_t launch_step_tma_batch_wide(const BatchInst* insts, const int* tile_inst, int n,
+                                       int max_q, int total_tiles, int t, cudaStream_t s);
 // Reverse step with TMA tiles (float32): lam_map describes the q planes of a.lam_in with
 // boxes of kAdjTmaBoxRows rows (paused directions with a vertical hop component read both x
 // and x + c_k), lam_map14 the same planes with boxes of kAdjTmaRows rows (propagating
