@@ -231,8 +231,11 @@ wlbm_status wlbm_set_sources(wlbm_handle* h, int32_t n, const int32_t* xy, const
  *              nx, ny, Q, storage and wall kinds (WLBM_ERR_INVALID_ARG otherwise, or for a
  *              truncated or corrupt header).  The handle's MFP field, wall temperatures and
  *              options are its own: load into a handle created with the same arguments.
- *              Clears the residual snapshot of wlbm_reduce and any adjoint forward run.
- *              Synchronous.  Handles owned by a batch are not supported. */
+ *              Only the frame of each plane is read from src (rows 1 .. ny+2 of the
+ *              framed rows, the nx+2 framed columns): the pads of the library's planes
+ *              stay zero whatever src holds there.  Clears the residual snapshot of
+ *              wlbm_reduce and any adjoint forward run.  Synchronous.  Handles owned by a
+ *              batch are not supported. */
 wlbm_status wlbm_save(wlbm_handle* h, void* dst, size_t capacity, size_t* written);
 wlbm_status wlbm_load(wlbm_handle* h, const void* src, size_t size);
 

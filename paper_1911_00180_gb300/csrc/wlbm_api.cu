@@ -1336,20 +1336,25 @@ wlbm_status wlbm_load(wlbm_handle* h, const void* src, size_t size) {
   h->adj.ready = false;
   const unsigned char* p = in + ckpt_cursor_bytes(g.q);
   unsigned char* planes = static_cast<unsigned char*>(h->planes);
+  // Only the frame of each plane (rows 1 .. ny + 2, columns kGhostCol .. kX0 + nx) is
+  // copied: the pads stay zero whatever the buffer holds there (the kernels that read a
+  // pad from memory, instead of a tensor copy's zero fill, rely on that).
+  auto copy_frame = [&](void* dst, const unsigned char* src, size_t elem) {
+    const size_t pitch = size_t(g.pitch) * elem, off = pitch + size_t(kGhostCol) * elem;
+    return h->cuda(cudaMemcpy2DAsync(static_cast<unsigned char*>(dst) + off, pitch, src + off,
+                                     pitch, size_t(g.nx + 2) * elem, size_t(g.ny + 2),
+                                     cudaMemcpyHostToDevice, h->stream),
+                   "wlbm_load");
+  };
   wlbm_status st = WLBM_OK;
   for (int i = 0; i < g.q && st == WLBM_OK; ++i) {
     const size_t dst = (size_t(h->tas.parity[i]) * g.q + i) * size_t(hd.plane_bytes);
-    st = h->cuda(cudaMemcpyAsync(planes + dst, p, size_t(hd.plane_bytes), cudaMemcpyHostToDevice,
-                                 h->stream), "wlbm_load");
+    st = copy_frame(planes + dst, p, h->elem());
     p += hd.plane_bytes;
   }
-  if (st == WLBM_OK)
-    st = h->cuda(cudaMemcpyAsync(h->e[h->e_cur], p, size_t(hd.energy_bytes),
-                                 cudaMemcpyHostToDevice, h->stream), "wlbm_load");
+  if (st == WLBM_OK) st = copy_frame(h->e[h->e_cur], p, 4);
   p += hd.energy_bytes;
-  if (st == WLBM_OK && h->e_ref >= 0)
-    st = h->cuda(cudaMemcpyAsync(h->e[h->e_ref], p, size_t(hd.energy_bytes),
-                                 cudaMemcpyHostToDevice, h->stream), "wlbm_load");
+  if (st == WLBM_OK && h->e_ref >= 0) st = copy_frame(h->e[h->e_ref], p, 4);
   if (st == WLBM_OK) st = h->cuda(cudaStreamSynchronize(h->stream), "wlbm_load");
   return st;
 }

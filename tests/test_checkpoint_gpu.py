@@ -68,6 +68,46 @@ def test_resume_is_bitwise(name, cfg, storage):
     h.close()
 
 
+@pytest.mark.parametrize("storage", [0, 1])
+def test_load_keeps_pads_zero(storage):
+    """A checkpoint whose pad bytes (the columns left of the ghost column and right of the
+    right ghost column, the rows outside the frame) hold garbage loads and steps bit for
+    bit like the clean one: wlbm_load copies only the frame.  Diffuse x walls put computed
+    ghost columns next to the pads: the first box of a row reads pad columns from memory,
+    and with an even width the bfloat16 256-column tiles read the first pad right of the
+    right ghost column from memory too."""
+    nx, ny, q = 150, 37, 32
+    cfg = dict(nx=nx, ny=ny, q=q, mfp=4.0, bc=(A, A, I, A), t_wall=(300.0, 300.0, 300.6, 300.0),
+               emulate_3d=True, dT=W.random_dT(nx, ny, seed=5, scale=0.5))
+    h = gpu_handle(cfg, storage)
+    h.wlbm_init_temperature(cfg["dT"])
+    h.wlbm_step(13)
+    blob = h.wlbm_save().copy()
+    h.wlbm_step(20)
+    want = _snapshot(h)
+    h.close()
+    # blob layout: 104-byte header (pitch at byte 28, plane and energy bytes at 72 and 80),
+    # the schedule cursor, then q planes and the energy planes, each (ny + 4) x pitch
+    pitch = int(blob[28:32].view(np.int32)[0])
+    plane_bytes, energy_bytes = (int(v) for v in blob[72:88].view(np.int64))
+    elem = plane_bytes // ((ny + 4) * pitch)
+    off = 104 + q * 24 + ((q + 7) // 8) * 8
+    frame = np.zeros((ny + 4, pitch), bool)
+    frame[1:ny + 3, 31:31 + nx + 2] = True
+    rng = np.random.default_rng(3)
+    bad = blob.copy()
+    for size, e in [(plane_bytes, elem)] * q + [(energy_bytes, 4)] * (2 if storage else 1):
+        region = bad[off:off + size].reshape(ny + 4, pitch, e)
+        region[~frame] = rng.integers(1, 255, size=(int((~frame).sum()), e), dtype=np.uint8)
+        off += size
+    assert off == bad.size
+    g = gpu_handle(cfg, storage)
+    g.wlbm_load(bad)
+    g.wlbm_step(20)
+    _same(_snapshot(g), want)
+    g.close()
+
+
 def test_resume_under_graph_replay():
     """Graph replay needs a stream of its own (not the legacy default stream): both
     handles run on one, so their 12-step chunks are captured graphs."""
