@@ -3,7 +3,7 @@
 // step kernel k_step_tma:
 //   * one producer thread per block issues, for direction k, a tensor box of the output
 //     adjoint's plane k and a 14 x 128 box (no column halo) of plane k of the recorded step
-//     input d~, into one stage of a 4-stage ring (full/empty mbarriers, bounded waits).  A
+//     input d~, into one stage of a 6-stage ring (full/empty mbarriers, bounded waits).  A
 //     propagating direction reads only l'(x + c_k): its adjoint box is the tile's 14 rows
 //     shifted by c_k's row; a paused one also reads l'(x): its box is the tile's 14 rows
 //     and, for a hop with a vertical component, the one row beyond them on c_k's side (15
@@ -32,7 +32,8 @@ constexpr int kATW = 128;                  // columns per tile
 constexpr int kAV = 4;                     // floats per 16 bytes
 constexpr int kABW = kATW + 2 * kAV;       // box width
 constexpr int kAC0 = kGhostCol & ~3;       // first column of the first tile
-constexpr int kAS = 4;                     // ring stages
+constexpr int kAS = 6;                     // ring stages (swept: 4, 6, 8 stages took the
+                                           // 1000-step backward pass 283.7, 278.7, 288.1 ms)
 constexpr uint32_t kBoxL = uint32_t(kAdjTmaBoxRows) * kABW * 4;   // adjoint box (paused)
 constexpr uint32_t kBoxL14 = uint32_t(kAdjTmaRows) * kABW * 4;    // adjoint box (14 rows)
 constexpr uint32_t kBoxLSlot = (kBoxL + 127) / 128 * 128;         // tape box offset
