@@ -54,7 +54,8 @@ enum {
 };
 
 typedef struct wlbm_grid {
-  int32_t nx, ny;      /* interior cells, >= 1 each                                   */
+  int32_t nx, ny;      /* interior cells, >= 1 each; (nx+2)(ny+2) <= 2^31 - 1 and     */
+                       /* ny <= 917488 (WLBM_ERR_INVALID_ARG otherwise)               */
   int32_t q;           /* directions Q = 8M of the worm-D2Q[8M] scheme (Sec. 2.5)       */
   int32_t storage;     /* WLBM_STORE_*                                                 */
   int32_t emulate_3d;  /* 1: apply the 3/2 factor of Eq. W-correction (2D emulating 3D) */

@@ -1,5 +1,6 @@
 // C ABI of libwlbm: handle lifecycle, boundary tables, the per-step launch sequence.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -441,7 +442,10 @@ wlbm_status wlbm_create(const wlbm_grid* grid, const float* mfp_cells, double mf
   }
   *out = nullptr;
   const wlbm_grid& G = *grid;
-  if (G.nx < 1 || G.ny < 1 || int64_t(G.nx) * G.ny > (int64_t(1) << 31) ||
+  // sizes: the framed cell count indexes 32-bit thread ids of the per-cell kernels, and the
+  // step kernels put 14-row tile rows in grid.y (at most 65535 of them)
+  if (G.nx < 1 || G.ny < 1 || (int64_t(G.nx) + 2) * (int64_t(G.ny) + 2) > INT32_MAX ||
+      int64_t(G.ny) + 2 > int64_t(65535) * 14 ||
       (G.storage != WLBM_STORE_FP32_DEV && G.storage != WLBM_STORE_BF16_DEV) ||
       (G.relax_mode != 0 && G.relax_mode != 1) || !(G.t_ref > 0) || !(G.theta > 0) ||
       !(G.speed == 0.0 || (G.speed > 0.0 && G.speed <= 1.0))) {

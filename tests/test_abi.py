@@ -83,6 +83,16 @@ def test_create_rejects_empty_grids_and_out_of_range_q(wl, nx, ny, q):
     assert not h.value
 
 
+def test_create_size_limits(wl):
+    """The framed cell count must fit the per-cell kernels' 32-bit thread ids and the tile
+    rows the step kernels' grid.y: just past either limit the call is refused before any
+    allocation; just inside it asks for memory (the test allocator has none: OOM)."""
+    assert _create(wl, nx=46340, ny=46340)[0] == wl.wlbm.WLBM_ERR_INVALID_ARG
+    assert _create(wl, nx=46338, ny=46338)[0] == wl.wlbm.WLBM_ERR_OOM
+    assert _create(wl, nx=1, ny=917489)[0] == wl.wlbm.WLBM_ERR_INVALID_ARG
+    assert _create(wl, nx=1, ny=917488)[0] == wl.wlbm.WLBM_ERR_OOM
+
+
 def test_batch_create_rejects_empty_batches_and_null_arguments(wl):
     """A batch of no instances, or without grids, boundaries or MFP, is refused before any
     instance is created."""
